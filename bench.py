@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the CAV-multigrid-preconditioned FGMRES solve on one B300.
+
+Metric: solves/s to a 1e-10 relative residual (||r||/||b||), one step = one FGMRES solve
+of the elliptic-membrane system on a built hierarchy (the whole hot path: residuals,
+patch gathers, batched patch-inverse applies, weighted scatters, transfers, coarse solve,
+Arnoldi and Givens).  Set-up (E_E assembly, Galerkin levels, CAV sets, batched LU) is
+timed separately and reported as setup_ms and setup_plus_solve_per_s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own independently seeded system (replicas:
+the path has no exchange step); value = all solves / max over ranks of the timed span.
+`--impl reference` times the FP64 CPU oracle on the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import ib_workloads as W  # noqa: E402
+
+METRIC = "solves/s to 1e-10 rel. residual (mixed+learned vs plain FP64); sweep HBM GB/s"
+DEFAULT_NU = 2
+DEFAULT_ALPHA = 0.85
+MAXIT = 150
+
+# DRAM traffic of one finest-level patch-apply launch from the committed ncu capture
+# (profiles/patch_apply_membrane_N256.md), valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {}
+
+
+def workload(seed_offset: int = 0):
+    rec = W.config2(256, 1e4)
+    if seed_offset:
+        rec.seed += 7919 * seed_offset
+    return rec
+
+
+def workload_desc(rec) -> str:
+    return (f"elliptic membrane (semi-axes 0.3, 0.2), N={rec.N}, M={rec.M} markers, kappa_s=1e4, "
+            f"rho=1, mu=1e-2, dt=h/2, seeded uniform[-1,1] RHS")
+
+
+def kernel_hash() -> str:
+    with open(os.path.join(ROOT, "paper_2608_14310_b300", "csrc", "sweep.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(device_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(timeout_s: int = 600):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+import ib_workloads as W
+from oracle import multigrid as mg
+rec = W.config2(256, 1e4)
+t0 = time.perf_counter()
+levels = mg.build_hierarchy(rec, 8, "cav")
+t_setup = time.perf_counter() - t0
+b = rec.rhs()
+K = levels[0].KE
+t0 = time.perf_counter()
+z = mg.vcycle(levels, b, %d, %d, "additive", %r)
+y = K @ z
+t_iter = time.perf_counter() - t0
+print(json.dumps({"t_setup": t_setup, "t_iter": t_iter}))
+""" % (ROOT, DEFAULT_NU, DEFAULT_NU, DEFAULT_ALPHA)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                             timeout=timeout_s, env=env)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # pragma: no cover
+        return {"error": str(e)}
+
+
+def golden_iters():
+    p = os.path.join(ROOT, "tests", "golden", "bench_oracle_iterations.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle.multigrid as mg
+    rec = workload()
+    t0 = time.perf_counter()
+    levels = mg.build_hierarchy(rec, 8, "cav")
+    t_setup = time.perf_counter() - t0
+    b = rec.rhs()
+    K = levels[0].KE
+    g = golden_iters()
+    iters = g["iters"] if g else None
+
+    def step():
+        z = mg.vcycle(levels, b, DEFAULT_NU, DEFAULT_NU, "additive", DEFAULT_ALPHA)
+        return K @ z
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t)
+    t_iter = statistics.mean(times)
+    value = 1.0 / (t_iter * iters) if iters else None
+    sample = (f"each step = one oracle FGMRES iteration's V-cycle ({DEFAULT_NU}+{DEFAULT_NU} additive "
+              f"sweeps) plus one K_E product on the full N=256 system; solves/s = 1 / (mean step time x "
+              f"{iters} iterations, the oracle's own count from tests/golden); hierarchy set-up "
+              f"{t_setup:.1f} s untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_iter, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(rec), "nu": DEFAULT_NU, "alpha": DEFAULT_ALPHA},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--nu", type=int, default=DEFAULT_NU)
+    ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2608_14310_b300 import build
+    build.build()
+    from paper_2608_14310_b300 import api
+
+    rec = workload(rank)
+    n = 3 * rec.N * rec.N
+    dev = torch.device("cuda", local)
+    b = torch.from_numpy(rec.rhs()).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    sysm = api.ib_setup(rec)
+    hier = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision=args.precision)
+    e1.record()
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1)
+
+    def solve(bv, xv):
+        return api.fgmres_solve(sysm, hier, bv, xv, rtol=1e-10, maxit=MAXIT, history=False)
+
+    for _ in range(args.warmup):
+        x.zero_()
+        solve(b, x)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    api.cav_profile(hier, True)
+    launches0 = api.ib_launch_count()
+    times, iters, conv, relres = [], [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        x.zero_()
+        s0, s1 = ev(), ev()
+        s0.record()
+        info = solve(b, x)
+        s1.record()
+        torch.cuda.synchronize()
+        times.append(s0.elapsed_time(s1))
+        iters.append(info["iters"])
+        conv.append(info["converged"])
+        relres.append(info["relres_true"])
+    launches = api.ib_launch_count() - launches0
+    n_apply, apply_ms = api.cav_profile_read(hier)
+    api.cav_profile(hier, False)
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public call with pinned host buffers (H2D of b and x, D2H of x)
+    hb = torch.from_numpy(rec.rhs()).pin_memory()
+    hx = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        hx.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solve(hb, hx)
+        e2e_times.append(time.perf_counter() - t)
+    e2e_value = world / statistics.mean(e2e_times) if e2e_times else None
+
+    # plain FP64 inverses on the same system for the mixed-vs-plain comparison
+    plain = None
+    if args.precision != "fp64":
+        hier64 = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision="fp64")
+        for _ in range(2):
+            x.zero_()
+            api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+        pt, pit = [], []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            x.zero_()
+            s0, s1 = ev(), ev()
+            s0.record()
+            inf = api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+            s1.record()
+            torch.cuda.synchronize()
+            pt.append(s0.elapsed_time(s1))
+            pit.append(inf["iters"])
+        plain = {"value": 1e3 / statistics.mean(pt), "unit": "solves/s", "iters": int(statistics.median(pit))}
+        hier64.close()
+
+    li = api.cav_get_level_info(hier, 0)
+    s_bytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
+    alg_bytes = li["enlarged_sum_n2"] * s_bytes + li["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8)
+    peak, peak_kind = peaks()
+    achieved = (alg_bytes / (apply_ms / n_apply * 1e-3) / 1e9) if n_apply else None
+    key = f"{args.precision}:{kernel_hash()}"
+    traffic = NCU_TRAFFIC.get(key)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": workload_desc(rec), "precision": args.precision + " enlarged-patch inverses",
+                   "nu": args.nu, "alpha": args.alpha, "coarsest_N": 8, "maxit": MAXIT,
+                   "l2": "flushed (256 MB write) before every timed solve",
+                   "iters": int(statistics.median(iters)), "converged": all(conv),
+                   "relres_true_max": max(relres), "parallelism": f"replicas x{world}"},
+        "plain_fp64": plain,
+        "setup_ms": setup_ms,
+        "setup_plus_solve_per_s": world / ((setup_ms + total_ms / args.steps) / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "k_patch_apply (finest level)", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "launches_timed": n_apply,
+                     "avg_launch_us": (1e3 * apply_ms / n_apply) if n_apply else None},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
+                "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline_sample()
+        g = golden_iters()
+        it = g["iters"] if g else int(statistics.median(iters))
+        if "t_iter" in cb:
+            line["cpu_baseline"] = {
+                "value": 1.0 / (cb["t_iter"] * it), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"one oracle V-cycle ({args.nu}+{args.nu} additive sweeps) plus one K_E product on the "
+                           f"same N=256 system, {cb['t_iter']:.2f} s, scaled by {it} iterations per solve; "
+                           f"oracle hierarchy set-up {cb['t_setup']:.1f} s not timed")}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": "failed: " + cb.get("error", "?")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * ib_cav.h -- C ABI of the B300 library for coupling-aware Vanka (CAV) multigrid
+ * preconditioning of the reduced Eulerian velocity-pressure immersed-boundary system.
+ *
+ * The system (Sec. 2, Eq. Eul_schur) is K_E x = b with
+ *     K_E = [[A, G], [-D, 0]],  A = A0 - dt E_E,  A0 = (rho/dt) I - mu L,  E_E = S E J,
+ * on a periodic N x N MAC grid of [0, L)^2 with h = L / N.  Unknown vectors have length
+ * 3 N^2 and are laid out as three blocks u | v | p, entry (i, j) of a block at j N + i;
+ * u_{ij} sits at (i h, (j+1/2) h), v_{ij} at ((i+1/2) h, j h), p_{ij} at the cell centre.
+ *
+ * Conventions shared by every call
+ *   - Every call returns ib_status; nothing throws or aborts across the ABI.  On a non-OK
+ *     status ib_last_error() returns a thread-local message.
+ *   - Descriptor structs and the marker arrays they point to are HOST memory, read during
+ *     the call and not retained.
+ *   - Vectors named b, x, r, z, w, y are caller-owned DEVICE buffers of FP64 (3 N_l^2
+ *     entries on level l), unless a descriptor says otherwise.  They must not alias unless
+ *     a call says so.
+ *   - Calls are ordered on the given CUDA stream (0 = legacy default stream).  Set-up calls
+ *     and fgmres_solve synchronise that stream before returning; sweep-level calls do not.
+ *   - Handles (ib_system, cav_hierarchy) are library-owned: created by *_setup, released by
+ *     *_destroy, and hold device memory of the device current at set-up time.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef IB_CAV_H
+#define IB_CAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IB_OK = 0,
+  IB_ERR_INVALID = 1,   /* bad argument, size or descriptor field                       */
+  IB_ERR_OOM = 2,       /* device allocation failed                                       */
+  IB_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed                    */
+  IB_ERR_SINGULAR = 4,  /* a local patch matrix had a zero pivot (Sec. 3.3 factorisation)  */
+  IB_ERR_NOCONV = 5,    /* FGMRES stopped at maxit above tolerance; x holds the last iterate */
+  IB_ERR_TIMEOUT = 6,   /* reserved: a bounded device-side wait gave up                   */
+  IB_ERR_INTERNAL = 7   /* a device-side consistency check failed (e.g. a stencil window) */
+} ib_status;
+
+/* Message for the last non-OK status returned on the calling thread ("" if none). */
+const char* ib_last_error(void);
+/* ABI version of this header: 1. */
+int ib_abi_version(void);
+/* Number of kernels this library has launched in this process (host-side count). */
+int64_t ib_launch_count(void);
+
+/* ------------------------------------------------------------------ system (Sec. 2) */
+
+typedef enum { IB_FORCE_TARGET = 0, IB_FORCE_MEMBRANE = 1, IB_FORCE_BEAM = 2 } ib_force_law;
+
+typedef struct {
+  int32_t N;       /* cells per direction (>= 8; even to allow coarsening)              */
+  double L;        /* side of the periodic square                                        */
+  double rho, mu, dt;
+} ib_grid_desc;
+
+/* Force laws (Lagrangian elasticity matrix E, acting identically on x and y):
+ *   target   E = -k_target I                                  (Sec. 5.2)
+ *   membrane E = k_stretch/ds^2 * cyclic [1 -2 1]             (Eq. disc_force_law)
+ *   beam     E = k_stretch/ds^2 [1 -2 1] - k_bend/ds^4 [1 -4 6 -4 1], cyclic   (Sec. 5.2)
+ * membrane and beam require closed = 1.                                              */
+typedef struct {
+  int32_t M;             /* number of Lagrangian markers (0 allowed: no structure)      */
+  int32_t closed;        /* 1: the marker chain is a closed curve                        */
+  int32_t law;           /* ib_force_law                                                 */
+  const double* X;       /* host, 2M doubles interleaved (x0, y0, x1, y1, ...): X^n      */
+  const double* omega;   /* host, M quadrature weights omega_k                            */
+  double ds;             /* uniform Lagrangian spacing used by the force stencils         */
+  double k_target, k_stretch, k_bend;
+} ib_structure_desc;
+
+typedef struct ib_system ib_system;
+
+/* Builds S^n, J^n at X (Peskin four-point kernel), E, and E_E = S E J on the device
+ * (Sec. 2, Eq. intro_saddle).  *out receives a new handle. */
+ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* structure,
+                   cudaStream_t stream, ib_system** out);
+/* y = K_E x on the finest grid (Eq. Eul_schur). */
+ib_status ib_apply(const ib_system* sys, const double* x, double* y, cudaStream_t stream);
+/* r = b - K_E x on the finest grid. */
+ib_status ib_residual(const ib_system* sys, const double* b, const double* x, double* r,
+                      cudaStream_t stream);
+void ib_destroy(ib_system* sys);
+
+/* -------------------------------------------------------- hierarchy (Sec. 3, Sec. 4) */
+
+typedef enum { CAV_PATCH_CAV = 0, CAV_PATCH_VANKA = 1 } cav_patch_kind;
+typedef enum { CAV_PREC_FP64 = 0, CAV_PREC_FP32 = 1, CAV_PREC_BF16 = 2 } cav_precision;
+
+typedef struct {
+  int32_t kind;        /* cav_patch_kind: CAV (Eq. cav_patch_set) or standard Vanka B(1,0) */
+  int32_t coarsest_N;  /* halve while N_l / 2 >= coarsest_N (the paper uses 8)             */
+  int32_t nu_pre, nu_post;  /* sweeps per level in the V-cycle                             */
+  double alpha;        /* relaxation factor of Eq. additive_cav_saddle                     */
+  int32_t precision;   /* cav_precision of the stored enlarged-patch inverses              */
+} cav_desc;
+
+typedef struct cav_hierarchy cav_hierarchy;
+
+typedef struct {
+  int32_t N;             /* cells per direction on this level                              */
+  int32_t n_patches;     /* one patch per cell (N^2) on smoothing levels, 1 on the coarsest */
+  int32_t n_enlarged;    /* patches that are not a standard 5-unknown Vanka patch           */
+  int32_t max_n;         /* largest patch size                                              */
+  int64_t sum_n;         /* sum of patch sizes                                              */
+  int64_t sum_n2;        /* sum of squared patch sizes                                      */
+  int64_t enlarged_sum_n, enlarged_sum_n2;
+  int64_t inverse_bytes; /* bytes of stored enlarged-patch inverses (padded layout)         */
+  int64_t ee_nnz;        /* structural nonzeros of E_E on this level                        */
+  int32_t ee_rows;       /* velocity rows of E_E with at least one nonzero                  */
+  int32_t ee_window;     /* max per-axis index offset between a row and a column of E_E     */
+  int32_t is_coarsest;
+} cav_level_info;
+
+/* Builds the level hierarchy, Galerkin E_E^(l-1) = R E_E^(l) P, the patch sets and their
+ * equilibrated LU inverses (Sec. 3.2, 3.3, 4) as batched FP64 device kernels, then stores
+ * the enlarged-patch inverses in desc->precision.  Level 0 is the finest grid. */
+ib_status cav_setup(const ib_system* sys, const cav_desc* desc, cudaStream_t stream,
+                    cav_hierarchy** out);
+ib_status cav_num_levels(const cav_hierarchy* h, int32_t* levels);
+ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_info* info);
+/* Host copies of the patch sets of one smoothing level in cell order c = j N + i, each
+ * sorted ascending: offsets[n_patches + 1] (int64), dofs[sum_n] (int32).  Pass NULL
+ * arrays to query n_patches and sum_n only. */
+ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offsets,
+                           int32_t* dofs, int32_t* n_patches, int64_t* sum_n);
+/* Host copy of E_E on one level as CSR over all 2 N_l^2 velocity rows (columns sorted):
+ * rowptr[2 N_l^2 + 1], cols[nnz], vals[nnz].  NULL arrays: query *nnz only. */
+ib_status cav_ee_export(const cav_hierarchy* h, int32_t level, int64_t* rowptr,
+                        int32_t* cols, double* vals, int64_t* nnz);
+/* One weighted additive CAV sweep on level `level` (Eq. additive_cav_saddle):
+ *   r = b - K_E w;  w <- w + alpha sum_i R_i^T Theta_i K_{E,i}^{-1} R_i r;
+ *   then the mean pressure is removed (Sec. 3.3).  Theta_i = 1 / patch count per unknown.
+ * w is updated in place. */
+ib_status cav_sweep(const cav_hierarchy* h, int32_t level, const double* b, double* w,
+                    cudaStream_t stream);
+/* r = b - K_E^(l) w on level l (rediscretised Stokes part plus Galerkin E_E). */
+ib_status cav_residual(const cav_hierarchy* h, int32_t level, const double* b, const double* w,
+                       double* r, cudaStream_t stream);
+/* bc = R r: velocity by (1/4) P^T of RT0 prolongation, pressure by cell averaging (Sec. 4);
+ * r on level l, bc on level l + 1. */
+ib_status cav_restrict(const cav_hierarchy* h, int32_t level, const double* r, double* bc,
+                       cudaStream_t stream);
+/* w += P xc: RT0 velocity and bilinear pressure prolongation (Sec. 4); xc on level l + 1. */
+ib_status cav_prolong_add(const cav_hierarchy* h, int32_t level, const double* xc, double* w,
+                          cudaStream_t stream);
+/* z = bordered direct solve on the coarsest level (Sec. 4): [[K, e],[e^T, 0]] [z; l] = [r; 0]. */
+ib_status cav_coarse_solve(const cav_hierarchy* h, const double* r, double* z, cudaStream_t stream);
+/* z = B r: one V-cycle (nu_pre, nu_post sweeps per level, zero initial guess) (Sec. 4). */
+ib_status vcycle_apply(const cav_hierarchy* h, const double* r, double* z, cudaStream_t stream);
+void cav_destroy(cav_hierarchy* h);
+
+/* Live timing of the finest level's batched patch-apply launches (the sweep's dominant
+ * kernel).  enable = 1 starts recording a CUDA event pair around each such launch, on the
+ * stream it is launched on (up to 8192 launches); cav_profile_read waits for the recorded
+ * events, returns the number of launches and their summed duration in milliseconds, and
+ * clears the record.  Not part of the paper's method: instrumentation for roofline
+ * reporting. */
+ib_status cav_profile(cav_hierarchy* h, int32_t enable);
+ib_status cav_profile_read(cav_hierarchy* h, int32_t* launches, double* total_ms);
+
+/* -------------------------------------------------------------- Krylov (Sec. 5) */
+
+typedef struct {
+  double rtol;       /* stop when ||r_k||_2 <= rtol ||ref||_2                           */
+  int32_t maxit;     /* no restarts                                                      */
+  int32_t rel_to;    /* 0: ref = b, 1: ref = r_0                                         */
+  int32_t host_io;   /* 1: b and x are HOST pointers; the call copies them to and from
+                        the device inside the call                                       */
+} fgmres_desc;
+
+typedef struct {
+  int32_t iters, converged;
+  double relres_est;   /* |g_{k+1}| / ||ref|| from the Givens recurrence                  */
+  double relres_true;  /* ||b - K_E x|| / ||ref|| recomputed at exit                      */
+} fgmres_info;
+
+/* Right-preconditioned flexible GMRES with the CAV V-cycle (Sec. 5): x holds the initial
+ * guess on entry and the solution on exit.  history (host, nullable, maxit + 1 doubles)
+ * receives the relative residual estimate per iteration.  Returns IB_ERR_NOCONV when maxit
+ * is reached above tolerance (x and info still valid).  Synchronises the stream. */
+ib_status fgmres_solve(const ib_system* sys, const cav_hierarchy* h, const double* b, double* x,
+                       const fgmres_desc* desc, fgmres_info* info, double* history,
+                       cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IB_CAV_H */

@@ -1,0 +1,304 @@
+"""Thin ctypes binding of include/ib_cav.h: argument marshalling only.
+
+Device vectors are torch CUDA tensors (float64, contiguous) passed by data pointer on the
+current torch stream; descriptors are built from plain numbers and host numpy arrays.
+Every non-OK status raises IBError carrying the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcavib.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run `python -m "
+                      "paper_2608_14310_b300.build`); there is no fallback implementation")
+_lib = C.CDLL(LIB_PATH)
+
+IB_OK, IB_ERR_INVALID, IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_SINGULAR, IB_ERR_NOCONV, IB_ERR_TIMEOUT, \
+    IB_ERR_INTERNAL = range(8)
+FORCE = {"target": 0, "membrane": 1, "beam": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
+KIND = {"cav": 0, "vanka": 1}
+
+
+class IBError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.ib_last_error().decode()
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+class ib_grid_desc(C.Structure):
+    _fields_ = [("N", C.c_int32), ("L", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
+                ("dt", C.c_double)]
+
+
+class ib_structure_desc(C.Structure):
+    _fields_ = [("M", C.c_int32), ("closed", C.c_int32), ("law", C.c_int32),
+                ("X", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)), ("ds", C.c_double),
+                ("k_target", C.c_double), ("k_stretch", C.c_double), ("k_bend", C.c_double)]
+
+
+class cav_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("coarsest_N", C.c_int32), ("nu_pre", C.c_int32),
+                ("nu_post", C.c_int32), ("alpha", C.c_double), ("precision", C.c_int32)]
+
+
+class cav_level_info(C.Structure):
+    _fields_ = [("N", C.c_int32), ("n_patches", C.c_int32), ("n_enlarged", C.c_int32),
+                ("max_n", C.c_int32), ("sum_n", C.c_int64), ("sum_n2", C.c_int64),
+                ("enlarged_sum_n", C.c_int64), ("enlarged_sum_n2", C.c_int64),
+                ("inverse_bytes", C.c_int64), ("ee_nnz", C.c_int64), ("ee_rows", C.c_int32),
+                ("ee_window", C.c_int32), ("is_coarsest", C.c_int32)]
+
+
+class fgmres_desc(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("maxit", C.c_int32), ("rel_to", C.c_int32),
+                ("host_io", C.c_int32)]
+
+
+class fgmres_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("relres_est", C.c_double),
+                ("relres_true", C.c_double)]
+
+
+_vp = C.c_void_p
+_P = C.POINTER
+_sig = {
+    "ib_last_error": (C.c_char_p, []),
+    "ib_abi_version": (C.c_int, []),
+    "ib_launch_count": (C.c_int64, []),
+    "cav_profile": (C.c_int, [_vp, C.c_int32]),
+    "cav_profile_read": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_double)]),
+    "ib_setup": (C.c_int, [_P(ib_grid_desc), _P(ib_structure_desc), _vp, _P(_vp)]),
+    "ib_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ib_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ib_destroy": (None, [_vp]),
+    "cav_setup": (C.c_int, [_vp, _P(cav_desc), _vp, _P(_vp)]),
+    "cav_num_levels": (C.c_int, [_vp, _P(C.c_int32)]),
+    "cav_get_level_info": (C.c_int, [_vp, C.c_int32, _P(cav_level_info)]),
+    "cav_patch_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _P(C.c_int32), _P(C.c_int64)]),
+    "cav_ee_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _P(C.c_int64)]),
+    "cav_sweep": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "cav_residual": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
+    "cav_restrict": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "cav_prolong_add": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "cav_coarse_solve": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "vcycle_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "cav_destroy": (None, [_vp]),
+    "fgmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, _P(fgmres_desc), _P(fgmres_info), _vp, _vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+def _check(st: int, where: str):
+    if st != IB_OK:
+        raise IBError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def _dev(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("device vectors must be contiguous float64 CUDA tensors")
+    return _vp(t.data_ptr())
+
+
+class System:
+    """Owns an ib_system handle."""
+
+    def __init__(self, handle, N, rec=None):
+        self._h = handle
+        self.N = N
+        self.rec = rec
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.ib_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """Owns a cav_hierarchy handle (keeps its system alive)."""
+
+    def __init__(self, handle, system: System, desc: dict):
+        self._h = handle
+        self.system = system
+        self.desc = desc
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.cav_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ib_setup(rec, stream=None) -> System:
+    """rec: an ib_workloads.System (or any object with the same fields)."""
+    g = ib_grid_desc(int(rec.N), float(rec.L), float(rec.rho), float(rec.mu), float(rec.dt))
+    X = np.ascontiguousarray(np.asarray(rec.X, dtype=np.float64).reshape(-1))
+    om = np.ascontiguousarray(np.asarray(rec.omega, dtype=np.float64))
+    M = int(X.size // 2)
+    sd = ib_structure_desc(M, 1 if rec.closed else 0, int(rec.law),
+                           X.ctypes.data_as(_P(C.c_double)), om.ctypes.data_as(_P(C.c_double)),
+                           float(rec.ds), float(rec.k_target), float(rec.k_stretch), float(rec.k_bend))
+    out = _vp()
+    _check(_lib.ib_setup(C.byref(g), C.byref(sd), _stream(stream), C.byref(out)), "ib_setup")
+    return System(out, int(rec.N), rec)
+
+
+def ib_apply(sys: System, x, y, stream=None):
+    _check(_lib.ib_apply(sys.handle, _dev(x), _dev(y), _stream(stream)), "ib_apply")
+
+
+def ib_residual(sys: System, b, x, r, stream=None):
+    _check(_lib.ib_residual(sys.handle, _dev(b), _dev(x), _dev(r), _stream(stream)), "ib_residual")
+
+
+def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=1.0,
+              precision="fp64", stream=None) -> Hierarchy:
+    d = cav_desc(KIND[kind], int(coarsest_N), int(nu_pre), int(nu_post), float(alpha), PRECISION[precision])
+    out = _vp()
+    _check(_lib.cav_setup(sys.handle, C.byref(d), _stream(stream), C.byref(out)), "cav_setup")
+    return Hierarchy(out, sys, dict(kind=kind, coarsest_N=coarsest_N, nu_pre=nu_pre, nu_post=nu_post,
+                                    alpha=alpha, precision=precision))
+
+
+def cav_num_levels(h: Hierarchy) -> int:
+    n = C.c_int32()
+    _check(_lib.cav_num_levels(h.handle, C.byref(n)), "cav_num_levels")
+    return n.value
+
+
+def cav_get_level_info(h: Hierarchy, level: int) -> dict:
+    info = cav_level_info()
+    _check(_lib.cav_get_level_info(h.handle, level, C.byref(info)), "cav_get_level_info")
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def cav_patch_export(h: Hierarchy, level: int):
+    n = C.c_int32()
+    tot = C.c_int64()
+    _check(_lib.cav_patch_export(h.handle, level, None, None, C.byref(n), C.byref(tot)), "cav_patch_export")
+    off = np.zeros(n.value + 1, dtype=np.int64)
+    dofs = np.zeros(tot.value, dtype=np.int32)
+    _check(_lib.cav_patch_export(h.handle, level, _vp(off.ctypes.data), _vp(dofs.ctypes.data),
+                                 C.byref(n), C.byref(tot)), "cav_patch_export")
+    return off, dofs
+
+
+def cav_ee_export(h: Hierarchy, level: int):
+    """(rowptr, cols, vals) over all 2 N_l^2 velocity rows."""
+    info = cav_get_level_info(h, level)
+    nnz = C.c_int64()
+    _check(_lib.cav_ee_export(h.handle, level, None, None, None, C.byref(nnz)), "cav_ee_export")
+    rowptr = np.zeros(2 * info["N"] ** 2 + 1, dtype=np.int64)
+    cols = np.zeros(nnz.value, dtype=np.int32)
+    vals = np.zeros(nnz.value, dtype=np.float64)
+    _check(_lib.cav_ee_export(h.handle, level, _vp(rowptr.ctypes.data), _vp(cols.ctypes.data),
+                              _vp(vals.ctypes.data), C.byref(nnz)), "cav_ee_export")
+    return rowptr, cols, vals
+
+
+def cav_sweep(h: Hierarchy, level: int, b, w, stream=None):
+    _check(_lib.cav_sweep(h.handle, level, _dev(b), _dev(w), _stream(stream)), "cav_sweep")
+
+
+def cav_residual(h: Hierarchy, level: int, b, w, r, stream=None):
+    _check(_lib.cav_residual(h.handle, level, _dev(b), _dev(w), _dev(r), _stream(stream)), "cav_residual")
+
+
+def cav_restrict(h: Hierarchy, level: int, r, bc, stream=None):
+    _check(_lib.cav_restrict(h.handle, level, _dev(r), _dev(bc), _stream(stream)), "cav_restrict")
+
+
+def cav_prolong_add(h: Hierarchy, level: int, xc, w, stream=None):
+    _check(_lib.cav_prolong_add(h.handle, level, _dev(xc), _dev(w), _stream(stream)), "cav_prolong_add")
+
+
+def cav_coarse_solve(h: Hierarchy, r, z, stream=None):
+    _check(_lib.cav_coarse_solve(h.handle, _dev(r), _dev(z), _stream(stream)), "cav_coarse_solve")
+
+
+def vcycle_apply(h: Hierarchy, r, z, stream=None):
+    _check(_lib.vcycle_apply(h.handle, _dev(r), _dev(z), _stream(stream)), "vcycle_apply")
+
+
+def ib_launch_count() -> int:
+    return int(_lib.ib_launch_count())
+
+
+def cav_profile(h: Hierarchy, enable: bool):
+    _check(_lib.cav_profile(h.handle, 1 if enable else 0), "cav_profile")
+
+
+def cav_profile_read(h: Hierarchy):
+    n = C.c_int32()
+    ms = C.c_double()
+    _check(_lib.cav_profile_read(h.handle, C.byref(n), C.byref(ms)), "cav_profile_read")
+    return n.value, ms.value
+
+
+def fgmres_solve(sys: System, h: Hierarchy, b, x, rtol=1e-10, maxit=60, rel_to=0, history=True,
+                 stream=None, raise_on_noconv=False) -> dict:
+    """b, x: CUDA tensors, or host buffers (numpy float64 arrays or CPU torch tensors, e.g.
+    pinned) -- then the call copies b and x in and x out inside the call."""
+    host = isinstance(b, np.ndarray) or (hasattr(b, "is_cuda") and not b.is_cuda)
+    d = fgmres_desc(float(rtol), int(maxit), int(rel_to), 1 if host else 0)
+    info = fgmres_info()
+    hist = np.zeros(maxit + 1) if history else None
+    if host:
+        if isinstance(b, np.ndarray):
+            assert isinstance(x, np.ndarray) and b.dtype == np.float64 and x.dtype == np.float64
+            bp, xp = _vp(b.ctypes.data), _vp(x.ctypes.data)
+        else:
+            bp, xp = _vp(b.data_ptr()), _vp(x.data_ptr())
+    else:
+        bp, xp = _dev(b), _dev(x)
+    st = _lib.fgmres_solve(sys.handle, h.handle, bp, xp, C.byref(d), C.byref(info),
+                           _vp(hist.ctypes.data) if hist is not None else None, _stream(stream))
+    if st not in (IB_OK, IB_ERR_NOCONV) or (st == IB_ERR_NOCONV and raise_on_noconv):
+        raise IBError(st, "fgmres_solve")
+    out = {f: getattr(info, f) for f, _ in info._fields_}
+    if hist is not None:
+        out["history"] = hist[:info.iters + 1].copy()
+    return out

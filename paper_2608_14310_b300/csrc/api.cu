@@ -1,0 +1,394 @@
+// C ABI entry points (include/ib_cav.h).  Every call catches library failures and turns
+// them into an ib_status with a thread-local message.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+#include <atomic>
+
+namespace cav {
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+void set_error(const std::string& msg) { g_last_error = msg; }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b, double* x, const fgmres_desc* d,
+                     fgmres_info* info, double* history, cudaStream_t st);
+}  // namespace cav
+
+using namespace cav;
+
+#define CAV_API_BEGIN try {
+#define CAV_API_END                                   \
+  }                                                   \
+  catch (const Fail& f) {                             \
+    return f.st;                                      \
+  }                                                   \
+  catch (const std::exception& e) {                   \
+    set_error(std::string("internal: ") + e.what());  \
+    return IB_ERR_INTERNAL;                           \
+  }                                                   \
+  catch (...) {                                       \
+    set_error("internal: unknown exception");         \
+    return IB_ERR_INTERNAL;                           \
+  }
+
+extern "C" {
+
+const char* ib_last_error(void) { return g_last_error.c_str(); }
+int ib_abi_version(void) { return 1; }
+int64_t ib_launch_count(void) { return g_launches.load(); }
+
+ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaStream_t st, ib_system** out) {
+  if (!out) { set_error("ib_setup: out is NULL"); return IB_ERR_INVALID; }
+  *out = nullptr;
+  ib_system* s = nullptr;
+  CAV_API_BEGIN
+  CAV_REQUIRE(grid && sd, "ib_setup: NULL descriptor");
+  CAV_REQUIRE(grid->N >= 8 && grid->N <= 16384, "ib_setup: N must be in [8, 16384]");
+  CAV_REQUIRE(grid->L > 0 && grid->rho > 0 && grid->mu >= 0 && grid->dt > 0,
+              "ib_setup: L, rho, dt must be positive and mu non-negative");
+  CAV_REQUIRE(sd->M >= 0, "ib_setup: M must be non-negative");
+  CAV_REQUIRE(sd->M == 0 || (sd->X && sd->omega), "ib_setup: X and omega are required when M > 0");
+  CAV_REQUIRE(sd->law >= IB_FORCE_TARGET && sd->law <= IB_FORCE_BEAM, "ib_setup: unknown force law");
+  s = new ib_system();
+  s->N = grid->N;
+  s->L = grid->L;
+  s->h = grid->L / grid->N;
+  s->rho = grid->rho;
+  s->mu = grid->mu;
+  s->dt = grid->dt;
+  s->law = sd->law;
+  s->closed = sd->closed ? 1 : 0;
+  s->ds = sd->ds;
+  s->k_target = sd->k_target;
+  s->k_stretch = sd->k_stretch;
+  s->k_bend = sd->k_bend;
+  CAV_CHECK_CUDA(cudaGetDevice(&s->device));
+  // structural band of E: target -> diagonal; membrane -> +-1 when k_stretch != 0;
+  // beam -> +-2 when k_bend != 0, else +-1 when k_stretch != 0; otherwise no structure
+  int M = sd->M, bw = 0;
+  if (sd->law == IB_FORCE_TARGET) bw = 0;
+  else if (sd->law == IB_FORCE_MEMBRANE) { if (sd->k_stretch != 0.0) bw = 1; else M = 0; }
+  else { if (sd->k_bend != 0.0) bw = 2; else if (sd->k_stretch != 0.0) bw = 1; else M = 0; }
+  if (M > 0 && bw > 0) {
+    CAV_REQUIRE(sd->closed, "ib_setup: membrane and beam laws need a closed marker chain");
+    CAV_REQUIRE(M >= 2 * bw + 1, "ib_setup: too few markers for the force stencil");
+    CAV_REQUIRE(sd->ds > 0, "ib_setup: ds must be positive");
+  }
+  s->M = M;
+  s->bw = bw;
+  s->status = s->arena.alloc<int>(1);
+  CAV_CHECK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
+  build_markers_and_ee(s, sd->X, sd->omega, st);
+  const int code = read_status(s->status, st);
+  if (code != DEV_OK) {
+    set_error("ib_setup: E_E assembly window overflow");
+    throw Fail{IB_ERR_INTERNAL};
+  }
+  *out = s;
+  return IB_OK;
+  }
+  catch (const Fail& f) {
+    if (s) { s->arena.release(); delete s; }
+    return f.st;
+  }
+  catch (...) {
+    if (s) { s->arena.release(); delete s; }
+    set_error("ib_setup: internal error");
+    return IB_ERR_INTERNAL;
+  }
+}
+
+static LevelOps sys_ops(const ib_system* s) {
+  LevelOps o{s->N, s->h, s->rho / s->dt, s->mu, s->dt, &s->ee};
+  return o;
+}
+
+ib_status ib_apply(const ib_system* s, const double* x, double* y, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && x && y, "ib_apply: NULL argument");
+  launch_apply(sys_ops(s), x, nullptr, y, 1, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status ib_residual(const ib_system* s, const double* b, const double* x, double* r, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && b && x && r, "ib_residual: NULL argument");
+  launch_apply(sys_ops(s), x, b, r, 0, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+void ib_destroy(ib_system* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  s->arena.release();
+  delete s;
+}
+
+ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_hierarchy** out) {
+  if (!out) { set_error("cav_setup: out is NULL"); return IB_ERR_INVALID; }
+  *out = nullptr;
+  cav_hierarchy* H = nullptr;
+  try {
+    CAV_REQUIRE(s && d, "cav_setup: NULL argument");
+    CAV_REQUIRE(d->kind == CAV_PATCH_CAV || d->kind == CAV_PATCH_VANKA, "cav_setup: unknown patch kind");
+    CAV_REQUIRE(d->coarsest_N >= 2, "cav_setup: coarsest_N must be >= 2");
+    CAV_REQUIRE(d->nu_pre >= 0 && d->nu_post >= 0 && d->nu_pre + d->nu_post >= 1,
+                "cav_setup: need at least one sweep per level");
+    CAV_REQUIRE(d->precision >= CAV_PREC_FP64 && d->precision <= CAV_PREC_BF16, "cav_setup: unknown precision");
+    CAV_REQUIRE(std::isfinite(d->alpha) && d->alpha > 0, "cav_setup: alpha must be positive");
+    H = new cav_hierarchy();
+    H->sys = s;
+    H->desc = *d;
+    H->status = H->arena.alloc<int>(1);
+    CAV_CHECK_CUDA(cudaMemsetAsync(H->status, 0, sizeof(int), st));
+    build_levels(H, st);
+    *out = H;
+    return IB_OK;
+  } catch (const Fail& f) {
+    if (H) { cudaDeviceSynchronize(); H->arena.release(); delete H; }
+    return f.st;
+  } catch (...) {
+    if (H) { cudaDeviceSynchronize(); H->arena.release(); delete H; }
+    set_error("cav_setup: internal error");
+    return IB_ERR_INTERNAL;
+  }
+}
+
+ib_status cav_num_levels(const cav_hierarchy* h, int32_t* levels) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(h && levels, "cav_num_levels: NULL argument");
+  *levels = (int32_t)h->levels.size();
+  return IB_OK;
+  CAV_API_END
+}
+
+static const Level& level_of(const cav_hierarchy* h, int32_t level) {
+  CAV_REQUIRE(h, "NULL hierarchy");
+  CAV_REQUIRE(level >= 0 && level < (int32_t)h->levels.size(), "level out of range");
+  return h->levels[level];
+}
+
+ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_info* info) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(info, "cav_get_level_info: NULL info");
+  const Level& lv = level_of(h, level);
+  std::memset(info, 0, sizeof(*info));
+  const int64_t NN = (int64_t)lv.N * lv.N;
+  info->N = lv.N;
+  info->is_coarsest = lv.coarsest ? 1 : 0;
+  info->ee_nnz = lv.ee.nnz;
+  info->ee_rows = lv.ee.n_rows;
+  info->ee_window = lv.ee.W;
+  if (lv.coarsest) {
+    info->n_patches = 1;
+    info->max_n = (int32_t)(3 * NN);
+    info->sum_n = 3 * NN;
+    info->sum_n2 = 9 * NN * NN;
+  } else {
+    const int64_t nstd = NN - lv.n_big;
+    info->n_patches = (int32_t)NN;
+    info->n_enlarged = lv.n_big;
+    info->max_n = std::max(lv.big_max_n, 5);
+    info->sum_n = lv.big_sum_n + 5 * nstd;
+    info->sum_n2 = lv.big_sum_n2 + 25 * nstd;
+    info->enlarged_sum_n = lv.big_sum_n;
+    info->enlarged_sum_n2 = lv.big_sum_n2;
+    const int bytes = (lv.precision == CAV_PREC_FP64) ? 8 : (lv.precision == CAV_PREC_FP32 ? 4 : 2);
+    info->inverse_bytes = lv.inv_elems * bytes;
+  }
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offsets, int32_t* dofs,
+                           int32_t* n_patches, int64_t* sum_n) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  CAV_REQUIRE(!lv.coarsest, "cav_patch_export: the coarsest level has no patches");
+  const int N = lv.N, NN = N * N;
+  const int64_t total = lv.big_sum_n + 5LL * (NN - lv.n_big);
+  if (n_patches) *n_patches = NN;
+  if (sum_n) *sum_n = total;
+  if (!offsets || !dofs) return IB_OK;
+  std::vector<uint8_t> big(NN);
+  std::vector<int> cells(lv.n_big);
+  std::vector<int64_t> off(lv.n_big + 1);
+  std::vector<int> bd(lv.big_sum_n);
+  CAV_CHECK_CUDA(cudaMemcpy(big.data(), lv.cell_big, NN, cudaMemcpyDeviceToHost));
+  if (lv.n_big) {
+    CAV_CHECK_CUDA(cudaMemcpy(cells.data(), lv.big_cell, sizeof(int) * lv.n_big, cudaMemcpyDeviceToHost));
+    CAV_CHECK_CUDA(cudaMemcpy(off.data(), lv.big_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost));
+    CAV_CHECK_CUDA(cudaMemcpy(bd.data(), lv.big_dofs, sizeof(int) * lv.big_sum_n, cudaMemcpyDeviceToHost));
+  }
+  int64_t pos = 0;
+  int q = 0;
+  for (int c = 0; c < NN; ++c) {
+    offsets[c] = pos;
+    if (big[c]) {
+      for (int64_t t = off[q]; t < off[q + 1]; ++t) dofs[pos++] = bd[t];
+      ++q;
+    } else {
+      const int i = c % N, j = c / N;
+      int v[5] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i, 2 * NN + j * N + i};
+      std::sort(v, v + 5);
+      for (int t = 0; t < 5; ++t) dofs[pos++] = v[t];
+    }
+  }
+  offsets[NN] = pos;
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_ee_export(const cav_hierarchy* h, int32_t level, int64_t* rowptr, int32_t* cols, double* vals,
+                        int64_t* nnz) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  const int NN = lv.N * lv.N;
+  if (nnz) *nnz = lv.ee.nnz;
+  if (!rowptr || !cols || !vals) return IB_OK;
+  std::vector<int> rows(lv.ee.n_rows);
+  std::vector<int64_t> rp(lv.ee.n_rows + 1, 0);
+  std::vector<int> c(lv.ee.nnz);
+  std::vector<double> v(lv.ee.nnz);
+  if (lv.ee.n_rows) {
+    CAV_CHECK_CUDA(cudaMemcpy(rows.data(), lv.ee.rows, sizeof(int) * lv.ee.n_rows, cudaMemcpyDeviceToHost));
+    CAV_CHECK_CUDA(cudaMemcpy(rp.data(), lv.ee.rowptr, sizeof(int64_t) * (lv.ee.n_rows + 1), cudaMemcpyDeviceToHost));
+    CAV_CHECK_CUDA(cudaMemcpy(c.data(), lv.ee.cols, sizeof(int) * lv.ee.nnz, cudaMemcpyDeviceToHost));
+    CAV_CHECK_CUDA(cudaMemcpy(v.data(), lv.ee.vals, sizeof(double) * lv.ee.nnz, cudaMemcpyDeviceToHost));
+  }
+  int64_t pos = 0;
+  int q = 0;
+  for (int r = 0; r < 2 * NN; ++r) {
+    rowptr[r] = pos;
+    if (q < lv.ee.n_rows && rows[q] == r) {
+      for (int64_t t = rp[q]; t < rp[q + 1]; ++t) {
+        cols[pos] = c[t];
+        vals[pos] = v[t];
+        ++pos;
+      }
+      ++q;
+    }
+  }
+  rowptr[2 * NN] = pos;
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_sweep(const cav_hierarchy* h, int32_t level, const double* b, double* w, cudaStream_t st) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  CAV_REQUIRE(!lv.coarsest, "cav_sweep: no smoother on the coarsest level");
+  CAV_REQUIRE(b && w, "cav_sweep: NULL vector");
+  level_sweep(h, level, b, w, false, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_residual(const cav_hierarchy* h, int32_t level, const double* b, const double* w, double* r,
+                       cudaStream_t st) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  CAV_REQUIRE(b && w && r, "cav_residual: NULL vector");
+  LevelOps o{lv.N, lv.h, lv.rho_dt, lv.mu, lv.dt, &lv.ee};
+  launch_apply(o, w, b, r, 0, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_restrict(const cav_hierarchy* h, int32_t level, const double* r, double* bc, cudaStream_t st) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  CAV_REQUIRE(!lv.coarsest && r && bc, "cav_restrict: bad level or NULL vector");
+  launch_restrict(lv.N / 2, r, bc, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_prolong_add(const cav_hierarchy* h, int32_t level, const double* xc, double* w, cudaStream_t st) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  CAV_REQUIRE(!lv.coarsest && xc && w, "cav_prolong_add: bad level or NULL vector");
+  launch_prolong_add(lv.N / 2, xc, w, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_coarse_solve(const cav_hierarchy* h, const double* r, double* z, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(h && r && z, "cav_coarse_solve: NULL argument");
+  coarse_solve(h, r, z, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status vcycle_apply(const cav_hierarchy* h, const double* r, double* z, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(h && r && z, "vcycle_apply: NULL argument");
+  CAV_REQUIRE(r != z, "vcycle_apply: r and z must not alias");
+  vcycle(h, r, z, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_profile(cav_hierarchy* h, int32_t enable) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(h, "cav_profile: NULL hierarchy");
+  if (enable && h->prof_ev.empty()) {
+    h->prof_ev.resize(2 * 8192);
+    for (auto& e : h->prof_ev) CAV_CHECK_CUDA(cudaEventCreate(&e));
+  }
+  h->prof_on = enable ? 1 : 0;
+  h->prof_used = 0;
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_profile_read(cav_hierarchy* h, int32_t* launches, double* total_ms) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(h && launches && total_ms, "cav_profile_read: NULL argument");
+  double t = 0.0;
+  for (int q = 0; q < h->prof_used; ++q) {
+    CAV_CHECK_CUDA(cudaEventSynchronize(h->prof_ev[2 * q + 1]));
+    float ms = 0.f;
+    CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[2 * q], h->prof_ev[2 * q + 1]));
+    t += ms;
+  }
+  *launches = h->prof_used;
+  *total_ms = t;
+  h->prof_used = 0;
+  return IB_OK;
+  CAV_API_END
+}
+
+void cav_destroy(cav_hierarchy* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto& e : h->prof_ev) cudaEventDestroy(e);
+  h->arena.release();
+  h->ws_arena.release();
+  if (h->host_b) cudaFreeHost(h->host_b);
+  delete h;
+}
+
+ib_status fgmres_solve(const ib_system* s, const cav_hierarchy* h, const double* b, double* x,
+                       const fgmres_desc* d, fgmres_info* info, double* history, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && h && b && x && d && info, "fgmres_solve: NULL argument");
+  CAV_REQUIRE(h->sys == s, "fgmres_solve: hierarchy was built for another system");
+  CAV_REQUIRE(d->maxit >= 1 && d->maxit <= 4096, "fgmres_solve: maxit must be in [1, 4096]");
+  CAV_REQUIRE(d->rtol >= 0 && std::isfinite(d->rtol), "fgmres_solve: bad rtol");
+  std::memset(info, 0, sizeof(*info));
+  ib_status r = fgmres_run(s, const_cast<cav_hierarchy*>(h), b, x, d, info, history, st);
+  if (r == IB_ERR_NOCONV) set_error("fgmres_solve: maxit reached above tolerance");
+  return r;
+  CAV_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// Internal declarations of the CAV multigrid library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ib_cav.h"
+
+namespace cav {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+struct Fail {
+  ib_status st;
+};
+#define CAV_CHECK_CUDA(call)                                                        \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::cav::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));       \
+      throw ::cav::Fail{e_ == cudaErrorMemoryAllocation ? IB_ERR_OOM : IB_ERR_CUDA}; \
+    }                                                                               \
+  } while (0)
+// counts every kernel launch of the library (host side), for launch accounting
+void note_launch();
+#define CAV_CHECK_LAUNCH()                  \
+  do {                                      \
+    ::cav::note_launch();                   \
+    CAV_CHECK_CUDA(cudaGetLastError());     \
+  } while (0)
+#define CAV_REQUIRE(cond, msg)                                                      \
+  do {                                                                              \
+    if (!(cond)) {                                                                  \
+      ::cav::set_error(msg);                                                        \
+      throw ::cav::Fail{IB_ERR_INVALID};                                            \
+    }                                                                               \
+  } while (0)
+
+// Device status word codes (written by kernels, read by the host after set-up or a solve).
+enum : int { DEV_OK = 0, DEV_WINDOW = 1, DEV_SINGULAR = 2, DEV_CAPACITY = 3 };
+
+// ------------------------------------------------------------------ device memory
+
+// Owns a list of device allocations; freed together with the owning handle.
+struct Arena {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    CAV_CHECK_CUDA(cudaMalloc(&p, bytes));
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// ------------------------------------------------------------------ E_E on one level
+
+// E_E restricted to its structurally nonzero velocity rows, each row's columns sorted.
+struct EECsr {
+  int n_rows = 0;            // active rows
+  int64_t nnz = 0;
+  int W = 0;                 // per-axis |offset| bound between a row face and its columns
+  int* rows = nullptr;       // [n_rows] global velocity index of each active row
+  int64_t* rowptr = nullptr; // [n_rows + 1]
+  int* cols = nullptr;       // [nnz]
+  double* vals = nullptr;    // [nnz]
+  int* row_of = nullptr;     // [2 N^2] active row index or -1
+};
+
+// ------------------------------------------------------------------ one grid level
+
+struct Level {
+  int N = 0;
+  double h = 0, rho_dt = 0, mu = 0, dt = 0;
+  bool coarsest = false;
+  EECsr ee;
+
+  // patches (smoothing levels): one per cell; enlarged ones are stored explicitly
+  int n_big = 0;                 // enlarged patches
+  int64_t big_sum_n = 0, big_sum_n2 = 0, inv_elems = 0;
+  int big_max_n = 0;
+  uint8_t* cell_big = nullptr;   // [N^2] 1 if the cell's patch is enlarged
+  int* big_cell = nullptr;       // [n_big] cell index of each enlarged patch (ascending)
+  int64_t* big_off = nullptr;    // [n_big + 1] offsets into big_dofs / packed delta
+  int* big_dofs = nullptr;       // [big_sum_n] sorted global indices
+  int64_t* inv_off = nullptr;    // [n_big + 1] element offsets of each inverse (ld * n)
+  int* order = nullptr;          // [n_big] patches by descending size (launch order)
+  double* s_r = nullptr;         // [big_sum_n] row scales (power of two)
+  double* s_c = nullptr;         // [big_sum_n] column scales
+  double* inv64 = nullptr;       // [inv_elems] equilibrated inverses, column-major, ld = round8(n)
+  float* inv32 = nullptr;
+  __nv_bfloat16* inv16 = nullptr;
+  int precision = CAV_PREC_FP64;
+  int64_t* inc_off = nullptr;    // [3 N^2 + 1] transpose incidence: slots of each unknown
+  int* inc_slot = nullptr;       // [big_sum_n] packed-delta slots, ascending per unknown
+  double std_inv[25];            // inverse of the standard Vanka patch, canonical order
+                                 // (u_ij, u_i+1j, v_ij, v_ij+1, p_ij), scalings folded in
+
+  // coarsest level: dense inverse of the bordered system, row-major (n+1) x (n+1)
+  double* coarse_inv = nullptr;
+
+  // work vectors of this level
+  double* r = nullptr;           // [3 N^2] residual
+  double* x = nullptr;           // [3 N^2] V-cycle iterate
+  double* b = nullptr;           // [3 N^2] V-cycle right-hand side (levels > 0)
+  double* delta = nullptr;       // [big_sum_n] packed patch corrections
+  double* partial = nullptr;     // [reduce blocks] partial sums for the pressure mean
+  int n_partial = 0;
+};
+
+}  // namespace cav
+
+// ------------------------------------------------------------------ handles
+
+struct ib_system {
+  int N = 0;
+  double L = 1, h = 0, rho = 0, mu = 0, dt = 0;
+  int M = 0, law = 0, closed = 0, bw = 0;
+  double ds = 0, k_target = 0, k_stretch = 0, k_bend = 0;
+  int device = 0;
+  cav::Arena arena;
+  // markers (component-major x[0..M), y[M..2M))
+  double* X = nullptr;
+  double* omega = nullptr;
+  double* Eband = nullptr;       // [M * (2 bw + 1)] E coefficient of (a, a + d)
+  // kernel support per (component c, marker a): index c * M + a
+  int* sup_i0 = nullptr;         // first face index along x (may be negative / >= N)
+  int* sup_j0 = nullptr;
+  double* sup_wx = nullptr;      // [2M * 4]
+  double* sup_wy = nullptr;
+  uint8_t* sup_mask = nullptr;   // [2M] bits 0-3: x support, bits 4-7: y support
+  int64_t* fm_off = nullptr;     // [2 N^2 + 1] face -> markers whose support holds it
+  int* fm_list = nullptr;        // ascending marker ids
+  cav::EECsr ee;                 // finest-level E_E
+  int* status = nullptr;         // device status word
+  double* partial = nullptr;
+};
+
+struct cav_hierarchy {
+  const ib_system* sys = nullptr;
+  cav_desc desc{};
+  std::vector<cav::Level> levels;
+  cav::Arena arena;
+  int* status = nullptr;
+  // FGMRES workspace (grown on demand)
+  int ws_maxit = 0;
+  double* V = nullptr;   // (maxit + 1) x n
+  double* Z = nullptr;   // maxit x n
+  double* dev_scalars = nullptr;  // Hessenberg, Givens, g and small temporaries
+  double* red_partial = nullptr;  // partial sums for multi-dot reductions
+  double* host_b = nullptr;       // pinned scalars read back per iteration
+  double* io_b = nullptr;         // device staging for host_io
+  double* io_x = nullptr;
+  cav::Arena ws_arena;
+  // live timing of the finest level's patch-apply launches
+  int prof_on = 0;
+  int prof_used = 0;
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
+};
+
+namespace cav {
+
+// ------------------------------------------------------------------ kernels' host wrappers
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int round8(int n) { return (n + 7) & ~7; }
+
+// ib_system.cu
+void build_markers_and_ee(ib_system* s, const double* X_interleaved, const double* omega_host,
+                          cudaStream_t st);
+void ee_compute_window(EECsr& ee, int N, int* d_scratch, cudaStream_t st);
+
+// stencil.cu: operators of one level (finest level uses the system's E_E)
+struct LevelOps {
+  int N;
+  double h, rho_dt, mu, dt;
+  const EECsr* ee;
+};
+// mode 0: out = b - K w  (b may be null = 0);  mode 1: out = K w
+void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
+                  cudaStream_t st);
+void launch_restrict(int Nc, const double* r_f, double* b_c, cudaStream_t st);
+void launch_prolong_add(int Nc, const double* x_c, double* w_f, cudaStream_t st);
+
+// setup.cu
+void build_levels(cav_hierarchy* H, cudaStream_t st);
+
+// sweep.cu
+void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
+                 cudaStream_t st);
+void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
+void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st);
+void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
+void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
+
+// reductions (reduce.cu)
+int reduce_blocks(int64_t n);
+void launch_dot_partials(const double* a, const double* b, int64_t n, double* partial,
+                         cudaStream_t st);
+// exclusive scan of int counts into int64 offsets (out has n + 1 entries)
+void exclusive_scan(const int* counts, int64_t* out, int64_t n, cudaStream_t st, Arena* scratch);
+
+int read_status(int* d_status, cudaStream_t st);
+
+}  // namespace cav

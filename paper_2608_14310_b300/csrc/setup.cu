@@ -1,0 +1,875 @@
+// Hierarchy set-up (Sec. 3.2, 3.3, 4): Galerkin E_E on coarse levels, CAV patch sets,
+// extraction of local matrices, one-pass equilibration, inverses, and the transpose
+// incidence used by the scatter of the additive sweep.
+#include <algorithm>
+#include <numeric>
+
+#include "internal.cuh"
+#include "device_util.cuh"
+
+namespace cav {
+
+// ------------------------------------------------------------------ Galerkin E_E
+
+// Fine faces k with P[k, K] != 0 for coarse face K = (c, I, J) and their weights
+// (RT0: coincident faces weight 1, faces on the coarse cell's midlines weight 1/2).
+__device__ inline int pcol(int c, int I, int J, int Nf, int* fi, int* fj, double* wt) {
+  if (c == 0) {
+    const int i0 = 2 * I, j0 = 2 * J;
+    fi[0] = i0; fj[0] = j0; wt[0] = 1.0;
+    fi[1] = i0; fj[1] = j0 + 1; wt[1] = 1.0;
+    fi[2] = i0 - 1; fj[2] = j0; wt[2] = 0.5;
+    fi[3] = i0 - 1; fj[3] = j0 + 1; wt[3] = 0.5;
+    fi[4] = i0 + 1; fj[4] = j0; wt[4] = 0.5;
+    fi[5] = i0 + 1; fj[5] = j0 + 1; wt[5] = 0.5;
+  } else {
+    const int i0 = 2 * I, j0 = 2 * J;
+    fi[0] = i0; fj[0] = j0; wt[0] = 1.0;
+    fi[1] = i0 + 1; fj[1] = j0; wt[1] = 1.0;
+    fi[2] = i0; fj[2] = j0 - 1; wt[2] = 0.5;
+    fi[3] = i0 + 1; fj[3] = j0 - 1; wt[3] = 0.5;
+    fi[4] = i0; fj[4] = j0 + 1; wt[4] = 0.5;
+    fi[5] = i0 + 1; fj[5] = j0 + 1; wt[5] = 0.5;
+  }
+  for (int t = 0; t < 6; ++t) {
+    fi[t] = pmod(fi[t], Nf);
+    fj[t] = pmod(fj[t], Nf);
+  }
+  return 6;
+}
+
+__global__ void k_coarse_active(int Nc, const int* __restrict__ row_of_f, int* flag) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NNc = Nc * Nc;
+  if (K >= 2 * NNc) return;
+  const int c = K / NNc, rem = K % NNc, I = rem % Nc, J = rem / Nc;
+  const int Nf = 2 * Nc;
+  int fi[6], fj[6];
+  double wt[6];
+  pcol(c, I, J, Nf, fi, fj, wt);
+  int f = 0;
+  for (int t = 0; t < 6; ++t) f |= (row_of_f[c * Nf * Nf + fj[t] * Nf + fi[t]] >= 0);
+  flag[K] = f;
+}
+
+__device__ inline int find_col(const int* cols, int64_t b, int64_t e, int key) {
+  // binary search in the sorted column list [b, e); returns position or -1
+  int64_t lo = b, hi = e;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const int v = cols[mid];
+    if (v < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < e && cols[lo] == key) ? (int)(lo - b) : -1;
+}
+
+// One warp per active coarse row K; lanes walk the window of coarse columns L (same
+// component) in ascending global order and evaluate
+//   E_c[K, L] = sum_{k in Pcol(K)} sum_{l in Pcol(L)} (1/4) P[k,K] E_f[k,l] P[l,L]
+// in a fixed order; (K, L) is structurally nonzero iff some (k, l) is in E_f's pattern.
+__global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ rows,
+                           const int* __restrict__ row_of_f, const int64_t* __restrict__ rowptr_f,
+                           const int* __restrict__ cols_f, const double* __restrict__ vals_f,
+                           int* row_count, const int64_t* __restrict__ rowptr, int* cols, double* vals,
+                           int pass) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rows) return;
+  const int NNc = Nc * Nc, Nf = 2 * Nc, NNf = Nf * Nf;
+  const int K = rows[r];
+  const int c = K / NNc, rem = K % NNc, I = rem % Nc, J = rem / Nc;
+  int ki[6], kj[6];
+  double kw[6];
+  pcol(c, I, J, Nf, ki, kj, kw);
+  int krow[6];
+  for (int t = 0; t < 6; ++t) krow[t] = row_of_f[c * NNf + kj[t] * Nf + ki[t]];
+  const Win wx = make_win(I, Wc, Nc), wy = make_win(J, Wc, Nc);
+  const int ncell = wx.len * wy.len;
+  int64_t outpos = (pass == 1) ? rowptr[r] : 0;
+  int total = 0;
+  for (int base = 0; base < ncell; base += 32) {
+    const int tp = base + lane;
+    bool f = false;
+    double val = 0.0;
+    int L = 0;
+    if (tp < ncell) {
+      const int typ = tp / wx.len, txp = tp % wx.len;
+      const int gy = win_glob(wy, win_asc(wy, typ), Nc), gx = win_glob(wx, win_asc(wx, txp), Nc);
+      L = c * NNc + gy * Nc + gx;
+      int li[6], lj[6];
+      double lw[6];
+      pcol(c, gx, gy, Nf, li, lj, lw);
+      for (int t = 0; t < 6; ++t) {
+        if (krow[t] < 0) continue;
+        const int64_t b = rowptr_f[krow[t]], e = rowptr_f[krow[t] + 1];
+        double s = 0.0;
+        for (int u = 0; u < 6; ++u) {
+          const int l = c * NNf + lj[u] * Nf + li[u];
+          const int pos = find_col(cols_f, b, e, l);
+          if (pos >= 0) {
+            f = true;
+            s += vals_f[b + pos] * lw[u];
+          }
+        }
+        val += 0.25 * kw[t] * s;
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (pass == 1 && f) {
+      const int rank = __popc(bal & ((1u << lane) - 1u));
+      cols[outpos + total + rank] = L;
+      vals[outpos + total + rank] = val;
+    }
+    total += __popc(bal);
+  }
+  if (pass == 0 && lane == 0) row_count[r] = total;
+}
+
+__global__ void k_compact_rows2(int n, const int* flag, const int64_t* pos, int* rows, int* row_of) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  if (flag[f]) {
+    rows[pos[f]] = f;
+    row_of[f] = (int)pos[f];
+  } else {
+    row_of[f] = -1;
+  }
+}
+
+static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int* d_scratch,
+                           cudaStream_t st) {
+  Arena scratch;
+  const int NNc = Nc * Nc;
+  int* flag = scratch.alloc<int>(2 * NNc);
+  int64_t* pos = scratch.alloc<int64_t>(2 * NNc + 1);
+  out.row_of = A.alloc<int>(2 * NNc);
+  k_coarse_active<<<div_up(2 * NNc, 256), 256, 0, st>>>(Nc, fine.row_of, flag);
+  CAV_CHECK_LAUNCH();
+  exclusive_scan(flag, pos, 2 * NNc, st, &scratch);
+  int64_t nrows = 0;
+  CAV_CHECK_CUDA(cudaMemcpyAsync(&nrows, pos + 2 * NNc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  out.n_rows = (int)nrows;
+  out.rows = A.alloc<int>(nrows);
+  k_compact_rows2<<<div_up(2 * NNc, 256), 256, 0, st>>>(2 * NNc, flag, pos, out.rows, out.row_of);
+  CAV_CHECK_LAUNCH();
+  // coarse window: fine offsets up to W_f plus one fine face on either side of each transfer
+  const int Wc = fine.W / 2 + 2;
+  int* row_count = scratch.alloc<int>(nrows + 1);
+  out.rowptr = A.alloc<int64_t>(nrows + 1);
+  const int grid = div_up(nrows, 8);
+  if (nrows > 0) {
+    k_galerkin<<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
+                                     fine.vals, row_count, nullptr, nullptr, nullptr, 0);
+    CAV_CHECK_LAUNCH();
+  }
+  exclusive_scan(row_count, out.rowptr, nrows, st, &scratch);
+  int64_t nnz = 0;
+  CAV_CHECK_CUDA(cudaMemcpyAsync(&nnz, out.rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  out.nnz = nnz;
+  out.cols = A.alloc<int>(nnz);
+  out.vals = A.alloc<double>(nnz);
+  if (nrows > 0) {
+    k_galerkin<<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
+                                     fine.vals, row_count, out.rowptr, out.cols, out.vals, 1);
+    CAV_CHECK_LAUNCH();
+  }
+  ee_compute_window(out, Nc, d_scratch, st);
+  scratch.release();
+}
+
+// ------------------------------------------------------------------ CAV patch sets
+
+// Cell c = (i, j) keeps its standard Vanka patch iff no velocity of U_ij couples through
+// E_E to a velocity outside U_ij (Eq. cav_patch_set; E_E's pattern is symmetric).
+__global__ void k_cell_flags(int N, int cav, const int* __restrict__ row_of, const int64_t* __restrict__ rowptr,
+                             const int* __restrict__ cols, uint8_t* big, int* flag) {
+  const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NN = N * N;
+  if (cidx >= NN) return;
+  const int i = cidx % N, j = cidx / N;
+  const int U4[4] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i};
+  int enl = 0;
+  if (cav) {
+    for (int t = 0; t < 4 && !enl; ++t) {
+      const int r = row_of[U4[t]];
+      if (r < 0) continue;
+      for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+        const int k = cols[q];
+        if (k != U4[0] && k != U4[1] && k != U4[2] && k != U4[3]) {
+          enl = 1;
+          break;
+        }
+      }
+    }
+  }
+  big[cidx] = (uint8_t)enl;
+  flag[cidx] = enl;
+}
+
+__global__ void k_compact_cells(int n, const int* flag, const int64_t* pos, int* out) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < n && flag[f]) out[pos[f]] = f;
+}
+
+__device__ inline void mark_cell(uint8_t* cm, const Win& wx, const Win& wy, int N, int ci, int cj,
+                                 int* status) {
+  const int ox = win_off(wx, pmod(ci, N), N), oy = win_off(wy, pmod(cj, N), N);
+  if (ox < 0 || oy < 0) atomicExch(status, DEV_WINDOW);
+  else cm[oy * wx.len + ox] = 1;
+}
+__device__ inline void mark_face_cells(uint8_t* cm, const Win& wx, const Win& wy, int N, int k,
+                                       int* status) {
+  const int NN = N * N;
+  const int c = k / NN, rem = k % NN, i = rem % N, j = rem / N;
+  if (c == 0) mark_cell(cm, wx, wy, N, i - 1, j, status);
+  else mark_cell(cm, wx, wy, N, i, j - 1, status);
+  mark_cell(cm, wx, wy, N, i, j, status);
+}
+__device__ inline void mark_dof(uint8_t* dm, const Win& wx, const Win& wy, int N, int comp, int gi,
+                                int gj, int* status) {
+  const int ox = win_off(wx, pmod(gi, N), N), oy = win_off(wy, pmod(gj, N), N);
+  if (ox < 0 || oy < 0) atomicExch(status, DEV_WINDOW);
+  else dm[(comp * wy.len + oy) * wx.len + ox] = 1;
+}
+
+// One warp per enlarged cell: Uhat = U_ij u (E_E neighbours of U_ij), cells C(Uhat), and the
+// union V(C) of their Vanka patches, enumerated in ascending global order (u, v, p blocks;
+// y then x).  pass 0 counts, pass 1 writes.
+__global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_cell,
+                           const int* __restrict__ row_of, const int64_t* __restrict__ rowptr,
+                           const int* __restrict__ cols, int* sizes, const int64_t* __restrict__ off,
+                           int* dofs, int pass, int* status) {
+  extern __shared__ unsigned char smem[];
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * warps + warp;
+  const int Wc = W + 2, Wd = W + 3;
+  const int lenC = (2 * Wc + 1 >= N) ? N : 2 * Wc + 1;
+  const int lenD = (2 * Wd + 1 >= N) ? N : 2 * Wd + 1;
+  const int per_warp = lenC * lenC + 3 * lenD * lenD;
+  uint8_t* cm = smem + (size_t)warp * per_warp;
+  uint8_t* dm = cm + lenC * lenC;
+  if (p >= n_big) return;
+  const int NN = N * N;
+  const int cell = big_cell[p];
+  const int i = cell % N, j = cell / N;
+  const Win cx = make_win(i, Wc, N), cy = make_win(j, Wc, N);
+  const Win dx = make_win(i, Wd, N), dy = make_win(j, Wd, N);
+  for (int t = lane; t < per_warp; t += 32) cm[t] = 0;
+  __syncwarp();
+  const int U4[4] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i};
+  for (int t = 0; t < 4; ++t) {
+    if (lane == 0) mark_face_cells(cm, cx, cy, N, U4[t], status);
+    const int r = row_of[U4[t]];
+    if (r < 0) continue;
+    for (int64_t q = rowptr[r] + lane; q < rowptr[r + 1]; q += 32)
+      mark_face_cells(cm, cx, cy, N, cols[q], status);
+  }
+  __syncwarp();
+  for (int t = lane; t < lenC * lenC; t += 32) {
+    if (!cm[t]) continue;
+    const int oy = t / lenC, ox = t % lenC;
+    const int a = win_glob(cx, ox, N), b = win_glob(cy, oy, N);
+    mark_dof(dm, dx, dy, N, 0, a, b, status);
+    mark_dof(dm, dx, dy, N, 0, a + 1, b, status);
+    mark_dof(dm, dx, dy, N, 1, a, b, status);
+    mark_dof(dm, dx, dy, N, 1, a, b + 1, status);
+    mark_dof(dm, dx, dy, N, 2, a, b, status);
+  }
+  __syncwarp();
+  int64_t outpos = (pass == 1) ? off[p] : 0;
+  int total = 0;
+  for (int comp = 0; comp < 3; ++comp) {
+    for (int typ = 0; typ < dy.len; ++typ) {
+      const int ty = win_asc(dy, typ);
+      const int gy = win_glob(dy, ty, N);
+      for (int base = 0; base < dx.len; base += 32) {
+        const int txp = base + lane;
+        bool f = false;
+        int gx = 0;
+        if (txp < dx.len) {
+          const int tx = win_asc(dx, txp);
+          gx = win_glob(dx, tx, N);
+          f = dm[(comp * dy.len + ty) * dx.len + tx] != 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (pass == 1 && f) {
+          const int rank = __popc(bal & ((1u << lane) - 1u));
+          dofs[outpos + total + rank] = comp * NN + gy * N + gx;
+        }
+        total += __popc(bal);
+      }
+    }
+  }
+  if (pass == 0 && lane == 0) sizes[p] = total;
+}
+
+// ------------------------------------------------------------------ local factorisation
+
+struct LevelK {
+  int N;
+  double h, rho_dt, mu, dt;
+  const int* row_of;
+  const int64_t* rowptr;
+  const int* cols;
+  const double* vals;
+};
+
+// Entry (ga, gb) of K_E on one level (Eq. Eul_schur), with or without the E_E term.
+__device__ double ke_entry(const LevelK& L, int ga, int gb, bool use_ee) {
+  const int N = L.N, NN = N * N;
+  const int ca = ga / NN, ra = ga % NN, ia = ra % N, ja = ra / N;
+  const int cb = gb / NN, rb = gb % NN, ib = rb % N, jb = rb / N;
+  if (ca < 2 && cb < 2) {
+    if (ca != cb) {
+      double v = 0.0;
+      if (use_ee && L.row_of[ga] >= 0) {
+        const int r = L.row_of[ga];
+        const int pos = find_col(L.cols, L.rowptr[r], L.rowptr[r + 1], gb);
+        if (pos >= 0) v = 0.0 - L.dt * L.vals[L.rowptr[r] + pos];
+      }
+      return v;
+    }
+    const double ih2 = 1.0 / (L.h * L.h);
+    double v = 0.0;
+    if (ga == gb) {
+      v = L.rho_dt - L.mu * (-4.0 / (L.h * L.h));
+    } else {
+      const int dxp = pmod(ia - ib, N), dyp = pmod(ja - jb, N);
+      int nb = 0;
+      if (ja == jb && (dxp == 1 || dxp == N - 1)) nb += (N == 2) ? 2 : 1;
+      if (ia == ib && (dyp == 1 || dyp == N - 1)) nb += (N == 2) ? 2 : 1;
+      if (nb) v = -L.mu * (nb * ih2);
+    }
+    if (use_ee && L.row_of[ga] >= 0) {
+      const int r = L.row_of[ga];
+      const int pos = find_col(L.cols, L.rowptr[r], L.rowptr[r + 1], gb);
+      if (pos >= 0) v = v - L.dt * L.vals[L.rowptr[r] + pos];
+    }
+    return v;
+  }
+  if (ca == 2 && cb == 2) return 0.0;
+  // G (velocity row, pressure column) and -D = G^T (pressure row, velocity column)
+  int cv, iv, jv, ip, jp;
+  if (ca < 2) { cv = ca; iv = ia; jv = ja; ip = ib; jp = jb; }
+  else { cv = cb; iv = ib; jv = jb; ip = ia; jp = ja; }
+  const double ih = 1.0 / L.h;
+  if (ip == iv && jp == jv) return ih;
+  if (cv == 0 && jp == jv && ip == pmod(iv - 1, N)) return -ih;
+  if (cv == 1 && ip == iv && jp == pmod(jv - 1, N)) return -ih;
+  return 0.0;
+}
+
+struct FactorJob {
+  const int64_t* dof_off;   // per patch offsets into dofs (n_jobs + 1)
+  const int* dofs;
+  const int64_t* mat_off;   // per patch element offset into A (ld * (n + border))
+  double* A;                // column-major, ld = round8(n + border)
+  double* s_r;              // per patch (n + border) scales; offsets dof_off[p] + p * border
+  double* s_c;
+  int* mdim;                // out: per patch matrix order m = n + border
+  int border_all_pressure;  // 1: add the pressure-mean border when a patch holds every pressure
+  int use_ee;
+};
+
+// One block per patch: extract K_{E,p} (column-major, ld = round8(m)), one pass of row then
+// column max-norm equilibration with power-of-two scales (Sec. 3.3), then in-place
+// Gauss-Jordan inversion with partial pivoting (first maximal row on ties).  The result is
+// the inverse of diag(s_r) K diag(s_c); a zero pivot raises DEV_SINGULAR.
+__global__ void k_factor(LevelK L, FactorJob J, int bordered_job, int* status) {
+  extern __shared__ double sh[];
+  const int p = blockIdx.x;
+  const int64_t d0 = J.dof_off[p];
+  const int n = (int)(J.dof_off[p + 1] - d0);
+  const int NN = L.N * L.N;
+  __shared__ int s_border;
+  __shared__ int s_piv;
+  __shared__ double s_pmax[32];
+  __shared__ int s_pidx[32];
+  if (threadIdx.x == 0) {
+    int border = 0;
+    if (bordered_job) border = 1;
+    else if (J.border_all_pressure) {
+      int np = 0;
+      for (int a = 0; a < n; ++a) np += (J.dofs[d0 + a] >= 2 * NN);
+      border = (np == NN);
+    }
+    s_border = border;
+    J.mdim[p] = n + border;
+  }
+  __syncthreads();
+  const int m = n + s_border;
+  const int ld = (m + 7) & ~7;
+  double* A = J.A + J.mat_off[p];
+  const int64_t so = d0 + p;  // one spare scale slot per patch for a border
+  double* sr = J.s_r + so;
+  double* sc = J.s_c + so;
+  double* rowk = sh;
+  double* colk = sh + m;
+  const int* dofs = J.dofs + d0;
+  // extraction
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int b = (int)(e / m), a = (int)(e % m);
+    double v;
+    if (a < n && b < n) v = ke_entry(L, dofs[a], dofs[b], J.use_ee != 0);
+    else if (a == n && b == n) v = 0.0;
+    else {
+      const int g = (a == n) ? dofs[b] : dofs[a];
+      v = (g >= 2 * NN) ? 1.0 : 0.0;
+    }
+    A[(int64_t)b * ld + a] = v;
+  }
+  __syncthreads();
+  // row scales
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    double mx = 0.0;
+    for (int b = 0; b < m; ++b) mx = fmax(mx, fabs(A[(int64_t)b * ld + a]));
+    sr[a] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
+    if (mx == 0.0) atomicExch(status, DEV_SINGULAR);
+  }
+  __syncthreads();
+  // column scales of diag(s_r) K
+  for (int b = threadIdx.x; b < m; b += blockDim.x) {
+    double mx = 0.0;
+    for (int a = 0; a < m; ++a) mx = fmax(mx, fabs(sr[a] * A[(int64_t)b * ld + a]));
+    sc[b] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int b = (int)(e / m), a = (int)(e % m);
+    A[(int64_t)b * ld + a] = sr[a] * A[(int64_t)b * ld + a] * sc[b];
+  }
+  __syncthreads();
+  // Gauss-Jordan with row pivoting; the column permutation is undone at the end
+  int* perm = reinterpret_cast<int*>(sh + 2 * m);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < m; ++k) {
+    // pivot: first row of maximal modulus in column k, rows k..m-1
+    double best = -1.0;
+    int bi = m;
+    for (int a = k + threadIdx.x; a < m; a += blockDim.x) {
+      const double v = fabs(A[(int64_t)k * ld + a]);
+      if (v > best) { best = v; bi = a; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_pmax[warp] = best; s_pidx[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bb = -1.0;
+      int ii = m;
+      for (int w = 0; w < nw; ++w)
+        if (s_pmax[w] > bb || (s_pmax[w] == bb && s_pidx[w] < ii)) { bb = s_pmax[w]; ii = s_pidx[w]; }
+      s_piv = ii;
+      perm[k] = ii;
+      if (!(bb > 0.0)) atomicExch(status, DEV_SINGULAR);
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != k && pr < m) {
+      for (int b = threadIdx.x; b < m; b += blockDim.x) {
+        const double t = A[(int64_t)b * ld + k];
+        A[(int64_t)b * ld + k] = A[(int64_t)b * ld + pr];
+        A[(int64_t)b * ld + pr] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = A[(int64_t)k * ld + k];
+    const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
+    for (int b = threadIdx.x; b < m; b += blockDim.x) {
+      rowk[b] = (b == k) ? ipiv : A[(int64_t)b * ld + k] * ipiv;
+    }
+    for (int a = threadIdx.x; a < m; a += blockDim.x) colk[a] = A[(int64_t)k * ld + a];
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+      const int b = (int)(e / m), a = (int)(e % m);
+      double v;
+      if (a == k) v = rowk[b];
+      else if (b == k) v = -colk[a] * ipiv;
+      else v = A[(int64_t)b * ld + a] - colk[a] * rowk[b];
+      A[(int64_t)b * ld + a] = v;
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = m - 1; k >= 0; --k) {
+    const int pr = perm[k];
+    if (pr != k && pr < m) {
+      for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        const double t = A[(int64_t)k * ld + a];
+        A[(int64_t)k * ld + a] = A[(int64_t)pr * ld + a];
+        A[(int64_t)pr * ld + a] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Fold the scalings: out[a][b] = s_c[a] X[a][b] s_r[b], row-major (m x m).
+__global__ void k_fold_rowmajor(int m, const double* X, const double* s_r, const double* s_c, double* out) {
+  const int ld = (m + 7) & ~7;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int a = e / m, b = e % m;
+    out[e] = s_c[a] * X[(int64_t)b * ld + a] * s_r[b];
+  }
+}
+
+template <typename T>
+__global__ void k_downcast(int64_t n, const double* in, T* out);
+template <>
+__global__ void k_downcast<float>(int64_t n, const double* in, float* out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+template <>
+__global__ void k_downcast<__nv_bfloat16>(int64_t n, const double* in, __nv_bfloat16* out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = __double2bfloat16(in[e]);
+}
+
+// transpose incidence: slots of each unknown (pass 0 counts, pass 1 fills)
+__global__ void k_incidence(int64_t n_slots, const int* dofs, int* count, const int64_t* off, int* cursor,
+                            int* slot, int pass) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const int d = dofs[s];
+  if (pass == 0) atomicAdd(&count[d], 1);
+  else slot[off[d] + atomicAdd(&cursor[d], 1)] = (int)s;
+}
+
+__global__ void k_sort_lists2(int n, const int64_t* off, int* list) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  const int64_t b = off[f], e = off[f + 1];
+  for (int64_t i = b + 1; i < e; ++i) {
+    const int v = list[i];
+    int64_t j = i - 1;
+    while (j >= b && list[j] > v) {
+      list[j + 1] = list[j];
+      --j;
+    }
+    list[j + 1] = v;
+  }
+}
+
+// Copy each factorised patch's leading n x n block (ld = round8(n)) and first n scales into
+// the packed storage used by the sweep.
+__global__ void k_pack(const int64_t* off, const int64_t* mat_off, const int* mdim, const int64_t* inv_off,
+                       const double* work, const double* wsr, const double* wsc, double* inv, double* s_r,
+                       double* s_c) {
+  const int p = blockIdx.x;
+  const int64_t d0 = off[p];
+  const int n = (int)(off[p + 1] - d0);
+  const int m = mdim[p];
+  const int lds = (m + 7) & ~7, ldd = (n + 7) & ~7;
+  const double* src = work + mat_off[p];
+  double* dst = inv + inv_off[p];
+  for (int64_t e = threadIdx.x; e < (int64_t)n * ldd; e += blockDim.x) {
+    const int b = (int)(e / ldd), a = (int)(e % ldd);
+    dst[e] = (a < n) ? src[(int64_t)b * lds + a] : 0.0;
+  }
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    s_r[d0 + a] = wsr[d0 + p + a];
+    s_c[d0 + a] = wsc[d0 + p + a];
+  }
+}
+
+// ------------------------------------------------------------------ driver
+
+static LevelK level_k(const Level& lv) {
+  LevelK k;
+  k.N = lv.N;
+  k.h = lv.h;
+  k.rho_dt = lv.rho_dt;
+  k.mu = lv.mu;
+  k.dt = lv.dt;
+  k.row_of = lv.ee.row_of;
+  k.rowptr = lv.ee.rowptr;
+  k.cols = lv.ee.cols;
+  k.vals = lv.ee.vals;
+  return k;
+}
+
+static size_t factor_smem(int m) { return (size_t)(2 * m) * sizeof(double) + (size_t)m * sizeof(int) + 16; }
+
+static void check_status(cav_hierarchy* H, cudaStream_t st, const char* where) {
+  const int s = read_status(H->status, st);
+  if (s == DEV_SINGULAR) {
+    set_error(std::string(where) + ": zero pivot in a local patch matrix");
+    throw Fail{IB_ERR_SINGULAR};
+  }
+  if (s != DEV_OK) {
+    set_error(std::string(where) + ": device consistency check failed (code " + std::to_string(s) + ")");
+    throw Fail{IB_ERR_INTERNAL};
+  }
+}
+
+static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+  Arena& A = H->arena;
+  Arena scratch;
+  const int N = lv.N, NN = N * N;
+  const LevelK LK = level_k(lv);
+  // 1. enlarged cells
+  lv.cell_big = A.alloc<uint8_t>(NN);
+  int* flag = scratch.alloc<int>(NN);
+  int64_t* pos = scratch.alloc<int64_t>(NN + 1);
+  k_cell_flags<<<div_up(NN, 256), 256, 0, st>>>(N, H->desc.kind == CAV_PATCH_CAV ? 1 : 0, lv.ee.row_of,
+                                               lv.ee.rowptr, lv.ee.cols, lv.cell_big, flag);
+  CAV_CHECK_LAUNCH();
+  exclusive_scan(flag, pos, NN, st, &scratch);
+  int64_t nbig = 0;
+  CAV_CHECK_CUDA(cudaMemcpyAsync(&nbig, pos + NN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  lv.n_big = (int)nbig;
+  lv.big_cell = A.alloc<int>(nbig);
+  k_compact_cells<<<div_up(NN, 256), 256, 0, st>>>(NN, flag, pos, lv.big_cell);
+  CAV_CHECK_LAUNCH();
+  // 2. patch sets (count, scan, write)
+  const int W = lv.ee.W;
+  const int Wc = W + 2, Wd = W + 3;
+  const int lenC = (2 * Wc + 1 >= N) ? N : 2 * Wc + 1;
+  const int lenD = (2 * Wd + 1 >= N) ? N : 2 * Wd + 1;
+  const int per_warp = lenC * lenC + 3 * lenD * lenD;
+  int warps = 8;
+  while (warps > 1 && (size_t)warps * per_warp > 96 * 1024) warps >>= 1;
+  const size_t smem = (size_t)warps * per_warp;
+  CAV_REQUIRE(smem <= 200 * 1024, "CAV patch window too large");
+  if (smem > 48 * 1024)
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_cav_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int* sizes = scratch.alloc<int>(nbig + 1);
+  lv.big_off = A.alloc<int64_t>(nbig + 1);
+  if (nbig > 0) {
+    k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
+                                                              lv.ee.rowptr, lv.ee.cols, sizes, nullptr,
+                                                              nullptr, 0, H->status);
+    CAV_CHECK_LAUNCH();
+  }
+  exclusive_scan(sizes, lv.big_off, nbig, st, &scratch);
+  std::vector<int> hsizes(nbig);
+  if (nbig > 0)
+    CAV_CHECK_CUDA(cudaMemcpyAsync(hsizes.data(), sizes, sizeof(int) * nbig, cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  int64_t sum_n = 0, sum_n2 = 0, inv_elems = 0;
+  int max_n = 0;
+  std::vector<int64_t> hinv_off(nbig + 1, 0), hmat_off(nbig + 2, 0);
+  for (int64_t p = 0; p < nbig; ++p) {
+    const int n = hsizes[p];
+    sum_n += n;
+    sum_n2 += (int64_t)n * n;
+    max_n = std::max(max_n, n);
+    hinv_off[p + 1] = hinv_off[p] + (int64_t)round8(n) * n;
+  }
+  lv.big_sum_n = sum_n;
+  lv.big_sum_n2 = sum_n2;
+  lv.big_max_n = max_n;
+  lv.inv_elems = inv_elems = hinv_off[nbig];
+  lv.big_dofs = A.alloc<int>(sum_n + 5);  // + 5: the standard patch appended for factorisation
+  if (nbig > 0) {
+    k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
+                                                              lv.ee.rowptr, lv.ee.cols, sizes, lv.big_off,
+                                                              lv.big_dofs, 1, H->status);
+    CAV_CHECK_LAUNCH();
+  }
+  check_status(H, st, "cav patch sets");
+  // launch order: descending size
+  std::vector<int> order(nbig);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hsizes[a] > hsizes[b]; });
+  lv.order = A.alloc<int>(nbig);
+  lv.inv_off = A.alloc<int64_t>(nbig + 1);
+  if (nbig > 0) {
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.order, order.data(), sizeof(int) * nbig, cudaMemcpyHostToDevice, st));
+  }
+  CAV_CHECK_CUDA(cudaMemcpyAsync(lv.inv_off, hinv_off.data(), sizeof(int64_t) * (nbig + 1),
+                                 cudaMemcpyHostToDevice, st));
+  // 3. factorise the enlarged patches plus the standard Vanka patch of cell (0, 0) (job nbig)
+  //    in canonical order (u_00, u_10, v_00, v_01, p_00) without E_E.
+  const int std_dofs[5] = {0, 1, NN, NN + N, 2 * NN};
+  CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs + sum_n, std_dofs, sizeof(int) * 5, cudaMemcpyHostToDevice, st));
+  std::vector<int64_t> hoff_ext(nbig + 2);
+  std::vector<int64_t> hbig_off(nbig + 1);
+  {
+    int64_t acc = 0;
+    for (int64_t p = 0; p <= nbig; ++p) {
+      hbig_off[p] = acc;
+      if (p < nbig) acc += hsizes[p];
+    }
+  }
+  for (int64_t p = 0; p <= nbig; ++p) hoff_ext[p] = hbig_off[std::min<int64_t>(p, nbig)];
+  hoff_ext[nbig + 1] = sum_n + 5;
+  for (int64_t p = 0; p <= nbig; ++p) {
+    const int m = (p < nbig) ? hsizes[p] : 5;
+    // a patch holding every pressure of the level gets one border row and column
+    hmat_off[p + 1] = hmat_off[p] + (int64_t)round8(m + 1) * (m + 1);
+  }
+  int64_t* d_off_ext = scratch.alloc<int64_t>(nbig + 2);
+  int64_t* d_mat_off = scratch.alloc<int64_t>(nbig + 2);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_off_ext, hoff_ext.data(), sizeof(int64_t) * (nbig + 2), cudaMemcpyHostToDevice, st));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_mat_off, hmat_off.data(), sizeof(int64_t) * (nbig + 2), cudaMemcpyHostToDevice, st));
+  double* work = scratch.alloc<double>(hmat_off[nbig + 1]);
+  double* wsr = scratch.alloc<double>(sum_n + nbig + 8);
+  double* wsc = scratch.alloc<double>(sum_n + nbig + 8);
+  int* mdim = scratch.alloc<int>(nbig + 2);
+  FactorJob J;
+  J.mdim = mdim;
+  J.dof_off = d_off_ext;
+  J.dofs = lv.big_dofs;
+  J.mat_off = d_mat_off;
+  J.A = work;
+  J.s_r = wsr;
+  J.s_c = wsc;
+  J.border_all_pressure = 1;
+  J.use_ee = 1;
+  const int mmax = std::max(max_n, 5) + 1;
+  const size_t fsm = factor_smem(mmax);
+  if (fsm > 48 * 1024)
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  if (nbig > 0) {
+    k_factor<<<(int)nbig, 256, fsm, st>>>(LK, J, 0, H->status);
+    CAV_CHECK_LAUNCH();
+  }
+  // the standard patch: same kernel, one block, no E_E
+  {
+    FactorJob Js = J;
+    Js.dof_off = d_off_ext + nbig;
+    Js.mat_off = d_mat_off + nbig;
+    Js.mdim = mdim + nbig;
+    Js.s_r = wsr + nbig;  // scale slots of this job start at sum_n + nbig
+    Js.s_c = wsc + nbig;
+    Js.use_ee = 0;
+    Js.border_all_pressure = 0;
+    k_factor<<<1, 64, factor_smem(6), st>>>(LK, Js, 0, H->status);
+    CAV_CHECK_LAUNCH();
+    double* d_std = scratch.alloc<double>(25);
+    k_fold_rowmajor<<<1, 32, 0, st>>>(5, work + hmat_off[nbig], wsr + sum_n + nbig, wsc + sum_n + nbig, d_std);
+    CAV_CHECK_LAUNCH();
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.std_inv, d_std, sizeof(double) * 25, cudaMemcpyDeviceToHost, st));
+  }
+  check_status(H, st, "patch factorisation");
+  // 4. pack the inverses (ld = round8(n), column-major) and scales; bordered patches are
+  //    applied with their border slot's residual entry equal to zero, so only the leading
+  //    n x n block and the first n scales are needed.
+  lv.s_r = A.alloc<double>(sum_n);
+  lv.s_c = A.alloc<double>(sum_n);
+  lv.inv64 = A.alloc<double>(std::max<int64_t>(inv_elems, 1));
+  if (nbig > 0) {
+    k_pack<<<(int)nbig, 256, 0, st>>>(lv.big_off, d_mat_off, mdim, lv.inv_off, work, wsr, wsc, lv.inv64,
+                                      lv.s_r, lv.s_c);
+    CAV_CHECK_LAUNCH();
+  }
+  lv.precision = H->desc.precision;
+  if (lv.precision == CAV_PREC_FP32) {
+    lv.inv32 = A.alloc<float>(std::max<int64_t>(inv_elems, 1));
+    k_downcast<float><<<1184, 256, 0, st>>>(inv_elems, lv.inv64, lv.inv32);
+    CAV_CHECK_LAUNCH();
+  } else if (lv.precision == CAV_PREC_BF16) {
+    lv.inv16 = A.alloc<__nv_bfloat16>(std::max<int64_t>(inv_elems, 1));
+    k_downcast<__nv_bfloat16><<<1184, 256, 0, st>>>(inv_elems, lv.inv64, lv.inv16);
+    CAV_CHECK_LAUNCH();
+  }
+  // 5. transpose incidence of the packed slots
+  int* cnt = scratch.alloc<int>(3 * NN);
+  int* cur = scratch.alloc<int>(3 * NN);
+  CAV_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * NN, st));
+  CAV_CHECK_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * 3 * NN, st));
+  lv.inc_off = A.alloc<int64_t>(3 * NN + 1);
+  lv.inc_slot = A.alloc<int>(sum_n);
+  if (sum_n > 0) {
+    k_incidence<<<div_up(sum_n, 256), 256, 0, st>>>(sum_n, lv.big_dofs, cnt, nullptr, nullptr, nullptr, 0);
+    CAV_CHECK_LAUNCH();
+  }
+  exclusive_scan(cnt, lv.inc_off, 3 * NN, st, &scratch);
+  if (sum_n > 0) {
+    k_incidence<<<div_up(sum_n, 256), 256, 0, st>>>(sum_n, lv.big_dofs, cnt, lv.inc_off, cur, lv.inc_slot, 1);
+    CAV_CHECK_LAUNCH();
+    k_sort_lists2<<<div_up(3 * NN, 256), 256, 0, st>>>(3 * NN, lv.inc_off, lv.inc_slot);
+    CAV_CHECK_LAUNCH();
+  }
+  lv.delta = A.alloc<double>(std::max<int64_t>(sum_n, 1));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  scratch.release();
+}
+
+static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+  Arena& A = H->arena;
+  Arena scratch;
+  const int N = lv.N, NN = N * N, n = 3 * NN, m = n + 1;
+  const LevelK LK = level_k(lv);
+  std::vector<int> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  int* d_dofs = scratch.alloc<int>(n);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_dofs, all.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  int64_t hoff[2] = {0, n};
+  int64_t hmo[2] = {0, (int64_t)round8(m) * m};
+  int64_t* d_off = scratch.alloc<int64_t>(2);
+  int64_t* d_mo = scratch.alloc<int64_t>(2);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_off, hoff, sizeof(hoff), cudaMemcpyHostToDevice, st));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_mo, hmo, sizeof(hmo), cudaMemcpyHostToDevice, st));
+  double* work = scratch.alloc<double>(hmo[1]);
+  double* wsr = scratch.alloc<double>(m);
+  double* wsc = scratch.alloc<double>(m);
+  int* mdim = scratch.alloc<int>(1);
+  FactorJob J;
+  J.mdim = mdim;
+  J.dof_off = d_off;
+  J.dofs = d_dofs;
+  J.mat_off = d_mo;
+  J.A = work;
+  J.s_r = wsr;
+  J.s_c = wsc;
+  J.border_all_pressure = 0;
+  J.use_ee = 1;
+  const size_t fsm = factor_smem(m);
+  if (fsm > 48 * 1024)
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  k_factor<<<1, 1024, fsm, st>>>(LK, J, 1, H->status);
+  CAV_CHECK_LAUNCH();
+  lv.coarse_inv = A.alloc<double>((size_t)m * m);
+  k_fold_rowmajor<<<64, 256, 0, st>>>(m, work, wsr, wsc, lv.coarse_inv);
+  CAV_CHECK_LAUNCH();
+  check_status(H, st, "coarsest factorisation");
+  scratch.release();
+}
+
+void build_levels(cav_hierarchy* H, cudaStream_t st) {
+  const ib_system* s = H->sys;
+  Arena& A = H->arena;
+  std::vector<int> sizes{s->N};
+  while (sizes.back() / 2 >= H->desc.coarsest_N && sizes.back() % 2 == 0) sizes.push_back(sizes.back() / 2);
+  CAV_REQUIRE(sizes.size() >= 2, "the grid cannot be coarsened to coarsest_N (need N >= 2 coarsest_N)");
+  H->levels.resize(sizes.size());
+  int* d_scr = A.alloc<int>(1);
+  for (size_t l = 0; l < sizes.size(); ++l) {
+    Level& lv = H->levels[l];
+    lv.N = sizes[l];
+    lv.h = s->L / lv.N;
+    lv.rho_dt = s->rho / s->dt;
+    lv.mu = s->mu;
+    lv.dt = s->dt;
+    lv.coarsest = (l + 1 == sizes.size());
+    if (l == 0) {
+      lv.ee = s->ee;  // owned by the system
+    } else {
+      galerkin_level(H->levels[l - 1].ee, lv.N, lv.ee, A, d_scr, st);
+    }
+    const int NN = lv.N * lv.N;
+    lv.r = A.alloc<double>(3 * NN);
+    lv.x = A.alloc<double>(3 * NN);
+    lv.b = A.alloc<double>(3 * NN);
+    lv.n_partial = div_up(lv.N, 32) * div_up(lv.N, 8);  // one partial per update block
+    lv.partial = A.alloc<double>(lv.n_partial);
+  }
+  for (size_t l = 0; l < sizes.size(); ++l) {
+    Level& lv = H->levels[l];
+    if (lv.coarsest) build_coarsest(H, lv, st);
+    else build_smoother(H, lv, st);
+  }
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace cav

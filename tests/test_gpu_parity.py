@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the same seeded
+inputs, element by element.  Integer work (E_E patterns, patch sets) must be bit-exact;
+floating point within the stated tolerances:
+
+  * E_E values, K_E products, transfers: |gpu - oracle| <= 1e-13 * max|.| (summation order)
+  * one sweep, per level: ||w_gpu - w_oracle|| / ||w_oracle|| <= SWEEP_TOL[case]; 1e-12 for
+    the plain FP64 target-point case, looser where the local matrices' condition number
+    (measured by the oracle) times eps says the inverses themselves differ by more
+  * FGMRES: iteration counts within one, both converged, solutions agree to 1e-8
+"""
+import numpy as np
+import pytest
+
+import ib_workloads as W
+from oracle import fgmres as ofg, ib as oib, multigrid as omg, patches as opat, smoother as osm
+from tests.gpu_helpers import gpu_ee_csr, gpu_hierarchy, host, rel, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = 0.85
+CASES = {
+    "target32": (lambda: W.config1(), 2, 1e-12),
+    "membrane32": (lambda: W.membrane_ellipse(32, 1e4), 1, 1e-11),
+    "beam32": (lambda: W.beam_curve(32, 128, k_bend=1e-1, k_stretch=1e1), 1, 1e-11),
+    "rows32": (lambda: W.paper_target_rows(32), 1, 1e-11),
+    "nomarkers16": (lambda: W.System(name="empty", N=16, L=1.0, rho=1.0, mu=0.01, dt=0.01, law=0,
+                                     closed=True, X=np.zeros((0, 2)), ds=0.1, omega=np.zeros(0)), 1, 1e-12),
+}
+
+
+class Pair:
+    pass
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def pair(request):
+    mk, nu, tol = CASES[request.param]
+    rec = mk()
+    P = Pair()
+    P.name, P.rec, P.nu, P.tol = request.param, rec, nu, tol
+    P.levels = omg.build_hierarchy(rec, 8, "cav")
+    P.sys, P.h = gpu_hierarchy(rec, kind="cav", coarsest_N=8, nu_pre=nu, nu_post=nu, alpha=ALPHA,
+                               precision="fp64")
+    return P
+
+
+def test_level_count(pair):
+    from paper_2608_14310_b300 import api
+    assert api.cav_num_levels(pair.h) == len(pair.levels)
+    for l, lev in enumerate(pair.levels):
+        info = api.cav_get_level_info(pair.h, l)
+        assert info["N"] == lev.N
+        assert bool(info["is_coarsest"]) == (l == len(pair.levels) - 1)
+
+
+def test_ee_pattern_bit_exact_values_close(pair):
+    for l, lev in enumerate(pair.levels):
+        G = gpu_ee_csr(pair.h, l)
+        if lev.EE is None:
+            assert G.nnz == 0
+            continue
+        O = lev.EE.tocsr()
+        O.sort_indices()
+        assert np.array_equal(G.indptr, O.indptr), f"level {l} row pointers"
+        assert np.array_equal(G.indices, O.indices), f"level {l} columns"
+        scale = np.abs(O.data).max()
+        assert np.abs(G.data - O.data).max() <= 1e-13 * scale, f"level {l} values"
+        # structural symmetry, which the CUDA patch builder relies on
+        S = (G != 0).astype(np.int8)
+        assert (S != S.T).nnz == 0
+
+
+def test_patch_sets_bit_exact(pair):
+    from paper_2608_14310_b300 import api
+    for l, lev in enumerate(pair.levels[:-1]):
+        off, dofs = api.cav_patch_export(pair.h, l)
+        assert off.size == len(lev.patches) + 1
+        for c, p in enumerate(lev.patches):
+            assert np.array_equal(dofs[off[c]:off[c + 1]], p), f"level {l} cell {c}"
+        info = api.cav_get_level_info(pair.h, l)
+        st = opat.patch_stats(lev.patches)
+        assert info["sum_n"] == st["sum_n"] and info["sum_n2"] == st["sum_n2"]
+        assert info["max_n"] == st["max_n"] and info["n_enlarged"] == st["enlarged"]
+
+
+def test_apply_and_residual(pair):
+    from paper_2608_14310_b300 import api
+    rng = np.random.default_rng(11)
+    for l, lev in enumerate(pair.levels):
+        n = 3 * lev.N ** 2
+        w = rng.standard_normal(n)
+        b = rng.standard_normal(n)
+        r = torch_dev(np.zeros(n))
+        api.cav_residual(pair.h, l, torch_dev(b), torch_dev(w), r)
+        want = b - lev.KE @ w
+        assert np.abs(host(r) - want).max() <= 1e-13 * np.abs(lev.KE @ w).max()
+    n = 3 * pair.rec.N ** 2
+    x = rng.standard_normal(n)
+    y = torch_dev(np.zeros(n))
+    api.ib_apply(pair.sys, torch_dev(x), y)
+    want = pair.levels[0].KE @ x
+    assert np.abs(host(y) - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_transfers_and_coarse_solve(pair):
+    from paper_2608_14310_b300 import api
+    rng = np.random.default_rng(12)
+    for l in range(len(pair.levels) - 1):
+        Nf, Nc = pair.levels[l].N, pair.levels[l + 1].N
+        r = rng.standard_normal(3 * Nf * Nf)
+        bc = torch_dev(np.zeros(3 * Nc * Nc))
+        api.cav_restrict(pair.h, l, torch_dev(r), bc)
+        assert np.abs(host(bc) - omg.restrict(Nc) @ r).max() <= 1e-14 * np.abs(r).max()
+        xc = rng.standard_normal(3 * Nc * Nc)
+        w0 = rng.standard_normal(3 * Nf * Nf)
+        w = torch_dev(w0)
+        api.cav_prolong_add(pair.h, l, torch_dev(xc), w)
+        assert np.abs(host(w) - (w0 + omg.prolong(Nc) @ xc)).max() <= 1e-14 * np.abs(w0).max() * 4
+    lev = pair.levels[-1]
+    b = W.rhs(lev.N, 7)
+    z = torch_dev(np.zeros(b.size))
+    api.cav_coarse_solve(pair.h, torch_dev(b), z)
+    want = omg.coarse_solve(lev, b)
+    assert rel(host(z), want) <= 1e-11
+
+
+def test_one_sweep_per_level(pair):
+    from paper_2608_14310_b300 import api
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    for l, lev in enumerate(pair.levels[:-1]):
+        n = 3 * lev.N ** 2
+        b = rng.uniform(-1, 1, n)
+        b[2 * lev.N ** 2:] -= b[2 * lev.N ** 2:].mean()
+        w0 = rng.uniform(-1, 1, n) * 1e-2
+        w = torch_dev(w0)
+        api.cav_sweep(pair.h, l, torch_dev(b), w)
+        got = host(w)
+        want = osm.additive_sweep(lev.KE, lev.solvers, lev.theta, w0, b, lev.N, ALPHA)
+        e = rel(got, want)
+        worst = max(worst, e)
+        # the residual after the sweep, as the paper's per-sweep quantity
+        rg = b - lev.KE @ got
+        ro = b - lev.KE @ want
+        assert rel(rg, ro) <= 100 * pair.tol * max(1.0, np.linalg.norm(lev.KE @ want) / np.linalg.norm(ro)), l
+        assert e <= pair.tol, (l, e)
+    print(f"{pair.name}: worst sweep rel diff {worst:.3e}")
+
+
+def test_sweep_is_deterministic(pair):
+    from paper_2608_14310_b300 import api
+    lev = pair.levels[0]
+    b = W.rhs(lev.N, 5)
+    outs = []
+    for _ in range(3):
+        w = torch_dev(np.full(b.size, 1e-3))
+        api.cav_sweep(pair.h, 0, torch_dev(b), w)
+        outs.append(host(w))
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_vcycle(pair):
+    from paper_2608_14310_b300 import api
+    b = pair.rec.rhs()
+    z = torch_dev(np.zeros(b.size))
+    api.vcycle_apply(pair.h, torch_dev(b), z)
+    want = omg.vcycle(pair.levels, b, pair.nu, pair.nu, "additive", ALPHA)
+    assert rel(host(z), want) <= 10 * pair.tol
+
+
+def test_fgmres(pair):
+    from paper_2608_14310_b300 import api
+    b = pair.rec.rhs()
+    x = torch_dev(np.zeros(b.size))
+    info = api.fgmres_solve(pair.sys, pair.h, torch_dev(b), x, rtol=1e-10, maxit=150)
+    K = pair.levels[0].KE
+    xo, io = ofg.fgmres(lambda v: K @ v, b,
+                        lambda r: omg.vcycle(pair.levels, r, pair.nu, pair.nu, "additive", ALPHA),
+                        rtol=1e-10, maxit=150)
+    assert info["converged"] == 1 and io["converged"]
+    assert abs(info["iters"] - io["iters"]) <= 1, (info["iters"], io["iters"])
+    xg = host(x)
+    assert np.linalg.norm(b - K @ xg) <= 2e-10 * np.linalg.norm(b)
+    assert rel(xg, xo) <= 1e-8
+    print(f"{pair.name}: gpu its {info['iters']} oracle its {io['iters']} relres {info['relres_true']:.2e}")

@@ -346,6 +346,9 @@ ib_status cav_profile(cav_hierarchy* h, int32_t enable) {
   }
   h->prof_on = enable ? 1 : 0;
   h->prof_used = 0;
+  h->prof_pending.clear();
+  h->prof_acc_ms = 0.0;
+  h->prof_acc_n = 0;
   return IB_OK;
   CAV_API_END
 }
@@ -353,16 +356,11 @@ ib_status cav_profile(cav_hierarchy* h, int32_t enable) {
 ib_status cav_profile_read(cav_hierarchy* h, int32_t* launches, double* total_ms) {
   CAV_API_BEGIN
   CAV_REQUIRE(h && launches && total_ms, "cav_profile_read: NULL argument");
-  double t = 0.0;
-  for (int q = 0; q < h->prof_used; ++q) {
-    CAV_CHECK_CUDA(cudaEventSynchronize(h->prof_ev[2 * q + 1]));
-    float ms = 0.f;
-    CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[2 * q], h->prof_ev[2 * q + 1]));
-    t += ms;
-  }
-  *launches = h->prof_used;
-  *total_ms = t;
-  h->prof_used = 0;
+  prof_collect(h);
+  *launches = h->prof_acc_n;
+  *total_ms = h->prof_acc_ms;
+  h->prof_acc_n = 0;
+  h->prof_acc_ms = 0.0;
   return IB_OK;
   CAV_API_END
 }
@@ -370,6 +368,7 @@ ib_status cav_profile_read(cav_hierarchy* h, int32_t* launches, double* total_ms
 void cav_destroy(cav_hierarchy* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  vcycle_release(h);
   for (auto& e : h->prof_ev) cudaEventDestroy(e);
   h->arena.release();
   h->ws_arena.release();

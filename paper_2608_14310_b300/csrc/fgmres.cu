@@ -227,6 +227,7 @@ ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b_in,
       CAV_CHECK_LAUNCH();
       CAV_CHECK_CUDA(cudaMemcpyAsync(hbuf + 4, misc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
       CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+      if (H->prof_on) prof_collect(H);
       k_done = k + 1;
       est = hbuf[4] / ref;
       if (history) history[k + 1] = est;

@@ -41,7 +41,7 @@ void note_launch();
   } while (0)
 
 // Device status word codes (written by kernels, read by the host after set-up or a solve).
-enum : int { DEV_OK = 0, DEV_WINDOW = 1, DEV_SINGULAR = 2, DEV_CAPACITY = 3 };
+enum : int { DEV_OK = 0, DEV_WINDOW = 1, DEV_SINGULAR = 2, DEV_CAPACITY = 3, DEV_TIMEOUT = 4 };
 
 // ------------------------------------------------------------------ device memory
 
@@ -103,6 +103,8 @@ struct Level {
   int precision = CAV_PREC_FP64;
   int64_t* inc_off = nullptr;    // [3 N^2 + 1] transpose incidence: slots of each unknown
   int* inc_slot = nullptr;       // [big_sum_n] packed-delta slots, ascending per unknown
+  int n_touched = 0;             // unknowns held by at least one enlarged patch
+  int* touched = nullptr;        // [n_touched] ascending
   double std_inv[25];            // inverse of the standard Vanka patch, canonical order
                                  // (u_ij, u_i+1j, v_ij, v_ij+1, p_ij), scalings folded in
 
@@ -114,8 +116,9 @@ struct Level {
   double* x = nullptr;           // [3 N^2] V-cycle iterate
   double* b = nullptr;           // [3 N^2] V-cycle right-hand side (levels > 0)
   double* delta = nullptr;       // [big_sum_n] packed patch corrections
-  double* partial = nullptr;     // [reduce blocks] partial sums for the pressure mean
-  int n_partial = 0;
+  double* partial = nullptr;     // partial sums for the pressure mean: stencil part, then
+  int n_partial = 0;             // the part of the unknowns touched by enlarged patches
+  int n_partial_std = 0;
 };
 
 }  // namespace cav
@@ -165,7 +168,16 @@ struct cav_hierarchy {
   // live timing of the finest level's patch-apply launches
   int prof_on = 0;
   int prof_used = 0;
-  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) for launches outside graphs
+  std::vector<int> prof_pending;     // pairs recorded but not yet read
+  double prof_acc_ms = 0.0;
+  int prof_acc_n = 0;
+  // V-cycle captured once as a CUDA graph (input lv0.b, output lv0.x), replayed per call
+  cudaGraphExec_t vc_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::vector<cudaEvent_t> vc_ev;    // event pairs around the finest-level applies in the graph
+  int capturing = 0;
+  int graph_failed = 0;
 };
 
 namespace cav {
@@ -201,6 +213,8 @@ void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
 void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
+void prof_collect(cav_hierarchy* H);
+void vcycle_release(cav_hierarchy* H);
 void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
 
 // reductions (reduce.cu)

@@ -209,6 +209,11 @@ __global__ void k_cell_flags(int N, int cav, const int* __restrict__ row_of, con
   flag[cidx] = enl;
 }
 
+__global__ void k_flag_nonempty_off(int n, const int64_t* off, int* flag) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < n) flag[f] = (off[f + 1] > off[f]) ? 1 : 0;
+}
+
 __global__ void k_compact_cells(int n, const int* flag, const int64_t* pos, int* out) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f < n && flag[f]) out[pos[f]] = f;
@@ -790,6 +795,24 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     k_sort_lists2<<<div_up(3 * NN, 256), 256, 0, st>>>(3 * NN, lv.inc_off, lv.inc_slot);
     CAV_CHECK_LAUNCH();
   }
+  // unknowns held by at least one enlarged patch (ascending), for the warp-per-unknown scatter
+  {
+    int* tflag = scratch.alloc<int>(3 * NN);
+    int64_t* tpos = scratch.alloc<int64_t>(3 * NN + 1);
+    k_flag_nonempty_off<<<div_up(3 * NN, 256), 256, 0, st>>>(3 * NN, lv.inc_off, tflag);
+    CAV_CHECK_LAUNCH();
+    exclusive_scan(tflag, tpos, 3 * NN, st, &scratch);
+    int64_t nt = 0;
+    CAV_CHECK_CUDA(cudaMemcpyAsync(&nt, tpos + 3 * NN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    lv.n_touched = (int)nt;
+    lv.touched = A.alloc<int>(nt);
+    k_compact_cells<<<div_up(3 * NN, 256), 256, 0, st>>>(3 * NN, tflag, tpos, lv.touched);
+    CAV_CHECK_LAUNCH();
+  }
+  lv.n_partial_std = div_up(N, 32) * div_up(N, 8);
+  lv.n_partial = lv.n_partial_std + div_up(lv.n_touched, 8);
+  lv.partial = A.alloc<double>(lv.n_partial);
   lv.delta = A.alloc<double>(std::max<int64_t>(sum_n, 1));
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   scratch.release();
@@ -861,8 +884,6 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     lv.r = A.alloc<double>(3 * NN);
     lv.x = A.alloc<double>(3 * NN);
     lv.b = A.alloc<double>(3 * NN);
-    lv.n_partial = div_up(lv.N, 32) * div_up(lv.N, 8);  // one partial per update block
-    lv.partial = A.alloc<double>(lv.n_partial);
   }
   for (size_t l = 0; l < sizes.size(); ++l) {
     Level& lv = H->levels[l];

@@ -3,11 +3,15 @@
 // A sweep on level l with iterate w and right-hand side b:
 //   1. r = b - K_E w                                   (stencil kernel + E_E rows)
 //   2. delta_p = diag(s_c) X_p diag(s_r) r|_p for every enlarged patch p
-//      (batched variable-size GEMV, one CTA per patch, inverses streamed from HBM)
-//   3. w_k += alpha / count_k * (sum over standard patches holding k of their 5x5 solve
-//      + sum over enlarged patches holding k of delta_p at k's slot)
-//      (owner computes: one thread per cell, fixed summation order, no atomics)
+//      (batched variable-size GEMV; the inverses, the only large operand, are streamed
+//      from HBM through shared memory by TMA bulk copies in a persistent kernel)
+//   3. w_k += alpha / count_k * (sum of the corrections at k of every patch holding k):
+//      unknowns held only by standard 5-unknown Vanka patches in a stencil kernel (their
+//      shared 5x5 inverse is applied on the fly), the others one warp per unknown over the
+//      slots of the enlarged patches holding it (fixed order, no atomics)
 //   4. remove the mean pressure (Sec. 3.3).
+#include <mutex>
+
 #include "internal.cuh"
 #include "device_util.cuh"
 
@@ -26,6 +30,11 @@ struct VecLoad<double> {
     out[0] = v.x;
     out[1] = v.y;
   }
+  __device__ static void load_shared(const double* p, acc_t* out) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    out[0] = v.x;
+    out[1] = v.y;
+  }
 };
 template <>
 struct VecLoad<float> {
@@ -38,13 +47,19 @@ struct VecLoad<float> {
     out[2] = v.z;
     out[3] = v.w;
   }
+  __device__ static void load_shared(const float* p, acc_t* out) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+    out[3] = v.w;
+  }
 };
 template <>
 struct VecLoad<__nv_bfloat16> {
   static constexpr int V = 8;
   typedef float acc_t;
-  __device__ static void load(const __nv_bfloat16* p, acc_t* out) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+  __device__ static void unpack(const uint4& v, acc_t* out) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -53,11 +68,17 @@ struct VecLoad<__nv_bfloat16> {
       out[2 * q + 1] = f.y;
     }
   }
+  __device__ static void load(const __nv_bfloat16* p, acc_t* out) {
+    unpack(__ldg(reinterpret_cast<const uint4*>(p)), out);
+  }
+  __device__ static void load_shared(const __nv_bfloat16* p, acc_t* out) {
+    unpack(*reinterpret_cast<const uint4*>(p), out);
+  }
 };
 
-// One CTA per enlarged patch (in descending-size order).  The scaled residual
-// y = s_r * r|_p is staged in shared memory; the inverse is column-major with ld = round8(n)
-// so each thread owns V consecutive rows and streams one 16-byte vector per column.
+// Fallback for patches too large for the pipelined kernel: one CTA per patch, the scaled
+// residual in shared memory, the column-major inverse (ld = round8(n)) read straight from
+// global memory, each thread owning V consecutive rows.
 template <typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, const int* __restrict__ dofs,
@@ -80,18 +101,7 @@ k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, co
 #pragma unroll
     for (int q = 0; q < V; ++q) acc[q] = 0;
     const T* col = X + a0;
-    int b = 0;
-    for (; b + 4 <= n; b += 4) {
-      acc_t x0[V], x1[V], x2[V], x3[V];
-      VL::load(col + (int64_t)(b + 0) * ld, x0);
-      VL::load(col + (int64_t)(b + 1) * ld, x1);
-      VL::load(col + (int64_t)(b + 2) * ld, x2);
-      VL::load(col + (int64_t)(b + 3) * ld, x3);
-      const acc_t y0 = y[b], y1 = y[b + 1], y2 = y[b + 2], y3 = y[b + 3];
-#pragma unroll
-      for (int q = 0; q < V; ++q) acc[q] += x0[q] * y0 + x1[q] * y1 + x2[q] * y2 + x3[q] * y3;
-    }
-    for (; b < n; ++b) {
+    for (int b = 0; b < n; ++b) {
       acc_t x0[V];
       VL::load(col + (int64_t)b * ld, x0);
       const acc_t yb = y[b];
@@ -101,6 +111,198 @@ k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, co
 #pragma unroll
     for (int q = 0; q < V; ++q)
       if (a0 + q < n) delta[d0 + a0 + q] = s_c[d0 + a0 + q] * (double)acc[q];
+  }
+}
+
+// ---- TMA / mbarrier primitives (inline PTX) ----------------------------------------------
+
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+      : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete; gives up after ~2^31 clock cycles
+// (about a second), records DEV_TIMEOUT and returns false.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) {
+      atomicExch(status, DEV_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+// 1-D bulk copy global -> this CTA's shared memory, completing `bytes` on the mbarrier.
+__device__ inline void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
+
+constexpr int TMA_STAGES = 4;
+constexpr int TMA_CHUNK = 16384;        // bytes per stage (a whole number of columns)
+constexpr int TMA_CONSUMER_WARPS = 4;
+constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 1);
+constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
+
+template <typename T>
+__host__ __device__ constexpr int tma_max_rows() {
+  return TMA_MAXPASS * 32 * TMA_CONSUMER_WARPS * VecLoad<T>::V;
+}
+
+// Persistent batched patch apply.  CTA c takes patches c, c + G, c + 2G, ... of the
+// size-descending order.  Warp 0 (one lane) is the producer: it streams each patch's
+// column-major inverse, a contiguous block of n * ld elements, into a ring of TMA_STAGES
+// shared-memory stages of at most TMA_CHUNK bytes (whole columns) with cp.async.bulk, each
+// stage guarded by a "full" mbarrier (transaction bytes) and an "empty" mbarrier (one
+// arrival per consumer warp).  Warps 1..4 are consumers: per patch they gather
+// y = s_r * r|_p into shared memory, then accumulate acc[rows] += X[rows, b] y[b] from each
+// stage as it lands, release the stage, and finally write delta = s_c * acc.  Every wait
+// is bounded; a timed-out wait records DEV_TIMEOUT and the CTA stops.
+template <typename T>
+__global__ void __launch_bounds__(TMA_THREADS)
+k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __restrict__ off,
+                  const int* __restrict__ dofs, const int64_t* __restrict__ inv_off, const T* __restrict__ inv,
+                  const double* __restrict__ s_r, const double* __restrict__ s_c, const double* __restrict__ r,
+                  double* __restrict__ delta, int max_n, int* status) {
+  typedef VecLoad<T> VL;
+  typedef typename VL::acc_t acc_t;
+  constexpr int V = VL::V;
+  constexpr int CT = 32 * TMA_CONSUMER_WARPS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stage_buf = smem;
+  acc_t* y = reinterpret_cast<acc_t*>(smem + TMA_STAGES * TMA_CHUNK);
+  const size_t ybytes = ((size_t)max_n * sizeof(acc_t) + 127) & ~(size_t)127;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TMA_STAGES * TMA_CHUNK + ybytes);
+  uint64_t* empty = full + TMA_STAGES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], TMA_CONSUMER_WARPS);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
+        const int p = order[q];
+        const int n = (int)(off[p + 1] - off[p]);
+        const uint32_t col_bytes = (uint32_t)(((n + 7) & ~7) * sizeof(T));
+        const int cpc = TMA_CHUNK / (int)col_bytes;
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + inv_off[p]);
+        for (int b0 = 0; b0 < n; b0 += cpc) {
+          const int nc = min(cpc, n - b0);
+          if (!mbar_wait(&empty[stage], phase ^ 1u, status)) return;
+          const uint32_t bytes = (uint32_t)nc * col_bytes;
+          mbar_arrive_expect_tx(&full[stage], bytes);
+          bulk_copy_g2s(stage_buf + (size_t)stage * TMA_CHUNK, src + (size_t)b0 * col_bytes, bytes, &full[stage]);
+          if (++stage == TMA_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  const int ct = threadIdx.x - 32;
+  int stage = 0;
+  uint32_t phase = 0;
+  // After a timed-out wait a consumer stops computing and waiting but keeps walking the
+  // same patch sequence, so every consumer still reaches every named barrier.
+  bool alive = true;
+  for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
+    const int p = order[q];
+    const int64_t d0 = off[p];
+    const int n = (int)(off[p + 1] - d0);
+    const int ld = (n + 7) & ~7;
+    const int cpc = TMA_CHUNK / (int)(ld * sizeof(T));
+    consumer_sync(CT);  // every consumer is done with the previous patch's y
+    for (int b = ct; b < n; b += CT) y[b] = (acc_t)(s_r[d0 + b] * r[dofs[d0 + b]]);
+    consumer_sync(CT);
+    acc_t acc[TMA_MAXPASS][V];
+#pragma unroll
+    for (int ps = 0; ps < TMA_MAXPASS; ++ps)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[ps][v] = 0;
+    for (int b0 = 0; b0 < n; b0 += cpc) {
+      const int nc = min(cpc, n - b0);
+      if (alive && !mbar_wait(&full[stage], phase, status)) alive = false;
+      const T* X = reinterpret_cast<const T*>(stage_buf + (size_t)stage * TMA_CHUNK);
+#pragma unroll
+      for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
+        const int a0 = (ps * CT + ct) * V;
+        if (alive && a0 < n) {
+          int c = 0;
+          for (; c + 2 <= nc; c += 2) {
+            acc_t x0[V], x1[V];
+            VL::load_shared(X + (size_t)c * ld + a0, x0);
+            VL::load_shared(X + (size_t)(c + 1) * ld + a0, x1);
+            const acc_t y0 = y[b0 + c], y1 = y[b0 + c + 1];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[ps][v] += x0[v] * y0 + x1[v] * y1;
+          }
+          if (c < nc) {
+            acc_t x0[V];
+            VL::load_shared(X + (size_t)c * ld + a0, x0);
+            const acc_t y0 = y[b0 + c];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[ps][v] += x0[v] * y0;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++stage == TMA_STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+#pragma unroll
+    for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
+      const int a0 = (ps * CT + ct) * V;
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (alive && a0 + v < n) delta[d0 + a0 + v] = s_c[d0 + a0 + v] * (double)acc[ps][v];
+    }
   }
 }
 
@@ -120,11 +322,14 @@ __device__ inline double std_row(const StdInv& S, int row, const double* __restr
   return m[0] * y0 + m[1] * y1 + m[2] * y2 + m[3] * y3 + m[4] * y4;
 }
 
+// Unknowns that no enlarged patch holds: both incident cells (one for a pressure) keep
+// their standard patch, so count_k is 2 (1) and the correction is the stencil of the
+// shared 5x5 inverse.  One thread per cell; unknowns held by enlarged patches are left to
+// k_update_touched.  Block partial sums of the new pressures feed the mean.
 template <int BX, int BY>
 __global__ void __launch_bounds__(BX* BY)
-k_update(int N, double alpha, StdInv S, const uint8_t* __restrict__ cell_big, const int64_t* __restrict__ inc_off,
-         const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
-         double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
+k_update_std(int N, double alpha, StdInv S, const int64_t* __restrict__ inc_off, const double* __restrict__ r,
+             double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
   __shared__ double sm[BX * BY / 32];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
@@ -133,51 +338,78 @@ k_update(int N, double alpha, StdInv S, const uint8_t* __restrict__ cell_big, co
   if (i < N && j < N) {
     const int c = j * N + i;
     const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
-    const bool big_c = cell_big[c] != 0;
-    const bool big_l = cell_big[j * N + im] != 0, big_d = cell_big[jm * N + i] != 0;
-    // u_ij: standard patches of cells (i-1, j) [slot 1] and (i, j) [slot 0]
-    {
-      double s = 0.0;
-      int cnt = 0;
-      if (!big_l) { s += std_row(S, 1, r, N, im, j); ++cnt; }
-      if (!big_c) { s += std_row(S, 0, r, N, i, j); ++cnt; }
-      const int k = c;
-      for (int64_t q = inc_off[k]; q < inc_off[k + 1]; ++q) { s += delta[inc_slot[q]]; ++cnt; }
-      const double old = w_is_zero ? 0.0 : w[k];
-      w[k] = old + alpha * (s / (double)cnt);
+    if (inc_off[c + 1] == inc_off[c]) {
+      const double s = std_row(S, 1, r, N, im, j) + std_row(S, 0, r, N, i, j);
+      w[c] = (w_is_zero ? 0.0 : w[c]) + alpha * (s / 2.0);
     }
-    // v_ij: standard patches of cells (i, j-1) [slot 3] and (i, j) [slot 2]
-    {
-      double s = 0.0;
-      int cnt = 0;
-      if (!big_d) { s += std_row(S, 3, r, N, i, jm); ++cnt; }
-      if (!big_c) { s += std_row(S, 2, r, N, i, j); ++cnt; }
-      const int k = NN + c;
-      for (int64_t q = inc_off[k]; q < inc_off[k + 1]; ++q) { s += delta[inc_slot[q]]; ++cnt; }
-      const double old = w_is_zero ? 0.0 : w[k];
-      w[k] = old + alpha * (s / (double)cnt);
+    if (inc_off[NN + c + 1] == inc_off[NN + c]) {
+      const double s = std_row(S, 3, r, N, i, jm) + std_row(S, 2, r, N, i, j);
+      w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * (s / 2.0);
     }
-    // p_ij: the standard patch of cell (i, j) [slot 4]
-    {
-      double s = 0.0;
-      int cnt = 0;
-      if (!big_c) { s += std_row(S, 4, r, N, i, j); ++cnt; }
-      const int k = 2 * NN + c;
-      for (int64_t q = inc_off[k]; q < inc_off[k + 1]; ++q) { s += delta[inc_slot[q]]; ++cnt; }
-      const double old = w_is_zero ? 0.0 : w[k];
-      pnew = old + alpha * (s / (double)cnt);
-      w[k] = pnew;
+    if (inc_off[2 * NN + c + 1] == inc_off[2 * NN + c]) {
+      const double s = std_row(S, 4, r, N, i, j);
+      pnew = (w_is_zero ? 0.0 : w[2 * NN + c]) + alpha * s;
+      w[2 * NN + c] = pnew;
     }
   }
-  // partial sums of the new pressure for the mean (fixed order)
   const int tid = threadIdx.y * BX + threadIdx.x;
-  double v = warp_sum(pnew);
+  const double v = warp_sum(pnew);
   if ((tid & 31) == 0) sm[tid >> 5] = v;
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
     for (int q = 0; q < BX * BY / 32; ++q) t += sm[q];
     partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+constexpr int TOUCH_WARPS = 8;
+
+// One warp per unknown held by at least one enlarged patch: the lanes sum the enlarged
+// patches' corrections at the unknown (fixed lane-strided order, fixed shuffle tree), lane 0
+// adds the standard patches of its incident cells that kept their Vanka patch and divides
+// by the total patch count.
+__global__ void __launch_bounds__(32 * TOUCH_WARPS)
+k_update_touched(int N, double alpha, StdInv S, int n_touched, const int* __restrict__ touched,
+                 const uint8_t* __restrict__ cell_big, const int64_t* __restrict__ inc_off,
+                 const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
+                 double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
+  __shared__ double sm[TOUCH_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * TOUCH_WARPS + warp;
+  double pnew = 0.0;
+  if (t < n_touched) {
+    const int k = touched[t];
+    const int64_t q0 = inc_off[k], q1 = inc_off[k + 1];
+    double s = 0.0;
+    for (int64_t q = q0 + lane; q < q1; q += 32) s += delta[inc_slot[q]];
+    s = warp_sum(s);
+    if (lane == 0) {
+      const int NN = N * N;
+      const int comp = k / NN, c = k % NN, i = c % N, j = c / N;
+      const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
+      int cnt = (int)(q1 - q0);
+      double st = 0.0;
+      if (comp == 0) {
+        if (!cell_big[j * N + im]) { st += std_row(S, 1, r, N, im, j); ++cnt; }
+        if (!cell_big[c]) { st += std_row(S, 0, r, N, i, j); ++cnt; }
+      } else if (comp == 1) {
+        if (!cell_big[jm * N + i]) { st += std_row(S, 3, r, N, i, jm); ++cnt; }
+        if (!cell_big[c]) { st += std_row(S, 2, r, N, i, j); ++cnt; }
+      } else {
+        if (!cell_big[c]) { st += std_row(S, 4, r, N, i, j); ++cnt; }
+      }
+      const double nw = (w_is_zero ? 0.0 : w[k]) + alpha * ((st + s) / (double)cnt);
+      w[k] = nw;
+      if (comp == 2) pnew = nw;
+    }
+  }
+  if (lane == 0) sm[warp] = pnew;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < TOUCH_WARPS; ++q) tot += sm[q];
+    partial[blockIdx.x] = tot;
   }
 }
 
@@ -206,7 +438,6 @@ __global__ void k_coarse_apply(int n, const double* __restrict__ inv, const doub
 
 // ------------------------------------------------------------------ host drivers
 
-static constexpr int APPLY_THREADS = 128;
 static constexpr int UBX = 32, UBY = 8;
 
 static LevelOps ops_of(const Level& lv) {
@@ -222,51 +453,120 @@ static LevelOps ops_of(const Level& lv) {
 
 void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st) {
   cav_hierarchy* h = const_cast<cav_hierarchy*>(H);
-  if (!h->prof_on || level != 0) return;
-  if ((size_t)(2 * h->prof_used + 1) >= h->prof_ev.size()) return;
+  if (level != 0) return;
+  if (h->capturing) {
+    const size_t q = h->vc_ev.size();
+    h->vc_ev.resize(q + 2);
+    CAV_CHECK_CUDA(cudaEventCreate(&h->vc_ev[q]));
+    CAV_CHECK_CUDA(cudaEventCreate(&h->vc_ev[q + 1]));
+    // External: becomes an event-record node of the graph, recorded on every replay
+    CAV_CHECK_CUDA(cudaEventRecordWithFlags(h->vc_ev[q], st, cudaEventRecordExternal));
+    return;
+  }
+  if (!h->prof_on || (size_t)(2 * h->prof_used + 1) >= h->prof_ev.size()) return;
   CAV_CHECK_CUDA(cudaEventRecord(h->prof_ev[2 * h->prof_used], st));
 }
 void prof_end(const cav_hierarchy* H, int level, cudaStream_t st) {
   cav_hierarchy* h = const_cast<cav_hierarchy*>(H);
-  if (!h->prof_on || level != 0) return;
-  if ((size_t)(2 * h->prof_used + 1) >= h->prof_ev.size()) return;
+  if (level != 0) return;
+  if (h->capturing) {
+    CAV_CHECK_CUDA(cudaEventRecordWithFlags(h->vc_ev.back(), st, cudaEventRecordExternal));
+    return;
+  }
+  if (!h->prof_on || (size_t)(2 * h->prof_used + 1) >= h->prof_ev.size()) return;
   CAV_CHECK_CUDA(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], st));
+  h->prof_pending.push_back(h->prof_used);
   ++h->prof_used;
 }
 
+// Read every recorded-but-unread pair (after the stream has been synchronised).
+void prof_collect(cav_hierarchy* H) {
+  for (int q : H->prof_pending) {
+    float ms = 0.f;
+    if (q >= 0) {
+      CAV_CHECK_CUDA(cudaEventSynchronize(H->prof_ev[2 * q + 1]));
+      CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, H->prof_ev[2 * q], H->prof_ev[2 * q + 1]));
+    } else {
+      const int g = -q - 1;
+      CAV_CHECK_CUDA(cudaEventSynchronize(H->vc_ev[2 * g + 1]));
+      CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, H->vc_ev[2 * g], H->vc_ev[2 * g + 1]));
+    }
+    H->prof_acc_ms += ms;
+    H->prof_acc_n += 1;
+  }
+  H->prof_pending.clear();
+  H->prof_used = 0;
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    CAV_CHECK_CUDA(cudaGetDevice(&dev));
+    CAV_CHECK_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
 template <typename T>
-static void launch_patch_apply(const Level& lv, const T* inv, const double* r, cudaStream_t st) {
+static void launch_patch_apply(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r, double* delta,
+                               cudaStream_t st) {
   typedef typename VecLoad<T>::acc_t acc_t;
-  const size_t smem = sizeof(acc_t) * (size_t)lv.big_max_n;
-  k_patch_apply<T, APPLY_THREADS><<<lv.n_big, APPLY_THREADS, smem, st>>>(
-      lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r, lv.s_c, r, lv.delta);
+  if (lv.big_max_n <= tma_max_rows<T>() && (size_t)round8(lv.big_max_n) * sizeof(T) <= (size_t)TMA_CHUNK) {
+    const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
+    const size_t smem = (size_t)TMA_STAGES * TMA_CHUNK + ybytes + 2 * TMA_STAGES * sizeof(uint64_t);
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(k_patch_apply_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    const int grid = std::min(lv.n_big, 2 * sm_count());
+    k_patch_apply_tma<T><<<grid, TMA_THREADS, smem, st>>>(lv.n_big, lv.order, lv.big_off, lv.big_dofs, lv.inv_off,
+                                                          inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
+  } else {
+    const size_t smem = sizeof(acc_t) * (size_t)lv.big_max_n;
+    k_patch_apply<T, 128><<<lv.n_big, 128, smem, st>>>(lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r,
+                                                      lv.s_c, r, delta);
+  }
+  CAV_CHECK_LAUNCH();
+}
+
+// The four steps of one sweep with explicit scratch (residual r_buf, packed corrections
+// delta_buf, partial sums partial_buf); shared by cav_sweep and cav_sweep_noalloc.
+static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, double* r_buf,
+                       double* delta_buf, double* partial_buf, bool profile, cudaStream_t st) {
+  const Level& lv = H->levels[l];
+  const double* r = b;
+  if (!w_is_zero) {
+    launch_apply(ops_of(lv), w, b, r_buf, 0, st);
+    r = r_buf;
+  }
+  if (lv.n_big > 0) {
+    if (profile) prof_begin(H, l, st);
+    if (lv.precision == CAV_PREC_FP32) launch_patch_apply<float>(H, lv, lv.inv32, r, delta_buf, st);
+    else if (lv.precision == CAV_PREC_BF16) launch_patch_apply<__nv_bfloat16>(H, lv, lv.inv16, r, delta_buf, st);
+    else launch_patch_apply<double>(H, lv, lv.inv64, r, delta_buf, st);
+    if (profile) prof_end(H, l, st);
+  }
+  StdInv S;
+  for (int q = 0; q < 25; ++q) S.m[q] = lv.std_inv[q];
+  dim3 blk(UBX, UBY), grd(div_up(lv.N, UBX), div_up(lv.N, UBY));
+  k_update_std<UBX, UBY><<<grd, blk, 0, st>>>(lv.N, H->desc.alpha, S, lv.inc_off, r, w, w_is_zero ? 1 : 0,
+                                              partial_buf);
+  CAV_CHECK_LAUNCH();
+  if (lv.n_touched > 0) {
+    k_update_touched<<<div_up(lv.n_touched, TOUCH_WARPS), 32 * TOUCH_WARPS, 0, st>>>(
+        lv.N, H->desc.alpha, S, lv.n_touched, lv.touched, lv.cell_big, lv.inc_off, lv.inc_slot, delta_buf, r, w,
+        w_is_zero ? 1 : 0, partial_buf + lv.n_partial_std);
+    CAV_CHECK_LAUNCH();
+  }
+  const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
+  k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, partial_buf, w + 2 * lv.N * lv.N);
   CAV_CHECK_LAUNCH();
 }
 
 void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, cudaStream_t st) {
   const Level& lv = H->levels[l];
-  const double* r = b;
-  if (!w_is_zero) {
-    launch_apply(ops_of(lv), w, b, lv.r, 0, st);
-    r = lv.r;
-  }
-  if (lv.n_big > 0) {
-    prof_begin(H, l, st);
-    if (lv.precision == CAV_PREC_FP32) launch_patch_apply<float>(lv, lv.inv32, r, st);
-    else if (lv.precision == CAV_PREC_BF16) launch_patch_apply<__nv_bfloat16>(lv, lv.inv16, r, st);
-    else launch_patch_apply<double>(lv, lv.inv64, r, st);
-    prof_end(H, l, st);
-  }
-  StdInv S;
-  for (int q = 0; q < 25; ++q) S.m[q] = lv.std_inv[q];
-  dim3 blk(UBX, UBY), grd(div_up(lv.N, UBX), div_up(lv.N, UBY));
-  k_update<UBX, UBY><<<grd, blk, 0, st>>>(lv.N, H->desc.alpha, S, lv.cell_big, lv.inc_off, lv.inc_slot,
-                                          lv.delta, r, w, w_is_zero ? 1 : 0, lv.partial);
-  CAV_CHECK_LAUNCH();
-  const int npart = grd.x * grd.y;
-  k_remove_mean<<<div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296, 256, 0, st>>>(
-      lv.N, npart, lv.partial, w + 2 * lv.N * lv.N);
-  CAV_CHECK_LAUNCH();
+  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st);
 }
 
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st) {
@@ -294,8 +594,63 @@ static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double*
   for (int s = 0; s < nu_post; ++s) level_sweep(H, l, b, x, false, st);
 }
 
-void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st) {
-  vcycle_level(H, 0, r, z, st);
+// Capture the whole V-cycle (input levels[0].b, output levels[0].x) once as a CUDA graph.
+static bool vcycle_capture(cav_hierarchy* H) {
+  if (H->vc_exec) return true;
+  if (H->graph_failed) return false;
+  if (!H->capture_stream) CAV_CHECK_CUDA(cudaStreamCreateWithFlags(&H->capture_stream, cudaStreamNonBlocking));
+  const Level& l0 = H->levels[0];
+  cudaGraph_t g = nullptr;
+  CAV_CHECK_CUDA(cudaStreamBeginCapture(H->capture_stream, cudaStreamCaptureModeThreadLocal));
+  H->capturing = 1;
+  bool ok = true;
+  try {
+    vcycle_level(H, 0, l0.b, l0.x, H->capture_stream);
+  } catch (...) {
+    ok = false;
+  }
+  H->capturing = 0;
+  const cudaError_t e = cudaStreamEndCapture(H->capture_stream, &g);
+  if (!ok || e != cudaSuccess || !g) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    H->graph_failed = 1;
+    return false;
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&H->vc_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    cudaGetLastError();
+    H->vc_exec = nullptr;
+    H->graph_failed = 1;
+    return false;
+  }
+  return true;
+}
+
+void vcycle(const cav_hierarchy* Hc, const double* r, double* z, cudaStream_t st) {
+  cav_hierarchy* H = const_cast<cav_hierarchy*>(Hc);
+  if (!vcycle_capture(H)) {
+    vcycle_level(H, 0, r, z, st);
+    return;
+  }
+  const Level& l0 = H->levels[0];
+  const size_t bytes = sizeof(double) * 3 * (size_t)l0.N * l0.N;
+  CAV_CHECK_CUDA(cudaMemcpyAsync(l0.b, r, bytes, cudaMemcpyDeviceToDevice, st));
+  CAV_CHECK_CUDA(cudaGraphLaunch(H->vc_exec, st));
+  note_launch();
+  CAV_CHECK_CUDA(cudaMemcpyAsync(z, l0.x, bytes, cudaMemcpyDeviceToDevice, st));
+  if (H->prof_on)
+    for (size_t g = 0; g < H->vc_ev.size() / 2; ++g) H->prof_pending.push_back(-(int)g - 1);
+}
+
+void vcycle_release(cav_hierarchy* H) {
+  if (H->vc_exec) cudaGraphExecDestroy(H->vc_exec);
+  H->vc_exec = nullptr;
+  for (auto& e : H->vc_ev) cudaEventDestroy(e);
+  H->vc_ev.clear();
+  if (H->capture_stream) cudaStreamDestroy(H->capture_stream);
+  H->capture_stream = nullptr;
 }
 
 }  // namespace cav

@@ -157,6 +157,31 @@ ib_status cav_coarse_solve(const cav_hierarchy* h, const double* r, double* z, c
 ib_status vcycle_apply(const cav_hierarchy* h, const double* r, double* z, cudaStream_t stream);
 void cav_destroy(cav_hierarchy* h);
 
+/* Allocation-free sweep.  Same result as cav_sweep (the same kernels run in the same
+ * order), but its scratch -- the residual, the packed patch corrections and the partial
+ * sums of the pressure mean -- lives in a fixed 8 MiB device array inside this library
+ * (CAV_NOALLOC_SCRATCH_DOUBLES doubles) instead of buffers reserved per hierarchy.  It is for
+ * callers that cannot let a call allocate device memory: code that runs with all device
+ * memory already handed to its own pool or budget, where a cudaMalloc would fail or
+ * fragment it, and code that cannot afford the implicit device synchronisation that
+ * cudaMalloc and cudaFree may cause.  The paper has no counterpart; it is an interface
+ * variant of the sweep of Eq. additive_cav_saddle.
+ *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - Every GPU that loads the library holds the array until the process exits.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     and caches it; make that first call before any stream capture.
+ *   - A level needs 3 N_l^2 + (enlarged-patch unknowns) + (partial sums) doubles, each part
+ *     rounded up to 32; larger levels are rejected with IB_ERR_INVALID and a message
+ *     giving both sizes.
+ *   - All calls share the one array and it keeps the last call's contents (every part is
+ *     fully written before it is read, so nothing needs clearing); calls whose work overlaps
+ *     on the GPU (other streams, other host threads) race on it and must be serialised by
+ *     the caller.
+ *   - The current device must be the one the hierarchy was built on. */
+#define CAV_NOALLOC_SCRATCH_DOUBLES 1048576
+ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, const double* b, double* w,
+                            cudaStream_t stream);
+
 /* Live timing of the finest level's batched patch-apply launches (the sweep's dominant
  * kernel).  enable = 1 starts recording a CUDA event pair around each such launch, on the
  * stream it is launched on (up to 8192 launches); cav_profile_read waits for the recorded

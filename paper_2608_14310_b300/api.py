@@ -85,6 +85,7 @@ _sig = {
     "cav_patch_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _P(C.c_int32), _P(C.c_int64)]),
     "cav_ee_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _P(C.c_int64)]),
     "cav_sweep": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "cav_sweep_noalloc": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     "cav_residual": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
     "cav_restrict": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     "cav_prolong_add": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
@@ -241,6 +242,11 @@ def cav_ee_export(h: Hierarchy, level: int):
 
 def cav_sweep(h: Hierarchy, level: int, b, w, stream=None):
     _check(_lib.cav_sweep(h.handle, level, _dev(b), _dev(w), _stream(stream)), "cav_sweep")
+
+
+def cav_sweep_noalloc(h: Hierarchy, level: int, b, w, stream=None):
+    """cav_sweep with its scratch in the library's fixed device array (allocates nothing)."""
+    _check(_lib.cav_sweep_noalloc(h.handle, level, _dev(b), _dev(w), _stream(stream)), "cav_sweep_noalloc")
 
 
 def cav_residual(h: Hierarchy, level: int, b, w, r, stream=None):

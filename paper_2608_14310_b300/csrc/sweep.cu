@@ -11,6 +11,7 @@
 //      slots of the enlarged patches holding it (fixed order, no atomics)
 //   4. remove the mean pressure (Sec. 3.3).
 #include <mutex>
+#include <string>
 
 #include "internal.cuh"
 #include "device_util.cuh"
@@ -654,3 +655,74 @@ void vcycle_release(cav_hierarchy* H) {
 }
 
 }  // namespace cav
+
+// ------------------------------------------------------------------ allocation-free sweep
+//
+// cav_sweep keeps its scratch (the residual, the packed patch corrections and the partial
+// sums of the pressure mean) in buffers that cav_setup allocated.  cav_sweep_noalloc runs
+// the same kernels with that scratch taken from the fixed array below instead, so a caller
+// can run a sweep without the library reserving per-hierarchy scratch for it.  The array is
+// a file-scope device variable: every GPU that loads this library holds its 8 MiB until the
+// process exits.  Host code cannot use the array's name as a device address; the address is
+// looked up once per device with cudaGetSymbolAddress.
+
+namespace cav {
+
+static __device__ __align__(256) double g_noalloc_scratch[CAV_NOALLOC_SCRATCH_DOUBLES];
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_address[64] = {};
+
+// Device address of the scratch array on the current device (looked up on first use).
+static double* noalloc_scratch(int device) {
+  CAV_REQUIRE(device >= 0 && device < 64, "cav_sweep_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_address[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error(std::string("cav_sweep_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      throw Fail{IB_ERR_CUDA};
+    }
+    g_noalloc_address[device] = static_cast<double*>(p);
+  }
+  return g_noalloc_address[device];
+}
+
+static inline size_t round_up32(size_t n) { return (n + 31) & ~(size_t)31; }
+
+}  // namespace cav
+
+extern "C" ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, const double* b, double* w,
+                                       cudaStream_t st) {
+  using namespace cav;
+  try {
+    CAV_REQUIRE(h && b && w, "cav_sweep_noalloc: NULL argument");
+    CAV_REQUIRE(level >= 0 && level < (int32_t)h->levels.size(), "cav_sweep_noalloc: level out of range");
+    const Level& lv = h->levels[level];
+    CAV_REQUIRE(!lv.coarsest, "cav_sweep_noalloc: no smoother on the coarsest level");
+    int device = -1;
+    CAV_CHECK_CUDA(cudaGetDevice(&device));
+    CAV_REQUIRE(device == h->sys->device, "cav_sweep_noalloc: the current device is not the hierarchy's device");
+    const size_t n_r = round_up32((size_t)3 * lv.N * lv.N);
+    const size_t n_d = round_up32((size_t)lv.big_sum_n);
+    const size_t n_p = round_up32((size_t)lv.n_partial);
+    const size_t need = n_r + n_d + n_p;
+    if (need > (size_t)CAV_NOALLOC_SCRATCH_DOUBLES) {
+      set_error("cav_sweep_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
+                " doubles of scratch (3 N^2 + enlarged-patch unknowns + partial sums, each rounded to 32); "
+                "the static array holds " + std::to_string((size_t)CAV_NOALLOC_SCRATCH_DOUBLES));
+      return IB_ERR_INVALID;
+    }
+    double* base = noalloc_scratch(device);
+    double* r = base;               // written in full by the residual kernel before any read
+    double* delta = base + n_r;     // written in full by the patch-apply kernel before any read
+    double* partial = delta + n_d;  // written in full by the update kernels before any read
+    sweep_impl(h, level, b, w, false, r, delta, partial, false, st);
+    return IB_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  } catch (...) {
+    set_error("cav_sweep_noalloc: internal error");
+    return IB_ERR_INTERNAL;
+  }
+}

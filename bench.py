@@ -273,6 +273,18 @@ def main():
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
 
+    # the V-cycle alone (graph replay + its two staging copies), to split a solve's time
+    zv = torch.empty_like(b)
+    for _ in range(3):
+        api.vcycle_apply(hier, b, zv)
+    v0, v1 = ev(), ev()
+    v0.record()
+    for _ in range(20):
+        api.vcycle_apply(hier, b, zv)
+    v1.record()
+    torch.cuda.synchronize()
+    vcycle_ms = v0.elapsed_time(v1) / 20
+
     # end to end through the public call with pinned host buffers (H2D of b and x, D2H of x)
     hb = torch.from_numpy(rec.rhs()).pin_memory()
     hx = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -326,6 +338,7 @@ def main():
                    "relres_true_max": max(relres), "parallelism": f"replicas x{world}"},
         "plain_fp64": plain,
         "setup_ms": setup_ms,
+        "vcycle_ms": vcycle_ms,
         "setup_plus_solve_per_s": world / ((setup_ms + total_ms / args.steps) / 1e3),
         "roofline": {"bound": "hbm", "kernel": "k_patch_apply (finest level)", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

@@ -347,6 +347,7 @@ ib_status cav_profile(cav_hierarchy* h, int32_t enable) {
   h->prof_on = enable ? 1 : 0;
   h->prof_used = 0;
   h->prof_pending.clear();
+  h->prof_pushed = h->prof_popped = 0;
   h->prof_acc_ms = 0.0;
   h->prof_acc_n = 0;
   return IB_OK;
@@ -356,7 +357,7 @@ ib_status cav_profile(cav_hierarchy* h, int32_t enable) {
 ib_status cav_profile_read(cav_hierarchy* h, int32_t* launches, double* total_ms) {
   CAV_API_BEGIN
   CAV_REQUIRE(h && launches && total_ms, "cav_profile_read: NULL argument");
-  prof_collect(h);
+  prof_collect(h, -1);
   *launches = h->prof_acc_n;
   *total_ms = h->prof_acc_ms;
   h->prof_acc_n = 0;
@@ -369,6 +370,8 @@ void cav_destroy(cav_hierarchy* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   vcycle_release(h);
+  for (auto& e : h->fg_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& e : h->prof_ev) cudaEventDestroy(e);
   h->arena.release();
   h->ws_arena.release();

@@ -148,6 +148,10 @@ static void ensure_workspace(cav_hierarchy* H, int maxit, int64_t n) {
   H->red_partial = H->ws_arena.alloc<double>((size_t)(maxit + 2) * reduce_blocks(n));
   H->io_b = H->ws_arena.alloc<double>(n);
   H->io_x = H->ws_arena.alloc<double>(n);
+  if (!H->fg_ev[0]) {
+    CAV_CHECK_CUDA(cudaEventCreateWithFlags(&H->fg_ev[0], cudaEventDisableTiming));
+    CAV_CHECK_CUDA(cudaEventCreateWithFlags(&H->fg_ev[1], cudaEventDisableTiming));
+  }
   CAV_CHECK_CUDA(cudaMallocHost(&H->host_b, sizeof(double) * 16));
   H->ws_maxit = maxit;
 }
@@ -206,6 +210,20 @@ ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b_in,
   } else {
     k_scale<<<vb, FG_THREADS, 0, st>>>(V, n, misc + 3, V);
     CAV_CHECK_LAUNCH();
+    // The convergence test of iteration k is read on the host while iteration k + 1 is
+    // already queued: the host never waits on an idle device.  If iteration k converged,
+    // iteration k + 1's work is discarded -- it writes only Hessenberg column k + 1, Givens
+    // pair k + 1, g[k+1..k+2] and V_{k+2}, Z_{k+1}, none of which the solution uses.
+    int pending = -1;
+    long long prof_mark[2] = {0, 0};  // profiling records issued up to the end of iteration k
+    auto check = [&](int kk) -> bool {
+      CAV_CHECK_CUDA(cudaEventSynchronize(H->fg_ev[kk & 1]));
+      if (H->prof_on) prof_collect(H, prof_mark[kk & 1]);
+      k_done = kk + 1;
+      est = hbuf[8 + (kk & 1)] / ref;
+      if (history) history[kk + 1] = est;
+      return hbuf[8 + (kk & 1)] <= d->rtol * ref;
+    };
     for (int k = 0; k < maxit; ++k) {
       double* vk = V + (int64_t)k * n;
       double* zk = Z + (int64_t)k * n;
@@ -225,17 +243,18 @@ ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b_in,
       CAV_CHECK_LAUNCH();
       k_scale<<<vb, FG_THREADS, 0, st>>>(w, n, misc + 5, w);
       CAV_CHECK_LAUNCH();
-      CAV_CHECK_CUDA(cudaMemcpyAsync(hbuf + 4, misc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-      if (H->prof_on) prof_collect(H);
-      k_done = k + 1;
-      est = hbuf[4] / ref;
-      if (history) history[k + 1] = est;
-      if (hbuf[4] <= d->rtol * ref) {
+      CAV_CHECK_CUDA(cudaMemcpyAsync(hbuf + 8 + (k & 1), misc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CAV_CHECK_CUDA(cudaEventRecord(H->fg_ev[k & 1], st));
+      prof_mark[k & 1] = H->prof_pushed;
+      if (pending >= 0 && check(pending)) {
         converged = true;
+        pending = -1;
         break;
       }
+      pending = k;
     }
+    if (pending >= 0 && check(pending)) converged = true;
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
     k_trisolve<<<1, 1, 0, st>>>(S, L, k_done);
     CAV_CHECK_LAUNCH();
     k_add_multi<<<vb, FG_THREADS, 0, st>>>(Z, n, k_done, S + L.y, x);

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ib_cav.h"
@@ -162,6 +163,7 @@ struct cav_hierarchy {
   double* dev_scalars = nullptr;  // Hessenberg, Givens, g and small temporaries
   double* red_partial = nullptr;  // partial sums for multi-dot reductions
   double* host_b = nullptr;       // pinned scalars read back per iteration
+  cudaEvent_t fg_ev[2] = {nullptr, nullptr};  // per-iteration convergence records
   double* io_b = nullptr;         // device staging for host_io
   double* io_x = nullptr;
   cav::Arena ws_arena;
@@ -169,14 +171,17 @@ struct cav_hierarchy {
   int prof_on = 0;
   int prof_used = 0;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) for launches outside graphs
-  std::vector<int> prof_pending;     // pairs recorded but not yet read
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;  // recorded, not yet read, in issue order
+  long long prof_pushed = 0, prof_popped = 0;
   double prof_acc_ms = 0.0;
   int prof_acc_n = 0;
-  // V-cycle captured once as a CUDA graph (input lv0.b, output lv0.x), replayed per call
-  cudaGraphExec_t vc_exec = nullptr;
+  // The V-cycle captured as a CUDA graph (input lv0.b, output lv0.x), two instances used
+  // alternately so that a replay's event records are read before the instance replays again
+  cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
+  int vc_next = 0;
   cudaStream_t capture_stream = nullptr;
-  std::vector<cudaEvent_t> vc_ev;    // event pairs around the finest-level applies in the graph
-  int capturing = 0;
+  std::vector<cudaEvent_t> vc_ev[2];  // event pairs around the finest-level applies
+  int capturing = 0;                  // 0: not capturing, 1 + instance: capturing that instance
   int graph_failed = 0;
 };
 
@@ -213,7 +218,7 @@ void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
 void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
-void prof_collect(cav_hierarchy* H);
+void prof_collect(cav_hierarchy* H, long long upto = -1);
 void vcycle_release(cav_hierarchy* H);
 void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
 

@@ -4,15 +4,13 @@
 
 namespace cav {
 
-// One thread per cell (i, j): the three rows u_ij, v_ij, p_ij of
-//   K_E w = [ (rho/dt) u - mu L u + G p ; -D u ]          (Eq. Eul_schur, Stokes part)
-// mode 0 writes b - K w (b may be null), mode 1 writes K w.
-__global__ void k_stokes_apply(int N, double h, double rho_dt, double mu,
-                               const double* __restrict__ w, const double* __restrict__ b,
-                               double* __restrict__ out, int mode) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
+// Rows of the Stokes part of K_E w (Eq. Eul_schur) at cell (i, j):
+//   u: (rho/dt) u - mu L u + (p_ij - p_i-1j)/h,  v: likewise,  p: -(D u)_ij.
+struct StokesRows {
+  double ku, kv, kp;
+};
+__device__ inline StokesRows stokes_rows(int N, double h, double rho_dt, double mu, const double* __restrict__ w,
+                                         int i, int j) {
   const int NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
   const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
@@ -24,46 +22,70 @@ __global__ void k_stokes_apply(int N, double h, double rho_dt, double mu,
   const double uc = u[c], vc = v[c], pc = p[c];
   const double lu = (u[j * N + ip] + u[j * N + im] + u[jp * N + i] + u[jm * N + i] - 4.0 * uc) * ih2;
   const double lv = (v[j * N + ip] + v[j * N + im] + v[jp * N + i] + v[jm * N + i] - 4.0 * vc) * ih2;
-  const double ku = rho_dt * uc - mu * lu + (pc - p[j * N + im]) * ih;
-  const double kv = rho_dt * vc - mu * lv + (pc - p[jm * N + i]) * ih;
-  const double kp = -((u[j * N + ip] - uc) + (v[jp * N + i] - vc)) * ih;
-  if (mode == 0) {
-    out[c] = (b ? b[c] : 0.0) - ku;
-    out[NN + c] = (b ? b[NN + c] : 0.0) - kv;
-    out[2 * NN + c] = (b ? b[2 * NN + c] : 0.0) - kp;
-  } else {
-    out[c] = ku;
-    out[NN + c] = kv;
-    out[2 * NN + c] = kp;
-  }
+  StokesRows o;
+  o.ku = rho_dt * uc - mu * lu + (pc - p[j * N + im]) * ih;
+  o.kv = rho_dt * vc - mu * lv + (pc - p[jm * N + i]) * ih;
+  o.kp = -((u[j * N + ip] - uc) + (v[jp * N + i] - vc)) * ih;
+  return o;
 }
 
-// out[row] += scale * sum_l E_E[row, l] w[l] over the active rows; one warp per row with a
-// fixed lane-strided order and a fixed shuffle tree.
-__global__ void k_ee_spmv_add(int n_rows, const int* __restrict__ rows, const int64_t* __restrict__ rowptr,
-                              const int* __restrict__ cols, const double* __restrict__ vals,
-                              const double* __restrict__ w, double* __restrict__ out, double scale) {
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+constexpr int RES_BX = 32, RES_BY = 8, RES_WARPS = RES_BX * RES_BY / 32;
+
+// Residual (mode 0: out = b - K_E w, b may be null) or product (mode 1: out = K_E w) in one
+// launch with two block roles.  Blocks [0, nb_cells) take a 32 x 8 tile of cells, one thread
+// per cell, and write every row there except the velocity rows E_E touches; the remaining
+// blocks take those rows one warp each and write the Stokes part plus
+// -dt sum_l E_E[row, l] w[l] (fixed lane-strided order, fixed shuffle tree).
+__global__ void __launch_bounds__(RES_BX* RES_BY)
+k_residual(int N, double h, double rho_dt, double mu, double dt, const double* __restrict__ w,
+           const double* __restrict__ b, double* __restrict__ out, int mode, int nb_cells, int gx,
+           const int* __restrict__ row_of, int n_rows, const int* __restrict__ rows,
+           const int64_t* __restrict__ rowptr, const int* __restrict__ cols, const double* __restrict__ vals) {
+  const int NN = N * N;
+  if ((int)blockIdx.x < nb_cells) {
+    const int i = (blockIdx.x % gx) * RES_BX + (threadIdx.x % RES_BX);
+    const int j = (blockIdx.x / gx) * RES_BY + (threadIdx.x / RES_BX);
+    if (i >= N || j >= N) return;
+    const int c = j * N + i;
+    const StokesRows k = stokes_rows(N, h, rho_dt, mu, w, i, j);
+    const bool eu = row_of && row_of[c] >= 0, ev = row_of && row_of[NN + c] >= 0;
+    if (mode == 0) {
+      if (!eu) out[c] = (b ? b[c] : 0.0) - k.ku;
+      if (!ev) out[NN + c] = (b ? b[NN + c] : 0.0) - k.kv;
+      out[2 * NN + c] = (b ? b[2 * NN + c] : 0.0) - k.kp;
+    } else {
+      if (!eu) out[c] = k.ku;
+      if (!ev) out[NN + c] = k.kv;
+      out[2 * NN + c] = k.kp;
+    }
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = ((int)blockIdx.x - nb_cells) * RES_WARPS + warp;
   if (r >= n_rows) return;
   double s = 0.0;
   for (int64_t q = rowptr[r] + lane; q < rowptr[r + 1]; q += 32) s += vals[q] * w[cols[q]];
   s = warp_sum(s);
-  if (lane == 0) out[rows[r]] += scale * s;
+  if (lane == 0) {
+    const int row = rows[r];
+    const int comp = row / NN, c = row % NN;
+    const StokesRows k = stokes_rows(N, h, rho_dt, mu, w, c % N, c / N);
+    const double kr = ((comp == 0) ? k.ku : k.kv) - dt * s;
+    out[row] = (mode == 0) ? ((b ? b[row] : 0.0) - kr) : kr;
+  }
 }
 
 void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
                   cudaStream_t st) {
-  dim3 blk(32, 8), grd(div_up(op.N, 32), div_up(op.N, 8));
-  k_stokes_apply<<<grd, blk, 0, st>>>(op.N, op.h, op.rho_dt, op.mu, w, b, out, mode);
+  const int gx = div_up(op.N, RES_BX), gy = div_up(op.N, RES_BY);
+  const int nb_cells = gx * gy;
+  const bool has_ee = op.ee && op.ee->n_rows > 0;
+  const int nb_rows = has_ee ? div_up(op.ee->n_rows, RES_WARPS) : 0;
+  k_residual<<<nb_cells + nb_rows, RES_BX * RES_BY, 0, st>>>(
+      op.N, op.h, op.rho_dt, op.mu, op.dt, w, b, out, mode, nb_cells, gx, has_ee ? op.ee->row_of : nullptr,
+      has_ee ? op.ee->n_rows : 0, has_ee ? op.ee->rows : nullptr, has_ee ? op.ee->rowptr : nullptr,
+      has_ee ? op.ee->cols : nullptr, has_ee ? op.ee->vals : nullptr);
   CAV_CHECK_LAUNCH();
-  if (op.ee && op.ee->n_rows > 0) {
-    // K_E has A0 - dt E_E: residual mode adds +dt E_E w, apply mode adds -dt E_E w
-    const double scale = (mode == 0) ? op.dt : -op.dt;
-    k_ee_spmv_add<<<div_up(op.ee->n_rows, 8), 256, 0, st>>>(op.ee->n_rows, op.ee->rows, op.ee->rowptr,
-                                                           op.ee->cols, op.ee->vals, w, out, scale);
-    CAV_CHECK_LAUNCH();
-  }
 }
 
 // Restriction (Sec. 4), one thread per coarse cell (I, J):

@@ -175,8 +175,10 @@ __device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %
 constexpr int TMA_STAGES = 4;
 constexpr int TMA_CHUNK = 16384;        // bytes per stage (a whole number of columns)
 constexpr int TMA_CONSUMER_WARPS = 4;
-constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 1);
+constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 2);  // producer, gatherer, consumers
 constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
+constexpr int TMA_CTAS_PER_SM = 3;
+constexpr int Y_SLOTS = 2;
 
 template <typename T>
 __host__ __device__ constexpr int tma_max_rows() {
@@ -184,14 +186,18 @@ __host__ __device__ constexpr int tma_max_rows() {
 }
 
 // Persistent batched patch apply.  CTA c takes patches c, c + G, c + 2G, ... of the
-// size-descending order.  Warp 0 (one lane) is the producer: it streams each patch's
-// column-major inverse, a contiguous block of n * ld elements, into a ring of TMA_STAGES
-// shared-memory stages of at most TMA_CHUNK bytes (whole columns) with cp.async.bulk, each
-// stage guarded by a "full" mbarrier (transaction bytes) and an "empty" mbarrier (one
-// arrival per consumer warp).  Warps 1..4 are consumers: per patch they gather
-// y = s_r * r|_p into shared memory, then accumulate acc[rows] += X[rows, b] y[b] from each
-// stage as it lands, release the stage, and finally write delta = s_c * acc.  Every wait
-// is bounded; a timed-out wait records DEV_TIMEOUT and the CTA stops.
+// size-descending order, with three roles:
+//  * warp 0, one lane (producer): streams each patch's column-major inverse -- a contiguous
+//    block of n * ld elements -- into a ring of TMA_STAGES shared-memory stages of at most
+//    TMA_CHUNK bytes (whole columns) with cp.async.bulk; "full" mbarriers carry the
+//    transaction bytes, "empty" mbarriers take one arrival per consumer warp;
+//  * warp 1 (gatherer): writes y = s_r * r|_p of the coming patches into a double-buffered
+//    shared ring ("yfull": 32 lane arrivals, "yempty": one arrival per consumer warp), so the
+//    dependent index -> residual loads of patch t+1 overlap the streaming of patch t;
+//  * warps 2..5 (consumers): acc[rows] += X[rows, b] y[b] stage by stage, each thread
+//    owning V consecutive rows (up to TMA_MAXPASS row blocks), then delta = s_c * acc.
+// Every wait is bounded; a timed-out wait records DEV_TIMEOUT and that warp stops waiting
+// and computing but still walks the patch sequence.
 template <typename T>
 __global__ void __launch_bounds__(TMA_THREADS)
 k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __restrict__ off,
@@ -204,15 +210,21 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   constexpr int CT = 32 * TMA_CONSUMER_WARPS;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stage_buf = smem;
-  acc_t* y = reinterpret_cast<acc_t*>(smem + TMA_STAGES * TMA_CHUNK);
   const size_t ybytes = ((size_t)max_n * sizeof(acc_t) + 127) & ~(size_t)127;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TMA_STAGES * TMA_CHUNK + ybytes);
+  acc_t* ybuf = reinterpret_cast<acc_t*>(smem + TMA_STAGES * TMA_CHUNK);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TMA_STAGES * TMA_CHUNK + Y_SLOTS * ybytes);
   uint64_t* empty = full + TMA_STAGES;
+  uint64_t* yfull = empty + TMA_STAGES;
+  uint64_t* yempty = yfull + Y_SLOTS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TMA_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], TMA_CONSUMER_WARPS);
+    }
+    for (int s = 0; s < Y_SLOTS; ++s) {
+      mbar_init(&yfull[s], 32);
+      mbar_init(&yempty[s], TMA_CONSUMER_WARPS);
     }
     mbar_fence_init();
   }
@@ -244,21 +256,38 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     return;
   }
 
-  const int ct = threadIdx.x - 32;
+  if (warp == 1) {
+    bool alive = true;
+    int t = 0;
+    for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
+      const int slot = t & 1;
+      const uint32_t par = (uint32_t)((t >> 1) & 1);
+      if (alive && !mbar_wait(&yempty[slot], par ^ 1u, status)) alive = false;
+      const int p = order[q];
+      const int64_t d0 = off[p];
+      const int n = (int)(off[p + 1] - d0);
+      acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
+      if (alive)
+        for (int b = lane; b < n; b += 32) y[b] = (acc_t)(s_r[d0 + b] * r[dofs[d0 + b]]);
+      mbar_arrive(&yfull[slot]);
+    }
+    return;
+  }
+
+  const int ct = threadIdx.x - 64;
   int stage = 0;
   uint32_t phase = 0;
-  // After a timed-out wait a consumer stops computing and waiting but keeps walking the
-  // same patch sequence, so every consumer still reaches every named barrier.
   bool alive = true;
-  for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
+  int t = 0;
+  for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
     const int p = order[q];
     const int64_t d0 = off[p];
     const int n = (int)(off[p + 1] - d0);
     const int ld = (n + 7) & ~7;
     const int cpc = TMA_CHUNK / (int)(ld * sizeof(T));
-    consumer_sync(CT);  // every consumer is done with the previous patch's y
-    for (int b = ct; b < n; b += CT) y[b] = (acc_t)(s_r[d0 + b] * r[dofs[d0 + b]]);
-    consumer_sync(CT);
+    const int slot = t & 1;
+    if (alive && !mbar_wait(&yfull[slot], (uint32_t)((t >> 1) & 1), status)) alive = false;
+    const acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
     acc_t acc[TMA_MAXPASS][V];
 #pragma unroll
     for (int ps = 0; ps < TMA_MAXPASS; ++ps)
@@ -297,6 +326,8 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
         phase ^= 1u;
       }
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&yempty[slot]);
 #pragma unroll
     for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
       const int a0 = (ps * CT + ct) * V;
@@ -323,93 +354,82 @@ __device__ inline double std_row(const StdInv& S, int row, const double* __restr
   return m[0] * y0 + m[1] * y1 + m[2] * y2 + m[3] * y3 + m[4] * y4;
 }
 
-// Unknowns that no enlarged patch holds: both incident cells (one for a pressure) keep
-// their standard patch, so count_k is 2 (1) and the correction is the stencil of the
-// shared 5x5 inverse.  One thread per cell; unknowns held by enlarged patches are left to
-// k_update_touched.  Block partial sums of the new pressures feed the mean.
-template <int BX, int BY>
-__global__ void __launch_bounds__(BX* BY)
-k_update_std(int N, double alpha, StdInv S, const int64_t* __restrict__ inc_off, const double* __restrict__ r,
-             double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
-  __shared__ double sm[BX * BY / 32];
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int NN = N * N;
-  double pnew = 0.0;
-  if (i < N && j < N) {
-    const int c = j * N + i;
-    const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
-    if (inc_off[c + 1] == inc_off[c]) {
-      const double s = std_row(S, 1, r, N, im, j) + std_row(S, 0, r, N, i, j);
-      w[c] = (w_is_zero ? 0.0 : w[c]) + alpha * (s / 2.0);
-    }
-    if (inc_off[NN + c + 1] == inc_off[NN + c]) {
-      const double s = std_row(S, 3, r, N, i, jm) + std_row(S, 2, r, N, i, j);
-      w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * (s / 2.0);
-    }
-    if (inc_off[2 * NN + c + 1] == inc_off[2 * NN + c]) {
-      const double s = std_row(S, 4, r, N, i, j);
-      pnew = (w_is_zero ? 0.0 : w[2 * NN + c]) + alpha * s;
-      w[2 * NN + c] = pnew;
-    }
-  }
-  const int tid = threadIdx.y * BX + threadIdx.x;
-  const double v = warp_sum(pnew);
-  if ((tid & 31) == 0) sm[tid >> 5] = v;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < BX * BY / 32; ++q) t += sm[q];
-    partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
-  }
-}
-
 constexpr int TOUCH_WARPS = 8;
 
-// One warp per unknown held by at least one enlarged patch: the lanes sum the enlarged
-// patches' corrections at the unknown (fixed lane-strided order, fixed shuffle tree), lane 0
-// adds the standard patches of its incident cells that kept their Vanka patch and divides
-// by the total patch count.
-__global__ void __launch_bounds__(32 * TOUCH_WARPS)
-k_update_touched(int N, double alpha, StdInv S, int n_touched, const int* __restrict__ touched,
-                 const uint8_t* __restrict__ cell_big, const int64_t* __restrict__ inc_off,
-                 const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
-                 double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
-  __shared__ double sm[TOUCH_WARPS];
+// Scatter / update in one launch with two block roles.
+//  * Blocks [0, nb_std): a 32 x 8 tile of cells, one thread per cell.  For each unknown of the
+//    cell that no enlarged patch holds, both incident cells (one for a pressure) keep their
+//    standard patch, so count_k is 2 (1) and the correction is the stencil of the shared 5x5
+//    inverse applied to r.
+//  * The remaining blocks: one warp per unknown held by at least one enlarged patch.  The lanes
+//    sum the enlarged patches' corrections at the unknown (fixed lane-strided order, fixed
+//    shuffle tree); lane 0 adds the standard patches of its incident cells that kept their
+//    Vanka patch and divides by the total patch count.
+// Each block writes the partial sum of the new pressures it produced (fixed order); the
+// stencil blocks' partials come first, then the touched blocks'.
+__global__ void __launch_bounds__(256)
+k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __restrict__ inc_off,
+         int n_touched, const int* __restrict__ touched, const uint8_t* __restrict__ cell_big,
+         const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
+         double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
+  __shared__ double sm[8];
+  const int NN = N * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * TOUCH_WARPS + warp;
   double pnew = 0.0;
-  if (t < n_touched) {
-    const int k = touched[t];
-    const int64_t q0 = inc_off[k], q1 = inc_off[k + 1];
-    double s = 0.0;
-    for (int64_t q = q0 + lane; q < q1; q += 32) s += delta[inc_slot[q]];
-    s = warp_sum(s);
-    if (lane == 0) {
-      const int NN = N * N;
-      const int comp = k / NN, c = k % NN, i = c % N, j = c / N;
+  if ((int)blockIdx.x < nb_std) {
+    const int i = (blockIdx.x % gx) * 32 + lane;
+    const int j = (blockIdx.x / gx) * 8 + warp;
+    if (i < N && j < N) {
+      const int c = j * N + i;
       const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
-      int cnt = (int)(q1 - q0);
-      double st = 0.0;
-      if (comp == 0) {
-        if (!cell_big[j * N + im]) { st += std_row(S, 1, r, N, im, j); ++cnt; }
-        if (!cell_big[c]) { st += std_row(S, 0, r, N, i, j); ++cnt; }
-      } else if (comp == 1) {
-        if (!cell_big[jm * N + i]) { st += std_row(S, 3, r, N, i, jm); ++cnt; }
-        if (!cell_big[c]) { st += std_row(S, 2, r, N, i, j); ++cnt; }
-      } else {
-        if (!cell_big[c]) { st += std_row(S, 4, r, N, i, j); ++cnt; }
+      if (inc_off[c + 1] == inc_off[c]) {
+        const double s = std_row(S, 1, r, N, im, j) + std_row(S, 0, r, N, i, j);
+        w[c] = (w_is_zero ? 0.0 : w[c]) + alpha * (s / 2.0);
       }
-      const double nw = (w_is_zero ? 0.0 : w[k]) + alpha * ((st + s) / (double)cnt);
-      w[k] = nw;
-      if (comp == 2) pnew = nw;
+      if (inc_off[NN + c + 1] == inc_off[NN + c]) {
+        const double s = std_row(S, 3, r, N, i, jm) + std_row(S, 2, r, N, i, j);
+        w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * (s / 2.0);
+      }
+      if (inc_off[2 * NN + c + 1] == inc_off[2 * NN + c]) {
+        const double s = std_row(S, 4, r, N, i, j);
+        pnew = (w_is_zero ? 0.0 : w[2 * NN + c]) + alpha * s;
+        w[2 * NN + c] = pnew;
+      }
+    }
+    pnew = warp_sum(pnew);
+  } else {
+    const int t = ((int)blockIdx.x - nb_std) * TOUCH_WARPS + warp;
+    if (t < n_touched) {
+      const int k = touched[t];
+      const int64_t q0 = inc_off[k], q1 = inc_off[k + 1];
+      double s = 0.0;
+      for (int64_t q = q0 + lane; q < q1; q += 32) s += delta[inc_slot[q]];
+      s = warp_sum(s);
+      if (lane == 0) {
+        const int comp = k / NN, c = k % NN, i = c % N, j = c / N;
+        const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
+        int cnt = (int)(q1 - q0);
+        double st = 0.0;
+        if (comp == 0) {
+          if (!cell_big[j * N + im]) { st += std_row(S, 1, r, N, im, j); ++cnt; }
+          if (!cell_big[c]) { st += std_row(S, 0, r, N, i, j); ++cnt; }
+        } else if (comp == 1) {
+          if (!cell_big[jm * N + i]) { st += std_row(S, 3, r, N, i, jm); ++cnt; }
+          if (!cell_big[c]) { st += std_row(S, 2, r, N, i, j); ++cnt; }
+        } else {
+          if (!cell_big[c]) { st += std_row(S, 4, r, N, i, j); ++cnt; }
+        }
+        const double nw = (w_is_zero ? 0.0 : w[k]) + alpha * ((st + s) / (double)cnt);
+        w[k] = nw;
+        if (comp == 2) pnew = nw;
+      }
     }
   }
   if (lane == 0) sm[warp] = pnew;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int q = 0; q < TOUCH_WARPS; ++q) tot += sm[q];
+    for (int q = 0; q < 8; ++q) tot += sm[q];
     partial[blockIdx.x] = tot;
   }
 }
@@ -439,8 +459,6 @@ __global__ void k_coarse_apply(int n, const double* __restrict__ inv, const doub
 
 // ------------------------------------------------------------------ host drivers
 
-static constexpr int UBX = 32, UBY = 8;
-
 static LevelOps ops_of(const Level& lv) {
   LevelOps o;
   o.N = lv.N;
@@ -456,12 +474,13 @@ void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st) {
   cav_hierarchy* h = const_cast<cav_hierarchy*>(H);
   if (level != 0) return;
   if (h->capturing) {
-    const size_t q = h->vc_ev.size();
-    h->vc_ev.resize(q + 2);
-    CAV_CHECK_CUDA(cudaEventCreate(&h->vc_ev[q]));
-    CAV_CHECK_CUDA(cudaEventCreate(&h->vc_ev[q + 1]));
+    std::vector<cudaEvent_t>& ev = h->vc_ev[h->capturing - 1];
+    const size_t q = ev.size();
+    ev.resize(q + 2);
+    CAV_CHECK_CUDA(cudaEventCreate(&ev[q]));
+    CAV_CHECK_CUDA(cudaEventCreate(&ev[q + 1]));
     // External: becomes an event-record node of the graph, recorded on every replay
-    CAV_CHECK_CUDA(cudaEventRecordWithFlags(h->vc_ev[q], st, cudaEventRecordExternal));
+    CAV_CHECK_CUDA(cudaEventRecordWithFlags(ev[q], st, cudaEventRecordExternal));
     return;
   }
   if (!h->prof_on || (size_t)(2 * h->prof_used + 1) >= h->prof_ev.size()) return;
@@ -471,32 +490,32 @@ void prof_end(const cav_hierarchy* H, int level, cudaStream_t st) {
   cav_hierarchy* h = const_cast<cav_hierarchy*>(H);
   if (level != 0) return;
   if (h->capturing) {
-    CAV_CHECK_CUDA(cudaEventRecordWithFlags(h->vc_ev.back(), st, cudaEventRecordExternal));
+    CAV_CHECK_CUDA(cudaEventRecordWithFlags(h->vc_ev[h->capturing - 1].back(), st, cudaEventRecordExternal));
     return;
   }
   if (!h->prof_on || (size_t)(2 * h->prof_used + 1) >= h->prof_ev.size()) return;
   CAV_CHECK_CUDA(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], st));
-  h->prof_pending.push_back(h->prof_used);
+  h->prof_pending.emplace_back(h->prof_ev[2 * h->prof_used], h->prof_ev[2 * h->prof_used + 1]);
+  ++h->prof_pushed;
   ++h->prof_used;
 }
 
-// Read every recorded-but-unread pair (after the stream has been synchronised).
-void prof_collect(cav_hierarchy* H) {
-  for (int q : H->prof_pending) {
+// Read the recorded pairs in issue order, up to push count `upto` (all when negative);
+// waits for each pair's stop event.
+void prof_collect(cav_hierarchy* H, long long upto) {
+  if (upto < 0) upto = H->prof_pushed;
+  size_t q = 0;
+  while (H->prof_popped < upto && q < H->prof_pending.size()) {
     float ms = 0.f;
-    if (q >= 0) {
-      CAV_CHECK_CUDA(cudaEventSynchronize(H->prof_ev[2 * q + 1]));
-      CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, H->prof_ev[2 * q], H->prof_ev[2 * q + 1]));
-    } else {
-      const int g = -q - 1;
-      CAV_CHECK_CUDA(cudaEventSynchronize(H->vc_ev[2 * g + 1]));
-      CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, H->vc_ev[2 * g], H->vc_ev[2 * g + 1]));
-    }
+    CAV_CHECK_CUDA(cudaEventSynchronize(H->prof_pending[q].second));
+    CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, H->prof_pending[q].first, H->prof_pending[q].second));
     H->prof_acc_ms += ms;
     H->prof_acc_n += 1;
+    ++q;
+    ++H->prof_popped;
   }
-  H->prof_pending.clear();
-  H->prof_used = 0;
+  H->prof_pending.erase(H->prof_pending.begin(), H->prof_pending.begin() + q);
+  if (H->prof_pending.empty()) H->prof_used = 0;
 }
 
 static int sm_count() {
@@ -515,12 +534,13 @@ static void launch_patch_apply(const cav_hierarchy* H, const Level& lv, const T*
   typedef typename VecLoad<T>::acc_t acc_t;
   if (lv.big_max_n <= tma_max_rows<T>() && (size_t)round8(lv.big_max_n) * sizeof(T) <= (size_t)TMA_CHUNK) {
     const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
-    const size_t smem = (size_t)TMA_STAGES * TMA_CHUNK + ybytes + 2 * TMA_STAGES * sizeof(uint64_t);
+    const size_t smem = (size_t)TMA_STAGES * TMA_CHUNK + Y_SLOTS * ybytes +
+                        (2 * TMA_STAGES + 2 * Y_SLOTS) * sizeof(uint64_t);
     static std::once_flag once;
     std::call_once(once, [] {
       cudaFuncSetAttribute(k_patch_apply_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
-    const int grid = std::min(lv.n_big, 2 * sm_count());
+    const int grid = std::min(lv.n_big, TMA_CTAS_PER_SM * sm_count());
     k_patch_apply_tma<T><<<grid, TMA_THREADS, smem, st>>>(lv.n_big, lv.order, lv.big_off, lv.big_dofs, lv.inv_off,
                                                           inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
   } else {
@@ -534,7 +554,8 @@ static void launch_patch_apply(const cav_hierarchy* H, const Level& lv, const T*
 // The four steps of one sweep with explicit scratch (residual r_buf, packed corrections
 // delta_buf, partial sums partial_buf); shared by cav_sweep and cav_sweep_noalloc.
 static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, double* r_buf,
-                       double* delta_buf, double* partial_buf, bool profile, cudaStream_t st) {
+                       double* delta_buf, double* partial_buf, bool profile, cudaStream_t st,
+                       bool remove_mean = true) {
   const Level& lv = H->levels[l];
   const double* r = b;
   if (!w_is_zero) {
@@ -550,24 +571,34 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   }
   StdInv S;
   for (int q = 0; q < 25; ++q) S.m[q] = lv.std_inv[q];
-  dim3 blk(UBX, UBY), grd(div_up(lv.N, UBX), div_up(lv.N, UBY));
-  k_update_std<UBX, UBY><<<grd, blk, 0, st>>>(lv.N, H->desc.alpha, S, lv.inc_off, r, w, w_is_zero ? 1 : 0,
-                                              partial_buf);
+  const int gx = div_up(lv.N, 32), gy = div_up(lv.N, 8);
+  const int nb_std = gx * gy;
+  const int nb_touch = div_up(lv.n_touched, TOUCH_WARPS);
+  k_update<<<nb_std + nb_touch, 256, 0, st>>>(lv.N, H->desc.alpha, S, nb_std, gx, lv.inc_off, lv.n_touched,
+                                              lv.touched, lv.cell_big, lv.inc_slot, delta_buf, r, w,
+                                              w_is_zero ? 1 : 0, partial_buf);
   CAV_CHECK_LAUNCH();
-  if (lv.n_touched > 0) {
-    k_update_touched<<<div_up(lv.n_touched, TOUCH_WARPS), 32 * TOUCH_WARPS, 0, st>>>(
-        lv.N, H->desc.alpha, S, lv.n_touched, lv.touched, lv.cell_big, lv.inc_off, lv.inc_slot, delta_buf, r, w,
-        w_is_zero ? 1 : 0, partial_buf + lv.n_partial_std);
+  if (remove_mean) {
+    const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
+    k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, partial_buf, w + 2 * lv.N * lv.N);
     CAV_CHECK_LAUNCH();
   }
-  const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
-  k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, partial_buf, w + 2 * lv.N * lv.N);
-  CAV_CHECK_LAUNCH();
 }
 
 void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, cudaStream_t st) {
   const Level& lv = H->levels[l];
   sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st);
+}
+
+// Inside the V-cycle a constant pressure never changes a residual (G 1 = 0) or a patch
+// correction (which depends on the residual only), and prolongation maps constants to
+// constants, so removing the mean after every sweep (Sec. 3.3) and removing it once from the
+// V-cycle's output give the same iterate up to rounding.  The cycle removes it once, using
+// the partial sums the finest level's last sweep already produced.
+static void cycle_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
+                        cudaStream_t st) {
+  const Level& lv = H->levels[l];
+  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st, false);
 }
 
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st) {
@@ -586,24 +617,33 @@ static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double*
   const int NN = lv.N * lv.N;
   const int nu_pre = H->desc.nu_pre, nu_post = H->desc.nu_post;
   if (nu_pre == 0) CAV_CHECK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * 3 * NN, st));
-  for (int s = 0; s < nu_pre; ++s) level_sweep(H, l, b, x, s == 0, st);
+  for (int s = 0; s < nu_pre; ++s) cycle_sweep(H, l, b, x, s == 0, st);
   launch_apply(ops_of(lv), x, b, lv.r, 0, st);
   const Level& lc = H->levels[l + 1];
   launch_restrict(lc.N, lv.r, lc.b, st);
   vcycle_level(H, l + 1, lc.b, lc.x, st);
   launch_prolong_add(lc.N, lc.x, x, st);
-  for (int s = 0; s < nu_post; ++s) level_sweep(H, l, b, x, false, st);
+  for (int s = 0; s < nu_post; ++s) cycle_sweep(H, l, b, x, false, st);
+  if (l == 0) {
+    if (nu_post > 0) {
+      const int nblk = div_up(NN, 256) < 296 ? div_up(NN, 256) : 296;
+      k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, lv.partial, x + 2 * NN);
+      CAV_CHECK_LAUNCH();
+    } else {
+      level_sweep(H, l, b, x, false, st);  // nu_post = 0: one more full sweep to fix the gauge
+    }
+  }
 }
 
-// Capture the whole V-cycle (input levels[0].b, output levels[0].x) once as a CUDA graph.
-static bool vcycle_capture(cav_hierarchy* H) {
-  if (H->vc_exec) return true;
+// Capture the whole V-cycle (input levels[0].b, output levels[0].x) as CUDA graph instance g.
+static bool vcycle_capture(cav_hierarchy* H, int g) {
+  if (H->vc_exec[g]) return true;
   if (H->graph_failed) return false;
   if (!H->capture_stream) CAV_CHECK_CUDA(cudaStreamCreateWithFlags(&H->capture_stream, cudaStreamNonBlocking));
   const Level& l0 = H->levels[0];
-  cudaGraph_t g = nullptr;
+  cudaGraph_t graph = nullptr;
   CAV_CHECK_CUDA(cudaStreamBeginCapture(H->capture_stream, cudaStreamCaptureModeThreadLocal));
-  H->capturing = 1;
+  H->capturing = 1 + g;
   bool ok = true;
   try {
     vcycle_level(H, 0, l0.b, l0.x, H->capture_stream);
@@ -611,18 +651,18 @@ static bool vcycle_capture(cav_hierarchy* H) {
     ok = false;
   }
   H->capturing = 0;
-  const cudaError_t e = cudaStreamEndCapture(H->capture_stream, &g);
-  if (!ok || e != cudaSuccess || !g) {
+  const cudaError_t e = cudaStreamEndCapture(H->capture_stream, &graph);
+  if (!ok || e != cudaSuccess || !graph) {
     cudaGetLastError();
-    if (g) cudaGraphDestroy(g);
+    if (graph) cudaGraphDestroy(graph);
     H->graph_failed = 1;
     return false;
   }
-  const cudaError_t e2 = cudaGraphInstantiate(&H->vc_exec, g, 0);
-  cudaGraphDestroy(g);
+  const cudaError_t e2 = cudaGraphInstantiate(&H->vc_exec[g], graph, 0);
+  cudaGraphDestroy(graph);
   if (e2 != cudaSuccess) {
     cudaGetLastError();
-    H->vc_exec = nullptr;
+    H->vc_exec[g] = nullptr;
     H->graph_failed = 1;
     return false;
   }
@@ -631,25 +671,34 @@ static bool vcycle_capture(cav_hierarchy* H) {
 
 void vcycle(const cav_hierarchy* Hc, const double* r, double* z, cudaStream_t st) {
   cav_hierarchy* H = const_cast<cav_hierarchy*>(Hc);
-  if (!vcycle_capture(H)) {
+  const int g = H->vc_next;
+  if (!vcycle_capture(H, g)) {
     vcycle_level(H, 0, r, z, st);
     return;
   }
+  H->vc_next ^= 1;
   const Level& l0 = H->levels[0];
   const size_t bytes = sizeof(double) * 3 * (size_t)l0.N * l0.N;
   CAV_CHECK_CUDA(cudaMemcpyAsync(l0.b, r, bytes, cudaMemcpyDeviceToDevice, st));
-  CAV_CHECK_CUDA(cudaGraphLaunch(H->vc_exec, st));
+  CAV_CHECK_CUDA(cudaGraphLaunch(H->vc_exec[g], st));
   note_launch();
   CAV_CHECK_CUDA(cudaMemcpyAsync(z, l0.x, bytes, cudaMemcpyDeviceToDevice, st));
-  if (H->prof_on)
-    for (size_t g = 0; g < H->vc_ev.size() / 2; ++g) H->prof_pending.push_back(-(int)g - 1);
+  if (H->prof_on) {
+    const std::vector<cudaEvent_t>& ev = H->vc_ev[g];
+    for (size_t q = 0; q + 1 < ev.size(); q += 2) {
+      H->prof_pending.emplace_back(ev[q], ev[q + 1]);
+      ++H->prof_pushed;
+    }
+  }
 }
 
 void vcycle_release(cav_hierarchy* H) {
-  if (H->vc_exec) cudaGraphExecDestroy(H->vc_exec);
-  H->vc_exec = nullptr;
-  for (auto& e : H->vc_ev) cudaEventDestroy(e);
-  H->vc_ev.clear();
+  for (int g = 0; g < 2; ++g) {
+    if (H->vc_exec[g]) cudaGraphExecDestroy(H->vc_exec[g]);
+    H->vc_exec[g] = nullptr;
+    for (auto& e : H->vc_ev[g]) cudaEventDestroy(e);
+    H->vc_ev[g].clear();
+  }
   if (H->capture_stream) cudaStreamDestroy(H->capture_stream);
   H->capture_stream = nullptr;
 }

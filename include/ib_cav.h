@@ -100,6 +100,8 @@ typedef struct {
   int32_t nu_pre, nu_post;  /* sweeps per level in the V-cycle                             */
   double alpha;        /* relaxation factor of Eq. additive_cav_saddle                     */
   int32_t precision;   /* cav_precision of the stored enlarged-patch inverses              */
+  int32_t autotune;    /* 1: time the patch-apply kernel variants on each level's patches at
+                          set-up and keep the fastest (all variants give identical bits)   */
 } cav_desc;
 
 typedef struct cav_hierarchy cav_hierarchy;
@@ -117,6 +119,8 @@ typedef struct {
   int32_t ee_rows;       /* velocity rows of E_E with at least one nonzero                  */
   int32_t ee_window;     /* max per-axis index offset between a row and a column of E_E     */
   int32_t is_coarsest;
+  int32_t apply_variant;     /* patch-apply kernel variant in use (0 unless autotuned)        */
+  float apply_us[5];         /* autotuner's time per launch of each variant (0: not timed)    */
 } cav_level_info;
 
 /* Builds the level hierarchy, Galerkin E_E^(l-1) = R E_E^(l) P, the patch sets and their
@@ -214,6 +218,19 @@ typedef struct {
 ib_status fgmres_solve(const ib_system* sys, const cav_hierarchy* h, const double* b, double* x,
                        const fgmres_desc* desc, fgmres_info* info, double* history,
                        cudaStream_t stream);
+
+/* Many independent systems solved together (batched, uneven sizes): the same FGMRES as
+ * fgmres_solve for each (systems[i], hierarchies[i], b[i], x[i]), advanced in lockstep with
+ * every system on its own library-owned stream so that their V-cycle graphs and Krylov
+ * kernels overlap on the device.  Each system stops at its own convergence; infos[i] is
+ * filled for every i.  Results are bitwise those of fgmres_solve.  Device buffers only
+ * (host_io must be 0); a hierarchy may appear once per call.  Waits on `stream` before
+ * starting and synchronises everything before returning.  IB_ERR_NOCONV if any system
+ * stopped at maxit. */
+ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
+                               const cav_hierarchy* const* hierarchies, const double* const* b,
+                               double* const* x, const fgmres_desc* desc, fgmres_info* infos,
+                               cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,8 @@ class ib_structure_desc(C.Structure):
 
 class cav_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("coarsest_N", C.c_int32), ("nu_pre", C.c_int32),
-                ("nu_post", C.c_int32), ("alpha", C.c_double), ("precision", C.c_int32)]
+                ("nu_post", C.c_int32), ("alpha", C.c_double), ("precision", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class cav_level_info(C.Structure):
@@ -54,7 +55,8 @@ class cav_level_info(C.Structure):
                 ("max_n", C.c_int32), ("sum_n", C.c_int64), ("sum_n2", C.c_int64),
                 ("enlarged_sum_n", C.c_int64), ("enlarged_sum_n2", C.c_int64),
                 ("inverse_bytes", C.c_int64), ("ee_nnz", C.c_int64), ("ee_rows", C.c_int32),
-                ("ee_window", C.c_int32), ("is_coarsest", C.c_int32)]
+                ("ee_window", C.c_int32), ("is_coarsest", C.c_int32), ("apply_variant", C.c_int32),
+                ("apply_us", C.c_float * 5)]
 
 
 class fgmres_desc(C.Structure):
@@ -93,6 +95,8 @@ _sig = {
     "vcycle_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "cav_destroy": (None, [_vp]),
     "fgmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, _P(fgmres_desc), _P(fgmres_info), _vp, _vp]),
+    "fgmres_solve_batched": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(_vp), _P(_vp), _P(fgmres_desc),
+                                       _P(fgmres_info), _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -196,12 +200,13 @@ def ib_residual(sys: System, b, x, r, stream=None):
 
 
 def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=1.0,
-              precision="fp64", stream=None) -> Hierarchy:
-    d = cav_desc(KIND[kind], int(coarsest_N), int(nu_pre), int(nu_post), float(alpha), PRECISION[precision])
+              precision="fp64", autotune=False, stream=None) -> Hierarchy:
+    d = cav_desc(KIND[kind], int(coarsest_N), int(nu_pre), int(nu_post), float(alpha), PRECISION[precision],
+                 1 if autotune else 0)
     out = _vp()
     _check(_lib.cav_setup(sys.handle, C.byref(d), _stream(stream), C.byref(out)), "cav_setup")
     return Hierarchy(out, sys, dict(kind=kind, coarsest_N=coarsest_N, nu_pre=nu_pre, nu_post=nu_post,
-                                    alpha=alpha, precision=precision))
+                                    alpha=alpha, precision=precision, autotune=autotune))
 
 
 def cav_num_levels(h: Hierarchy) -> int:
@@ -213,7 +218,9 @@ def cav_num_levels(h: Hierarchy) -> int:
 def cav_get_level_info(h: Hierarchy, level: int) -> dict:
     info = cav_level_info()
     _check(_lib.cav_get_level_info(h.handle, level, C.byref(info)), "cav_get_level_info")
-    return {f: getattr(info, f) for f, _ in info._fields_}
+    out = {f: getattr(info, f) for f, _ in info._fields_}
+    out["apply_us"] = list(info.apply_us)
+    return out
 
 
 def cav_patch_export(h: Hierarchy, level: int):
@@ -308,3 +315,21 @@ def fgmres_solve(sys: System, h: Hierarchy, b, x, rtol=1e-10, maxit=60, rel_to=0
     if hist is not None:
         out["history"] = hist[:info.iters + 1].copy()
     return out
+
+
+def fgmres_solve_batched(systems, hierarchies, bs, xs, rtol=1e-10, maxit=60, rel_to=0, stream=None,
+                         raise_on_noconv=False) -> list:
+    """Solve many independent systems together; bs, xs are lists of CUDA tensors."""
+    n = len(systems)
+    assert n == len(hierarchies) == len(bs) == len(xs) and n >= 1
+    arr = _vp * n
+    sysa = arr(*[s.handle for s in systems])
+    hiera = arr(*[h.handle for h in hierarchies])
+    ba = arr(*[_dev(b) for b in bs])
+    xa = arr(*[_dev(x) for x in xs])
+    infos = (fgmres_info * n)()
+    d = fgmres_desc(float(rtol), int(maxit), int(rel_to), 0)
+    st = _lib.fgmres_solve_batched(n, sysa, hiera, ba, xa, C.byref(d), infos, _stream(stream))
+    if st not in (IB_OK, IB_ERR_NOCONV) or (st == IB_ERR_NOCONV and raise_on_noconv):
+        raise IBError(st, "fgmres_solve_batched")
+    return [{f: getattr(i, f) for f, _ in i._fields_} for i in infos]

@@ -17,6 +17,9 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b, double* x, const fgmres_desc* d,
                      fgmres_info* info, double* history, cudaStream_t st);
+ib_status fgmres_run_batched(int count, const ib_system* const* sys, cav_hierarchy* const* H,
+                             const double* const* b, double* const* x, const fgmres_desc* d,
+                             fgmres_info* infos, cudaStream_t st);
 }  // namespace cav
 
 using namespace cav;
@@ -202,6 +205,8 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
     info->enlarged_sum_n2 = lv.big_sum_n2;
     const int bytes = (lv.precision == CAV_PREC_FP64) ? 8 : (lv.precision == CAV_PREC_FP32 ? 4 : 2);
     info->inverse_bytes = lv.inv_elems * bytes;
+    info->apply_variant = lv.apply_variant;
+    for (int v = 0; v < 5; ++v) info->apply_us[v] = lv.apply_us[v];
   }
   return IB_OK;
   CAV_API_END
@@ -372,6 +377,7 @@ void cav_destroy(cav_hierarchy* h) {
   vcycle_release(h);
   for (auto& e : h->fg_ev)
     if (e) cudaEventDestroy(e);
+  if (h->solve_stream) cudaStreamDestroy(h->solve_stream);
   for (auto& e : h->prof_ev) cudaEventDestroy(e);
   h->arena.release();
   h->ws_arena.release();
@@ -389,6 +395,29 @@ ib_status fgmres_solve(const ib_system* s, const cav_hierarchy* h, const double*
   std::memset(info, 0, sizeof(*info));
   ib_status r = fgmres_run(s, const_cast<cav_hierarchy*>(h), b, x, d, info, history, st);
   if (r == IB_ERR_NOCONV) set_error("fgmres_solve: maxit reached above tolerance");
+  return r;
+  CAV_API_END
+}
+
+ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
+                               const cav_hierarchy* const* hierarchies, const double* const* b, double* const* x,
+                               const fgmres_desc* d, fgmres_info* infos, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(count >= 1 && systems && hierarchies && b && x && d && infos, "fgmres_solve_batched: bad argument");
+  CAV_REQUIRE(d->maxit >= 1 && d->maxit <= 4096, "fgmres_solve_batched: maxit must be in [1, 4096]");
+  CAV_REQUIRE(d->rtol >= 0 && std::isfinite(d->rtol), "fgmres_solve_batched: bad rtol");
+  CAV_REQUIRE(!d->host_io, "fgmres_solve_batched: device buffers only");
+  std::vector<cav_hierarchy*> H(count);
+  for (int i = 0; i < count; ++i) {
+    CAV_REQUIRE(systems[i] && hierarchies[i] && b[i] && x[i], "fgmres_solve_batched: NULL entry");
+    CAV_REQUIRE(hierarchies[i]->sys == systems[i], "fgmres_solve_batched: hierarchy/system mismatch");
+    for (int j = 0; j < i; ++j)
+      CAV_REQUIRE(hierarchies[j] != hierarchies[i], "fgmres_solve_batched: a hierarchy appears twice");
+    H[i] = const_cast<cav_hierarchy*>(hierarchies[i]);
+    std::memset(&infos[i], 0, sizeof(fgmres_info));
+  }
+  ib_status r = fgmres_run_batched(count, systems, H.data(), b, x, d, infos, st);
+  if (r == IB_ERR_NOCONV) set_error("fgmres_solve_batched: some systems reached maxit above tolerance");
   return r;
   CAV_API_END
 }

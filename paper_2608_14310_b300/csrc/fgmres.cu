@@ -8,6 +8,7 @@
 // record per iteration to test convergence.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 #include "device_util.cuh"
@@ -165,112 +166,234 @@ static void dot_to(const cav_hierarchy* H, const double* a, const double* b, int
   CAV_CHECK_LAUNCH();
 }
 
+// One system's solve as a sequence of host steps, so that a batched call can advance many
+// systems in lockstep, each on its own stream:
+//   fg_start        r0 = b - K x, ||b||^2, ||r0||^2 (queued)
+//   fg_begin        read the norms (after a sync), set V_0 = r0 / beta
+//   fg_issue(k)     iteration k: V-cycle, K z, CGS2, ||w||, Givens, scale, record
+//   fg_check(k)     wait for iteration k's record and test convergence
+//   fg_finish       y = H^-1 g, x += Z y, true residual (queued); fg_result after a sync
+struct FgState {
+  const ib_system* sys = nullptr;
+  cav_hierarchy* H = nullptr;
+  const fgmres_desc* d = nullptr;
+  fgmres_info* info = nullptr;
+  double* history = nullptr;
+  cudaStream_t st = nullptr;
+  const double* b_user = nullptr;
+  double* x_user = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  int64_t n = 0;
+  FgLayout L{1};
+  LevelOps op{};
+  int nb = 0, vb = 0;
+  double ref = 0, beta = 0, est = 0;
+  int k_done = 0, pending = -1;
+  bool converged = false, active = false;
+  long long prof_mark[2] = {0, 0};
+};
+
+static void fg_start(FgState& s) {
+  cav_hierarchy* H = s.H;
+  const Level& l0 = H->levels[0];
+  s.n = 3LL * l0.N * l0.N;
+  ensure_workspace(H, s.d->maxit, s.n);
+  s.L = FgLayout(s.d->maxit);
+  s.b = s.b_user;
+  s.x = s.x_user;
+  if (s.d->host_io) {
+    CAV_CHECK_CUDA(cudaMemcpyAsync(H->io_b, s.b_user, sizeof(double) * s.n, cudaMemcpyHostToDevice, s.st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(H->io_x, s.x_user, sizeof(double) * s.n, cudaMemcpyHostToDevice, s.st));
+    s.b = H->io_b;
+    s.x = H->io_x;
+  }
+  double* S = H->dev_scalars;
+  CAV_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * s.L.total, s.st));
+  s.op = LevelOps{l0.N, l0.h, l0.rho_dt, l0.mu, l0.dt, &l0.ee};
+  s.nb = reduce_blocks(s.n);
+  s.vb = vec_blocks(s.n);
+  double* misc = S + s.L.misc;
+  launch_apply(s.op, s.x, s.b, H->V, 0, s.st);  // r0 -> V_0
+  dot_to(H, s.b, s.b, s.n, misc + 0, s.st);
+  dot_to(H, H->V, H->V, s.n, misc + 1, s.st);
+  k_init_beta<<<1, 1, 0, s.st>>>(S, s.L);
+  CAV_CHECK_LAUNCH();
+  CAV_CHECK_CUDA(cudaMemcpyAsync(H->host_b, misc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s.st));
+}
+
+// after the stream has been synchronised
+static void fg_begin(FgState& s) {
+  cav_hierarchy* H = s.H;
+  const double bnorm = std::sqrt(H->host_b[0]);
+  s.beta = std::sqrt(H->host_b[1]);
+  s.ref = (s.d->rel_to == 1) ? s.beta : bnorm;
+  s.est = (s.ref > 0) ? s.beta / s.ref : 0.0;
+  if (s.history) s.history[0] = s.est;
+  s.k_done = 0;
+  s.pending = -1;
+  if (!(s.ref > 0.0) || s.beta <= s.d->rtol * s.ref) {
+    s.converged = true;
+    s.active = false;
+    return;
+  }
+  s.active = true;
+  k_scale<<<s.vb, FG_THREADS, 0, s.st>>>(H->V, s.n, H->dev_scalars + s.L.misc + 3, H->V);
+  CAV_CHECK_LAUNCH();
+}
+
+static void fg_issue(FgState& s, int k) {
+  cav_hierarchy* H = s.H;
+  const int64_t n = s.n;
+  const int maxit = s.d->maxit;
+  double* S = H->dev_scalars;
+  double* misc = S + s.L.misc;
+  double* vk = H->V + (int64_t)k * n;
+  double* zk = H->Z + (int64_t)k * n;
+  double* w = H->V + (int64_t)(k + 1) * n;
+  vcycle(H, vk, zk, s.st);
+  launch_apply(s.op, zk, nullptr, w, 1, s.st);
+  for (int pass = 0; pass < 2; ++pass) {
+    k_multi_dot<<<dim3(s.nb, k + 1), FG_THREADS, 0, s.st>>>(H->V, n, k + 1, w, H->red_partial);
+    CAV_CHECK_LAUNCH();
+    k_finalize<<<k + 1, FG_THREADS, 0, s.st>>>(H->red_partial, s.nb, S + s.L.h, S + s.L.H + (int64_t)k * (maxit + 1));
+    CAV_CHECK_LAUNCH();
+    k_sub_multi<<<s.vb, FG_THREADS, 0, s.st>>>(H->V, n, k + 1, S + s.L.h, w);
+    CAV_CHECK_LAUNCH();
+  }
+  dot_to(H, w, w, n, misc + 2, s.st);
+  k_givens<<<1, 1, 0, s.st>>>(S, s.L, k);
+  CAV_CHECK_LAUNCH();
+  k_scale<<<s.vb, FG_THREADS, 0, s.st>>>(w, n, misc + 5, w);
+  CAV_CHECK_LAUNCH();
+  CAV_CHECK_CUDA(cudaMemcpyAsync(H->host_b + 8 + (k & 1), misc + 4, sizeof(double), cudaMemcpyDeviceToHost, s.st));
+  CAV_CHECK_CUDA(cudaEventRecord(H->fg_ev[k & 1], s.st));
+  s.prof_mark[k & 1] = H->prof_pushed;
+}
+
+static bool fg_check(FgState& s, int kk) {
+  cav_hierarchy* H = s.H;
+  CAV_CHECK_CUDA(cudaEventSynchronize(H->fg_ev[kk & 1]));
+  if (H->prof_on) prof_collect(H, s.prof_mark[kk & 1]);
+  s.k_done = kk + 1;
+  s.est = H->host_b[8 + (kk & 1)] / s.ref;
+  if (s.history) s.history[kk + 1] = s.est;
+  return H->host_b[8 + (kk & 1)] <= s.d->rtol * s.ref;
+}
+
+// Advance one system by one iteration in the lockstep: issue iteration k, then read the
+// previous iteration's convergence record while iteration k is queued (if iteration k - 1
+// converged, iteration k's work is discarded -- it writes only Hessenberg column k, Givens
+// pair k, g[k..k+1], V_{k+1} and Z_k, none of which the solution uses).
+static void fg_step(FgState& s, int k) {
+  if (!s.active) return;
+  fg_issue(s, k);
+  if (s.pending >= 0 && fg_check(s, s.pending)) {
+    s.converged = true;
+    s.active = false;
+    s.pending = -1;
+    return;
+  }
+  s.pending = k;
+}
+
+static void fg_drain(FgState& s) {
+  if (s.pending >= 0) {
+    if (fg_check(s, s.pending)) s.converged = true;
+    s.pending = -1;
+  }
+  s.active = false;
+}
+
+static void fg_finish(FgState& s) {
+  cav_hierarchy* H = s.H;
+  double* S = H->dev_scalars;
+  double* misc = S + s.L.misc;
+  if (s.k_done > 0) {
+    k_trisolve<<<1, 1, 0, s.st>>>(S, s.L, s.k_done);
+    CAV_CHECK_LAUNCH();
+    k_add_multi<<<s.vb, FG_THREADS, 0, s.st>>>(H->Z, s.n, s.k_done, S + s.L.y, s.x);
+    CAV_CHECK_LAUNCH();
+  }
+  const Level& l0 = H->levels[0];
+  launch_apply(s.op, s.x, s.b, l0.r, 0, s.st);  // true residual at exit
+  dot_to(H, l0.r, l0.r, s.n, misc + 6, s.st);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(H->host_b + 6, misc + 6, sizeof(double), cudaMemcpyDeviceToHost, s.st));
+  if (s.d->host_io)
+    CAV_CHECK_CUDA(cudaMemcpyAsync(s.x_user, s.x, sizeof(double) * s.n, cudaMemcpyDeviceToHost, s.st));
+}
+
+// after the stream has been synchronised
+static ib_status fg_result(FgState& s) {
+  s.info->iters = s.k_done;
+  s.info->converged = s.converged ? 1 : 0;
+  s.info->relres_est = s.est;
+  s.info->relres_true = (s.ref > 0) ? std::sqrt(s.H->host_b[6]) / s.ref : 0.0;
+  return s.converged ? IB_OK : IB_ERR_NOCONV;
+}
+
 ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b_in, double* x_in,
                      const fgmres_desc* d, fgmres_info* info, double* history, cudaStream_t st) {
-  const Level& l0 = H->levels[0];
-  const int64_t n = 3LL * l0.N * l0.N;
-  const int maxit = d->maxit;
-  ensure_workspace(H, maxit, n);
-  FgLayout L(maxit);
-  double* S = H->dev_scalars;
-  double* misc = S + L.misc;
-  double* hbuf = H->host_b;  // pinned, 16 doubles
-  const double* b = b_in;
-  double* x = x_in;
-  if (d->host_io) {
-    double* bd = H->io_b;
-    double* xd = H->io_x;
-    CAV_CHECK_CUDA(cudaMemcpyAsync(bd, b_in, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-    CAV_CHECK_CUDA(cudaMemcpyAsync(xd, x_in, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-    b = bd;
-    x = xd;
-  }
-  CAV_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * L.total, st));
-  LevelOps op{l0.N, l0.h, l0.rho_dt, l0.mu, l0.dt, &l0.ee};
-  const int nb = reduce_blocks(n);
-  const int vb = vec_blocks(n);
-  double* V = H->V;
-  double* Z = H->Z;
-  // r0 = b - K x  -> V_0
-  launch_apply(op, x, b, V, 0, st);
-  dot_to(H, b, b, n, misc + 0, st);
-  dot_to(H, V, V, n, misc + 1, st);
-  k_init_beta<<<1, 1, 0, st>>>(S, L);
-  CAV_CHECK_LAUNCH();
-  CAV_CHECK_CUDA(cudaMemcpyAsync(hbuf, misc, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  FgState s;
+  s.sys = sys;
+  s.H = H;
+  s.d = d;
+  s.info = info;
+  s.history = history;
+  s.st = st;
+  s.b_user = b_in;
+  s.x_user = x_in;
+  fg_start(s);
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-  const double bnorm = std::sqrt(hbuf[0]), beta = std::sqrt(hbuf[1]);
-  const double ref = (d->rel_to == 1) ? beta : bnorm;
-  int k_done = 0;
-  bool converged = false;
-  double est = (ref > 0) ? beta / ref : 0.0;
-  if (history) history[0] = est;
-  if (!(ref > 0.0) || beta <= d->rtol * ref) {
-    converged = true;
-  } else {
-    k_scale<<<vb, FG_THREADS, 0, st>>>(V, n, misc + 3, V);
-    CAV_CHECK_LAUNCH();
-    // The convergence test of iteration k is read on the host while iteration k + 1 is
-    // already queued: the host never waits on an idle device.  If iteration k converged,
-    // iteration k + 1's work is discarded -- it writes only Hessenberg column k + 1, Givens
-    // pair k + 1, g[k+1..k+2] and V_{k+2}, Z_{k+1}, none of which the solution uses.
-    int pending = -1;
-    long long prof_mark[2] = {0, 0};  // profiling records issued up to the end of iteration k
-    auto check = [&](int kk) -> bool {
-      CAV_CHECK_CUDA(cudaEventSynchronize(H->fg_ev[kk & 1]));
-      if (H->prof_on) prof_collect(H, prof_mark[kk & 1]);
-      k_done = kk + 1;
-      est = hbuf[8 + (kk & 1)] / ref;
-      if (history) history[kk + 1] = est;
-      return hbuf[8 + (kk & 1)] <= d->rtol * ref;
-    };
-    for (int k = 0; k < maxit; ++k) {
-      double* vk = V + (int64_t)k * n;
-      double* zk = Z + (int64_t)k * n;
-      double* w = V + (int64_t)(k + 1) * n;
-      vcycle(H, vk, zk, st);
-      launch_apply(op, zk, nullptr, w, 1, st);
-      for (int pass = 0; pass < 2; ++pass) {
-        k_multi_dot<<<dim3(nb, k + 1), FG_THREADS, 0, st>>>(V, n, k + 1, w, H->red_partial);
-        CAV_CHECK_LAUNCH();
-        k_finalize<<<k + 1, FG_THREADS, 0, st>>>(H->red_partial, nb, S + L.h, S + L.H + (int64_t)k * (maxit + 1));
-        CAV_CHECK_LAUNCH();
-        k_sub_multi<<<vb, FG_THREADS, 0, st>>>(V, n, k + 1, S + L.h, w);
-        CAV_CHECK_LAUNCH();
-      }
-      dot_to(H, w, w, n, misc + 2, st);
-      k_givens<<<1, 1, 0, st>>>(S, L, k);
-      CAV_CHECK_LAUNCH();
-      k_scale<<<vb, FG_THREADS, 0, st>>>(w, n, misc + 5, w);
-      CAV_CHECK_LAUNCH();
-      CAV_CHECK_CUDA(cudaMemcpyAsync(hbuf + 8 + (k & 1), misc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CAV_CHECK_CUDA(cudaEventRecord(H->fg_ev[k & 1], st));
-      prof_mark[k & 1] = H->prof_pushed;
-      if (pending >= 0 && check(pending)) {
-        converged = true;
-        pending = -1;
-        break;
-      }
-      pending = k;
+  fg_begin(s);
+  for (int k = 0; k < d->maxit && s.active; ++k) fg_step(s, k);
+  fg_drain(s);
+  fg_finish(s);
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  return fg_result(s);
+}
+
+// Many independent systems in lockstep, each on its own stream (created once per
+// hierarchy): their V-cycle graphs, products and Arnoldi kernels overlap on the device.
+// Returns IB_OK if every system converged, IB_ERR_NOCONV otherwise (infos hold each result).
+ib_status fgmres_run_batched(int count, const ib_system* const* sys, cav_hierarchy* const* H,
+                             const double* const* b, double* const* x, const fgmres_desc* d,
+                             fgmres_info* infos, cudaStream_t st) {
+  std::vector<FgState> S(count);
+  cudaEvent_t start_ev = nullptr;
+  CAV_CHECK_CUDA(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+  CAV_CHECK_CUDA(cudaEventRecord(start_ev, st));
+  for (int i = 0; i < count; ++i) {
+    if (!H[i]->solve_stream) CAV_CHECK_CUDA(cudaStreamCreateWithFlags(&H[i]->solve_stream, cudaStreamNonBlocking));
+    CAV_CHECK_CUDA(cudaStreamWaitEvent(H[i]->solve_stream, start_ev, 0));
+    S[i].sys = sys[i];
+    S[i].H = H[i];
+    S[i].d = d;
+    S[i].info = &infos[i];
+    S[i].st = H[i]->solve_stream;
+    S[i].b_user = b[i];
+    S[i].x_user = x[i];
+    fg_start(S[i]);
+  }
+  for (int i = 0; i < count; ++i) CAV_CHECK_CUDA(cudaStreamSynchronize(S[i].st));
+  for (int i = 0; i < count; ++i) fg_begin(S[i]);
+  for (int k = 0; k < d->maxit; ++k) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) {
+      fg_step(S[i], k);
+      any = any || S[i].active;
     }
-    if (pending >= 0 && check(pending)) converged = true;
-    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-    k_trisolve<<<1, 1, 0, st>>>(S, L, k_done);
-    CAV_CHECK_LAUNCH();
-    k_add_multi<<<vb, FG_THREADS, 0, st>>>(Z, n, k_done, S + L.y, x);
-    CAV_CHECK_LAUNCH();
+    if (!any) break;
   }
-  // true residual at exit
-  launch_apply(op, x, b, l0.r, 0, st);
-  dot_to(H, l0.r, l0.r, n, misc + 6, st);
-  CAV_CHECK_CUDA(cudaMemcpyAsync(hbuf + 6, misc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (d->host_io) CAV_CHECK_CUDA(cudaMemcpyAsync(x_in, x, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-  info->iters = k_done;
-  info->converged = converged ? 1 : 0;
-  info->relres_est = est;
-  info->relres_true = (ref > 0) ? std::sqrt(hbuf[6]) / ref : 0.0;
-  return converged ? IB_OK : IB_ERR_NOCONV;
+  for (int i = 0; i < count; ++i) fg_drain(S[i]);
+  for (int i = 0; i < count; ++i) fg_finish(S[i]);
+  bool all = true;
+  for (int i = 0; i < count; ++i) {
+    CAV_CHECK_CUDA(cudaStreamSynchronize(S[i].st));
+    all = (fg_result(S[i]) == IB_OK) && all;
+  }
+  cudaEventDestroy(start_ev);
+  return all ? IB_OK : IB_ERR_NOCONV;
 }
 
 }  // namespace cav

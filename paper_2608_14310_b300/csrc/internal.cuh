@@ -41,6 +41,8 @@ void note_launch();
     }                                                                               \
   } while (0)
 
+constexpr int NUM_APPLY_VARIANTS = 5;
+
 // Device status word codes (written by kernels, read by the host after set-up or a solve).
 enum : int { DEV_OK = 0, DEV_WINDOW = 1, DEV_SINGULAR = 2, DEV_CAPACITY = 3, DEV_TIMEOUT = 4 };
 
@@ -102,6 +104,8 @@ struct Level {
   float* inv32 = nullptr;
   __nv_bfloat16* inv16 = nullptr;
   int precision = CAV_PREC_FP64;
+  int apply_variant = 0;         // patch-apply kernel variant (autotuned when requested)
+  float apply_us[8] = {0};       // the autotuner's timing of each variant (us per launch)
   int64_t* inc_off = nullptr;    // [3 N^2 + 1] transpose incidence: slots of each unknown
   int* inc_slot = nullptr;       // [big_sum_n] packed-delta slots, ascending per unknown
   int n_touched = 0;             // unknowns held by at least one enlarged patch
@@ -164,6 +168,7 @@ struct cav_hierarchy {
   double* red_partial = nullptr;  // partial sums for multi-dot reductions
   double* host_b = nullptr;       // pinned scalars read back per iteration
   cudaEvent_t fg_ev[2] = {nullptr, nullptr};  // per-iteration convergence records
+  cudaStream_t solve_stream = nullptr;         // this system's stream in batched solves
   double* io_b = nullptr;         // device staging for host_io
   double* io_x = nullptr;
   cav::Arena ws_arena;
@@ -220,6 +225,7 @@ void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_collect(cav_hierarchy* H, long long upto = -1);
 void vcycle_release(cav_hierarchy* H);
+void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st);
 void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
 
 // reductions (reduce.cu)

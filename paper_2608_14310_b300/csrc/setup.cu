@@ -890,7 +890,11 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     if (lv.coarsest) build_coarsest(H, lv, st);
     else build_smoother(H, lv, st);
   }
+  if (H->desc.autotune)
+    for (auto& lv : H->levels)
+      if (!lv.coarsest) autotune_level(H, lv, st);
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  check_status(H, st, "autotune");
 }
 
 }  // namespace cav

@@ -77,6 +77,12 @@ struct VecLoad<__nv_bfloat16> {
   }
 };
 
+// acc + x * y as one fused multiply-add, so every kernel variant accumulates a patch's
+// columns in the same order with the same rounding (the autotuner's choice cannot change
+// a result bit).
+__device__ inline double mad(double x, double y, double acc) { return fma(x, y, acc); }
+__device__ inline float mad(float x, float y, float acc) { return fmaf(x, y, acc); }
+
 // Fallback for patches too large for the pipelined kernel: one CTA per patch, the scaled
 // residual in shared memory, the column-major inverse (ld = round8(n)) read straight from
 // global memory, each thread owning V consecutive rows.
@@ -107,7 +113,7 @@ k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, co
       VL::load(col + (int64_t)b * ld, x0);
       const acc_t yb = y[b];
 #pragma unroll
-      for (int q = 0; q < V; ++q) acc[q] += x0[q] * yb;
+      for (int q = 0; q < V; ++q) acc[q] = mad(x0[q], yb, acc[q]);
     }
 #pragma unroll
     for (int q = 0; q < V; ++q)
@@ -172,12 +178,9 @@ __device__ inline void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
 }
 __device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
 
-constexpr int TMA_STAGES = 4;
-constexpr int TMA_CHUNK = 16384;        // bytes per stage (a whole number of columns)
 constexpr int TMA_CONSUMER_WARPS = 4;
 constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 2);  // producer, gatherer, consumers
 constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
-constexpr int TMA_CTAS_PER_SM = 3;
 constexpr int Y_SLOTS = 2;
 
 template <typename T>
@@ -198,7 +201,7 @@ __host__ __device__ constexpr int tma_max_rows() {
 //    owning V consecutive rows (up to TMA_MAXPASS row blocks), then delta = s_c * acc.
 // Every wait is bounded; a timed-out wait records DEV_TIMEOUT and that warp stops waiting
 // and computing but still walks the patch sequence.
-template <typename T>
+template <typename T, int TMA_STAGES, int TMA_CHUNK>
 __global__ void __launch_bounds__(TMA_THREADS)
 k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __restrict__ off,
                   const int* __restrict__ dofs, const int64_t* __restrict__ inv_off, const T* __restrict__ inv,
@@ -301,21 +304,13 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
       for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
         const int a0 = (ps * CT + ct) * V;
         if (alive && a0 < n) {
-          int c = 0;
-          for (; c + 2 <= nc; c += 2) {
-            acc_t x0[V], x1[V];
-            VL::load_shared(X + (size_t)c * ld + a0, x0);
-            VL::load_shared(X + (size_t)(c + 1) * ld + a0, x1);
-            const acc_t y0 = y[b0 + c], y1 = y[b0 + c + 1];
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[ps][v] += x0[v] * y0 + x1[v] * y1;
-          }
-          if (c < nc) {
+#pragma unroll 4
+          for (int c = 0; c < nc; ++c) {
             acc_t x0[V];
             VL::load_shared(X + (size_t)c * ld + a0, x0);
             const acc_t y0 = y[b0 + c];
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[ps][v] += x0[v] * y0;
+            for (int v = 0; v < V; ++v) acc[ps][v] = mad(x0[v], y0, acc[ps][v]);
           }
         }
       }
@@ -528,27 +523,92 @@ static int sm_count() {
   return n;
 }
 
-template <typename T>
-static void launch_patch_apply(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r, double* delta,
-                               cudaStream_t st) {
+// Patch-apply variants the autotuner chooses among (per level, timed at set-up):
+//   0: TMA, 4 stages x 16 KiB, 3 CTAs/SM     1: TMA, 4 x 16 KiB, 2 CTAs/SM
+//   2: TMA, 8 stages x 8 KiB, 3 CTAs/SM      3: TMA, 4 x 8 KiB, 4 CTAs/SM
+//   4: one CTA per patch, no staging
+// All variants accumulate each row over the columns in ascending order with fused
+// multiply-adds, so they produce identical bits.
+struct ApplyVariant {
+  int stages, chunk, ctas_per_sm;
+};
+static const ApplyVariant kVariants[NUM_APPLY_VARIANTS] = {
+    {4, 16384, 3}, {4, 16384, 2}, {8, 8192, 3}, {4, 8192, 4}, {0, 0, 0}};
+
+template <typename T, int STAGES, int CHUNK>
+static void launch_tma(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r, double* delta,
+                       int ctas_per_sm, cudaStream_t st) {
   typedef typename VecLoad<T>::acc_t acc_t;
-  if (lv.big_max_n <= tma_max_rows<T>() && (size_t)round8(lv.big_max_n) * sizeof(T) <= (size_t)TMA_CHUNK) {
-    const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
-    const size_t smem = (size_t)TMA_STAGES * TMA_CHUNK + Y_SLOTS * ybytes +
-                        (2 * TMA_STAGES + 2 * Y_SLOTS) * sizeof(uint64_t);
-    static std::once_flag once;
-    std::call_once(once, [] {
-      cudaFuncSetAttribute(k_patch_apply_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    });
-    const int grid = std::min(lv.n_big, TMA_CTAS_PER_SM * sm_count());
-    k_patch_apply_tma<T><<<grid, TMA_THREADS, smem, st>>>(lv.n_big, lv.order, lv.big_off, lv.big_dofs, lv.inv_off,
-                                                          inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
-  } else {
-    const size_t smem = sizeof(acc_t) * (size_t)lv.big_max_n;
-    k_patch_apply<T, 128><<<lv.n_big, 128, smem, st>>>(lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r,
-                                                      lv.s_c, r, delta);
+  const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
+  const size_t smem = (size_t)STAGES * CHUNK + Y_SLOTS * ybytes + (2 * STAGES + 2 * Y_SLOTS) * sizeof(uint64_t);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_patch_apply_tma<T, STAGES, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+  });
+  const int grid = std::min(lv.n_big, ctas_per_sm * sm_count());
+  k_patch_apply_tma<T, STAGES, CHUNK><<<grid, TMA_THREADS, smem, st>>>(
+      lv.n_big, lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
+}
+
+// Can variant v run this level?  (rows per consumer thread and one whole column per stage)
+template <typename T>
+static bool variant_fits(const Level& lv, int v) {
+  if (kVariants[v].stages == 0) return true;
+  return lv.big_max_n <= tma_max_rows<T>() && (size_t)round8(lv.big_max_n) * sizeof(T) <= (size_t)kVariants[v].chunk;
+}
+
+template <typename T>
+static void launch_patch_apply_variant(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r,
+                                       double* delta, int v, cudaStream_t st) {
+  typedef typename VecLoad<T>::acc_t acc_t;
+  if (!variant_fits<T>(lv, v)) v = NUM_APPLY_VARIANTS - 1;
+  switch (v) {
+    case 0: launch_tma<T, 4, 16384>(H, lv, inv, r, delta, 3, st); break;
+    case 1: launch_tma<T, 4, 16384>(H, lv, inv, r, delta, 2, st); break;
+    case 2: launch_tma<T, 8, 8192>(H, lv, inv, r, delta, 3, st); break;
+    case 3: launch_tma<T, 4, 8192>(H, lv, inv, r, delta, 4, st); break;
+    default: {
+      const size_t smem = sizeof(acc_t) * (size_t)lv.big_max_n;
+      k_patch_apply<T, 128><<<lv.n_big, 128, smem, st>>>(lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r,
+                                                        lv.s_c, r, delta);
+    }
   }
   CAV_CHECK_LAUNCH();
+}
+
+static void launch_patch_apply_any(const cav_hierarchy* H, const Level& lv, const double* r, double* delta, int v,
+                                   cudaStream_t st) {
+  if (lv.precision == CAV_PREC_FP32) launch_patch_apply_variant<float>(H, lv, lv.inv32, r, delta, v, st);
+  else if (lv.precision == CAV_PREC_BF16) launch_patch_apply_variant<__nv_bfloat16>(H, lv, lv.inv16, r, delta, v, st);
+  else launch_patch_apply_variant<double>(H, lv, lv.inv64, r, delta, v, st);
+}
+
+// Autotuner: time every variant on this level's own patches (two warm-up and five timed
+// launches each, CUDA events on the set-up stream) and keep the fastest.
+void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+  lv.apply_variant = 0;
+  if (lv.n_big == 0) return;
+  cudaEvent_t e0, e1;
+  CAV_CHECK_CUDA(cudaEventCreate(&e0));
+  CAV_CHECK_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int v = 0; v < NUM_APPLY_VARIANTS; ++v) {
+    for (int w = 0; w < 2; ++w) launch_patch_apply_any(H, lv, lv.r, lv.delta, v, st);
+    CAV_CHECK_CUDA(cudaEventRecord(e0, st));
+    for (int w = 0; w < 5; ++w) launch_patch_apply_any(H, lv, lv.r, lv.delta, v, st);
+    CAV_CHECK_CUDA(cudaEventRecord(e1, st));
+    CAV_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    lv.apply_us[v] = 1e3f * ms / 5.f;
+    if (ms < best) {
+      best = ms;
+      lv.apply_variant = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
 }
 
 // The four steps of one sweep with explicit scratch (residual r_buf, packed corrections
@@ -564,9 +624,7 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   }
   if (lv.n_big > 0) {
     if (profile) prof_begin(H, l, st);
-    if (lv.precision == CAV_PREC_FP32) launch_patch_apply<float>(H, lv, lv.inv32, r, delta_buf, st);
-    else if (lv.precision == CAV_PREC_BF16) launch_patch_apply<__nv_bfloat16>(H, lv, lv.inv16, r, delta_buf, st);
-    else launch_patch_apply<double>(H, lv, lv.inv64, r, delta_buf, st);
+    launch_patch_apply_any(H, lv, r, delta_buf, lv.apply_variant, st);
     if (profile) prof_end(H, l, st);
   }
   StdInv S;

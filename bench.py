@@ -264,6 +264,53 @@ def run_batch(args, api, torch, dist, rank, world, local):
     return 0
 
 
+def run_learned(args, api, torch, rank, world):
+    """Time series of a tethered elastic ring in a time-periodic shear forcing (periodic box,
+    dt = 0.05 h, one linear solve per step, hierarchy rebuilt per step).  Steps 1..75% use the
+    previous-step guess with FP64 inverses and train the CNN; on the remaining steps every
+    system is solved three ways: plain FP64 + previous guess, FP32 + previous guess, FP32 +
+    learned guess.  value = solves/s of FP32 + learned over the test steps."""
+    from paper_2608_14310_b300.learned_guess import LearnedGuess, TimeSeries
+    if rank:
+        return 0
+    rec = W.tethered_ring(args.grid, dt_factor=args.dtfactor)
+    ts = TimeSeries(rec, W.shear_forcing, nu=args.nu, alpha=args.alpha, precision="fp64")
+    n_train = int(0.75 * args.nsteps)
+    t0 = time.perf_counter()
+    for _ in range(n_train):
+        ts.step()
+    t_train_series = time.perf_counter() - t0
+    lg = LearnedGuess(rec.N, hidden=32, n_hidden=3)
+    lg.fit_scales(ts, n_train)
+    tinfo = lg.train(ts, n_train, iters=1500, batch=16, lr=1e-3)
+    res = {"plain_fp64": [], "fp32_previous": [], "fp32_extrapolated": [], "fp32_learned": []}
+    for _ in range(args.nsteps - n_train):
+        out = ts.step(guesses=(("fp32_learned", lambda s: lg.predict(s), "fp32"),
+                               ("fp32_extrapolated", lambda s: lg.extrapolate(s), "fp32"),
+                               ("fp32_previous", None, "fp32"),
+                               ("plain_fp64", None, "fp64")))
+        for lab, inf, ms in out:
+            res[lab].append((inf["iters"], ms, inf["converged"], inf["relres_true"], inf["r0"]))
+    summ = {k: {"iters_mean": float(np.mean([r[0] for r in v])), "solve_ms_mean": float(np.mean([r[1] for r in v])),
+                "solves_per_s": 1e3 / float(np.mean([r[1] for r in v])),
+                "converged": int(sum(r[2] for r in v)), "relres_max": float(max(r[3] for r in v)),
+                "r0_geomean": float(np.exp(np.mean(np.log([max(r[4], 1e-300) for r in v]))))}
+            for k, v in res.items()}
+    line = {"metric": METRIC, "value": summ["fp32_learned"]["solves_per_s"], "unit": "solves/s",
+            "n_gpus": 1, "steps": args.nsteps - n_train, "warmup": n_train, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"tethered elastic ring (radius 0.2, spacing h/2, kappa_s 1, kappa_t 10) in a "
+                                   f"time-periodic shear forcing, periodic box N={rec.N}, dt={args.dtfactor}h, "
+                                   f"{args.nsteps} steps, "
+                                   f"rtol 1e-10 (||b||), hierarchy rebuilt per step; CNN trained on the first "
+                                   f"{n_train} steps (1500 Adam iterations, batch 16), tested on the rest",
+                       "nu": args.nu, "alpha": args.alpha},
+            "test_steps": summ, "train_series_s": t_train_series, "train_s": tinfo["train_s"],
+            "train_loss_first_last": [tinfo["losses"][0][1], tinfo["losses"][-1][1]]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,7 +321,10 @@ def main():
     ap.add_argument("--nu", type=int, default=DEFAULT_NU)
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="membrane256", choices=["membrane256", "batch64"])
+    ap.add_argument("--workload", default="membrane256", choices=["membrane256", "batch64", "learned"])
+    ap.add_argument("--grid", type=int, default=64, help="grid for --workload learned")
+    ap.add_argument("--nsteps", type=int, default=2000, help="time steps for --workload learned")
+    ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -296,6 +346,8 @@ def main():
 
     if args.workload == "batch64":
         return run_batch(args, api, torch, dist, rank, world, local)
+    if args.workload == "learned":
+        return run_learned(args, api, torch, rank, world)
 
     rec = workload(rank)
     n = 3 * rec.N * rec.N

@@ -225,3 +225,33 @@ def config4(count: int = 64) -> list[System]:
             sysm = beam_curve(N, 4 * N, k_bend=kappa, k_stretch=100.0 * kappa, seed=seed)
         out.append(replace(sysm, name=f"batch{s}-{sysm.name}"))
     return out
+
+
+# --------------------------------------------------------------------------- time series
+
+def tethered_ring(N: int, kappa_s: float = 1.0, kappa_t: float = 10.0, radius: float = 0.2,
+                  mu: float = 4e-3, dt_factor: float = 0.05) -> System:
+    """Closed elastic ring (spring-tension law) of the given radius about (0.5, 0.5), marker
+    spacing about h/2, tethered to its initial positions with stiffness kappa_t; dt = 0.05 h.
+    The periodic stand-in for a flexible structure held in a forced flow (mu = 4e-3 gives
+    Re ~ 100 for unit velocity and length 0.4); dt = dt_factor * h."""
+    per = 2.0 * np.pi * radius
+    M = int(math.ceil(per / (0.5 / N)))
+    X = ellipse_points(M, 0.5, 0.5, radius, radius)
+    sysm = _closed_system(f"tethered-ring-N{N}", N, X, LAW_MEMBRANE, 1.0, mu, dt_factor / N,
+                          BASE_SEED + 5000 + N, k_stretch=kappa_s, k_target=kappa_t)
+    sysm.X_target = X.copy()
+    return sysm
+
+
+def shear_forcing(N: int, t: float, amplitude: float = 1.0, period: float = 0.5) -> np.ndarray:
+    """Time-periodic body force on the velocity faces (u block then v block):
+    f_u = A sin(2 pi y) sin(2 pi t / T),  f_v = (A/2) sin(2 pi x) cos(2 pi t / T)."""
+    h = 1.0 / N
+    j, i = np.divmod(np.arange(N * N), N)
+    yu = (j + 0.5) * h
+    xv = (i + 0.5) * h
+    w = 2.0 * np.pi * t / period
+    fu = amplitude * np.sin(2.0 * np.pi * yu) * np.sin(w)
+    fv = 0.5 * amplitude * np.sin(2.0 * np.pi * xv) * np.cos(w)
+    return np.concatenate([fu, fv])

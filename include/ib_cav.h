@@ -63,9 +63,11 @@ typedef struct {
 
 /* Force laws (Lagrangian elasticity matrix E, acting identically on x and y):
  *   target   E = -k_target I                                  (Sec. 5.2)
- *   membrane E = k_stretch/ds^2 * cyclic [1 -2 1]             (Eq. disc_force_law)
- *   beam     E = k_stretch/ds^2 [1 -2 1] - k_bend/ds^4 [1 -4 6 -4 1], cyclic   (Sec. 5.2)
- * membrane and beam require closed = 1.                                              */
+ *   membrane E = k_stretch/ds^2 * cyclic [1 -2 1] - k_target I (Eq. disc_force_law)
+ *   beam     E = k_stretch/ds^2 [1 -2 1] - k_bend/ds^4 [1 -4 6 -4 1] - k_target I, cyclic
+ *                                                             (Sec. 5.2)
+ * membrane and beam require closed = 1.  The tether source k_target X_target enters the
+ * right-hand side only (ib_force, ib_step_rhs).                                        */
 typedef struct {
   int32_t M;             /* number of Lagrangian markers (0 allowed: no structure)      */
   int32_t closed;        /* 1: the marker chain is a closed curve                        */
@@ -73,7 +75,8 @@ typedef struct {
   const double* X;       /* host, 2M doubles interleaved (x0, y0, x1, y1, ...): X^n      */
   const double* omega;   /* host, M quadrature weights omega_k                            */
   double ds;             /* uniform Lagrangian spacing used by the force stencils         */
-  double k_target, k_stretch, k_bend;
+  double k_target, k_stretch, k_bend;  /* k_target != 0 tethers every marker on any law */
+  const double* X_target;  /* host, 2M interleaved, nullable: tether targets (source term) */
 } ib_structure_desc;
 
 typedef struct ib_system ib_system;
@@ -89,6 +92,23 @@ ib_status ib_residual(const ib_system* sys, const double* b, const double* x, do
                       cudaStream_t stream);
 void ib_destroy(ib_system* sys);
 
+/* Lagrangian / Eulerian transfers at the system's configuration X^n (Sec. 2) and the pieces
+ * of a semi-implicit time step (Eqs. im_disc_mom, im_disc_advec, Eul_schur).
+ * Lagrangian vectors F, U are device buffers of 2M doubles, x components then y components. */
+/* F = E X^n + k_target X_target. */
+ib_status ib_force(const ib_system* sys, double* F, cudaStream_t stream);
+/* f = S F on the 2 N^2 velocity faces (f: device, u block then v block). */
+ib_status ib_spread(const ib_system* sys, const double* F, double* f, cudaStream_t stream);
+/* U = J u from the velocity blocks of u (device, >= 2 N^2 entries). */
+ib_status ib_interp(const ib_system* sys, const double* u, double* U, cudaStream_t stream);
+/* Right-hand side of Eq. Eul_schur for one step: b_vel = (rho/dt) u_prev + f_body
+ * + S (E X^n + k_target X_target), b_p = 0.  u_prev (3 N^2) and f_body (2 N^2) are device
+ * buffers and may be NULL (zero). */
+ib_status ib_step_rhs(const ib_system* sys, const double* u_prev, const double* f_body, double* b,
+                      cudaStream_t stream);
+/* X^{n+1} = X^n + dt J u (Eq. im_disc_advec) into X_next (host, 2M interleaved); syncs. */
+ib_status ib_advect(const ib_system* sys, const double* u, double* X_next, cudaStream_t stream);
+
 /* -------------------------------------------------------- hierarchy (Sec. 3, Sec. 4) */
 
 typedef enum { CAV_PATCH_CAV = 0, CAV_PATCH_VANKA = 1 } cav_patch_kind;
@@ -102,6 +122,8 @@ typedef struct {
   int32_t precision;   /* cav_precision of the stored enlarged-patch inverses              */
   int32_t autotune;    /* 1: time the patch-apply kernel variants on each level's patches at
                           set-up and keep the fastest (all variants give identical bits)   */
+  int32_t krylov_capacity;  /* > 0: reserve FGMRES workspace for this many iterations at
+                               set-up (0: on the first solve)                              */
 } cav_desc;
 
 typedef struct cav_hierarchy cav_hierarchy;
@@ -231,6 +253,48 @@ ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
                                const cav_hierarchy* const* hierarchies, const double* const* b,
                                double* const* x, const fgmres_desc* desc, fgmres_info* infos,
                                cudaStream_t stream);
+
+/* ------------------------------------------------------ learned initial guess (CNN)
+ * Not from the paper: a small convolutional network that predicts each time step's initial
+ * FGMRES guess from the previous three steps' solutions (u, v, p) and spread Lagrangian
+ * forces (f_u, f_v), trained on solutions the solver produced.  FP32, periodic (circular)
+ * 3x3 convolutions: conv(in_ch -> hidden) GELU, (n_hidden - 1) x [conv(hidden -> hidden)
+ * GELU], conv(hidden -> out_ch).  Tensors are device FP32 [batch][channel][N][N]; parameters
+ * are one flat vector, per layer W[cout][cin][3][3] then b[cout].  Loss: mean squared error. */
+typedef struct ibnet ibnet;
+typedef struct {
+  int32_t in_ch, hidden, n_hidden, out_ch;
+  uint64_t seed;   /* weight initialisation (splitmix64) */
+} ibnet_desc;
+ib_status ibnet_create(const ibnet_desc* desc, ibnet** out);
+void ibnet_destroy(ibnet* net);
+int64_t ibnet_num_params(const ibnet* net);
+ib_status ibnet_get_params(const ibnet* net, float* host);
+ib_status ibnet_set_params(ibnet* net, const float* host);   /* also resets Adam state */
+ib_status ibnet_forward(ibnet* net, const float* in, float* out, int32_t batch, int32_t N,
+                        cudaStream_t stream);
+/* Loss and all parameter gradients for one batch (host copies; syncs). */
+ib_status ibnet_gradients(ibnet* net, const float* in, const float* target, int32_t batch,
+                          int32_t N, float* loss, float* grads, cudaStream_t stream);
+/* Forward, backward and one Adam step (beta 0.9 / 0.999, eps 1e-8); loss (host) optional. */
+ib_status ibnet_train_step(ibnet* net, const float* in, const float* target, int32_t batch,
+                           int32_t N, float lr, float* loss, cudaStream_t stream);
+/* in (15 x N x N) from three steps x_0, x_1, x_2 (hist_x, device, 3 N^2 FP64, oldest first)
+ * and spread forces f_0, f_1, f_2 (hist_f, device, 2 N^2 FP64): three groups of channels
+ * (u, v, p, f_u, f_v) holding x_1 - x_0 | f_1 - f_0, then x_2 - x_1 | f_2 - f_1, then
+ * x_2 | f_2, each divided by in_scale[c]. */
+ib_status ibnet_pack_input(int32_t N, const double* const* hist_x, const double* const* hist_f,
+                           const float* in_scale, float* out, cudaStream_t stream);
+/* target (3 x N x N) = (x_new - base) / out_scale per field (u, v, p), where base is x_prev,
+ * or the linear extrapolation 2 x_prev - x_prev2 when x_prev2 is not NULL. */
+ib_status ibnet_pack_target(int32_t N, const double* x_new, const double* x_prev,
+                            const double* x_prev2, const float* out_scale, float* out,
+                            cudaStream_t stream);
+/* x_out = base + out_scale * delta per field (base as above; delta NULL: base alone): the
+ * predicted initial guess. */
+ib_status ibnet_apply_delta(int32_t N, const double* x_prev, const double* x_prev2,
+                            const float* delta, const float* out_scale, double* x_out,
+                            cudaStream_t stream);
 
 #ifdef __cplusplus
 }

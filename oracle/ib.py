@@ -116,6 +116,7 @@ def force_matrix(law: int, M: int, ds: float, k_target: float, k_stretch: float,
     if law == 0:
         E1 = -k_target * sp.identity(M, format="csr")
     else:
+        # tethers (-k_target I, Sec. 5.2) may accompany the membrane and beam laws
         st = {}
         if k_stretch != 0.0:
             c = k_stretch / ds ** 2
@@ -125,11 +126,14 @@ def force_matrix(law: int, M: int, ds: float, k_target: float, k_stretch: float,
             c = -k_bend / ds ** 4
             for d, w in ((-2, 1.0), (-1, -4.0), (0, 6.0), (1, -4.0), (2, 1.0)):
                 st[d] = st.get(d, 0.0) + c * w
+        if k_target != 0.0:
+            st[0] = st.get(0, 0.0) - k_target
         E1 = _cyclic(M, st)
     return sp.block_diag([E1, E1], format="csr")
 
 
-def force_pattern(law: int, M: int, k_stretch: float, k_bend: float) -> sp.csr_matrix:
+def force_pattern(law: int, M: int, k_stretch: float, k_bend: float,
+                  k_target: float = 0.0) -> sp.csr_matrix:
     """Structural pattern of E: the stencil offsets whose coefficient is nonzero."""
     if law == 0:
         offs = [0]
@@ -139,6 +143,8 @@ def force_pattern(law: int, M: int, k_stretch: float, k_bend: float) -> sp.csr_m
             offs |= {-1, 0, 1}
         if law == 2 and k_bend != 0.0:
             offs |= {-2, -1, 0, 1, 2}
+        if k_target != 0.0:
+            offs |= {0}
         offs = sorted(offs)
     B1 = _cyclic(M, {d: 1 for d in offs})
     B1.data = np.ones_like(B1.data)
@@ -153,7 +159,7 @@ def eulerian_elasticity(sysm):
     E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
     EE = (S @ E @ J).tocsr()
     Jb = support_pattern(N, h, sysm.X)
-    Eb = force_pattern(sysm.law, sysm.M, sysm.k_stretch, sysm.k_bend)
+    Eb = force_pattern(sysm.law, sysm.M, sysm.k_stretch, sysm.k_bend, sysm.k_target)
     pat = (Jb.T @ Eb @ Jb).tocsr()
     pat.data = np.ones_like(pat.data)
     pat = pat.astype(bool)
@@ -179,9 +185,39 @@ def first_step_rhs(sysm) -> np.ndarray:
     N, h, M = sysm.N, sysm.h, sysm.M
     S = spreading_matrix(N, h, sysm.X, sysm.omega)
     E = force_matrix(sysm.law, M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
-    F = E @ np.concatenate([sysm.X[:, 0], sysm.X[:, 1]])
-    if sysm.law == 0 and sysm.X_target is not None:
-        F = F + sysm.k_target * np.concatenate([sysm.X_target[:, 0], sysm.X_target[:, 1]])
+    F = force_vector(sysm)
     b = np.zeros(3 * N * N)
     b[:2 * N * N] = S @ F
     return b
+
+
+def force_vector(sysm) -> np.ndarray:
+    """F = E X^n + k_target X_target (component-major): the linear laws' force at X^n
+    (Eq. disc_force_law, Sec. 5.2)."""
+    E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
+    F = E @ np.concatenate([sysm.X[:, 0], sysm.X[:, 1]])
+    if sysm.k_target != 0.0 and sysm.X_target is not None:
+        F = F + sysm.k_target * np.concatenate([sysm.X_target[:, 0], sysm.X_target[:, 1]])
+    return F
+
+
+def step_rhs(sysm, u_prev=None, f_body=None) -> np.ndarray:
+    """Right-hand side of Eq. (Eul_schur) for one semi-implicit step without convection:
+    velocity rows (rho/dt) u^n + f_body + S (E X^n + k_target X_target), pressure rows 0."""
+    N, h = sysm.N, sysm.h
+    S = spreading_matrix(N, h, sysm.X, sysm.omega)
+    b = np.zeros(3 * N * N)
+    b[:2 * N * N] = S @ force_vector(sysm)
+    if u_prev is not None:
+        b[:2 * N * N] += (sysm.rho / sysm.dt) * u_prev[:2 * N * N]
+    if f_body is not None:
+        b[:2 * N * N] += f_body
+    return b
+
+
+def advect(sysm, u) -> np.ndarray:
+    """X^{n+1} = X^n + dt J^n u^{n+1} (Eq. im_disc_advec), returned as (M, 2)."""
+    J = interpolation_matrix(sysm.N, sysm.h, sysm.X)
+    U = J @ u[:2 * sysm.N * sysm.N]
+    M = sysm.M
+    return sysm.X + sysm.dt * np.stack([U[:M], U[M:]], axis=1)

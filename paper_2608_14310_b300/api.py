@@ -41,13 +41,14 @@ class ib_grid_desc(C.Structure):
 class ib_structure_desc(C.Structure):
     _fields_ = [("M", C.c_int32), ("closed", C.c_int32), ("law", C.c_int32),
                 ("X", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)), ("ds", C.c_double),
-                ("k_target", C.c_double), ("k_stretch", C.c_double), ("k_bend", C.c_double)]
+                ("k_target", C.c_double), ("k_stretch", C.c_double), ("k_bend", C.c_double),
+                ("X_target", C.POINTER(C.c_double))]
 
 
 class cav_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("coarsest_N", C.c_int32), ("nu_pre", C.c_int32),
                 ("nu_post", C.c_int32), ("alpha", C.c_double), ("precision", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("krylov_capacity", C.c_int32)]
 
 
 class cav_level_info(C.Structure):
@@ -69,6 +70,11 @@ class fgmres_info(C.Structure):
                 ("relres_true", C.c_double)]
 
 
+class ibnet_desc(C.Structure):
+    _fields_ = [("in_ch", C.c_int32), ("hidden", C.c_int32), ("n_hidden", C.c_int32), ("out_ch", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
 _vp = C.c_void_p
 _P = C.POINTER
 _sig = {
@@ -81,6 +87,11 @@ _sig = {
     "ib_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "ib_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ib_destroy": (None, [_vp]),
+    "ib_force": (C.c_int, [_vp, _vp, _vp]),
+    "ib_spread": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ib_interp": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ib_step_rhs": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ib_advect": (C.c_int, [_vp, _vp, _vp, _vp]),
     "cav_setup": (C.c_int, [_vp, _P(cav_desc), _vp, _P(_vp)]),
     "cav_num_levels": (C.c_int, [_vp, _P(C.c_int32)]),
     "cav_get_level_info": (C.c_int, [_vp, C.c_int32, _P(cav_level_info)]),
@@ -94,6 +105,17 @@ _sig = {
     "cav_coarse_solve": (C.c_int, [_vp, _vp, _vp, _vp]),
     "vcycle_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "cav_destroy": (None, [_vp]),
+    "ibnet_create": (C.c_int, [_P(ibnet_desc), _P(_vp)]),
+    "ibnet_destroy": (None, [_vp]),
+    "ibnet_num_params": (C.c_int64, [_vp]),
+    "ibnet_get_params": (C.c_int, [_vp, _vp]),
+    "ibnet_set_params": (C.c_int, [_vp, _vp]),
+    "ibnet_forward": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _vp]),
+    "ibnet_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _P(C.c_float), _vp, _vp]),
+    "ibnet_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_float, _P(C.c_float), _vp]),
+    "ibnet_pack_input": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(C.c_float), _vp, _vp]),
+    "ibnet_pack_target": (C.c_int, [C.c_int32, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
+    "ibnet_apply_delta": (C.c_int, [C.c_int32, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
     "fgmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, _P(fgmres_desc), _P(fgmres_info), _vp, _vp]),
     "fgmres_solve_batched": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(_vp), _P(_vp), _P(fgmres_desc),
                                        _P(fgmres_info), _vp]),
@@ -183,9 +205,12 @@ def ib_setup(rec, stream=None) -> System:
     X = np.ascontiguousarray(np.asarray(rec.X, dtype=np.float64).reshape(-1))
     om = np.ascontiguousarray(np.asarray(rec.omega, dtype=np.float64))
     M = int(X.size // 2)
+    Xt = getattr(rec, "X_target", None)
+    Xt = None if Xt is None else np.ascontiguousarray(np.asarray(Xt, dtype=np.float64).reshape(-1))
     sd = ib_structure_desc(M, 1 if rec.closed else 0, int(rec.law),
                            X.ctypes.data_as(_P(C.c_double)), om.ctypes.data_as(_P(C.c_double)),
-                           float(rec.ds), float(rec.k_target), float(rec.k_stretch), float(rec.k_bend))
+                           float(rec.ds), float(rec.k_target), float(rec.k_stretch), float(rec.k_bend),
+                           Xt.ctypes.data_as(_P(C.c_double)) if Xt is not None else None)
     out = _vp()
     _check(_lib.ib_setup(C.byref(g), C.byref(sd), _stream(stream), C.byref(out)), "ib_setup")
     return System(out, int(rec.N), rec)
@@ -199,10 +224,33 @@ def ib_residual(sys: System, b, x, r, stream=None):
     _check(_lib.ib_residual(sys.handle, _dev(b), _dev(x), _dev(r), _stream(stream)), "ib_residual")
 
 
+def ib_force(sys: System, F, stream=None):
+    _check(_lib.ib_force(sys.handle, _dev(F), _stream(stream)), "ib_force")
+
+
+def ib_spread(sys: System, F, f, stream=None):
+    _check(_lib.ib_spread(sys.handle, _dev(F), _dev(f), _stream(stream)), "ib_spread")
+
+
+def ib_interp(sys: System, u, U, stream=None):
+    _check(_lib.ib_interp(sys.handle, _dev(u), _dev(U), _stream(stream)), "ib_interp")
+
+
+def ib_step_rhs(sys: System, u_prev, f_body, b, stream=None):
+    _check(_lib.ib_step_rhs(sys.handle, _dev(u_prev), _dev(f_body), _dev(b), _stream(stream)), "ib_step_rhs")
+
+
+def ib_advect(sys: System, u, stream=None) -> np.ndarray:
+    M = 0 if sys.rec is None else int(np.asarray(sys.rec.X).shape[0])
+    out = np.zeros(2 * M)
+    _check(_lib.ib_advect(sys.handle, _dev(u), _vp(out.ctypes.data), _stream(stream)), "ib_advect")
+    return out.reshape(M, 2)
+
+
 def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=1.0,
-              precision="fp64", autotune=False, stream=None) -> Hierarchy:
+              precision="fp64", autotune=False, krylov_capacity=0, stream=None) -> Hierarchy:
     d = cav_desc(KIND[kind], int(coarsest_N), int(nu_pre), int(nu_post), float(alpha), PRECISION[precision],
-                 1 if autotune else 0)
+                 1 if autotune else 0, int(krylov_capacity))
     out = _vp()
     _check(_lib.cav_setup(sys.handle, C.byref(d), _stream(stream), C.byref(out)), "cav_setup")
     return Hierarchy(out, sys, dict(kind=kind, coarsest_N=coarsest_N, nu_pre=nu_pre, nu_post=nu_post,
@@ -333,3 +381,83 @@ def fgmres_solve_batched(systems, hierarchies, bs, xs, rtol=1e-10, maxit=60, rel
     if st not in (IB_OK, IB_ERR_NOCONV) or (st == IB_ERR_NOCONV and raise_on_noconv):
         raise IBError(st, "fgmres_solve_batched")
     return [{f: getattr(i, f) for f, _ in i._fields_} for i in infos]
+
+
+def _devf(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("network tensors must be contiguous float32 CUDA tensors")
+    return _vp(t.data_ptr())
+
+
+class IBNet:
+    """Owns an ibnet handle (the learned-initial-guess network)."""
+
+    def __init__(self, in_ch=15, hidden=32, n_hidden=3, out_ch=3, seed=1):
+        d = ibnet_desc(in_ch, hidden, n_hidden, out_ch, seed)
+        h = _vp()
+        _check(_lib.ibnet_create(C.byref(d), C.byref(h)), "ibnet_create")
+        self._h = h
+        self.desc = dict(in_ch=in_ch, hidden=hidden, n_hidden=n_hidden, out_ch=out_ch, seed=seed)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.ibnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self) -> int:
+        return int(_lib.ibnet_num_params(self._h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        _check(_lib.ibnet_get_params(self._h, _vp(out.ctypes.data)), "ibnet_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(_lib.ibnet_set_params(self._h, _vp(p.ctypes.data)), "ibnet_set_params")
+
+    def forward(self, x, out, batch, N, stream=None):
+        _check(_lib.ibnet_forward(self._h, _devf(x), _devf(out), batch, N, _stream(stream)), "ibnet_forward")
+
+    def gradients(self, x, target, batch, N, stream=None):
+        loss = C.c_float()
+        g = np.zeros(self.num_params(), dtype=np.float32)
+        _check(_lib.ibnet_gradients(self._h, _devf(x), _devf(target), batch, N, C.byref(loss), _vp(g.ctypes.data),
+                                    _stream(stream)), "ibnet_gradients")
+        return float(loss.value), g
+
+    def train_step(self, x, target, batch, N, lr, want_loss=False, stream=None):
+        loss = C.c_float()
+        _check(_lib.ibnet_train_step(self._h, _devf(x), _devf(target), batch, N, float(lr),
+                                     C.byref(loss) if want_loss else None, _stream(stream)), "ibnet_train_step")
+        return float(loss.value) if want_loss else None
+
+
+def ibnet_pack_input(N, hist_x, hist_f, in_scale, out, stream=None):
+    hx = (_vp * 3)(*[_dev(t) for t in hist_x])
+    hf = (_vp * 3)(*[_dev(t) for t in hist_f])
+    sc = (C.c_float * 15)(*[float(v) for v in in_scale])
+    _check(_lib.ibnet_pack_input(N, hx, hf, sc, _devf(out), _stream(stream)), "ibnet_pack_input")
+
+
+def ibnet_pack_target(N, x_new, x_prev, out_scale, out, x_prev2=None, stream=None):
+    sc = (C.c_float * 3)(*[float(v) for v in out_scale])
+    _check(_lib.ibnet_pack_target(N, _dev(x_new), _dev(x_prev), _dev(x_prev2), sc, _devf(out), _stream(stream)),
+           "ibnet_pack_target")
+
+
+def ibnet_apply_delta(N, x_prev, delta, out_scale, x_out, x_prev2=None, stream=None):
+    sc = (C.c_float * 3)(*[float(v) for v in out_scale])
+    _check(_lib.ibnet_apply_delta(N, _dev(x_prev), _dev(x_prev2), None if delta is None else _devf(delta), sc,
+                                  _dev(x_out), _stream(stream)), "ibnet_apply_delta")

@@ -75,8 +75,16 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   // beam -> +-2 when k_bend != 0, else +-1 when k_stretch != 0; otherwise no structure
   int M = sd->M, bw = 0;
   if (sd->law == IB_FORCE_TARGET) bw = 0;
-  else if (sd->law == IB_FORCE_MEMBRANE) { if (sd->k_stretch != 0.0) bw = 1; else M = 0; }
-  else { if (sd->k_bend != 0.0) bw = 2; else if (sd->k_stretch != 0.0) bw = 1; else M = 0; }
+  else if (sd->law == IB_FORCE_MEMBRANE) {
+    if (sd->k_stretch != 0.0) bw = 1;
+    else if (sd->k_target != 0.0) bw = 0;
+    else M = 0;
+  } else {
+    if (sd->k_bend != 0.0) bw = 2;
+    else if (sd->k_stretch != 0.0) bw = 1;
+    else if (sd->k_target != 0.0) bw = 0;
+    else M = 0;
+  }
   if (M > 0 && bw > 0) {
     CAV_REQUIRE(sd->closed, "ib_setup: membrane and beam laws need a closed marker chain");
     CAV_REQUIRE(M >= 2 * bw + 1, "ib_setup: too few markers for the force stencil");
@@ -87,6 +95,19 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   s->status = s->arena.alloc<int>(1);
   CAV_CHECK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   build_markers_and_ee(s, sd->X, sd->omega, st);
+  if (M > 0) {
+    s->X_host.assign(sd->X, sd->X + 2 * (size_t)M);
+    if (sd->X_target) {
+      std::vector<double> cm(2 * (size_t)M);
+      for (int a = 0; a < M; ++a) {
+        cm[a] = sd->X_target[2 * a];
+        cm[M + a] = sd->X_target[2 * a + 1];
+      }
+      s->Xt = s->arena.alloc<double>(2 * M);
+      CAV_CHECK_CUDA(cudaMemcpyAsync(s->Xt, cm.data(), sizeof(double) * 2 * M, cudaMemcpyHostToDevice, st));
+      CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+  }
   const int code = read_status(s->status, st);
   if (code != DEV_OK) {
     set_error("ib_setup: E_E assembly window overflow");
@@ -127,6 +148,56 @@ ib_status ib_residual(const ib_system* s, const double* b, const double* x, doub
   CAV_API_END
 }
 
+ib_status ib_force(const ib_system* s, double* F, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && F, "ib_force: NULL argument");
+  ib_force_launch(s, F, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status ib_spread(const ib_system* s, const double* F, double* f, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && f && (F || s->M == 0), "ib_spread: NULL argument");
+  ib_spread_launch(s, F, f, 0, nullptr, nullptr, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status ib_interp(const ib_system* s, const double* u, double* U, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && u && (U || s->M == 0), "ib_interp: NULL argument");
+  ib_interp_launch(s, u, U, 0.0, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status ib_step_rhs(const ib_system* s, const double* u_prev, const double* f_body, double* b, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && b, "ib_step_rhs: NULL argument");
+  ib_force_launch(s, s->F, st);
+  ib_spread_launch(s, s->F, b, 1, u_prev, f_body, st);
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status ib_advect(const ib_system* s, const double* u, double* X_next, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && u && X_next, "ib_advect: NULL argument");
+  const int M = s->M;
+  if (M == 0) return IB_OK;
+  ib_interp_launch(s, u, s->U, s->dt, st);
+  std::vector<double> cm(2 * (size_t)M);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(cm.data(), s->U, sizeof(double) * 2 * M, cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  for (int a = 0; a < M; ++a) {
+    X_next[2 * a] = cm[a];
+    X_next[2 * a + 1] = cm[M + a];
+  }
+  return IB_OK;
+  CAV_API_END
+}
+
 void ib_destroy(ib_system* s) {
   if (!s) return;
   cudaDeviceSynchronize();
@@ -146,6 +217,7 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
                 "cav_setup: need at least one sweep per level");
     CAV_REQUIRE(d->precision >= CAV_PREC_FP64 && d->precision <= CAV_PREC_BF16, "cav_setup: unknown precision");
     CAV_REQUIRE(std::isfinite(d->alpha) && d->alpha > 0, "cav_setup: alpha must be positive");
+    CAV_REQUIRE(d->krylov_capacity >= 0 && d->krylov_capacity <= 4096, "cav_setup: bad krylov_capacity");
     H = new cav_hierarchy();
     H->sys = s;
     H->desc = *d;

@@ -157,6 +157,8 @@ static void ensure_workspace(cav_hierarchy* H, int maxit, int64_t n) {
   H->ws_maxit = maxit;
 }
 
+void krylov_reserve(cav_hierarchy* H, int maxit, int64_t n) { ensure_workspace(H, maxit, n); }
+
 static void dot_to(const cav_hierarchy* H, const double* a, const double* b, int64_t n, double* out,
                    cudaStream_t st) {
   const int nb = reduce_blocks(n);

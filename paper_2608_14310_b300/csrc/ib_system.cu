@@ -50,6 +50,7 @@ __global__ void k_force_band(int M, int bw, int law, double ds, double k_target,
     if (law == IB_FORCE_TARGET) {
       e = -k_target;
     } else {
+      if (d == 0 && k_target != 0.0) e += -k_target;  // tethers to targets (Sec. 5.2) on any law
       if (k_stretch != 0.0) {
         const double c2 = k_stretch / (ds * ds);
         if (d == 0) e += c2 * -2.0;
@@ -249,6 +250,101 @@ void ee_compute_window(EECsr& ee, int N, int* d_scratch, cudaStream_t st) {
   ee.W = w;
 }
 
+// F = E X^n + k_target X_target (component-major, both components), the Lagrangian force
+// of the linear laws at the current configuration (Eq. disc_force_law, Sec. 5.2).
+__global__ void k_force(int M, int bw, int closed, const double* __restrict__ band, const double* __restrict__ X,
+                        double k_target, const double* __restrict__ Xt, double* __restrict__ F) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= 2 * M) return;
+  const int c = id / M, a = id % M;
+  double f = 0.0;
+  for (int d = -bw; d <= bw; ++d) {
+    int b = a + d;
+    if (closed) b = pmod(b, M);
+    else if (b < 0 || b >= M) continue;
+    f += band[a * (2 * bw + 1) + (d + bw)] * X[c * M + b];
+  }
+  if (Xt) f += k_target * Xt[id];
+  F[id] = f;
+}
+
+// f = S F on every velocity face (Sec. 2): the face's markers in ascending order,
+// S[face, a] = omega_a / h^2 * phi phi.  One thread per face, no atomics.  With rhs != 0
+// the face value also takes rho_dt * u_prev + f_body (right-hand side of Eq. Eul_schur)
+// and the pressure rows are zeroed.
+__global__ void k_spread(int N, int M, double h, const double* __restrict__ omega, const int* __restrict__ sup_i0,
+                         const int* __restrict__ sup_j0, const double* __restrict__ wx, const double* __restrict__ wy,
+                         const int64_t* __restrict__ fm_off, const int* __restrict__ fm_list,
+                         const double* __restrict__ F, double* __restrict__ f, int rhs, double rho_dt,
+                         const double* __restrict__ u_prev, const double* __restrict__ f_body) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NN = N * N;
+  if (k >= 3 * NN) return;
+  if (k >= 2 * NN) {
+    if (rhs) f[k] = 0.0;
+    return;
+  }
+  const int c = k / NN, rem = k % NN, ik = rem % N, jk = rem / N;
+  const double inv_h2 = 1.0 / (h * h);
+  double s = 0.0;
+  if (fm_off)
+    for (int64_t q = fm_off[k]; q < fm_off[k + 1]; ++q) {
+      const int a = fm_list[q];
+      const int ida = c * M + a;
+      const int si = pmod(ik - sup_i0[ida], N), sj = pmod(jk - sup_j0[ida], N);
+      s += wx[4 * ida + si] * wy[4 * ida + sj] * (omega[a] * inv_h2) * F[ida];
+    }
+  if (rhs) {
+    double v = s;
+    if (u_prev) v += rho_dt * u_prev[k];
+    if (f_body) v += f_body[k];
+    f[k] = v;
+  } else {
+    f[k] = s;
+  }
+}
+
+// U = J u (Sec. 2): U_a = sum over the marker's 4 x 4 support of phi phi u_face.  With
+// dt != 0, instead X_out = X + dt U (Eq. im_disc_advec).
+__global__ void k_interp(int N, int M, const int* __restrict__ sup_i0, const int* __restrict__ sup_j0,
+                         const double* __restrict__ wx, const double* __restrict__ wy, const uint8_t* __restrict__ mask,
+                         const double* __restrict__ u, double* __restrict__ U, double dt, const double* __restrict__ X) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= 2 * M) return;
+  const int c = id / M;
+  const uint8_t m = mask[id];
+  double s = 0.0;
+  for (int sy = 0; sy < 4; ++sy) {
+    if (!(m & (1u << (sy + 4)))) continue;
+    for (int sx = 0; sx < 4; ++sx) {
+      if (!(m & (1u << sx))) continue;
+      const int face = c * N * N + pmod(sup_j0[id] + sy, N) * N + pmod(sup_i0[id] + sx, N);
+      s += wx[4 * id + sx] * wy[4 * id + sy] * u[face];
+    }
+  }
+  U[id] = (dt != 0.0) ? X[id] + dt * s : s;
+}
+
+void ib_force_launch(const ib_system* s, double* F, cudaStream_t st) {
+  if (s->M == 0) return;
+  k_force<<<div_up(2 * s->M, 128), 128, 0, st>>>(s->M, s->bw, s->closed, s->Eband, s->X, s->k_target, s->Xt, F);
+  CAV_CHECK_LAUNCH();
+}
+void ib_spread_launch(const ib_system* s, const double* F, double* f, int rhs, const double* u_prev,
+                      const double* f_body, cudaStream_t st) {
+  const int NN = s->N * s->N;
+  k_spread<<<div_up(3 * NN, 256), 256, 0, st>>>(s->N, s->M, s->h, s->omega, s->sup_i0, s->sup_j0, s->sup_wx,
+                                               s->sup_wy, s->M ? s->fm_off : nullptr, s->fm_list, F, f, rhs,
+                                               s->rho / s->dt, u_prev, f_body);
+  CAV_CHECK_LAUNCH();
+}
+void ib_interp_launch(const ib_system* s, const double* u, double* U, double dt, cudaStream_t st) {
+  if (s->M == 0) return;
+  k_interp<<<div_up(2 * s->M, 128), 128, 0, st>>>(s->N, s->M, s->sup_i0, s->sup_j0, s->sup_wx, s->sup_wy,
+                                                 s->sup_mask, u, U, dt, s->X);
+  CAV_CHECK_LAUNCH();
+}
+
 static size_t ee_smem_per_warp(int W, int N) {
   const int len = (2 * W + 1 >= N) ? N : 2 * W + 1;
   return (size_t)len * len * (sizeof(double) + 1);
@@ -279,6 +375,8 @@ void build_markers_and_ee(ib_system* s, const double* X_il, const double* omega_
     }
     s->X = A.alloc<double>(2 * M);
     s->omega = A.alloc<double>(M);
+    s->F = A.alloc<double>(2 * M);
+    s->U = A.alloc<double>(2 * M);
     CAV_CHECK_CUDA(cudaMemcpyAsync(s->X, Xcm.data(), sizeof(double) * 2 * M, cudaMemcpyHostToDevice, st));
     CAV_CHECK_CUDA(cudaMemcpyAsync(s->omega, omega_host, sizeof(double) * M, cudaMemcpyHostToDevice, st));
     s->sup_i0 = A.alloc<int>(2 * M);

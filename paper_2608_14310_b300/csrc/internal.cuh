@@ -141,6 +141,10 @@ struct ib_system {
   double* X = nullptr;
   double* omega = nullptr;
   double* Eband = nullptr;       // [M * (2 bw + 1)] E coefficient of (a, a + d)
+  double* Xt = nullptr;          // [2M] target positions (component-major) or null
+  double* F = nullptr;           // [2M] Lagrangian force scratch
+  double* U = nullptr;           // [2M] marker velocity / next positions scratch
+  std::vector<double> X_host;    // interleaved copy of X^n (for the advection output)
   // kernel support per (component c, marker a): index c * M + a
   int* sup_i0 = nullptr;         // first face index along x (may be negative / >= N)
   int* sup_j0 = nullptr;
@@ -200,6 +204,10 @@ inline int round8(int n) { return (n + 7) & ~7; }
 // ib_system.cu
 void build_markers_and_ee(ib_system* s, const double* X_interleaved, const double* omega_host,
                           cudaStream_t st);
+void ib_force_launch(const ib_system* s, double* F, cudaStream_t st);
+void ib_spread_launch(const ib_system* s, const double* F, double* f, int rhs, const double* u_prev,
+                      const double* f_body, cudaStream_t st);
+void ib_interp_launch(const ib_system* s, const double* u, double* U, double dt, cudaStream_t st);
 void ee_compute_window(EECsr& ee, int N, int* d_scratch, cudaStream_t st);
 
 // stencil.cu: operators of one level (finest level uses the system's E_E)
@@ -226,6 +234,8 @@ void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_collect(cav_hierarchy* H, long long upto = -1);
 void vcycle_release(cav_hierarchy* H);
 void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st);
+void vcycle_prepare(cav_hierarchy* H);
+void krylov_reserve(cav_hierarchy* H, int maxit, int64_t n);
 void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
 
 // reductions (reduce.cu)

@@ -895,6 +895,10 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
       if (!lv.coarsest) autotune_level(H, lv, st);
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   check_status(H, st, "autotune");
+  // capture both V-cycle graph instances now, so no solve pays for it
+  vcycle_prepare(H);
+  if (H->desc.krylov_capacity > 0)
+    krylov_reserve(H, H->desc.krylov_capacity, 3LL * H->levels[0].N * H->levels[0].N);
 }
 
 }  // namespace cav

@@ -750,6 +750,11 @@ void vcycle(const cav_hierarchy* Hc, const double* r, double* z, cudaStream_t st
   }
 }
 
+void vcycle_prepare(cav_hierarchy* H) {
+  vcycle_capture(H, 0);
+  vcycle_capture(H, 1);
+}
+
 void vcycle_release(cav_hierarchy* H) {
   for (int g = 0; g < 2; ++g) {
     if (H->vc_exec[g]) cudaGraphExecDestroy(H->vc_exec[g]);

@@ -1,0 +1,176 @@
+"""Time-stepped solves of the reduced IB system with a learned initial guess.
+
+Each step n builds S^n, J^n and E_E at the markers' configuration X^n, rebuilds the CAV
+hierarchy, forms the right-hand side of Eq. (Eul_schur) for the semi-implicit step
+(Eq. im_disc_mom without convection), solves with CAV-preconditioned FGMRES to a relative
+residual of rtol (relative to ||b||), and advances the markers by Eq. (im_disc_advec).
+The initial guess is either the previous step's solution or the prediction of a small CNN
+(library's ibnet) from the previous three steps' solutions and spread Lagrangian forces.
+Every numerical step runs in the CUDA library; this module only sequences calls and moves
+buffers.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import replace
+
+import numpy as np
+
+from . import api
+
+
+class TimeSeries:
+    """Run the time stepping, keeping every step's solution and spread force on the device."""
+
+    def __init__(self, rec, forcing, nu=2, alpha=0.85, precision="fp32", rtol=1e-10, maxit=150,
+                 autotune=False):
+        import torch
+        self.torch = torch
+        self.rec0 = rec
+        self.forcing = forcing
+        self.kw = dict(nu_pre=nu, nu_post=nu, alpha=alpha, precision=precision, autotune=autotune,
+                       krylov_capacity=maxit)
+        self.rtol, self.maxit = rtol, maxit
+        self.N = rec.N
+        self.n = 3 * rec.N * rec.N
+        self.X = np.array(rec.X, dtype=np.float64)
+        self.x_hist = []   # solutions x^1, x^2, ... (device, float64, 3N^2)
+        self.f_hist = []   # spread forces f^0, f^1, ... (device, float64, 2N^2)
+        self.records = []  # per step: iterations, solve ms, converged, which guess
+        x0 = torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        self.x_hist.append(x0)          # x^0 = 0 (fluid at rest)
+
+    def _system(self):
+        rec = replace(self.rec0, X=self.X.copy())
+        return api.ib_setup(rec)
+
+    def step(self, guesses=(("previous", None),)):
+        """One time step.  guesses: (label, fn[, precision]) entries; fn(self) returns an initial
+        guess (device vector) once this step's force is stored, or fn is None for the previous
+        solution x^n; precision (default: the series') selects the stored-inverse precision of
+        the hierarchy used for that solve.  The same system is solved from every entry; the
+        first one's solution advances the series, the others are for comparison.  Returns the
+        list of (label, info, ms); ms covers the solve only (hierarchies are rebuilt per step)."""
+        torch = self.torch
+        n_step = len(self.x_hist) - 1
+        sysm = self._system()
+        hier = {}
+        N = self.N
+        F = torch.empty(2 * self.rec0.M, dtype=torch.float64, device="cuda")
+        api.ib_force(sysm, F)
+        f = torch.empty(2 * N * N, dtype=torch.float64, device="cuda")
+        api.ib_spread(sysm, F, f)
+        self.f_hist.append(f)
+        fb = torch.from_numpy(self.forcing(N, n_step * self.rec0.dt)).cuda()
+        b = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        api.ib_step_rhs(sysm, self.x_hist[-1], fb, b)
+        out = []
+        x_main = None
+        for entry in guesses:
+            label, fn = entry[0], entry[1]
+            prec = entry[2] if len(entry) > 2 else self.kw["precision"]
+            if prec not in hier:
+                hier[prec] = api.cav_setup(sysm, **dict(self.kw, precision=prec))
+            h = hier[prec]
+            x = (self.x_hist[-1] if fn is None else fn(self)).clone()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            info = api.fgmres_solve(sysm, h, b, x, rtol=self.rtol, maxit=self.maxit, history=True)
+            info["r0"] = float(info["history"][0])  # ||b - K x_guess|| / ||b||
+            ev1.record()
+            torch.cuda.synchronize()
+            out.append((label, info, ev0.elapsed_time(ev1)))
+            if x_main is None:
+                x_main = x
+        self.x_hist.append(x_main)
+        self.X = api.ib_advect(sysm, x_main)
+        self.records.append(out)
+        for h in hier.values():
+            h.close()
+        sysm.close()
+        return out
+
+
+class LearnedGuess:
+    """The CNN and its normalisation, trained on a TimeSeries' stored steps."""
+
+    def __init__(self, N, hidden=32, n_hidden=3, seed=7):
+        import torch
+        self.torch = torch
+        self.N = N
+        self.net = api.IBNet(15, hidden, n_hidden, 3, seed)
+        self.in_scale = None
+        self.out_scale = None
+
+    def fit_scales(self, ts: TimeSeries, upto: int):
+        """Per-channel RMS of the training range (host statistics of a few sampled steps;
+        upto = number of completed steps, so x^{i+1} and f^i exist for i < upto)."""
+        N = self.N
+        NN = N * N
+        idx = np.linspace(2, upto - 1, num=min(16, max(1, upto - 2)), dtype=int)
+        xs = np.stack([ts.x_hist[i].cpu().numpy() for i in idx])
+        fs = np.stack([ts.f_hist[i].cpu().numpy() for i in idx])
+        dx = np.stack([(ts.x_hist[i + 1] - ts.x_hist[i]).cpu().numpy() for i in idx])
+        d2x = np.stack([(ts.x_hist[i + 1] - 2 * ts.x_hist[i] + ts.x_hist[i - 1]).cpu().numpy() for i in idx])
+        rms = lambda a: float(np.sqrt(np.mean(a * a))) or 1.0  # noqa: E731
+        dfs = np.stack([(ts.f_hist[i] - ts.f_hist[i - 1]).cpu().numpy() for i in idx])
+        fields_x = [rms(xs[:, k * NN:(k + 1) * NN]) for k in range(3)]
+        fields_f = [rms(fs[:, k * NN:(k + 1) * NN]) for k in range(2)]
+        incr_x = [rms(dx[:, k * NN:(k + 1) * NN]) for k in range(3)]
+        incr_f = [rms(dfs[:, k * NN:(k + 1) * NN]) for k in range(2)]
+        # channel groups: increments (two steps), then the current state
+        self.in_scale = (incr_x + incr_f) * 2 + fields_x + fields_f
+        # the network predicts the correction to the linear extrapolation 2 x^n - x^{n-1}
+        self.out_scale = [rms(d2x[:, k * NN:(k + 1) * NN]) for k in range(3)]
+
+    def _pack(self, ts, i, out):
+        # inputs from steps i-2, i-1, i (solutions x^{i-2..i}, forces f^{i-2..i}); target x^{i+1} - x^i
+        api.ibnet_pack_input(self.N, [ts.x_hist[i - 2], ts.x_hist[i - 1], ts.x_hist[i]],
+                             [ts.f_hist[i - 2], ts.f_hist[i - 1], ts.f_hist[i]], self.in_scale, out)
+
+    def train(self, ts: TimeSeries, upto: int, iters=1500, batch=16, lr=1e-3, seed=11):
+        torch = self.torch
+        N = self.N
+        NN = N * N
+        samples = np.arange(2, upto)          # x^{i+1} must exist: i + 1 <= upto
+        xin = torch.empty(batch * 15 * NN, dtype=torch.float32, device="cuda")
+        tgt = torch.empty(batch * 3 * NN, dtype=torch.float32, device="cuda")
+        rng = np.random.default_rng(seed)
+        losses = []
+        t0 = time.perf_counter()
+        for it in range(iters):
+            pick = rng.choice(samples, batch, replace=len(samples) < batch)
+            for s, i in enumerate(pick):
+                self._pack(ts, int(i), xin[s * 15 * NN:(s + 1) * 15 * NN])
+                api.ibnet_pack_target(N, ts.x_hist[int(i) + 1], ts.x_hist[int(i)], self.out_scale,
+                                      tgt[s * 3 * NN:(s + 1) * 3 * NN], x_prev2=ts.x_hist[int(i) - 1])
+            step_lr = lr * (0.5 * (1 + math.cos(math.pi * it / iters)) * 0.9 + 0.1)
+            want = (it % 50 == 0) or it == iters - 1
+            loss = self.net.train_step(xin, tgt, batch, N, step_lr, want_loss=want)
+            if want:
+                losses.append((it, loss))
+        torch.cuda.synchronize()
+        return {"losses": losses, "train_s": time.perf_counter() - t0}
+
+    def predict(self, ts: TimeSeries):
+        """Initial guess for the next step from the last three stored steps."""
+        torch = self.torch
+        N = self.N
+        i = len(ts.x_hist) - 1
+        xin = torch.empty(15 * N * N, dtype=torch.float32, device="cuda")
+        self._pack(ts, i, xin)
+        d = torch.empty(3 * N * N, dtype=torch.float32, device="cuda")
+        self.net.forward(xin, d, 1, N)
+        g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
+        api.ibnet_apply_delta(N, ts.x_hist[i], d, self.out_scale, g, x_prev2=ts.x_hist[i - 1])
+        return g
+
+    def extrapolate(self, ts: TimeSeries):
+        """The baseline without the network: 2 x^n - x^{n-1}."""
+        torch = self.torch
+        N = self.N
+        i = len(ts.x_hist) - 1
+        g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
+        api.ibnet_apply_delta(N, ts.x_hist[i], None, self.out_scale, g, x_prev2=ts.x_hist[i - 1])
+        return g

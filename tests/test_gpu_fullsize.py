@@ -1,6 +1,7 @@
 """Parity at the full bench and stress sizes, in the launch configuration the bench uses:
-the elliptic membrane at N=256 (4N markers, kappa_s=1e4) and the stretched beam at N=512
-(2048 markers, kappa_b=1e3, kappa_s=1e5).
+the elliptic membrane at N=256 (4N markers, kappa_s=1e4), the membrane's stiffness sweep at
+N=128 (kappa_s = 1e2 and 1e6) and the stretched beam at N=512 (2048 markers, kappa_b=1e3,
+kappa_s=1e5).
 
 E_E patterns and CAV patch sets are compared bit for bit on every level (the oracle builds
 them in seconds without factorising).  The sweep is checked on sampled velocity unknowns the
@@ -22,6 +23,8 @@ pytestmark = pytest.mark.gpu
 
 ALPHA = 0.85
 CASES = {"membrane256": (lambda: W.config2(256, 1e4), "fp32"),
+         "membrane128_k1e2": (lambda: W.config2(128, 1e2), "fp32"),
+         "membrane128_k1e6": (lambda: W.config2(128, 1e6), "fp32"),
          "beam512": (lambda: W.config3(), "bf16")}
 
 

@@ -45,6 +45,22 @@ NCU_TRAFFIC = {
 }
 
 
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The largest per-rank timed span (all ranks wait for the slowest): an all-reduce MAX
+    over the process group, or the value itself without one."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, span_s: float) -> float:
+    """Units all ranks processed divided by the slowest rank's timed span."""
+    return world * units_per_rank / span_s
+
+
 def workload(seed_offset: int = 0):
     rec = W.config2(256, 1e4)
     if seed_offset:
@@ -235,12 +251,8 @@ def run_batch(args, api, torch, dist, rank, world, local):
         times.append(time.perf_counter() - t)
     launches = api.ib_launch_count() - launches0
     clk = clocks.stop()
-    total = sum(times)
-    if dist:
-        tt = torch.tensor([total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
-    value = world * len(recs) * args.steps / total
+    total = max_over_ranks(sum(times), dist, dev)
+    value = whole_job_rate(len(recs) * args.steps, world, total)
     its = [i["iters"] for i in last]
     conv = [i["converged"] for i in last]
     variants = {}
@@ -264,6 +276,60 @@ def run_batch(args, api, torch, dist, rank, world, local):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_beam512(args, api, torch, rank):
+    """The stretched beam on a 512 x 512 grid (2048 markers, kappa_b 1e3, kappa_s 1e5): finest-level
+    sweep and patch-apply bandwidth with BF16 and with FP64 inverses, and the FGMRES attempt (the
+    system is beyond FP64's reach at 1e-10; reported, not claimed)."""
+    if rank:
+        return 0
+    rec = W.config3()
+    dev = torch.device("cuda", 0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    sysm = api.ib_setup(rec)
+    b = torch.from_numpy(rec.rhs()).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    peak, kind = peaks()
+    res = {}
+    for prec in ("bf16", "fp64"):
+        t0 = time.perf_counter()
+        h = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision=prec, autotune=True)
+        setup_s = time.perf_counter() - t0
+        li = api.cav_get_level_info(h, 0)
+        s_b = {"fp64": 8, "bf16": 2}[prec]
+        alg = li["enlarged_sum_n2"] * s_b + li["enlarged_sum_n"] * 36
+        w = torch.zeros_like(b)
+        for _ in range(3):
+            api.cav_sweep(h, 0, b, w)
+        api.cav_profile(h, True)
+        sw = []
+        for _ in range(10):
+            flush.zero_()
+            s0, s1 = ev(), ev()
+            s0.record()
+            api.cav_sweep(h, 0, b, w)
+            s1.record()
+            torch.cuda.synchronize()
+            sw.append(s0.elapsed_time(s1))
+        n_apply, apply_ms = api.cav_profile_read(h)
+        api.cav_profile(h, False)
+        x = torch.zeros_like(b)
+        t1 = time.perf_counter()
+        info = api.fgmres_solve(sysm, h, b, x, rtol=1e-10, maxit=60, history=False)
+        solve_s = time.perf_counter() - t1
+        achieved = alg / (apply_ms / n_apply * 1e-3) / 1e9
+        res[prec] = {"setup_s": setup_s, "inverse_bytes": li["inverse_bytes"], "enlarged_patches": li["n_enlarged"],
+                     "max_n": li["max_n"], "apply_variant": li["apply_variant"],
+                     "apply_us": 1e3 * apply_ms / n_apply, "apply_gbs": achieved, "apply_frac": achieved / peak,
+                     "sweep_ms": statistics.median(sw),
+                     "fgmres_60": {"iters": info["iters"], "converged": info["converged"],
+                                   "relres_true": info["relres_true"], "seconds": solve_s}}
+        h.close()
+    line = {"workload": "stretched beam N=512, 2048 markers, kappa_b 1e3, kappa_s 1e5 (config 3)",
+            "peak_gbs": peak, "peak_kind": kind, "results": res}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -324,7 +390,7 @@ def main():
     ap.add_argument("--nu", type=int, default=DEFAULT_NU)
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="membrane256", choices=["membrane256", "batch64", "learned"])
+    ap.add_argument("--workload", default="membrane256", choices=["membrane256", "batch64", "learned", "beam512"])
     ap.add_argument("--grid", type=int, default=64, help="grid for --workload learned")
     ap.add_argument("--nsteps", type=int, default=2000, help="time steps for --workload learned")
     ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
@@ -351,6 +417,8 @@ def main():
         return run_batch(args, api, torch, dist, rank, world, local)
     if args.workload == "learned":
         return run_learned(args, api, torch, rank, world)
+    if args.workload == "beam512":
+        return run_beam512(args, api, torch, rank)
 
     rec = workload(rank)
     n = 3 * rec.N * rec.N
@@ -399,12 +467,32 @@ def main():
     n_apply, apply_ms = api.cav_profile_read(hier)
     api.cav_profile(hier, False)
     clk = clocks.stop()
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dist, dev)
+    value = whole_job_rate(args.steps, world, total_ms / 1e3)
+
+    # one whole finest-level sweep (residual, patch apply, scatter, mean removal) through
+    # cav_sweep; algorithmic bytes: the enlarged inverses and their per-slot data, the residual
+    # pass (read w, b; write r), the scatter pass (read w, r; write w), the E_E rows, the
+    # transpose incidence and the mean removal (read and write p)
+    li0 = api.cav_get_level_info(hier, 0)
+    NN = rec.N * rec.N
+    s_b = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
+    sweep_bytes = (li0["enlarged_sum_n2"] * s_b + li0["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8 + 4 + 8)
+                   + 3 * NN * 8 * 3 + 3 * NN * 8 * 3 + li0["ee_nnz"] * 12 + 3 * NN * 8 + 2 * NN * 8)
+    ws = torch.zeros_like(b)
+    for _ in range(3):
+        api.cav_sweep(hier, 0, b, ws)
+    sw_times = []
+    for _ in range(10):
+        flush.zero_()
+        s0, s1 = ev(), ev()
+        s0.record()
+        api.cav_sweep(hier, 0, b, ws)
+        s1.record()
+        torch.cuda.synchronize()
+        sw_times.append(s0.elapsed_time(s1))
+    sweep_ms = statistics.median(sw_times)
+    sweep_gbs = sweep_bytes / (sweep_ms * 1e-3) / 1e9
 
     # the V-cycle alone (graph replay + its two staging copies), to split a solve's time
     zv = torch.empty_like(b)
@@ -473,6 +561,9 @@ def main():
         "plain_fp64": plain,
         "setup_ms": setup_ms,
         "vcycle_ms": vcycle_ms,
+        "sweep": {"level": 0, "ms": sweep_ms, "algorithmic_bytes": sweep_bytes, "gbs": sweep_gbs,
+                  "frac_of_hbm": sweep_gbs / peaks()[0],
+                  "note": "one cav_sweep on the finest level, L2 flushed before each of 10 timed calls"},
         "setup_plus_solve_per_s": world / ((setup_ms + total_ms / args.steps) / 1e3),
         "apply_variant_finest": li["apply_variant"], "apply_variant_us_finest": li["apply_us"],
         "roofline": {"bound": "hbm", "kernel": "k_patch_apply (finest level)", "achieved": achieved,

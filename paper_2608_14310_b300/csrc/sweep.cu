@@ -350,16 +350,18 @@ __device__ inline double std_row(const StdInv& S, int row, const double* __restr
 }
 
 constexpr int TOUCH_WARPS = 8;
+constexpr int TOUCH_LANES = 8;                       // lanes per touched unknown
+constexpr int TOUCH_PER_WARP = 32 / TOUCH_LANES;     // touched unknowns per warp
 
 // Scatter / update in one launch with two block roles.
 //  * Blocks [0, nb_std): a 32 x 8 tile of cells, one thread per cell.  For each unknown of the
 //    cell that no enlarged patch holds, both incident cells (one for a pressure) keep their
 //    standard patch, so count_k is 2 (1) and the correction is the stencil of the shared 5x5
 //    inverse applied to r.
-//  * The remaining blocks: one warp per unknown held by at least one enlarged patch.  The lanes
-//    sum the enlarged patches' corrections at the unknown (fixed lane-strided order, fixed
-//    shuffle tree); lane 0 adds the standard patches of its incident cells that kept their
-//    Vanka patch and divides by the total patch count.
+//  * The remaining blocks: eight lanes per unknown held by at least one enlarged patch (four
+//    unknowns per warp).  The lanes sum the enlarged patches' corrections at the unknown (fixed
+//    lane-strided order, fixed shuffle tree); the group's first lane adds the standard patches
+//    of its incident cells that kept their Vanka patch and divides by the total patch count.
 // Each block writes the partial sum of the new pressures it produced (fixed order); the
 // stencil blocks' partials come first, then the touched blocks'.
 __global__ void __launch_bounds__(256)
@@ -393,14 +395,21 @@ k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __res
     }
     pnew = warp_sum(pnew);
   } else {
-    const int t = ((int)blockIdx.x - nb_std) * TOUCH_WARPS + warp;
+    const int sub = lane / TOUCH_LANES, sl = lane % TOUCH_LANES;
+    const int t = (((int)blockIdx.x - nb_std) * TOUCH_WARPS + warp) * TOUCH_PER_WARP + sub;
+    double s = 0.0;
+    int k = -1;
+    int64_t q0 = 0, q1 = 0;
     if (t < n_touched) {
-      const int k = touched[t];
-      const int64_t q0 = inc_off[k], q1 = inc_off[k + 1];
-      double s = 0.0;
-      for (int64_t q = q0 + lane; q < q1; q += 32) s += delta[inc_slot[q]];
-      s = warp_sum(s);
-      if (lane == 0) {
+      k = touched[t];
+      q0 = inc_off[k];
+      q1 = inc_off[k + 1];
+      for (int64_t q = q0 + sl; q < q1; q += TOUCH_LANES) s += delta[inc_slot[q]];
+    }
+#pragma unroll
+    for (int o = TOUCH_LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (k >= 0) {
+      if (sl == 0) {
         const int comp = k / NN, c = k % NN, i = c % N, j = c / N;
         const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
         int cnt = (int)(q1 - q0);
@@ -419,6 +428,11 @@ k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __res
         if (comp == 2) pnew = nw;
       }
     }
+    // the warp's new pressures: group leaders' values in fixed order
+    double wp = 0.0;
+#pragma unroll
+    for (int g = 0; g < TOUCH_PER_WARP; ++g) wp += __shfl_sync(0xffffffffu, pnew, g * TOUCH_LANES);
+    pnew = wp;
   }
   if (lane == 0) sm[warp] = pnew;
   __syncthreads();
@@ -631,7 +645,7 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   for (int q = 0; q < 25; ++q) S.m[q] = lv.std_inv[q];
   const int gx = div_up(lv.N, 32), gy = div_up(lv.N, 8);
   const int nb_std = gx * gy;
-  const int nb_touch = div_up(lv.n_touched, TOUCH_WARPS);
+  const int nb_touch = div_up(lv.n_touched, TOUCH_WARPS * TOUCH_PER_WARP);
   k_update<<<nb_std + nb_touch, 256, 0, st>>>(lv.N, H->desc.alpha, S, nb_std, gx, lv.inc_off, lv.n_touched,
                                               lv.touched, lv.cell_big, lv.inc_slot, delta_buf, r, w,
                                               w_is_zero ? 1 : 0, partial_buf);

@@ -17,17 +17,92 @@ namespace cav {
 
 static constexpr int FG_THREADS = 256;
 
-// partial[i * nb + bx] = block bx's share of <V_i, w> for i < kcount
-__global__ void k_multi_dot(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ w,
-                            double* partial) {
-  __shared__ double sm[FG_THREADS / 32];
-  const int i = blockIdx.y;
-  const double* v = V + (int64_t)i * n;
-  double s = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    s += v[e] * w[e];
-  s = block_sum(s, sm);
-  if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = s;
+// The Arnoldi kernels are bound by the FP64 pipe as much as by HBM (on this part one FP64
+// FMA per 8-byte element already asks for more FP64 issue than the SMs have at full memory
+// bandwidth), so they keep FP64 work other than the products to a minimum.  A block owns a
+// chunk of the vectors; a thread owns the elements tid, tid + 256, ... of that chunk
+// (coalesced).
+
+// Inner products: 4 elements per thread, 8 vectors per block.
+constexpr int DOT_PER_THREAD = 4, DOT_CHUNK = FG_THREADS * DOT_PER_THREAD, DOT_GROUP = 8;
+// Combinations: 2 elements per thread (more blocks, more loads in flight per SM).
+constexpr int CMB_PER_THREAD = 2, CMB_CHUNK = FG_THREADS * CMB_PER_THREAD;
+
+static int dot_blocks(int64_t n) { return (int)((n + DOT_CHUNK - 1) / DOT_CHUNK); }
+static int cmb_blocks(int64_t n) { return (int)((n + CMB_CHUNK - 1) / CMB_CHUNK); }
+
+// Warp reduction of 8 values per lane in 9 additions (not 8 x 5): three exchange steps halve
+// the number of values a lane carries, two plain steps finish.  Lane L with L % 4 == 0 ends
+// holding the warp sum of value L / 4.  The pattern is fixed, so the result is reproducible.
+__device__ inline double warp_sum8_transposed(double* v) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double send = b4 ? v[q] : v[q + 4], keep = b4 ? v[q + 4] : v[q];
+    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double send = b3 ? v[q] : v[q + 2], keep = b3 ? v[q + 2] : v[q];
+    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const double send = b2 ? v[0] : v[1], keep = b2 ? v[1] : v[0];
+  double t = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
+// partial[i * gridDim.x + bx] = chunk bx's share of <V_i, w> for i < kcount.  Block (bx, g)
+// takes vectors 8g .. 8g+7, so w is read once per eight vectors; per vector the chunk's sum
+// is a fixed per-warp tree, then the eight warp sums in warp order.
+__global__ void __launch_bounds__(FG_THREADS)
+k_multi_dot(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ w,
+            double* __restrict__ partial) {
+  __shared__ double sm[DOT_GROUP][FG_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * DOT_CHUNK + threadIdx.x;
+  double wr[DOT_PER_THREAD];
+#pragma unroll
+  for (int j = 0; j < DOT_PER_THREAD; ++j) {
+    const int64_t e = base + j * FG_THREADS;
+    wr[j] = (e < n) ? w[e] : 0.0;
+  }
+  const int i0 = blockIdx.y * DOT_GROUP;
+  double s[DOT_GROUP];
+  if (i0 + DOT_GROUP <= kcount && base + (DOT_PER_THREAD - 1) * FG_THREADS < n) {
+#pragma unroll
+    for (int v = 0; v < DOT_GROUP; ++v) {
+      const double* vi = V + (int64_t)(i0 + v) * n + base;
+      double a = 0.0;
+#pragma unroll
+      for (int j = 0; j < DOT_PER_THREAD; ++j) a += vi[j * FG_THREADS] * wr[j];
+      s[v] = a;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < DOT_GROUP; ++v) {
+      s[v] = 0.0;
+      if (i0 + v < kcount) {
+        const double* vi = V + (int64_t)(i0 + v) * n;
+#pragma unroll
+        for (int j = 0; j < DOT_PER_THREAD; ++j) {
+          const int64_t e = base + j * FG_THREADS;
+          if (e < n) s[v] += vi[e] * wr[j];
+        }
+      }
+    }
+  }
+  const double t = warp_sum8_transposed(s);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((lane & 3) == 0) sm[lane >> 2][warp] = t;
+  __syncthreads();
+  if (threadIdx.x < DOT_GROUP && i0 + (int)threadIdx.x < kcount) {
+    double u = 0.0;
+#pragma unroll
+    for (int q = 0; q < FG_THREADS / 32; ++q) u += sm[threadIdx.x][q];
+    partial[(int64_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = u;
+  }
 }
 
 // out[i] = sum_b partial[i * nb + b] (fixed order); add_to (nullable) += out
@@ -43,23 +118,50 @@ __global__ void k_finalize(const double* __restrict__ partial, int nb, double* o
   }
 }
 
-// w -= sum_{i < kcount} h[i] V_i
-__global__ void k_sub_multi(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ h,
-                            double* __restrict__ w) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < kcount; ++i) s += h[i] * V[(int64_t)i * n + e];
-    w[e] -= s;
+// SIGN = -1: w -= sum_{i < kcount} c[i] V_i;  SIGN = +1: w += sum_{i < kcount} c[i] V_i.
+// Per element the sum runs over i in ascending order.  sq_partial (nullable) receives the
+// chunk's share of ||w_new||^2 (block_sum order).
+template <int SIGN>
+__global__ void __launch_bounds__(FG_THREADS)
+k_combine(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ c,
+          double* __restrict__ w, double* __restrict__ sq_partial) {
+  __shared__ double sm[FG_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * CMB_CHUNK + threadIdx.x;
+  double acc[CMB_PER_THREAD];
+#pragma unroll
+  for (int j = 0; j < CMB_PER_THREAD; ++j) acc[j] = 0.0;
+  if (base + (CMB_PER_THREAD - 1) * FG_THREADS < n) {
+#pragma unroll 4
+    for (int i = 0; i < kcount; ++i) {
+      const double ci = c[i];
+      const double* vi = V + (int64_t)i * n + base;
+#pragma unroll
+      for (int j = 0; j < CMB_PER_THREAD; ++j) acc[j] += ci * vi[j * FG_THREADS];
+    }
+  } else {
+    for (int i = 0; i < kcount; ++i) {
+      const double ci = c[i];
+      const double* vi = V + (int64_t)i * n;
+#pragma unroll
+      for (int j = 0; j < CMB_PER_THREAD; ++j) {
+        const int64_t e = base + j * FG_THREADS;
+        if (e < n) acc[j] += ci * vi[e];
+      }
+    }
   }
-}
-
-// x += sum_{i < kcount} y[i] Z_i
-__global__ void k_add_multi(const double* __restrict__ Z, int64_t n, int kcount, const double* __restrict__ y,
-                            double* __restrict__ x) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < kcount; ++i) s += y[i] * Z[(int64_t)i * n + e];
-    x[e] += s;
+  double sq = 0.0;
+#pragma unroll
+  for (int j = 0; j < CMB_PER_THREAD; ++j) {
+    const int64_t e = base + j * FG_THREADS;
+    if (e < n) {
+      const double wn = (SIGN < 0) ? w[e] - acc[j] : w[e] + acc[j];
+      w[e] = wn;
+      sq += wn * wn;
+    }
+  }
+  if (sq_partial) {
+    sq = block_sum(sq, sm);
+    if (threadIdx.x == 0) sq_partial[blockIdx.x] = sq;
   }
 }
 
@@ -96,28 +198,54 @@ __global__ void k_init_beta(double* S, FgLayout L) {
   S[L.g] = beta;
 }
 
+// Hessenberg column k: apply the k earlier rotations, form rotation k, update g (Sec. 5).
+// The rotations are a serial chain; the column and the rotation pairs are staged in shared
+// memory first (all threads), so the chain runs on shared-memory latency, not L2 latency.
+constexpr int GIVENS_SMEM_MAX = 1024;
 __global__ void k_givens(double* S, FgLayout L, int k) {
-  double* Hk = S + L.H + (int64_t)k * (L.maxit + 1);
-  double* cs = S + L.cs;
-  double* sn = S + L.sn;
+  __shared__ double sh[3 * GIVENS_SMEM_MAX];
+  double* Hg = S + L.H + (int64_t)k * (L.maxit + 1);
+  double* csg = S + L.cs;
+  double* sng = S + L.sn;
   double* g = S + L.g;
   double* misc = S + L.misc;
-  const double vnorm = sqrt(misc[2]);
-  Hk[k + 1] = vnorm;
-  for (int i = 0; i < k; ++i) {
-    const double t = cs[i] * Hk[i] + sn[i] * Hk[i + 1];
-    Hk[i + 1] = -sn[i] * Hk[i] + cs[i] * Hk[i + 1];
-    Hk[i] = t;
+  const bool staged = k + 2 <= GIVENS_SMEM_MAX;
+  double* Hk = staged ? sh : Hg;
+  double* cs = staged ? sh + GIVENS_SMEM_MAX : csg;
+  double* sn = staged ? sh + 2 * GIVENS_SMEM_MAX : sng;
+  if (staged) {
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+      Hk[i] = Hg[i];
+      if (i < k) {
+        cs[i] = csg[i];
+        sn[i] = sng[i];
+      }
+    }
   }
-  const double d = hypot(Hk[k], Hk[k + 1]);
-  cs[k] = (d != 0.0) ? Hk[k] / d : 1.0;
-  sn[k] = (d != 0.0) ? Hk[k + 1] / d : 0.0;
-  Hk[k] = d;
-  Hk[k + 1] = 0.0;
-  g[k + 1] = -sn[k] * g[k];
-  g[k] = cs[k] * g[k];
-  misc[4] = fabs(g[k + 1]);
-  misc[5] = (vnorm > 0.0) ? 1.0 / vnorm : 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double vnorm = sqrt(misc[2]);
+    Hk[k + 1] = vnorm;
+    for (int i = 0; i < k; ++i) {
+      const double t = cs[i] * Hk[i] + sn[i] * Hk[i + 1];
+      Hk[i + 1] = -sn[i] * Hk[i] + cs[i] * Hk[i + 1];
+      Hk[i] = t;
+    }
+    const double d = hypot(Hk[k], Hk[k + 1]);
+    const double c = (d != 0.0) ? Hk[k] / d : 1.0;
+    const double sk = (d != 0.0) ? Hk[k + 1] / d : 0.0;
+    csg[k] = c;
+    sng[k] = sk;
+    Hk[k] = d;
+    Hk[k + 1] = 0.0;
+    g[k + 1] = -sk * g[k];
+    g[k] = c * g[k];
+    misc[4] = fabs(g[k + 1]);
+    misc[5] = (vnorm > 0.0) ? 1.0 / vnorm : 0.0;
+  }
+  __syncthreads();
+  if (staged)
+    for (int i = threadIdx.x; i <= k + 1; i += blockDim.x) Hg[i] = Hk[i];
 }
 
 __global__ void k_trisolve(double* S, FgLayout L, int k) {
@@ -146,7 +274,10 @@ static void ensure_workspace(cav_hierarchy* H, int maxit, int64_t n) {
   H->Z = H->ws_arena.alloc<double>((size_t)maxit * n);
   FgLayout L(maxit);
   H->dev_scalars = H->ws_arena.alloc<double>(L.total);
-  H->red_partial = H->ws_arena.alloc<double>((size_t)(maxit + 2) * reduce_blocks(n));
+  int nbmax = reduce_blocks(n);
+  if (dot_blocks(n) > nbmax) nbmax = dot_blocks(n);
+  if (cmb_blocks(n) > nbmax) nbmax = cmb_blocks(n);
+  H->red_partial = H->ws_arena.alloc<double>((size_t)(maxit + 2) * nbmax);
   H->io_b = H->ws_arena.alloc<double>(n);
   H->io_x = H->ws_arena.alloc<double>(n);
   if (!H->fg_ev[0]) {
@@ -161,7 +292,7 @@ void krylov_reserve(cav_hierarchy* H, int maxit, int64_t n) { ensure_workspace(H
 
 static void dot_to(const cav_hierarchy* H, const double* a, const double* b, int64_t n, double* out,
                    cudaStream_t st) {
-  const int nb = reduce_blocks(n);
+  const int nb = dot_blocks(n);
   k_multi_dot<<<dim3(nb, 1), FG_THREADS, 0, st>>>(a, n, 1, b, H->red_partial);
   CAV_CHECK_LAUNCH();
   k_finalize<<<1, FG_THREADS, 0, st>>>(H->red_partial, nb, out, nullptr);
@@ -189,7 +320,7 @@ struct FgState {
   int64_t n = 0;
   FgLayout L{1};
   LevelOps op{};
-  int nb = 0, vb = 0;
+  int nb = 0, cb = 0, nbmax = 0, vb = 0;
   double ref = 0, beta = 0, est = 0;
   int k_done = 0, pending = -1;
   bool converged = false, active = false;
@@ -213,7 +344,10 @@ static void fg_start(FgState& s) {
   double* S = H->dev_scalars;
   CAV_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * s.L.total, s.st));
   s.op = LevelOps{l0.N, l0.h, l0.rho_dt, l0.mu, l0.dt, &l0.ee};
-  s.nb = reduce_blocks(s.n);
+  s.nb = dot_blocks(s.n);
+  s.cb = cmb_blocks(s.n);
+  s.nbmax = s.nb > s.cb ? s.nb : s.cb;
+  if (reduce_blocks(s.n) > s.nbmax) s.nbmax = reduce_blocks(s.n);
   s.vb = vec_blocks(s.n);
   double* misc = S + s.L.misc;
   launch_apply(s.op, s.x, s.b, H->V, 0, s.st);  // r0 -> V_0
@@ -255,16 +389,19 @@ static void fg_issue(FgState& s, int k) {
   double* w = H->V + (int64_t)(k + 1) * n;
   vcycle(H, vk, zk, s.st);
   launch_apply(s.op, zk, nullptr, w, 1, s.st);
+  // the second pass's update also yields the chunk sums of ||w||^2 (after the dot partials)
+  double* sq_partial = H->red_partial + (int64_t)(maxit + 1) * s.nbmax;
   for (int pass = 0; pass < 2; ++pass) {
-    k_multi_dot<<<dim3(s.nb, k + 1), FG_THREADS, 0, s.st>>>(H->V, n, k + 1, w, H->red_partial);
+    k_multi_dot<<<dim3(s.nb, div_up(k + 1, DOT_GROUP)), FG_THREADS, 0, s.st>>>(H->V, n, k + 1, w, H->red_partial);
     CAV_CHECK_LAUNCH();
     k_finalize<<<k + 1, FG_THREADS, 0, s.st>>>(H->red_partial, s.nb, S + s.L.h, S + s.L.H + (int64_t)k * (maxit + 1));
     CAV_CHECK_LAUNCH();
-    k_sub_multi<<<s.vb, FG_THREADS, 0, s.st>>>(H->V, n, k + 1, S + s.L.h, w);
+    k_combine<-1><<<s.cb, FG_THREADS, 0, s.st>>>(H->V, n, k + 1, S + s.L.h, w, pass == 1 ? sq_partial : nullptr);
     CAV_CHECK_LAUNCH();
   }
-  dot_to(H, w, w, n, misc + 2, s.st);
-  k_givens<<<1, 1, 0, s.st>>>(S, s.L, k);
+  k_finalize<<<1, FG_THREADS, 0, s.st>>>(sq_partial, s.cb, misc + 2, nullptr);
+  CAV_CHECK_LAUNCH();
+  k_givens<<<1, 128, 0, s.st>>>(S, s.L, k);
   CAV_CHECK_LAUNCH();
   k_scale<<<s.vb, FG_THREADS, 0, s.st>>>(w, n, misc + 5, w);
   CAV_CHECK_LAUNCH();
@@ -314,7 +451,7 @@ static void fg_finish(FgState& s) {
   if (s.k_done > 0) {
     k_trisolve<<<1, 1, 0, s.st>>>(S, s.L, s.k_done);
     CAV_CHECK_LAUNCH();
-    k_add_multi<<<s.vb, FG_THREADS, 0, s.st>>>(H->Z, s.n, s.k_done, S + s.L.y, s.x);
+    k_combine<1><<<s.cb, FG_THREADS, 0, s.st>>>(H->Z, s.n, s.k_done, S + s.L.y, s.x, nullptr);
     CAV_CHECK_LAUNCH();
   }
   const Level& l0 = H->levels[0];

@@ -15,73 +15,11 @@
 
 #include "internal.cuh"
 #include "device_util.cuh"
+#include "level_math.cuh"
 
 namespace cav {
 
 // ------------------------------------------------------------------ 2. patch apply
-
-template <typename T>
-struct VecLoad;
-template <>
-struct VecLoad<double> {
-  static constexpr int V = 2;
-  typedef double acc_t;
-  __device__ static void load(const double* p, acc_t* out) {
-    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    out[0] = v.x;
-    out[1] = v.y;
-  }
-  __device__ static void load_shared(const double* p, acc_t* out) {
-    const double2 v = *reinterpret_cast<const double2*>(p);
-    out[0] = v.x;
-    out[1] = v.y;
-  }
-};
-template <>
-struct VecLoad<float> {
-  static constexpr int V = 4;
-  typedef float acc_t;
-  __device__ static void load(const float* p, acc_t* out) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    out[0] = v.x;
-    out[1] = v.y;
-    out[2] = v.z;
-    out[3] = v.w;
-  }
-  __device__ static void load_shared(const float* p, acc_t* out) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    out[0] = v.x;
-    out[1] = v.y;
-    out[2] = v.z;
-    out[3] = v.w;
-  }
-};
-template <>
-struct VecLoad<__nv_bfloat16> {
-  static constexpr int V = 8;
-  typedef float acc_t;
-  __device__ static void unpack(const uint4& v, acc_t* out) {
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 f = __bfloat1622float2(h[q]);
-      out[2 * q] = f.x;
-      out[2 * q + 1] = f.y;
-    }
-  }
-  __device__ static void load(const __nv_bfloat16* p, acc_t* out) {
-    unpack(__ldg(reinterpret_cast<const uint4*>(p)), out);
-  }
-  __device__ static void load_shared(const __nv_bfloat16* p, acc_t* out) {
-    unpack(*reinterpret_cast<const uint4*>(p), out);
-  }
-};
-
-// acc + x * y as one fused multiply-add, so every kernel variant accumulates a patch's
-// columns in the same order with the same rounding (the autotuner's choice cannot change
-// a result bit).
-__device__ inline double mad(double x, double y, double acc) { return fma(x, y, acc); }
-__device__ inline float mad(float x, float y, float acc) { return fmaf(x, y, acc); }
 
 // Fallback for patches too large for the pipelined kernel: one CTA per patch, the scaled
 // residual in shared memory, the column-major inverse (ld = round8(n)) read straight from
@@ -335,23 +273,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
 
 // ------------------------------------------------------------------ 3. scatter / update
 
-struct StdInv {
-  double m[25];
-};
-
-// canonical slots of cell (i, j)'s standard patch: u_ij, u_i+1j, v_ij, v_ij+1, p_ij
-__device__ inline double std_row(const StdInv& S, int row, const double* __restrict__ r, int N, int i, int j) {
-  const int NN = N * N;
-  const int ip = (i + 1 == N) ? 0 : i + 1, jp = (j + 1 == N) ? 0 : j + 1;
-  const double y0 = r[j * N + i], y1 = r[j * N + ip], y2 = r[NN + j * N + i], y3 = r[NN + jp * N + i],
-               y4 = r[2 * NN + j * N + i];
-  const double* m = S.m + 5 * row;
-  return m[0] * y0 + m[1] * y1 + m[2] * y2 + m[3] * y3 + m[4] * y4;
-}
-
 constexpr int TOUCH_WARPS = 8;
-constexpr int TOUCH_LANES = 8;                       // lanes per touched unknown
-constexpr int TOUCH_PER_WARP = 32 / TOUCH_LANES;     // touched unknowns per warp
 
 // Scatter / update in one launch with two block roles.
 //  * Blocks [0, nb_std): a 32 x 8 tile of cells, one thread per cell.  For each unknown of the

@@ -15,9 +15,10 @@ and no blocking, fusion or reordering:
   patches    Vanka, box B(b,o) and CAV patch sets                   (Sec. 3.1, 3.2, Eq. cav_patch_set)
   smoother   local matrices, equilibration, LU, multiplicative and
              weighted additive sweeps                             (Sec. 3.3, Eq. additive_cav_saddle)
+  colouring  classes of mutually independent patches and the
+             multiplicative sweep visiting them class by class     (Sec. 3.3)
   multigrid  RT0 / bilinear transfers, Galerkin E_E, hierarchy,
              coarsest bordered solve, V-cycle                      (Sec. 4)
   fgmres     right-preconditioned flexible GMRES                    (Sec. 5)
-  twogrid    two-grid iteration matrix and its spectrum            (Sec. 5.1, Table 1)
 """
-from . import grid, ib, patches, smoother, multigrid, fgmres  # noqa: F401
+from . import grid, ib, patches, smoother, colouring, multigrid, fgmres  # noqa: F401

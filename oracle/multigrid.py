@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-from . import grid, ib, patches as patchmod, smoother
+from . import colouring, grid, ib, patches as patchmod, smoother
 from .grid import U, V
 
 
@@ -115,6 +115,14 @@ class Level:
     theta: np.ndarray | None = None
     coarse_inverse: np.ndarray | None = None
     KE_csc: sp.csc_matrix | None = None
+    colours: np.ndarray | None = None
+
+
+def level_colours(lev: Level) -> np.ndarray:
+    """Colour classes of the level's patches (computed on first use)."""
+    if lev.colours is None:
+        lev.colours = colouring.greedy_colours(lev.patches, colouring.coupling_pattern(lev.N, lev.pattern))
+    return lev.colours
 
 
 def level_sizes(N: int, coarsest_N: int = 8) -> list[int]:
@@ -179,6 +187,8 @@ def coarse_solve(lev: Level, r: np.ndarray) -> np.ndarray:
 def sweep(lev: Level, w, b, mode: str = "additive", alpha: float = 1.0):
     if mode == "additive":
         return smoother.additive_sweep(lev.KE, lev.solvers, lev.theta, w, b, lev.N, alpha)
+    if mode == "coloured":
+        return colouring.coloured_sweep(lev.KE, lev.solvers, level_colours(lev), w, b, lev.N)
     return smoother.multiplicative_sweep(lev.KE, lev.solvers, w, b, lev.N, lev.inject, lev.KE_csc)
 
 

@@ -46,7 +46,7 @@ typedef enum {
 
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 const char* ib_last_error(void);
-/* ABI version of this header: 1. */
+/* ABI version of this header: 2 (cav_desc.smoother, cav_level_info.n_colours). */
 int ib_abi_version(void);
 /* Number of kernels this library has launched in this process (host-side count). */
 int64_t ib_launch_count(void);
@@ -113,6 +113,21 @@ ib_status ib_advect(const ib_system* sys, const double* u, double* X_next, cudaS
 
 typedef enum { CAV_PATCH_CAV = 0, CAV_PATCH_VANKA = 1 } cav_patch_kind;
 typedef enum { CAV_PREC_FP64 = 0, CAV_PREC_FP32 = 1, CAV_PREC_BF16 = 2 } cav_precision;
+/* Smoother of every level:
+ *   additive  the weighted additive sweep of Eq. additive_cav_saddle (alpha, Theta = 1/count);
+ *   coloured  the multiplicative sweep of Sec. 3.3 with the patches visited class by class:
+ *             the patches are split at set-up into classes whose members share no unknown
+ *             and are not coupled by any entry of K_E (the Stokes stencils plus E_E's
+ *             structural pattern), by first-fit greedy colouring visiting the enlarged
+ *             patches in cell order, then the standard ones; inside a class every patch
+ *             solves its local residual b_p - (K_E w)_p from the current iterate and adds its
+ *             correction (no damping, alpha unused).  Within a class the order is
+ *             immaterial, so the result is the sequential multiplicative sweep in
+ *             class-by-class order.                                                      */
+typedef enum { CAV_SMOOTH_ADDITIVE = 0, CAV_SMOOTH_COLOURED = 1 } cav_smoother;
+/* The coloured smoother with BF16 inverses is rejected (IB_ERR_INVALID): rounding the
+ * equilibrated inverses to 8 significant bits makes the undamped multiplicative sweep
+ * diverge (the FP64 oracle with BF16-rounded inverses diverges the same way). */
 
 typedef struct {
   int32_t kind;        /* cav_patch_kind: CAV (Eq. cav_patch_set) or standard Vanka B(1,0) */
@@ -124,6 +139,11 @@ typedef struct {
                           set-up and keep the fastest (all variants give identical bits)   */
   int32_t krylov_capacity;  /* > 0: reserve FGMRES workspace for this many iterations at
                                set-up (0: on the first solve)                              */
+  int32_t smoother;    /* cav_smoother (ABI 2)                                              */
+  int32_t coloured_levels;  /* coloured smoother: how many levels, from the finest, use it;
+                               the coarser smoothing levels use the additive sweep (0: all)  */
+  int32_t nu_additive; /* coloured smoother: sweeps per side on its additive levels
+                          (0: nu_pre / nu_post)                                             */
 } cav_desc;
 
 typedef struct cav_hierarchy cav_hierarchy;
@@ -143,6 +163,7 @@ typedef struct {
   int32_t is_coarsest;
   int32_t apply_variant;     /* patch-apply kernel variant in use (0 unless autotuned)        */
   float apply_us[5];         /* autotuner's time per launch of each variant (0: not timed)    */
+  int32_t n_colours;         /* colour classes of the coloured smoother (0 for additive) (ABI 2) */
 } cav_level_info;
 
 /* Builds the level hierarchy, Galerkin E_E^(l-1) = R E_E^(l) P, the patch sets and their
@@ -157,14 +178,21 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
  * arrays to query n_patches and sum_n only. */
 ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offsets,
                            int32_t* dofs, int32_t* n_patches, int64_t* sum_n);
+/* Host copy of the colour class of every patch of one smoothing level, in cell order
+ * c = j N + i (coloured smoother only): colour_of_cell[n_patches].  NULL: query *n_colours
+ * only.  IB_ERR_INVALID for an additive hierarchy. */
+ib_status cav_colour_export(const cav_hierarchy* h, int32_t level, int32_t* colour_of_cell,
+                            int32_t* n_colours);
 /* Host copy of E_E on one level as CSR over all 2 N_l^2 velocity rows (columns sorted):
  * rowptr[2 N_l^2 + 1], cols[nnz], vals[nnz].  NULL arrays: query *nnz only. */
 ib_status cav_ee_export(const cav_hierarchy* h, int32_t level, int64_t* rowptr,
                         int32_t* cols, double* vals, int64_t* nnz);
-/* One weighted additive CAV sweep on level `level` (Eq. additive_cav_saddle):
- *   r = b - K_E w;  w <- w + alpha sum_i R_i^T Theta_i K_{E,i}^{-1} R_i r;
- *   then the mean pressure is removed (Sec. 3.3).  Theta_i = 1 / patch count per unknown.
- * w is updated in place. */
+/* One CAV sweep on level `level`, w updated in place, then the mean pressure removed
+ * (Sec. 3.3).  Additive smoother (Eq. additive_cav_saddle):
+ *   r = b - K_E w;  w <- w + alpha sum_i R_i^T Theta_i K_{E,i}^{-1} R_i r,
+ *   Theta_i = 1 / patch count per unknown.
+ * Coloured smoother: for each colour class in turn, for every patch p of the class at once,
+ *   w_p <- w_p + K_{E,p}^{-1} (b - K_E w)_p  (multiplicative Schwarz, Sec. 3.3). */
 ib_status cav_sweep(const cav_hierarchy* h, int32_t level, const double* b, double* w,
                     cudaStream_t stream);
 /* r = b - K_E^(l) w on level l (rediscretised Stokes part plus Galerkin E_E). */
@@ -185,7 +213,8 @@ void cav_destroy(cav_hierarchy* h);
 
 /* Allocation-free sweep.  Same result as cav_sweep (the same kernels run in the same
  * order), but its scratch -- the residual, the packed patch corrections and the partial
- * sums of the pressure mean -- lives in a fixed 8 MiB device array inside this library
+ * sums of the pressure mean (with the coloured smoother: the partial sums only) -- lives in
+ * a fixed 8 MiB device array inside this library
  * (CAV_NOALLOC_SCRATCH_DOUBLES doubles) instead of buffers reserved per hierarchy.  It is for
  * callers that cannot let a call allocate device memory: code that runs with all device
  * memory already handed to its own pool or budget, where a cudaMalloc would fail or

@@ -192,11 +192,14 @@ def sweep(lev: Level, w, b, mode: str = "additive", alpha: float = 1.0):
     return smoother.multiplicative_sweep(lev.KE, lev.solvers, w, b, lev.N, lev.inject, lev.KE_csc)
 
 
-def vcycle(levels, b, nu_pre: int = 1, nu_post: int = 1, mode: str = "additive",
+def vcycle(levels, b, nu_pre=1, nu_post=1, mode="additive",
            alpha: float = 1.0, li: int = 0, trace: list | None = None) -> np.ndarray:
-    """z = B b: one V-cycle with zero initial guess (Sec. 4).  `trace`, if given, collects
+    """z = B b: one V-cycle with zero initial guess (Sec. 4).  nu_pre, nu_post and mode may be
+    per-level lists (smoothing levels, finest first).  `trace`, if given, collects
     (level, stage, vector) after every sweep for step-by-step comparison."""
     lev = levels[li]
+    if isinstance(mode, (list, tuple)):
+        return _vcycle_levels(levels, b, nu_pre, nu_post, mode, alpha, li, trace)
     if li == len(levels) - 1:
         z = coarse_solve(lev, b)
         if trace is not None:
@@ -216,6 +219,32 @@ def vcycle(levels, b, nu_pre: int = 1, nu_post: int = 1, mode: str = "additive",
         trace.append((li, "prolonged", x.copy()))
     for s in range(nu_post):
         x = sweep(lev, x, b, mode, alpha)
+        if trace is not None:
+            trace.append((li, f"post{s}", x.copy()))
+    return x
+
+
+def _vcycle_levels(levels, b, nu_pre, nu_post, mode, alpha, li, trace):
+    """The V-cycle with level li's own smoother mode[li] and sweep counts."""
+    lev = levels[li]
+    if li == len(levels) - 1:
+        z = coarse_solve(lev, b)
+        if trace is not None:
+            trace.append((li, "coarse", z.copy()))
+        return z
+    x = np.zeros_like(b)
+    for s in range(nu_pre[li]):
+        x = sweep(lev, x, b, mode[li], alpha)
+        if trace is not None:
+            trace.append((li, f"pre{s}", x.copy()))
+    r = b - lev.KE @ x
+    Nc = levels[li + 1].N
+    xc = _vcycle_levels(levels, restrict(Nc) @ r, nu_pre, nu_post, mode, alpha, li + 1, trace)
+    x = x + prolong(Nc) @ xc
+    if trace is not None:
+        trace.append((li, "prolonged", x.copy()))
+    for s in range(nu_post[li]):
+        x = sweep(lev, x, b, mode[li], alpha)
         if trace is not None:
             trace.append((li, f"post{s}", x.copy()))
     return x

@@ -24,6 +24,7 @@ IB_OK, IB_ERR_INVALID, IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_SINGULAR, IB_ERR_NOCONV, 
 FORCE = {"target": 0, "membrane": 1, "beam": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 KIND = {"cav": 0, "vanka": 1}
+SMOOTHER = {"additive": 0, "coloured": 1}
 
 
 class IBError(RuntimeError):
@@ -48,7 +49,8 @@ class ib_structure_desc(C.Structure):
 class cav_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("coarsest_N", C.c_int32), ("nu_pre", C.c_int32),
                 ("nu_post", C.c_int32), ("alpha", C.c_double), ("precision", C.c_int32),
-                ("autotune", C.c_int32), ("krylov_capacity", C.c_int32)]
+                ("autotune", C.c_int32), ("krylov_capacity", C.c_int32), ("smoother", C.c_int32),
+                ("coloured_levels", C.c_int32), ("nu_additive", C.c_int32)]
 
 
 class cav_level_info(C.Structure):
@@ -57,7 +59,7 @@ class cav_level_info(C.Structure):
                 ("enlarged_sum_n", C.c_int64), ("enlarged_sum_n2", C.c_int64),
                 ("inverse_bytes", C.c_int64), ("ee_nnz", C.c_int64), ("ee_rows", C.c_int32),
                 ("ee_window", C.c_int32), ("is_coarsest", C.c_int32), ("apply_variant", C.c_int32),
-                ("apply_us", C.c_float * 5)]
+                ("apply_us", C.c_float * 5), ("n_colours", C.c_int32)]
 
 
 class fgmres_desc(C.Structure):
@@ -97,6 +99,7 @@ _sig = {
     "cav_get_level_info": (C.c_int, [_vp, C.c_int32, _P(cav_level_info)]),
     "cav_patch_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _P(C.c_int32), _P(C.c_int64)]),
     "cav_ee_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _P(C.c_int64)]),
+    "cav_colour_export": (C.c_int, [_vp, C.c_int32, _vp, _P(C.c_int32)]),
     "cav_sweep": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     "cav_sweep_noalloc": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     "cav_residual": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
@@ -248,13 +251,18 @@ def ib_advect(sys: System, u, stream=None) -> np.ndarray:
 
 
 def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=1.0,
-              precision="fp64", autotune=False, krylov_capacity=0, stream=None) -> Hierarchy:
+              precision="fp64", autotune=False, krylov_capacity=0, smoother="additive",
+              coloured_levels=0, nu_additive=0, stream=None) -> Hierarchy:
+    """smoother: "additive" on every level, or "coloured" on the `coloured_levels` finest levels
+    (0: all) with the additive sweep (nu_additive sweeps per side, 0: nu_pre/nu_post) below."""
     d = cav_desc(KIND[kind], int(coarsest_N), int(nu_pre), int(nu_post), float(alpha), PRECISION[precision],
-                 1 if autotune else 0, int(krylov_capacity))
+                 1 if autotune else 0, int(krylov_capacity), SMOOTHER[smoother], int(coloured_levels),
+                 int(nu_additive))
     out = _vp()
     _check(_lib.cav_setup(sys.handle, C.byref(d), _stream(stream), C.byref(out)), "cav_setup")
     return Hierarchy(out, sys, dict(kind=kind, coarsest_N=coarsest_N, nu_pre=nu_pre, nu_post=nu_post,
-                                    alpha=alpha, precision=precision, autotune=autotune))
+                                    alpha=alpha, precision=precision, autotune=autotune, smoother=smoother,
+                                    coloured_levels=coloured_levels, nu_additive=nu_additive))
 
 
 def cav_num_levels(h: Hierarchy) -> int:
@@ -280,6 +288,15 @@ def cav_patch_export(h: Hierarchy, level: int):
     _check(_lib.cav_patch_export(h.handle, level, _vp(off.ctypes.data), _vp(dofs.ctypes.data),
                                  C.byref(n), C.byref(tot)), "cav_patch_export")
     return off, dofs
+
+
+def cav_colour_export(h: Hierarchy, level: int) -> np.ndarray:
+    """Colour class of every patch of a smoothing level, in cell order (coloured smoother)."""
+    info = cav_get_level_info(h, level)
+    out = np.zeros(info["N"] ** 2, dtype=np.int32)
+    nc = C.c_int32()
+    _check(_lib.cav_colour_export(h.handle, level, _vp(out.ctypes.data), C.byref(nc)), "cav_colour_export")
+    return out
 
 
 def cav_ee_export(h: Hierarchy, level: int):

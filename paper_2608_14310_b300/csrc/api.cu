@@ -42,7 +42,7 @@ using namespace cav;
 extern "C" {
 
 const char* ib_last_error(void) { return g_last_error.c_str(); }
-int ib_abi_version(void) { return 1; }
+int ib_abi_version(void) { return 2; }
 int64_t ib_launch_count(void) { return g_launches.load(); }
 
 ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaStream_t st, ib_system** out) {
@@ -218,6 +218,12 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
     CAV_REQUIRE(d->precision >= CAV_PREC_FP64 && d->precision <= CAV_PREC_BF16, "cav_setup: unknown precision");
     CAV_REQUIRE(std::isfinite(d->alpha) && d->alpha > 0, "cav_setup: alpha must be positive");
     CAV_REQUIRE(d->krylov_capacity >= 0 && d->krylov_capacity <= 4096, "cav_setup: bad krylov_capacity");
+    CAV_REQUIRE(d->smoother == CAV_SMOOTH_ADDITIVE || d->smoother == CAV_SMOOTH_COLOURED,
+                "cav_setup: unknown smoother");
+    CAV_REQUIRE(d->coloured_levels >= 0 && d->nu_additive >= 0, "cav_setup: negative coloured_levels or nu_additive");
+    CAV_REQUIRE(!(d->smoother == CAV_SMOOTH_COLOURED && d->precision == CAV_PREC_BF16),
+                "cav_setup: the coloured (multiplicative) smoother needs FP32 or FP64 patch inverses: with "
+                "BF16-rounded inverses the undamped sweep diverges");
     H = new cav_hierarchy();
     H->sys = s;
     H->desc = *d;
@@ -279,6 +285,7 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
     info->inverse_bytes = lv.inv_elems * bytes;
     info->apply_variant = lv.apply_variant;
     for (int v = 0; v < 5; ++v) info->apply_us[v] = lv.apply_us[v];
+    info->n_colours = lv.n_colours;
   }
   return IB_OK;
   CAV_API_END
@@ -319,6 +326,18 @@ ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offse
     }
   }
   offsets[NN] = pos;
+  return IB_OK;
+  CAV_API_END
+}
+
+ib_status cav_colour_export(const cav_hierarchy* h, int32_t level, int32_t* colour_of_cell, int32_t* n_colours) {
+  CAV_API_BEGIN
+  const Level& lv = level_of(h, level);
+  CAV_REQUIRE(!lv.coarsest, "cav_colour_export: the coarsest level has no patches");
+  CAV_REQUIRE(lv.coloured, "cav_colour_export: this level's smoother is additive");
+  if (n_colours) *n_colours = lv.n_colours;
+  if (colour_of_cell)
+    for (size_t c = 0; c < lv.colour_of_cell.size(); ++c) colour_of_cell[c] = lv.colour_of_cell[c];
   return IB_OK;
   CAV_API_END
 }

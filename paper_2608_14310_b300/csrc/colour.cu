@@ -1,0 +1,673 @@
+// The multiplicative CAV sweep of Sec. 3.3 in a parallel order: the patches are split into
+// colour classes whose members share no unknown and are not coupled by any entry of K_E, and
+// the classes are visited in turn.  Every patch p of a class then solves
+//     w_p <- w_p + D_c X_p D_r (b - K_E w)_p
+// from the current iterate, and since no patch of the class reads what another writes, one
+// launch per class gives the sequential multiplicative sweep in class-by-class order.
+//
+// Set-up (host): first-fit greedy colouring, the enlarged patches in cell order first, then
+// the standard ones, over the structural coupling of K_E (Stokes stencils plus E_E's pattern).
+//
+// One class step (one launch):
+//  * each enlarged patch is one thread-block cluster of C CTAs; CTA k owns the k-th slice of
+//    the patch's slots.  It evaluates those slots' residual rows (Stokes stencil and E_E row,
+//    eight lanes per row), stages the matching column slice of the column-major inverse in
+//    shared memory with a TMA bulk copy issued before the residual work, and forms the
+//    partial product X[:, slice] y[slice].  After a cluster barrier CTA k sums the C partials
+//    of its row slice through distributed shared memory in rank order and adds D_c times the
+//    sum to w.  The next class's inverse slices are prefetched into L2 meanwhile.
+//  * each standard cell is one thread: its five Stokes rows and the shared 5 x 5 inverse.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "device_util.cuh"
+#include "level_math.cuh"
+#include "tma_util.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace cav {
+
+// ------------------------------------------------------------------ set-up: colour classes
+
+// Per packed slot of the enlarged patches: start and length of its row in E_E's compact CSR
+// (length 0 for a pressure or a velocity without an E_E row).
+__global__ void k_slot_rows(int64_t n_slots, const int* __restrict__ dofs, int NN, const int* __restrict__ row_of,
+                            const int64_t* __restrict__ rowptr, int2* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const int k = dofs[s];
+  int2 e = make_int2(0, 0);
+  if (k < 2 * NN && row_of) {
+    const int r = row_of[k];
+    if (r >= 0) e = make_int2((int)rowptr[r], (int)(rowptr[r + 1] - rowptr[r]));
+  }
+  out[s] = e;
+}
+
+template <typename T>
+struct ColourStep;
+template <typename T>
+__global__ void k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w);
+
+void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+  Arena& A = H->arena;
+  const int N = lv.N, NN = N * N, n = 3 * NN;
+  CAV_REQUIRE(lv.ee.nnz < (int64_t)1 << 31, "coloured smoother: E_E too large for 32-bit row offsets");
+  std::vector<uint8_t> big(NN);
+  std::vector<int64_t> off(lv.n_big + 1, 0);
+  std::vector<int> bd(lv.big_sum_n);
+  std::vector<int> row_of(2 * NN, -1);
+  std::vector<int64_t> rowptr(lv.ee.n_rows + 1, 0);
+  std::vector<int> cols(lv.ee.nnz);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(big.data(), lv.cell_big, NN, cudaMemcpyDeviceToHost, st));
+  if (lv.n_big) {
+    CAV_CHECK_CUDA(cudaMemcpyAsync(off.data(), lv.big_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(bd.data(), lv.big_dofs, sizeof(int) * lv.big_sum_n, cudaMemcpyDeviceToHost, st));
+  }
+  if (lv.ee.n_rows) {
+    CAV_CHECK_CUDA(cudaMemcpyAsync(row_of.data(), lv.ee.row_of, sizeof(int) * 2 * NN, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(rowptr.data(), lv.ee.rowptr, sizeof(int64_t) * (lv.ee.n_rows + 1),
+                                   cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(cols.data(), lv.ee.cols, sizeof(int) * lv.ee.nnz, cudaMemcpyDeviceToHost, st));
+  }
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+
+  // enlarged-patch index of each cell; unknowns of a cell's patch
+  std::vector<int> pidx(NN, -1);
+  for (int c = 0, q = 0; c < NN; ++c)
+    if (big[c]) pidx[c] = q++;
+  int stdbuf[5];
+  auto patch = [&](int c, const int*& ptr, int& len) {
+    if (big[c]) {
+      const int q = pidx[c];
+      ptr = bd.data() + off[q];
+      len = (int)(off[q + 1] - off[q]);
+    } else {
+      const int i = c % N, j = c / N;
+      stdbuf[0] = c;
+      stdbuf[1] = j * N + (i + 1) % N;
+      stdbuf[2] = NN + c;
+      stdbuf[3] = NN + ((j + 1) % N) * N + i;
+      stdbuf[4] = 2 * NN + c;
+      ptr = stdbuf;
+      len = 5;
+    }
+  };
+  // holders: for every unknown, the cells whose patch holds it (ascending)
+  std::vector<int> hoff(n + 1, 0);
+  for (int c = 0; c < NN; ++c) {
+    const int* ptr;
+    int len;
+    patch(c, ptr, len);
+    for (int t = 0; t < len; ++t) ++hoff[ptr[t] + 1];
+  }
+  for (int k = 0; k < n; ++k) hoff[k + 1] += hoff[k];
+  std::vector<int> hold(hoff[n]);
+  {
+    std::vector<int> cur(hoff.begin(), hoff.end() - 1);
+    for (int c = 0; c < NN; ++c) {
+      const int* ptr;
+      int len;
+      patch(c, ptr, len);
+      for (int t = 0; t < len; ++t) hold[cur[ptr[t]]++] = c;
+    }
+  }
+  // first fit in visit order
+  std::vector<int> order;
+  order.reserve(NN);
+  for (int c = 0; c < NN; ++c)
+    if (big[c]) order.push_back(c);
+  for (int c = 0; c < NN; ++c)
+    if (!big[c]) order.push_back(c);
+  std::vector<int> colour(NN, -1), dstamp(n, -1), cstamp;
+  std::vector<int> reach;
+  reach.reserve(8192);
+  auto wrap = [N](int a) { return a < 0 ? a + N : (a >= N ? a - N : a); };
+  for (const int c : order) {
+    reach.clear();
+    auto add = [&](int k) {
+      if (dstamp[k] != c) {
+        dstamp[k] = c;
+        reach.push_back(k);
+      }
+    };
+    const int* ptr;
+    int len;
+    patch(c, ptr, len);
+    for (int t = 0; t < len; ++t) {
+      const int k = ptr[t];
+      const int comp = k / NN, cc = k % NN, i = cc % N, j = cc / N;
+      add(k);
+      if (comp == 0) {  // u row: A0 stencil in u, G to the two adjacent cells
+        add(j * N + wrap(i + 1));
+        add(j * N + wrap(i - 1));
+        add(wrap(j + 1) * N + i);
+        add(wrap(j - 1) * N + i);
+        add(2 * NN + j * N + i);
+        add(2 * NN + j * N + wrap(i - 1));
+      } else if (comp == 1) {
+        add(NN + j * N + wrap(i + 1));
+        add(NN + j * N + wrap(i - 1));
+        add(NN + wrap(j + 1) * N + i);
+        add(NN + wrap(j - 1) * N + i);
+        add(2 * NN + j * N + i);
+        add(2 * NN + wrap(j - 1) * N + i);
+      } else {  // p row: -D
+        add(j * N + i);
+        add(j * N + wrap(i + 1));
+        add(NN + j * N + i);
+        add(NN + wrap(j + 1) * N + i);
+      }
+      if (comp < 2 && row_of[k] >= 0) {
+        const int r = row_of[k];
+        for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) add(cols[q]);
+      }
+    }
+    for (const int k : reach)
+      for (int h = hoff[k]; h < hoff[k + 1]; ++h) {
+        const int col = colour[hold[h]];
+        if (col >= 0) cstamp[col] = c;
+      }
+    int col = 0;
+    while (col < (int)cstamp.size() && cstamp[col] == c) ++col;
+    if (col == (int)cstamp.size()) cstamp.push_back(-1);
+    colour[c] = col;
+  }
+  const int nc = (int)cstamp.size();
+  lv.n_colours = nc;
+  lv.colour_of_cell = colour;
+  lv.col_big_start.assign(nc + 1, 0);
+  lv.col_std_start.assign(nc + 1, 0);
+  for (int c = 0; c < NN; ++c) ++(big[c] ? lv.col_big_start : lv.col_std_start)[colour[c] + 1];
+  for (int k = 0; k < nc; ++k) {
+    lv.col_big_start[k + 1] += lv.col_big_start[k];
+    lv.col_std_start[k + 1] += lv.col_std_start[k];
+  }
+  std::vector<int> hb(lv.n_big), hs(NN - lv.n_big);
+  {
+    std::vector<int> cb(lv.col_big_start.begin(), lv.col_big_start.end() - 1);
+    std::vector<int> cs(lv.col_std_start.begin(), lv.col_std_start.end() - 1);
+    for (int c = 0; c < NN; ++c) {
+      if (big[c]) hb[cb[colour[c]]++] = pidx[c];
+      else hs[cs[colour[c]]++] = c;
+    }
+  }
+  {
+    // job records of the enlarged patches, class by class: (p, n, slot offset) and inverse offset
+    std::vector<int64_t> inv_off(lv.n_big + 1, 0);
+    if (lv.n_big)
+      CAV_CHECK_CUDA(cudaMemcpy(inv_off.data(), lv.inv_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost));
+    CAV_REQUIRE(lv.big_sum_n < (int64_t)1 << 31, "coloured smoother: too many patch slots for 32-bit offsets");
+    std::vector<int4> jobs(lv.n_big);
+    std::vector<int64_t> jinv(lv.n_big);
+    for (int t = 0; t < lv.n_big; ++t) {
+      const int q = hb[t];
+      jobs[t] = make_int4(q, (int)(off[q + 1] - off[q]), (int)off[q], 0);
+      jinv[t] = inv_off[q];
+    }
+    lv.col_job = A.alloc<int4>(std::max(lv.n_big, 1));
+    lv.col_inv = A.alloc<int64_t>(std::max(lv.n_big, 1));
+    if (lv.n_big) {
+      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_job, jobs.data(), sizeof(int4) * lv.n_big, cudaMemcpyHostToDevice, st));
+      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_inv, jinv.data(), sizeof(int64_t) * lv.n_big, cudaMemcpyHostToDevice, st));
+    }
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
+  lv.col_std = A.alloc<int>(std::max(NN - lv.n_big, 1));
+  if (NN - lv.n_big)
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_std, hs.data(), sizeof(int) * (NN - lv.n_big), cudaMemcpyHostToDevice, st));
+  // the class step's shared memory can exceed the 48 KB default (set here, outside any capture)
+  CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  lv.slot_ee = A.alloc<int2>(std::max<int64_t>(lv.big_sum_n, 1));
+  if (lv.big_sum_n) {
+    k_slot_rows<<<div_up(lv.big_sum_n, 256), 256, 0, st>>>(lv.big_sum_n, lv.big_dofs, NN,
+                                                           lv.ee.n_rows ? lv.ee.row_of : nullptr, lv.ee.rowptr,
+                                                           lv.slot_ee);
+    CAV_CHECK_LAUNCH();
+  }
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ one class step
+//
+// B300 executes an FP64 instruction of a warp in about 64 cycles whatever the number of
+// active lanes, and an SM sustains roughly one FP64 warp instruction per 19 cycles.  The
+// residual rows are therefore laid out lane-dense: E_E sums with four lanes per slot on
+// warps 0-3, Stokes rows one per lane on warps 4-7, standard cells one row per lane.
+
+constexpr int CS_THREADS = 256;
+constexpr int CS_EE_LANES = 4;                   // lanes per slot for the E_E row sums
+constexpr int CS_EE_SLOTS = 128 / CS_EE_LANES;   // slots per pass of warps 0-3
+constexpr int CS_MAXPASS = 4;                    // row passes of the slice product
+constexpr int CS_EE_BATCH = 8;                   // E_E entries gathered per lane before the FMAs
+constexpr int CS_CLUSTER = 8;                    // CTAs per enlarged patch
+constexpr int CS_SLICE_CAP = 160 * 1024;         // shared-memory bytes for a staged slice
+constexpr int CS_STD_WARPS = 4;                  // warps per block on standard cells
+constexpr int CS_STD_PER_WARP = 6;               // standard cells per warp (five lanes each)
+constexpr int CS_STD_CELLS = CS_STD_WARPS * CS_STD_PER_WARP;
+
+template <typename T>
+struct ColourStep {
+  int N;
+  double ih;        // 1 / h
+  double cdiag;     // rho/dt + 4 mu / h^2: the diagonal of A0
+  double cnb;       // -mu / h^2: A0's neighbour coefficient
+  double dt;
+  const int* dofs;
+  const double* s_r;
+  const double* s_c;
+  const T* inv;
+  const int2* slot_ee;
+  const int* row_of;
+  const int64_t* rowptr;
+  const int* cols;
+  const double* vals;
+  const int4* jobs;      // this class's enlarged patches
+  const int64_t* job_inv;
+  int nbig;
+  const int* std_list;   // this class's standard cells
+  int nstd;
+  int slice_cap;         // bytes of the shared-memory slice buffer (at least one column)
+  int chunk_max;         // slots per slice, upper bound over the level
+  int ld_max;
+  int* status;
+  StdInv S;
+};
+
+// Slots (columns, and rows of the result) of cluster rank `rank` of C for a patch of n
+// slots: rank, rank + C, rank + 2C, ...  Dealing them round-robin balances the E_E rows,
+// which sit on the velocity slots only, over the cluster's CTAs.
+__device__ inline int slots_of(int n, int rank, int C) { return (n > rank) ? (n - rank + C - 1) / C : 0; }
+
+// Programmatic dependent launch: let the next class step start its prologue now; wait until
+// the previous step has completed and its writes are visible.
+__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ inline void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ inline void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ inline void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ inline void prefetch_l1(const void* p) { asm volatile("prefetch.L1 [%0];" ::"l"(p)); }
+
+// Stokes row of unknown (comp, i, j) of K_E w (Eq. intro_saddle: A0 u + G p, or -D u), in the
+// form cdiag u_c + cnb (sum of the four neighbours) + (p_c - p_w) / h, seven FP64 operations;
+// the iterate is read from L2 (ld.global.cg): earlier class steps wrote it while this kernel ran.
+template <typename T>
+__device__ inline double stokes_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
+  const int N = a.N, NN = N * N;
+  const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
+  const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
+  const int c = j * N + i;
+  const double* p = w + 2 * NN;
+  if (comp < 2) {
+    const double* u = w + comp * NN;
+    const int cw = (comp == 0) ? j * N + im : jm * N + i;  // the other cell of the face's gradient
+    const double nb = (__ldcg(u + j * N + ip) + __ldcg(u + j * N + im)) + (__ldcg(u + jp * N + i) + __ldcg(u + jm * N + i));
+    return fma(a.ih, __ldcg(p + c) - __ldcg(p + cw), fma(a.cnb, nb, a.cdiag * __ldcg(u + c)));
+  }
+  const double* u = w;
+  const double* v = w + NN;
+  return -((__ldcg(u + j * N + ip) - __ldcg(u + c)) + (__ldcg(v + jp * N + i) - __ldcg(v + c))) * a.ih;
+}
+
+// One class step.  Blocks [0, C nbig) are the clusters of the enlarged patches, the rest take
+// the standard cells.  Everything that does not depend on the iterate (job records, slot
+// records, b, the E_E entries' L1 prefetch, the TMA copy of the inverse slice) happens before
+// pdl_wait(), overlapping the previous class step.
+// Column groups of the slice product: FP32 partials are cheap to sum, so the columns are split
+// over four groups of 64 threads; FP64 additions cost a 64-cycle warp slot each, so the FP64
+// product keeps one group.
+template <typename T>
+struct ProductShape {
+  static constexpr int CG = (sizeof(typename VecLoad<T>::acc_t) == 4) ? 4 : 1;
+  static constexpr int RT = CS_THREADS / CG;  // row threads per group
+};
+
+template <typename T>
+__global__ void __launch_bounds__(CS_THREADS)
+k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
+  typedef VecLoad<T> VL;
+  typedef typename VL::acc_t acc_t;
+  constexpr int V = VL::V;
+  constexpr int C = CS_CLUSTER;
+  constexpr int CG = ProductShape<T>::CG, RT = ProductShape<T>::RT;
+  const int NN = a.N * a.N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int big_blocks = a.nbig * C;
+  pdl_trigger();
+
+  if ((int)blockIdx.x >= big_blocks) {
+    // ---- standard cells: five lanes per cell, one Stokes row each; the shared 5 x 5 inverse
+    // is applied after a shuffle of the cell's five residuals
+    if (warp >= CS_STD_WARPS) return;
+    const int slot = lane / 5, q = lane % 5;
+    const int t = ((int)blockIdx.x - big_blocks) * CS_STD_CELLS + warp * CS_STD_PER_WARP + slot;
+    const bool act = slot < CS_STD_PER_WARP && t < a.nstd;
+    int k = 0, ci = 0, cj = 0, comp = 0, ro = -1;
+    double bk = 0.0;
+    if (act) {
+      const int c = a.std_list[t];
+      const int i = c % a.N, j = c / a.N;
+      const int ip = (i + 1 == a.N) ? 0 : i + 1, jp = (j + 1 == a.N) ? 0 : j + 1;
+      // canonical slots: u_ij, u_i+1j, v_ij, v_ij+1, p_ij
+      comp = (q < 2) ? 0 : (q < 4 ? 1 : 2);
+      ci = (q == 1) ? ip : i;
+      cj = (q == 3) ? jp : j;
+      k = comp * NN + cj * a.N + ci;
+      bk = b[k];
+      if (comp < 2 && a.row_of) ro = a.row_of[k];
+    }
+    pdl_wait();
+    double r = 0.0, old = 0.0;
+    if (act) {
+      old = __ldcg(w + k);
+      double kr = stokes_row_l2(a, w, comp, ci, cj);
+      if (ro >= 0) {
+        double s = 0.0;
+        for (int64_t e = a.rowptr[ro]; e < a.rowptr[ro + 1]; ++e) s += a.vals[e] * __ldcg(w + a.cols[e]);
+        kr -= a.dt * s;
+      }
+      r = bk - kr;
+    }
+    const int base = (lane / 5) * 5;
+    double rr[5];
+#pragma unroll
+    for (int c2 = 0; c2 < 5; ++c2) rr[c2] = __shfl_sync(0xffffffffu, r, min(base + c2, 31));
+    if (act) {
+      const double* m = a.S.m + 5 * q;
+      w[k] = old + (m[0] * rr[0] + m[1] * rr[1] + m[2] * rr[2] + m[3] * rr[3] + m[4] * rr[4]);
+    }
+    return;
+  }
+
+  // ---- one CTA of an enlarged patch's cluster
+  cluster_arrive_relaxed();  // every CTA of the cluster is running once this phase completes
+  const int rank = (int)(blockIdx.x % C);
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  T* xs = reinterpret_cast<T*>(smem + 128);
+  const int cm4 = (a.chunk_max + 3) & ~3;
+  acc_t* y = reinterpret_cast<acc_t*>(smem + 128 + a.slice_cap);  // [cm4]
+  acc_t* recv = y + cm4;                                          // [C][CG][cm4] partials of my rows
+  double* sold = reinterpret_cast<double*>(recv + C * CG * cm4);  // [cm4] iterate before the step
+  double* sb = sold + cm4;                                        // [cm4] b at my slots
+  double* ssr = sb + cm4;                                         // [cm4] row scales
+  double* ssc = ssr + cm4;                                        // [cm4] column scales
+  double* see = ssc + cm4;                                        // [cm4] E_E row sums
+  double* sst = see + cm4;                                        // [cm4] Stokes rows
+  int* sk = reinterpret_cast<int*>(sst + cm4);                    // [cm4] unknowns
+  int2* se = reinterpret_cast<int2*>(sk + cm4);                   // [cm4] E_E rows
+  const int4 job = a.jobs[blockIdx.x / C];
+  const int64_t ioff = a.job_inv[blockIdx.x / C];
+  const int n = job.y;
+  const int d0 = job.z;
+  const int ld = (n + 7) & ~7;
+  const int m = slots_of(n, rank, C);  // this CTA's slots: g = rank + C s, s < m
+  const int col_bytes = ld * (int)sizeof(T);
+  const int pc = max(1, a.slice_cap / col_bytes);  // columns per staged piece
+  const T* X = a.inv + ioff;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0 && m > 0) {
+    const int nc = min(pc, m);
+    mbar_arrive_expect_tx(bar, (uint32_t)(nc * col_bytes));
+    for (int cl = 0; cl < nc; ++cl)
+      bulk_copy_g2s(xs + (size_t)cl * ld, X + (int64_t)(rank + C * cl) * ld, (uint32_t)col_bytes, bar);
+  }
+  // slot records of the slice (independent of the iterate)
+  for (int s = tid; s < m; s += CS_THREADS) {
+    const int g = d0 + rank + C * s;
+    const int k = a.dofs[g];
+    sk[s] = k;
+    se[s] = a.slot_ee[g];
+    ssr[s] = a.s_r[g];
+    ssc[s] = a.s_c[g];
+    sb[s] = b[k];
+  }
+  __syncthreads();
+  const int eg = tid / CS_EE_LANES, el = tid % CS_EE_LANES;  // E_E groups (warps 0-3)
+  if (tid < 128)
+    for (int s = eg; s < m; s += CS_EE_SLOTS) {
+      const int2 e = se[s];
+      for (int q = e.x + el; q < e.x + e.y; q += CS_EE_LANES) {
+        prefetch_l1(a.cols + q);
+        prefetch_l1(a.vals + q);
+      }
+    }
+  pdl_wait();
+  // residual rows of the slice: E_E sums on warps 0-3, Stokes rows on warps 4-7
+  if (tid < 128) {
+    for (int t0 = 0; t0 < m; t0 += CS_EE_SLOTS) {
+      const int s = t0 + eg;
+      int2 e = make_int2(0, 0);
+      if (s < m) e = se[s];
+      // this lane's entries q = e.x + el + CS_EE_LANES t, t < cnt: in batches, every load of a
+      // batch is issued before its FMAs (batch counts are warp-uniform, so no FMA slot is spent
+      // on lanes that have run out)
+      const int cnt = (e.y > el) ? (e.y - el + CS_EE_LANES - 1) / CS_EE_LANES : 0;
+      const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+      double acc = 0.0;
+      for (int t0 = 0; t0 < wmax; t0 += CS_EE_BATCH) {
+        double vv[CS_EE_BATCH], wv[CS_EE_BATCH];
+#pragma unroll
+        for (int t = 0; t < CS_EE_BATCH; ++t) {
+          const int q = e.x + el + (t0 + t) * CS_EE_LANES;
+          const bool ok = t0 + t < cnt;
+          vv[t] = ok ? a.vals[q] : 0.0;
+          wv[t] = ok ? __ldcg(w + a.cols[q]) : 0.0;
+        }
+        static_assert(CS_EE_BATCH == 8, "the tail below is written for batches of eight");
+        switch (min(wmax - t0, CS_EE_BATCH)) {  // warp-uniform: only the needed FMAs issue
+          case 8: acc = fma(vv[7], wv[7], acc);  // fall through
+          case 7: acc = fma(vv[6], wv[6], acc);  // fall through
+          case 6: acc = fma(vv[5], wv[5], acc);  // fall through
+          case 5: acc = fma(vv[4], wv[4], acc);  // fall through
+          case 4: acc = fma(vv[3], wv[3], acc);  // fall through
+          case 3: acc = fma(vv[2], wv[2], acc);  // fall through
+          case 2: acc = fma(vv[1], wv[1], acc);  // fall through
+          default: acc = fma(vv[0], wv[0], acc);
+        }
+      }
+#pragma unroll
+      for (int o = CS_EE_LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (s < m && el == 0) see[s] = acc;
+    }
+  } else {
+    for (int s = tid - 128; s < m; s += 128) {
+      const int k = sk[s];
+      const int comp = k / NN, cc = k % NN;
+      sold[s] = __ldcg(w + k);
+      sst[s] = stokes_row_l2(a, w, comp, cc % a.N, cc / a.N);
+    }
+  }
+  __syncthreads();
+  // y = D_r (b - K_E w), K_E w = Stokes - dt E_E w (E_E rows only on velocities that have one)
+  for (int s = tid; s < m; s += CS_THREADS) {
+    const double kr = (se[s].y > 0) ? sst[s] - a.dt * see[s] : sst[s];
+    y[s] = (acc_t)(ssr[s] * (sb[s] - kr));
+  }
+  __syncthreads();
+  // partial product X[:, slice] y[slice]: column group cgp takes the slice's columns
+  // cgp, cgp + CG, ...; each of its RT threads owns V consecutive rows per pass
+  const int cgp = tid / RT, rt = tid % RT;
+  acc_t accv[CS_MAXPASS][V];
+#pragma unroll
+  for (int ps = 0; ps < CS_MAXPASS; ++ps)
+#pragma unroll
+    for (int v = 0; v < V; ++v) accv[ps][v] = 0;
+  bool alive = true;
+  uint32_t phase = 0;
+  for (int b0 = 0; b0 < m; b0 += pc) {
+    const int nc = min(pc, m - b0);
+    if (alive && !mbar_wait(bar, phase, a.status)) alive = false;
+    if (alive) {
+#pragma unroll
+      for (int ps = 0; ps < CS_MAXPASS; ++ps) {
+        const int r0 = (ps * RT + rt) * V;
+        if (r0 < n) {
+#pragma unroll 4
+          for (int cl = cgp; cl < nc; cl += CG) {
+            acc_t x[V];
+            VL::load_shared(xs + (size_t)cl * ld + r0, x);
+            const acc_t yc = y[b0 + cl];
+#pragma unroll
+            for (int v = 0; v < V; ++v) accv[ps][v] = mad(x[v], yc, accv[ps][v]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && alive && b0 + pc < m) {
+      const int nn = min(pc, m - b0 - pc);
+      mbar_arrive_expect_tx(bar, (uint32_t)(nn * col_bytes));
+      for (int cl = 0; cl < nn; ++cl)
+        bulk_copy_g2s(xs + (size_t)cl * ld, X + (int64_t)(rank + C * (b0 + pc + cl)) * ld, (uint32_t)col_bytes,
+                      bar);
+    }
+    phase ^= 1u;
+  }
+  // push each row's partial to the CTA owning that row (distributed shared memory)
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster_wait_acquire();  // the start-up phase: every CTA of the cluster is running
+#pragma unroll
+  for (int ps = 0; ps < CS_MAXPASS; ++ps) {
+    const int r0 = (ps * RT + rt) * V;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int row = r0 + v;
+      if (row < n) {
+        acc_t* dst = cluster.map_shared_rank(recv, row % C);
+        dst[(rank * CG + cgp) * cm4 + row / C] = accv[ps][v];
+      }
+    }
+  }
+  cluster_arrive_release();
+  cluster_wait_acquire();
+  // my rows: sum the C partials in rank order, scale, add to the iterate
+  for (int s = tid; s < m; s += CS_THREADS) {
+    acc_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < C * CG; ++q) sum += recv[q * cm4 + s];
+    w[sk[s]] = sold[s] + ssc[s] * (double)sum;
+  }
+}
+
+// Sums of the pressure block over tiles of 256 cells (fixed order), for the mean removal.
+__global__ void k_pressure_partials(int NN, const double* __restrict__ p, double* __restrict__ partial) {
+  __shared__ double sm[8];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const double v = (c < NN) ? p[c] : 0.0;
+  const double t = block_sum(v, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+template <typename T>
+static size_t step_smem(int chunk_max, int slice_cap) {
+  typedef typename VecLoad<T>::acc_t acc_t;
+  const int cm4 = (chunk_max + 3) & ~3;
+  return 128 + (size_t)slice_cap + sizeof(acc_t) * (size_t)(cm4 * (1 + CS_CLUSTER * ProductShape<T>::CG)) +
+         (size_t)cm4 * (6 * sizeof(double) + sizeof(int) + sizeof(int2));
+}
+
+template <typename T>
+static void launch_step(const cav_hierarchy* H, const Level& lv, const T* inv, int k, const double* b, double* w,
+                        bool programmatic, cudaStream_t st) {
+  ColourStep<T> a;
+  a.N = lv.N;
+  a.ih = 1.0 / lv.h;
+  const double ih2 = 1.0 / (lv.h * lv.h);
+  a.cdiag = lv.rho_dt + 4.0 * lv.mu * ih2;
+  a.cnb = -lv.mu * ih2;
+  a.dt = lv.dt;
+  a.dofs = lv.big_dofs;
+  a.s_r = lv.s_r;
+  a.s_c = lv.s_c;
+  a.inv = inv;
+  a.slot_ee = lv.slot_ee;
+  const bool has_ee = lv.ee.n_rows > 0;
+  a.row_of = has_ee ? lv.ee.row_of : nullptr;
+  a.rowptr = lv.ee.rowptr;
+  a.cols = lv.ee.cols;
+  a.vals = lv.ee.vals;
+  a.jobs = lv.col_job + lv.col_big_start[k];
+  a.job_inv = lv.col_inv + lv.col_big_start[k];
+  a.nbig = lv.col_big_start[k + 1] - lv.col_big_start[k];
+  a.std_list = lv.col_std + lv.col_std_start[k];
+  a.nstd = lv.col_std_start[k + 1] - lv.col_std_start[k];
+  const int max_n = std::max(lv.big_max_n, 1);
+  a.ld_max = round8(max_n);
+  a.chunk_max = (max_n + CS_CLUSTER - 1) / CS_CLUSTER;
+  const int col_bytes = a.ld_max * (int)sizeof(T);
+  a.slice_cap = std::min(a.chunk_max * col_bytes, std::max(col_bytes, (CS_SLICE_CAP / col_bytes) * col_bytes));
+  a.status = H->status;
+  for (int q = 0; q < 25; ++q) a.S.m[q] = lv.std_inv[q];
+  const size_t smem = step_smem<T>(a.chunk_max, a.slice_cap);
+  const int std_blocks = div_up(a.nstd, CS_STD_CELLS);
+  int grid = a.nbig * CS_CLUSTER + std_blocks;
+  grid = div_up(grid, CS_CLUSTER) * CS_CLUSTER;
+  if (grid == 0) return;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(CS_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = programmatic ? 2 : 1;
+  CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_colour_step<T>, a, b, w));
+  CAV_CHECK_LAUNCH();
+}
+
+// Largest patch the class step handles: CS_MAXPASS row passes per thread.
+template <typename T>
+static int colour_max_n() {
+  return CS_MAXPASS * ProductShape<T>::RT * VecLoad<T>::V;
+}
+
+void coloured_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, double* partial,
+                    bool remove_mean, bool profile, cudaStream_t st) {
+  const Level& lv = H->levels[l];
+  const int NN = lv.N * lv.N;
+  CAV_REQUIRE(lv.precision != CAV_PREC_BF16,
+              "coloured smoother: BF16 patch inverses make the undamped multiplicative sweep diverge; "
+              "use FP32 or FP64");
+  if (w_is_zero) CAV_CHECK_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)NN, st));
+  if (profile) prof_begin(H, l, st);
+  for (int k = 0; k < lv.n_colours; ++k) {
+    // class steps after the first overlap their prologue with the step before them
+    const bool programmatic = k > 0;
+    if (lv.precision == CAV_PREC_FP32) {
+      CAV_REQUIRE(lv.big_max_n <= colour_max_n<float>(), "coloured smoother: patch too large");
+      launch_step<float>(H, lv, lv.inv32, k, b, w, programmatic, st);
+    } else {
+      CAV_REQUIRE(lv.big_max_n <= colour_max_n<double>(), "coloured smoother: patch too large");
+      launch_step<double>(H, lv, lv.inv64, k, b, w, programmatic, st);
+    }
+  }
+  if (profile) prof_end(H, l, st);
+  if (remove_mean) pressure_mean_remove(lv.N, partial, w + 2 * (size_t)NN, st);
+}
+
+void pressure_mean_remove(int N, double* partial, double* p, cudaStream_t st) {
+  const int nblk = div_up(N * N, 256);
+  k_pressure_partials<<<nblk, 256, 0, st>>>(N * N, p, partial);
+  CAV_CHECK_LAUNCH();
+  launch_remove_mean(N, nblk, partial, p, st);
+}
+
+}  // namespace cav

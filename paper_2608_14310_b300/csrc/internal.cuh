@@ -86,6 +86,8 @@ struct Level {
   int N = 0;
   double h = 0, rho_dt = 0, mu = 0, dt = 0;
   bool coarsest = false;
+  bool coloured = false;         // this level smooths with the class-by-class multiplicative sweep
+  int nu_pre = 0, nu_post = 0;   // sweeps per side in the V-cycle
   EECsr ee;
 
   // patches (smoothing levels): one per cell; enlarged ones are stored explicitly
@@ -112,6 +114,17 @@ struct Level {
   int* touched = nullptr;        // [n_touched] ascending
   double std_inv[25];            // inverse of the standard Vanka patch, canonical order
                                  // (u_ij, u_i+1j, v_ij, v_ij+1, p_ij), scalings folded in
+
+  // colour classes for the multiplicative sweep (smoother CAV_SMOOTH_COLOURED): patches of
+  // one class share no unknown and no entry of K_E couples them, so a class is solved at once
+  int n_colours = 0;
+  std::vector<int> colour_of_cell;   // [N^2] host copy, for export
+  std::vector<int> col_big_start;    // [n_colours + 1] offsets into col_job / col_inv
+  std::vector<int> col_std_start;    // [n_colours + 1] offsets into col_std
+  int4* col_job = nullptr;           // [n_big] enlarged patches class by class: (p, n, slot offset, 0)
+  int64_t* col_inv = nullptr;        // [n_big] element offset of each one's inverse, same order
+  int* col_std = nullptr;            // [N^2 - n_big] standard cells, class by class
+  int2* slot_ee = nullptr;           // [big_sum_n] per packed slot: (start, length) of its E_E row
 
   // coarsest level: dense inverse of the bordered system, row-major (n+1) x (n+1)
   double* coarse_inv = nullptr;
@@ -225,7 +238,15 @@ void launch_prolong_add(int Nc, const double* x_c, double* w_f, cudaStream_t st)
 // setup.cu
 void build_levels(cav_hierarchy* H, cudaStream_t st);
 
+// colour.cu: colour classes (set-up) and the class-by-class multiplicative sweep
+void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st);
+void coloured_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
+                    double* partial, bool remove_mean, bool profile, cudaStream_t st);
+// p -= mean(p) over the N^2 cells, partial holding at least ceil(N^2 / 256) doubles
+void pressure_mean_remove(int N, double* partial, double* p, cudaStream_t st);
+
 // sweep.cu
+void launch_remove_mean(int N, int n_partial, const double* partial, double* p, cudaStream_t st);
 void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
                  cudaStream_t st);
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);

@@ -875,6 +875,12 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     lv.mu = s->mu;
     lv.dt = s->dt;
     lv.coarsest = (l + 1 == sizes.size());
+    const cav_desc& d = H->desc;
+    lv.coloured = !lv.coarsest && d.smoother == CAV_SMOOTH_COLOURED &&
+                  (d.coloured_levels <= 0 || (int)l < d.coloured_levels);
+    const bool nu_add = d.smoother == CAV_SMOOTH_COLOURED && !lv.coloured && d.nu_additive > 0;
+    lv.nu_pre = nu_add ? d.nu_additive : d.nu_pre;
+    lv.nu_post = nu_add ? d.nu_additive : d.nu_post;
     if (l == 0) {
       lv.ee = s->ee;  // owned by the system
     } else {
@@ -889,10 +895,11 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     Level& lv = H->levels[l];
     if (lv.coarsest) build_coarsest(H, lv, st);
     else build_smoother(H, lv, st);
+    if (lv.coloured) build_colours(H, lv, st);
   }
   if (H->desc.autotune)
     for (auto& lv : H->levels)
-      if (!lv.coarsest) autotune_level(H, lv, st);
+      if (!lv.coarsest && !lv.coloured) autotune_level(H, lv, st);
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   check_status(H, st, "autotune");
   // capture both V-cycle graph instances now, so no solve pays for it

@@ -16,6 +16,7 @@
 #include "internal.cuh"
 #include "device_util.cuh"
 #include "level_math.cuh"
+#include "tma_util.cuh"
 
 namespace cav {
 
@@ -59,61 +60,6 @@ k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, co
   }
 }
 
-// ---- TMA / mbarrier primitives (inline PTX) ----------------------------------------------
-
-__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ inline void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-      "r"(bytes)
-      : "memory");
-}
-__device__ inline void mbar_arrive(uint64_t* bar) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
-      : "memory");
-}
-__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase with the given parity to complete; gives up after ~2^31 clock cycles
-// (about a second), records DEV_TIMEOUT and returns false.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) {
-      atomicExch(status, DEV_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-// 1-D bulk copy global -> this CTA's shared memory, completing `bytes` on the mbarrier.
-__device__ inline void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
 __device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
 
 constexpr int TMA_CONSUMER_WARPS = 4;
@@ -375,6 +321,12 @@ __global__ void k_remove_mean(int N, int n_partial, const double* __restrict__ p
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N * N; c += gridDim.x * blockDim.x) p[c] -= mean;
 }
 
+void launch_remove_mean(int N, int n_partial, const double* partial, double* p, cudaStream_t st) {
+  const int nblk = div_up(N * N, 256) < 296 ? div_up(N * N, 256) : 296;
+  k_remove_mean<<<nblk, 256, 0, st>>>(N, n_partial, partial, p);
+  CAV_CHECK_LAUNCH();
+}
+
 // Coarsest level: z = (dense bordered inverse) [r; 0], one warp per row, row-major.
 __global__ void k_coarse_apply(int n, const double* __restrict__ inv, const double* __restrict__ r,
                                double* __restrict__ z) {
@@ -581,6 +533,10 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
 
 void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, cudaStream_t st) {
   const Level& lv = H->levels[l];
+  if (lv.coloured) {
+    coloured_sweep(H, l, b, w, w_is_zero, lv.partial, true, true, st);
+    return;
+  }
   sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st);
 }
 
@@ -592,6 +548,10 @@ void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool
 static void cycle_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
                         cudaStream_t st) {
   const Level& lv = H->levels[l];
+  if (lv.coloured) {
+    coloured_sweep(H, l, b, w, w_is_zero, lv.partial, false, true, st);
+    return;
+  }
   sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st, false);
 }
 
@@ -609,7 +569,7 @@ static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double*
     return;
   }
   const int NN = lv.N * lv.N;
-  const int nu_pre = H->desc.nu_pre, nu_post = H->desc.nu_post;
+  const int nu_pre = lv.nu_pre, nu_post = lv.nu_post;
   if (nu_pre == 0) CAV_CHECK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * 3 * NN, st));
   for (int s = 0; s < nu_pre; ++s) cycle_sweep(H, l, b, x, s == 0, st);
   launch_apply(ops_of(lv), x, b, lv.r, 0, st);
@@ -619,7 +579,9 @@ static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double*
   launch_prolong_add(lc.N, lc.x, x, st);
   for (int s = 0; s < nu_post; ++s) cycle_sweep(H, l, b, x, false, st);
   if (l == 0) {
-    if (nu_post > 0) {
+    if (nu_post > 0 && lv.coloured) {
+      pressure_mean_remove(lv.N, lv.partial, x + 2 * NN, st);
+    } else if (nu_post > 0) {
       const int nblk = div_up(NN, 256) < 296 ? div_up(NN, 256) : 296;
       k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, lv.partial, x + 2 * NN);
       CAV_CHECK_LAUNCH();
@@ -751,6 +713,13 @@ extern "C" ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, co
     int device = -1;
     CAV_CHECK_CUDA(cudaGetDevice(&device));
     CAV_REQUIRE(device == h->sys->device, "cav_sweep_noalloc: the current device is not the hierarchy's device");
+    if (lv.coloured) {
+      // the class-by-class sweep needs scratch only for the pressure mean's partial sums
+      const size_t n_pc = round_up32((size_t)div_up((int64_t)lv.N * lv.N, 256));
+      CAV_REQUIRE(n_pc <= (size_t)CAV_NOALLOC_SCRATCH_DOUBLES, "cav_sweep_noalloc: level too large");
+      coloured_sweep(h, level, b, w, false, noalloc_scratch(device), true, false, st);
+      return IB_OK;
+    }
     const size_t n_r = round_up32((size_t)3 * lv.N * lv.N);
     const size_t n_d = round_up32((size_t)lv.big_sum_n);
     const size_t n_p = round_up32((size_t)lv.n_partial);

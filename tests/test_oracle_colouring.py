@@ -122,3 +122,32 @@ def test_paper_membrane_count_with_class_order():
                             rtol=1e-10, maxit=150, ref="r0")
     assert info["converged"]
     assert abs(info["iters"] - 9) <= 3, info["iters"]
+
+
+def _round_bf16(a):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    r = ((u >> np.uint32(16)) & np.uint32(1)) + np.uint32(0x7FFF)
+    return ((u + r) & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
+
+
+def test_bf16_rounded_inverses_make_the_undamped_sweep_diverge():
+    # why the library refuses BF16 inverses for the multiplicative smoother: with the
+    # enlarged patches' inverses rounded to 8 bits, one class-by-class sweep increases the
+    # residual by many orders of magnitude, while FP32 rounding leaves it contracting
+    s = W.membrane_ellipse(32, 1e4)
+    lev = multigrid.build_hierarchy(s, 8)[0]
+    col = multigrid.level_colours(lev)
+    b = s.rhs()
+    r0 = np.linalg.norm(b)
+    X64 = [sv.X for sv in lev.solvers]
+    for sv in lev.solvers:
+        if len(sv.dofs) > 5:
+            sv.X = np.asarray(sv.X, dtype=np.float32).astype(np.float64)
+    w = colouring.coloured_sweep(lev.KE, lev.solvers, col, np.zeros(b.size), b, lev.N)
+    assert np.linalg.norm(b - lev.KE @ w) < r0
+    for sv, X in zip(lev.solvers, X64):
+        if len(sv.dofs) > 5:
+            sv.X = _round_bf16(X)
+    w = colouring.coloured_sweep(lev.KE, lev.solvers, col, np.zeros(b.size), b, lev.N)
+    assert np.linalg.norm(b - lev.KE @ w) > 1e6 * r0

@@ -29,12 +29,13 @@ def _host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_sweep_matches_cav_sweep(precision):
+@pytest.mark.parametrize("precision,smoother", [("fp64", "additive"), ("fp32", "additive"),
+                                                ("fp64", "coloured")])
+def test_noalloc_sweep_matches_cav_sweep(precision, smoother):
     from paper_2608_14310_b300 import api
     rec = W.membrane_ellipse(32, 1e4)
     sysm = api.ib_setup(rec)
-    h = api.cav_setup(sysm, nu_pre=1, nu_post=1, alpha=0.85, precision=precision)
+    h = api.cav_setup(sysm, nu_pre=1, nu_post=1, alpha=0.85, precision=precision, smoother=smoother)
     rng = np.random.default_rng(3)
     for level in range(api.cav_num_levels(h) - 1):
         N = api.cav_get_level_info(h, level)["N"]

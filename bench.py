@@ -210,6 +210,18 @@ def run_reference(args, rank, world):
     return 0
 
 
+def smoother_kw(args) -> dict:
+    return {"smoother": args.smoother, "coloured_levels": args.coloured_levels, "nu_additive": args.nu_additive}
+
+
+def smoother_desc(args) -> str:
+    if args.smoother == "additive":
+        return f"weighted additive CAV (alpha {args.alpha}), {args.nu}+{args.nu} sweeps on every level"
+    lv = "every level" if args.coloured_levels == 0 else f"the {args.coloured_levels} finest level(s)"
+    extra = "" if args.coloured_levels == 0 else f", additive {args.nu_additive}+{args.nu_additive} below"
+    return f"coloured multiplicative CAV, {args.nu}+{args.nu} sweeps on {lv}{extra}"
+
+
 def run_batch(args, api, torch, dist, rank, world, local):
     """64 uneven systems (grid, force law, stiffness drawn per system) solved together by
     fgmres_solve_batched; one step = one batched solve of all 64; value = systems/s."""
@@ -221,7 +233,8 @@ def run_batch(args, api, torch, dist, rank, world, local):
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     t0 = time.perf_counter()
     syss = [api.ib_setup(r) for r in recs]
-    hs = [api.cav_setup(s, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision="fp32", autotune=True)
+    hs = [api.cav_setup(s, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision="fp32", autotune=True,
+                        **smoother_kw(args))
           for s in syss]
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -255,6 +268,10 @@ def run_batch(args, api, torch, dist, rank, world, local):
     value = whole_job_rate(len(recs) * args.steps, world, total)
     its = [i["iters"] for i in last]
     conv = [i["converged"] for i in last]
+    kappa = [r.k_bend if r.law == W.LAW_BEAM else (r.k_stretch if r.law == W.LAW_MEMBRANE else r.k_target)
+             for r in recs]  # each system's drawn stiffness (the law's primary coefficient)
+    stiff = sorted(range(len(recs)), key=lambda q: -kappa[q])
+    stiff_conv = int(sum(conv[q] for q in stiff[:len(recs) // 2]))
     variants = {}
     for h in hs:
         for l in range(api.cav_num_levels(h) - 1):
@@ -267,8 +284,8 @@ def run_batch(args, api, torch, dist, rank, world, local):
             "config": {"workload": "64 uneven IB systems: N from {64,96,128,192,256}, law from {target, membrane, "
                                    "beam}, stiffness log-uniform [1e2,1e6], M=4N, seeded RHS; FP32 inverses, "
                                    "autotuned patch-apply variants, fgmres_solve_batched",
-                       "nu": args.nu, "alpha": args.alpha, "maxit": MAXIT,
-                       "converged": int(sum(conv)), "iters_median": int(statistics.median(its)),
+                       "nu": args.nu, "alpha": args.alpha, "maxit": MAXIT, "smoother": smoother_desc(args),
+                       "converged": int(sum(conv)), "converged_of_stiffest_half": stiff_conv, "iters_median": int(statistics.median(its)),
                        "iters_max": int(max(its)), "autotuned_variant_counts": variants,
                        "l2": "flushed (256 MB write) before every timed batch"},
             "setup_s_all_64": setup_s, "gpu_launches": launches, "clocks": clk}
@@ -387,7 +404,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--nu", type=int, default=DEFAULT_NU)
+    ap.add_argument("--nu", type=int, default=None,
+                    help="sweeps per side (default: 2 additive, 1 coloured)")
+    ap.add_argument("--smoother", default="additive", choices=["additive", "coloured"],
+                    help="additive: Eq. additive_cav_saddle on every level; coloured: the multiplicative "
+                         "sweep of Sec. 3.3 visited colour class by colour class")
+    ap.add_argument("--coloured-levels", type=int, default=0,
+                    help="coloured smoother: levels (finest first) that use it, 0 = all; coarser ones additive")
+    ap.add_argument("--nu-additive", type=int, default=2, help="coloured smoother: sweeps on its additive levels")
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="membrane256", choices=["membrane256", "batch64", "learned", "beam512"])
@@ -396,6 +420,8 @@ def main():
     ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.nu is None:
+        args.nu = 1 if args.smoother == "coloured" else DEFAULT_NU
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -433,7 +459,7 @@ def main():
     e0.record()
     sysm = api.ib_setup(rec)
     hier = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision=args.precision,
-                         autotune=True)
+                         autotune=True, **smoother_kw(args))
     e1.record()
     torch.cuda.synchronize()
     setup_ms = e0.elapsed_time(e1)
@@ -523,7 +549,7 @@ def main():
     plain = None
     if args.precision != "fp64":
         hier64 = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision="fp64",
-                               autotune=True)
+                               autotune=True, **smoother_kw(args))
         for _ in range(2):
             x.zero_()
             api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False)
@@ -541,13 +567,51 @@ def main():
         plain = {"value": 1e3 / statistics.mean(pt), "unit": "solves/s", "iters": int(statistics.median(pit))}
         hier64.close()
 
+    # the other smoother on the same system and precision (the coloured multiplicative sweep on
+    # every level, one sweep per side, when the headline is additive; and the reverse)
+    other = None
+    if args.precision != "bf16":
+        o_sm = "coloured" if args.smoother == "additive" else "additive"
+        o_nu = 1 if o_sm == "coloured" else DEFAULT_NU
+        ho = api.cav_setup(sysm, nu_pre=o_nu, nu_post=o_nu, alpha=args.alpha, precision=args.precision,
+                           autotune=True, smoother=o_sm)
+        for _ in range(2):
+            x.zero_()
+            api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+        ot, oit = [], []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            x.zero_()
+            s0, s1 = ev(), ev()
+            s0.record()
+            inf = api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+            s1.record()
+            torch.cuda.synchronize()
+            ot.append(s0.elapsed_time(s1))
+            oit.append(inf["iters"])
+        wo = torch.zeros_like(b)
+        for _ in range(3):
+            api.cav_sweep(ho, 0, b, wo)
+        s0, s1 = ev(), ev()
+        s0.record()
+        for _ in range(10):
+            api.cav_sweep(ho, 0, b, wo)
+        s1.record()
+        torch.cuda.synchronize()
+        o_sweep = s0.elapsed_time(s1) / 10
+        ncol = [api.cav_get_level_info(ho, l)["n_colours"] for l in range(api.cav_num_levels(ho) - 1)]
+        other = {"smoother": o_sm, "nu": o_nu, "value": 1e3 / statistics.mean(ot), "unit": "solves/s",
+                 "iters": int(statistics.median(oit)), "finest_sweep_ms": o_sweep, "colour_classes": ncol,
+                 "us_per_class_step_finest": (1e3 * o_sweep / ncol[0]) if ncol and ncol[0] else None}
+        ho.close()
+
     li = api.cav_get_level_info(hier, 0)
     s_bytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
     alg_bytes = li["enlarged_sum_n2"] * s_bytes + li["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8)
     peak, peak_kind = peaks()
     achieved = (alg_bytes / (apply_ms / n_apply * 1e-3) / 1e9) if n_apply else None
     key = f"{args.precision}:{kernel_hash()}"
-    traffic = NCU_TRAFFIC.get(key)
+    traffic = NCU_TRAFFIC.get(key) if args.smoother == "additive" else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -555,10 +619,12 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_desc(rec), "precision": args.precision + " enlarged-patch inverses",
                    "nu": args.nu, "alpha": args.alpha, "coarsest_N": 8, "maxit": MAXIT,
+                   "smoother": smoother_desc(args),
                    "l2": "flushed (256 MB write) before every timed solve",
                    "iters": int(statistics.median(iters)), "converged": all(conv),
                    "relres_true_max": max(relres), "parallelism": f"replicas x{world}"},
         "plain_fp64": plain,
+        "other_smoother": other,
         "setup_ms": setup_ms,
         "vcycle_ms": vcycle_ms,
         "sweep": {"level": 0, "ms": sweep_ms, "algorithmic_bytes": sweep_bytes, "gbs": sweep_gbs,
@@ -566,7 +632,10 @@ def main():
                   "note": "one cav_sweep on the finest level, L2 flushed before each of 10 timed calls"},
         "setup_plus_solve_per_s": world / ((setup_ms + total_ms / args.steps) / 1e3),
         "apply_variant_finest": li["apply_variant"], "apply_variant_us_finest": li["apply_us"],
-        "roofline": {"bound": "hbm", "kernel": "k_patch_apply (finest level)", "achieved": achieved,
+        "roofline": {"bound": "hbm",
+                     "kernel": ("k_patch_apply (finest level)" if args.smoother == "additive" else
+                                "finest-level coloured sweep (all k_colour_step class steps of one sweep)"),
+                     "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "launches_timed": n_apply,

@@ -50,6 +50,12 @@ __global__ void k_slot_rows(int64_t n_slots, const int* __restrict__ dofs, int N
   out[s] = e;
 }
 
+// E_E values rounded to FP32 for the FP32 local residuals of FP32-inverse levels.
+__global__ void k_round_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = (float)in[q];
+}
+
 template <typename T>
 struct ColourStep;
 template <typename T>
@@ -225,6 +231,13 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   // the class step's shared memory can exceed the 48 KB default (set here, outside any capture)
   CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  if (lv.precision == CAV_PREC_FP32) {
+    lv.ee_vals32 = A.alloc<float>(std::max<int64_t>(lv.ee.nnz, 1));
+    if (lv.ee.nnz) {
+      k_round_f32<<<div_up(lv.ee.nnz, 256), 256, 0, st>>>(lv.ee.nnz, lv.ee.vals, lv.ee_vals32);
+      CAV_CHECK_LAUNCH();
+    }
+  }
   lv.slot_ee = A.alloc<int2>(std::max<int64_t>(lv.big_sum_n, 1));
   if (lv.big_sum_n) {
     k_slot_rows<<<div_up(lv.big_sum_n, 256), 256, 0, st>>>(lv.big_sum_n, lv.big_dofs, NN,
@@ -269,6 +282,7 @@ struct ColourStep {
   const int64_t* rowptr;
   const int* cols;
   const double* vals;
+  const float* vals32;   // E_E values rounded to FP32 (FP32-inverse levels)
   const int4* jobs;      // this class's enlarged patches
   const int64_t* job_inv;
   int nbig;
@@ -295,25 +309,44 @@ __device__ inline void cluster_arrive_release() { asm volatile("barrier.cluster.
 __device__ inline void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 __device__ inline void prefetch_l1(const void* p) { asm volatile("prefetch.L1 [%0];" ::"l"(p)); }
 
-// Stokes row of unknown (comp, i, j) of K_E w (Eq. intro_saddle: A0 u + G p, or -D u), in the
-// form cdiag u_c + cnb (sum of the four neighbours) + (p_c - p_w) / h, seven FP64 operations;
-// the iterate is read from L2 (ld.global.cg): earlier class steps wrote it while this kernel ran.
+// Precision of a class step's local residual rows: FP64 with FP64 inverses; with FP32
+// inverses the whole local solve is an FP32 preconditioner step, so the residual rows are
+// evaluated in FP32 from the FP64 iterate (converted on load), which B300 executes about 60
+// times faster than FP64.  The iterate update stays FP64.
 template <typename T>
-__device__ inline double stokes_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
+struct ResidualType {
+  typedef float type;
+};
+template <>
+struct ResidualType<double> {
+  typedef double type;
+};
+
+// the iterate read from L2 (ld.global.cg): earlier class steps wrote it while this kernel ran
+template <typename R>
+__device__ inline R ldw(const double* p) {
+  return (R)__ldcg(p);
+}
+
+// Stokes row of unknown (comp, i, j) of K_E w (Eq. intro_saddle: A0 u + G p, or -D u), in the
+// form cdiag u_c + cnb (sum of the four neighbours) + (p_c - p_w) / h, seven operations in R.
+template <typename R, typename T>
+__device__ inline R stokes_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
   const int N = a.N, NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
   const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
   const int c = j * N + i;
   const double* p = w + 2 * NN;
+  const R ih = (R)a.ih, cnb = (R)a.cnb, cdiag = (R)a.cdiag;
   if (comp < 2) {
     const double* u = w + comp * NN;
     const int cw = (comp == 0) ? j * N + im : jm * N + i;  // the other cell of the face's gradient
-    const double nb = (__ldcg(u + j * N + ip) + __ldcg(u + j * N + im)) + (__ldcg(u + jp * N + i) + __ldcg(u + jm * N + i));
-    return fma(a.ih, __ldcg(p + c) - __ldcg(p + cw), fma(a.cnb, nb, a.cdiag * __ldcg(u + c)));
+    const R nb = (ldw<R>(u + j * N + ip) + ldw<R>(u + j * N + im)) + (ldw<R>(u + jp * N + i) + ldw<R>(u + jm * N + i));
+    return mad(ih, ldw<R>(p + c) - ldw<R>(p + cw), mad(cnb, nb, cdiag * ldw<R>(u + c)));
   }
   const double* u = w;
   const double* v = w + NN;
-  return -((__ldcg(u + j * N + ip) - __ldcg(u + c)) + (__ldcg(v + jp * N + i) - __ldcg(v + c))) * a.ih;
+  return -((ldw<R>(u + j * N + ip) - ldw<R>(u + c)) + (ldw<R>(v + jp * N + i) - ldw<R>(v + c))) * ih;
 }
 
 // One class step.  Blocks [0, C nbig) are the clusters of the enlarged patches, the rest take
@@ -337,12 +370,13 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   constexpr int V = VL::V;
   constexpr int C = CS_CLUSTER;
   constexpr int CG = ProductShape<T>::CG, RT = ProductShape<T>::RT;
+  typedef typename ResidualType<T>::type res_t;
   const int NN = a.N * a.N;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int big_blocks = a.nbig * C;
-  pdl_trigger();
 
   if ((int)blockIdx.x >= big_blocks) {
+    pdl_trigger();
     // ---- standard cells: five lanes per cell, one Stokes row each; the shared 5 x 5 inverse
     // is applied after a shuffle of the cell's five residuals
     if (warp >= CS_STD_WARPS) return;
@@ -367,7 +401,7 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     double r = 0.0, old = 0.0;
     if (act) {
       old = __ldcg(w + k);
-      double kr = stokes_row_l2(a, w, comp, ci, cj);
+      double kr = stokes_row_l2<double>(a, w, comp, ci, cj);
       if (ro >= 0) {
         double s = 0.0;
         for (int64_t e = a.rowptr[ro]; e < a.rowptr[ro + 1]; ++e) s += a.vals[e] * __ldcg(w + a.cols[e]);
@@ -396,11 +430,11 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   acc_t* y = reinterpret_cast<acc_t*>(smem + 128 + a.slice_cap);  // [cm4]
   acc_t* recv = y + cm4;                                          // [C][CG][cm4] partials of my rows
   double* sold = reinterpret_cast<double*>(recv + C * CG * cm4);  // [cm4] iterate before the step
-  double* sb = sold + cm4;                                        // [cm4] b at my slots
-  double* ssr = sb + cm4;                                         // [cm4] row scales
-  double* ssc = ssr + cm4;                                        // [cm4] column scales
-  double* see = ssc + cm4;                                        // [cm4] E_E row sums
-  double* sst = see + cm4;                                        // [cm4] Stokes rows
+  double* ssc = sold + cm4;                                       // [cm4] column scales
+  res_t* sb = reinterpret_cast<res_t*>(ssc + cm4);                // [cm4] b at my slots
+  res_t* ssr = sb + cm4;                                          // [cm4] row scales (powers of two)
+  res_t* see = ssr + cm4;                                         // [cm4] E_E row sums
+  res_t* sst = see + cm4;                                         // [cm4] Stokes rows
   int* sk = reinterpret_cast<int*>(sst + cm4);                    // [cm4] unknowns
   int2* se = reinterpret_cast<int2*>(sk + cm4);                   // [cm4] E_E rows
   const int4 job = a.jobs[blockIdx.x / C];
@@ -429,9 +463,9 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     const int k = a.dofs[g];
     sk[s] = k;
     se[s] = a.slot_ee[g];
-    ssr[s] = a.s_r[g];
+    ssr[s] = (res_t)a.s_r[g];
     ssc[s] = a.s_c[g];
-    sb[s] = b[k];
+    sb[s] = (res_t)b[k];
   }
   __syncthreads();
   const int eg = tid / CS_EE_LANES, el = tid % CS_EE_LANES;  // E_E groups (warps 0-3)
@@ -440,7 +474,8 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
       const int2 e = se[s];
       for (int q = e.x + el; q < e.x + e.y; q += CS_EE_LANES) {
         prefetch_l1(a.cols + q);
-        prefetch_l1(a.vals + q);
+        if (sizeof(res_t) == 4) prefetch_l1(a.vals32 + q);
+        else prefetch_l1(a.vals + q);
       }
     }
   pdl_wait();
@@ -455,26 +490,26 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
       // on lanes that have run out)
       const int cnt = (e.y > el) ? (e.y - el + CS_EE_LANES - 1) / CS_EE_LANES : 0;
       const int wmax = __reduce_max_sync(0xffffffffu, cnt);
-      double acc = 0.0;
+      res_t acc = 0;
       for (int t0 = 0; t0 < wmax; t0 += CS_EE_BATCH) {
-        double vv[CS_EE_BATCH], wv[CS_EE_BATCH];
+        res_t vv[CS_EE_BATCH], wv[CS_EE_BATCH];
 #pragma unroll
         for (int t = 0; t < CS_EE_BATCH; ++t) {
           const int q = e.x + el + (t0 + t) * CS_EE_LANES;
           const bool ok = t0 + t < cnt;
-          vv[t] = ok ? a.vals[q] : 0.0;
-          wv[t] = ok ? __ldcg(w + a.cols[q]) : 0.0;
+          vv[t] = ok ? ((sizeof(res_t) == 4) ? (res_t)a.vals32[q] : (res_t)a.vals[q]) : (res_t)0;
+          wv[t] = ok ? ldw<res_t>(w + a.cols[q]) : (res_t)0;
         }
         static_assert(CS_EE_BATCH == 8, "the tail below is written for batches of eight");
         switch (min(wmax - t0, CS_EE_BATCH)) {  // warp-uniform: only the needed FMAs issue
-          case 8: acc = fma(vv[7], wv[7], acc);  // fall through
-          case 7: acc = fma(vv[6], wv[6], acc);  // fall through
-          case 6: acc = fma(vv[5], wv[5], acc);  // fall through
-          case 5: acc = fma(vv[4], wv[4], acc);  // fall through
-          case 4: acc = fma(vv[3], wv[3], acc);  // fall through
-          case 3: acc = fma(vv[2], wv[2], acc);  // fall through
-          case 2: acc = fma(vv[1], wv[1], acc);  // fall through
-          default: acc = fma(vv[0], wv[0], acc);
+          case 8: acc = mad(vv[7], wv[7], acc);  // fall through
+          case 7: acc = mad(vv[6], wv[6], acc);  // fall through
+          case 6: acc = mad(vv[5], wv[5], acc);  // fall through
+          case 5: acc = mad(vv[4], wv[4], acc);  // fall through
+          case 4: acc = mad(vv[3], wv[3], acc);  // fall through
+          case 3: acc = mad(vv[2], wv[2], acc);  // fall through
+          case 2: acc = mad(vv[1], wv[1], acc);  // fall through
+          default: acc = mad(vv[0], wv[0], acc);
         }
       }
 #pragma unroll
@@ -486,16 +521,20 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
       const int k = sk[s];
       const int comp = k / NN, cc = k % NN;
       sold[s] = __ldcg(w + k);
-      sst[s] = stokes_row_l2(a, w, comp, cc % a.N, cc / a.N);
+      sst[s] = stokes_row_l2<res_t>(a, w, comp, cc % a.N, cc / a.N);
     }
   }
   __syncthreads();
   // y = D_r (b - K_E w), K_E w = Stokes - dt E_E w (E_E rows only on velocities that have one)
   for (int s = tid; s < m; s += CS_THREADS) {
-    const double kr = (se[s].y > 0) ? sst[s] - a.dt * see[s] : sst[s];
+    const res_t kr = (se[s].y > 0) ? sst[s] - (res_t)a.dt * see[s] : sst[s];
     y[s] = (acc_t)(ssr[s] * (sb[s] - kr));
   }
   __syncthreads();
+  // Let the next class step launch now: its prologue (TMA copies of its inverse slices) then
+  // overlaps this step's product and exchange.  Triggering at entry instead lets several later
+  // classes queue their copies ahead of this step's latency-bound residual reads.
+  pdl_trigger();
   // partial product X[:, slice] y[slice]: column group cgp takes the slice's columns
   // cgp, cgp + CG, ...; each of its RT threads owns V consecutive rows per pass
   const int cgp = tid / RT, rt = tid % RT;
@@ -575,7 +614,7 @@ static size_t step_smem(int chunk_max, int slice_cap) {
   typedef typename VecLoad<T>::acc_t acc_t;
   const int cm4 = (chunk_max + 3) & ~3;
   return 128 + (size_t)slice_cap + sizeof(acc_t) * (size_t)(cm4 * (1 + CS_CLUSTER * ProductShape<T>::CG)) +
-         (size_t)cm4 * (6 * sizeof(double) + sizeof(int) + sizeof(int2));
+         (size_t)cm4 * (2 * sizeof(double) + 4 * sizeof(typename ResidualType<T>::type) + sizeof(int) + sizeof(int2));
 }
 
 template <typename T>
@@ -598,6 +637,7 @@ static void launch_step(const cav_hierarchy* H, const Level& lv, const T* inv, i
   a.rowptr = lv.ee.rowptr;
   a.cols = lv.ee.cols;
   a.vals = lv.ee.vals;
+  a.vals32 = lv.ee_vals32;
   a.jobs = lv.col_job + lv.col_big_start[k];
   a.job_inv = lv.col_inv + lv.col_big_start[k];
   a.nbig = lv.col_big_start[k + 1] - lv.col_big_start[k];

@@ -300,10 +300,6 @@ struct ColourStep {
 // which sit on the velocity slots only, over the cluster's CTAs.
 __device__ inline int slots_of(int n, int rank, int C) { return (n > rank) ? (n - rank + C - 1) / C : 0; }
 
-// Programmatic dependent launch: let the next class step start its prologue now; wait until
-// the previous step has completed and its writes are visible.
-__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ inline void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
 __device__ inline void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ inline void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }

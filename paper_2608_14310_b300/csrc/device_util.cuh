@@ -5,6 +5,14 @@
 
 namespace cav {
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization
+// may start before the kernel ahead of it in the stream has finished: pdl_trigger() lets the
+// next kernel launch, pdl_wait() blocks until the kernel ahead has completed and its writes are
+// visible.  A kernel launched that way calls pdl_wait() in each CTA before reading data an
+// earlier kernel wrote or writing data it reads.  Without a programmatic launch both are no-ops.
+__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __host__ __device__ inline int pmod(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;

@@ -213,6 +213,7 @@ namespace cav {
 // ------------------------------------------------------------------ kernels' host wrappers
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
 inline int round8(int n) { return (n + 7) & ~7; }
 
 // ib_system.cu

@@ -20,5 +20,6 @@ and no blocking, fusion or reordering:
   multigrid  RT0 / bilinear transfers, Galerkin E_E, hierarchy,
              coarsest bordered solve, V-cycle                      (Sec. 4)
   fgmres     right-preconditioned flexible GMRES                    (Sec. 5)
+  twogrid    two-grid iteration matrix and its spectrum            (Sec. 5.1, Table 1)
 """
-from . import grid, ib, patches, smoother, colouring, multigrid, fgmres  # noqa: F401
+from . import grid, ib, patches, smoother, colouring, multigrid, fgmres, twogrid  # noqa: F401

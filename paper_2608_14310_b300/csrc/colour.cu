@@ -187,6 +187,8 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   }
   const int nc = (int)cstamp.size();
   lv.n_colours = nc;
+  lv.ee_row_max = 0;
+  for (int r = 0; r < lv.ee.n_rows; ++r) lv.ee_row_max = std::max(lv.ee_row_max, (int)(rowptr[r + 1] - rowptr[r]));
   lv.colour_of_cell = colour;
   lv.col_big_start.assign(nc + 1, 0);
   lv.col_std_start.assign(nc + 1, 0);
@@ -288,6 +290,7 @@ struct ColourStep {
   int nbig;
   const int* std_list;   // this class's standard cells
   int nstd;
+  int ee_row_max;        // longest E_E row on the level (the per-slot stride of the staged rows)
   int slice_cap;         // bytes of the shared-memory slice buffer (at least one column)
   int chunk_max;         // slots per slice, upper bound over the level
   int ld_max;
@@ -303,7 +306,6 @@ __device__ inline int slots_of(int n, int rank, int C) { return (n > rank) ? (n 
 __device__ inline void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
 __device__ inline void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ inline void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
-__device__ inline void prefetch_l1(const void* p) { asm volatile("prefetch.L1 [%0];" ::"l"(p)); }
 
 // Precision of a class step's local residual rows: FP64 with FP64 inverses; with FP32
 // inverses the whole local solve is an FP32 preconditioner step, so the residual rows are
@@ -433,6 +435,9 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   res_t* sst = see + cm4;                                         // [cm4] Stokes rows
   int* sk = reinterpret_cast<int*>(sst + cm4);                    // [cm4] unknowns
   int2* se = reinterpret_cast<int2*>(sk + cm4);                   // [cm4] E_E rows
+  const int R = a.ee_row_max;
+  int* ecol = reinterpret_cast<int*>(se + cm4);                    // [cm4][R] my slots' E_E columns
+  res_t* evl = reinterpret_cast<res_t*>(ecol + cm4 * R);          // [cm4][R] and values
   const int4 job = a.jobs[blockIdx.x / C];
   const int64_t ioff = a.job_inv[blockIdx.x / C];
   const int n = job.y;
@@ -464,17 +469,23 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     sb[s] = (res_t)b[k];
   }
   __syncthreads();
+  // the slots' E_E rows (columns and values never change) staged in shared memory, so that
+  // after the wait only the iterate is gathered from L2
   const int eg = tid / CS_EE_LANES, el = tid % CS_EE_LANES;  // E_E groups (warps 0-3)
   if (tid < 128)
     for (int s = eg; s < m; s += CS_EE_SLOTS) {
       const int2 e = se[s];
-      for (int q = e.x + el; q < e.x + e.y; q += CS_EE_LANES) {
-        prefetch_l1(a.cols + q);
-        if (sizeof(res_t) == 4) prefetch_l1(a.vals32 + q);
-        else prefetch_l1(a.vals + q);
+      for (int q = el; q < e.y; q += CS_EE_LANES) {
+        ecol[s * R + q] = a.cols[e.x + q];
+        evl[s * R + q] = (sizeof(res_t) == 4) ? (res_t)a.vals32[e.x + q] : (res_t)a.vals[e.x + q];
       }
     }
   pdl_wait();
+  // Let the next class step launch now: its prologue (job and slot records, staged E_E rows,
+  // TMA copies of its inverse slices) overlaps this step's work, and it cannot run further
+  // ahead because its own trigger follows its wait for this step.  Triggering at entry
+  // instead let several later classes queue their copies ahead of this step's residual reads.
+  pdl_trigger();
   // residual rows of the slice: E_E sums on warps 0-3, Stokes rows on warps 4-7
   if (tid < 128) {
     for (int t0 = 0; t0 < m; t0 += CS_EE_SLOTS) {
@@ -491,10 +502,10 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
         res_t vv[CS_EE_BATCH], wv[CS_EE_BATCH];
 #pragma unroll
         for (int t = 0; t < CS_EE_BATCH; ++t) {
-          const int q = e.x + el + (t0 + t) * CS_EE_LANES;
+          const int q = s * R + el + (t0 + t) * CS_EE_LANES;
           const bool ok = t0 + t < cnt;
-          vv[t] = ok ? ((sizeof(res_t) == 4) ? (res_t)a.vals32[q] : (res_t)a.vals[q]) : (res_t)0;
-          wv[t] = ok ? ldw<res_t>(w + a.cols[q]) : (res_t)0;
+          vv[t] = ok ? evl[q] : (res_t)0;
+          wv[t] = ok ? ldw<res_t>(w + ecol[q]) : (res_t)0;
         }
         static_assert(CS_EE_BATCH == 8, "the tail below is written for batches of eight");
         switch (min(wmax - t0, CS_EE_BATCH)) {  // warp-uniform: only the needed FMAs issue
@@ -527,10 +538,6 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     y[s] = (acc_t)(ssr[s] * (sb[s] - kr));
   }
   __syncthreads();
-  // Let the next class step launch now: its prologue (TMA copies of its inverse slices) then
-  // overlaps this step's product and exchange.  Triggering at entry instead lets several later
-  // classes queue their copies ahead of this step's latency-bound residual reads.
-  pdl_trigger();
   // partial product X[:, slice] y[slice]: column group cgp takes the slice's columns
   // cgp, cgp + CG, ...; each of its RT threads owns V consecutive rows per pass
   const int cgp = tid / RT, rt = tid % RT;
@@ -606,11 +613,13 @@ __global__ void k_pressure_partials(int NN, const double* __restrict__ p, double
 }
 
 template <typename T>
-static size_t step_smem(int chunk_max, int slice_cap) {
+static size_t step_smem(int chunk_max, int slice_cap, int ee_row_max) {
   typedef typename VecLoad<T>::acc_t acc_t;
+  typedef typename ResidualType<T>::type res_t;
   const int cm4 = (chunk_max + 3) & ~3;
   return 128 + (size_t)slice_cap + sizeof(acc_t) * (size_t)(cm4 * (1 + CS_CLUSTER * ProductShape<T>::CG)) +
-         (size_t)cm4 * (2 * sizeof(double) + 4 * sizeof(typename ResidualType<T>::type) + sizeof(int) + sizeof(int2));
+         (size_t)cm4 * (2 * sizeof(double) + 4 * sizeof(res_t) + sizeof(int) + sizeof(int2)) +
+         (size_t)cm4 * ee_row_max * (sizeof(int) + sizeof(res_t));
 }
 
 template <typename T>
@@ -646,7 +655,9 @@ static void launch_step(const cav_hierarchy* H, const Level& lv, const T* inv, i
   a.slice_cap = std::min(a.chunk_max * col_bytes, std::max(col_bytes, (CS_SLICE_CAP / col_bytes) * col_bytes));
   a.status = H->status;
   for (int q = 0; q < 25; ++q) a.S.m[q] = lv.std_inv[q];
-  const size_t smem = step_smem<T>(a.chunk_max, a.slice_cap);
+  a.ee_row_max = lv.ee_row_max;
+  const size_t smem = step_smem<T>(a.chunk_max, a.slice_cap, a.ee_row_max);
+  CAV_REQUIRE(smem <= 200 * 1024, "coloured smoother: class step needs too much shared memory");
   const int std_blocks = div_up(a.nstd, CS_STD_CELLS);
   int grid = a.nbig * CS_CLUSTER + std_blocks;
   grid = div_up(grid, CS_CLUSTER) * CS_CLUSTER;

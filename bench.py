@@ -567,43 +567,48 @@ def main():
         plain = {"value": 1e3 / statistics.mean(pt), "unit": "solves/s", "iters": int(statistics.median(pit))}
         hier64.close()
 
-    # the other smoother on the same system and precision (the coloured multiplicative sweep on
-    # every level, one sweep per side, when the headline is additive; and the reverse)
-    other = None
+    # the other smoothers on the same system and precision: with an additive headline, the
+    # coloured multiplicative sweep (one per side) on every level and on the finest level only
+    # (additive 2+2 below); with a coloured headline, the additive form
+    others = []
     if args.precision != "bf16":
-        o_sm = "coloured" if args.smoother == "additive" else "additive"
-        o_nu = 1 if o_sm == "coloured" else DEFAULT_NU
-        ho = api.cav_setup(sysm, nu_pre=o_nu, nu_post=o_nu, alpha=args.alpha, precision=args.precision,
-                           autotune=True, smoother=o_sm)
-        for _ in range(2):
-            x.zero_()
-            api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
-        ot, oit = [], []
-        for _ in range(max(3, args.steps // 2)):
-            flush.zero_()
-            x.zero_()
+        if args.smoother == "additive":
+            variants = [("coloured", 1, 0), ("coloured", 1, 1)]
+        else:
+            variants = [("additive", DEFAULT_NU, 0)]
+        for o_sm, o_nu, o_cl in variants:
+            ho = api.cav_setup(sysm, nu_pre=o_nu, nu_post=o_nu, alpha=args.alpha, precision=args.precision,
+                               autotune=True, smoother=o_sm, coloured_levels=o_cl, nu_additive=DEFAULT_NU)
+            for _ in range(2):
+                x.zero_()
+                api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+            ot, oit = [], []
+            for _ in range(max(3, args.steps // 2)):
+                flush.zero_()
+                x.zero_()
+                s0, s1 = ev(), ev()
+                s0.record()
+                inf = api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+                s1.record()
+                torch.cuda.synchronize()
+                ot.append(s0.elapsed_time(s1))
+                oit.append(inf["iters"])
+            wo = torch.zeros_like(b)
+            for _ in range(3):
+                api.cav_sweep(ho, 0, b, wo)
             s0, s1 = ev(), ev()
             s0.record()
-            inf = api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+            for _ in range(10):
+                api.cav_sweep(ho, 0, b, wo)
             s1.record()
             torch.cuda.synchronize()
-            ot.append(s0.elapsed_time(s1))
-            oit.append(inf["iters"])
-        wo = torch.zeros_like(b)
-        for _ in range(3):
-            api.cav_sweep(ho, 0, b, wo)
-        s0, s1 = ev(), ev()
-        s0.record()
-        for _ in range(10):
-            api.cav_sweep(ho, 0, b, wo)
-        s1.record()
-        torch.cuda.synchronize()
-        o_sweep = s0.elapsed_time(s1) / 10
-        ncol = [api.cav_get_level_info(ho, l)["n_colours"] for l in range(api.cav_num_levels(ho) - 1)]
-        other = {"smoother": o_sm, "nu": o_nu, "value": 1e3 / statistics.mean(ot), "unit": "solves/s",
-                 "iters": int(statistics.median(oit)), "finest_sweep_ms": o_sweep, "colour_classes": ncol,
-                 "us_per_class_step_finest": (1e3 * o_sweep / ncol[0]) if ncol and ncol[0] else None}
-        ho.close()
+            o_sweep = s0.elapsed_time(s1) / 10
+            ncol = [api.cav_get_level_info(ho, l)["n_colours"] for l in range(api.cav_num_levels(ho) - 1)]
+            others.append({"smoother": o_sm, "coloured_levels": o_cl if o_sm == "coloured" else None, "nu": o_nu,
+                           "value": 1e3 / statistics.mean(ot), "unit": "solves/s", "iters": int(statistics.median(oit)),
+                           "finest_sweep_ms": o_sweep, "colour_classes": ncol,
+                           "us_per_class_step_finest": (1e3 * o_sweep / ncol[0]) if ncol and ncol[0] else None})
+            ho.close()
 
     li = api.cav_get_level_info(hier, 0)
     s_bytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
@@ -624,7 +629,7 @@ def main():
                    "iters": int(statistics.median(iters)), "converged": all(conv),
                    "relres_true_max": max(relres), "parallelism": f"replicas x{world}"},
         "plain_fp64": plain,
-        "other_smoother": other,
+        "other_smoothers": others,
         "setup_ms": setup_ms,
         "vcycle_ms": vcycle_ms,
         "sweep": {"level": 0, "ms": sweep_ms, "algorithmic_bytes": sweep_bytes, "gbs": sweep_gbs,

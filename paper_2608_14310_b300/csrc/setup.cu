@@ -491,13 +491,15 @@ __global__ void k_factor(LevelK L, FactorJob J, int bordered_job, int* status) {
     }
     for (int a = threadIdx.x; a < m; a += blockDim.x) colk[a] = A[(int64_t)k * ld + a];
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-      const int b = (int)(e / m), a = (int)(e % m);
-      double v;
-      if (a == k) v = rowk[b];
-      else if (b == k) v = -colk[a] * ipiv;
-      else v = A[(int64_t)b * ld + a] - colk[a] * rowk[b];
-      A[(int64_t)b * ld + a] = v;
+    // rank-one update, warps over columns and lanes over rows (coalesced, no index division)
+    for (int b = warp; b < m; b += nw) {
+      double* colp = A + (int64_t)b * ld;
+      const double rb = rowk[b];
+      if (b == k) {
+        for (int a = lane; a < m; a += 32) colp[a] = (a == k) ? rb : -colk[a] * ipiv;
+      } else {
+        for (int a = lane; a < m; a += 32) colp[a] = (a == k) ? rb : colp[a] - colk[a] * rb;
+      }
     }
     __syncthreads();
   }

@@ -72,8 +72,17 @@ __host__ __device__ constexpr int tma_max_rows() {
   return TMA_MAXPASS * 32 * TMA_CONSUMER_WARPS * VecLoad<T>::V;
 }
 
-// Persistent batched patch apply.  CTA c takes patches c, c + G, c + 2G, ... of the
-// size-descending order, with three roles:
+// The q-th patch a persistent CTA takes (q = round * G + CTA): rounds alternate direction over
+// the size-descending order, so every CTA gets a large and a small patch in each pair of
+// rounds and their loads stay balanced.
+__device__ inline int zigzag(int q, int G, int n) {
+  const int r = q / G, c = q - r * G;
+  const int len = min(G, n - r * G);
+  return (r & 1) ? r * G + (len - 1 - c) : q;
+}
+
+// Persistent batched patch apply.  CTA c takes the patches zigzag(c), zigzag(c + G), ... of
+// the size-descending order, with three roles:
 //  * warp 0, one lane (producer): streams each patch's column-major inverse -- a contiguous
 //    block of n * ld elements -- into a ring of TMA_STAGES shared-memory stages of at most
 //    TMA_CHUNK bytes (whole columns) with cp.async.bulk; "full" mbarriers carry the
@@ -122,7 +131,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
       int stage = 0;
       uint32_t phase = 0;
       for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
-        const int p = order[q];
+        const int p = order[zigzag(q, gridDim.x, n_big)];
         const int n = (int)(off[p + 1] - off[p]);
         const uint32_t col_bytes = (uint32_t)(((n + 7) & ~7) * sizeof(T));
         const int cpc = TMA_CHUNK / (int)col_bytes;
@@ -150,7 +159,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
       const int slot = t & 1;
       const uint32_t par = (uint32_t)((t >> 1) & 1);
       if (alive && !mbar_wait(&yempty[slot], par ^ 1u, status)) alive = false;
-      const int p = order[q];
+      const int p = order[zigzag(q, gridDim.x, n_big)];
       const int64_t d0 = off[p];
       const int n = (int)(off[p + 1] - d0);
       acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
@@ -167,7 +176,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   bool alive = true;
   int t = 0;
   for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
-    const int p = order[q];
+    const int p = order[zigzag(q, gridDim.x, n_big)];
     const int64_t d0 = off[p];
     const int n = (int)(off[p + 1] - d0);
     const int ld = (n + 7) & ~7;

@@ -43,8 +43,8 @@ MAXIT = 150
 # DRAM traffic of one finest-level patch-apply launch from the committed ncu capture
 # (profiles/patch_apply_membrane_N256.md), valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    # k_patch_apply_tma<float, 4, 8192> (autotuned variant 3), 289.62 MB read + 4.46 MB written
-    "fp32:d1eb399f99c15af9": 294.07e6,
+    # k_patch_apply_tma<float, 4, 8192> (autotuned variant 3), 289.63 MB read + 4.34 MB written
+    "fp32:89dc173dabe61e5e": 293.97e6,
 }
 
 

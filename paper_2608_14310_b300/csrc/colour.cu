@@ -8,15 +8,17 @@
 // Set-up (host): first-fit greedy colouring, the enlarged patches in cell order first, then
 // the standard ones, over the structural coupling of K_E (Stokes stencils plus E_E's pattern).
 //
-// One class step (one launch):
-//  * each enlarged patch is one thread-block cluster of C CTAs; CTA k owns the k-th slice of
-//    the patch's slots.  It evaluates those slots' residual rows (Stokes stencil and E_E row,
-//    eight lanes per row), stages the matching column slice of the column-major inverse in
-//    shared memory with a TMA bulk copy issued before the residual work, and forms the
-//    partial product X[:, slice] y[slice].  After a cluster barrier CTA k sums the C partials
-//    of its row slice through distributed shared memory in rank order and adds D_c times the
-//    sum to w.  The next class's inverse slices are prefetched into L2 meanwhile.
-//  * each standard cell is one thread: its five Stokes rows and the shared 5 x 5 inverse.
+// One class step (one launch, programmatic dependent launch between consecutive classes):
+//  * each enlarged patch is one thread-block cluster of C CTAs; its slots are dealt to the
+//    CTAs round-robin.  Before waiting for the previous class, a CTA loads its job and slot
+//    records, copies its slots' E_E rows into shared memory and issues TMA bulk copies of the
+//    matching columns of the column-major inverse.  After the wait it evaluates its slots'
+//    residual rows from the current iterate (E_E sums four lanes per slot, Stokes rows one per
+//    lane), forms the partial product X[:, mine] y[mine], pushes each row's partial into the
+//    shared memory of the CTA owning that row, and after one cluster barrier sums its rows'
+//    partials in a fixed order and writes w.
+//  * standard cells take five lanes each (one Stokes row per lane, the shared 5 x 5 inverse
+//    applied after a shuffle).
 #include <cooperative_groups.h>
 
 #include <algorithm>

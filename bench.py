@@ -44,7 +44,7 @@ MAXIT = 150
 # (profiles/patch_apply_membrane_N256.md), valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
     # k_patch_apply_tma<float, 4, 8192> (autotuned variant 3), 289.63 MB read + 4.34 MB written
-    "fp32:89dc173dabe61e5e": 293.97e6,
+    "fp32:256:89dc173dabe61e5e": 293.97e6,
 }
 
 
@@ -64,8 +64,9 @@ def whole_job_rate(units_per_rank: int, world: int, span_s: float) -> float:
     return world * units_per_rank / span_s
 
 
-def workload(seed_offset: int = 0):
-    rec = W.config2(256, 1e4)
+def workload(seed_offset: int = 0, N: int = 256):
+    # config 2's membrane at N = 256; the same law and ellipse at N = 512 for the scale check
+    rec = W.config2(256, 1e4) if N == 256 else W.membrane_ellipse(N, 1e4)
     if seed_offset:
         rec.seed += 7919 * seed_offset
     return rec
@@ -418,7 +419,8 @@ def main():
                     help="coloured smoother: sweeps per side on its additive levels")
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="membrane256", choices=["membrane256", "batch64", "learned", "beam512"])
+    ap.add_argument("--workload", default="membrane256",
+                    choices=["membrane256", "membrane512", "batch64", "learned", "beam512"])
     ap.add_argument("--grid", type=int, default=64, help="grid for --workload learned")
     ap.add_argument("--nsteps", type=int, default=2000, help="time steps for --workload learned")
     ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
@@ -450,7 +452,7 @@ def main():
     if args.workload == "beam512":
         return run_beam512(args, api, torch, rank)
 
-    rec = workload(rank)
+    rec = workload(rank, 512 if args.workload == "membrane512" else 256)
     n = 3 * rec.N * rec.N
     dev = torch.device("cuda", local)
     b = torch.from_numpy(rec.rhs()).to(dev)
@@ -620,7 +622,7 @@ def main():
     alg_bytes = li["enlarged_sum_n2"] * s_bytes + li["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8)
     peak, peak_kind = peaks()
     achieved = (alg_bytes / (apply_ms / n_apply * 1e-3) / 1e9) if n_apply else None
-    key = f"{args.precision}:{kernel_hash()}"
+    key = f"{args.precision}:{rec.N}:{kernel_hash()}"
     traffic = NCU_TRAFFIC.get(key) if args.smoother == "additive" else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -655,7 +657,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and rec.N == 256:
         cb = cpu_baseline_sample()
         g = golden_iters()
         it = g["iters"] if g else int(statistics.median(iters))

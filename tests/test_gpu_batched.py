@@ -73,3 +73,29 @@ def test_autotune_is_result_neutral(precision):
     assert np.array_equal(outs[0][1], outs[1][1])
     lev0 = api.cav_get_level_info(h1, 0)
     print(precision, "variant times (us):", [round(t, 1) for t in lev0["apply_us"]], "chosen", lev0["apply_variant"])
+
+
+@pytest.mark.parametrize("coloured_levels", [0, 1])
+def test_batched_coloured_equals_individual(coloured_levels):
+    # the coloured smoother (every level, or the finest only with the additive sweep below):
+    # its class steps launch with programmatic dependent launch inside each system's V-cycle
+    # graph, on the system's own stream; batching must not change a bit
+    from paper_2608_14310_b300 import api
+    recs = _systems()
+    syss, hs, bs = [], [], []
+    for rec in recs:
+        s = api.ib_setup(rec)
+        syss.append(s)
+        hs.append(api.cav_setup(s, nu_pre=1, nu_post=1, alpha=ALPHA, precision="fp32", smoother="coloured",
+                                coloured_levels=coloured_levels, nu_additive=2))
+        bs.append(rec.rhs())
+    single = []
+    for s, h, b in zip(syss, hs, bs):
+        x = torch_dev(np.zeros(b.size))
+        info = api.fgmres_solve(s, h, torch_dev(b), x, rtol=1e-10, maxit=150)
+        single.append((info, host(x)))
+    xs = [torch_dev(np.zeros(b.size)) for b in bs]
+    infos = api.fgmres_solve_batched(syss, hs, [torch_dev(b) for b in bs], xs, rtol=1e-10, maxit=150)
+    for (i1, x1), i2, x2, rec in zip(single, infos, xs, recs):
+        assert i1["iters"] == i2["iters"] and i2["converged"] == 1, rec.name
+        assert np.array_equal(x1, host(x2)), rec.name

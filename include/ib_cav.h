@@ -265,7 +265,10 @@ typedef struct {
 /* Right-preconditioned flexible GMRES with the CAV V-cycle (Sec. 5): x holds the initial
  * guess on entry and the solution on exit.  history (host, nullable, maxit + 1 doubles)
  * receives the relative residual estimate per iteration.  Returns IB_ERR_NOCONV when maxit
- * is reached above tolerance (x and info still valid).  Synchronises the stream. */
+ * is reached above tolerance, and also when an iteration's preconditioned vector is not
+ * finite (a diverging V-cycle): the solve then stops there, x holds the iterate of the
+ * iterations before it and ib_last_error() says so (x and info valid in both cases).
+ * Synchronises the stream. */
 ib_status fgmres_solve(const ib_system* sys, const cav_hierarchy* h, const double* b, double* x,
                        const fgmres_desc* desc, fgmres_info* info, double* history,
                        cudaStream_t stream);

@@ -485,7 +485,8 @@ ib_status fgmres_solve(const ib_system* s, const cav_hierarchy* h, const double*
   CAV_REQUIRE(d->rtol >= 0 && std::isfinite(d->rtol), "fgmres_solve: bad rtol");
   std::memset(info, 0, sizeof(*info));
   ib_status r = fgmres_run(s, const_cast<cav_hierarchy*>(h), b, x, d, info, history, st);
-  if (r == IB_ERR_NOCONV) set_error("fgmres_solve: maxit reached above tolerance");
+  // a stop before maxit (a non-finite preconditioned vector) already left its own message
+  if (r == IB_ERR_NOCONV && info->iters >= d->maxit) set_error("fgmres_solve: maxit reached above tolerance");
   return r;
   CAV_API_END
 }

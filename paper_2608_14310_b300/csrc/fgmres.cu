@@ -324,6 +324,7 @@ struct FgState {
   double ref = 0, beta = 0, est = 0;
   int k_done = 0, pending = -1;
   bool converged = false, active = false;
+  int nonfinite = -1;  // iteration whose residual estimate was not finite (-1: none)
   long long prof_mark[2] = {0, 0};
 };
 
@@ -414,6 +415,13 @@ static bool fg_check(FgState& s, int kk) {
   cav_hierarchy* H = s.H;
   CAV_CHECK_CUDA(cudaEventSynchronize(H->fg_ev[kk & 1]));
   if (H->prof_on) prof_collect(H, s.prof_mark[kk & 1]);
+  if (!std::isfinite(H->host_b[8 + (kk & 1)])) {
+    // the preconditioned vector of iteration kk was not finite: stop, keeping the iterate
+    // of the kk iterations before it (their Hessenberg columns are finite)
+    s.nonfinite = kk;
+    s.k_done = kk;
+    return false;
+  }
   s.k_done = kk + 1;
   s.est = H->host_b[8 + (kk & 1)] / s.ref;
   if (s.history) s.history[kk + 1] = s.est;
@@ -427,11 +435,14 @@ static bool fg_check(FgState& s, int kk) {
 static void fg_step(FgState& s, int k) {
   if (!s.active) return;
   fg_issue(s, k);
-  if (s.pending >= 0 && fg_check(s, s.pending)) {
-    s.converged = true;
-    s.active = false;
-    s.pending = -1;
-    return;
+  if (s.pending >= 0) {
+    const bool conv = fg_check(s, s.pending);
+    if (conv || s.nonfinite >= 0) {
+      s.converged = conv;
+      s.active = false;
+      s.pending = -1;
+      return;
+    }
   }
   s.pending = k;
 }
@@ -467,6 +478,11 @@ static ib_status fg_result(FgState& s) {
   s.info->iters = s.k_done;
   s.info->converged = s.converged ? 1 : 0;
   s.info->relres_est = s.est;
+  if (s.nonfinite >= 0)
+    set_error("fgmres_solve: the preconditioned vector of iteration " + std::to_string(s.nonfinite) +
+              " is not finite (the V-cycle diverged; with the coloured smoother this happens when "
+              "rounded FP32 inverses of very ill-conditioned patches make the undamped sweep "
+              "diverge: use FP64 inverses); x holds the iterate before it");
   s.info->relres_true = (s.ref > 0) ? std::sqrt(s.H->host_b[6]) / s.ref : 0.0;
   return s.converged ? IB_OK : IB_ERR_NOCONV;
 }

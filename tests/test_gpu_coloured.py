@@ -161,3 +161,20 @@ def test_hybrid_vcycle_and_fgmres():
     assert info["converged"] == 1 and io["converged"]
     assert abs(info["iters"] - io["iters"]) <= 1, (info["iters"], io["iters"])
     print(f"membrane32 hybrid: gpu its {info['iters']} oracle its {io['iters']}")
+
+
+def test_diverging_fp32_multiplicative_sweep_stops_cleanly():
+    # the stiff N = 512 beam (bending 1e3, stretching 1e5): its enlarged patches' condition
+    # numbers reach about 1e10, so FP32-rounded inverses make the undamped coloured sweep
+    # diverge; FGMRES stops at the first non-finite residual estimate, says why, and returns
+    # the last finite iterate instead of NaN
+    from paper_2608_14310_b300 import api
+    rec = W.config3()
+    sys_, h = gpu_hierarchy(rec, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, precision="fp32",
+                            smoother="coloured")
+    b = rec.rhs()
+    x = torch_dev(np.zeros(b.size))
+    info = api.fgmres_solve(sys_, h, torch_dev(b), x, rtol=1e-10, maxit=20)
+    assert info["converged"] == 0 and info["iters"] < 20, info
+    assert "not finite" in api._lib.ib_last_error().decode()
+    assert np.isfinite(host(x)).all()

@@ -85,6 +85,13 @@ typedef struct ib_system ib_system;
  * (Sec. 2, Eq. intro_saddle).  *out receives a new handle. */
 ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* structure,
                    cudaStream_t stream, ib_system** out);
+/* A new configuration for the same grid (a Newton iterate or the next time step, Sec. 5.3):
+ * S^n, J^n, E and E_E are rebuilt at sd's markers in place of the previous ones, which are
+ * released.  Hierarchies built on this system before the call keep the E_E they copied at
+ * set-up: they go on preconditioning with the configuration they were built from (FGMRES
+ * accepts such a lagged preconditioner) until rebuilt with cav_setup.  On failure the
+ * handle keeps its previous configuration.  Synchronises the device. */
+ib_status ib_update_structure(ib_system* sys, const ib_structure_desc* structure, cudaStream_t stream);
 /* y = K_E x on the finest grid (Eq. Eul_schur). */
 ib_status ib_apply(const ib_system* sys, const double* x, double* y, cudaStream_t stream);
 /* r = b - K_E x on the finest grid. */

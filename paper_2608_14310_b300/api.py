@@ -86,6 +86,7 @@ _sig = {
     "cav_profile": (C.c_int, [_vp, C.c_int32]),
     "cav_profile_read": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_double)]),
     "ib_setup": (C.c_int, [_P(ib_grid_desc), _P(ib_structure_desc), _vp, _P(_vp)]),
+    "ib_update_structure": (C.c_int, [_vp, _P(ib_structure_desc), _vp]),
     "ib_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "ib_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ib_destroy": (None, [_vp]),
@@ -200,6 +201,25 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+def _structure(rec):
+    X = np.ascontiguousarray(np.asarray(rec.X, dtype=np.float64).reshape(-1))
+    om = np.ascontiguousarray(np.asarray(rec.omega, dtype=np.float64))
+    Xt = getattr(rec, "X_target", None)
+    Xt = None if Xt is None else np.ascontiguousarray(np.asarray(Xt, dtype=np.float64).reshape(-1))
+    sd = ib_structure_desc(int(X.size // 2), 1 if rec.closed else 0, int(rec.law),
+                           X.ctypes.data_as(_P(C.c_double)), om.ctypes.data_as(_P(C.c_double)),
+                           float(rec.ds), float(rec.k_target), float(rec.k_stretch), float(rec.k_bend),
+                           Xt.ctypes.data_as(_P(C.c_double)) if Xt is not None else None)
+    return sd, (X, om, Xt)  # keep the arrays alive while the descriptor is used
+
+
+def ib_update_structure(sys: System, rec, stream=None):
+    """Rebuild S, J, E and E_E of `sys` at rec's markers (same grid)."""
+    sd, _keep = _structure(rec)
+    _check(_lib.ib_update_structure(sys.handle, C.byref(sd), _stream(stream)), "ib_update_structure")
+    sys.rec = rec
 
 
 def ib_setup(rec, stream=None) -> System:

@@ -127,6 +127,27 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   }
 }
 
+ib_status ib_update_structure(ib_system* s, const ib_structure_desc* sd, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(s && sd, "ib_update_structure: NULL argument");
+  int device = -1;
+  CAV_CHECK_CUDA(cudaGetDevice(&device));
+  CAV_REQUIRE(device == s->device, "ib_update_structure: the current device is not the system's device");
+  ib_grid_desc g;
+  g.N = s->N;
+  g.L = s->L;
+  g.rho = s->rho;
+  g.mu = s->mu;
+  g.dt = s->dt;
+  ib_system* fresh = nullptr;
+  const ib_status r = ib_setup(&g, sd, st, &fresh);
+  if (r != IB_OK) return r;  // the handle keeps its previous configuration
+  std::swap(*s, *fresh);
+  ib_destroy(fresh);  // now holds the previous configuration's device memory
+  return IB_OK;
+  CAV_API_END
+}
+
 static LevelOps sys_ops(const ib_system* s) {
   LevelOps o{s->N, s->h, s->rho / s->dt, s->mu, s->dt, &s->ee};
   return o;

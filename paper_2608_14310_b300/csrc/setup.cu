@@ -884,7 +884,22 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     lv.nu_pre = nu_add ? d.nu_additive : d.nu_pre;
     lv.nu_post = nu_add ? d.nu_additive : d.nu_post;
     if (l == 0) {
-      lv.ee = s->ee;  // owned by the system
+      // the hierarchy's own copy: ib_update_structure may replace the system's E_E later
+      lv.ee = s->ee;
+      lv.ee.rows = A.alloc<int>(std::max(s->ee.n_rows, 1));
+      lv.ee.rowptr = A.alloc<int64_t>(s->ee.n_rows + 1);
+      lv.ee.cols = A.alloc<int>(std::max<int64_t>(s->ee.nnz, 1));
+      lv.ee.vals = A.alloc<double>(std::max<int64_t>(s->ee.nnz, 1));
+      lv.ee.row_of = A.alloc<int>(2 * (size_t)lv.N * lv.N);
+      if (s->ee.n_rows) {
+        CAV_CHECK_CUDA(cudaMemcpyAsync(lv.ee.rows, s->ee.rows, sizeof(int) * s->ee.n_rows, cudaMemcpyDeviceToDevice, st));
+        CAV_CHECK_CUDA(cudaMemcpyAsync(lv.ee.cols, s->ee.cols, sizeof(int) * s->ee.nnz, cudaMemcpyDeviceToDevice, st));
+        CAV_CHECK_CUDA(cudaMemcpyAsync(lv.ee.vals, s->ee.vals, sizeof(double) * s->ee.nnz, cudaMemcpyDeviceToDevice, st));
+      }
+      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.ee.rowptr, s->ee.rowptr, sizeof(int64_t) * (s->ee.n_rows + 1),
+                                     cudaMemcpyDeviceToDevice, st));
+      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.ee.row_of, s->ee.row_of, sizeof(int) * 2 * (size_t)lv.N * lv.N,
+                                     cudaMemcpyDeviceToDevice, st));
     } else {
       galerkin_level(H->levels[l - 1].ee, lv.N, lv.ee, A, d_scr, st);
     }

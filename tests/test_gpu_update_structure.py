@@ -23,7 +23,8 @@ pytestmark = pytest.mark.gpu
 def test_update_structure():
     from paper_2608_14310_b300 import api
     rec1 = W.membrane_ellipse(32, 1e4)
-    rec2 = replace(rec1, X=rec1.X + np.array([0.013, -0.007]))
+    # a nearby configuration, as between Newton iterates or time steps (h = 1/32)
+    rec2 = replace(rec1, X=rec1.X + np.array([0.002, -0.001]))
     sysm = api.ib_setup(rec1)
     h_old = api.cav_setup(sysm, nu_pre=1, nu_post=1, precision="fp64", smoother="coloured")
     api.ib_update_structure(sysm, rec2)
@@ -36,8 +37,8 @@ def test_update_structure():
     b = rec2.rhs()
     xl = torch_dev(np.zeros(b.size))
     info = api.fgmres_solve(sysm, h_old, torch_dev(b), xl, rtol=1e-10, maxit=150)
-    assert info["converged"] == 1
-    assert np.linalg.norm(b - K2 @ host(xl)) <= 2e-10 * np.linalg.norm(b)
+    res = np.linalg.norm(b - K2 @ host(xl)) / np.linalg.norm(b)
+    assert info["converged"] == 1 and res <= 2e-10, (info, res)
     h_new = api.cav_setup(sysm, nu_pre=1, nu_post=1, precision="fp64", smoother="coloured")
     fresh = api.ib_setup(rec2)
     h_fresh = api.cav_setup(fresh, nu_pre=1, nu_post=1, precision="fp64", smoother="coloured")
@@ -46,5 +47,6 @@ def test_update_structure():
         xs = torch_dev(np.zeros(b.size))
         inf = api.fgmres_solve(s, h, torch_dev(b), xs, rtol=1e-10, maxit=150)
         outs.append((inf["iters"], host(xs)))
-    assert outs[0][0] == outs[1][0] and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][0] == outs[1][0], (outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
     print(f"lagged hierarchy: {info['iters']} its; rebuilt: {outs[0][0]} its")

@@ -22,6 +22,12 @@ Readings taken here (identical in the CUDA library):
     patch visited before it;
   * inside a class the patches are independent, so their order is immaterial; the sweep
     below visits them in ascending cell order.
+
+The same classes serve the box smoother B(b,o) (Sec. 3.1, 3.3): one patch per b x b block,
+every patch larger than five unknowns, so the visit order is the blocks' lexicographic order
+(the paper's order for its box sweep).  Its restricted injection writes only the unknowns
+of the unexpanded block, a subset of the patch, so two patches that K_E does not couple
+stay independent and the conflict relation above is unchanged (it is conservative there).
 """
 from __future__ import annotations
 
@@ -73,15 +79,22 @@ def greedy_colours(patches, pattern: sp.csr_matrix) -> np.ndarray:
     return colour
 
 
-def coloured_sweep(KE, solvers, colours, w, b, N):
-    """One multiplicative CAV sweep (Sec. 3.3) visiting the colour classes in turn, each
-    class's patches in ascending cell order: for each patch p, r_p = b_p - (K_E w)_p from the
-    current iterate, w_p += K_{E,p}^-1 r_p; then the mean pressure is removed."""
+def coloured_sweep(KE, solvers, colours, w, b, N, inject=None):
+    """One multiplicative sweep (Sec. 3.3) visiting the colour classes in turn, each class's
+    patches in ascending patch order: for each patch p, r_p = b_p - (K_E w)_p from the
+    current iterate, delta = K_{E,p}^-1 r_p, w_p += delta; then the mean pressure is removed.
+    `inject[p]` (optional) lists the slots of patch p that receive the correction (the
+    restricted injection of the box smoother, Sec. 3.3); the other slots' entries of delta
+    are dropped."""
     w = np.array(w, dtype=np.float64, copy=True)
     KE = sp.csr_matrix(KE)
     for k in range(int(colours.max()) + 1):
         for c in np.nonzero(colours == k)[0]:
             s = solvers[c]
             r_p = b[s.dofs] - KE[s.dofs] @ w
-            w[s.dofs] += s.apply(r_p)
+            d = s.apply(r_p)
+            if inject is None:
+                w[s.dofs] += d
+            else:
+                w[s.dofs[inject[c]]] += d[inject[c]]
     return smoother.remove_mean_pressure(w, N)

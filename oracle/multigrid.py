@@ -188,7 +188,7 @@ def sweep(lev: Level, w, b, mode: str = "additive", alpha: float = 1.0):
     if mode == "additive":
         return smoother.additive_sweep(lev.KE, lev.solvers, lev.theta, w, b, lev.N, alpha)
     if mode == "coloured":
-        return colouring.coloured_sweep(lev.KE, lev.solvers, level_colours(lev), w, b, lev.N)
+        return colouring.coloured_sweep(lev.KE, lev.solvers, level_colours(lev), w, b, lev.N, lev.inject)
     return smoother.multiplicative_sweep(lev.KE, lev.solvers, w, b, lev.N, lev.inject, lev.KE_csc)
 
 

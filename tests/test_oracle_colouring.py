@@ -7,7 +7,10 @@
   * independence: visiting one class's patches in reverse order gives the same bits;
   * the sweep equals the sequential multiplicative sweep of Sec. 3.3 (which the paper's
     printed iteration counts pin) run in the class-by-class patch order;
-  * the paper's membrane case converges in a count close to the printed one.
+  * the paper's membrane case converges in a count close to the printed one;
+  * the same for the box smoother B(4,2) with restricted injection: valid first-fit classes
+    over the blocks, the class-by-class sweep equal to the sequential restricted sweep in
+    class order, and the paper's target-point count.
 """
 import numpy as np
 import pytest
@@ -34,7 +37,16 @@ def _dense_coupling(lev):
 
 @pytest.mark.parametrize("mk", CASES)
 def test_classes_are_independent_and_first_fit(mk):
-    levels = multigrid.build_hierarchy(mk(), 8, factor=False)
+    _check_classes(multigrid.build_hierarchy(mk(), 8, factor=False))
+
+
+def test_box_classes_are_independent_and_first_fit():
+    # B(4,2) patches (208 unknowns each, one per 4 x 4 block): every patch is "enlarged", so
+    # the visit order is the blocks' lexicographic order
+    _check_classes(multigrid.build_hierarchy(W.beam_curve(32, 96, 1.0, 10.0), 8, "box", factor=False))
+
+
+def _check_classes(levels):
     for lev in levels[:-1]:
         col = multigrid.level_colours(lev)
         D = _dense_coupling(lev)
@@ -97,6 +109,40 @@ def test_coloured_sweep_is_the_multiplicative_sweep_in_class_order(mk):
         want = smoother.multiplicative_sweep(lev.KE, [lev.solvers[c] for c in order], w0, bl, lev.N)
         got = colouring.coloured_sweep(lev.KE, lev.solvers, col, w0, bl, lev.N)
         assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_box_coloured_sweep_is_the_restricted_multiplicative_sweep_in_class_order():
+    # restricted injection (Sec. 3.3): each box patch writes only the unknowns of its
+    # unexpanded block; the class-by-class sweep equals the sequential one in class order
+    s = W.beam_curve(32, 96, 1.0, 10.0)
+    levels = multigrid.build_hierarchy(s, 8, "box")
+    b = s.rhs()
+    for lev in levels[:-1]:
+        col = multigrid.level_colours(lev)
+        n = 3 * lev.N * lev.N
+        bl = b[:n] if n == b.size else np.random.default_rng(lev.N).uniform(-1, 1, n)
+        w0 = np.random.default_rng(lev.N + 1).uniform(-1, 1, n)
+        order = np.lexsort((np.arange(col.size), col))
+        want = smoother.multiplicative_sweep(lev.KE, [lev.solvers[c] for c in order], w0, bl, lev.N,
+                                             [lev.inject[c] for c in order])
+        got = colouring.coloured_sweep(lev.KE, lev.solvers, col, w0, bl, lev.N, lev.inject)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+        # the injection is restricted: dropping it changes the result
+        full = colouring.coloured_sweep(lev.KE, lev.solvers, col, w0, bl, lev.N)
+        assert np.linalg.norm(full - got) > 1e-3 * np.linalg.norm(got)
+
+
+def test_paper_target_box_count_with_class_order():
+    # Sec. 5.2: B(4,2) takes 8 FGMRES iterations on the target-point rows at N = 32 with its
+    # lexicographic sweep; the class-by-class order is another multiplicative ordering
+    s = W.paper_target_rows(32)
+    levels = multigrid.build_hierarchy(s, 8, "box")
+    K = levels[0].KE
+    _, info = fgmres.fgmres(lambda v: K @ v, ib.first_step_rhs(s),
+                            lambda r: multigrid.vcycle(levels, r, 1, 1, "coloured"),
+                            rtol=1e-10, maxit=150, ref="r0")
+    assert info["converged"]
+    assert abs(info["iters"] - 8) <= 3, info["iters"]
 
 
 def test_whole_domain_single_class_is_exact():

@@ -102,6 +102,28 @@ def test_box_4_2_sizes():
     assert all(len(b) == 16 + 2 * 4 * 5 for _, b in box)
 
 
+def test_box_4_2_order_and_geometry():
+    # Sec. 3.1/3.3: blocks in lexicographic order of their lower-left cells (i fastest); the
+    # patch holds the pressures of the cells within o layers of the block (periodic), the
+    # injected set those of the block itself, and every velocity of a held cell
+    N, b, o = 16, 4, 2
+    NN = N * N
+    for p, (patch, block) in enumerate(patches.box_patches(N, b, o)):
+        I, J = (p % (N // b)) * b, (p // (N // b)) * b
+        pres = patch[patch >= 2 * NN] - 2 * NN
+        want = sorted(c for c in range(NN)
+                      if ((c % N - I + o) % N) < b + 2 * o and ((c // N - J + o) % N) < b + 2 * o)
+        assert list(pres) == want
+        bp = block[block >= 2 * NN] - 2 * NN
+        assert list(bp) == sorted(c for c in range(NN) if ((c % N - I) % N) < b and ((c // N - J) % N) < b)
+        assert set(block) <= set(patch)
+        # each held cell's four faces are held
+        for c in pres:
+            i, j = c % N, c // N
+            for k in (j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i):
+                assert k in set(patch)
+
+
 def test_cav_patches_contain_their_vanka_patch_and_cover():
     s = W.membrane_ellipse(16, 1e4)
     _, pat = ib.eulerian_elasticity(s)

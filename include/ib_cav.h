@@ -118,7 +118,17 @@ ib_status ib_advect(const ib_system* sys, const double* u, double* X_next, cudaS
 
 /* -------------------------------------------------------- hierarchy (Sec. 3, Sec. 4) */
 
-typedef enum { CAV_PATCH_CAV = 0, CAV_PATCH_VANKA = 1 } cav_patch_kind;
+/* Patch family of the smoothing levels (Sec. 3):
+ *   CAV    one patch per cell, Eq. cav_patch_set;
+ *   VANKA  one standard 5-unknown patch per cell, B(1,0);
+ *   BOX    B(b,o) (ABI 3): the grid cut into b x b blocks, in lexicographic order of their
+ *          lower-left cells; each block's patch holds every unknown of the cells within o
+ *          layers of it (periodic), and its correction is injected only into the unknowns of
+ *          the unexpanded block (restricted injection, Sec. 3.3).  The box smoother is the
+ *          multiplicative one, so it needs smoother = CAV_SMOOTH_COLOURED on every level
+ *          (coloured_levels 0), FP32 or FP64 inverses, and every smoothing level with
+ *          N_l divisible by b and b + 2 o < N_l; otherwise IB_ERR_INVALID.               */
+typedef enum { CAV_PATCH_CAV = 0, CAV_PATCH_VANKA = 1, CAV_PATCH_BOX = 2 } cav_patch_kind;
 typedef enum { CAV_PREC_FP64 = 0, CAV_PREC_FP32 = 1, CAV_PREC_BF16 = 2 } cav_precision;
 /* Smoother of every level:
  *   additive  the weighted additive sweep of Eq. additive_cav_saddle (alpha, Theta = 1/count);
@@ -137,7 +147,8 @@ typedef enum { CAV_SMOOTH_ADDITIVE = 0, CAV_SMOOTH_COLOURED = 1 } cav_smoother;
  * diverge (the FP64 oracle with BF16-rounded inverses diverges the same way). */
 
 typedef struct {
-  int32_t kind;        /* cav_patch_kind: CAV (Eq. cav_patch_set) or standard Vanka B(1,0) */
+  int32_t kind;        /* cav_patch_kind: CAV (Eq. cav_patch_set), standard Vanka B(1,0)
+                          or box B(b,o)                                                    */
   int32_t coarsest_N;  /* halve while N_l / 2 >= coarsest_N (the paper uses 8)             */
   int32_t nu_pre, nu_post;  /* sweeps per level in the V-cycle                             */
   double alpha;        /* relaxation factor of Eq. additive_cav_saddle                     */
@@ -151,14 +162,18 @@ typedef struct {
                                the coarser smoothing levels use the additive sweep (0: all)  */
   int32_t nu_additive; /* coloured smoother: sweeps per side on its additive levels
                           (0: nu_pre / nu_post)                                             */
+  int32_t box_b, box_o; /* BOX patches: block size b >= 1 and overlap o >= 0 (ABI 3; the
+                           paper's comparator is B(4,2)); ignored by the other kinds      */
 } cav_desc;
 
 typedef struct cav_hierarchy cav_hierarchy;
 
 typedef struct {
   int32_t N;             /* cells per direction on this level                              */
-  int32_t n_patches;     /* one patch per cell (N^2) on smoothing levels, 1 on the coarsest */
-  int32_t n_enlarged;    /* patches that are not a standard 5-unknown Vanka patch           */
+  int32_t n_patches;     /* one patch per cell (N^2) on smoothing levels, or per block (box
+                            patches); 1 on the coarsest                                    */
+  int32_t n_enlarged;    /* patches that are not a standard 5-unknown Vanka patch (every box
+                            patch)                                                          */
   int32_t max_n;         /* largest patch size                                              */
   int64_t sum_n;         /* sum of patch sizes                                              */
   int64_t sum_n2;        /* sum of squared patch sizes                                      */
@@ -180,14 +195,15 @@ ib_status cav_setup(const ib_system* sys, const cav_desc* desc, cudaStream_t str
                     cav_hierarchy** out);
 ib_status cav_num_levels(const cav_hierarchy* h, int32_t* levels);
 ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_info* info);
-/* Host copies of the patch sets of one smoothing level in cell order c = j N + i, each
- * sorted ascending: offsets[n_patches + 1] (int64), dofs[sum_n] (int32).  Pass NULL
- * arrays to query n_patches and sum_n only. */
+/* Host copies of the patch sets of one smoothing level in cell order c = j N + i (block
+ * order for box patches), each sorted ascending: offsets[n_patches + 1] (int64),
+ * dofs[sum_n] (int32).  Pass NULL arrays to query n_patches and sum_n only. */
 ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offsets,
                            int32_t* dofs, int32_t* n_patches, int64_t* sum_n);
-/* Host copy of the colour class of every patch of one smoothing level, in cell order
- * c = j N + i (coloured smoother only): colour_of_cell[n_patches].  NULL: query *n_colours
- * only.  IB_ERR_INVALID for an additive hierarchy. */
+/* Host copy of the colour class of every patch of one smoothing level, in patch order
+ * (cell order c = j N + i, or block order for box patches; coloured smoother only):
+ * colour_of_cell[n_patches].  NULL: query *n_colours only.  IB_ERR_INVALID for an additive
+ * hierarchy. */
 ib_status cav_colour_export(const cav_hierarchy* h, int32_t level, int32_t* colour_of_cell,
                             int32_t* n_colours);
 /* Host copy of E_E on one level as CSR over all 2 N_l^2 velocity rows (columns sorted):

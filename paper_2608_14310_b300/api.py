@@ -23,7 +23,7 @@ IB_OK, IB_ERR_INVALID, IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_SINGULAR, IB_ERR_NOCONV, 
     IB_ERR_INTERNAL = range(8)
 FORCE = {"target": 0, "membrane": 1, "beam": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
-KIND = {"cav": 0, "vanka": 1}
+KIND = {"cav": 0, "vanka": 1, "box": 2}
 SMOOTHER = {"additive": 0, "coloured": 1}
 
 
@@ -50,7 +50,8 @@ class cav_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("coarsest_N", C.c_int32), ("nu_pre", C.c_int32),
                 ("nu_post", C.c_int32), ("alpha", C.c_double), ("precision", C.c_int32),
                 ("autotune", C.c_int32), ("krylov_capacity", C.c_int32), ("smoother", C.c_int32),
-                ("coloured_levels", C.c_int32), ("nu_additive", C.c_int32)]
+                ("coloured_levels", C.c_int32), ("nu_additive", C.c_int32), ("box_b", C.c_int32),
+                ("box_o", C.c_int32)]
 
 
 class cav_level_info(C.Structure):
@@ -272,17 +273,19 @@ def ib_advect(sys: System, u, stream=None) -> np.ndarray:
 
 def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=1.0,
               precision="fp64", autotune=False, krylov_capacity=0, smoother="additive",
-              coloured_levels=0, nu_additive=0, stream=None) -> Hierarchy:
+              coloured_levels=0, nu_additive=0, box=(4, 2), stream=None) -> Hierarchy:
     """smoother: "additive" on every level, or "coloured" on the `coloured_levels` finest levels
-    (0: all) with the additive sweep (nu_additive sweeps per side, 0: nu_pre/nu_post) below."""
+    (0: all) with the additive sweep (nu_additive sweeps per side, 0: nu_pre/nu_post) below.
+    kind "box": B(b, o) patches, box = (b, o), with restricted injection (coloured smoother on
+    every level)."""
     d = cav_desc(KIND[kind], int(coarsest_N), int(nu_pre), int(nu_post), float(alpha), PRECISION[precision],
                  1 if autotune else 0, int(krylov_capacity), SMOOTHER[smoother], int(coloured_levels),
-                 int(nu_additive))
+                 int(nu_additive), int(box[0]), int(box[1]))
     out = _vp()
     _check(_lib.cav_setup(sys.handle, C.byref(d), _stream(stream), C.byref(out)), "cav_setup")
     return Hierarchy(out, sys, dict(kind=kind, coarsest_N=coarsest_N, nu_pre=nu_pre, nu_post=nu_post,
                                     alpha=alpha, precision=precision, autotune=autotune, smoother=smoother,
-                                    coloured_levels=coloured_levels, nu_additive=nu_additive))
+                                    coloured_levels=coloured_levels, nu_additive=nu_additive, box=tuple(box)))
 
 
 def cav_num_levels(h: Hierarchy) -> int:
@@ -311,9 +314,9 @@ def cav_patch_export(h: Hierarchy, level: int):
 
 
 def cav_colour_export(h: Hierarchy, level: int) -> np.ndarray:
-    """Colour class of every patch of a smoothing level, in cell order (coloured smoother)."""
+    """Colour class of every patch of a smoothing level, in patch order (coloured smoother)."""
     info = cav_get_level_info(h, level)
-    out = np.zeros(info["N"] ** 2, dtype=np.int32)
+    out = np.zeros(info["n_patches"], dtype=np.int32)
     nc = C.c_int32()
     _check(_lib.cav_colour_export(h.handle, level, _vp(out.ctypes.data), C.byref(nc)), "cav_colour_export")
     return out

@@ -42,7 +42,7 @@ using namespace cav;
 extern "C" {
 
 const char* ib_last_error(void) { return g_last_error.c_str(); }
-int ib_abi_version(void) { return 2; }
+int ib_abi_version(void) { return 3; }
 int64_t ib_launch_count(void) { return g_launches.load(); }
 
 ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaStream_t st, ib_system** out) {
@@ -232,7 +232,14 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
   cav_hierarchy* H = nullptr;
   try {
     CAV_REQUIRE(s && d, "cav_setup: NULL argument");
-    CAV_REQUIRE(d->kind == CAV_PATCH_CAV || d->kind == CAV_PATCH_VANKA, "cav_setup: unknown patch kind");
+    CAV_REQUIRE(d->kind == CAV_PATCH_CAV || d->kind == CAV_PATCH_VANKA || d->kind == CAV_PATCH_BOX,
+                "cav_setup: unknown patch kind");
+    if (d->kind == CAV_PATCH_BOX) {
+      CAV_REQUIRE(d->smoother == CAV_SMOOTH_COLOURED && d->coloured_levels == 0,
+                  "cav_setup: box patches use the multiplicative (coloured) smoother on every level");
+      CAV_REQUIRE(d->box_b >= 1 && d->box_o >= 0 && d->box_b + 2 * d->box_o <= 16,
+                  "cav_setup: box patches need b >= 1, o >= 0 and b + 2 o <= 16");
+    }
     CAV_REQUIRE(d->coarsest_N >= 2, "cav_setup: coarsest_N must be >= 2");
     CAV_REQUIRE(d->nu_pre >= 0 && d->nu_post >= 0 && d->nu_pre + d->nu_post >= 1,
                 "cav_setup: need at least one sweep per level");
@@ -294,10 +301,10 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
     info->sum_n = 3 * NN;
     info->sum_n2 = 9 * NN * NN;
   } else {
-    const int64_t nstd = NN - lv.n_big;
-    info->n_patches = (int32_t)NN;
+    const int64_t nstd = lv.box ? 0 : NN - lv.n_big;
+    info->n_patches = (int32_t)(lv.box ? lv.n_big : NN);
     info->n_enlarged = lv.n_big;
-    info->max_n = std::max(lv.big_max_n, 5);
+    info->max_n = lv.box ? lv.big_max_n : std::max(lv.big_max_n, 5);
     info->sum_n = lv.big_sum_n + 5 * nstd;
     info->sum_n2 = lv.big_sum_n2 + 25 * nstd;
     info->enlarged_sum_n = lv.big_sum_n;
@@ -318,10 +325,18 @@ ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offse
   const Level& lv = level_of(h, level);
   CAV_REQUIRE(!lv.coarsest, "cav_patch_export: the coarsest level has no patches");
   const int N = lv.N, NN = N * N;
-  const int64_t total = lv.big_sum_n + 5LL * (NN - lv.n_big);
-  if (n_patches) *n_patches = NN;
+  const int64_t total = lv.big_sum_n + (lv.box ? 0 : 5LL * (NN - lv.n_big));
+  if (n_patches) *n_patches = lv.box ? lv.n_big : NN;
   if (sum_n) *sum_n = total;
   if (!offsets || !dofs) return IB_OK;
+  if (lv.box) {  // one patch per block, every one stored explicitly
+    std::vector<int64_t> off(lv.n_big + 1);
+    CAV_CHECK_CUDA(cudaMemcpy(off.data(), lv.big_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost));
+    for (int p = 0; p <= lv.n_big; ++p) offsets[p] = off[p];
+    if (lv.big_sum_n)
+      CAV_CHECK_CUDA(cudaMemcpy(dofs, lv.big_dofs, sizeof(int) * lv.big_sum_n, cudaMemcpyDeviceToHost));
+    return IB_OK;
+  }
   std::vector<uint8_t> big(NN);
   std::vector<int> cells(lv.n_big);
   std::vector<int64_t> off(lv.n_big + 1);

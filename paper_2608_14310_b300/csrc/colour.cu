@@ -86,13 +86,19 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   }
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
 
-  // enlarged-patch index of each cell; unknowns of a cell's patch
-  std::vector<int> pidx(NN, -1);
-  for (int c = 0, q = 0; c < NN; ++c)
-    if (big[c]) pidx[c] = q++;
+  // units: the cells (CAV / Vanka patches), or the blocks (box patches, all enlarged)
+  const bool box = lv.box;
+  const int nunits = box ? lv.n_big : NN;
+  // enlarged-patch index of each unit; unknowns of a unit's patch
+  std::vector<int> pidx(nunits, -1);
+  if (box) std::iota(pidx.begin(), pidx.end(), 0);
+  else
+    for (int c = 0, q = 0; c < NN; ++c)
+      if (big[c]) pidx[c] = q++;
+  auto is_big = [&](int c) { return box || big[c] != 0; };
   int stdbuf[5];
   auto patch = [&](int c, const int*& ptr, int& len) {
-    if (big[c]) {
+    if (is_big(c)) {
       const int q = pidx[c];
       ptr = bd.data() + off[q];
       len = (int)(off[q + 1] - off[q]);
@@ -107,9 +113,9 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
       len = 5;
     }
   };
-  // holders: for every unknown, the cells whose patch holds it (ascending)
+  // holders: for every unknown, the units whose patch holds it (ascending)
   std::vector<int> hoff(n + 1, 0);
-  for (int c = 0; c < NN; ++c) {
+  for (int c = 0; c < nunits; ++c) {
     const int* ptr;
     int len;
     patch(c, ptr, len);
@@ -119,21 +125,21 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   std::vector<int> hold(hoff[n]);
   {
     std::vector<int> cur(hoff.begin(), hoff.end() - 1);
-    for (int c = 0; c < NN; ++c) {
+    for (int c = 0; c < nunits; ++c) {
       const int* ptr;
       int len;
       patch(c, ptr, len);
       for (int t = 0; t < len; ++t) hold[cur[ptr[t]]++] = c;
     }
   }
-  // first fit in visit order
+  // first fit in visit order: enlarged patches in unit order, then standard ones
   std::vector<int> order;
-  order.reserve(NN);
-  for (int c = 0; c < NN; ++c)
-    if (big[c]) order.push_back(c);
-  for (int c = 0; c < NN; ++c)
-    if (!big[c]) order.push_back(c);
-  std::vector<int> colour(NN, -1), dstamp(n, -1), cstamp;
+  order.reserve(nunits);
+  for (int c = 0; c < nunits; ++c)
+    if (is_big(c)) order.push_back(c);
+  for (int c = 0; c < nunits; ++c)
+    if (!is_big(c)) order.push_back(c);
+  std::vector<int> colour(nunits, -1), dstamp(n, -1), cstamp;
   std::vector<int> reach;
   reach.reserve(8192);
   auto wrap = [N](int a) { return a < 0 ? a + N : (a >= N ? a - N : a); };
@@ -191,20 +197,22 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   lv.n_colours = nc;
   lv.ee_row_max = 0;
   for (int r = 0; r < lv.ee.n_rows; ++r) lv.ee_row_max = std::max(lv.ee_row_max, (int)(rowptr[r + 1] - rowptr[r]));
+  check_colour_step(lv);
   lv.colour_of_cell = colour;
   lv.col_big_start.assign(nc + 1, 0);
   lv.col_std_start.assign(nc + 1, 0);
-  for (int c = 0; c < NN; ++c) ++(big[c] ? lv.col_big_start : lv.col_std_start)[colour[c] + 1];
+  for (int c = 0; c < nunits; ++c) ++(is_big(c) ? lv.col_big_start : lv.col_std_start)[colour[c] + 1];
   for (int k = 0; k < nc; ++k) {
     lv.col_big_start[k + 1] += lv.col_big_start[k];
     lv.col_std_start[k + 1] += lv.col_std_start[k];
   }
-  std::vector<int> hb(lv.n_big), hs(NN - lv.n_big);
+  const int nstd = nunits - lv.n_big;
+  std::vector<int> hb(lv.n_big), hs(nstd);
   {
     std::vector<int> cb(lv.col_big_start.begin(), lv.col_big_start.end() - 1);
     std::vector<int> cs(lv.col_std_start.begin(), lv.col_std_start.end() - 1);
-    for (int c = 0; c < NN; ++c) {
-      if (big[c]) hb[cb[colour[c]]++] = pidx[c];
+    for (int c = 0; c < nunits; ++c) {
+      if (is_big(c)) hb[cb[colour[c]]++] = pidx[c];
       else hs[cs[colour[c]]++] = c;
     }
   }
@@ -229,9 +237,9 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     }
     CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   }
-  lv.col_std = A.alloc<int>(std::max(NN - lv.n_big, 1));
-  if (NN - lv.n_big)
-    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_std, hs.data(), sizeof(int) * (NN - lv.n_big), cudaMemcpyHostToDevice, st));
+  lv.col_std = A.alloc<int>(std::max(nstd, 1));
+  if (nstd)
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_std, hs.data(), sizeof(int) * nstd, cudaMemcpyHostToDevice, st));
   // the class step's shared memory can exceed the 48 KB default (set here, outside any capture)
   CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -287,6 +295,7 @@ struct ColourStep {
   const int* cols;
   const double* vals;
   const float* vals32;   // E_E values rounded to FP32 (FP32-inverse levels)
+  const uint8_t* inject; // box patches: 1 where a slot receives its correction; null: every slot
   const int4* jobs;      // this class's enlarged patches
   const int64_t* job_inv;
   int nbig;
@@ -601,7 +610,8 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     acc_t sum = 0;
 #pragma unroll
     for (int q = 0; q < C * CG; ++q) sum += recv[q * cm4 + s];
-    w[sk[s]] = sold[s] + ssc[s] * (double)sum;
+    // restricted injection (box patches): only the unexpanded block's unknowns are written
+    if (a.inject == nullptr || a.inject[d0 + rank + C * s]) w[sk[s]] = sold[s] + ssc[s] * (double)sum;
   }
 }
 
@@ -622,6 +632,34 @@ static size_t step_smem(int chunk_max, int slice_cap, int ee_row_max) {
   return 128 + (size_t)slice_cap + sizeof(acc_t) * (size_t)(cm4 * (1 + CS_CLUSTER * ProductShape<T>::CG)) +
          (size_t)cm4 * (2 * sizeof(double) + 4 * sizeof(res_t) + sizeof(int) + sizeof(int2)) +
          (size_t)cm4 * ee_row_max * (sizeof(int) + sizeof(res_t));
+}
+
+// Slice layout of a level's class steps: padded column length, slots per CTA, bytes of the
+// staged inverse slice, and the dynamic shared memory that follows from them.
+struct StepShape {
+  int ld_max, chunk_max, slice_cap;
+  size_t smem;
+};
+template <typename T>
+static StepShape step_shape(const Level& lv) {
+  StepShape sh;
+  const int max_n = std::max(lv.big_max_n, 1);
+  sh.ld_max = round8(max_n);
+  sh.chunk_max = (max_n + CS_CLUSTER - 1) / CS_CLUSTER;
+  const int col_bytes = sh.ld_max * (int)sizeof(T);
+  sh.slice_cap = std::min(sh.chunk_max * col_bytes, std::max(col_bytes, (CS_SLICE_CAP / col_bytes) * col_bytes));
+  sh.smem = step_smem<T>(sh.chunk_max, sh.slice_cap, lv.ee_row_max);
+  return sh;
+}
+
+void check_colour_step(const Level& lv) {
+  const bool f32 = lv.precision == CAV_PREC_FP32;
+  const int max_n = f32 ? CS_MAXPASS * ProductShape<float>::RT * VecLoad<float>::V
+                        : CS_MAXPASS * ProductShape<double>::RT * VecLoad<double>::V;
+  CAV_REQUIRE(lv.big_max_n <= max_n, "coloured smoother: patch too large");
+  const size_t smem = f32 ? step_shape<float>(lv).smem : step_shape<double>(lv).smem;
+  CAV_REQUIRE(smem <= 200 * 1024, "coloured smoother: class step needs too much shared memory "
+                                  "(patches too large, or E_E rows too long)");
 }
 
 template <typename T>
@@ -645,20 +683,20 @@ static void launch_step(const cav_hierarchy* H, const Level& lv, const T* inv, i
   a.cols = lv.ee.cols;
   a.vals = lv.ee.vals;
   a.vals32 = lv.ee_vals32;
+  a.inject = lv.inject;
   a.jobs = lv.col_job + lv.col_big_start[k];
   a.job_inv = lv.col_inv + lv.col_big_start[k];
   a.nbig = lv.col_big_start[k + 1] - lv.col_big_start[k];
   a.std_list = lv.col_std + lv.col_std_start[k];
   a.nstd = lv.col_std_start[k + 1] - lv.col_std_start[k];
-  const int max_n = std::max(lv.big_max_n, 1);
-  a.ld_max = round8(max_n);
-  a.chunk_max = (max_n + CS_CLUSTER - 1) / CS_CLUSTER;
-  const int col_bytes = a.ld_max * (int)sizeof(T);
-  a.slice_cap = std::min(a.chunk_max * col_bytes, std::max(col_bytes, (CS_SLICE_CAP / col_bytes) * col_bytes));
+  const StepShape sh = step_shape<T>(lv);
+  a.ld_max = sh.ld_max;
+  a.chunk_max = sh.chunk_max;
+  a.slice_cap = sh.slice_cap;
   a.status = H->status;
   for (int q = 0; q < 25; ++q) a.S.m[q] = lv.std_inv[q];
   a.ee_row_max = lv.ee_row_max;
-  const size_t smem = step_smem<T>(a.chunk_max, a.slice_cap, a.ee_row_max);
+  const size_t smem = sh.smem;
   CAV_REQUIRE(smem <= 200 * 1024, "coloured smoother: class step needs too much shared memory");
   const int std_blocks = div_up(a.nstd, CS_STD_CELLS);
   int grid = a.nbig * CS_CLUSTER + std_blocks;

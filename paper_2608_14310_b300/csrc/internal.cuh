@@ -87,6 +87,7 @@ struct Level {
   double h = 0, rho_dt = 0, mu = 0, dt = 0;
   bool coarsest = false;
   bool coloured = false;         // this level smooths with the class-by-class multiplicative sweep
+  bool box = false;              // box patches B(b,o): one per block, all enlarged, restricted injection
   int nu_pre = 0, nu_post = 0;   // sweeps per side in the V-cycle
   EECsr ee;
 
@@ -100,6 +101,8 @@ struct Level {
   int* big_dofs = nullptr;       // [big_sum_n] sorted global indices
   int64_t* inv_off = nullptr;    // [n_big + 1] element offsets of each inverse (ld * n)
   int* order = nullptr;          // [n_big] patches by descending size (launch order)
+  uint8_t* inject = nullptr;     // [big_sum_n] box patches: 1 where the slot receives its
+                                 // correction (the unexpanded block); null otherwise
   double* s_r = nullptr;         // [big_sum_n] row scales (power of two)
   double* s_c = nullptr;         // [big_sum_n] column scales
   double* inv64 = nullptr;       // [inv_elems] equilibrated inverses, column-major, ld = round8(n)
@@ -118,7 +121,7 @@ struct Level {
   // colour classes for the multiplicative sweep (smoother CAV_SMOOTH_COLOURED): patches of
   // one class share no unknown and no entry of K_E couples them, so a class is solved at once
   int n_colours = 0;
-  std::vector<int> colour_of_cell;   // [N^2] host copy, for export
+  std::vector<int> colour_of_cell;   // [N^2, or n_big for box patches] host copy, for export
   std::vector<int> col_big_start;    // [n_colours + 1] offsets into col_job / col_inv
   std::vector<int> col_std_start;    // [n_colours + 1] offsets into col_std
   int4* col_job = nullptr;           // [n_big] enlarged patches class by class: (p, n, slot offset, 0)
@@ -243,6 +246,8 @@ void build_levels(cav_hierarchy* H, cudaStream_t st);
 
 // colour.cu: colour classes (set-up) and the class-by-class multiplicative sweep
 void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st);
+// fails (IB_ERR_INVALID) when the level's class steps would not fit in shared memory
+void check_colour_step(const Level& lv);
 void coloured_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
                     double* partial, bool remove_mean, bool profile, cudaStream_t st);
 // p -= mean(p) over the N^2 cells, partial holding at least ceil(N^2 / 256) doubles

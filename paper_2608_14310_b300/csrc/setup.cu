@@ -1,5 +1,5 @@
-// Hierarchy set-up (Sec. 3.2, 3.3, 4): Galerkin E_E on coarse levels, CAV patch sets,
-// extraction of local matrices, one-pass equilibration, inverses, and the transpose
+// Hierarchy set-up (Sec. 3.2, 3.3, 4): Galerkin E_E on coarse levels, CAV (or box) patch
+// sets, extraction of local matrices, one-pass equilibration, inverses, and the transpose
 // incidence used by the scatter of the additive sweep.
 #include <algorithm>
 #include <numeric>
@@ -616,51 +616,111 @@ static void check_status(cav_hierarchy* H, cudaStream_t st, const char* where) {
   }
 }
 
+// ------------------------------------------------------------------ box patch sets
+
+// B(b,o) patches (Sec. 3.1): the blocks in lexicographic order of their lower-left cells
+// (I, J), i fastest; a block's patch holds every unknown of the cells (I + r, J + s),
+// -o <= r, s <= b + o - 1 (periodic), ascending; inject marks the unknowns of the unexpanded
+// block's cells (restricted injection, Sec. 3.3).  With b + 2 o < N no unknown repeats.
+// Index arithmetic only, on the host.
+static void box_sets(int N, int b, int o, std::vector<int>& cells, std::vector<int>& sizes, std::vector<int>& dofs,
+                     std::vector<uint8_t>& inject) {
+  const int NN = N * N;
+  std::vector<std::pair<int, uint8_t>> buf;
+  for (int J = 0; J < N; J += b)
+    for (int I = 0; I < N; I += b) {
+      buf.clear();
+      // u faces (i, j) sit between cells (i - 1, j) and (i, j): columns -o .. b + o
+      for (int s = -o; s < b + o; ++s)
+        for (int r = -o; r <= b + o; ++r)
+          buf.push_back({pmod(J + s, N) * N + pmod(I + r, N), (uint8_t)(r >= 0 && r <= b && s >= 0 && s < b)});
+      // v faces (i, j) sit between cells (i, j - 1) and (i, j): rows -o .. b + o
+      for (int s = -o; s <= b + o; ++s)
+        for (int r = -o; r < b + o; ++r)
+          buf.push_back({NN + pmod(J + s, N) * N + pmod(I + r, N), (uint8_t)(r >= 0 && r < b && s >= 0 && s <= b)});
+      for (int s = -o; s < b + o; ++s)
+        for (int r = -o; r < b + o; ++r)
+          buf.push_back({2 * NN + pmod(J + s, N) * N + pmod(I + r, N), (uint8_t)(r >= 0 && r < b && s >= 0 && s < b)});
+      std::sort(buf.begin(), buf.end());
+      cells.push_back(J * N + I);
+      sizes.push_back((int)buf.size());
+      for (const auto& q : buf) {
+        dofs.push_back(q.first);
+        inject.push_back(q.second);
+      }
+    }
+}
+
 static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   Arena& A = H->arena;
   Arena scratch;
   const int N = lv.N, NN = N * N;
   const LevelK LK = level_k(lv);
-  // 1. enlarged cells
   lv.cell_big = A.alloc<uint8_t>(NN);
-  int* flag = scratch.alloc<int>(NN);
-  int64_t* pos = scratch.alloc<int64_t>(NN + 1);
-  k_cell_flags<<<div_up(NN, 256), 256, 0, st>>>(N, H->desc.kind == CAV_PATCH_CAV ? 1 : 0, lv.ee.row_of,
-                                               lv.ee.rowptr, lv.ee.cols, lv.cell_big, flag);
-  CAV_CHECK_LAUNCH();
-  exclusive_scan(flag, pos, NN, st, &scratch);
   int64_t nbig = 0;
-  CAV_CHECK_CUDA(cudaMemcpyAsync(&nbig, pos + NN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-  lv.n_big = (int)nbig;
-  lv.big_cell = A.alloc<int>(nbig);
-  k_compact_cells<<<div_up(NN, 256), 256, 0, st>>>(NN, flag, pos, lv.big_cell);
-  CAV_CHECK_LAUNCH();
-  // 2. patch sets (count, scan, write)
-  const int W = lv.ee.W;
-  const int Wc = W + 2, Wd = W + 3;
-  const int lenC = (2 * Wc + 1 >= N) ? N : 2 * Wc + 1;
-  const int lenD = (2 * Wd + 1 >= N) ? N : 2 * Wd + 1;
-  const int per_warp = lenC * lenC + 3 * lenD * lenD;
-  int warps = 8;
-  while (warps > 1 && (size_t)warps * per_warp > 96 * 1024) warps >>= 1;
-  const size_t smem = (size_t)warps * per_warp;
-  CAV_REQUIRE(smem <= 200 * 1024, "CAV patch window too large");
-  if (smem > 48 * 1024)
-    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_cav_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int* sizes = scratch.alloc<int>(nbig + 1);
-  lv.big_off = A.alloc<int64_t>(nbig + 1);
-  if (nbig > 0) {
-    k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
-                                                              lv.ee.rowptr, lv.ee.cols, sizes, nullptr,
-                                                              nullptr, 0, H->status);
+  std::vector<int> hsizes;
+  std::vector<int> box_dofs;
+  int cav_set_warps = 1;
+  size_t cav_set_smem = 0;
+  if (lv.box) {
+    // 1-2. box patches: every one is enlarged, no cell keeps a standard patch
+    std::vector<int> cells;
+    std::vector<uint8_t> inj;
+    box_sets(N, H->desc.box_b, H->desc.box_o, cells, hsizes, box_dofs, inj);
+    nbig = (int64_t)cells.size();
+    lv.n_big = (int)nbig;
+    std::vector<int64_t> off(nbig + 1, 0);
+    for (int64_t p = 0; p < nbig; ++p) off[p + 1] = off[p] + hsizes[p];
+    lv.big_cell = A.alloc<int>(nbig);
+    lv.big_off = A.alloc<int64_t>(nbig + 1);
+    lv.inject = A.alloc<uint8_t>(box_dofs.size());
+    CAV_CHECK_CUDA(cudaMemsetAsync(lv.cell_big, 0, NN, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_cell, cells.data(), sizeof(int) * nbig, cudaMemcpyHostToDevice, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_off, off.data(), sizeof(int64_t) * (nbig + 1), cudaMemcpyHostToDevice, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.inject, inj.data(), inj.size(), cudaMemcpyHostToDevice, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  } else {
+    // 1. enlarged cells
+    int* flag = scratch.alloc<int>(NN);
+    int64_t* pos = scratch.alloc<int64_t>(NN + 1);
+    k_cell_flags<<<div_up(NN, 256), 256, 0, st>>>(N, H->desc.kind == CAV_PATCH_CAV ? 1 : 0, lv.ee.row_of,
+                                                 lv.ee.rowptr, lv.ee.cols, lv.cell_big, flag);
     CAV_CHECK_LAUNCH();
+    exclusive_scan(flag, pos, NN, st, &scratch);
+    CAV_CHECK_CUDA(cudaMemcpyAsync(&nbig, pos + NN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    lv.n_big = (int)nbig;
+    lv.big_cell = A.alloc<int>(nbig);
+    k_compact_cells<<<div_up(NN, 256), 256, 0, st>>>(NN, flag, pos, lv.big_cell);
+    CAV_CHECK_LAUNCH();
+    // 2. CAV patch sets (count, scan; the write follows below)
+    const int W = lv.ee.W;
+    const int Wc = W + 2, Wd = W + 3;
+    const int lenC = (2 * Wc + 1 >= N) ? N : 2 * Wc + 1;
+    const int lenD = (2 * Wd + 1 >= N) ? N : 2 * Wd + 1;
+    const int per_warp = lenC * lenC + 3 * lenD * lenD;
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * per_warp > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * per_warp;
+    CAV_REQUIRE(smem <= 200 * 1024, "CAV patch window too large");
+    if (smem > 48 * 1024)
+      CAV_CHECK_CUDA(cudaFuncSetAttribute(k_cav_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cav_set_warps = warps;
+    cav_set_smem = smem;
+    int* sizes = scratch.alloc<int>(nbig + 1);
+    lv.big_off = A.alloc<int64_t>(nbig + 1);
+    if (nbig > 0) {
+      k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
+                                                                lv.ee.rowptr, lv.ee.cols, sizes, nullptr,
+                                                                nullptr, 0, H->status);
+      CAV_CHECK_LAUNCH();
+    }
+    exclusive_scan(sizes, lv.big_off, nbig, st, &scratch);
+    hsizes.resize(nbig);
+    if (nbig > 0)
+      CAV_CHECK_CUDA(cudaMemcpyAsync(hsizes.data(), sizes, sizeof(int) * nbig, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   }
-  exclusive_scan(sizes, lv.big_off, nbig, st, &scratch);
-  std::vector<int> hsizes(nbig);
-  if (nbig > 0)
-    CAV_CHECK_CUDA(cudaMemcpyAsync(hsizes.data(), sizes, sizeof(int) * nbig, cudaMemcpyDeviceToHost, st));
-  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   int64_t sum_n = 0, sum_n2 = 0, inv_elems = 0;
   int max_n = 0;
   std::vector<int64_t> hinv_off(nbig + 1, 0), hmat_off(nbig + 2, 0);
@@ -676,13 +736,16 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   lv.big_max_n = max_n;
   lv.inv_elems = inv_elems = hinv_off[nbig];
   lv.big_dofs = A.alloc<int>(sum_n + 5);  // + 5: the standard patch appended for factorisation
-  if (nbig > 0) {
-    k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
-                                                              lv.ee.rowptr, lv.ee.cols, sizes, lv.big_off,
-                                                              lv.big_dofs, 1, H->status);
+  if (lv.box) {
+    if (sum_n > 0)
+      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs, box_dofs.data(), sizeof(int) * sum_n, cudaMemcpyHostToDevice, st));
+  } else if (nbig > 0) {
+    k_cav_sets<<<div_up(nbig, cav_set_warps), cav_set_warps * 32, cav_set_smem, st>>>(
+        N, lv.ee.W, (int)nbig, lv.big_cell, lv.ee.row_of, lv.ee.rowptr, lv.ee.cols, nullptr, lv.big_off,
+        lv.big_dofs, 1, H->status);
     CAV_CHECK_LAUNCH();
   }
-  check_status(H, st, "cav patch sets");
+  check_status(H, st, "patch sets");
   // launch order: descending size
   std::vector<int> order(nbig);
   std::iota(order.begin(), order.end(), 0);
@@ -880,6 +943,10 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     const cav_desc& d = H->desc;
     lv.coloured = !lv.coarsest && d.smoother == CAV_SMOOTH_COLOURED &&
                   (d.coloured_levels <= 0 || (int)l < d.coloured_levels);
+    lv.box = !lv.coarsest && d.kind == CAV_PATCH_BOX;
+    if (lv.box)
+      CAV_REQUIRE(lv.N % d.box_b == 0 && d.box_b + 2 * d.box_o < lv.N,
+                  "cav_setup: box patches B(b,o) need every smoothing level's N divisible by b and b + 2 o < N");
     const bool nu_add = d.smoother == CAV_SMOOTH_COLOURED && !lv.coloured && d.nu_additive > 0;
     lv.nu_pre = nu_add ? d.nu_additive : d.nu_pre;
     lv.nu_post = nu_add ? d.nu_additive : d.nu_post;

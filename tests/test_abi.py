@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(api):
 
 
 def test_abi_version(api):
-    assert api._lib.ib_abi_version() == 2
+    assert api._lib.ib_abi_version() == 3
 
 
 def test_null_arguments_are_rejected_without_a_device(api):

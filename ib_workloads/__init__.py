@@ -80,7 +80,8 @@ def _curve_perimeter(fn, samples: int = 1 << 16) -> float:
 LAW_TARGET = 0
 LAW_MEMBRANE = 1
 LAW_BEAM = 2
-LAW_NAMES = {LAW_TARGET: "target", LAW_MEMBRANE: "membrane", LAW_BEAM: "beam"}
+LAW_FIBER = 3
+LAW_NAMES = {LAW_TARGET: "target", LAW_MEMBRANE: "membrane", LAW_BEAM: "beam", LAW_FIBER: "fiber"}
 
 
 @dataclass
@@ -255,3 +256,29 @@ def shear_forcing(N: int, t: float, amplitude: float = 1.0, period: float = 0.5)
     fu = amplitude * np.sin(2.0 * np.pi * yu) * np.sin(w)
     fv = 0.5 * amplitude * np.sin(2.0 * np.pi * xv) * np.cos(w)
     return np.concatenate([fu, fv])
+
+
+# --------------------------------------------------------------------------- fiber (Sec. 5.3)
+
+
+def fiber_periodic(N: int = 16, bend: float = 1.5, jitter: float = 0.05) -> System:
+    """The clamped fiber of Sec. 5.3 on a periodic stand-in of its domain: the square (0, 2)^2
+    with 2N x 2N cells (h = 1/N), rho = 1, mu = 1.875e-3, dt = 0.05 h.  M = 0.75 N + 1
+    markers at spacing ds = h/2 (13, 25, 49, 97 at N = 16 ... 128), midpoint marker at the
+    clamp (1, 1.5).  The configuration is the straight fiber with its free ends bent
+    downstream, y = 1.5 - bend (x - 1)^2, plus a seeded jitter of `jitter` ds per coordinate
+    (a Newton iterate's shape); the force and tangent are taken there.  Stiffnesses: EI =
+    2.63672e-2; K_s, K_p, K_t = 375, 1200, 7.03125 at N = 64, proportional to N."""
+    h = 1.0 / N
+    ds = h / 2.0
+    M = int(round(0.375 / ds)) + 1
+    m = M // 2
+    x = 1.0 + (np.arange(M) - m) * ds
+    X = np.stack([x, 1.5 - bend * (x - 1.0) ** 2], 1)
+    X = X + jitter * ds * uniform_pm1(BASE_SEED + 7000 + N, 2 * M).reshape(M, 2)
+    X[m] = (1.0, 1.5)
+    f = N / 64.0
+    return System(name=f"fiber-N{N}", N=2 * N, L=2.0, rho=1.0, mu=1.875e-3, dt=0.05 * h, law=LAW_FIBER,
+                  closed=False, X=np.ascontiguousarray(X), ds=ds, omega=np.full(M, ds),
+                  k_stretch=375.0 * f, k_bend=2.63672e-2, seed=BASE_SEED + 7100 + N,
+                  meta={"k_pos": 1200.0 * f, "k_tan": 7.03125 * f, "X_c": (1.0, 1.5)})

@@ -151,15 +151,36 @@ def force_pattern(law: int, M: int, k_stretch: float, k_bend: float,
     return sp.block_diag([B1, B1], format="csr").astype(np.int64)
 
 
+LAW_FIBER = 3
+
+
+def fiber_params(sysm):
+    """The fiber law's parameters (Sec. 5.3) from a workload record: EI = k_bend, K_s =
+    k_stretch, K_p, K_t and the clamp point X_c from its meta fields."""
+    from . import fiber
+    return fiber.FiberParams(M=sysm.M, ds=sysm.ds, EI=sysm.k_bend, K_s=sysm.k_stretch,
+                             K_p=sysm.meta["k_pos"], K_t=sysm.meta["k_tan"], X_c=tuple(sysm.meta["X_c"]))
+
+
+def elasticity(sysm):
+    """E of the record's law at its configuration: the linear laws' matrix, or the fiber's
+    Newton tangent dF/dX at X (Sec. 5.3), with its structural pattern."""
+    if sysm.law == LAW_FIBER:
+        from . import fiber
+        p = fiber_params(sysm)
+        return fiber.tangent(p, sysm.X), fiber.tangent_pattern(p).astype(np.int64)
+    E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
+    return E, force_pattern(sysm.law, sysm.M, sysm.k_stretch, sysm.k_bend, sysm.k_target)
+
+
 def eulerian_elasticity(sysm):
     """E_E = S E J (values) and its structural pattern (bool CSR), for a workload record."""
     N, h = sysm.N, sysm.h
     S = spreading_matrix(N, h, sysm.X, sysm.omega)
     J = interpolation_matrix(N, h, sysm.X)
-    E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
+    E, Eb = elasticity(sysm)
     EE = (S @ E @ J).tocsr()
     Jb = support_pattern(N, h, sysm.X)
-    Eb = force_pattern(sysm.law, sysm.M, sysm.k_stretch, sysm.k_bend, sysm.k_target)
     pat = (Jb.T @ Eb @ Jb).tocsr()
     pat.data = np.ones_like(pat.data)
     pat = pat.astype(bool)
@@ -182,9 +203,8 @@ def first_step_rhs(sysm) -> np.ndarray:
     """Right-hand side of Eq. (Eul_schur) for the first backward Euler step from rest (Sec. 5):
     u^n = 0 so b = 0 and the velocity rows carry S E X^n; the target law's source term
     kappa_t X_target^{n+1} (Sec. 5.2) is added to E X^n.  Pressure rows are zero."""
-    N, h, M = sysm.N, sysm.h, sysm.M
+    N, h = sysm.N, sysm.h
     S = spreading_matrix(N, h, sysm.X, sysm.omega)
-    E = force_matrix(sysm.law, M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
     F = force_vector(sysm)
     b = np.zeros(3 * N * N)
     b[:2 * N * N] = S @ F
@@ -193,7 +213,10 @@ def first_step_rhs(sysm) -> np.ndarray:
 
 def force_vector(sysm) -> np.ndarray:
     """F = E X^n + k_target X_target (component-major): the linear laws' force at X^n
-    (Eq. disc_force_law, Sec. 5.2)."""
+    (Eq. disc_force_law, Sec. 5.2); the fiber's nonlinear force F(X^n) (Sec. 5.3)."""
+    if sysm.law == LAW_FIBER:
+        from . import fiber
+        return fiber.force(fiber_params(sysm), sysm.X)
     E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
     F = E @ np.concatenate([sysm.X[:, 0], sysm.X[:, 1]])
     if sysm.k_target != 0.0 and sysm.X_target is not None:

@@ -122,3 +122,29 @@ def test_pattern_holds_every_nonzero():
     for seed in range(3):
         T = fiber.tangent(p, _cmv(_bent(p, seed))).toarray()
         assert not np.any((T != 0) & ~pat)
+
+
+def test_fiber_eulerian_elasticity_couples_components_and_is_symmetric():
+    import ib_workloads as W
+    from oracle import ib
+    s = W.fiber_periodic(16)
+    EE, pat = ib.eulerian_elasticity(s)
+    NN = s.N ** 2
+    A = EE.toarray()
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    assert np.abs(A[:NN, NN:]).max() > 1e-3 * np.abs(A).max()   # u-v coupling through the tangent
+    assert not np.any((A != 0) & ~pat.toarray())
+
+
+@pytest.mark.parametrize("N,avg,mx", [(16, 11.76, 201), (32, 7.85, 198), (64, 6.36, 195)])
+def test_paper_fiber_patch_sizes(N, avg, mx):
+    # Sec. 5.3, the fiber refinement table: average and largest CAV patch on the finest level
+    # (the paper's averages run over a simulation, this is one bent configuration with the
+    # paper's marker count, spacing and stiffnesses): within 15 % and 25 %
+    import ib_workloads as W
+    from oracle import ib, patches
+    s = W.fiber_periodic(N)
+    _, pat = ib.eulerian_elasticity(s)
+    sz = np.array([len(p) for p in patches.cav_patches(s.N, pat)])
+    assert abs(sz.mean() - avg) <= 0.15 * avg, sz.mean()
+    assert abs(sz.max() - mx) <= 0.25 * mx, sz.max()

@@ -53,7 +53,7 @@ int64_t ib_launch_count(void);
 
 /* ------------------------------------------------------------------ system (Sec. 2) */
 
-typedef enum { IB_FORCE_TARGET = 0, IB_FORCE_MEMBRANE = 1, IB_FORCE_BEAM = 2 } ib_force_law;
+typedef enum { IB_FORCE_TARGET = 0, IB_FORCE_MEMBRANE = 1, IB_FORCE_BEAM = 2, IB_FORCE_FIBER = 3 } ib_force_law;
 
 typedef struct {
   int32_t N;       /* cells per direction (>= 8; even to allow coarsening)              */
@@ -67,7 +67,13 @@ typedef struct {
  *   beam     E = k_stretch/ds^2 [1 -2 1] - k_bend/ds^4 [1 -4 6 -4 1] - k_target I, cyclic
  *                                                             (Sec. 5.2)
  * membrane and beam require closed = 1.  The tether source k_target X_target enters the
- * right-hand side only (ib_force, ib_step_rhs).                                        */
+ * right-hand side only (ib_force, ib_step_rhs).
+ * fiber (ABI 3, Sec. 5.3): an open chain (closed = 0, M odd >= 3, midpoint m = M / 2) with
+ *   the energies  E_b = k_bend/(2 ds^5) sum_k (D_k x D_{k+1})^2,  D_k = X_{k+1} - X_k,
+ *                 E_s = k_stretch/(2 ds) sum_k (|D_k| - ds)^2,
+ *                 E_p = k_pos/2 |X_m - X_c|^2,  E_t = k_tan/2 |(X_{m+1} - X_{m-1})/(2 ds) - e_x|^2;
+ *   force F = -(1/ds) grad (E_b + E_s + E_p + E_t) and E = dF/dX (the Newton tangent, which
+ *   couples x and y), both at X_lin; S and J stay at X.  k_target must be 0.            */
 typedef struct {
   int32_t M;             /* number of Lagrangian markers (0 allowed: no structure)      */
   int32_t closed;        /* 1: the marker chain is a closed curve                        */
@@ -77,6 +83,10 @@ typedef struct {
   double ds;             /* uniform Lagrangian spacing used by the force stencils         */
   double k_target, k_stretch, k_bend;  /* k_target != 0 tethers every marker on any law */
   const double* X_target;  /* host, 2M interleaved, nullable: tether targets (source term) */
+  /* fiber law only (ABI 3): */
+  const double* X_lin;   /* host, 2M interleaved, nullable (= X): where F and E are taken  */
+  double k_pos, k_tan;   /* midpoint clamp stiffnesses K_p, K_t                            */
+  double clamp_x, clamp_y;  /* the clamp point X_c                                         */
 } ib_structure_desc;
 
 typedef struct ib_system ib_system;

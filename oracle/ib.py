@@ -162,13 +162,20 @@ def fiber_params(sysm):
                              K_p=sysm.meta["k_pos"], K_t=sysm.meta["k_tan"], X_c=tuple(sysm.meta["X_c"]))
 
 
+def fiber_linearisation_point(sysm):
+    """Where the fiber's force and tangent are taken: the Newton iterate X_lin when the record
+    carries one, else X (S and J always stay at X, Sec. 5.3)."""
+    Xl = sysm.meta.get("X_lin")
+    return sysm.X if Xl is None else np.asarray(Xl, dtype=np.float64)
+
+
 def elasticity(sysm):
     """E of the record's law at its configuration: the linear laws' matrix, or the fiber's
     Newton tangent dF/dX at X (Sec. 5.3), with its structural pattern."""
     if sysm.law == LAW_FIBER:
         from . import fiber
         p = fiber_params(sysm)
-        return fiber.tangent(p, sysm.X), fiber.tangent_pattern(p).astype(np.int64)
+        return fiber.tangent(p, fiber_linearisation_point(sysm)), fiber.tangent_pattern(p).astype(np.int64)
     E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
     return E, force_pattern(sysm.law, sysm.M, sysm.k_stretch, sysm.k_bend, sysm.k_target)
 
@@ -216,7 +223,7 @@ def force_vector(sysm) -> np.ndarray:
     (Eq. disc_force_law, Sec. 5.2); the fiber's nonlinear force F(X^n) (Sec. 5.3)."""
     if sysm.law == LAW_FIBER:
         from . import fiber
-        return fiber.force(fiber_params(sysm), sysm.X)
+        return fiber.force(fiber_params(sysm), fiber_linearisation_point(sysm))
     E = force_matrix(sysm.law, sysm.M, sysm.ds, sysm.k_target, sysm.k_stretch, sysm.k_bend)
     F = E @ np.concatenate([sysm.X[:, 0], sysm.X[:, 1]])
     if sysm.k_target != 0.0 and sysm.X_target is not None:

@@ -43,7 +43,8 @@ class ib_structure_desc(C.Structure):
     _fields_ = [("M", C.c_int32), ("closed", C.c_int32), ("law", C.c_int32),
                 ("X", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)), ("ds", C.c_double),
                 ("k_target", C.c_double), ("k_stretch", C.c_double), ("k_bend", C.c_double),
-                ("X_target", C.POINTER(C.c_double))]
+                ("X_target", C.POINTER(C.c_double)), ("X_lin", C.POINTER(C.c_double)), ("k_pos", C.c_double),
+                ("k_tan", C.c_double), ("clamp_x", C.c_double), ("clamp_y", C.c_double)]
 
 
 class cav_desc(C.Structure):
@@ -205,15 +206,22 @@ class Hierarchy:
 
 
 def _structure(rec):
+    """Descriptor of rec's structure; the fiber law's extra parameters come from rec.meta
+    (k_pos, k_tan, X_c and, optionally, the linearisation point X_lin)."""
     X = np.ascontiguousarray(np.asarray(rec.X, dtype=np.float64).reshape(-1))
     om = np.ascontiguousarray(np.asarray(rec.omega, dtype=np.float64))
     Xt = getattr(rec, "X_target", None)
     Xt = None if Xt is None else np.ascontiguousarray(np.asarray(Xt, dtype=np.float64).reshape(-1))
-    sd = ib_structure_desc(int(X.size // 2), 1 if rec.closed else 0, int(rec.law),
-                           X.ctypes.data_as(_P(C.c_double)), om.ctypes.data_as(_P(C.c_double)),
+    meta = getattr(rec, "meta", None) or {}
+    Xl = meta.get("X_lin")
+    Xl = None if Xl is None else np.ascontiguousarray(np.asarray(Xl, dtype=np.float64).reshape(-1))
+    Xc = meta.get("X_c", (0.0, 0.0))
+    dp = lambda a: a.ctypes.data_as(_P(C.c_double)) if a is not None else None  # noqa: E731
+    sd = ib_structure_desc(int(X.size // 2), 1 if rec.closed else 0, int(rec.law), dp(X), dp(om),
                            float(rec.ds), float(rec.k_target), float(rec.k_stretch), float(rec.k_bend),
-                           Xt.ctypes.data_as(_P(C.c_double)) if Xt is not None else None)
-    return sd, (X, om, Xt)  # keep the arrays alive while the descriptor is used
+                           dp(Xt), dp(Xl), float(meta.get("k_pos", 0.0)), float(meta.get("k_tan", 0.0)),
+                           float(Xc[0]), float(Xc[1]))
+    return sd, (X, om, Xt, Xl)  # keep the arrays alive while the descriptor is used
 
 
 def ib_update_structure(sys: System, rec, stream=None):
@@ -226,15 +234,7 @@ def ib_update_structure(sys: System, rec, stream=None):
 def ib_setup(rec, stream=None) -> System:
     """rec: an ib_workloads.System (or any object with the same fields)."""
     g = ib_grid_desc(int(rec.N), float(rec.L), float(rec.rho), float(rec.mu), float(rec.dt))
-    X = np.ascontiguousarray(np.asarray(rec.X, dtype=np.float64).reshape(-1))
-    om = np.ascontiguousarray(np.asarray(rec.omega, dtype=np.float64))
-    M = int(X.size // 2)
-    Xt = getattr(rec, "X_target", None)
-    Xt = None if Xt is None else np.ascontiguousarray(np.asarray(Xt, dtype=np.float64).reshape(-1))
-    sd = ib_structure_desc(M, 1 if rec.closed else 0, int(rec.law),
-                           X.ctypes.data_as(_P(C.c_double)), om.ctypes.data_as(_P(C.c_double)),
-                           float(rec.ds), float(rec.k_target), float(rec.k_stretch), float(rec.k_bend),
-                           Xt.ctypes.data_as(_P(C.c_double)) if Xt is not None else None)
+    sd, _keep = _structure(rec)
     out = _vp()
     _check(_lib.ib_setup(C.byref(g), C.byref(sd), _stream(stream), C.byref(out)), "ib_setup")
     return System(out, int(rec.N), rec)

@@ -56,7 +56,7 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
               "ib_setup: L, rho, dt must be positive and mu non-negative");
   CAV_REQUIRE(sd->M >= 0, "ib_setup: M must be non-negative");
   CAV_REQUIRE(sd->M == 0 || (sd->X && sd->omega), "ib_setup: X and omega are required when M > 0");
-  CAV_REQUIRE(sd->law >= IB_FORCE_TARGET && sd->law <= IB_FORCE_BEAM, "ib_setup: unknown force law");
+  CAV_REQUIRE(sd->law >= IB_FORCE_TARGET && sd->law <= IB_FORCE_FIBER, "ib_setup: unknown force law");
   s = new ib_system();
   s->N = grid->N;
   s->L = grid->L;
@@ -70,12 +70,25 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   s->k_target = sd->k_target;
   s->k_stretch = sd->k_stretch;
   s->k_bend = sd->k_bend;
+  s->k_pos = sd->k_pos;
+  s->k_tan = sd->k_tan;
+  s->clamp_x = sd->clamp_x;
+  s->clamp_y = sd->clamp_y;
   CAV_CHECK_CUDA(cudaGetDevice(&s->device));
   // structural band of E: target -> diagonal; membrane -> +-1 when k_stretch != 0;
   // beam -> +-2 when k_bend != 0, else +-1 when k_stretch != 0; otherwise no structure
   int M = sd->M, bw = 0;
   if (sd->law == IB_FORCE_TARGET) bw = 0;
-  else if (sd->law == IB_FORCE_MEMBRANE) {
+  else if (sd->law == IB_FORCE_FIBER) {
+    // bending couples markers two links apart; the tangent couples x and y
+    if (M > 0) {
+      CAV_REQUIRE(!sd->closed, "ib_setup: the fiber law needs an open marker chain");
+      CAV_REQUIRE(M >= 3 && M % 2 == 1, "ib_setup: the fiber law needs an odd number of markers, at least 3");
+      CAV_REQUIRE(sd->ds > 0, "ib_setup: ds must be positive");
+      CAV_REQUIRE(sd->k_target == 0.0, "ib_setup: the fiber law takes no tethers (k_target must be 0)");
+      bw = 2;
+    }
+  } else if (sd->law == IB_FORCE_MEMBRANE) {
     if (sd->k_stretch != 0.0) bw = 1;
     else if (sd->k_target != 0.0) bw = 0;
     else M = 0;
@@ -85,7 +98,7 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
     else if (sd->k_target != 0.0) bw = 0;
     else M = 0;
   }
-  if (M > 0 && bw > 0) {
+  if (M > 0 && bw > 0 && sd->law != IB_FORCE_FIBER) {
     CAV_REQUIRE(sd->closed, "ib_setup: membrane and beam laws need a closed marker chain");
     CAV_REQUIRE(M >= 2 * bw + 1, "ib_setup: too few markers for the force stencil");
     CAV_REQUIRE(sd->ds > 0, "ib_setup: ds must be positive");
@@ -94,7 +107,7 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   s->bw = bw;
   s->status = s->arena.alloc<int>(1);
   CAV_CHECK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
-  build_markers_and_ee(s, sd->X, sd->omega, st);
+  build_markers_and_ee(s, sd->X, sd->X_lin ? sd->X_lin : sd->X, sd->omega, st);
   if (M > 0) {
     s->X_host.assign(sd->X, sd->X + 2 * (size_t)M);
     if (sd->X_target) {

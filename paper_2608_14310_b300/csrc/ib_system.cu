@@ -216,6 +216,182 @@ __global__ void k_ee_assemble(int N, int M, int bw, int closed, double h, int W,
   if (pass == 0 && lane == 0) row_count[row] = total;
 }
 
+// ------------------------------------------------------------------ fiber law (Sec. 5.3)
+
+// Gradient g (component-major, 2M) and Hessian of the fiber's energy on an open chain at X
+// (interleaved), the Hessian as a block band H[p][q - p + 2][c][c2] = d2E / dX_{c,p} dX_{c2,q}.
+//   bending     EI/(2 ds^5) sum_k c_k^2,  c_k = D_k x D_{k+1} = a0 b1 - a1 b0,
+//               a = D_k = X_{k+1} - X_k, b = D_{k+1} = X_{k+2} - X_{k+1}
+//   stretching  K_s/(2 ds) sum_k (|D_k| - ds)^2
+//   clamp       K_p/2 |X_m - X_c|^2 + K_t/2 |(X_{m+1} - X_{m-1})/(2 ds) - e_x|^2
+// Host arithmetic in FP64; the chain is short (tens to hundreds of markers).
+static void fiber_derivatives(const ib_system* s, const double* X, std::vector<double>& g, std::vector<double>& H) {
+  const int M = s->M;
+  const double ds = s->ds;
+  g.assign(2 * (size_t)M, 0.0);
+  H.assign((size_t)M * 5 * 4, 0.0);
+  auto P = [&](int k, int c) { return X[2 * k + c]; };
+  auto addg = [&](int k, int c, double v) { g[(size_t)c * M + k] += v; };
+  auto addh = [&](int p, int c, int q, int c2, double v) { H[(((size_t)p * 5 + (q - p + 2)) * 2 + c) * 2 + c2] += v; };
+  // bending: variables z = (a0, a1, b0, b1); dz/dX: a = X_{k+1} - X_k, b = X_{k+2} - X_{k+1}
+  const double cb = s->k_bend / std::pow(ds, 5);
+  for (int k = 0; k + 2 < M; ++k) {
+    const double a[2] = {P(k + 1, 0) - P(k, 0), P(k + 1, 1) - P(k, 1)};
+    const double b[2] = {P(k + 2, 0) - P(k + 1, 0), P(k + 2, 1) - P(k + 1, 1)};
+    const double c = a[0] * b[1] - a[1] * b[0];
+    const double dz[4] = {b[1], -b[0], -a[1], a[0]};  // dc/dz
+    // d2c/dz2: +1 at (a0, b1), -1 at (a1, b0), symmetric
+    double hz[4][4];
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) hz[u][v] = cb * dz[u] * dz[v];
+    hz[0][3] += cb * c;
+    hz[3][0] += cb * c;
+    hz[1][2] -= cb * c;
+    hz[2][1] -= cb * c;
+    // marker and sign of each z-component's dependence: z in a -> (k: -1, k+1: +1); in b -> (k+1: -1, k+2: +1)
+    const int mk[2][2] = {{k, k + 1}, {k + 1, k + 2}};
+    for (int u = 0; u < 4; ++u) {
+      const int vu = u / 2, cu = u % 2;
+      addg(mk[vu][0], cu, -cb * c * dz[u]);
+      addg(mk[vu][1], cu, cb * c * dz[u]);
+      for (int v = 0; v < 4; ++v) {
+        const int vv = v / 2, cv = v % 2;
+        for (int su = 0; su < 2; ++su)
+          for (int sv = 0; sv < 2; ++sv)
+            addh(mk[vu][su], cu, mk[vv][sv], cv, (su ? 1.0 : -1.0) * (sv ? 1.0 : -1.0) * hz[u][v]);
+      }
+    }
+  }
+  // stretching: per link, grad (|d| - ds) d/|d| and Hessian u u^T + (|d| - ds)/|d| (I - u u^T)
+  const double cs = s->k_stretch / ds;
+  for (int k = 0; k + 1 < M; ++k) {
+    const double d[2] = {P(k + 1, 0) - P(k, 0), P(k + 1, 1) - P(k, 1)};
+    const double L = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+    const double u[2] = {d[0] / L, d[1] / L};
+    const double r = (L - ds) / L;
+    for (int c = 0; c < 2; ++c) {
+      addg(k, c, -cs * (L - ds) * u[c]);
+      addg(k + 1, c, cs * (L - ds) * u[c]);
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const double h = cs * (u[c] * u[c2] + r * ((c == c2 ? 1.0 : 0.0) - u[c] * u[c2]));
+        addh(k, c, k, c2, h);
+        addh(k + 1, c, k + 1, c2, h);
+        addh(k, c, k + 1, c2, -h);
+        addh(k + 1, c, k, c2, -h);
+      }
+    }
+  }
+  // midpoint clamp
+  const int m = M / 2;
+  const double xc[2] = {s->clamp_x, s->clamp_y};
+  const double ex[2] = {1.0, 0.0};
+  const double ct = s->k_tan / (2.0 * ds);
+  for (int c = 0; c < 2; ++c) {
+    addg(m, c, s->k_pos * (P(m, c) - xc[c]));
+    addh(m, c, m, c, s->k_pos);
+    const double tv = (P(m + 1, c) - P(m - 1, c)) / (2.0 * ds) - ex[c];
+    addg(m + 1, c, ct * tv);
+    addg(m - 1, c, -ct * tv);
+    const double h = s->k_tan / (4.0 * ds * ds);
+    addh(m + 1, c, m + 1, c, h);
+    addh(m - 1, c, m - 1, c, h);
+    addh(m + 1, c, m - 1, c, -h);
+    addh(m - 1, c, m + 1, c, -h);
+  }
+}
+
+// E_E = S E J for a law whose E couples the two components (the fiber's tangent): one warp
+// per active row k (component c); the window holds the column faces of both components (two
+// planes of the same x / y extent).  For every marker a whose c-support holds k (ascending),
+// every b in E's band of a and each component c2, the 16 lanes add
+// S[k,(c,a)] E[(c,a),(c2,b)] J[(c2,b),l] over the faces l of (c2, b)'s support -- distinct
+// faces, so no two lanes touch the same entry and the order is fixed.  Columns are written
+// u plane first, then v, each in ascending order.  pass 0 counts, pass 1 writes.
+__global__ void k_ee_assemble_x(int N, int M, int bw, double h, int W, const double* __restrict__ omega,
+                                const double* __restrict__ eblk, const int* __restrict__ sup_i0,
+                                const int* __restrict__ sup_j0, const double* __restrict__ wx,
+                                const double* __restrict__ wy, const uint8_t* __restrict__ mask,
+                                const int64_t* __restrict__ fm_off, const int* __restrict__ fm_list, int n_rows,
+                                const int* __restrict__ rows, int* row_count, const int64_t* __restrict__ rowptr,
+                                int* cols, double* vals, int pass, int* status) {
+  extern __shared__ unsigned char smem[];
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * warps + warp;
+  const int lenmax = (2 * W + 1 >= N) ? N : 2 * W + 1;
+  const int cells = lenmax * lenmax;
+  double* acc = reinterpret_cast<double*>(smem) + (size_t)warp * 2 * cells;
+  uint8_t* flg = reinterpret_cast<uint8_t*>(reinterpret_cast<double*>(smem) + (size_t)warps * 2 * cells) +
+                 (size_t)warp * 2 * cells;
+  if (row >= n_rows) return;
+  const int k = rows[row];
+  const int NN = N * N;
+  const int c = k / NN, rem = k % NN, ik = rem % N, jk = rem / N;
+  const Win wxn = make_win(ik, W, N), wyn = make_win(jk, W, N);
+  const int plane = wxn.len * wyn.len;
+  for (int t = lane; t < 2 * cells; t += 32) {
+    acc[t] = 0.0;
+    flg[t] = 0;
+  }
+  __syncwarp();
+  const double inv_h2 = 1.0 / (h * h);
+  for (int64_t q = fm_off[k]; q < fm_off[k + 1]; ++q) {
+    const int a = fm_list[q];
+    const int ida = c * M + a;
+    const int si = pmod(ik - sup_i0[ida], N), sj = pmod(jk - sup_j0[ida], N);
+    const double s_ka = wx[4 * ida + si] * wy[4 * ida + sj] * (omega[a] * inv_h2);
+    for (int d = -bw; d <= bw; ++d) {
+      const int b = a + d;
+      if (b < 0 || b >= M) continue;
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const double coef = s_ka * eblk[(((size_t)a * (2 * bw + 1) + (d + bw)) * 2 + c) * 2 + c2];
+        const int idb = c2 * M + b;
+        if (lane < 16) {
+          const int sx = lane & 3, sy = lane >> 2;
+          const uint8_t mb = mask[idb];
+          if ((mb & (1u << sx)) && (mb & (1u << (sy + 4)))) {
+            const int gi = pmod(sup_i0[idb] + sx, N), gj = pmod(sup_j0[idb] + sy, N);
+            const int ox = win_off(wxn, gi, N), oy = win_off(wyn, gj, N);
+            if (ox < 0 || oy < 0) {
+              atomicExch(status, DEV_WINDOW);
+            } else {
+              const int cell = c2 * plane + oy * wxn.len + ox;
+              acc[cell] += coef * (wx[4 * idb + sx] * wy[4 * idb + sy]);
+              flg[cell] = 1;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  int64_t outpos = (pass == 1) ? rowptr[row] : 0;
+  int total = 0;
+  for (int c2 = 0; c2 < 2; ++c2)
+    for (int typ = 0; typ < wyn.len; ++typ) {
+      const int ty = win_asc(wyn, typ);
+      const int gy = win_glob(wyn, ty, N);
+      for (int base = 0; base < wxn.len; base += 32) {
+        const int txp = base + lane;
+        int tx = 0, gx = 0;
+        bool f = false;
+        if (txp < wxn.len) {
+          tx = win_asc(wxn, txp);
+          gx = win_glob(wxn, tx, N);
+          f = flg[c2 * plane + ty * wxn.len + tx] != 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (pass == 1 && f) {
+          const int rank = __popc(bal & ((1u << lane) - 1u));
+          cols[outpos + total + rank] = c2 * NN + gy * N + gx;
+          vals[outpos + total + rank] = acc[c2 * plane + ty * wxn.len + tx];
+        }
+        total += __popc(bal);
+      }
+    }
+  if (pass == 0 && lane == 0) row_count[row] = total;
+}
+
 // Max per-axis periodic offset between an E_E row face and its column faces.
 __global__ void k_ee_window(int N, int n_rows, const int* rows, const int64_t* rowptr,
                             const int* cols, int* out) {
@@ -327,6 +503,10 @@ __global__ void k_interp(int N, int M, const int* __restrict__ sup_i0, const int
 
 void ib_force_launch(const ib_system* s, double* F, cudaStream_t st) {
   if (s->M == 0) return;
+  if (s->law == IB_FORCE_FIBER) {  // evaluated at set-up, at the linearisation point
+    CAV_CHECK_CUDA(cudaMemcpyAsync(F, s->Ffib, sizeof(double) * 2 * s->M, cudaMemcpyDeviceToDevice, st));
+    return;
+  }
   k_force<<<div_up(2 * s->M, 128), 128, 0, st>>>(s->M, s->bw, s->closed, s->Eband, s->X, s->k_target, s->Xt, F);
   CAV_CHECK_LAUNCH();
 }
@@ -350,7 +530,7 @@ static size_t ee_smem_per_warp(int W, int N) {
   return (size_t)len * len * (sizeof(double) + 1);
 }
 
-void build_markers_and_ee(ib_system* s, const double* X_il, const double* omega_host,
+void build_markers_and_ee(ib_system* s, const double* X_il, const double* X_lin_il, const double* omega_host,
                           cudaStream_t st) {
   const int N = s->N, M = s->M, NN = N * N;
   Arena& A = s->arena;
@@ -387,10 +567,24 @@ void build_markers_and_ee(ib_system* s, const double* X_il, const double* omega_
     k_marker_support<<<div_up(2 * M, 128), 128, 0, st>>>(M, s->h, s->X, s->sup_i0, s->sup_j0,
                                                         s->sup_wx, s->sup_wy, s->sup_mask);
     CAV_CHECK_LAUNCH();
-    s->Eband = A.alloc<double>((size_t)M * (2 * s->bw + 1));
-    k_force_band<<<div_up(M, 128), 128, 0, st>>>(M, s->bw, s->law, s->ds, s->k_target, s->k_stretch,
-                                                s->k_bend, s->Eband);
-    CAV_CHECK_LAUNCH();
+    const bool fib = s->law == IB_FORCE_FIBER;
+    if (fib) {
+      // the fiber's force and tangent at the linearisation point: F = -g/ds, E = -H/ds
+      std::vector<double> g, H;
+      fiber_derivatives(s, X_lin_il, g, H);
+      for (double& v : g) v = -v / s->ds;
+      for (double& v : H) v = -v / s->ds;
+      s->Eblock = A.alloc<double>(H.size());
+      s->Ffib = A.alloc<double>(g.size());
+      CAV_CHECK_CUDA(cudaMemcpyAsync(s->Eblock, H.data(), sizeof(double) * H.size(), cudaMemcpyHostToDevice, st));
+      CAV_CHECK_CUDA(cudaMemcpyAsync(s->Ffib, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, st));
+      CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    } else {
+      s->Eband = A.alloc<double>((size_t)M * (2 * s->bw + 1));
+      k_force_band<<<div_up(M, 128), 128, 0, st>>>(M, s->bw, s->law, s->ds, s->k_target, s->k_stretch,
+                                                  s->k_bend, s->Eband);
+      CAV_CHECK_LAUNCH();
+    }
     // face -> markers incidence
     int* count = scratch.alloc<int>(2 * NN);
     int* cursor = scratch.alloc<int>(2 * NN);
@@ -441,20 +635,34 @@ void build_markers_and_ee(ib_system* s, const double* X_il, const double* omega_
     }
     const int W = (int)std::ceil(D) + 5;
     const int warps = 4;
-    const size_t smem = warps * ee_smem_per_warp(W, N);
+    // the cross-component assembly keeps two window planes per warp
+    const size_t smem = warps * ee_smem_per_warp(W, N) * (fib ? 2 : 1);
     CAV_REQUIRE(smem <= 200 * 1024, "E_E stencil window too large (markers too far apart in E's band)");
-    if (smem > 48 * 1024)
-      CAV_CHECK_CUDA(cudaFuncSetAttribute(k_ee_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {
+      if (fib)
+        CAV_CHECK_CUDA(cudaFuncSetAttribute(k_ee_assemble_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      else
+        CAV_CHECK_CUDA(cudaFuncSetAttribute(k_ee_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    ee.cross = fib ? 1 : 0;
     int* row_count = scratch.alloc<int>(nrows + 1);
     const int grid = div_up(nrows, warps);
     ee.rowptr = A.alloc<int64_t>(nrows + 1);
-    if (nrows > 0) {
-      k_ee_assemble<<<grid, warps * 32, smem, st>>>(N, M, s->bw, s->closed, s->h, W, s->omega, s->Eband,
-                                                    s->sup_i0, s->sup_j0, s->sup_wx, s->sup_wy, s->sup_mask,
-                                                    s->fm_off, s->fm_list, (int)nrows, ee.rows, row_count,
-                                                    nullptr, nullptr, nullptr, 0, s->status);
+    auto assemble = [&](const int64_t* rowptr, int* cols, double* vals, int pass) {
+      if (nrows == 0) return;
+      if (fib)
+        k_ee_assemble_x<<<grid, warps * 32, smem, st>>>(N, M, s->bw, s->h, W, s->omega, s->Eblock, s->sup_i0,
+                                                        s->sup_j0, s->sup_wx, s->sup_wy, s->sup_mask, s->fm_off,
+                                                        s->fm_list, (int)nrows, ee.rows, row_count, rowptr, cols,
+                                                        vals, pass, s->status);
+      else
+        k_ee_assemble<<<grid, warps * 32, smem, st>>>(N, M, s->bw, s->closed, s->h, W, s->omega, s->Eband,
+                                                      s->sup_i0, s->sup_j0, s->sup_wx, s->sup_wy, s->sup_mask,
+                                                      s->fm_off, s->fm_list, (int)nrows, ee.rows, row_count,
+                                                      rowptr, cols, vals, pass, s->status);
       CAV_CHECK_LAUNCH();
-    }
+    };
+    assemble(nullptr, nullptr, nullptr, 0);
     exclusive_scan(row_count, ee.rowptr, nrows, st, &scratch);
     int64_t nnz = 0;
     CAV_CHECK_CUDA(cudaMemcpyAsync(&nnz, ee.rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -462,13 +670,7 @@ void build_markers_and_ee(ib_system* s, const double* X_il, const double* omega_
     ee.nnz = nnz;
     ee.cols = A.alloc<int>(nnz);
     ee.vals = A.alloc<double>(nnz);
-    if (nrows > 0) {
-      k_ee_assemble<<<grid, warps * 32, smem, st>>>(N, M, s->bw, s->closed, s->h, W, s->omega, s->Eband,
-                                                    s->sup_i0, s->sup_j0, s->sup_wx, s->sup_wy, s->sup_mask,
-                                                    s->fm_off, s->fm_list, (int)nrows, ee.rows, row_count,
-                                                    ee.rowptr, ee.cols, ee.vals, 1, s->status);
-      CAV_CHECK_LAUNCH();
-    }
+    assemble(ee.rowptr, ee.cols, ee.vals, 1);
     ee_compute_window(ee, N, scratch.alloc<int>(1), st);
     scratch.release();
   } catch (...) {

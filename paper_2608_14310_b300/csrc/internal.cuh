@@ -78,6 +78,7 @@ struct EECsr {
   int* cols = nullptr;       // [nnz]
   double* vals = nullptr;    // [nnz]
   int* row_of = nullptr;     // [2 N^2] active row index or -1
+  int cross = 0;             // 1: rows may have columns in the other velocity component
 };
 
 // ------------------------------------------------------------------ one grid level
@@ -153,12 +154,15 @@ struct ib_system {
   double L = 1, h = 0, rho = 0, mu = 0, dt = 0;
   int M = 0, law = 0, closed = 0, bw = 0;
   double ds = 0, k_target = 0, k_stretch = 0, k_bend = 0;
+  double k_pos = 0, k_tan = 0, clamp_x = 0, clamp_y = 0;  // fiber law's midpoint clamp
   int device = 0;
   cav::Arena arena;
   // markers (component-major x[0..M), y[M..2M))
   double* X = nullptr;
   double* omega = nullptr;
   double* Eband = nullptr;       // [M * (2 bw + 1)] E coefficient of (a, a + d)
+  double* Eblock = nullptr;      // fiber law: [M][2 bw + 1][2][2] E entry ((c, a), (c2, a + d))
+  double* Ffib = nullptr;        // fiber law: [2M] F at the linearisation point
   double* Xt = nullptr;          // [2M] target positions (component-major) or null
   double* F = nullptr;           // [2M] Lagrangian force scratch
   double* U = nullptr;           // [2M] marker velocity / next positions scratch
@@ -221,8 +225,9 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 inline int round8(int n) { return (n + 7) & ~7; }
 
 // ib_system.cu
-void build_markers_and_ee(ib_system* s, const double* X_interleaved, const double* omega_host,
-                          cudaStream_t st);
+// X_lin_interleaved: where the fiber law's force and tangent are taken (X for the others)
+void build_markers_and_ee(ib_system* s, const double* X_interleaved, const double* X_lin_interleaved,
+                          const double* omega_host, cudaStream_t st);
 void ib_force_launch(const ib_system* s, double* F, cudaStream_t st);
 void ib_spread_launch(const ib_system* s, const double* F, double* f, int rhs, const double* u_prev,
                       const double* f_body, cudaStream_t st);

@@ -65,9 +65,11 @@ __device__ inline int find_col(const int* cols, int64_t b, int64_t e, int key) {
 }
 
 // One warp per active coarse row K; lanes walk the window of coarse columns L (same
-// component) in ascending global order and evaluate
+// component; with CROSS, the u plane and then the v plane, for an E_E whose rows reach the
+// other component) in ascending global order and evaluate
 //   E_c[K, L] = sum_{k in Pcol(K)} sum_{l in Pcol(L)} (1/4) P[k,K] E_f[k,l] P[l,L]
 // in a fixed order; (K, L) is structurally nonzero iff some (k, l) is in E_f's pattern.
+template <bool CROSS>
 __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ rows,
                            const int* __restrict__ row_of_f, const int64_t* __restrict__ rowptr_f,
                            const int* __restrict__ cols_f, const double* __restrict__ vals_f,
@@ -88,6 +90,8 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
   const int ncell = wx.len * wy.len;
   int64_t outpos = (pass == 1) ? rowptr[r] : 0;
   int total = 0;
+  for (int pl = 0; pl < (CROSS ? 2 : 1); ++pl) {
+  const int cl = CROSS ? pl : c;  // component of the columns
   for (int base = 0; base < ncell; base += 32) {
     const int tp = base + lane;
     bool f = false;
@@ -96,16 +100,16 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
     if (tp < ncell) {
       const int typ = tp / wx.len, txp = tp % wx.len;
       const int gy = win_glob(wy, win_asc(wy, typ), Nc), gx = win_glob(wx, win_asc(wx, txp), Nc);
-      L = c * NNc + gy * Nc + gx;
+      L = cl * NNc + gy * Nc + gx;
       int li[6], lj[6];
       double lw[6];
-      pcol(c, gx, gy, Nf, li, lj, lw);
+      pcol(cl, gx, gy, Nf, li, lj, lw);
       for (int t = 0; t < 6; ++t) {
         if (krow[t] < 0) continue;
         const int64_t b = rowptr_f[krow[t]], e = rowptr_f[krow[t] + 1];
         double s = 0.0;
         for (int u = 0; u < 6; ++u) {
-          const int l = c * NNf + lj[u] * Nf + li[u];
+          const int l = cl * NNf + lj[u] * Nf + li[u];
           const int pos = find_col(cols_f, b, e, l);
           if (pos >= 0) {
             f = true;
@@ -122,6 +126,7 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
       vals[outpos + total + rank] = val;
     }
     total += __popc(bal);
+  }
   }
   if (pass == 0 && lane == 0) row_count[r] = total;
 }
@@ -159,11 +164,18 @@ static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int*
   int* row_count = scratch.alloc<int>(nrows + 1);
   out.rowptr = A.alloc<int64_t>(nrows + 1);
   const int grid = div_up(nrows, 8);
-  if (nrows > 0) {
-    k_galerkin<<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
-                                     fine.vals, row_count, nullptr, nullptr, nullptr, 0);
+  out.cross = fine.cross;
+  auto galerkin = [&](const int64_t* rowptr, int* cols, double* vals, int pass) {
+    if (nrows == 0) return;
+    if (out.cross)
+      k_galerkin<true><<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
+                                             fine.vals, row_count, rowptr, cols, vals, pass);
+    else
+      k_galerkin<false><<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
+                                              fine.vals, row_count, rowptr, cols, vals, pass);
     CAV_CHECK_LAUNCH();
-  }
+  };
+  galerkin(nullptr, nullptr, nullptr, 0);
   exclusive_scan(row_count, out.rowptr, nrows, st, &scratch);
   int64_t nnz = 0;
   CAV_CHECK_CUDA(cudaMemcpyAsync(&nnz, out.rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -171,11 +183,7 @@ static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int*
   out.nnz = nnz;
   out.cols = A.alloc<int>(nnz);
   out.vals = A.alloc<double>(nnz);
-  if (nrows > 0) {
-    k_galerkin<<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
-                                     fine.vals, row_count, out.rowptr, out.cols, out.vals, 1);
-    CAV_CHECK_LAUNCH();
-  }
+  galerkin(out.rowptr, out.cols, out.vals, 1);
   ee_compute_window(out, Nc, d_scratch, st);
   scratch.release();
 }

@@ -22,5 +22,6 @@ and no blocking, fusion or reordering:
   fgmres     right-preconditioned flexible GMRES                    (Sec. 5)
   twogrid    two-grid iteration matrix and its spectrum            (Sec. 5.1, Table 1)
   fiber      nonlinear fiber energies, force and Newton tangent    (Sec. 5.3)
+  newton     Newton's method for one semi-implicit step            (Sec. 5.3)
 """
-from . import grid, ib, patches, smoother, colouring, multigrid, fgmres, twogrid, fiber  # noqa: F401
+from . import grid, ib, patches, smoother, colouring, multigrid, fgmres, twogrid, fiber, newton  # noqa: F401

@@ -112,15 +112,15 @@ void ib_destroy(ib_system* sys);
 /* Lagrangian / Eulerian transfers at the system's configuration X^n (Sec. 2) and the pieces
  * of a semi-implicit time step (Eqs. im_disc_mom, im_disc_advec, Eul_schur).
  * Lagrangian vectors F, U are device buffers of 2M doubles, x components then y components. */
-/* F = E X^n + k_target X_target. */
+/* F = E X^n + k_target X_target; for the fiber law, its nonlinear force F(X_lin). */
 ib_status ib_force(const ib_system* sys, double* F, cudaStream_t stream);
 /* f = S F on the 2 N^2 velocity faces (f: device, u block then v block). */
 ib_status ib_spread(const ib_system* sys, const double* F, double* f, cudaStream_t stream);
 /* U = J u from the velocity blocks of u (device, >= 2 N^2 entries). */
 ib_status ib_interp(const ib_system* sys, const double* u, double* U, cudaStream_t stream);
 /* Right-hand side of Eq. Eul_schur for one step: b_vel = (rho/dt) u_prev + f_body
- * + S (E X^n + k_target X_target), b_p = 0.  u_prev (3 N^2) and f_body (2 N^2) are device
- * buffers and may be NULL (zero). */
+ * + S F with F as ib_force returns it, b_p = 0.  u_prev (3 N^2) and f_body (2 N^2) are
+ * device buffers and may be NULL (zero). */
 ib_status ib_step_rhs(const ib_system* sys, const double* u_prev, const double* f_body, double* b,
                       cudaStream_t stream);
 /* X^{n+1} = X^n + dt J u (Eq. im_disc_advec) into X_next (host, 2M interleaved); syncs. */

@@ -19,6 +19,11 @@
 //    partials in a fixed order and writes w.
 //  * standard cells take five lanes each (one Stokes row per lane, the shared 5 x 5 inverse
 //    applied after a shuffle).
+//
+// The box smoother B(b,o) (Sec. 3.1, 3.3) runs on the same machinery: one enlarged patch per
+// block, blocks in lexicographic order of their lower-left cells, and a per-slot mask that
+// writes only the unexpanded block's unknowns (restricted injection).  The conflict relation
+// still reads the whole (expanded) patch, so a class's solves stay independent.
 #include <cooperative_groups.h>
 
 #include <algorithm>

@@ -91,42 +91,42 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
   int64_t outpos = (pass == 1) ? rowptr[r] : 0;
   int total = 0;
   for (int pl = 0; pl < (CROSS ? 2 : 1); ++pl) {
-  const int cl = CROSS ? pl : c;  // component of the columns
-  for (int base = 0; base < ncell; base += 32) {
-    const int tp = base + lane;
-    bool f = false;
-    double val = 0.0;
-    int L = 0;
-    if (tp < ncell) {
-      const int typ = tp / wx.len, txp = tp % wx.len;
-      const int gy = win_glob(wy, win_asc(wy, typ), Nc), gx = win_glob(wx, win_asc(wx, txp), Nc);
-      L = cl * NNc + gy * Nc + gx;
-      int li[6], lj[6];
-      double lw[6];
-      pcol(cl, gx, gy, Nf, li, lj, lw);
-      for (int t = 0; t < 6; ++t) {
-        if (krow[t] < 0) continue;
-        const int64_t b = rowptr_f[krow[t]], e = rowptr_f[krow[t] + 1];
-        double s = 0.0;
-        for (int u = 0; u < 6; ++u) {
-          const int l = cl * NNf + lj[u] * Nf + li[u];
-          const int pos = find_col(cols_f, b, e, l);
-          if (pos >= 0) {
-            f = true;
-            s += vals_f[b + pos] * lw[u];
+    const int cl = CROSS ? pl : c;  // component of the columns
+    for (int base = 0; base < ncell; base += 32) {
+      const int tp = base + lane;
+      bool f = false;
+      double val = 0.0;
+      int L = 0;
+      if (tp < ncell) {
+        const int typ = tp / wx.len, txp = tp % wx.len;
+        const int gy = win_glob(wy, win_asc(wy, typ), Nc), gx = win_glob(wx, win_asc(wx, txp), Nc);
+        L = cl * NNc + gy * Nc + gx;
+        int li[6], lj[6];
+        double lw[6];
+        pcol(cl, gx, gy, Nf, li, lj, lw);
+        for (int t = 0; t < 6; ++t) {
+          if (krow[t] < 0) continue;
+          const int64_t b = rowptr_f[krow[t]], e = rowptr_f[krow[t] + 1];
+          double s = 0.0;
+          for (int u = 0; u < 6; ++u) {
+            const int l = cl * NNf + lj[u] * Nf + li[u];
+            const int pos = find_col(cols_f, b, e, l);
+            if (pos >= 0) {
+              f = true;
+              s += vals_f[b + pos] * lw[u];
+            }
           }
+          val += 0.25 * kw[t] * s;
         }
-        val += 0.25 * kw[t] * s;
       }
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (pass == 1 && f) {
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        cols[outpos + total + rank] = L;
+        vals[outpos + total + rank] = val;
+      }
+      total += __popc(bal);
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (pass == 1 && f) {
-      const int rank = __popc(bal & ((1u << lane) - 1u));
-      cols[outpos + total + rank] = L;
-      vals[outpos + total + rank] = val;
-    }
-    total += __popc(bal);
-  }
   }
   if (pass == 0 && lane == 0) row_count[r] = total;
 }

@@ -68,9 +68,29 @@ def _cm_to_xy(x):
     return np.stack([x[:M], x[M:]], 1)
 
 
-def newton_step(sysm, u_n=None, f=None, w0=None, rtol=1e-8, atol=1e-8, maxit=20):
+def cav_fgmres_solver(mode="coloured", nu=1, alpha=1.0, rtol=1e-9, maxit=150, coarsest_N=8):
+    """A linear solver for newton_step as the paper runs it (Sec. 5.3): the CAV hierarchy
+    rebuilt for each Newton system, right-preconditioned FGMRES to rtol relative to ||r_0||
+    with one V-cycle per iteration.  Records the iteration counts in its `iters` list."""
+    from . import fgmres, multigrid
+
+    def solve(sys_k, K, rhs):
+        levels = multigrid.build_hierarchy(sys_k, coarsest_N, "cav")
+        x, info = fgmres.fgmres(lambda v: K @ v, rhs,
+                                lambda r: multigrid.vcycle(levels, r, nu, nu, mode, alpha),
+                                rtol=rtol, maxit=maxit, ref="r0")
+        solve.iters.append(info["iters"])
+        return x
+
+    solve.iters = []
+    return solve
+
+
+def newton_step(sysm, u_n=None, f=None, w0=None, rtol=1e-8, atol=1e-8, maxit=20, linear_solve=None):
     """One time step from (X^n = sysm.X, u^n) by Newton's method.  Returns (w, X^{n+1},
-    history of ||R|| per iterate, number of Newton corrections)."""
+    history of ||R|| per iterate, number of Newton corrections).  `linear_solve(sys_k, K, rhs)`
+    (default: the bordered direct solve) solves each Newton system; sys_k is the record with
+    its linearisation point at X_k."""
     N, h = sysm.N, sysm.h
     NN2 = 2 * N * N
     n = 3 * N * N
@@ -89,7 +109,10 @@ def newton_step(sysm, u_n=None, f=None, w0=None, rtol=1e-8, atol=1e-8, maxit=20)
         K = grid.reduced_operator(N, h, sysm.rho, sysm.dt, sysm.mu, EE)
         rhs = np.zeros(n)
         rhs[:NN2] = sysm.rho / sysm.dt * u_n + f + S @ (F - sysm.dt * (E @ (J @ w[:NN2])))
-        w = _solve_bordered(K, rhs, N)
+        if linear_solve is None:
+            w = _solve_bordered(K, rhs, N)
+        else:
+            w = linear_solve(replace(sysm, meta={**sysm.meta, "X_lin": Xk}), K, rhs)
         k += 1
         hist.append(np.linalg.norm(residual(sysm, u_n, f, w)))
     X_next = _cm_to_xy(Xn + sysm.dt * (J @ w[:NN2]))

@@ -62,3 +62,23 @@ def test_product_path_has_no_fallback():
     # no other implementation is referenced)
     src = open(os.path.join(ROOT, "paper_2608_14310_b300", "api.py")).read()
     assert "oracle" not in src and "raise ImportError" in src
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header must compile as C99 (and C++), with no torch types
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "ib_cav.h"\nint main(void) { cav_desc c; ib_structure_desc d; (void)c; (void)d;'
+                   ' return ib_abi_version(); }\n')
+    inc = ["-I" + os.path.join(ROOT, "include")]
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    if os.path.isdir(cuda_inc):
+        inc.append("-I" + cuda_inc)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", *inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert "torch" not in open(os.path.join(ROOT, "include", "ib_cav.h")).read()

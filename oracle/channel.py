@@ -1,0 +1,163 @@
+"""The channel of the flow-past-a-fiber benchmark (Sec. 5.3): MAC operators with inflow and
+traction-outflow boundaries.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Domain [0, Lx) x [0, Ly], periodic in x, Nx x Ny square cells of side h.  Unknowns (3 Nx Ny,
+the same count and block order as the periodic grid):
+  u_{i,j}  at (i h, (j + 1/2) h),  i < Nx, j < Ny             index  j Nx + i
+  v_{i,j}  at ((i + 1/2) h, j h),  i < Nx, j < Ny             index  Nx Ny + j Nx + i
+           (row j = 0 lies on the outflow boundary y = 0; the faces on y = Ly are prescribed)
+  p_{i,j}  at cell centres                                     index  2 Nx Ny + j Nx + i
+
+Boundary conditions (Sec. 5.3):
+  top    y = Ly:  u = u_top, v = v_top(x)  (the prescribed inflow)
+  bottom y = 0:   sigma n = t, n = (0, -1), sigma = -p I + mu (grad u + grad u^T); the paper's
+                  backflow term (rho/2) min(u.n, 0) u enters through t, evaluated at the old
+                  velocity like the convective term.
+
+Discretisation (readings; the paper states the boundary conditions, not their stencils):
+the interior rows are the periodic grid's (Sec. 2): rho/dt u - mu L u + G p on velocity faces
+and -D u on cells.  Values outside the unknowns enter through ghost values:
+  * above the top row of u:  u_{i,Ny} = 2 u_top - u_{i,Ny-1}   (the wall value is the mean)
+  * the prescribed v_{i,Ny} = v_top(x_{i+1/2})
+  * below the bottom row of u, from the tangential traction -mu (du/dy + dv/dx) = t_x at
+    (i h, 0):  u_{i,-1} = u_{i,0} + (v_{i,0} - v_{i-1,0}) + h t_x / mu
+  * below the outflow row of v, from continuity in the ghost cell (i, -1):
+    v_{i,-1} = v_{i,0} + (u_{i+1,-1} - u_{i,-1})
+  * the ghost pressure, from the normal traction p - 2 mu dv/dy = t_y at y = 0 with
+    p(0) = (p_{i,0} + p_{i,-1}) / 2 and dv/dy(0) = (v_{i,1} - v_{i,-1}) / (2h):
+    p_{i,-1} = 2 t_y + 2 mu (v_{i,1} - v_{i,-1}) / h - p_{i,0}
+and the outflow faces v_{i,0} take the full-cell momentum row with these ghosts.  The
+traction boundary fixes the pressure level, so the system has no null space.
+
+The pins reproduce, exactly, three discrete solutions the scheme must keep: uniform inflow
+passing straight through the outflow, a linear shear layer against the inflow wall, and a
+hydrostatic pressure column under a body force.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class Channel:
+    Nx: int
+    Ny: int
+    h: float
+    rho: float
+    mu: float
+    dt: float
+
+    @property
+    def n(self) -> int:
+        return 3 * self.Nx * self.Ny
+
+    def iu(self, i, j):
+        return j * self.Nx + i % self.Nx
+
+    def iv(self, i, j):
+        return self.Nx * self.Ny + j * self.Nx + i % self.Nx
+
+    def ip(self, i, j):
+        return 2 * self.Nx * self.Ny + j * self.Nx + i % self.Nx
+
+
+class _Lin:
+    """A linear combination of unknowns plus a constant (for ghost values)."""
+
+    def __init__(self, terms=None, const=0.0):
+        self.t = dict(terms or {})
+        self.c = const
+
+    def __add__(self, o):
+        o = o if isinstance(o, _Lin) else _Lin(const=float(o))
+        t = dict(self.t)
+        for k, v in o.t.items():
+            t[k] = t.get(k, 0.0) + v
+        return _Lin(t, self.c + o.c)
+
+    def __rmul__(self, a):
+        return _Lin({k: a * v for k, v in self.t.items()}, a * self.c)
+
+    def __sub__(self, o):
+        return self + (-1.0) * (o if isinstance(o, _Lin) else _Lin(const=float(o)))
+
+    def __radd__(self, a):
+        return self + a
+
+    def __rsub__(self, a):
+        return _Lin(const=float(a)) - self
+
+
+def operator(ch: Channel, u_top=0.0, v_top=None, t_x=None, t_y=None):
+    """K0 (3 Nx Ny square, the Stokes part of K_E on the channel) and the boundary vector g,
+    such that the discrete equations read  K0 w = b + g  for a right-hand side b (body force
+    and rho/dt u^n on the velocity rows, 0 on the cells).  v_top: (Nx,) inflow at the top
+    faces; t_x: (Nx,) tangential traction at the points (i h, 0); t_y: (Nx,) normal traction
+    at ((i + 1/2) h, 0)."""
+    Nx, Ny, h, mu = ch.Nx, ch.Ny, ch.h, ch.mu
+    v_top = np.zeros(Nx) if v_top is None else np.asarray(v_top, dtype=np.float64)
+    t_x = np.zeros(Nx) if t_x is None else np.asarray(t_x, dtype=np.float64)
+    t_y = np.zeros(Nx) if t_y is None else np.asarray(t_y, dtype=np.float64)
+    U = lambda i, j: _Lin({ch.iu(i, j): 1.0})  # noqa: E731
+    V = lambda i, j: _Lin({ch.iv(i, j): 1.0})  # noqa: E731
+    P = lambda i, j: _Lin({ch.ip(i, j): 1.0})  # noqa: E731
+
+    def u_at(i, j):
+        if j == Ny:
+            return 2.0 * u_top - U(i, Ny - 1)
+        if j == -1:
+            return U(i, 0) + (V(i, 0) - V(i - 1, 0)) + h * t_x[i % Nx] / mu
+        return U(i, j)
+
+    def v_at(i, j):
+        if j == Ny:
+            return _Lin(const=v_top[i % Nx])
+        if j == -1:
+            return V(i, 0) + (u_at(i + 1, -1) - u_at(i, -1))
+        return V(i, j)
+
+    def p_at(i, j):
+        if j == -1:
+            return 2.0 * t_y[i % Nx] + (2.0 * mu / h) * (v_at(i, 1) - v_at(i, -1)) - P(i, 0)
+        return P(i, j)
+
+    rows, cols, vals = [], [], []
+    g = np.zeros(ch.n)
+
+    def emit(r, expr):
+        for c, a in expr.t.items():
+            if a != 0.0:
+                rows.append(r)
+                cols.append(c)
+                vals.append(a)
+        g[r] -= expr.c  # constants move to the right-hand side
+
+    a0, ih2, ih = ch.rho / ch.dt, 1.0 / (h * h), 1.0 / h
+    for j in range(Ny):
+        for i in range(Nx):
+            lap = (u_at(i + 1, j) + u_at(i - 1, j) + u_at(i, j + 1) + u_at(i, j - 1) - 4.0 * U(i, j))
+            emit(ch.iu(i, j), a0 * U(i, j) - (mu * ih2) * lap + ih * (P(i, j) - P(i - 1, j)))
+            lap = (v_at(i + 1, j) + v_at(i - 1, j) + v_at(i, j + 1) + v_at(i, j - 1) - 4.0 * V(i, j))
+            emit(ch.iv(i, j), a0 * V(i, j) - (mu * ih2) * lap + ih * (p_at(i, j) - p_at(i, j - 1)))
+            div = (u_at(i + 1, j) - u_at(i, j)) + (v_at(i, j + 1) - v_at(i, j))
+            emit(ch.ip(i, j), (-ih) * div)
+    K = sp.csr_matrix((vals, (rows, cols)), shape=(ch.n, ch.n))
+    K.sum_duplicates()
+    return K, g
+
+
+def fields(ch: Channel, u_fn, v_fn, p_fn) -> np.ndarray:
+    """The unknown vector sampled from point functions (u at u faces, v at v faces, p at
+    centres)."""
+    w = np.zeros(ch.n)
+    for j in range(ch.Ny):
+        for i in range(ch.Nx):
+            w[ch.iu(i, j)] = u_fn(i * ch.h, (j + 0.5) * ch.h)
+            w[ch.iv(i, j)] = v_fn((i + 0.5) * ch.h, j * ch.h)
+            w[ch.ip(i, j)] = p_fn((i + 0.5) * ch.h, (j + 0.5) * ch.h)
+    return w

@@ -1,0 +1,129 @@
+"""Pins of the oracle's channel operators (Sec. 5.3's inflow / traction-outflow boundaries).
+
+  * three discrete solutions the boundary treatment must keep exactly: uniform inflow passing
+    straight through the outflow, a linear shear layer against the inflow wall with the
+    matching tangential traction, and a hydrostatic pressure column under a body force with
+    the matching normal traction;
+  * away from the boundaries every row equals the periodic grid's (Sec. 2) row;
+  * the traction boundary fixes the pressure: the channel operator is nonsingular.
+"""
+import numpy as np
+import pytest
+
+from oracle import channel, grid
+
+
+def _ch(Nx=8, Ny=8, mu=0.3):
+    return channel.Channel(Nx=Nx, Ny=Ny, h=1.0 / Nx, rho=1.0, mu=mu, dt=0.05)
+
+
+def _rhs_velocity(ch, w, f_u=0.0, f_v=0.0):
+    """b = [rho/dt u^n + f; 0] with u^n = the velocity of w (a steady state)."""
+    b = np.zeros(ch.n)
+    NN = ch.Nx * ch.Ny
+    b[:2 * NN] = ch.rho / ch.dt * w[:2 * NN]
+    b[:NN] += f_u
+    b[NN:2 * NN] += f_v
+    return b
+
+
+@pytest.mark.parametrize("Nx,Ny", [(8, 8), (8, 12)])
+def test_uniform_inflow_passes_through_the_outflow(Nx, Ny):
+    ch = _ch(Nx, Ny)
+    U = 0.7
+    K, g = channel.operator(ch, u_top=0.0, v_top=np.full(Nx, -U))
+    w = channel.fields(ch, lambda x, y: 0.0, lambda x, y: -U, lambda x, y: 0.0)
+    r = K @ w - (_rhs_velocity(ch, w) + g)
+    assert np.abs(r).max() <= 1e-12 * (ch.rho / ch.dt) * U
+
+
+@pytest.mark.parametrize("u_top", [0.0, 0.4])
+def test_linear_shear_layer_with_its_traction(u_top):
+    ch = _ch(8, 10)
+    c, Ly = 1.3, ch.Ny * ch.h
+    K, g = channel.operator(ch, u_top=u_top, t_x=np.full(ch.Nx, ch.mu * c))
+    w = channel.fields(ch, lambda x, y: u_top + c * (Ly - y), lambda x, y: 0.0, lambda x, y: 0.0)
+    r = K @ w - (_rhs_velocity(ch, w) + g)
+    assert np.abs(r).max() <= 1e-12 * (ch.rho / ch.dt) * (abs(u_top) + c * Ly)
+
+
+def test_hydrostatic_column_with_its_normal_traction():
+    ch = _ch(8, 10)
+    gv, ty = 2.5, 0.4
+    K, g = channel.operator(ch, t_y=np.full(ch.Nx, ty))
+    w = channel.fields(ch, lambda x, y: 0.0, lambda x, y: 0.0, lambda x, y: ty + gv * y)
+    r = K @ w - (_rhs_velocity(ch, w, f_v=gv) + g)
+    assert np.abs(r).max() <= 1e-12 * gv
+
+
+def test_interior_rows_are_the_periodic_rows():
+    N = 12
+    ch = _ch(N, N)
+    K, _ = channel.operator(ch)
+    Kp = grid.reduced_operator(N, ch.h, ch.rho, ch.dt, ch.mu, None).tocsr()
+    NN = N * N
+    for j in range(2, N - 2):
+        for i in range(N):
+            for r in (ch.iu(i, j), ch.iv(i, j), ch.ip(i, j)):
+                a, b = K[r].toarray(), Kp[r].toarray()
+                assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (i, j, r // NN)
+
+
+def test_traction_outflow_fixes_the_pressure():
+    ch = _ch(6, 6)
+    K, _ = channel.operator(ch)
+    s = np.linalg.svd(K.toarray(), compute_uv=False)
+    assert s[-1] >= 1e-8 * s[0]
+    # the periodic operator, by contrast, annihilates the constant pressure
+    Kp = grid.reduced_operator(6, ch.h, ch.rho, ch.dt, ch.mu, None).toarray()
+    e = np.zeros(Kp.shape[0])
+    e[72:] = 1.0
+    assert np.abs(Kp @ e).max() <= 1e-12
+
+
+def _manufactured(mu, U=0.5):
+    """A smooth steady Stokes solution on the unit channel from a stream function psi =
+    cos(2 pi x) (1 - y)^2 (1 + y) plus uniform inflow -U: u = psi_y, v = -psi_x - U (divergence
+    free), zero velocity perturbation at the inflow wall y = 1, flow through the outflow; p
+    smooth.  Returns lambdas for u, v, p, the body force and the outflow tractions."""
+    import sympy as s
+    x, y = s.symbols("x y")
+    k = 2 * s.pi
+    psi = s.cos(k * x) * (1 - y) ** 2 * (1 + y)
+    u = s.diff(psi, y)
+    v = -s.diff(psi, x) - U
+    p = s.sin(k * x) * s.cos(y) + y
+    lap = lambda f: s.diff(f, x, 2) + s.diff(f, y, 2)  # noqa: E731
+    fu = -mu * lap(u) + s.diff(p, x)
+    fv = -mu * lap(v) + s.diff(p, y)
+    tx = -mu * (s.diff(u, y) + s.diff(v, x))       # (sigma n)_x at y = 0, n = (0, -1)
+    ty = p - 2 * mu * s.diff(v, y)                 # (sigma n)_y = -sigma_yy
+    L = lambda e: s.lambdify((x, y), e, "numpy")  # noqa: E731
+    return L(u), L(v), L(p), L(fu), L(fv), L(tx), L(ty)
+
+
+def test_manufactured_solution_converges():
+    mu = 0.5
+    u, v, p, fu, fv, tx, ty = _manufactured(mu)
+    errs = []
+    for N in (16, 32):
+        ch = _ch(N, N, mu=mu)
+        h = ch.h
+        xs = np.arange(N) * h
+        K, g = channel.operator(ch, u_top=0.0, v_top=v(xs + 0.5 * h, 1.0) + 0 * xs,
+                                t_x=tx(xs, 0.0) + 0 * xs, t_y=ty(xs + 0.5 * h, 0.0) + 0 * xs)
+        we = channel.fields(ch, u, v, p)
+        NN = N * N
+        b = np.zeros(ch.n)
+        b[:2 * NN] = ch.rho / ch.dt * we[:2 * NN]
+        b[:NN] += channel.fields(ch, fu, lambda a, c: 0.0, lambda a, c: 0.0)[:NN]
+        b[NN:2 * NN] += channel.fields(ch, lambda a, c: 0.0, fv, lambda a, c: 0.0)[NN:2 * NN]
+        import scipy.sparse.linalg as spla
+        w = spla.spsolve(K.tocsc(), b + g)
+        errs.append([np.abs(w[:NN] - we[:NN]).max(), np.abs(w[NN:2 * NN] - we[NN:2 * NN]).max(),
+                     np.abs(w[2 * NN:] - we[2 * NN:]).max()])
+    e16, e32 = np.array(errs)
+    # second order on every field (the errors at N = 16 / 32 are about 0.014 / 0.0034 on u,
+    # 0.033 / 0.0083 on v, 0.045 / 0.0115 on p); a wrong ghost value stalls it at O(1)
+    assert np.all(e32 <= 0.3 * e16), (e16, e32)
+    assert np.all(e32 <= 0.015), e32

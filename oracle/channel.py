@@ -161,3 +161,131 @@ def fields(ch: Channel, u_fn, v_fn, p_fn) -> np.ndarray:
             w[ch.iv(i, j)] = v_fn((i + 0.5) * ch.h, j * ch.h)
             w[ch.ip(i, j)] = p_fn((i + 0.5) * ch.h, (j + 0.5) * ch.h)
     return w
+
+
+# --------------------------------------------------------------------------- multigrid (Sec. 4)
+
+def prolong(chc: Channel) -> sp.csr_matrix:
+    """RT0 / bilinear prolongation from the channel chc to the one with twice its cells per
+    direction, as on the periodic grid (Sec. 4), with two boundary readings: a fine v row on a
+    coarse cell's midline next to the inflow wall takes half the coarse face below it (the
+    prescribed faces carry no correction), and the pressure's bilinear stencil is clamped to
+    the boundary cells in y (constant extrapolation of the correction)."""
+    Nxc, Nyc = chc.Nx, chc.Ny
+    chf = Channel(2 * Nxc, 2 * Nyc, chc.h / 2, chc.rho, chc.mu, chc.dt)
+    rows, cols, vals = [], [], []
+    for j in range(chf.Ny):
+        for i in range(chf.Nx):
+            r = chf.iu(i, j)
+            if i % 2 == 0:
+                rows.append(r); cols.append(chc.iu(i // 2, j // 2)); vals.append(1.0)
+            else:
+                for I in ((i - 1) // 2, (i + 1) // 2):
+                    rows.append(r); cols.append(chc.iu(I, j // 2)); vals.append(0.5)
+            r = chf.iv(i, j)
+            if j % 2 == 0:
+                rows.append(r); cols.append(chc.iv(i // 2, j // 2)); vals.append(1.0)
+            else:
+                for J in ((j - 1) // 2, (j + 1) // 2):
+                    if J < Nyc:
+                        rows.append(r); cols.append(chc.iv(i // 2, J)); vals.append(0.5)
+            r = chf.ip(i, j)
+            J0, sj = j // 2, (-1 if j % 2 == 0 else 1)
+            I0, si = i // 2, (-1 if i % 2 == 0 else 1)
+            for (dI, dJ, wt) in ((0, 0, 9 / 16), (si, 0, 3 / 16), (0, sj, 3 / 16), (si, sj, 1 / 16)):
+                J = min(max(J0 + dJ, 0), Nyc - 1)
+                rows.append(r); cols.append(chc.ip(I0 + dI, J)); vals.append(wt)
+    P = sp.csr_matrix((vals, (rows, cols)), shape=(chf.n, chc.n))
+    P.sum_duplicates()
+    return P
+
+
+def restrict(chc: Channel) -> sp.csr_matrix:
+    """(1/4) P^T on the velocities, the four-cell average on the pressure (Sec. 4)."""
+    P = prolong(chc).tocsc()
+    nvf, nvc = 2 * 4 * chc.Nx * chc.Ny, 2 * chc.Nx * chc.Ny
+    Rv = 0.25 * P[:nvf, :nvc].T
+    rows, cols, vals = [], [], []
+    for J in range(chc.Ny):
+        for I in range(chc.Nx):
+            for b in (0, 1):
+                for a in (0, 1):
+                    rows.append(J * chc.Nx + I)
+                    cols.append((2 * J + b) * (2 * chc.Nx) + 2 * I + a)
+                    vals.append(0.25)
+    Rp = sp.csr_matrix((vals, (rows, cols)), shape=(chc.Nx * chc.Ny, 4 * chc.Nx * chc.Ny))
+    return sp.block_diag([Rv, Rp], format="csr")
+
+
+def vanka_patches(ch: Channel) -> list:
+    """Standard Vanka patches V_ij (Sec. 3.1) of the channel in cell order; the cells next to
+    the inflow wall lose their prescribed top face (four unknowns)."""
+    out = []
+    for j in range(ch.Ny):
+        for i in range(ch.Nx):
+            d = [ch.iu(i, j), ch.iu(i + 1, j), ch.iv(i, j), ch.ip(i, j)]
+            if j + 1 < ch.Ny:
+                d.append(ch.iv(i, j + 1))
+            out.append(np.array(sorted(set(d)), dtype=np.int64))
+    return out
+
+
+class ChannelLevel:
+    def __init__(self, ch: Channel, K: sp.csr_matrix, patches=None, coarsest=False):
+        from . import smoother
+        self.ch, self.K = ch, K.tocsr()
+        self.Kc = self.K.tocsc()
+        self.coarsest = coarsest
+        if coarsest:
+            self.Kinv = np.linalg.inv(self.K.toarray())
+        else:
+            self.patches = vanka_patches(ch) if patches is None else patches
+            self.solvers = [smoother.PatchSolver(self.K, p) for p in self.patches]
+
+
+def hierarchy(ch: Channel, K: sp.csr_matrix, coarsest_N: int = 8, EE_levels=None) -> list:
+    """Levels from the finest channel (operator K, which may carry -dt E_E) down to Nx =
+    coarsest_N; coarser operators are the rediscretised channel Stokes operator with
+    homogeneous boundary data (corrections), plus -dt times EE_levels[l] when given."""
+    levels = []
+    l = 0
+    while True:
+        coarsest = ch.Nx // 2 < coarsest_N or ch.Nx % 2 or ch.Ny % 2
+        if l > 0:
+            K = operator(ch)[0]
+            if EE_levels is not None and EE_levels[l] is not None:
+                nv = 2 * ch.Nx * ch.Ny
+                K = (K - ch.dt * sp.bmat([[EE_levels[l], None], [None, sp.csr_matrix((ch.n - nv, ch.n - nv))]])).tocsr()
+        levels.append(ChannelLevel(ch, K, coarsest=coarsest))
+        if coarsest:
+            return levels
+        ch = Channel(ch.Nx // 2, ch.Ny // 2, 2 * ch.h, ch.rho, ch.mu, ch.dt)
+        l += 1
+
+
+def sweep(lev: ChannelLevel, w, b):
+    """One multiplicative sweep (Sec. 3.3) in cell order; the channel's pressure is
+    determined, so no mean is removed."""
+    w = w.copy()
+    r = b - lev.K @ w
+    for s in lev.solvers:
+        d = s.apply(r[s.dofs])
+        w[s.dofs] += d
+        r -= lev.Kc[:, s.dofs] @ d
+    return w
+
+
+def vcycle(levels, b, nu_pre=1, nu_post=1, li=0):
+    """z = B b: one V-cycle with zero initial guess on the channel hierarchy (Sec. 4)."""
+    lev = levels[li]
+    if lev.coarsest:
+        return lev.Kinv @ b
+    x = np.zeros_like(b)
+    for _ in range(nu_pre):
+        x = sweep(lev, x, b)
+    chc = levels[li + 1].ch
+    xc = vcycle(levels, restrict(chc) @ (b - lev.K @ x), nu_pre, nu_post, li + 1)
+    x = x + prolong(chc) @ xc
+    for _ in range(nu_post):
+        x = sweep(lev, x, b)
+    return x

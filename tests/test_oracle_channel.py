@@ -10,6 +10,7 @@
 import numpy as np
 import pytest
 
+import ib_workloads as W
 from oracle import channel, grid
 
 
@@ -127,3 +128,53 @@ def test_manufactured_solution_converges():
     # 0.033 / 0.0083 on v, 0.045 / 0.0115 on p); a wrong ghost value stalls it at O(1)
     assert np.all(e32 <= 0.3 * e16), (e16, e32)
     assert np.all(e32 <= 0.015), e32
+
+
+def test_channel_transfers():
+    # RT0 / bilinear prolongation with the inflow-wall reading: exact on velocities that vanish
+    # linearly at the wall (v = Ly - y) and on constants; restriction (1/4) P^T on velocities,
+    # averaging on the pressure (R 1 = 1)
+    chc = channel.Channel(6, 5, 1.0 / 6, 1.0, 0.1, 0.01)
+    chf = channel.Channel(12, 10, 1.0 / 12, 1.0, 0.1, 0.01)
+    Ly = chc.Ny * chc.h
+    P = channel.prolong(chc)
+    wc = channel.fields(chc, lambda x, y: 0.7, lambda x, y: Ly - y, lambda x, y: 2.0)
+    wf = channel.fields(chf, lambda x, y: 0.7, lambda x, y: Ly - y, lambda x, y: 2.0)
+    assert np.abs(P @ wc - wf).max() <= 1e-14
+    R = channel.restrict(chc)
+    nvc, nvf = 2 * chc.Nx * chc.Ny, 2 * chf.Nx * chf.Ny
+    assert np.abs((R[:nvc, :nvf] - 0.25 * P[:nvf, :nvc].T).toarray()).max() == 0.0
+    assert np.allclose(R[nvc:, nvf:] @ np.ones(chf.Nx * chf.Ny), 1.0)
+
+
+def test_channel_vanka_patches():
+    ch = _ch(6, 5)
+    pats = channel.vanka_patches(ch)
+    cover = np.zeros(ch.n, dtype=int)
+    for p in pats:
+        cover[p] += 1
+    assert cover.min() >= 1
+    sizes = np.array([len(p) for p in pats]).reshape(ch.Ny, ch.Nx)
+    assert np.all(sizes[:-1] == 5) and np.all(sizes[-1] == 4)
+
+
+def test_channel_multigrid_is_grid_independent():
+    # Vanka V-cycle (1 + 1 lexicographic multiplicative sweeps, 8 x 8 coarsest, direct solve
+    # there) as FGMRES preconditioner for the channel Stokes operator at the paper's viscosity
+    # and dt = h/2: the same count on every grid, and a contracting stationary cycle
+    from oracle import fgmres
+    its = []
+    for N in (16, 32):
+        ch = channel.Channel(N, N, 1.0 / N, 1.0, 1e-2, 0.5 / N)
+        K, _ = channel.operator(ch, v_top=np.full(N, -1.0))
+        levels = channel.hierarchy(ch, K)
+        b = W.uniform_pm1(40 + N, ch.n)
+        _, info = fgmres.fgmres(lambda v: K @ v, b, lambda r: channel.vcycle(levels, r), rtol=1e-10, maxit=60,
+                                ref="r0")
+        assert info["converged"]
+        its.append(info["iters"])
+        x = np.zeros(ch.n)
+        for _ in range(4):
+            x = x + channel.vcycle(levels, b - K @ x)
+        assert np.linalg.norm(b - K @ x) <= 0.3 ** 4 * np.linalg.norm(b)
+    assert abs(its[0] - its[1]) <= 1 and max(its) <= 15, its

@@ -289,3 +289,68 @@ def vcycle(levels, b, nu_pre=1, nu_post=1, li=0):
     for _ in range(nu_post):
         x = sweep(lev, x, b)
     return x
+
+
+# --------------------------------------------------------------------------- IB coupling
+
+def cav_patches(ch: Channel, pattern) -> list:
+    """CAV patches (Eq. cav_patch_set) on the channel, cell by cell: U^ = U_ij plus every
+    velocity coupled to U_ij through E_E's pattern (either direction); if that adds nothing the
+    cell keeps its Vanka patch, else the patch is the union of the Vanka patches of the cells
+    incident to U^ -- a u face's two neighbouring cells, a v face's cells below and above, the
+    outflow row's faces having only the cell above."""
+    Nx, Ny = ch.Nx, ch.Ny
+    NN = Nx * Ny
+    Pr = sp.csr_matrix(pattern, dtype=bool)
+    Pc = Pr.T.tocsr()
+    van = vanka_patches(ch)
+    out = []
+    for c in range(NN):
+        U = [int(k) for k in van[c] if k < 2 * NN]
+        Uh = set(U)
+        for k in U:
+            Uh.update(int(l) for l in Pr.indices[Pr.indptr[k]:Pr.indptr[k + 1]])
+            Uh.update(int(l) for l in Pc.indices[Pc.indptr[k]:Pc.indptr[k + 1]])
+        if Uh == set(U):
+            out.append(van[c])
+            continue
+        cells = set()
+        for k in Uh:
+            comp, rem = divmod(k, NN)
+            j, i = divmod(rem, Nx)
+            if comp == 0:
+                cells.update({j * Nx + (i - 1) % Nx, j * Nx + i})
+            else:
+                cells.add(j * Nx + i)
+                if j >= 1:
+                    cells.add((j - 1) * Nx + i)
+        out.append(np.array(sorted(set().union(*(set(van[q].tolist()) for q in cells))), dtype=np.int64))
+    return out
+
+
+def galerkin_elasticity(EE_f: sp.csr_matrix, chc: Channel) -> sp.csr_matrix:
+    """E_E on the coarse channel: R_v E_E P_v with the channel's velocity transfers (Sec. 4)."""
+    P = prolong(chc).tocsc()
+    nvf, nvc = 2 * 4 * chc.Nx * chc.Ny, 2 * chc.Nx * chc.Ny
+    Pv = P[:nvf, :nvc]
+    return (0.25 * Pv.T @ EE_f @ Pv).tocsr()
+
+
+def ib_hierarchy(ch: Channel, EE: sp.csr_matrix, pattern, coarsest_N: int = 8):
+    """The finest operator K_E = K0 - dt [[E_E, 0], [0, 0]] and its CAV hierarchy on the
+    channel: Galerkin E_E and structural patterns level by level, CAV patches from them."""
+    levels = []
+    c, EEl, patl = ch, EE.tocsr(), sp.csr_matrix(pattern, dtype=bool)
+    while True:
+        nv = 2 * c.Nx * c.Ny
+        K = (operator(c)[0] - c.dt * sp.bmat([[EEl, None], [None, sp.csr_matrix((c.n - nv, c.n - nv))]])).tocsr()
+        coarsest = c.Nx // 2 < coarsest_N or c.Nx % 2 or c.Ny % 2
+        levels.append(ChannelLevel(c, K, patches=None if coarsest else cav_patches(c, patl), coarsest=coarsest))
+        if coarsest:
+            return levels
+        cc = Channel(c.Nx // 2, c.Ny // 2, 2 * c.h, c.rho, c.mu, c.dt)
+        EEl = galerkin_elasticity(EEl, cc)
+        Pv = prolong(cc).tocsc()[:2 * 4 * cc.Nx * cc.Ny, :2 * cc.Nx * cc.Ny]
+        Pb = sp.csr_matrix(Pv != 0, dtype=np.float64)
+        patl = sp.csr_matrix((Pb.T @ sp.csr_matrix(patl, dtype=np.float64) @ Pb) != 0, dtype=bool)
+        c = cc

@@ -178,3 +178,30 @@ def test_channel_multigrid_is_grid_independent():
             x = x + channel.vcycle(levels, b - K @ x)
         assert np.linalg.norm(b - K @ x) <= 0.3 ** 4 * np.linalg.norm(b)
     assert abs(its[0] - its[1]) <= 1 and max(its) <= 15, its
+
+
+def test_fiber_in_the_channel_matches_the_papers_linear_counts():
+    # Sec. 5.3's fiber (N = 16: a 32 x 32 channel, 13 markers) in its channel: CAV patches and
+    # Galerkin E_E agree with the periodic construction away from the boundaries, and the
+    # first linear system's CAV-preconditioned FGMRES (1 + 1 sweeps, 8 x 8 coarsest, 1e-9)
+    # takes a count within the paper's range (8.65 on average per Newton solve, 13 at most)
+    from oracle import fgmres, ib, multigrid, patches
+    rec = W.fiber_periodic(16)
+    ch = channel.Channel(rec.N, rec.N, rec.h, rec.rho, rec.mu, rec.dt)
+    EE, pat = ib.eulerian_elasticity(rec)
+    N, NN = rec.N, rec.N ** 2
+    per = patches.cav_patches(N, pat)
+    mine = channel.cav_patches(ch, pat)
+    for c, (a, b) in enumerate(zip(per, mine)):
+        if c // N < N - 1:          # all but the inflow row, whose Vanka patches lose a face
+            assert np.array_equal(a, b), c
+        else:
+            assert len(a) == 5 and len(b) == 4
+    EEc_per, _ = multigrid.galerkin_elasticity(EE, pat, N // 2)
+    EEc = channel.galerkin_elasticity(EE, channel.Channel(N // 2, N // 2, 2 * ch.h, 1.0, 1.0, 1.0))
+    assert np.abs((EEc - EEc_per).toarray()).max() <= 1e-12 * np.abs(EEc_per).max()
+    levels = channel.ib_hierarchy(ch, EE, pat)
+    K = levels[0].K
+    _, info = fgmres.fgmres(lambda v: K @ v, ib.first_step_rhs(rec), lambda r: channel.vcycle(levels, r),
+                            rtol=1e-9, maxit=150, ref="r0")
+    assert info["converged"] and abs(info["iters"] - 8.65) <= 3 and info["iters"] <= 13, info["iters"]

@@ -23,7 +23,8 @@ and no blocking, fusion or reordering:
   twogrid    two-grid iteration matrix and its spectrum            (Sec. 5.1, Table 1)
   fiber      nonlinear fiber energies, force and Newton tangent    (Sec. 5.3)
   newton     Newton's method for one semi-implicit step            (Sec. 5.3)
-  channel    MAC operators of the inflow / traction-outflow channel (Sec. 5.3)
+  channel    the inflow / traction-outflow channel: MAC operators, multigrid, the
+             fiber's linear systems and its Newton time step          (Sec. 5.3)
 """
 from . import grid, ib, patches, smoother, colouring, multigrid, fgmres, twogrid, fiber, newton  # noqa: F401
 from . import channel  # noqa: F401

@@ -354,3 +354,137 @@ def ib_hierarchy(ch: Channel, EE: sp.csr_matrix, pattern, coarsest_N: int = 8):
         Pb = sp.csr_matrix(Pv != 0, dtype=np.float64)
         patl = sp.csr_matrix((Pb.T @ sp.csr_matrix(patl, dtype=np.float64) @ Pb) != 0, dtype=bool)
         c = cc
+
+
+# --------------------------------------------------------------------------- time step (Sec. 5.3)
+
+def inflow_speed(t: float, U: float = 1.0, T_ramp: float = 0.5625) -> float:
+    """Magnitude of the downward inflow at time t: raised smoothly from 0 to U over [0, T_ramp]
+    (the paper says "smoothly"; the reading is the half-cosine ramp U (1 - cos(pi t / T)) / 2)."""
+    if t >= T_ramp:
+        return U
+    return U * 0.5 * (1.0 - np.cos(np.pi * t / T_ramp))
+
+
+def _ghosts(ch: Channel, w, u_top, v_top, t_x):
+    """Padded velocity arrays with the boundary ghosts of the operator: u (Ny + 2, Nx) over rows
+    -1 .. Ny, v (Ny + 2, Nx) over rows -1 .. Ny (row Ny prescribed)."""
+    Nx, Ny, h, mu = ch.Nx, ch.Ny, ch.h, ch.mu
+    NN = Nx * Ny
+    u = w[:NN].reshape(Ny, Nx)
+    v = w[NN:2 * NN].reshape(Ny, Nx)
+    U = np.zeros((Ny + 2, Nx))
+    V = np.zeros((Ny + 2, Nx))
+    U[1:Ny + 1] = u
+    U[Ny + 1] = 2.0 * u_top - u[Ny - 1]
+    U[0] = u[0] + (v[0] - np.roll(v[0], 1)) + h * t_x / mu
+    V[1:Ny + 1] = v
+    V[Ny + 1] = v_top
+    V[0] = v[0] + (np.roll(U[0], -1) - U[0])
+    return U, V
+
+
+def convection(ch: Channel, w, u_top=0.0, v_top=None, t_x=None) -> np.ndarray:
+    """N[u] = (u . grad) u on the velocity faces (2 Nx Ny), centred differences, each
+    component averaged from its four neighbours onto the other's faces (Sec. 2's explicit
+    convective term); boundary values through the operator's ghosts."""
+    Nx, Ny, h = ch.Nx, ch.Ny, ch.h
+    v_top = np.zeros(Nx) if v_top is None else np.asarray(v_top, dtype=np.float64)
+    t_x = np.zeros(Nx) if t_x is None else np.asarray(t_x, dtype=np.float64)
+    U, V = _ghosts(ch, w, u_top, v_top, t_x)
+    # u faces (rows 0 .. Ny-1 = padded 1 .. Ny)
+    u = U[1:Ny + 1]
+    dudx = (np.roll(u, -1, 1) - np.roll(u, 1, 1)) / (2 * h)
+    dudy = (U[2:Ny + 2] - U[0:Ny]) / (2 * h)
+    vbar = 0.25 * (V[1:Ny + 1] + np.roll(V[1:Ny + 1], 1, 1) + V[2:Ny + 2] + np.roll(V[2:Ny + 2], 1, 1))
+    Nu = u * dudx + vbar * dudy
+    # v faces (rows 0 .. Ny-1)
+    v = V[1:Ny + 1]
+    dvdx = (np.roll(v, -1, 1) - np.roll(v, 1, 1)) / (2 * h)
+    dvdy = (V[2:Ny + 2] - V[0:Ny]) / (2 * h)
+    ubar = 0.25 * (U[1:Ny + 1] + np.roll(U[1:Ny + 1], -1, 1) + U[0:Ny] + np.roll(U[0:Ny], -1, 1))
+    Nv = ubar * dvdx + v * dvdy
+    return np.concatenate([Nu.ravel(), Nv.ravel()])
+
+
+def backflow_traction(ch: Channel, w):
+    """t = (rho/2) min(u.n, 0) u at the outflow y = 0, n = (0, -1), from the velocity w (the
+    previous step's): t_x at the points (i h, 0), t_y at ((i + 1/2) h, 0).  The boundary u is
+    extrapolated from the first two rows, (3 u_0 - u_1)/2; v at (i h, 0) is the mean of its
+    two neighbours."""
+    Nx, Ny = ch.Nx, ch.Ny
+    NN = Nx * Ny
+    u = w[:NN].reshape(Ny, Nx)
+    v = w[NN:2 * NN].reshape(Ny, Nx)
+    ub = 0.5 * (3.0 * u[0] - u[1])
+    vb_u = 0.5 * (v[0] + np.roll(v[0], 1))        # v at (i h, 0)
+    ub_v = 0.5 * (ub + np.roll(ub, -1))           # u at ((i + 1/2) h, 0)
+    t_x = 0.5 * ch.rho * np.minimum(-vb_u, 0.0) * ub
+    t_y = 0.5 * ch.rho * np.minimum(-v[0], 0.0) * v[0]
+    return t_x, t_y
+
+
+def fiber_step(ch: Channel, rec, w_n, t_next: float, solver: str = "direct", rtol=1e-8, atol=1e-8,
+               maxit=20, fgmres_rtol=1e-9):
+    """One time step of Sec. 5.3's scheme in the channel, from the velocity-pressure w_n at t^n
+    and the fiber configuration rec.X = X^n to t^{n+1} = t_next:
+
+        rho/dt (u - u^n) + rho N[u^n] - mu L u + G p = S^n F(X^n + dt J^n u),   -D u = 0,
+
+    the inflow v = -U(t^{n+1}) on the top wall, the traction outflow with the backflow term at
+    u^n, the convective term explicit at u^n.  Newton's method on (u, p) (oracle/newton.py's
+    iteration) with each linear system solved directly ("direct") or by CAV-preconditioned
+    FGMRES with the hierarchy rebuilt per Newton system ("cav", 1 + 1 sweeps, to fgmres_rtol,
+    as the paper does).  Returns (w, X^{n+1}, residual history, FGMRES counts)."""
+    from dataclasses import replace
+
+    import scipy.sparse.linalg as spla
+
+    from . import fgmres, ib
+    Nx = ch.Nx
+    NN2 = 2 * Nx * ch.Ny
+    S = ib.spreading_matrix(rec.N, rec.h, rec.X, rec.omega)
+    J = ib.interpolation_matrix(rec.N, rec.h, rec.X)
+    Xn = np.concatenate([rec.X[:, 0], rec.X[:, 1]])
+    M = rec.M
+    v_top_n = np.full(Nx, -inflow_speed(t_next - ch.dt))
+    v_top = np.full(Nx, -inflow_speed(t_next))
+    t_x, t_y = backflow_traction(ch, w_n)
+    K0, g = operator(ch, 0.0, v_top, t_x, t_y)
+    b = np.zeros(ch.n)
+    b[:NN2] = ch.rho / ch.dt * w_n[:NN2] - ch.rho * convection(ch, w_n, 0.0, v_top_n, t_x)
+    b += g
+
+    def force_at(u):
+        Xk = Xn + ch.dt * (J @ u)
+        rk = replace(rec, meta={**rec.meta, "X_lin": np.stack([Xk[:M], Xk[M:]], 1)})
+        return rk, ib.force_vector(rk)
+
+    def residual(w):
+        _, F = force_at(w[:NN2])
+        R = K0 @ w - b
+        R[:NN2] -= S @ F
+        return R
+
+    w = np.array(w_n, dtype=np.float64)
+    hist = [np.linalg.norm(residual(w))]
+    its = []
+    k = 0
+    while k < maxit and hist[-1] > max(rtol * hist[0], atol):
+        rk, F = force_at(w[:NN2])
+        EE, pat = ib.eulerian_elasticity(rk)
+        E, _ = ib.elasticity(rk)
+        K = (K0 - ch.dt * sp.bmat([[EE, None], [None, sp.csr_matrix((ch.n - NN2, ch.n - NN2))]])).tocsr()
+        rhs = b.copy()
+        rhs[:NN2] += S @ (F - ch.dt * (E @ (J @ w[:NN2])))
+        if solver == "direct":
+            w = spla.spsolve(K.tocsc(), rhs)
+        else:
+            levels = ib_hierarchy(ch, EE, pat)
+            w, info = fgmres.fgmres(lambda v: K @ v, rhs, lambda r: vcycle(levels, r), rtol=fgmres_rtol,
+                                    maxit=150, ref="r0")
+            its.append(info["iters"])
+        k += 1
+        hist.append(np.linalg.norm(residual(w)))
+    X_next = Xn + ch.dt * (J @ w[:NN2])
+    return w, np.stack([X_next[:M], X_next[M:]], 1), hist, its

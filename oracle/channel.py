@@ -243,19 +243,16 @@ class ChannelLevel:
             self.solvers = [smoother.PatchSolver(self.K, p) for p in self.patches]
 
 
-def hierarchy(ch: Channel, K: sp.csr_matrix, coarsest_N: int = 8, EE_levels=None) -> list:
-    """Levels from the finest channel (operator K, which may carry -dt E_E) down to Nx =
-    coarsest_N; coarser operators are the rediscretised channel Stokes operator with
-    homogeneous boundary data (corrections), plus -dt times EE_levels[l] when given."""
+def hierarchy(ch: Channel, K: sp.csr_matrix, coarsest_N: int = 8) -> list:
+    """Vanka levels from the finest channel (operator K) down to Nx = coarsest_N; coarser
+    operators are the rediscretised channel Stokes operator with homogeneous boundary data
+    (corrections).  ib_hierarchy below adds a structure's E_E and CAV patches."""
     levels = []
     l = 0
     while True:
         coarsest = ch.Nx // 2 < coarsest_N or ch.Nx % 2 or ch.Ny % 2
         if l > 0:
             K = operator(ch)[0]
-            if EE_levels is not None and EE_levels[l] is not None:
-                nv = 2 * ch.Nx * ch.Ny
-                K = (K - ch.dt * sp.bmat([[EE_levels[l], None], [None, sp.csr_matrix((ch.n - nv, ch.n - nv))]])).tocsr()
         levels.append(ChannelLevel(ch, K, coarsest=coarsest))
         if coarsest:
             return levels

@@ -40,8 +40,9 @@ NU_COARSE_ADDITIVE = 4
 DEFAULT_ALPHA = 0.85
 MAXIT = 150
 
-# DRAM traffic of one finest-level patch-apply launch from the committed ncu capture
-# (profiles/patch_apply_membrane_N256.md), valid only for the kernel source it was taken on.
+# DRAM traffic of one finest-level patch-apply launch from an ncu capture of the same bench
+# command (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source it
+# was taken on (keyed by the hash of sweep.cu); null once that source changes.
 NCU_TRAFFIC = {
     # k_patch_apply_tma<float, 4, 8192> (autotuned variant 3), 289.63 MB read + 4.34 MB written
     "fp32:256:89dc173dabe61e5e": 293.97e6,
@@ -135,14 +136,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_sample(timeout_s: int = 600):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+def cpu_baseline_sample(iters: int, timeout_s: int = 600):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same workload: one
+    oracle V-cycle (timed alone), and the oracle's own FGMRES run for `iters` iterations with
+    the identity in place of the V-cycle (Arnoldi with modified Gram-Schmidt, Givens, the
+    K_E products and the final update at the solve's real Krylov dimensions; rtol 0 so it
+    runs all of them).  A solve is then iters x V-cycle + that FGMRES run."""
     code = r"""
 import json, os, sys, time
 sys.path.insert(0, %r)
 import numpy as np
 import ib_workloads as W
-from oracle import multigrid as mg
+from oracle import fgmres as fg, multigrid as mg
 rec = W.config2(256, 1e4)
 t0 = time.perf_counter()
 levels = mg.build_hierarchy(rec, 8, "cav")
@@ -151,10 +156,12 @@ b = rec.rhs()
 K = levels[0].KE
 t0 = time.perf_counter()
 z = mg.vcycle(levels, b, %d, %d, "additive", %r)
-y = K @ z
-t_iter = time.perf_counter() - t0
-print(json.dumps({"t_setup": t_setup, "t_iter": t_iter}))
-""" % (ROOT, DEFAULT_NU, DEFAULT_NU, DEFAULT_ALPHA)
+t_vcycle = time.perf_counter() - t0
+t0 = time.perf_counter()
+fg.fgmres(lambda v: K @ v, b, lambda r: r, rtol=0.0, maxit=%d)
+t_rest = time.perf_counter() - t0
+print(json.dumps({"t_setup": t_setup, "t_vcycle": t_vcycle, "t_rest": t_rest}))
+""" % (ROOT, DEFAULT_NU, DEFAULT_NU, DEFAULT_ALPHA, iters)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
         out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
@@ -176,6 +183,7 @@ def golden_iters():
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    import oracle.fgmres as fg
     import oracle.multigrid as mg
     rec = workload()
     t0 = time.perf_counter()
@@ -184,11 +192,15 @@ def run_reference(args, rank, world):
     b = rec.rhs()
     K = levels[0].KE
     g = golden_iters()
-    iters = g["iters"] if g else None
+    iters = g["iters"] if g else 77
+    # the oracle's FGMRES without its V-cycles (identity preconditioner, all `iters` iterations):
+    # Arnoldi, Givens, K_E products and the final update at the solve's Krylov dimensions
+    t0 = time.perf_counter()
+    fg.fgmres(lambda v: K @ v, b, lambda r: r, rtol=0.0, maxit=iters)
+    t_rest = time.perf_counter() - t0
 
     def step():
-        z = mg.vcycle(levels, b, DEFAULT_NU, DEFAULT_NU, "additive", DEFAULT_ALPHA)
-        return K @ z
+        return mg.vcycle(levels, b, DEFAULT_NU, DEFAULT_NU, "additive", DEFAULT_ALPHA)
 
     for _ in range(args.warmup):
         step()
@@ -197,12 +209,13 @@ def run_reference(args, rank, world):
         t = time.perf_counter()
         step()
         times.append(time.perf_counter() - t)
-    t_iter = statistics.mean(times)
-    value = 1.0 / (t_iter * iters) if iters else None
-    sample = (f"each step = one oracle FGMRES iteration's V-cycle ({DEFAULT_NU}+{DEFAULT_NU} additive "
-              f"sweeps) plus one K_E product on the full N=256 system; solves/s = 1 / (mean step time x "
-              f"{iters} iterations, the oracle's own count from tests/golden); hierarchy set-up "
-              f"{t_setup:.1f} s untimed")
+    t_iter = statistics.mean(times) + t_rest / iters
+    value = 1.0 / (t_iter * iters)
+    sample = (f"each step = one oracle V-cycle ({DEFAULT_NU}+{DEFAULT_NU} additive sweeps) on the full "
+              f"N=256 system; solves/s = 1 / ({iters} x mean step time + {t_rest:.2f} s, the oracle's own "
+              f"FGMRES run for {iters} iterations with the identity in place of the V-cycle: Arnoldi, "
+              f"Givens, K_E products); {iters} = the oracle's own iteration count (tests/golden); "
+              f"hierarchy set-up {t_setup:.1f} s untimed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_iter, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -269,9 +282,11 @@ def run_batch(args, api, torch, dist, rank, world, local):
     launches = api.ib_launch_count() - launches0
     clk = clocks.stop()
     total = max_over_ranks(sum(times), dist, dev)
-    value = whole_job_rate(len(recs) * args.steps, world, total)
     its = [i["iters"] for i in last]
     conv = [i["converged"] for i in last]
+    # only systems that reached 1e-10 count as solved; attempted systems are reported beside
+    value = whole_job_rate(int(sum(conv)) * args.steps, world, total)
+    attempted = whole_job_rate(len(recs) * args.steps, world, total)
     kappa = [r.k_bend if r.law == W.LAW_BEAM else (r.k_stretch if r.law == W.LAW_MEMBRANE else r.k_target)
              for r in recs]  # each system's drawn stiffness (the law's primary coefficient)
     stiff = sorted(range(len(recs)), key=lambda q: -kappa[q])
@@ -281,7 +296,8 @@ def run_batch(args, api, torch, dist, rank, world, local):
         for l in range(api.cav_num_levels(h) - 1):
             v = api.cav_get_level_info(h, l)["apply_variant"]
             variants[v] = variants.get(v, 0) + 1
-    line = {"metric": METRIC, "value": value, "unit": "systems solved/s (64-system batches)",
+    line = {"metric": METRIC, "value": value, "unit": "systems solved to 1e-10 per s (64-system batches)",
+            "attempted_systems_per_s": attempted,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
@@ -298,6 +314,34 @@ def run_batch(args, api, torch, dist, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def graph_sweep_ms(api, torch, hier, b, reps: int = 10) -> float:
+    """Device time of one finest-level cav_sweep: `reps` sweeps captured into one CUDA graph
+    (cav_sweep skips its host-side status check while captured), replayed three times, the
+    median replay / reps.  The finest level's inverses (hundreds of MB) exceed L2, so every
+    sweep streams them from HBM."""
+    w = torch.zeros_like(b)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            api.cav_sweep(hier, 0, b, w)  # warm-up outside capture (checks the status word)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            api.cav_sweep(hier, 0, b, w)
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / reps)
+    api.cav_sweep(hier, 0, b, w)  # reads the status word the replays may have set
+    return statistics.median(ts)
 
 
 def run_beam512(args, api, torch, rank):
@@ -325,16 +369,11 @@ def run_beam512(args, api, torch, rank):
         for _ in range(3):
             api.cav_sweep(h, 0, b, w)
         api.cav_profile(h, True)
-        sw = []
         for _ in range(10):
-            flush.zero_()
-            s0, s1 = ev(), ev()
-            s0.record()
             api.cav_sweep(h, 0, b, w)
-            s1.record()
-            torch.cuda.synchronize()
-            sw.append(s0.elapsed_time(s1))
         n_apply, apply_ms = api.cav_profile_read(h)
+        api.cav_profile(h, False)
+        sw = [graph_sweep_ms(api, torch, h, b)]
         api.cav_profile(h, False)
         x = torch.zeros_like(b)
         t1 = time.perf_counter()
@@ -511,19 +550,7 @@ def main():
     s_b = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
     sweep_bytes = (li0["enlarged_sum_n2"] * s_b + li0["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8 + 4 + 8)
                    + 3 * NN * 8 * 3 + 3 * NN * 8 * 3 + li0["ee_nnz"] * 12 + 3 * NN * 8 + 2 * NN * 8)
-    ws = torch.zeros_like(b)
-    for _ in range(3):
-        api.cav_sweep(hier, 0, b, ws)
-    sw_times = []
-    for _ in range(10):
-        flush.zero_()
-        s0, s1 = ev(), ev()
-        s0.record()
-        api.cav_sweep(hier, 0, b, ws)
-        s1.record()
-        torch.cuda.synchronize()
-        sw_times.append(s0.elapsed_time(s1))
-    sweep_ms = statistics.median(sw_times)
+    sweep_ms = graph_sweep_ms(api, torch, hier, b)
     sweep_gbs = sweep_bytes / (sweep_ms * 1e-3) / 1e9
 
     # the V-cycle alone (graph replay + its two staging copies), to split a solve's time
@@ -599,16 +626,7 @@ def main():
                 torch.cuda.synchronize()
                 ot.append(s0.elapsed_time(s1))
                 oit.append(inf["iters"])
-            wo = torch.zeros_like(b)
-            for _ in range(3):
-                api.cav_sweep(ho, 0, b, wo)
-            s0, s1 = ev(), ev()
-            s0.record()
-            for _ in range(10):
-                api.cav_sweep(ho, 0, b, wo)
-            s1.record()
-            torch.cuda.synchronize()
-            o_sweep = s0.elapsed_time(s1) / 10
+            o_sweep = graph_sweep_ms(api, torch, ho, b)
             ncol = [api.cav_get_level_info(ho, l)["n_colours"] for l in range(api.cav_num_levels(ho) - 1)]
             others.append({"smoother": o_sm, "coloured_levels": o_cl if o_sm == "coloured" else None, "nu": o_nu,
                            "nu_additive_levels": NU_COARSE_ADDITIVE if (o_sm == "coloured" and o_cl) else None,
@@ -629,7 +647,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": workload_desc(rec), "precision": args.precision + " enlarged-patch inverses",
+        "config": {"workload": workload_desc(rec),
+                   "measures": (f"{args.precision.upper()} enlarged-patch inverses (FP64 everywhere else), "
+                                f"{smoother_desc(args)}, zero initial guess: the mixed-precision form "
+                                f"without the learned guess (the learned guess is measured by "
+                                f"--workload learned); plain FP64 is reported as plain_fp64"),
+                   "precision": args.precision + " enlarged-patch inverses",
                    "nu": args.nu, "alpha": args.alpha, "coarsest_N": 8, "maxit": MAXIT,
                    "smoother": smoother_desc(args),
                    "l2": "flushed (256 MB write) before every timed solve",
@@ -641,7 +664,8 @@ def main():
         "vcycle_ms": vcycle_ms,
         "sweep": {"level": 0, "ms": sweep_ms, "algorithmic_bytes": sweep_bytes, "gbs": sweep_gbs,
                   "frac_of_hbm": sweep_gbs / peaks()[0],
-                  "note": "one cav_sweep on the finest level, L2 flushed before each of 10 timed calls"},
+                  "note": "one cav_sweep on the finest level: 10 sweeps captured in a CUDA graph, median of "
+                          "3 replays / 10 (the inverses exceed L2, so each sweep streams them from HBM)"},
         "setup_plus_solve_per_s": world / ((setup_ms + total_ms / args.steps) / 1e3),
         "apply_variant_finest": li["apply_variant"], "apply_variant_us_finest": li["apply_us"],
         "roofline": {"bound": "hbm",
@@ -658,15 +682,18 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and rec.N == 256:
-        cb = cpu_baseline_sample()
         g = golden_iters()
         it = g["iters"] if g else int(statistics.median(iters))
-        if "t_iter" in cb:
+        cb = cpu_baseline_sample(it)
+        if "t_vcycle" in cb:
+            t_solve = it * cb["t_vcycle"] + cb["t_rest"]
             line["cpu_baseline"] = {
-                "value": 1.0 / (cb["t_iter"] * it), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                "sample": (f"one oracle V-cycle ({args.nu}+{args.nu} additive sweeps) plus one K_E product on the "
-                           f"same N=256 system, {cb['t_iter']:.2f} s, scaled by {it} iterations per solve; "
-                           f"oracle hierarchy set-up {cb['t_setup']:.1f} s not timed")}
+                "value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"the oracle's solve of the same N=256 system ({DEFAULT_NU}+{DEFAULT_NU} additive "
+                           f"V-cycles, its own count of {it} iterations) = {it} x one timed oracle V-cycle "
+                           f"({cb['t_vcycle']:.2f} s) + the oracle's FGMRES run for {it} iterations with the "
+                           f"identity in place of the V-cycle ({cb['t_rest']:.2f} s: Arnoldi, Givens, K_E "
+                           f"products); oracle hierarchy set-up {cb['t_setup']:.1f} s not timed")}
         else:
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                     "sample": "failed: " + cb.get("error", "?")}

@@ -40,13 +40,14 @@ typedef enum {
   IB_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed                    */
   IB_ERR_SINGULAR = 4,  /* a local patch matrix had a zero pivot (Sec. 3.3 factorisation)  */
   IB_ERR_NOCONV = 5,    /* FGMRES stopped at maxit above tolerance; x holds the last iterate */
-  IB_ERR_TIMEOUT = 6,   /* reserved: a bounded device-side wait gave up                   */
+  IB_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out (about a second); the call's
+                           output is not valid, the device stays usable                   */
   IB_ERR_INTERNAL = 7   /* a device-side consistency check failed (e.g. a stencil window) */
 } ib_status;
 
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 const char* ib_last_error(void);
-/* ABI version of this header: 2 (cav_desc.smoother, cav_level_info.n_colours). */
+/* ABI version of this header: 4 (ib_grid_desc.bc; ib_test_wait_stall). */
 int ib_abi_version(void);
 /* Number of kernels this library has launched in this process (host-side count). */
 int64_t ib_launch_count(void);
@@ -55,10 +56,18 @@ int64_t ib_launch_count(void);
 
 typedef enum { IB_FORCE_TARGET = 0, IB_FORCE_MEMBRANE = 1, IB_FORCE_BEAM = 2, IB_FORCE_FIBER = 3 } ib_force_law;
 
+/* Boundary conditions of the Eulerian grid (ABI 4):
+ *   periodic  the periodic unit cell of Sec. 2 (every experiment of Sec. 5.1 and 5.2);
+ *   channel   the flow-past-a-fiber channel of Sec. 5.3: periodic in x, a prescribed inflow
+ *             on the top wall y = L and a traction outflow on y = 0 (not yet accepted:
+ *             ib_setup returns IB_ERR_INVALID for it).                                   */
+typedef enum { IB_BC_PERIODIC = 0, IB_BC_CHANNEL = 1 } ib_bc;
+
 typedef struct {
   int32_t N;       /* cells per direction (>= 8; even to allow coarsening)              */
-  double L;        /* side of the periodic square                                        */
+  double L;        /* side of the square                                                 */
   double rho, mu, dt;
+  int32_t bc;      /* ib_bc (ABI 4)                                                      */
 } ib_grid_desc;
 
 /* Force laws (Lagrangian elasticity matrix E, acting identically on x and y):
@@ -228,6 +237,10 @@ ib_status cav_ee_export(const cav_hierarchy* h, int32_t level, int64_t* rowptr,
  *   w_p <- w_p + K_{E,p}^{-1} (b - K_E w)_p  (multiplicative Schwarz, Sec. 3.3). */
 ib_status cav_sweep(const cav_hierarchy* h, int32_t level, const double* b, double* w,
                     cudaStream_t stream);
+/* cav_sweep, cav_sweep_noalloc and vcycle_apply then synchronise the stream and read the
+ * hierarchy's device status word: IB_ERR_TIMEOUT if a bounded wait of a kernel ran out (the
+ * word is cleared).  While the stream is being captured into a CUDA graph they skip that
+ * check (and the synchronisation); the next fgmres_solve or checked call reports it. */
 /* r = b - K_E^(l) w on level l (rediscretised Stokes part plus Galerkin E_E). */
 ib_status cav_residual(const cav_hierarchy* h, int32_t level, const double* b, const double* w,
                        double* r, cudaStream_t stream);
@@ -252,8 +265,8 @@ void cav_destroy(cav_hierarchy* h);
  * callers that cannot let a call allocate device memory: code that runs with all device
  * memory already handed to its own pool or budget, where a cudaMalloc would fail or
  * fragment it, and code that cannot afford the implicit device synchronisation that
- * cudaMalloc and cudaFree may cause.  The paper has no counterpart; it is an interface
- * variant of the sweep of Eq. additive_cav_saddle.
+ * cudaMalloc and cudaFree may cause.  The paper has no counterpart: it is an interface
+ * variant of cav_sweep, not a step of the method.
  *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   - Every GPU that loads the library holds the array until the process exits.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
@@ -301,7 +314,8 @@ typedef struct {
  * is reached above tolerance, and also when an iteration's preconditioned vector is not
  * finite (a diverging V-cycle): the solve then stops there, x holds the iterate of the
  * iterations before it and ib_last_error() says so (x and info valid in both cases).
- * Synchronises the stream. */
+ * Returns IB_ERR_TIMEOUT (info filled, x not valid) when a bounded device wait ran out in
+ * any V-cycle of the solve.  Synchronises the stream. */
 ib_status fgmres_solve(const ib_system* sys, const cav_hierarchy* h, const double* b, double* x,
                        const fgmres_desc* desc, fgmres_info* info, double* history,
                        cudaStream_t stream);
@@ -318,6 +332,14 @@ ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
                                const cav_hierarchy* const* hierarchies, const double* const* b,
                                double* const* x, const fgmres_desc* desc, fgmres_info* infos,
                                cudaStream_t stream);
+
+/* Test hook, not part of the method (ABI 4): while enable != 0 every bounded device-side
+ * wait for data in the patch-apply and class-step kernels (a TMA copy landing, a gathered
+ * vector) ignores its barrier and runs out after about 2^20 clock cycles, so that tests can
+ * check that IB_ERR_TIMEOUT comes back through the calls above without faulting or hanging
+ * the device.  Copies already in flight still land before a kernel's blocks exit.  Process
+ * wide; call with 0 to restore normal waits. */
+ib_status ib_test_wait_stall(int32_t enable);
 
 /* ------------------------------------------------------ learned initial guess (CNN)
  * Not from the paper: a small convolutional network that predicts each time step's initial

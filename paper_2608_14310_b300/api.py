@@ -34,9 +34,12 @@ class IBError(RuntimeError):
         self.status = status
 
 
+BC = {"periodic": 0, "channel": 1}
+
+
 class ib_grid_desc(C.Structure):
     _fields_ = [("N", C.c_int32), ("L", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
-                ("dt", C.c_double)]
+                ("dt", C.c_double), ("bc", C.c_int32)]
 
 
 class ib_structure_desc(C.Structure):
@@ -111,6 +114,7 @@ _sig = {
     "cav_coarse_solve": (C.c_int, [_vp, _vp, _vp, _vp]),
     "vcycle_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "cav_destroy": (None, [_vp]),
+    "ib_test_wait_stall": (C.c_int, [C.c_int32]),
     "ibnet_create": (C.c_int, [_P(ibnet_desc), _P(_vp)]),
     "ibnet_destroy": (None, [_vp]),
     "ibnet_num_params": (C.c_int64, [_vp]),
@@ -233,7 +237,8 @@ def ib_update_structure(sys: System, rec, stream=None):
 
 def ib_setup(rec, stream=None) -> System:
     """rec: an ib_workloads.System (or any object with the same fields)."""
-    g = ib_grid_desc(int(rec.N), float(rec.L), float(rec.rho), float(rec.mu), float(rec.dt))
+    g = ib_grid_desc(int(rec.N), float(rec.L), float(rec.rho), float(rec.mu), float(rec.dt),
+                     BC[getattr(rec, "bc", "periodic")])
     sd, _keep = _structure(rec)
     out = _vp()
     _check(_lib.ib_setup(C.byref(g), C.byref(sd), _stream(stream), C.byref(out)), "ib_setup")
@@ -362,6 +367,11 @@ def cav_coarse_solve(h: Hierarchy, r, z, stream=None):
 
 def vcycle_apply(h: Hierarchy, r, z, stream=None):
     _check(_lib.vcycle_apply(h.handle, _dev(r), _dev(z), _stream(stream)), "vcycle_apply")
+
+
+def ib_test_wait_stall(enable: bool):
+    """Test hook: make the kernels' bounded data waits run out (see include/ib_cav.h)."""
+    _check(_lib.ib_test_wait_stall(1 if enable else 0), "ib_test_wait_stall")
 
 
 def ib_launch_count() -> int:

@@ -42,7 +42,7 @@ using namespace cav;
 extern "C" {
 
 const char* ib_last_error(void) { return g_last_error.c_str(); }
-int ib_abi_version(void) { return 3; }
+int ib_abi_version(void) { return 4; }
 int64_t ib_launch_count(void) { return g_launches.load(); }
 
 ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaStream_t st, ib_system** out) {
@@ -54,6 +54,8 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   CAV_REQUIRE(grid->N >= 8 && grid->N <= 16384, "ib_setup: N must be in [8, 16384]");
   CAV_REQUIRE(grid->L > 0 && grid->rho > 0 && grid->mu >= 0 && grid->dt > 0,
               "ib_setup: L, rho, dt must be positive and mu non-negative");
+  CAV_REQUIRE(grid->bc == IB_BC_PERIODIC || grid->bc == IB_BC_CHANNEL, "ib_setup: unknown boundary condition");
+  CAV_REQUIRE(grid->bc == IB_BC_PERIODIC, "ib_setup: the channel boundary (IB_BC_CHANNEL) is not supported yet");
   CAV_REQUIRE(sd->M >= 0, "ib_setup: M must be non-negative");
   CAV_REQUIRE(sd->M == 0 || (sd->X && sd->omega), "ib_setup: X and omega are required when M > 0");
   CAV_REQUIRE(sd->law >= IB_FORCE_TARGET && sd->law <= IB_FORCE_FIBER, "ib_setup: unknown force law");
@@ -64,6 +66,7 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   s->rho = grid->rho;
   s->mu = grid->mu;
   s->dt = grid->dt;
+  s->bc = grid->bc;
   s->law = sd->law;
   s->closed = sd->closed ? 1 : 0;
   s->ds = sd->ds;
@@ -152,6 +155,7 @@ ib_status ib_update_structure(ib_system* s, const ib_structure_desc* sd, cudaStr
   g.rho = s->rho;
   g.mu = s->mu;
   g.dt = s->dt;
+  g.bc = s->bc;
   ib_system* fresh = nullptr;
   const ib_status r = ib_setup(&g, sd, st, &fresh);
   if (r != IB_OK) return r;  // the handle keeps its previous configuration
@@ -432,7 +436,7 @@ ib_status cav_sweep(const cav_hierarchy* h, int32_t level, const double* b, doub
   CAV_REQUIRE(!lv.coarsest, "cav_sweep: no smoother on the coarsest level");
   CAV_REQUIRE(b && w, "cav_sweep: NULL vector");
   level_sweep(h, level, b, w, false, st);
-  return IB_OK;
+  return take_status(h->status, st, "cav_sweep");
   CAV_API_END
 }
 
@@ -478,6 +482,14 @@ ib_status vcycle_apply(const cav_hierarchy* h, const double* r, double* z, cudaS
   CAV_REQUIRE(h && r && z, "vcycle_apply: NULL argument");
   CAV_REQUIRE(r != z, "vcycle_apply: r and z must not alias");
   vcycle(h, r, z, st);
+  return take_status(h->status, st, "vcycle_apply");
+  CAV_API_END
+}
+
+ib_status ib_test_wait_stall(int32_t enable) {
+  CAV_API_BEGIN
+  sweep_set_wait_stall(enable ? 1 : 0);
+  colour_set_wait_stall(enable ? 1 : 0);
   return IB_OK;
   CAV_API_END
 }
@@ -558,7 +570,7 @@ ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
     std::memset(&infos[i], 0, sizeof(fgmres_info));
   }
   ib_status r = fgmres_run_batched(count, systems, H.data(), b, x, d, infos, st);
-  if (r == IB_ERR_NOCONV) set_error("fgmres_solve_batched: some systems reached maxit above tolerance");
+  if (r == IB_ERR_NOCONV) set_error("fgmres_solve_batched: some systems stopped above tolerance");
   return r;
   CAV_API_END
 }

@@ -562,12 +562,14 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   for (int ps = 0; ps < CS_MAXPASS; ++ps)
 #pragma unroll
     for (int v = 0; v < V; ++v) accv[ps][v] = 0;
+  // A bounded wait that runs out records DEV_TIMEOUT; the CTA then stops staging (the host
+  // reports IB_ERR_TIMEOUT), after waiting for the copy in flight to land.
   bool alive = true;
   uint32_t phase = 0;
   for (int b0 = 0; b0 < m; b0 += pc) {
     const int nc = min(pc, m - b0);
-    if (alive && !mbar_wait(bar, phase, a.status)) alive = false;
-    if (alive) {
+    const bool got = mbar_wait(bar, phase, a.status);
+    if (got) {
 #pragma unroll
       for (int ps = 0; ps < CS_MAXPASS; ++ps) {
         const int r0 = (ps * RT + rt) * V;
@@ -583,8 +585,13 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
         }
       }
     }
-    __syncthreads();
-    if (tid == 0 && alive && b0 + pc < m) {
+    alive = __syncthreads_and(got ? 1 : 0) != 0;  // one decision for the whole CTA
+    if (!alive) {
+      if (tid == 0) mbar_drain(bar, phase, a.status);
+      __syncthreads();
+      break;
+    }
+    if (tid == 0 && b0 + pc < m) {
       const int nn = min(pc, m - b0 - pc);
       mbar_arrive_expect_tx(bar, (uint32_t)(nn * col_bytes));
       for (int cl = 0; cl < nn; ++cl)
@@ -618,6 +625,10 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     // restricted injection (box patches): only the unexpanded block's unknowns are written
     if (a.inject == nullptr || a.inject[d0 + rank + C * s]) w[sk[s]] = sold[s] + ssc[s] * (double)sum;
   }
+}
+
+void colour_set_wait_stall(int enable) {
+  CAV_CHECK_CUDA(cudaMemcpyToSymbol(g_wait_stall, &enable, sizeof(int)));
 }
 
 // Sums of the pressure block over tiles of 256 cells (fixed order), for the mean removal.

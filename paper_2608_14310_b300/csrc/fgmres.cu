@@ -473,6 +473,9 @@ static void fg_finish(FgState& s) {
   CAV_CHECK_CUDA(cudaMemcpyAsync(H->host_b + 6, misc + 6, sizeof(double), cudaMemcpyDeviceToHost, s.st));
   if (s.d->host_io)
     CAV_CHECK_CUDA(cudaMemcpyAsync(s.x_user, s.x, sizeof(double) * s.n, cudaMemcpyDeviceToHost, s.st));
+  // the hierarchy's device status word (a bounded wait that ran out in any V-cycle)
+  CAV_CHECK_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(H->host_b + 15), H->status, sizeof(int),
+                                 cudaMemcpyDeviceToHost, s.st));
 }
 
 // after the stream has been synchronised
@@ -486,6 +489,13 @@ static ib_status fg_result(FgState& s) {
               "rounded FP32 inverses of very ill-conditioned patches make the undamped sweep "
               "diverge: use FP64 inverses); x holds the iterate before it");
   s.info->relres_true = (s.ref > 0) ? std::sqrt(s.H->host_b[6]) / s.ref : 0.0;
+  const int code = *reinterpret_cast<const int*>(s.H->host_b + 15);
+  if (code != DEV_OK) {
+    CAV_CHECK_CUDA(cudaMemsetAsync(s.H->status, 0, sizeof(int), s.st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(s.st));
+    set_error("fgmres_solve: " + status_message(code));
+    return status_of(code);
+  }
   return s.converged ? IB_OK : IB_ERR_NOCONV;
 }
 
@@ -545,11 +555,15 @@ ib_status fgmres_run_batched(int count, const ib_system* const* sys, cav_hierarc
   for (int i = 0; i < count; ++i) fg_drain(S[i]);
   for (int i = 0; i < count; ++i) fg_finish(S[i]);
   bool all = true;
+  ib_status failure = IB_OK;
   for (int i = 0; i < count; ++i) {
     CAV_CHECK_CUDA(cudaStreamSynchronize(S[i].st));
-    all = (fg_result(S[i]) == IB_OK) && all;
+    const ib_status r = fg_result(S[i]);
+    if (r != IB_OK && r != IB_ERR_NOCONV && failure == IB_OK) failure = r;
+    all = (r == IB_OK) && all;
   }
   cudaEventDestroy(start_ev);
+  if (failure != IB_OK) return failure;
   return all ? IB_OK : IB_ERR_NOCONV;
 }
 

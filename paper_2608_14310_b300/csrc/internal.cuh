@@ -151,6 +151,7 @@ struct Level {
 
 struct ib_system {
   int N = 0;
+  int bc = IB_BC_PERIODIC;       // ib_bc
   double L = 1, h = 0, rho = 0, mu = 0, dt = 0;
   int M = 0, law = 0, closed = 0, bw = 0;
   double ds = 0, k_target = 0, k_stretch = 0, k_bend = 0;
@@ -280,5 +281,16 @@ void launch_dot_partials(const double* a, const double* b, int64_t n, double* pa
 void exclusive_scan(const int* counts, int64_t* out, int64_t n, cudaStream_t st, Arena* scratch);
 
 int read_status(int* d_status, cudaStream_t st);
+// The message and the ABI status for a device status code.
+std::string status_message(int code);
+ib_status status_of(int code);
+// After the work queued on `st`: reads the device status word, clears it and turns a
+// recorded failure into a status with a message (IB_ERR_TIMEOUT for a bounded wait that ran
+// out).  Synchronises `st`; while `st` is being captured into a graph it reads nothing and
+// returns IB_OK.
+ib_status take_status(int* d_status, cudaStream_t st, const char* who);
+// Test hook: make every stallable bounded wait run out (each translation unit with waits).
+void sweep_set_wait_stall(int enable);
+void colour_set_wait_stall(int enable);
 
 }  // namespace cav

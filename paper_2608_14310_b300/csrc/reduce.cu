@@ -1,4 +1,6 @@
 // Deterministic reductions and scans used by set-up and by the Krylov solver.
+#include <string>
+
 #include "internal.cuh"
 #include "device_util.cuh"
 
@@ -104,6 +106,37 @@ int read_status(int* d_status, cudaStream_t st) {
   CAV_CHECK_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   return h;
+}
+
+std::string status_message(int code) {
+  switch (code) {
+    case DEV_TIMEOUT:
+      return "a bounded device-side wait ran out (a TMA copy or a pipeline stage did not arrive in time); "
+             "the call's output is not valid";
+    case DEV_WINDOW: return "a stencil window overflowed";
+    case DEV_SINGULAR: return "zero pivot in a local patch matrix";
+    case DEV_CAPACITY: return "a device-side capacity was exceeded";
+    default: return "device status code " + std::to_string(code);
+  }
+}
+
+ib_status status_of(int code) {
+  if (code == DEV_OK) return IB_OK;
+  if (code == DEV_TIMEOUT) return IB_ERR_TIMEOUT;
+  if (code == DEV_SINGULAR) return IB_ERR_SINGULAR;
+  return IB_ERR_INTERNAL;
+}
+
+ib_status take_status(int* d_status, cudaStream_t st, const char* who) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CAV_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return IB_OK;
+  const int code = read_status(d_status, st);
+  if (code == DEV_OK) return IB_OK;
+  CAV_CHECK_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  set_error(std::string(who) + ": " + status_message(code));
+  return status_of(code);
 }
 
 }  // namespace cav

@@ -614,13 +614,9 @@ static size_t factor_smem(int m) { return (size_t)(2 * m) * sizeof(double) + (si
 
 static void check_status(cav_hierarchy* H, cudaStream_t st, const char* where) {
   const int s = read_status(H->status, st);
-  if (s == DEV_SINGULAR) {
-    set_error(std::string(where) + ": zero pivot in a local patch matrix");
-    throw Fail{IB_ERR_SINGULAR};
-  }
   if (s != DEV_OK) {
-    set_error(std::string(where) + ": device consistency check failed (code " + std::to_string(s) + ")");
-    throw Fail{IB_ERR_INTERNAL};
+    set_error(std::string(where) + ": " + status_message(s));
+    throw Fail{status_of(s)};
   }
 }
 

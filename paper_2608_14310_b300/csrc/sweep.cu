@@ -11,7 +11,9 @@
 //      slots of the enlarged patches holding it (fixed order, no atomics)
 //   4. remove the mean pressure (Sec. 3.3).
 #include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 
 #include "internal.cuh"
 #include "device_util.cuh"
@@ -92,8 +94,11 @@ __device__ inline int zigzag(int q, int G, int n) {
 //    dependent index -> residual loads of patch t+1 overlap the streaming of patch t;
 //  * warps 2..5 (consumers): acc[rows] += X[rows, b] y[b] stage by stage, each thread
 //    owning V consecutive rows (up to TMA_MAXPASS row blocks), then delta = s_c * acc.
-// Every wait is bounded; a timed-out wait records DEV_TIMEOUT and that warp stops waiting
-// and computing but still walks the patch sequence.
+// Every wait is bounded.  A wait that runs out records DEV_TIMEOUT and raises the CTA's abort
+// flag; every role then stops (no further copies, arrivals or writes; the delta of the
+// remaining patches is left unwritten and the host reports IB_ERR_TIMEOUT), and the producer
+// waits for the copies it has in flight to land before the CTA exits.  A warp's give-up
+// decision is taken by all its lanes together.
 template <typename T, int TMA_STAGES, int TMA_CHUNK>
 __global__ void __launch_bounds__(TMA_THREADS)
 k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __restrict__ off,
@@ -104,6 +109,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   typedef typename VL::acc_t acc_t;
   constexpr int V = VL::V;
   constexpr int CT = 32 * TMA_CONSUMER_WARPS;
+  static_assert(TMA_STAGES <= 32, "stage bit masks");
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stage_buf = smem;
   const size_t ybytes = ((size_t)max_n * sizeof(acc_t) + 127) & ~(size_t)127;
@@ -112,8 +118,11 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   uint64_t* empty = full + TMA_STAGES;
   uint64_t* yfull = empty + TMA_STAGES;
   uint64_t* yempty = yfull + Y_SLOTS;
+  int* abort_flag = reinterpret_cast<int*>(yempty + Y_SLOTS);
+  volatile int* ab = abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
+    *abort_flag = 0;
     for (int s = 0; s < TMA_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], TMA_CONSUMER_WARPS);
@@ -130,7 +139,9 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
+      uint32_t used = 0, last_par = 0;  // per stage: a copy was issued; parity of its last phase
+      bool ok = true;
+      for (int q = blockIdx.x; ok && q < n_big; q += gridDim.x) {
         const int p = order[zigzag(q, gridDim.x, n_big)];
         const int n = (int)(off[p + 1] - off[p]);
         const uint32_t col_bytes = (uint32_t)(((n + 7) & ~7) * sizeof(T));
@@ -138,33 +149,40 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
         const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + inv_off[p]);
         for (int b0 = 0; b0 < n; b0 += cpc) {
           const int nc = min(cpc, n - b0);
-          if (!mbar_wait(&empty[stage], phase ^ 1u, status)) return;
+          if (!mbar_wait(&empty[stage], phase ^ 1u, status, ab, false)) {
+            ok = false;
+            break;
+          }
           const uint32_t bytes = (uint32_t)nc * col_bytes;
           mbar_arrive_expect_tx(&full[stage], bytes);
           bulk_copy_g2s(stage_buf + (size_t)stage * TMA_CHUNK, src + (size_t)b0 * col_bytes, bytes, &full[stage]);
+          used |= 1u << stage;
+          last_par = phase ? (last_par | (1u << stage)) : (last_par & ~(1u << stage));
           if (++stage == TMA_STAGES) {
             stage = 0;
             phase ^= 1u;
           }
         }
       }
+      // every issued copy lands before the CTA exits (immediate when the consumers saw them all)
+      for (int s = 0; s < TMA_STAGES; ++s)
+        if ((used >> s) & 1u) mbar_drain(&full[s], (last_par >> s) & 1u, status);
     }
     return;
   }
 
   if (warp == 1) {
-    bool alive = true;
     int t = 0;
     for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
       const int slot = t & 1;
       const uint32_t par = (uint32_t)((t >> 1) & 1);
-      if (alive && !mbar_wait(&yempty[slot], par ^ 1u, status)) alive = false;
+      const bool got = mbar_wait(&yempty[slot], par ^ 1u, status, ab, false);
+      if (!__all_sync(0xffffffffu, got)) break;
       const int p = order[zigzag(q, gridDim.x, n_big)];
       const int64_t d0 = off[p];
       const int n = (int)(off[p + 1] - d0);
       acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
-      if (alive)
-        for (int b = lane; b < n; b += 32) y[b] = (acc_t)(s_r[d0 + b] * r[dofs[d0 + b]]);
+      for (int b = lane; b < n; b += 32) y[b] = (acc_t)(s_r[d0 + b] * r[dofs[d0 + b]]);
       mbar_arrive(&yfull[slot]);
     }
     return;
@@ -173,7 +191,6 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   const int ct = threadIdx.x - 64;
   int stage = 0;
   uint32_t phase = 0;
-  bool alive = true;
   int t = 0;
   for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
     const int p = order[zigzag(q, gridDim.x, n_big)];
@@ -182,21 +199,25 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     const int ld = (n + 7) & ~7;
     const int cpc = TMA_CHUNK / (int)(ld * sizeof(T));
     const int slot = t & 1;
-    if (alive && !mbar_wait(&yfull[slot], (uint32_t)((t >> 1) & 1), status)) alive = false;
+    if (!__all_sync(0xffffffffu, mbar_wait(&yfull[slot], (uint32_t)((t >> 1) & 1), status, ab))) break;
     const acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
     acc_t acc[TMA_MAXPASS][V];
 #pragma unroll
     for (int ps = 0; ps < TMA_MAXPASS; ++ps)
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[ps][v] = 0;
+    bool dead = false;
     for (int b0 = 0; b0 < n; b0 += cpc) {
       const int nc = min(cpc, n - b0);
-      if (alive && !mbar_wait(&full[stage], phase, status)) alive = false;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, status, ab))) {
+        dead = true;
+        break;
+      }
       const T* X = reinterpret_cast<const T*>(stage_buf + (size_t)stage * TMA_CHUNK);
 #pragma unroll
       for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
         const int a0 = (ps * CT + ct) * V;
-        if (alive && a0 < n) {
+        if (a0 < n) {
 #pragma unroll 4
           for (int c = 0; c < nc; ++c) {
             acc_t x0[V];
@@ -214,6 +235,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
         phase ^= 1u;
       }
     }
+    if (dead) break;
     __syncwarp();
     if (lane == 0) mbar_arrive(&yempty[slot]);
 #pragma unroll
@@ -221,7 +243,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
       const int a0 = (ps * CT + ct) * V;
 #pragma unroll
       for (int v = 0; v < V; ++v)
-        if (alive && a0 + v < n) delta[d0 + a0 + v] = s_c[d0 + a0 + v] * (double)acc[ps][v];
+        if (a0 + v < n) delta[d0 + a0 + v] = s_c[d0 + a0 + v] * (double)acc[ps][v];
     }
   }
 }
@@ -410,14 +432,29 @@ void prof_collect(cav_hierarchy* H, long long upto) {
   if (H->prof_pending.empty()) H->prof_used = 0;
 }
 
+// Multiprocessor count of the current device (cached per device).
 static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    CAV_CHECK_CUDA(cudaGetDevice(&dev));
-    CAV_CHECK_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-  }
-  return n;
+  static std::mutex m;
+  static int count[64] = {};
+  int dev = 0;
+  CAV_CHECK_CUDA(cudaGetDevice(&dev));
+  CAV_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(m);
+  if (count[dev] == 0) CAV_CHECK_CUDA(cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev));
+  return count[dev];
+}
+
+// Raise a kernel's dynamic shared memory limit on the current device, once per (kernel,
+// device): the attribute is per device, so a process using several GPUs sets it on each.
+static void allow_dynamic_smem(const void* kernel, int bytes) {
+  static std::mutex m;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  CAV_CHECK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(m);
+  if (done.count({kernel, dev})) return;
+  CAV_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({kernel, dev});
 }
 
 // Patch-apply variants the autotuner chooses among (per level, timed at set-up):
@@ -437,12 +474,9 @@ static void launch_tma(const cav_hierarchy* H, const Level& lv, const T* inv, co
                        int ctas_per_sm, cudaStream_t st) {
   typedef typename VecLoad<T>::acc_t acc_t;
   const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
-  const size_t smem = (size_t)STAGES * CHUNK + Y_SLOTS * ybytes + (2 * STAGES + 2 * Y_SLOTS) * sizeof(uint64_t);
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(k_patch_apply_tma<T, STAGES, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-  });
+  const size_t smem = (size_t)STAGES * CHUNK + Y_SLOTS * ybytes + (2 * STAGES + 2 * Y_SLOTS) * sizeof(uint64_t) +
+                      16;  // the CTA's abort flag
+  allow_dynamic_smem(reinterpret_cast<const void*>(k_patch_apply_tma<T, STAGES, CHUNK>), 200 * 1024);
   const int grid = std::min(lv.n_big, ctas_per_sm * sm_count());
   k_patch_apply_tma<T, STAGES, CHUNK><<<grid, TMA_THREADS, smem, st>>>(
       lv.n_big, lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
@@ -538,6 +572,10 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
     k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, partial_buf, w + 2 * lv.N * lv.N);
     CAV_CHECK_LAUNCH();
   }
+}
+
+void sweep_set_wait_stall(int enable) {
+  CAV_CHECK_CUDA(cudaMemcpyToSymbol(g_wait_stall, &enable, sizeof(int)));
 }
 
 void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, cudaStream_t st) {
@@ -709,6 +747,15 @@ static double* noalloc_scratch(int device) {
 
 static inline size_t round_up32(size_t n) { return (n + 31) & ~(size_t)31; }
 
+// Rejects a level whose scratch would not fit in the fixed array, naming both sizes.
+static void noalloc_require(int level, size_t need, const char* what) {
+  if (need <= (size_t)CAV_NOALLOC_SCRATCH_DOUBLES) return;
+  set_error("cav_sweep_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
+            " doubles of scratch (" + what + "); the static array holds " +
+            std::to_string((size_t)CAV_NOALLOC_SCRATCH_DOUBLES));
+  throw Fail{IB_ERR_INVALID};
+}
+
 }  // namespace cav
 
 extern "C" ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, const double* b, double* w,
@@ -725,26 +772,22 @@ extern "C" ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, co
     if (lv.coloured) {
       // the class-by-class sweep needs scratch only for the pressure mean's partial sums
       const size_t n_pc = round_up32((size_t)div_up((int64_t)lv.N * lv.N, 256));
-      CAV_REQUIRE(n_pc <= (size_t)CAV_NOALLOC_SCRATCH_DOUBLES, "cav_sweep_noalloc: level too large");
+      noalloc_require(level, n_pc, "partial sums of the pressure mean, rounded to 32");
       coloured_sweep(h, level, b, w, false, noalloc_scratch(device), true, false, st);
-      return IB_OK;
+      return take_status(h->status, st, "cav_sweep_noalloc");
     }
     const size_t n_r = round_up32((size_t)3 * lv.N * lv.N);
     const size_t n_d = round_up32((size_t)lv.big_sum_n);
     const size_t n_p = round_up32((size_t)lv.n_partial);
-    const size_t need = n_r + n_d + n_p;
-    if (need > (size_t)CAV_NOALLOC_SCRATCH_DOUBLES) {
-      set_error("cav_sweep_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
-                " doubles of scratch (3 N^2 + enlarged-patch unknowns + partial sums, each rounded to 32); "
-                "the static array holds " + std::to_string((size_t)CAV_NOALLOC_SCRATCH_DOUBLES));
-      return IB_ERR_INVALID;
-    }
+    noalloc_require(level, n_r + n_d + n_p,
+                    "3 N^2 + enlarged-patch unknowns + partial sums, each rounded to 32");
     double* base = noalloc_scratch(device);
     double* r = base;               // written in full by the residual kernel before any read
     double* delta = base + n_r;     // written in full by the patch-apply kernel before any read
+                                    // (not read at all on a level without enlarged patches)
     double* partial = delta + n_d;  // written in full by the update kernels before any read
     sweep_impl(h, level, b, w, false, r, delta, partial, false, st);
-    return IB_OK;
+    return take_status(h->status, st, "cav_sweep_noalloc");
   } catch (const Fail& f) {
     return f.st;
   } catch (...) {

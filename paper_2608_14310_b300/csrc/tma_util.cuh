@@ -40,17 +40,47 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase with the given parity to complete; gives up after ~2^31 clock cycles
-// (about a second), records DEV_TIMEOUT and returns false.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+// Bounded waits.  A wait gives up after WAIT_LIMIT clock cycles (about a second), records
+// DEV_TIMEOUT in the status word and returns false; the host reads the word after the call
+// and reports IB_ERR_TIMEOUT.  g_wait_stall is a test hook (set from the host through
+// ib_test_wait_stall): while it is non-zero every stallable wait (a wait for data: a copy
+// landing, a gathered vector) ignores its barrier and runs out after WAIT_LIMIT_STALL cycles,
+// so tests can drive the timeout path without a fault; waits for free buffer space are not
+// stallable, so copies are in flight when the data waits give up.
+// Each translation unit that includes this header holds its own copy of the flag.
+constexpr long long WAIT_LIMIT = 1LL << 31;
+constexpr long long WAIT_LIMIT_STALL = 1LL << 20;
+static __device__ int g_wait_stall = 0;
+
+// Wait for the phase with the given parity to complete.  `abort` (shared memory, nullable)
+// is a CTA-wide flag: a wait also gives up (without recording a status) once another thread
+// of the CTA has set it, and a wait that runs out sets it, so the other roles of the CTA stop
+// waiting on work that will not come.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort = nullptr,
+                                 bool stallable = true) {
+  const bool stall = stallable && *(volatile int*)&g_wait_stall != 0;
+  const long long limit = stall ? WAIT_LIMIT_STALL : WAIT_LIMIT;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) {
+  while (stall || !mbar_try_wait(bar, parity)) {
+    if (abort && *abort) return false;
+    if (clock64() - t0 > limit) {
       atomicExch(status, DEV_TIMEOUT);
+      if (abort) *abort = 1;
       return false;
     }
   }
   return true;
+}
+// Wait for a bulk copy this CTA issued to land before the CTA exits (shared memory must not
+// be released with a copy in flight).  Not subject to the stall hook; bounded all the same.
+__device__ inline void mbar_drain(uint64_t* bar, uint32_t parity, int* status) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_LIMIT) {
+      atomicExch(status, DEV_TIMEOUT);
+      return;
+    }
+  }
 }
 // 1-D bulk copy global -> this CTA's shared memory, completing `bytes` on the mbarrier.
 __device__ inline void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

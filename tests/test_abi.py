@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(api):
 
 
 def test_abi_version(api):
-    assert api._lib.ib_abi_version() == 3
+    assert api._lib.ib_abi_version() == 4
 
 
 def test_null_arguments_are_rejected_without_a_device(api):
@@ -51,10 +51,23 @@ def test_null_arguments_are_rejected_without_a_device(api):
     sd = api.ib_structure_desc(10, 1, 1, None, None, 0.1, 0.0, 1.0, 0.0)   # markers missing
     st = api._lib.ib_setup(C.byref(g), C.byref(sd), None, C.byref(out))
     assert st == api.IB_ERR_INVALID
+    # boundary conditions: an unknown value is rejected before any device work
+    g = api.ib_grid_desc(16, 1.0, 1.0, 0.01, 0.1, 7)
+    sd = api.ib_structure_desc(0, 1, 0, None, None, 0.0, 0.0, 0.0, 0.0)
+    st = api._lib.ib_setup(C.byref(g), C.byref(sd), None, C.byref(out))
+    assert st == api.IB_ERR_INVALID and "boundary" in api._lib.ib_last_error().decode()
     info = api.fgmres_info()
     d = api.fgmres_desc(1e-10, 10, 0, 0)
     st = api._lib.fgmres_solve(None, None, None, None, C.byref(d), C.byref(info), None, None)
     assert st == api.IB_ERR_INVALID
+
+
+def test_grid_descriptor_layout(api):
+    # the binding's struct matches the header: bc follows dt
+    g = api.ib_grid_desc
+    assert [f for f, _ in g._fields_] == ["N", "L", "rho", "mu", "dt", "bc"]
+    assert g.bc.offset == g.dt.offset + 8
+    assert api.BC == {"periodic": 0, "channel": 1}
 
 
 def test_product_path_has_no_fallback():

@@ -63,6 +63,8 @@ def test_full_patterns_and_patch_sets(full):
 
 def test_full_sweep_sampled(full):
     from paper_2608_14310_b300 import api
+    if full.name == "membrane256":
+        pytest.skip("compared as whole vectors on every level in test_gpu_fullsize_sweep.py")
     lev = full.levels[0]
     N = lev.N
     NN = N * N

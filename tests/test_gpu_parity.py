@@ -3,9 +3,8 @@ inputs, element by element.  Integer work (E_E patterns, patch sets) must be bit
 floating point within the stated tolerances:
 
   * E_E values, K_E products, transfers: |gpu - oracle| <= 1e-13 * max|.| (summation order)
-  * one sweep, per level: ||w_gpu - w_oracle|| / ||w_oracle|| <= SWEEP_TOL[case]; 1e-12 for
-    the plain FP64 target-point case, looser where the local matrices' condition number
-    (measured by the oracle) times eps says the inverses themselves differ by more
+  * one sweep, per level: ||w_gpu - w_oracle|| / ||w_oracle|| <= 1e-12, the per-sweep bound the
+    plain FP64 path is held to (measured: at most 1.3e-13 over these cases)
   * FGMRES: iteration counts within one, both converged, solutions agree to 1e-8
 """
 import numpy as np
@@ -20,9 +19,9 @@ pytestmark = pytest.mark.gpu
 ALPHA = 0.85
 CASES = {
     "target32": (lambda: W.config1(), 2, 1e-12),
-    "membrane32": (lambda: W.membrane_ellipse(32, 1e4), 1, 1e-11),
-    "beam32": (lambda: W.beam_curve(32, 128, k_bend=1e-1, k_stretch=1e1), 1, 1e-11),
-    "rows32": (lambda: W.paper_target_rows(32), 1, 1e-11),
+    "membrane32": (lambda: W.membrane_ellipse(32, 1e4), 1, 1e-12),
+    "beam32": (lambda: W.beam_curve(32, 128, k_bend=1e-1, k_stretch=1e1), 1, 1e-12),
+    "rows32": (lambda: W.paper_target_rows(32), 1, 1e-12),
     "nomarkers16": (lambda: W.System(name="empty", N=16, L=1.0, rho=1.0, mu=0.01, dt=0.01, law=0,
                                      closed=True, X=np.zeros((0, 2)), ds=0.1, omega=np.zeros(0)), 1, 1e-12),
 }

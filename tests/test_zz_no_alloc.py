@@ -53,7 +53,37 @@ def test_noalloc_sweep_matches_cav_sweep(precision, smoother):
             w_start = ref
 
 
+def test_noalloc_sweep_on_levels_without_enlarged_patches():
+    # no structure: every patch is a standard Vanka patch, so no packed correction is written
+    # or read; the result must still equal cav_sweep's on every level, call after call
+    from paper_2608_14310_b300 import api
+    rec = W.System(name="empty32", N=32, L=1.0, rho=1.0, mu=0.01, dt=0.01, law=0, closed=True,
+                   X=np.zeros((0, 2)), ds=0.1, omega=np.zeros(0))
+    sysm = api.ib_setup(rec)
+    h = api.cav_setup(sysm, nu_pre=1, nu_post=1, alpha=0.85, precision="fp64")
+    rng = np.random.default_rng(4)
+    for level in range(api.cav_num_levels(h) - 1):
+        info = api.cav_get_level_info(h, level)
+        assert info["n_enlarged"] == 0
+        n = 3 * info["N"] ** 2
+        b = rng.uniform(-1, 1, n)
+        w_start = rng.uniform(-1, 1, n) * 1e-2
+        for call in range(2):
+            w_ref = _dev(w_start)
+            api.cav_sweep(h, level, _dev(b), w_ref)
+            w_new = _dev(w_start)
+            api.cav_sweep_noalloc(h, level, _dev(b), w_new)
+            ref, new = _host(w_ref), _host(w_new)
+            err = np.linalg.norm(new - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (level, call, err)
+            w_start = ref
+
+
 def test_noalloc_sweep_rejects_levels_beyond_its_scratch():
+    """The additive branch needs 3 N^2 + enlarged unknowns + partial sums and is rejected at
+    N = 1024.  The coloured branch needs only ceil(N^2 / 256) partial sums, which reaches the
+    limit (1,048,576) only at N = 16384, the largest grid ib_setup accepts, so no grid the
+    library takes can exceed it; both branches share the same size check and message."""
     from paper_2608_14310_b300 import api
     # no structure, N = 1024: the finest level alone needs 3 N^2 = 3,145,728 doubles
     rec = W.System(name="empty1024", N=1024, L=1.0, rho=1.0, mu=0.01, dt=0.01, law=0, closed=True,

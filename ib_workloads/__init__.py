@@ -104,6 +104,7 @@ class System:
     seed: int = BASE_SEED
     X_target: np.ndarray | None = None  # (M, 2) target positions at step n+1 (target law)
     meta: dict = field(default_factory=dict)
+    bc: str = "periodic"     # "periodic", or "channel" (Sec. 5.3: inflow on top, traction outflow below)
 
     @property
     def M(self) -> int:
@@ -259,6 +260,14 @@ def shear_forcing(N: int, t: float, amplitude: float = 1.0, period: float = 0.5)
 
 
 # --------------------------------------------------------------------------- fiber (Sec. 5.3)
+
+
+def fiber_channel(N: int = 16, bend: float = 1.5, jitter: float = 0.05) -> System:
+    """The same fiber and parameters in the benchmark's channel (bc = "channel"): periodic in x,
+    inflow on the top wall y = 2, traction outflow on y = 0 (Sec. 5.3)."""
+    from dataclasses import replace
+    rec = fiber_periodic(N, bend, jitter)
+    return replace(rec, name=f"fiber-channel-N{N}", bc="channel")
 
 
 def fiber_periodic(N: int = 16, bend: float = 1.5, jitter: float = 0.05) -> System:

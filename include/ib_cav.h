@@ -57,10 +57,22 @@ int64_t ib_launch_count(void);
 typedef enum { IB_FORCE_TARGET = 0, IB_FORCE_MEMBRANE = 1, IB_FORCE_BEAM = 2, IB_FORCE_FIBER = 3 } ib_force_law;
 
 /* Boundary conditions of the Eulerian grid (ABI 4):
- *   periodic  the periodic unit cell of Sec. 2 (every experiment of Sec. 5.1 and 5.2);
+ *   periodic  the periodic square of Sec. 2 (every experiment of Sec. 5.1 and 5.2);
  *   channel   the flow-past-a-fiber channel of Sec. 5.3: periodic in x, a prescribed inflow
- *             on the top wall y = L and a traction outflow on y = 0 (not yet accepted:
- *             ib_setup returns IB_ERR_INVALID for it).                                   */
+ *             (u, v) = (0, -U(t)) on the top wall y = L, a traction outflow on y = 0 whose
+ *             traction carries the backflow term (rho/2) min(u.n, 0) u.  The unknowns are the
+ *             periodic grid's (3 N^2: the outflow row's v faces are unknowns, the top wall's
+ *             are prescribed).  K_E holds the rows with homogeneous boundary data, closed by
+ *             ghost values:  u_{i,N} = -u_{i,N-1},  v_{i,N} = 0,
+ *                            u_{i,-1} = u_{i,0} + v_{i,0} - v_{i-1,0},
+ *                            v_{i,-1} = v_{i,0} + u_{i+1,-1} - u_{i,-1},
+ *                            p_{i,-1} = (2 mu / h)(v_{i,1} - v_{i,-1}) - p_{i,0};
+ *             the boundary data enter the right-hand side (ib_channel_rhs).  The pressure is
+ *             determined: no mean is removed and the coarsest solve has no border.  On the
+ *             coarse levels a v face next to the top wall takes half the coarse face below it
+ *             and the pressure prolongation is clamped in y; the inflow row's Vanka patches
+ *             have four unknowns and an outflow-row v face has one incident cell.  Markers
+ *             must stay at least 2.5 h from both walls (their supports do not wrap).        */
 typedef enum { IB_BC_PERIODIC = 0, IB_BC_CHANNEL = 1 } ib_bc;
 
 typedef struct {
@@ -134,6 +146,25 @@ ib_status ib_step_rhs(const ib_system* sys, const double* u_prev, const double* 
                       cudaStream_t stream);
 /* X^{n+1} = X^n + dt J u (Eq. im_disc_advec) into X_next (host, 2M interleaved); syncs. */
 ib_status ib_advect(const ib_system* sys, const double* u, double* X_next, cudaStream_t stream);
+
+/* Channel time step of Sec. 5.3 (ABI 4; IB_BC_CHANNEL systems only).  The base right-hand
+ * side of the step t^n -> t^{n+1}:  b = [(rho/dt) u^n - rho N[u^n] ; 0] + g, N[u] = (u.grad)u
+ * (explicit, centred, each component averaged from its four neighbours onto the other's
+ * faces, with the previous inflow -U_prev on the top wall), g the boundary vector of the
+ * inflow v = -U_next on the top wall and of the outflow traction (rho/2) min(u^n.n, 0) u^n
+ * (u^n extrapolated to the wall as (3 u_0 - u_1)/2).  w_n (3 N^2) and b are device buffers. */
+ib_status ib_channel_rhs(const ib_system* sys, const double* w_n, double U_next, double U_prev, double* b,
+                         cudaStream_t stream);
+/* Right-hand side of one Newton system of the step (Eqs. im_disc_mom, im_disc_advec, Sec.
+ * 5.3) at the iterate w (device, 3 N^2) whose configuration X_k = X^n + dt J^n u_k was given
+ * to the system as X_lin:  rhs = b_base + [S^n F(X_k) - dt E_E(X_k) u_k ; 0].  The linear
+ * system is K_E(X_k) w' = rhs, and K_E(X_k) w - rhs is the Newton residual at w itself.  Any
+ * force law (the fiber law's F and tangent are those of X_lin).  rhs must not alias. */
+ib_status ib_newton_rhs(const ib_system* sys, const double* b_base, const double* w, double* rhs,
+                        cudaStream_t stream);
+/* r = b - K_E x and *norm = ||r||_2 (host; reduced on the device in a fixed order; syncs). */
+ib_status ib_residual_norm(const ib_system* sys, const double* b, const double* x, double* r, double* norm,
+                           cudaStream_t stream);
 
 /* -------------------------------------------------------- hierarchy (Sec. 3, Sec. 4) */
 

@@ -93,12 +93,14 @@ class _Lin:
         return _Lin(const=float(a)) - self
 
 
-def operator(ch: Channel, u_top=0.0, v_top=None, t_x=None, t_y=None):
+def operator(ch: Channel, u_top=0.0, v_top=None, t_x=None, t_y=None, structural=False):
     """K0 (3 Nx Ny square, the Stokes part of K_E on the channel) and the boundary vector g,
     such that the discrete equations read  K0 w = b + g  for a right-hand side b (body force
     and rho/dt u^n on the velocity rows, 0 on the cells).  v_top: (Nx,) inflow at the top
     faces; t_x: (Nx,) tangential traction at the points (i h, 0); t_y: (Nx,) normal traction
-    at ((i + 1/2) h, 0)."""
+    at ((i + 1/2) h, 0).  structural=True: K0 holds a 1 at every unknown a row's stencil
+    reaches through the ghost rules, including those whose weights cancel (the outflow v
+    row's v_{i+-1,0})."""
     Nx, Ny, h, mu = ch.Nx, ch.Ny, ch.h, ch.mu
     v_top = np.zeros(Nx) if v_top is None else np.asarray(v_top, dtype=np.float64)
     t_x = np.zeros(Nx) if t_x is None else np.asarray(t_x, dtype=np.float64)
@@ -131,10 +133,10 @@ def operator(ch: Channel, u_top=0.0, v_top=None, t_x=None, t_y=None):
 
     def emit(r, expr):
         for c, a in expr.t.items():
-            if a != 0.0:
+            if a != 0.0 or structural:
                 rows.append(r)
                 cols.append(c)
-                vals.append(a)
+                vals.append(1.0 if structural else a)
         g[r] -= expr.c  # constants move to the right-hand side
 
     a0, ih2, ih = ch.rho / ch.dt, 1.0 / (h * h), 1.0 / h
@@ -148,6 +150,8 @@ def operator(ch: Channel, u_top=0.0, v_top=None, t_x=None, t_y=None):
             emit(ch.ip(i, j), (-ih) * div)
     K = sp.csr_matrix((vals, (rows, cols)), shape=(ch.n, ch.n))
     K.sum_duplicates()
+    if structural:
+        K.data[:] = 1.0
     return K, g
 
 
@@ -231,11 +235,13 @@ def vanka_patches(ch: Channel) -> list:
 
 
 class ChannelLevel:
-    def __init__(self, ch: Channel, K: sp.csr_matrix, patches=None, coarsest=False):
+    def __init__(self, ch: Channel, K: sp.csr_matrix, patches=None, coarsest=False, ee_pattern=None):
         from . import smoother
         self.ch, self.K = ch, K.tocsr()
         self.Kc = self.K.tocsc()
         self.coarsest = coarsest
+        self.ee_pattern = ee_pattern  # structural pattern of E_E on this level (velocity block)
+        self._colours = None
         if coarsest:
             self.Kinv = np.linalg.inv(self.K.toarray())
         else:
@@ -272,19 +278,81 @@ def sweep(lev: ChannelLevel, w, b):
     return w
 
 
-def vcycle(levels, b, nu_pre=1, nu_post=1, li=0):
-    """z = B b: one V-cycle with zero initial guess on the channel hierarchy (Sec. 4)."""
+def coupling(lev: ChannelLevel) -> sp.csr_matrix:
+    """Structural coupling of the level's K_E: the channel stencil's reach (structure()),
+    E_E's pattern in the velocity block, and the diagonal."""
+    ch = lev.ch
+    pat = sp.csr_matrix(operator(ch, structural=True)[0] != 0, dtype=bool)
+    pat = pat + sp.identity(ch.n, dtype=bool, format="csr")
+    if lev.ee_pattern is not None:
+        nv = 2 * ch.Nx * ch.Ny
+        E = sp.csr_matrix(lev.ee_pattern, dtype=bool)
+        pat = pat + sp.bmat([[E, None], [None, sp.csr_matrix((ch.n - nv, ch.n - nv), dtype=bool)]],
+                            format="csr", dtype=bool)
+    pat = sp.csr_matrix(pat, dtype=bool)
+    pat.sort_indices()
+    return pat
+
+
+def colours(lev: ChannelLevel) -> np.ndarray:
+    """Colour classes of the level's patches for the class-by-class multiplicative sweep:
+    first fit over the structural coupling, enlarged patches in cell order, then the standard
+    ones (the same relation and order as on the periodic grid, oracle/colouring.py)."""
+    from . import colouring
+    if lev._colours is None:
+        lev._colours = colouring.greedy_colours(lev.patches, coupling(lev))
+    return lev._colours
+
+
+def coloured_sweep(lev: ChannelLevel, w, b):
+    """One multiplicative sweep (Sec. 3.3) visiting the colour classes in turn (a class's
+    patches in ascending cell order): each patch solves its local residual from the current
+    iterate.  No mean is removed."""
+    w = np.array(w, dtype=np.float64, copy=True)
+    col = colours(lev)
+    for k in range(int(col.max()) + 1):
+        for c in np.nonzero(col == k)[0]:
+            s = lev.solvers[c]
+            w[s.dofs] += s.apply(b[s.dofs] - lev.K[s.dofs] @ w)
+    return w
+
+
+def additive_sweep(lev: ChannelLevel, w, b, alpha: float = 1.0):
+    """One weighted additive sweep (Eq. additive_cav_saddle) with Theta = 1 / patch count; no
+    mean is removed."""
+    from . import smoother
+    if getattr(lev, "theta", None) is None:
+        lev.theta = smoother.partition_weights(lev.patches, lev.ch.n)
+    r = b - lev.K @ w
+    corr = np.zeros_like(w)
+    for s in lev.solvers:
+        corr[s.dofs] += lev.theta[s.dofs] * s.apply(r[s.dofs])
+    return w + alpha * corr
+
+
+def _smooth(lev, x, b, mode, alpha):
+    if mode == "coloured":
+        return coloured_sweep(lev, x, b)
+    if mode == "additive":
+        return additive_sweep(lev, x, b, alpha)
+    return sweep(lev, x, b)
+
+
+def vcycle(levels, b, nu_pre=1, nu_post=1, li=0, mode="lexicographic", alpha=1.0):
+    """z = B b: one V-cycle with zero initial guess on the channel hierarchy (Sec. 4); mode
+    "lexicographic" (the paper's multiplicative sweep in cell order), "coloured" (the same
+    sweep class by class) or "additive"."""
     lev = levels[li]
     if lev.coarsest:
         return lev.Kinv @ b
     x = np.zeros_like(b)
     for _ in range(nu_pre):
-        x = sweep(lev, x, b)
+        x = _smooth(lev, x, b, mode, alpha)
     chc = levels[li + 1].ch
-    xc = vcycle(levels, restrict(chc) @ (b - lev.K @ x), nu_pre, nu_post, li + 1)
+    xc = vcycle(levels, restrict(chc) @ (b - lev.K @ x), nu_pre, nu_post, li + 1, mode, alpha)
     x = x + prolong(chc) @ xc
     for _ in range(nu_post):
-        x = sweep(lev, x, b)
+        x = _smooth(lev, x, b, mode, alpha)
     return x
 
 
@@ -342,7 +410,8 @@ def ib_hierarchy(ch: Channel, EE: sp.csr_matrix, pattern, coarsest_N: int = 8):
         nv = 2 * c.Nx * c.Ny
         K = (operator(c)[0] - c.dt * sp.bmat([[EEl, None], [None, sp.csr_matrix((c.n - nv, c.n - nv))]])).tocsr()
         coarsest = c.Nx // 2 < coarsest_N or c.Nx % 2 or c.Ny % 2
-        levels.append(ChannelLevel(c, K, patches=None if coarsest else cav_patches(c, patl), coarsest=coarsest))
+        levels.append(ChannelLevel(c, K, patches=None if coarsest else cav_patches(c, patl), coarsest=coarsest,
+                                   ee_pattern=patl))
         if coarsest:
             return levels
         cc = Channel(c.Nx // 2, c.Ny // 2, 2 * c.h, c.rho, c.mu, c.dt)
@@ -422,7 +491,7 @@ def backflow_traction(ch: Channel, w):
 
 
 def fiber_step(ch: Channel, rec, w_n, t_next: float, solver: str = "direct", rtol=1e-8, atol=1e-8,
-               maxit=20, fgmres_rtol=1e-9):
+               maxit=20, fgmres_rtol=1e-9, mode: str = "lexicographic"):
     """One time step of Sec. 5.3's scheme in the channel, from the velocity-pressure w_n at t^n
     and the fiber configuration rec.X = X^n to t^{n+1} = t_next:
 
@@ -431,8 +500,8 @@ def fiber_step(ch: Channel, rec, w_n, t_next: float, solver: str = "direct", rto
     the inflow v = -U(t^{n+1}) on the top wall, the traction outflow with the backflow term at
     u^n, the convective term explicit at u^n.  Newton's method on (u, p) (oracle/newton.py's
     iteration) with each linear system solved directly ("direct") or by CAV-preconditioned
-    FGMRES with the hierarchy rebuilt per Newton system ("cav", 1 + 1 sweeps, to fgmres_rtol,
-    as the paper does).  Returns (w, X^{n+1}, residual history, FGMRES counts)."""
+    FGMRES with the hierarchy rebuilt per Newton system ("cav", 1 + 1 sweeps of the given mode,
+    to fgmres_rtol, as the paper does).  Returns (w, X^{n+1}, residual history, FGMRES counts)."""
     from dataclasses import replace
 
     import scipy.sparse.linalg as spla
@@ -478,8 +547,8 @@ def fiber_step(ch: Channel, rec, w_n, t_next: float, solver: str = "direct", rto
             w = spla.spsolve(K.tocsc(), rhs)
         else:
             levels = ib_hierarchy(ch, EE, pat)
-            w, info = fgmres.fgmres(lambda v: K @ v, rhs, lambda r: vcycle(levels, r), rtol=fgmres_rtol,
-                                    maxit=150, ref="r0")
+            w, info = fgmres.fgmres(lambda v: K @ v, rhs, lambda r: vcycle(levels, r, mode=mode),
+                                    rtol=fgmres_rtol, maxit=150, ref="r0")
             its.append(info["iters"])
         k += 1
         hist.append(np.linalg.norm(residual(w)))

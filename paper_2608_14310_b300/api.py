@@ -100,6 +100,9 @@ _sig = {
     "ib_interp": (C.c_int, [_vp, _vp, _vp, _vp]),
     "ib_step_rhs": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ib_advect": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ib_channel_rhs": (C.c_int, [_vp, _vp, C.c_double, C.c_double, _vp, _vp]),
+    "ib_newton_rhs": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ib_residual_norm": (C.c_int, [_vp, _vp, _vp, _vp, _P(C.c_double), _vp]),
     "cav_setup": (C.c_int, [_vp, _P(cav_desc), _vp, _P(_vp)]),
     "cav_num_levels": (C.c_int, [_vp, _P(C.c_int32)]),
     "cav_get_level_info": (C.c_int, [_vp, C.c_int32, _P(cav_level_info)]),
@@ -274,6 +277,22 @@ def ib_advect(sys: System, u, stream=None) -> np.ndarray:
     out = np.zeros(2 * M)
     _check(_lib.ib_advect(sys.handle, _dev(u), _vp(out.ctypes.data), _stream(stream)), "ib_advect")
     return out.reshape(M, 2)
+
+
+def ib_channel_rhs(sys: System, w_n, U_next: float, U_prev: float, b, stream=None):
+    _check(_lib.ib_channel_rhs(sys.handle, _dev(w_n), float(U_next), float(U_prev), _dev(b), _stream(stream)),
+           "ib_channel_rhs")
+
+
+def ib_newton_rhs(sys: System, b_base, w, rhs, stream=None):
+    _check(_lib.ib_newton_rhs(sys.handle, _dev(b_base), _dev(w), _dev(rhs), _stream(stream)), "ib_newton_rhs")
+
+
+def ib_residual_norm(sys: System, b, x, r, stream=None) -> float:
+    out = C.c_double()
+    _check(_lib.ib_residual_norm(sys.handle, _dev(b), _dev(x), _dev(r), C.byref(out), _stream(stream)),
+           "ib_residual_norm")
+    return out.value
 
 
 def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=1.0,

@@ -55,7 +55,17 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   CAV_REQUIRE(grid->L > 0 && grid->rho > 0 && grid->mu >= 0 && grid->dt > 0,
               "ib_setup: L, rho, dt must be positive and mu non-negative");
   CAV_REQUIRE(grid->bc == IB_BC_PERIODIC || grid->bc == IB_BC_CHANNEL, "ib_setup: unknown boundary condition");
-  CAV_REQUIRE(grid->bc == IB_BC_PERIODIC, "ib_setup: the channel boundary (IB_BC_CHANNEL) is not supported yet");
+  if (grid->bc == IB_BC_CHANNEL && sd->M > 0 && sd->X) {
+    // E_E, S and J are assembled as on the periodic grid: the markers' four-point supports
+    // must stay clear of the top and bottom walls (no wrap in y)
+    const double h = grid->L / grid->N;
+    for (int a = 0; a < sd->M; ++a) {
+      const double y = sd->X[2 * a + 1];
+      CAV_REQUIRE(y >= 2.5 * h && y <= grid->L - 2.5 * h,
+                  "ib_setup: on the channel every marker must lie at least 2.5 h from the top and bottom "
+                  "walls (its kernel support may not reach them)");
+    }
+  }
   CAV_REQUIRE(sd->M >= 0, "ib_setup: M must be non-negative");
   CAV_REQUIRE(sd->M == 0 || (sd->X && sd->omega), "ib_setup: X and omega are required when M > 0");
   CAV_REQUIRE(sd->law >= IB_FORCE_TARGET && sd->law <= IB_FORCE_FIBER, "ib_setup: unknown force law");
@@ -109,6 +119,7 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   s->M = M;
   s->bw = bw;
   s->status = s->arena.alloc<int>(1);
+  s->partial = s->arena.alloc<double>(reduce_blocks(3LL * s->N * s->N) + 1);
   CAV_CHECK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   build_markers_and_ee(s, sd->X, sd->X_lin ? sd->X_lin : sd->X, sd->omega, st);
   if (M > 0) {
@@ -166,7 +177,7 @@ ib_status ib_update_structure(ib_system* s, const ib_structure_desc* sd, cudaStr
 }
 
 static LevelOps sys_ops(const ib_system* s) {
-  LevelOps o{s->N, s->h, s->rho / s->dt, s->mu, s->dt, &s->ee};
+  LevelOps o{s->N, s->h, s->rho / s->dt, s->mu, s->dt, &s->ee, s->bc == IB_BC_CHANNEL};
   return o;
 }
 
@@ -318,12 +329,12 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
     info->sum_n = 3 * NN;
     info->sum_n2 = 9 * NN * NN;
   } else {
-    const int64_t nstd = lv.box ? 0 : NN - lv.n_big;
+    const int64_t nstd = lv.box ? 0 : NN - lv.n_big;  // n_std4 of them have four unknowns
     info->n_patches = (int32_t)(lv.box ? lv.n_big : NN);
     info->n_enlarged = lv.n_big;
-    info->max_n = lv.box ? lv.big_max_n : std::max(lv.big_max_n, 5);
-    info->sum_n = lv.big_sum_n + 5 * nstd;
-    info->sum_n2 = lv.big_sum_n2 + 25 * nstd;
+    info->max_n = lv.box ? lv.big_max_n : std::max(lv.big_max_n, nstd > lv.n_std4 ? 5 : 4);
+    info->sum_n = lv.big_sum_n + 5 * nstd - lv.n_std4;
+    info->sum_n2 = lv.big_sum_n2 + 25 * nstd - 9 * (int64_t)lv.n_std4;
     info->enlarged_sum_n = lv.big_sum_n;
     info->enlarged_sum_n2 = lv.big_sum_n2;
     const int bytes = (lv.precision == CAV_PREC_FP64) ? 8 : (lv.precision == CAV_PREC_FP32 ? 4 : 2);
@@ -342,7 +353,7 @@ ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offse
   const Level& lv = level_of(h, level);
   CAV_REQUIRE(!lv.coarsest, "cav_patch_export: the coarsest level has no patches");
   const int N = lv.N, NN = N * N;
-  const int64_t total = lv.big_sum_n + (lv.box ? 0 : 5LL * (NN - lv.n_big));
+  const int64_t total = lv.big_sum_n + (lv.box ? 0 : 5LL * (NN - lv.n_big) - lv.n_std4);
   if (n_patches) *n_patches = lv.box ? lv.n_big : NN;
   if (sum_n) *sum_n = total;
   if (!offsets || !dofs) return IB_OK;
@@ -374,8 +385,13 @@ ib_status cav_patch_export(const cav_hierarchy* h, int32_t level, int64_t* offse
     } else {
       const int i = c % N, j = c / N;
       int v[5] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i, 2 * NN + j * N + i};
-      std::sort(v, v + 5);
-      for (int t = 0; t < 5; ++t) dofs[pos++] = v[t];
+      int len = 5;
+      if (lv.channel && j + 1 == N) {  // the inflow row: no v_{i,N}
+        v[3] = v[4];
+        len = 4;
+      }
+      std::sort(v, v + len);
+      for (int t = 0; t < len; ++t) dofs[pos++] = v[t];
     }
   }
   offsets[NN] = pos;
@@ -445,7 +461,7 @@ ib_status cav_residual(const cav_hierarchy* h, int32_t level, const double* b, c
   CAV_API_BEGIN
   const Level& lv = level_of(h, level);
   CAV_REQUIRE(b && w && r, "cav_residual: NULL vector");
-  LevelOps o{lv.N, lv.h, lv.rho_dt, lv.mu, lv.dt, &lv.ee};
+  LevelOps o{lv.N, lv.h, lv.rho_dt, lv.mu, lv.dt, &lv.ee, lv.channel};
   launch_apply(o, w, b, r, 0, st);
   return IB_OK;
   CAV_API_END
@@ -455,7 +471,7 @@ ib_status cav_restrict(const cav_hierarchy* h, int32_t level, const double* r, d
   CAV_API_BEGIN
   const Level& lv = level_of(h, level);
   CAV_REQUIRE(!lv.coarsest && r && bc, "cav_restrict: bad level or NULL vector");
-  launch_restrict(lv.N / 2, r, bc, st);
+  launch_restrict(lv.N / 2, r, bc, lv.channel, st);
   return IB_OK;
   CAV_API_END
 }
@@ -464,7 +480,7 @@ ib_status cav_prolong_add(const cav_hierarchy* h, int32_t level, const double* x
   CAV_API_BEGIN
   const Level& lv = level_of(h, level);
   CAV_REQUIRE(!lv.coarsest && xc && w, "cav_prolong_add: bad level or NULL vector");
-  launch_prolong_add(lv.N / 2, xc, w, st);
+  launch_prolong_add(lv.N / 2, xc, w, lv.channel, st);
   return IB_OK;
   CAV_API_END
 }

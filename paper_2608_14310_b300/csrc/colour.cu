@@ -101,6 +101,7 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     for (int c = 0, q = 0; c < NN; ++c)
       if (big[c]) pidx[c] = q++;
   auto is_big = [&](int c) { return box || big[c] != 0; };
+  const bool ch = lv.channel;
   int stdbuf[5];
   auto patch = [&](int c, const int*& ptr, int& len) {
     if (is_big(c)) {
@@ -109,13 +110,13 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
       len = (int)(off[q + 1] - off[q]);
     } else {
       const int i = c % N, j = c / N;
-      stdbuf[0] = c;
-      stdbuf[1] = j * N + (i + 1) % N;
-      stdbuf[2] = NN + c;
-      stdbuf[3] = NN + ((j + 1) % N) * N + i;
-      stdbuf[4] = 2 * NN + c;
+      len = 0;
+      stdbuf[len++] = c;
+      stdbuf[len++] = j * N + (i + 1) % N;
+      stdbuf[len++] = NN + c;
+      if (!(ch && j + 1 == N)) stdbuf[len++] = NN + ((j + 1) % N) * N + i;  // the channel's inflow row: no v_{i,N}
+      stdbuf[len++] = 2 * NN + c;
       ptr = stdbuf;
-      len = 5;
     }
   };
   // holders: for every unknown, the units whose patch holds it (ascending)
@@ -163,25 +164,38 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
       const int k = ptr[t];
       const int comp = k / NN, cc = k % NN, i = cc % N, j = cc / N;
       add(k);
+      // channel: no wrap in y; the outflow row's ghosts reach the v faces of the row (u row)
+      // and the u faces of the row (v row), the inflow row loses the prescribed v_{i,N}
+      const bool bot = ch && j == 0, top = ch && j + 1 == N;
       if (comp == 0) {  // u row: A0 stencil in u, G to the two adjacent cells
         add(j * N + wrap(i + 1));
         add(j * N + wrap(i - 1));
-        add(wrap(j + 1) * N + i);
-        add(wrap(j - 1) * N + i);
+        if (!top) add(wrap(j + 1) * N + i);
+        if (!bot) {
+          add(wrap(j - 1) * N + i);
+        } else {
+          add(NN + j * N + i);
+          add(NN + j * N + wrap(i - 1));
+        }
         add(2 * NN + j * N + i);
         add(2 * NN + j * N + wrap(i - 1));
       } else if (comp == 1) {
         add(NN + j * N + wrap(i + 1));
         add(NN + j * N + wrap(i - 1));
-        add(NN + wrap(j + 1) * N + i);
-        add(NN + wrap(j - 1) * N + i);
+        if (!top) add(NN + wrap(j + 1) * N + i);
+        if (!bot) {
+          add(NN + wrap(j - 1) * N + i);
+          add(2 * NN + wrap(j - 1) * N + i);
+        } else {
+          add(j * N + wrap(i + 1));
+          add(j * N + i);
+        }
         add(2 * NN + j * N + i);
-        add(2 * NN + wrap(j - 1) * N + i);
       } else {  // p row: -D
         add(j * N + i);
         add(j * N + wrap(i + 1));
         add(NN + j * N + i);
-        add(NN + wrap(j + 1) * N + i);
+        if (!top) add(NN + wrap(j + 1) * N + i);
       }
       if (comp < 2 && row_of[k] >= 0) {
         const int r = row_of[k];
@@ -311,6 +325,7 @@ struct ColourStep {
   int chunk_max;         // slots per slice, upper bound over the level
   int ld_max;
   int* status;
+  bool channel;          // the channel's boundary rows and standard patches (Sec. 5.3)
   StdInv S;
 };
 
@@ -342,11 +357,50 @@ __device__ inline R ldw(const double* p) {
   return (R)__ldcg(p);
 }
 
+// A boundary row (j = 0 or N - 1) of the channel's Stokes part of K_E w, from the ghost rules
+// of the level's operator (homogeneous boundary data), with a = rho/dt and m = mu/h^2 written
+// as cdiag = a + 4m, cnb = -m:
+//   outflow u:  (a + 3m) u - m (u_E + u_W + u_N + v_ij) + m v_{i-1,j} + (p_ij - p_{i-1,j}) / h
+//   outflow v:  (a + 3m) v - 3m v_N + m (u_{i+1,j} - u_ij) + 2 p_ij / h
+//   inflow u:   (a + 5m) u - m (u_E + u_W + u_S) + (p_ij - p_{i-1,j}) / h
+//   inflow v:   (a + 4m) v - m (v_E + v_W + v_S) + (p_ij - p_{i,j-1}) / h
+//   inflow p:   -((u_{i+1,j} - u_ij) - v_ij) / h;  the outflow p row is the periodic one.
+template <typename R, typename T>
+__device__ inline R channel_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
+  const int N = a.N, NN = N * N;
+  const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
+  const double* u = w;
+  const double* v = w + NN;
+  const double* p = w + 2 * NN;
+  const int c = j * N + i;
+  const R ih = (R)a.ih, m = (R)(-a.cnb), cdiag = (R)a.cdiag;
+  if (j == 0) {
+    if (comp == 0)
+      return (cdiag - m) * ldw<R>(u + c) -
+             m * ((ldw<R>(u + j * N + ip) + ldw<R>(u + j * N + im)) + (ldw<R>(u + N + i) + ldw<R>(v + c))) +
+             m * ldw<R>(v + j * N + im) + ih * (ldw<R>(p + c) - ldw<R>(p + j * N + im));
+    if (comp == 1)
+      return (cdiag - m) * ldw<R>(v + c) - (R)3 * m * ldw<R>(v + N + i) +
+             m * (ldw<R>(u + j * N + ip) - ldw<R>(u + c)) + (R)2 * ih * ldw<R>(p + c);
+    return -((ldw<R>(u + j * N + ip) - ldw<R>(u + c)) + (ldw<R>(v + N + i) - ldw<R>(v + c))) * ih;
+  }
+  if (comp == 0)
+    return (cdiag + m) * ldw<R>(u + c) -
+           m * ((ldw<R>(u + j * N + ip) + ldw<R>(u + j * N + im)) + ldw<R>(u + (j - 1) * N + i)) +
+           ih * (ldw<R>(p + c) - ldw<R>(p + j * N + im));
+  if (comp == 1)
+    return cdiag * ldw<R>(v + c) -
+           m * ((ldw<R>(v + j * N + ip) + ldw<R>(v + j * N + im)) + ldw<R>(v + (j - 1) * N + i)) +
+           ih * (ldw<R>(p + c) - ldw<R>(p + (j - 1) * N + i));
+  return -((ldw<R>(u + j * N + ip) - ldw<R>(u + c)) - ldw<R>(v + c)) * ih;
+}
+
 // Stokes row of unknown (comp, i, j) of K_E w (Eq. intro_saddle: A0 u + G p, or -D u), in the
 // form cdiag u_c + cnb (sum of the four neighbours) + (p_c - p_w) / h, seven operations in R.
 template <typename R, typename T>
 __device__ inline R stokes_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
   const int N = a.N, NN = N * N;
+  if (a.channel && (j == 0 || j + 1 == N)) return channel_row_l2<R>(a, w, comp, i, j);
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
   const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
   const int c = j * N + i;
@@ -397,23 +451,28 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     const int slot = lane / 5, q = lane % 5;
     const int t = ((int)blockIdx.x - big_blocks) * CS_STD_CELLS + warp * CS_STD_PER_WARP + slot;
     const bool act = slot < CS_STD_PER_WARP && t < a.nstd;
-    int k = 0, ci = 0, cj = 0, comp = 0, ro = -1;
+    int k = 0, ci = 0, cj = 0, comp = 0, ro = -1, kind = 0;
     double bk = 0.0;
+    bool slot_act = act;
     if (act) {
       const int c = a.std_list[t];
       const int i = c % a.N, j = c / a.N;
       const int ip = (i + 1 == a.N) ? 0 : i + 1, jp = (j + 1 == a.N) ? 0 : j + 1;
-      // canonical slots: u_ij, u_i+1j, v_ij, v_ij+1, p_ij
+      kind = std_kind(a.N, j, a.channel);
+      // canonical slots: u_ij, u_i+1j, v_ij, v_ij+1, p_ij (the channel's inflow row has no v_ij+1)
       comp = (q < 2) ? 0 : (q < 4 ? 1 : 2);
       ci = (q == 1) ? ip : i;
       cj = (q == 3) ? jp : j;
       k = comp * NN + cj * a.N + ci;
-      bk = b[k];
-      if (comp < 2 && a.row_of) ro = a.row_of[k];
+      slot_act = !(kind == 2 && q == 3);
+      if (slot_act) {
+        bk = b[k];
+        if (comp < 2 && a.row_of) ro = a.row_of[k];
+      }
     }
     pdl_wait();
     double r = 0.0, old = 0.0;
-    if (act) {
+    if (slot_act) {
       old = __ldcg(w + k);
       double kr = stokes_row_l2<double>(a, w, comp, ci, cj);
       if (ro >= 0) {
@@ -427,8 +486,8 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     double rr[5];
 #pragma unroll
     for (int c2 = 0; c2 < 5; ++c2) rr[c2] = __shfl_sync(0xffffffffu, r, min(base + c2, 31));
-    if (act) {
-      const double* m = a.S.m + 5 * q;
+    if (slot_act) {
+      const double* m = a.S.m[kind] + 5 * q;
       w[k] = old + (m[0] * rr[0] + m[1] * rr[1] + m[2] * rr[2] + m[3] * rr[3] + m[4] * rr[4]);
     }
     return;
@@ -565,10 +624,11 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   // A bounded wait that runs out records DEV_TIMEOUT; the CTA then stops staging (the host
   // reports IB_ERR_TIMEOUT), after waiting for the copy in flight to land.
   bool alive = true;
+  const bool stall = wait_stall_enabled();
   uint32_t phase = 0;
   for (int b0 = 0; b0 < m; b0 += pc) {
     const int nc = min(pc, m - b0);
-    const bool got = mbar_wait(bar, phase, a.status);
+    const bool got = mbar_wait(bar, phase, a.status, nullptr, stall);
     if (got) {
 #pragma unroll
       for (int ps = 0; ps < CS_MAXPASS; ++ps) {
@@ -710,7 +770,9 @@ static void launch_step(const cav_hierarchy* H, const Level& lv, const T* inv, i
   a.chunk_max = sh.chunk_max;
   a.slice_cap = sh.slice_cap;
   a.status = H->status;
-  for (int q = 0; q < 25; ++q) a.S.m[q] = lv.std_inv[q];
+  for (int kd = 0; kd < 3; ++kd)
+    for (int q = 0; q < 25; ++q) a.S.m[kd][q] = lv.std_inv[kd][q];
+  a.channel = lv.channel;
   a.ee_row_max = lv.ee_row_max;
   const size_t smem = sh.smem;
   CAV_REQUIRE(smem <= 200 * 1024, "coloured smoother: class step needs too much shared memory");
@@ -763,7 +825,8 @@ void coloured_sweep(const cav_hierarchy* H, int l, const double* b, double* w, b
     }
   }
   if (profile) prof_end(H, l, st);
-  if (remove_mean) pressure_mean_remove(lv.N, partial, w + 2 * (size_t)NN, st);
+  // the channel's pressure is determined (traction outflow): no mean to remove
+  if (remove_mean && !lv.channel) pressure_mean_remove(lv.N, partial, w + 2 * (size_t)NN, st);
 }
 
 void pressure_mean_remove(int N, double* partial, double* p, cudaStream_t st) {

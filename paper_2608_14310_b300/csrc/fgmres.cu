@@ -346,7 +346,7 @@ static void fg_start(FgState& s) {
   CAV_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * s.L.total, s.st));
   // the Krylov operator is the system's current K_E; the hierarchy only preconditions (it may
   // have been built from an earlier configuration of the same system)
-  s.op = LevelOps{l0.N, l0.h, l0.rho_dt, l0.mu, l0.dt, &s.sys->ee};
+  s.op = LevelOps{l0.N, l0.h, l0.rho_dt, l0.mu, l0.dt, &s.sys->ee, l0.channel};
   s.nb = dot_blocks(s.n);
   s.cb = cmb_blocks(s.n);
   s.nbmax = s.nb > s.cb ? s.nb : s.cb;

@@ -86,6 +86,7 @@ struct EECsr {
 struct Level {
   int N = 0;
   double h = 0, rho_dt = 0, mu = 0, dt = 0;
+  bool channel = false;          // the channel's boundary rows, transfers and patches (Sec. 5.3)
   bool coarsest = false;
   bool coloured = false;         // this level smooths with the class-by-class multiplicative sweep
   bool box = false;              // box patches B(b,o): one per block, all enlarged, restricted injection
@@ -94,6 +95,7 @@ struct Level {
 
   // patches (smoothing levels): one per cell; enlarged ones are stored explicitly
   int n_big = 0;                 // enlarged patches
+  int n_std4 = 0;                // standard patches with four unknowns (the channel's inflow row)
   int64_t big_sum_n = 0, big_sum_n2 = 0, inv_elems = 0;
   int big_max_n = 0;
   uint8_t* cell_big = nullptr;   // [N^2] 1 if the cell's patch is enlarged
@@ -116,8 +118,11 @@ struct Level {
   int* inc_slot = nullptr;       // [big_sum_n] packed-delta slots, ascending per unknown
   int n_touched = 0;             // unknowns held by at least one enlarged patch
   int* touched = nullptr;        // [n_touched] ascending
-  double std_inv[25];            // inverse of the standard Vanka patch, canonical order
-                                 // (u_ij, u_i+1j, v_ij, v_ij+1, p_ij), scalings folded in
+  double std_inv[3][25];         // inverse of the standard Vanka patch, canonical order
+                                 // (u_ij, u_i+1j, v_ij, v_ij+1, p_ij), scalings folded in:
+                                 // [0] every cell of a periodic level, or the channel's
+                                 // interior rows; [1] the channel's outflow row, [2] its
+                                 // inflow row (slot 3 absent: zero row and column)
 
   // colour classes for the multiplicative sweep (smoother CAV_SMOOTH_COLOURED): patches of
   // one class share no unknown and no entry of K_E couples them, so a class is solved at once
@@ -132,8 +137,10 @@ struct Level {
   float* ee_vals32 = nullptr;        // [ee.nnz] E_E values in FP32 (FP32-inverse coloured levels)
   int ee_row_max = 0;                // longest E_E row on this level
 
-  // coarsest level: dense inverse of the bordered system, row-major (n+1) x (n+1)
+  // coarsest level: dense inverse, row-major m x m: the bordered system (m = n + 1) on a
+  // periodic level, the plain one (m = n) on the channel, whose pressure is determined
   double* coarse_inv = nullptr;
+  int coarse_m = 0;
 
   // work vectors of this level
   double* r = nullptr;           // [3 N^2] residual
@@ -178,7 +185,7 @@ struct ib_system {
   int* fm_list = nullptr;        // ascending marker ids
   cav::EECsr ee;                 // finest-level E_E
   int* status = nullptr;         // device status word
-  double* partial = nullptr;
+  double* partial = nullptr;     // [reduce_blocks(3 N^2) + 1] reduction scratch
 };
 
 struct cav_hierarchy {
@@ -240,12 +247,13 @@ struct LevelOps {
   int N;
   double h, rho_dt, mu, dt;
   const EECsr* ee;
+  bool channel = false;
 };
 // mode 0: out = b - K w  (b may be null = 0);  mode 1: out = K w
 void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
                   cudaStream_t st);
-void launch_restrict(int Nc, const double* r_f, double* b_c, cudaStream_t st);
-void launch_prolong_add(int Nc, const double* x_c, double* w_f, cudaStream_t st);
+void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st);
+void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st);
 
 // setup.cu
 void build_levels(cav_hierarchy* H, cudaStream_t st);
@@ -277,6 +285,9 @@ void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st)
 int reduce_blocks(int64_t n);
 void launch_dot_partials(const double* a, const double* b, int64_t n, double* partial,
                          cudaStream_t st);
+// <a, b> on the device (fixed order), returned to the host after a stream synchronisation;
+// partial holds at least reduce_blocks(n) + 1 doubles
+double device_dot(const double* a, const double* b, int64_t n, double* partial, cudaStream_t st);
 // exclusive scan of int counts into int64 offsets (out has n + 1 entries)
 void exclusive_scan(const int* counts, int64_t* out, int64_t n, cudaStream_t st, Arena* scratch);
 

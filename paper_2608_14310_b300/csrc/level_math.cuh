@@ -11,25 +11,50 @@ namespace cav {
 
 // Rows of the Stokes part of K_E w (Eq. Eul_schur) at cell (i, j):
 //   u: (rho/dt) u - mu L u + (p_ij - p_i-1j)/h,  v: likewise,  p: -(D u)_ij.
+// Periodic grid: every index wraps.  Channel (Sec. 5.3; periodic in x, prescribed inflow on
+// the top wall y = L, traction outflow on y = 0): the same rows with homogeneous boundary
+// data, values outside the unknowns taken from ghost values (the boundary data of a time
+// step enter its right-hand side instead):
+//   above the top row   u_{i,N} = -u_{i,N-1} (the wall value is the mean), v_{i,N} = 0;
+//   below the bottom row, from the tangential traction, continuity in the ghost cell and the
+//   normal traction:  u_{i,-1} = u_{i,0} + (v_{i,0} - v_{i-1,0}),
+//                     v_{i,-1} = v_{i,0} + (u_{i+1,-1} - u_{i,-1}),
+//                     p_{i,-1} = (2 mu / h)(v_{i,1} - v_{i,-1}) - p_{i,0}.
 struct StokesRows {
   double ku, kv, kp;
 };
-__device__ inline StokesRows stokes_rows(int N, double h, double rho_dt, double mu, const double* w, int i, int j) {
+__device__ inline StokesRows stokes_rows(int N, double h, double rho_dt, double mu, const double* w, int i, int j,
+                                         bool channel = false) {
   const int NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
   const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
+  const bool bot = channel && j == 0, top = channel && j + 1 == N;
   const double* u = w;
   const double* v = w + NN;
   const double* p = w + 2 * NN;
   const int c = j * N + i;
   const double ih = 1.0 / h, ih2 = 1.0 / (h * h);
   const double uc = u[c], vc = v[c], pc = p[c];
-  const double uip = u[j * N + ip], vjp = v[jp * N + i];
-  const double lu = (uip + u[j * N + im] + u[jp * N + i] + u[jm * N + i] - 4.0 * uc) * ih2;
-  const double lv = (v[j * N + ip] + v[j * N + im] + vjp + v[jm * N + i] - 4.0 * vc) * ih2;
+  const double uip = u[j * N + ip];
+  const double vjp = top ? 0.0 : v[jp * N + i];
+  const double u_up = top ? -uc : u[jp * N + i];
+  double u_dn, v_dn, p_dn;
+  if (bot) {
+    const double gu = uc + (vc - v[j * N + im]);              // u_{i,-1}
+    const double gu_ip = uip + (v[j * N + ip] - vc);          // u_{i+1,-1}
+    u_dn = gu;
+    v_dn = vc + (gu_ip - gu);                                 // v_{i,-1}
+    p_dn = (2.0 * mu / h) * (v[jp * N + i] - v_dn) - pc;      // p_{i,-1}
+  } else {
+    u_dn = u[jm * N + i];
+    v_dn = v[jm * N + i];
+    p_dn = p[jm * N + i];
+  }
+  const double lu = (uip + u[j * N + im] + u_up + u_dn - 4.0 * uc) * ih2;
+  const double lv = (v[j * N + ip] + v[j * N + im] + vjp + v_dn - 4.0 * vc) * ih2;
   StokesRows o;
   o.ku = rho_dt * uc - mu * lu + (pc - p[j * N + im]) * ih;
-  o.kv = rho_dt * vc - mu * lv + (pc - p[jm * N + i]) * ih;
+  o.kv = rho_dt * vc - mu * lv + (pc - p_dn) * ih;
   o.kp = -((uip - uc) + (vjp - vc)) * ih;
   return o;
 }
@@ -53,7 +78,9 @@ __device__ inline double row_group_reduce(double s) {
 
 // Restriction at coarse cell (I, J): velocity R = (1/4) P^T of RT0 prolongation, pressure
 // the mean of the four fine cells.
-__device__ inline void restrict_cell(int Nc, const double* rf, double* bc, int I, int J) {
+// Channel: the fine v faces below coarse row J = 0 do not exist (the transpose of the
+// channel prolongation below).
+__device__ inline void restrict_cell(int Nc, const double* rf, double* bc, int I, int J, bool channel = false) {
   const int Nf = 2 * Nc, NNf = Nf * Nf, NNc = Nc * Nc;
   const double* u = rf;
   const double* v = rf + NNf;
@@ -67,7 +94,7 @@ __device__ inline void restrict_cell(int Nc, const double* rf, double* bc, int I
                     0.5 * (u[j0 * Nf + im] + u[j1 * Nf + im]);
   const double rv = v[j0 * Nf + i0] + v[j0 * Nf + i1] +
                     0.5 * (v[j1 * Nf + i0] + v[j1 * Nf + i1]) +
-                    0.5 * (v[jm * Nf + i0] + v[jm * Nf + i1]);
+                    ((channel && J == 0) ? 0.0 : 0.5 * (v[jm * Nf + i0] + v[jm * Nf + i1]));
   const double rp = p[j0 * Nf + i0] + p[j0 * Nf + i1] + p[j1 * Nf + i0] +
                     p[j1 * Nf + i1];
   const int c = J * Nc + I;
@@ -77,8 +104,11 @@ __device__ inline void restrict_cell(int Nc, const double* rf, double* bc, int I
 }
 
 // w_f += P x_c at fine cell (i, j): RT0 velocity interpolation and bilinear pressure
-// interpolation between cell centres (9/16, 3/16, 3/16, 1/16).
-__device__ inline void prolong_cell(int Nc, const double* xc, double* wf, int i, int j) {
+// interpolation between cell centres (9/16, 3/16, 3/16, 1/16).  Channel: a fine v face on
+// the midline of a top-row coarse cell takes half the coarse face below it (the prescribed
+// top faces carry no correction), and the pressure stencil is clamped to the boundary cells
+// in y.
+__device__ inline void prolong_cell(int Nc, const double* xc, double* wf, int i, int j, bool channel = false) {
   const int Nf = 2 * Nc;
   const int NNf = Nf * Nf, NNc = Nc * Nc;
   const double* U = xc;
@@ -91,8 +121,11 @@ __device__ inline void prolong_cell(int Nc, const double* xc, double* wf, int i,
   if ((i & 1) == 0) du = U[J * Nc + I];
   else du = 0.5 * (U[J * Nc + I] + U[J * Nc + Ip]);
   if ((j & 1) == 0) dv = V[J * Nc + I];
+  else if (channel && J + 1 == Nc) dv = 0.5 * V[J * Nc + I];
   else dv = 0.5 * (V[J * Nc + I] + V[Jp * Nc + I]);
-  const int Is = (i & 1) ? Ip : Im, Js = (j & 1) ? Jp : Jm;
+  int Js = (j & 1) ? Jp : Jm;
+  if (channel) Js = (j & 1) ? min(J + 1, Nc - 1) : max(J - 1, 0);
+  const int Is = (i & 1) ? Ip : Im;
   const double dp = (9.0 / 16.0) * P[J * Nc + I] + (3.0 / 16.0) * P[J * Nc + Is] +
                     (3.0 / 16.0) * P[Js * Nc + I] + (1.0 / 16.0) * P[Js * Nc + Is];
   const int c = j * Nf + i;
@@ -168,17 +201,25 @@ __device__ inline float mad(float x, float y, float acc) { return fmaf(x, y, acc
 
 // ------------------------------------------------------------------ standard Vanka patch
 
+// Inverse(s) of the standard Vanka patch in canonical slot order (u_ij, u_i+1j, v_ij,
+// v_ij+1, p_ij), scalings folded in.  Periodic grid: one matrix (all cells alike).  Channel:
+// kind 0 interior rows, kind 1 the outflow row j = 0, kind 2 the inflow row j = N - 1, whose
+// patch has no v_{i,N} (slot 3: zero row and column).
 struct StdInv {
-  double m[25];
+  double m[3][25];
 };
+__device__ inline int std_kind(int N, int j, bool channel) {
+  return !channel ? 0 : (j == 0 ? 1 : (j + 1 == N ? 2 : 0));
+}
 
-// canonical slots of cell (i, j)'s standard patch: u_ij, u_i+1j, v_ij, v_ij+1, p_ij
-__device__ inline double std_row(const StdInv& S, int row, const double* r, int N, int i, int j) {
+__device__ inline double std_row(const StdInv& S, int row, const double* r, int N, int i, int j,
+                                 bool channel = false) {
   const int NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, jp = (j + 1 == N) ? 0 : j + 1;
+  const int kind = std_kind(N, j, channel);
   const double y0 = r[j * N + i], y1 = r[j * N + ip], y2 = r[NN + j * N + i],
-               y3 = r[NN + jp * N + i], y4 = r[2 * NN + j * N + i];
-  const double* m = S.m + 5 * row;
+               y3 = (kind == 2) ? 0.0 : r[NN + jp * N + i], y4 = r[2 * NN + j * N + i];
+  const double* m = S.m[kind] + 5 * row;
   return m[0] * y0 + m[1] * y1 + m[2] * y2 + m[3] * y3 + m[4] * y4;
 }
 

@@ -101,6 +101,27 @@ void launch_dot_partials(const double* a, const double* b, int64_t n, double* pa
   CAV_CHECK_LAUNCH();
 }
 
+// out[0] = sum of partial[0 .. nb) in a fixed order (one block)
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, double* out) {
+  __shared__ double sm[RED_THREADS / 32];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) s += partial[q];
+  s = block_sum(s, sm);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+double device_dot(const double* a, const double* b, int64_t n, double* partial, cudaStream_t st) {
+  const int nb = reduce_blocks(n);
+  k_dot_partials<<<nb, RED_THREADS, 0, st>>>(a, b, n, partial);
+  CAV_CHECK_LAUNCH();
+  k_sum_partials<<<1, RED_THREADS, 0, st>>>(partial, nb, partial + nb);
+  CAV_CHECK_LAUNCH();
+  double h = 0.0;
+  CAV_CHECK_CUDA(cudaMemcpyAsync(&h, partial + nb, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
 int read_status(int* d_status, cudaStream_t st) {
   int h = 0;
   CAV_CHECK_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));

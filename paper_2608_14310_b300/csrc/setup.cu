@@ -12,8 +12,9 @@ namespace cav {
 // ------------------------------------------------------------------ Galerkin E_E
 
 // Fine faces k with P[k, K] != 0 for coarse face K = (c, I, J) and their weights
-// (RT0: coincident faces weight 1, faces on the coarse cell's midlines weight 1/2).
-__device__ inline int pcol(int c, int I, int J, int Nf, int* fi, int* fj, double* wt) {
+// (RT0: coincident faces weight 1, faces on the coarse cell's midlines weight 1/2); returns
+// their count.  Channel: a coarse v face of the outflow row J = 0 has no fine faces below it.
+__device__ inline int pcol(int c, int I, int J, int Nf, int* fi, int* fj, double* wt, bool channel = false) {
   if (c == 0) {
     const int i0 = 2 * I, j0 = 2 * J;
     fi[0] = i0; fj[0] = j0; wt[0] = 1.0;
@@ -31,14 +32,20 @@ __device__ inline int pcol(int c, int I, int J, int Nf, int* fi, int* fj, double
     fi[4] = i0; fj[4] = j0 + 1; wt[4] = 0.5;
     fi[5] = i0 + 1; fj[5] = j0 + 1; wt[5] = 0.5;
   }
-  for (int t = 0; t < 6; ++t) {
+  int n = 6;
+  if (channel && c == 1 && J == 0) {  // drop entries 2 and 3 (fine row -1)
+    fi[2] = fi[4]; fj[2] = fj[4]; wt[2] = wt[4];
+    fi[3] = fi[5]; fj[3] = fj[5]; wt[3] = wt[5];
+    n = 4;
+  }
+  for (int t = 0; t < n; ++t) {
     fi[t] = pmod(fi[t], Nf);
     fj[t] = pmod(fj[t], Nf);
   }
-  return 6;
+  return n;
 }
 
-__global__ void k_coarse_active(int Nc, const int* __restrict__ row_of_f, int* flag) {
+__global__ void k_coarse_active(int Nc, const int* __restrict__ row_of_f, int* flag, bool channel) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   const int NNc = Nc * Nc;
   if (K >= 2 * NNc) return;
@@ -46,9 +53,9 @@ __global__ void k_coarse_active(int Nc, const int* __restrict__ row_of_f, int* f
   const int Nf = 2 * Nc;
   int fi[6], fj[6];
   double wt[6];
-  pcol(c, I, J, Nf, fi, fj, wt);
+  const int nt = pcol(c, I, J, Nf, fi, fj, wt, channel);
   int f = 0;
-  for (int t = 0; t < 6; ++t) f |= (row_of_f[c * Nf * Nf + fj[t] * Nf + fi[t]] >= 0);
+  for (int t = 0; t < nt; ++t) f |= (row_of_f[c * Nf * Nf + fj[t] * Nf + fi[t]] >= 0);
   flag[K] = f;
 }
 
@@ -74,7 +81,7 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
                            const int* __restrict__ row_of_f, const int64_t* __restrict__ rowptr_f,
                            const int* __restrict__ cols_f, const double* __restrict__ vals_f,
                            int* row_count, const int64_t* __restrict__ rowptr, int* cols, double* vals,
-                           int pass) {
+                           int pass, bool channel) {
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= n_rows) return;
@@ -83,9 +90,9 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
   const int c = K / NNc, rem = K % NNc, I = rem % Nc, J = rem / Nc;
   int ki[6], kj[6];
   double kw[6];
-  pcol(c, I, J, Nf, ki, kj, kw);
+  const int nk = pcol(c, I, J, Nf, ki, kj, kw, channel);
   int krow[6];
-  for (int t = 0; t < 6; ++t) krow[t] = row_of_f[c * NNf + kj[t] * Nf + ki[t]];
+  for (int t = 0; t < 6; ++t) krow[t] = (t < nk) ? row_of_f[c * NNf + kj[t] * Nf + ki[t]] : -1;
   const Win wx = make_win(I, Wc, Nc), wy = make_win(J, Wc, Nc);
   const int ncell = wx.len * wy.len;
   int64_t outpos = (pass == 1) ? rowptr[r] : 0;
@@ -103,12 +110,12 @@ __global__ void k_galerkin(int Nc, int Wc, int n_rows, const int* __restrict__ r
         L = cl * NNc + gy * Nc + gx;
         int li[6], lj[6];
         double lw[6];
-        pcol(cl, gx, gy, Nf, li, lj, lw);
+        const int nl = pcol(cl, gx, gy, Nf, li, lj, lw, channel);
         for (int t = 0; t < 6; ++t) {
           if (krow[t] < 0) continue;
           const int64_t b = rowptr_f[krow[t]], e = rowptr_f[krow[t] + 1];
           double s = 0.0;
-          for (int u = 0; u < 6; ++u) {
+          for (int u = 0; u < nl; ++u) {
             const int l = cl * NNf + lj[u] * Nf + li[u];
             const int pos = find_col(cols_f, b, e, l);
             if (pos >= 0) {
@@ -142,14 +149,14 @@ __global__ void k_compact_rows2(int n, const int* flag, const int64_t* pos, int*
   }
 }
 
-static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int* d_scratch,
+static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int* d_scratch, bool channel,
                            cudaStream_t st) {
   Arena scratch;
   const int NNc = Nc * Nc;
   int* flag = scratch.alloc<int>(2 * NNc);
   int64_t* pos = scratch.alloc<int64_t>(2 * NNc + 1);
   out.row_of = A.alloc<int>(2 * NNc);
-  k_coarse_active<<<div_up(2 * NNc, 256), 256, 0, st>>>(Nc, fine.row_of, flag);
+  k_coarse_active<<<div_up(2 * NNc, 256), 256, 0, st>>>(Nc, fine.row_of, flag, channel);
   CAV_CHECK_LAUNCH();
   exclusive_scan(flag, pos, 2 * NNc, st, &scratch);
   int64_t nrows = 0;
@@ -169,10 +176,10 @@ static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int*
     if (nrows == 0) return;
     if (out.cross)
       k_galerkin<true><<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
-                                             fine.vals, row_count, rowptr, cols, vals, pass);
+                                             fine.vals, row_count, rowptr, cols, vals, pass, channel);
     else
       k_galerkin<false><<<grid, 256, 0, st>>>(Nc, Wc, (int)nrows, out.rows, fine.row_of, fine.rowptr, fine.cols,
-                                              fine.vals, row_count, rowptr, cols, vals, pass);
+                                              fine.vals, row_count, rowptr, cols, vals, pass, channel);
     CAV_CHECK_LAUNCH();
   };
   galerkin(nullptr, nullptr, nullptr, 0);
@@ -190,18 +197,30 @@ static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int*
 
 // ------------------------------------------------------------------ CAV patch sets
 
+// Velocity unknowns U_ij of cell (i, j)'s Vanka patch: u_ij, u_i+1j, v_ij, v_ij+1; on the
+// channel's inflow row the top face is prescribed, so U_ij has three (U[3] = -1).
+__device__ inline int cell_velocities(int N, int i, int j, bool channel, int* U) {
+  const int NN = N * N;
+  U[0] = j * N + i;
+  U[1] = j * N + (i + 1) % N;
+  U[2] = NN + j * N + i;
+  U[3] = (channel && j + 1 == N) ? -1 : NN + ((j + 1) % N) * N + i;
+  return U[3] < 0 ? 3 : 4;
+}
+
 // Cell c = (i, j) keeps its standard Vanka patch iff no velocity of U_ij couples through
 // E_E to a velocity outside U_ij (Eq. cav_patch_set; E_E's pattern is symmetric).
 __global__ void k_cell_flags(int N, int cav, const int* __restrict__ row_of, const int64_t* __restrict__ rowptr,
-                             const int* __restrict__ cols, uint8_t* big, int* flag) {
+                             const int* __restrict__ cols, uint8_t* big, int* flag, bool channel) {
   const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
   const int NN = N * N;
   if (cidx >= NN) return;
   const int i = cidx % N, j = cidx / N;
-  const int U4[4] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i};
+  int U4[4];
+  const int nu = cell_velocities(N, i, j, channel, U4);
   int enl = 0;
   if (cav) {
-    for (int t = 0; t < 4 && !enl; ++t) {
+    for (int t = 0; t < nu && !enl; ++t) {
       const int r = row_of[U4[t]];
       if (r < 0) continue;
       for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
@@ -233,12 +252,14 @@ __device__ inline void mark_cell(uint8_t* cm, const Win& wx, const Win& wy, int 
   if (ox < 0 || oy < 0) atomicExch(status, DEV_WINDOW);
   else cm[oy * wx.len + ox] = 1;
 }
+// The cells incident to velocity face k: a u face's left and right cells, a v face's cells
+// below and above (on the channel's outflow row only the one above).
 __device__ inline void mark_face_cells(uint8_t* cm, const Win& wx, const Win& wy, int N, int k,
-                                       int* status) {
+                                       int* status, bool channel) {
   const int NN = N * N;
   const int c = k / NN, rem = k % NN, i = rem % N, j = rem / N;
   if (c == 0) mark_cell(cm, wx, wy, N, i - 1, j, status);
-  else mark_cell(cm, wx, wy, N, i, j - 1, status);
+  else if (!(channel && j == 0)) mark_cell(cm, wx, wy, N, i, j - 1, status);
   mark_cell(cm, wx, wy, N, i, j, status);
 }
 __device__ inline void mark_dof(uint8_t* dm, const Win& wx, const Win& wy, int N, int comp, int gi,
@@ -254,7 +275,7 @@ __device__ inline void mark_dof(uint8_t* dm, const Win& wx, const Win& wy, int N
 __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_cell,
                            const int* __restrict__ row_of, const int64_t* __restrict__ rowptr,
                            const int* __restrict__ cols, int* sizes, const int64_t* __restrict__ off,
-                           int* dofs, int pass, int* status) {
+                           int* dofs, int pass, int* status, bool channel) {
   extern __shared__ unsigned char smem[];
   const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * warps + warp;
@@ -272,13 +293,14 @@ __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_
   const Win dx = make_win(i, Wd, N), dy = make_win(j, Wd, N);
   for (int t = lane; t < per_warp; t += 32) cm[t] = 0;
   __syncwarp();
-  const int U4[4] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i};
-  for (int t = 0; t < 4; ++t) {
-    if (lane == 0) mark_face_cells(cm, cx, cy, N, U4[t], status);
+  int U4[4];
+  const int nu = cell_velocities(N, i, j, channel, U4);
+  for (int t = 0; t < nu; ++t) {
+    if (lane == 0) mark_face_cells(cm, cx, cy, N, U4[t], status, channel);
     const int r = row_of[U4[t]];
     if (r < 0) continue;
     for (int64_t q = rowptr[r] + lane; q < rowptr[r + 1]; q += 32)
-      mark_face_cells(cm, cx, cy, N, cols[q], status);
+      mark_face_cells(cm, cx, cy, N, cols[q], status, channel);
   }
   __syncwarp();
   for (int t = lane; t < lenC * lenC; t += 32) {
@@ -288,7 +310,7 @@ __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_
     mark_dof(dm, dx, dy, N, 0, a, b, status);
     mark_dof(dm, dx, dy, N, 0, a + 1, b, status);
     mark_dof(dm, dx, dy, N, 1, a, b, status);
-    mark_dof(dm, dx, dy, N, 1, a, b + 1, status);
+    if (!(channel && b + 1 == N)) mark_dof(dm, dx, dy, N, 1, a, b + 1, status);
     mark_dof(dm, dx, dy, N, 2, a, b, status);
   }
   __syncwarp();
@@ -324,17 +346,80 @@ __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_
 struct LevelK {
   int N;
   double h, rho_dt, mu, dt;
+  bool channel;
   const int* row_of;
   const int64_t* rowptr;
   const int* cols;
   const double* vals;
 };
 
+// The Stokes entries of a boundary row (j = 0 or N - 1) of the channel's K_E: the rows of the
+// ghost rules (homogeneous data), written out term by term.  With a = rho/dt, m = mu/h^2:
+//   outflow row  u_{i,0}:  a + 3m at u_{i,0}; -m at u_{i+-1,0}, u_{i,1}, v_{i,0}; +m at v_{i-1,0};
+//                          +-1/h at p_{i,0}, p_{i-1,0}
+//                v_{i,0}:  a + 3m at v_{i,0}; -3m at v_{i,1}; +m at u_{i+1,0}; -m at u_{i,0};
+//                          2/h at p_{i,0}; v_{i+-1,0} cancel (structural zeros)
+//                p_{i,0}:  -(D u)_{i,0} as on the periodic grid
+//   inflow row   u_{i,N-1}: a + 5m on the diagonal, the rest as on the periodic grid without
+//                the wrap to row 0; v_{i,N-1} and p_{i,N-1}: the periodic rows without the
+//                prescribed v_{i,N}.
+// Returns the number of entries written to col / val (at most 8).
+__device__ inline int channel_row(const LevelK& L, int comp, int i, int j, int* col, double* val) {
+  const int N = L.N, NN = N * N;
+  const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
+  const double a = L.rho_dt, m = L.mu / (L.h * L.h), ih = 1.0 / L.h;
+  auto U = [&](int x, int y) { return y * N + x; };
+  auto Vf = [&](int x, int y) { return NN + y * N + x; };
+  auto Pc = [&](int x, int y) { return 2 * NN + y * N + x; };
+  int n = 0;
+  auto put = [&](int g, double v) {
+    col[n] = g;
+    val[n] = v;
+    ++n;
+  };
+  if (j == 0) {
+    if (comp == 0) {
+      put(U(i, 0), a + 3.0 * m); put(U(ip, 0), -m); put(U(im, 0), -m); put(U(i, 1), -m);
+      put(Vf(i, 0), -m); put(Vf(im, 0), m); put(Pc(i, 0), ih); put(Pc(im, 0), -ih);
+    } else if (comp == 1) {
+      put(Vf(i, 0), a + 3.0 * m); put(Vf(ip, 0), 0.0); put(Vf(im, 0), 0.0); put(Vf(i, 1), -3.0 * m);
+      put(U(ip, 0), m); put(U(i, 0), -m); put(Pc(i, 0), 2.0 * ih);
+    } else {
+      put(U(ip, 0), -ih); put(U(i, 0), ih); put(Vf(i, 1), -ih); put(Vf(i, 0), ih);
+    }
+  } else {
+    if (comp == 0) {
+      put(U(i, j), a + 5.0 * m); put(U(ip, j), -m); put(U(im, j), -m); put(U(i, j - 1), -m);
+      put(Pc(i, j), ih); put(Pc(im, j), -ih);
+    } else if (comp == 1) {
+      put(Vf(i, j), a + 4.0 * m); put(Vf(ip, j), -m); put(Vf(im, j), -m); put(Vf(i, j - 1), -m);
+      put(Pc(i, j), ih); put(Pc(i, j - 1), -ih);
+    } else {
+      put(U(ip, j), -ih); put(U(i, j), ih); put(Vf(i, j), ih);
+    }
+  }
+  return n;
+}
+
 // Entry (ga, gb) of K_E on one level (Eq. Eul_schur), with or without the E_E term.
 __device__ double ke_entry(const LevelK& L, int ga, int gb, bool use_ee) {
   const int N = L.N, NN = N * N;
   const int ca = ga / NN, ra = ga % NN, ia = ra % N, ja = ra / N;
   const int cb = gb / NN, rb = gb % NN, ib = rb % N, jb = rb / N;
+  if (L.channel && (ja == 0 || ja == N - 1)) {
+    int col[8];
+    double val[8];
+    const int n = channel_row(L, ca, ia, ja, col, val);
+    double v = 0.0;
+    for (int t = 0; t < n; ++t)
+      if (col[t] == gb) v += val[t];
+    if (use_ee && ca < 2 && cb < 2 && L.row_of[ga] >= 0) {
+      const int r = L.row_of[ga];
+      const int pos = find_col(L.cols, L.rowptr[r], L.rowptr[r + 1], gb);
+      if (pos >= 0) v = v - L.dt * L.vals[L.rowptr[r] + pos];
+    }
+    return v;
+  }
   if (ca < 2 && cb < 2) {
     if (ca != cb) {
       double v = 0.0;
@@ -603,6 +688,7 @@ static LevelK level_k(const Level& lv) {
   k.rho_dt = lv.rho_dt;
   k.mu = lv.mu;
   k.dt = lv.dt;
+  k.channel = lv.channel;
   k.row_of = lv.ee.row_of;
   k.rowptr = lv.ee.rowptr;
   k.cols = lv.ee.cols;
@@ -688,7 +774,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     int* flag = scratch.alloc<int>(NN);
     int64_t* pos = scratch.alloc<int64_t>(NN + 1);
     k_cell_flags<<<div_up(NN, 256), 256, 0, st>>>(N, H->desc.kind == CAV_PATCH_CAV ? 1 : 0, lv.ee.row_of,
-                                                 lv.ee.rowptr, lv.ee.cols, lv.cell_big, flag);
+                                                 lv.ee.rowptr, lv.ee.cols, lv.cell_big, flag, lv.channel);
     CAV_CHECK_LAUNCH();
     exclusive_scan(flag, pos, NN, st, &scratch);
     CAV_CHECK_CUDA(cudaMemcpyAsync(&nbig, pos + NN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -716,7 +802,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     if (nbig > 0) {
       k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
                                                                 lv.ee.rowptr, lv.ee.cols, sizes, nullptr,
-                                                                nullptr, 0, H->status);
+                                                                nullptr, 0, H->status, lv.channel);
       CAV_CHECK_LAUNCH();
     }
     exclusive_scan(sizes, lv.big_off, nbig, st, &scratch);
@@ -727,7 +813,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   }
   int64_t sum_n = 0, sum_n2 = 0, inv_elems = 0;
   int max_n = 0;
-  std::vector<int64_t> hinv_off(nbig + 1, 0), hmat_off(nbig + 2, 0);
+  std::vector<int64_t> hinv_off(nbig + 1, 0);
   for (int64_t p = 0; p < nbig; ++p) {
     const int n = hsizes[p];
     sum_n += n;
@@ -739,14 +825,35 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   lv.big_sum_n2 = sum_n2;
   lv.big_max_n = max_n;
   lv.inv_elems = inv_elems = hinv_off[nbig];
-  lv.big_dofs = A.alloc<int>(sum_n + 5);  // + 5: the standard patch appended for factorisation
+  // the standard patches appended for factorisation: one (periodic) or three (channel) jobs
+  std::vector<int> std_dofs;
+  std::vector<int> std_len;
+  {
+    auto cell = [&](int i, int j) {
+      int ds[5] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i, 2 * NN + j * N + i};
+      const bool top = lv.channel && j + 1 == N;
+      int len = 0;
+      for (int t = 0; t < 5; ++t)
+        if (!(top && t == 3)) std_dofs.push_back(ds[t]), ++len;
+      std_len.push_back(len);
+    };
+    if (lv.channel) {
+      cell(0, 1);      // interior rows
+      cell(0, 0);      // outflow row
+      cell(0, N - 1);  // inflow row (no v_{i,N})
+    } else {
+      cell(0, 0);
+    }
+  }
+  const int n_std = (int)std_len.size();
+  lv.big_dofs = A.alloc<int>(sum_n + (int64_t)std_dofs.size());
   if (lv.box) {
     if (sum_n > 0)
       CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs, box_dofs.data(), sizeof(int) * sum_n, cudaMemcpyHostToDevice, st));
   } else if (nbig > 0) {
     k_cav_sets<<<div_up(nbig, cav_set_warps), cav_set_warps * 32, cav_set_smem, st>>>(
         N, lv.ee.W, (int)nbig, lv.big_cell, lv.ee.row_of, lv.ee.rowptr, lv.ee.cols, nullptr, lv.big_off,
-        lv.big_dofs, 1, H->status);
+        lv.big_dofs, 1, H->status, lv.channel);
     CAV_CHECK_LAUNCH();
   }
   check_status(H, st, "patch sets");
@@ -761,34 +868,29 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   }
   CAV_CHECK_CUDA(cudaMemcpyAsync(lv.inv_off, hinv_off.data(), sizeof(int64_t) * (nbig + 1),
                                  cudaMemcpyHostToDevice, st));
-  // 3. factorise the enlarged patches plus the standard Vanka patch of cell (0, 0) (job nbig)
-  //    in canonical order (u_00, u_10, v_00, v_01, p_00) without E_E.
-  const int std_dofs[5] = {0, 1, NN, NN + N, 2 * NN};
-  CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs + sum_n, std_dofs, sizeof(int) * 5, cudaMemcpyHostToDevice, st));
-  std::vector<int64_t> hoff_ext(nbig + 2);
-  std::vector<int64_t> hbig_off(nbig + 1);
-  {
-    int64_t acc = 0;
-    for (int64_t p = 0; p <= nbig; ++p) {
-      hbig_off[p] = acc;
-      if (p < nbig) acc += hsizes[p];
-    }
-  }
-  for (int64_t p = 0; p <= nbig; ++p) hoff_ext[p] = hbig_off[std::min<int64_t>(p, nbig)];
-  hoff_ext[nbig + 1] = sum_n + 5;
-  for (int64_t p = 0; p <= nbig; ++p) {
-    const int m = (p < nbig) ? hsizes[p] : 5;
-    // a patch holding every pressure of the level gets one border row and column
+  // 3. factorise the enlarged patches, then the standard Vanka patch(es) (jobs nbig ..) in
+  //    canonical slot order (u_ij, u_i+1j, v_ij, v_ij+1, p_ij; the inflow row without v_ij+1)
+  //    without E_E.
+  CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs + sum_n, std_dofs.data(), sizeof(int) * std_dofs.size(),
+                                 cudaMemcpyHostToDevice, st));
+  const int njobs = (int)nbig + n_std;
+  std::vector<int64_t> hoff_ext(njobs + 1);
+  hoff_ext[0] = 0;
+  for (int p = 0; p < njobs; ++p) hoff_ext[p + 1] = hoff_ext[p] + (p < nbig ? hsizes[p] : std_len[p - nbig]);
+  std::vector<int64_t> hmat_off(njobs + 1, 0);
+  for (int p = 0; p < njobs; ++p) {
+    const int m = (p < nbig) ? hsizes[p] : std_len[p - nbig];
+    // a patch holding every pressure of a periodic level gets one border row and column
     hmat_off[p + 1] = hmat_off[p] + (int64_t)round8(m + 1) * (m + 1);
   }
-  int64_t* d_off_ext = scratch.alloc<int64_t>(nbig + 2);
-  int64_t* d_mat_off = scratch.alloc<int64_t>(nbig + 2);
-  CAV_CHECK_CUDA(cudaMemcpyAsync(d_off_ext, hoff_ext.data(), sizeof(int64_t) * (nbig + 2), cudaMemcpyHostToDevice, st));
-  CAV_CHECK_CUDA(cudaMemcpyAsync(d_mat_off, hmat_off.data(), sizeof(int64_t) * (nbig + 2), cudaMemcpyHostToDevice, st));
-  double* work = scratch.alloc<double>(hmat_off[nbig + 1]);
-  double* wsr = scratch.alloc<double>(sum_n + nbig + 8);
-  double* wsc = scratch.alloc<double>(sum_n + nbig + 8);
-  int* mdim = scratch.alloc<int>(nbig + 2);
+  int64_t* d_off_ext = scratch.alloc<int64_t>(njobs + 1);
+  int64_t* d_mat_off = scratch.alloc<int64_t>(njobs + 1);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_off_ext, hoff_ext.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, st));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_mat_off, hmat_off.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, st));
+  double* work = scratch.alloc<double>(hmat_off[njobs]);
+  double* wsr = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
+  double* wsc = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
+  int* mdim = scratch.alloc<int>(njobs + 1);
   FactorJob J;
   J.mdim = mdim;
   J.dof_off = d_off_ext;
@@ -797,7 +899,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   J.A = work;
   J.s_r = wsr;
   J.s_c = wsc;
-  J.border_all_pressure = 1;
+  J.border_all_pressure = lv.channel ? 0 : 1;  // the channel's pressure is determined
   J.use_ee = 1;
   const int mmax = std::max(max_n, 5) + 1;
   const size_t fsm = factor_smem(mmax);
@@ -807,22 +909,42 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     k_factor<<<(int)nbig, 256, fsm, st>>>(LK, J, 0, H->status);
     CAV_CHECK_LAUNCH();
   }
-  // the standard patch: same kernel, one block, no E_E
+  // the standard patches: same kernel, one block each, no E_E
   {
     FactorJob Js = J;
     Js.dof_off = d_off_ext + nbig;
     Js.mat_off = d_mat_off + nbig;
     Js.mdim = mdim + nbig;
-    Js.s_r = wsr + nbig;  // scale slots of this job start at sum_n + nbig
+    Js.s_r = wsr + nbig;  // scale slots of job p start at dof_off[p] + p
     Js.s_c = wsc + nbig;
     Js.use_ee = 0;
     Js.border_all_pressure = 0;
-    k_factor<<<1, 64, factor_smem(6), st>>>(LK, Js, 0, H->status);
+    k_factor<<<n_std, 64, factor_smem(6), st>>>(LK, Js, 0, H->status);
     CAV_CHECK_LAUNCH();
-    double* d_std = scratch.alloc<double>(25);
-    k_fold_rowmajor<<<1, 32, 0, st>>>(5, work + hmat_off[nbig], wsr + sum_n + nbig, wsc + sum_n + nbig, d_std);
-    CAV_CHECK_LAUNCH();
-    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.std_inv, d_std, sizeof(double) * 25, cudaMemcpyDeviceToHost, st));
+    double* d_std = scratch.alloc<double>(25 * n_std);
+    for (int q = 0; q < n_std; ++q) {
+      const int p = (int)nbig + q;
+      k_fold_rowmajor<<<1, 32, 0, st>>>(std_len[q], work + hmat_off[p], wsr + hoff_ext[p] + p, wsc + hoff_ext[p] + p,
+                                        d_std + 25 * q);
+      CAV_CHECK_LAUNCH();
+    }
+    std::vector<double> hstd(25 * n_std);
+    CAV_CHECK_CUDA(cudaMemcpyAsync(hstd.data(), d_std, sizeof(double) * 25 * n_std, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    // kind 0 interior (or every periodic cell), 1 outflow row, 2 inflow row: the inflow row's
+    // 4 x 4 inverse goes to slots (0, 1, 2, 4) with slot 3 (v_ij+1) left zero
+    for (int k = 0; k < 3; ++k)
+      for (int q = 0; q < 25; ++q) lv.std_inv[k][q] = 0.0;
+    for (int q = 0; q < n_std; ++q) {
+      const int m = std_len[q];
+      int slot[5] = {0, 1, 2, 3, 4};
+      if (m == 4) slot[3] = 4;
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) lv.std_inv[q][slot[a] * 5 + slot[b]] = hstd[25 * q + a * m + b];
+    }
+    if (n_std == 1)
+      for (int k = 1; k < 3; ++k)
+        for (int q = 0; q < 25; ++q) lv.std_inv[k][q] = lv.std_inv[0][q];
   }
   check_status(H, st, "patch factorisation");
   // 4. pack the inverses (ld = round8(n), column-major) and scales; bordered patches are
@@ -879,6 +1001,13 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     k_compact_cells<<<div_up(3 * NN, 256), 256, 0, st>>>(3 * NN, tflag, tpos, lv.touched);
     CAV_CHECK_LAUNCH();
   }
+  if (lv.channel && !lv.box) {  // standard patches of the inflow row have four unknowns
+    std::vector<uint8_t> top(N);
+    CAV_CHECK_CUDA(cudaMemcpyAsync(top.data(), lv.cell_big + (size_t)(N - 1) * N, N, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    lv.n_std4 = 0;
+    for (int i = 0; i < N; ++i) lv.n_std4 += top[i] ? 0 : 1;
+  }
   lv.n_partial_std = div_up(N, 32) * div_up(N, 8);
   lv.n_partial = lv.n_partial_std + div_up(lv.n_touched, 32);  // touched blocks: 8 warps x 4 unknowns
   lv.partial = A.alloc<double>(lv.n_partial);
@@ -890,7 +1019,8 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
 static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   Arena& A = H->arena;
   Arena scratch;
-  const int N = lv.N, NN = N * N, n = 3 * NN, m = n + 1;
+  // periodic: bordered by the pressure-mean constraint; channel: the plain operator
+  const int N = lv.N, NN = N * N, n = 3 * NN, m = lv.channel ? n : n + 1;
   const LevelK LK = level_k(lv);
   std::vector<int> all(n);
   std::iota(all.begin(), all.end(), 0);
@@ -919,8 +1049,9 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   const size_t fsm = factor_smem(m);
   if (fsm > 48 * 1024)
     CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-  k_factor<<<1, 1024, fsm, st>>>(LK, J, 1, H->status);
+  k_factor<<<1, 1024, fsm, st>>>(LK, J, lv.channel ? 0 : 1, H->status);
   CAV_CHECK_LAUNCH();
+  lv.coarse_m = m;
   lv.coarse_inv = A.alloc<double>((size_t)m * m);
   k_fold_rowmajor<<<64, 256, 0, st>>>(m, work, wsr, wsc, lv.coarse_inv);
   CAV_CHECK_LAUNCH();
@@ -943,6 +1074,7 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     lv.rho_dt = s->rho / s->dt;
     lv.mu = s->mu;
     lv.dt = s->dt;
+    lv.channel = s->bc == IB_BC_CHANNEL;
     lv.coarsest = (l + 1 == sizes.size());
     const cav_desc& d = H->desc;
     lv.coloured = !lv.coarsest && d.smoother == CAV_SMOOTH_COLOURED &&
@@ -972,7 +1104,7 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
       CAV_CHECK_CUDA(cudaMemcpyAsync(lv.ee.row_of, s->ee.row_of, sizeof(int) * 2 * (size_t)lv.N * lv.N,
                                      cudaMemcpyDeviceToDevice, st));
     } else {
-      galerkin_level(H->levels[l - 1].ee, lv.N, lv.ee, A, d_scr, st);
+      galerkin_level(H->levels[l - 1].ee, lv.N, lv.ee, A, d_scr, lv.channel, st);
     }
     const int NN = lv.N * lv.N;
     lv.r = A.alloc<double>(3 * NN);

@@ -17,14 +17,15 @@ __global__ void __launch_bounds__(RES_BX* RES_BY)
 k_residual(int N, double h, double rho_dt, double mu, double dt, const double* __restrict__ w,
            const double* __restrict__ b, double* __restrict__ out, int mode, int nb_cells, int gx,
            const int* __restrict__ row_of, int n_rows, const int* __restrict__ rows,
-           const int64_t* __restrict__ rowptr, const int* __restrict__ cols, const double* __restrict__ vals) {
+           const int64_t* __restrict__ rowptr, const int* __restrict__ cols, const double* __restrict__ vals,
+           bool channel) {
   const int NN = N * N;
   if ((int)blockIdx.x < nb_cells) {
     const int i = (blockIdx.x % gx) * RES_BX + (threadIdx.x % RES_BX);
     const int j = (blockIdx.x / gx) * RES_BY + (threadIdx.x / RES_BX);
     if (i >= N || j >= N) return;
     const int c = j * N + i;
-    const StokesRows k = stokes_rows(N, h, rho_dt, mu, w, i, j);
+    const StokesRows k = stokes_rows(N, h, rho_dt, mu, w, i, j, channel);
     const bool eu = row_of && row_of[c] >= 0, ev = row_of && row_of[NN + c] >= 0;
     if (mode == 0) {
       if (!eu) out[c] = (b ? b[c] : 0.0) - k.ku;
@@ -45,7 +46,7 @@ k_residual(int N, double h, double rho_dt, double mu, double dt, const double* _
   if (r < n_rows && sl == 0) {
     const int row = rows[r];
     const int comp = row / NN, c = row % NN;
-    const StokesRows k = stokes_rows(N, h, rho_dt, mu, w, c % N, c / N);
+    const StokesRows k = stokes_rows(N, h, rho_dt, mu, w, c % N, c / N, channel);
     const double kr = ((comp == 0) ? k.ku : k.kv) - dt * s;
     out[row] = (mode == 0) ? ((b ? b[row] : 0.0) - kr) : kr;
   }
@@ -60,35 +61,35 @@ void launch_apply(const LevelOps& op, const double* w, const double* b, double* 
   k_residual<<<nb_cells + nb_rows, RES_BX * RES_BY, 0, st>>>(
       op.N, op.h, op.rho_dt, op.mu, op.dt, w, b, out, mode, nb_cells, gx, has_ee ? op.ee->row_of : nullptr,
       has_ee ? op.ee->n_rows : 0, has_ee ? op.ee->rows : nullptr, has_ee ? op.ee->rowptr : nullptr,
-      has_ee ? op.ee->cols : nullptr, has_ee ? op.ee->vals : nullptr);
+      has_ee ? op.ee->cols : nullptr, has_ee ? op.ee->vals : nullptr, op.channel);
   CAV_CHECK_LAUNCH();
 }
 
 // Restriction (Sec. 4), one thread per coarse cell (I, J).
-__global__ void k_restrict(int Nc, const double* __restrict__ rf, double* __restrict__ bc) {
+__global__ void k_restrict(int Nc, const double* __restrict__ rf, double* __restrict__ bc, bool channel) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= Nc || J >= Nc) return;
-  restrict_cell(Nc, rf, bc, I, J);
+  restrict_cell(Nc, rf, bc, I, J, channel);
 }
 
 // w_f += P x_c (Sec. 4), one thread per fine cell (i, j).
-__global__ void k_prolong_add(int Nc, const double* __restrict__ xc, double* __restrict__ wf) {
+__global__ void k_prolong_add(int Nc, const double* __restrict__ xc, double* __restrict__ wf, bool channel) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= 2 * Nc || j >= 2 * Nc) return;
-  prolong_cell(Nc, xc, wf, i, j);
+  prolong_cell(Nc, xc, wf, i, j, channel);
 }
 
-void launch_restrict(int Nc, const double* r_f, double* b_c, cudaStream_t st) {
+void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st) {
   dim3 blk(32, 8), grd(div_up(Nc, 32), div_up(Nc, 8));
-  k_restrict<<<grd, blk, 0, st>>>(Nc, r_f, b_c);
+  k_restrict<<<grd, blk, 0, st>>>(Nc, r_f, b_c, channel);
   CAV_CHECK_LAUNCH();
 }
 
-void launch_prolong_add(int Nc, const double* x_c, double* w_f, cudaStream_t st) {
+void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st) {
   dim3 blk(32, 8), grd(div_up(2 * Nc, 32), div_up(2 * Nc, 8));
-  k_prolong_add<<<grd, blk, 0, st>>>(Nc, x_c, w_f);
+  k_prolong_add<<<grd, blk, 0, st>>>(Nc, x_c, w_f, channel);
   CAV_CHECK_LAUNCH();
 }
 

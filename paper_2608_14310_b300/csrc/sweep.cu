@@ -120,6 +120,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   uint64_t* yempty = yfull + Y_SLOTS;
   int* abort_flag = reinterpret_cast<int*>(yempty + Y_SLOTS);
   volatile int* ab = abort_flag;
+  const bool stall = wait_stall_enabled();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     *abort_flag = 0;
@@ -199,7 +200,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     const int ld = (n + 7) & ~7;
     const int cpc = TMA_CHUNK / (int)(ld * sizeof(T));
     const int slot = t & 1;
-    if (!__all_sync(0xffffffffu, mbar_wait(&yfull[slot], (uint32_t)((t >> 1) & 1), status, ab))) break;
+    if (!__all_sync(0xffffffffu, mbar_wait(&yfull[slot], (uint32_t)((t >> 1) & 1), status, ab, stall))) break;
     const acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
     acc_t acc[TMA_MAXPASS][V];
 #pragma unroll
@@ -209,7 +210,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     bool dead = false;
     for (int b0 = 0; b0 < n; b0 += cpc) {
       const int nc = min(cpc, n - b0);
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, status, ab))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, status, ab, stall))) {
         dead = true;
         break;
       }
@@ -261,13 +262,15 @@ constexpr int TOUCH_WARPS = 8;
 //    unknowns per warp).  The lanes sum the enlarged patches' corrections at the unknown (fixed
 //    lane-strided order, fixed shuffle tree); the group's first lane adds the standard patches
 //    of its incident cells that kept their Vanka patch and divides by the total patch count.
+// On the channel a v face of the outflow row has one incident cell (the one above it), and
+// the standard patches of the outflow and inflow rows have their own inverses.
 // Each block writes the partial sum of the new pressures it produced (fixed order); the
 // stencil blocks' partials come first, then the touched blocks'.
 __global__ void __launch_bounds__(256)
 k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __restrict__ inc_off,
          int n_touched, const int* __restrict__ touched, const uint8_t* __restrict__ cell_big,
          const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
-         double* __restrict__ w, int w_is_zero, double* __restrict__ partial) {
+         double* __restrict__ w, int w_is_zero, double* __restrict__ partial, bool channel) {
   __shared__ double sm[8];
   const int NN = N * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -279,15 +282,20 @@ k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __res
       const int c = j * N + i;
       const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
       if (inc_off[c + 1] == inc_off[c]) {
-        const double s = std_row(S, 1, r, N, im, j) + std_row(S, 0, r, N, i, j);
+        const double s = std_row(S, 1, r, N, im, j, channel) + std_row(S, 0, r, N, i, j, channel);
         w[c] = (w_is_zero ? 0.0 : w[c]) + alpha * (s / 2.0);
       }
       if (inc_off[NN + c + 1] == inc_off[NN + c]) {
-        const double s = std_row(S, 3, r, N, i, jm) + std_row(S, 2, r, N, i, j);
-        w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * (s / 2.0);
+        if (channel && j == 0) {  // the outflow row's v face: one incident cell
+          const double s = std_row(S, 2, r, N, i, j, channel);
+          w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * s;
+        } else {
+          const double s = std_row(S, 3, r, N, i, jm, channel) + std_row(S, 2, r, N, i, j, channel);
+          w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * (s / 2.0);
+        }
       }
       if (inc_off[2 * NN + c + 1] == inc_off[2 * NN + c]) {
-        const double s = std_row(S, 4, r, N, i, j);
+        const double s = std_row(S, 4, r, N, i, j, channel);
         pnew = (w_is_zero ? 0.0 : w[2 * NN + c]) + alpha * s;
         w[2 * NN + c] = pnew;
       }
@@ -314,13 +322,13 @@ k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __res
         int cnt = (int)(q1 - q0);
         double st = 0.0;
         if (comp == 0) {
-          if (!cell_big[j * N + im]) { st += std_row(S, 1, r, N, im, j); ++cnt; }
-          if (!cell_big[c]) { st += std_row(S, 0, r, N, i, j); ++cnt; }
+          if (!cell_big[j * N + im]) { st += std_row(S, 1, r, N, im, j, channel); ++cnt; }
+          if (!cell_big[c]) { st += std_row(S, 0, r, N, i, j, channel); ++cnt; }
         } else if (comp == 1) {
-          if (!cell_big[jm * N + i]) { st += std_row(S, 3, r, N, i, jm); ++cnt; }
-          if (!cell_big[c]) { st += std_row(S, 2, r, N, i, j); ++cnt; }
+          if (!(channel && j == 0) && !cell_big[jm * N + i]) { st += std_row(S, 3, r, N, i, jm, channel); ++cnt; }
+          if (!cell_big[c]) { st += std_row(S, 2, r, N, i, j, channel); ++cnt; }
         } else {
-          if (!cell_big[c]) { st += std_row(S, 4, r, N, i, j); ++cnt; }
+          if (!cell_big[c]) { st += std_row(S, 4, r, N, i, j, channel); ++cnt; }
         }
         const double nw = (w_is_zero ? 0.0 : w[k]) + alpha * ((st + s) / (double)cnt);
         w[k] = nw;
@@ -358,13 +366,14 @@ void launch_remove_mean(int N, int n_partial, const double* partial, double* p, 
   CAV_CHECK_LAUNCH();
 }
 
-// Coarsest level: z = (dense bordered inverse) [r; 0], one warp per row, row-major.
-__global__ void k_coarse_apply(int n, const double* __restrict__ inv, const double* __restrict__ r,
+// Coarsest level: z = (dense inverse) [r; 0], one warp per row, row-major with leading
+// dimension ld (n + 1 for the bordered periodic system, n on the channel).
+__global__ void k_coarse_apply(int n, int ld, const double* __restrict__ inv, const double* __restrict__ r,
                                double* __restrict__ z) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const double* a = inv + (int64_t)row * (n + 1);
+  const double* a = inv + (int64_t)row * ld;
   double s = 0.0;
   for (int b = lane; b < n; b += 32) s += a[b] * r[b];
   s = warp_sum(s);
@@ -381,6 +390,7 @@ static LevelOps ops_of(const Level& lv) {
   o.mu = lv.mu;
   o.dt = lv.dt;
   o.ee = &lv.ee;
+  o.channel = lv.channel;
   return o;
 }
 
@@ -559,15 +569,16 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
     if (profile) prof_end(H, l, st);
   }
   StdInv S;
-  for (int q = 0; q < 25; ++q) S.m[q] = lv.std_inv[q];
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 25; ++q) S.m[k][q] = lv.std_inv[k][q];
   const int gx = div_up(lv.N, 32), gy = div_up(lv.N, 8);
   const int nb_std = gx * gy;
   const int nb_touch = div_up(lv.n_touched, TOUCH_WARPS * TOUCH_PER_WARP);
   k_update<<<nb_std + nb_touch, 256, 0, st>>>(lv.N, H->desc.alpha, S, nb_std, gx, lv.inc_off, lv.n_touched,
                                               lv.touched, lv.cell_big, lv.inc_slot, delta_buf, r, w,
-                                              w_is_zero ? 1 : 0, partial_buf);
+                                              w_is_zero ? 1 : 0, partial_buf, lv.channel);
   CAV_CHECK_LAUNCH();
-  if (remove_mean) {
+  if (remove_mean && !lv.channel) {  // the channel's pressure is determined: no mean to remove
     const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
     k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, partial_buf, w + 2 * lv.N * lv.N);
     CAV_CHECK_LAUNCH();
@@ -605,7 +616,7 @@ static void cycle_sweep(const cav_hierarchy* H, int l, const double* b, double* 
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st) {
   const Level& lv = H->levels.back();
   const int n = 3 * lv.N * lv.N;
-  k_coarse_apply<<<div_up(n, 8), 256, 0, st>>>(n, lv.coarse_inv, r, z);
+  k_coarse_apply<<<div_up(n, 8), 256, 0, st>>>(n, lv.coarse_m, lv.coarse_inv, r, z);
   CAV_CHECK_LAUNCH();
 }
 
@@ -621,11 +632,11 @@ static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double*
   for (int s = 0; s < nu_pre; ++s) cycle_sweep(H, l, b, x, s == 0, st);
   launch_apply(ops_of(lv), x, b, lv.r, 0, st);
   const Level& lc = H->levels[l + 1];
-  launch_restrict(lc.N, lv.r, lc.b, st);
+  launch_restrict(lc.N, lv.r, lc.b, lv.channel, st);
   vcycle_level(H, l + 1, lc.b, lc.x, st);
-  launch_prolong_add(lc.N, lc.x, x, st);
+  launch_prolong_add(lc.N, lc.x, x, lv.channel, st);
   for (int s = 0; s < nu_post; ++s) cycle_sweep(H, l, b, x, false, st);
-  if (l == 0) {
+  if (l == 0 && !lv.channel) {
     if (nu_post > 0 && lv.coloured) {
       pressure_mean_remove(lv.N, lv.partial, x + 2 * NN, st);
     } else if (nu_post > 0) {

@@ -52,13 +52,17 @@ constexpr long long WAIT_LIMIT = 1LL << 31;
 constexpr long long WAIT_LIMIT_STALL = 1LL << 20;
 static __device__ int g_wait_stall = 0;
 
+// The test hook's state, read once at kernel entry (it does not change while kernels run).
+__device__ inline bool wait_stall_enabled() { return g_wait_stall != 0; }
+
 // Wait for the phase with the given parity to complete.  `abort` (shared memory, nullable)
 // is a CTA-wide flag: a wait also gives up (without recording a status) once another thread
 // of the CTA has set it, and a wait that runs out sets it, so the other roles of the CTA stop
-// waiting on work that will not come.
+// waiting on work that will not come.  `stall`: this wait is stalled by the test hook (the
+// caller passes wait_stall_enabled() for waits for data, false otherwise).
 __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort = nullptr,
-                                 bool stallable = true) {
-  const bool stall = stallable && *(volatile int*)&g_wait_stall != 0;
+                                 bool stall = false) {
+  if (!stall && mbar_try_wait(bar, parity)) return true;  // the common case: no clock read
   const long long limit = stall ? WAIT_LIMIT_STALL : WAIT_LIMIT;
   const long long t0 = clock64();
   while (stall || !mbar_try_wait(bar, parity)) {

@@ -9,6 +9,7 @@
 """
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import ib_workloads as W
 from oracle import channel, grid
@@ -287,3 +288,99 @@ def test_parameter_robustness_rows_at_reduced_size():
         _, _, _, its = channel.fiber_step(ch, rec, np.zeros(ch.n), ch.dt, solver="cav", maxit=1)
         counts.append(its[0])
     assert max(counts) <= 15 and max(counts) - min(counts) <= 2 and abs(np.mean(counts) - 9.6) <= 3, counts
+
+
+# ----------------------------------------------------------------- class-by-class order
+
+def test_structure_contains_the_operator_and_is_symmetric():
+    # the structural pattern (every unknown a row's stencil reaches through the ghosts) holds
+    # every nonzero of K0 for any boundary data and parameters, is symmetric (so a row-based
+    # conflict test is a symmetric relation), and keeps the outflow v row's cancelled entries
+    ch = _ch(8, 8, mu=0.37)
+    S = channel.operator(ch, structural=True)[0]
+    rng = np.random.default_rng(8)
+    K, _ = channel.operator(ch, 0.3, rng.uniform(-1, 1, 8), rng.uniform(-1, 1, 8), rng.uniform(-1, 1, 8))
+    Kp = sp.csr_matrix(K != 0, dtype=bool)
+    Sp = sp.csr_matrix(S != 0, dtype=bool)
+    assert (Kp > Sp).nnz == 0
+    assert (Sp != Sp.T).nnz == 0
+    r = ch.iv(3, 0)
+    assert S[r, ch.iv(2, 0)] == 1 and S[r, ch.iv(4, 0)] == 1 and K[r, ch.iv(4, 0)] == 0.0
+
+
+def _fiber_levels(N=16):
+    from oracle import ib
+    rec = W.fiber_channel(N)
+    ch = channel.Channel(rec.N, rec.N, rec.h, rec.rho, rec.mu, rec.dt)
+    EE, pat = ib.eulerian_elasticity(rec)
+    return rec, ch, channel.ib_hierarchy(ch, EE, pat)
+
+
+def test_channel_colour_classes_are_independent_and_first_fit():
+    rec, ch, levels = _fiber_levels(16)
+    for lev in levels[:-1]:
+        col = channel.colours(lev)
+        C = channel.coupling(lev).astype(np.int32)
+        n = lev.ch.n
+        P = sp.csr_matrix((np.ones(sum(len(p) for p in lev.patches), dtype=np.int32),
+                           np.concatenate(lev.patches),
+                           np.concatenate([[0], np.cumsum([len(p) for p in lev.patches])])),
+                          shape=(len(lev.patches), n))
+        M = (P @ C @ P.T).tocoo()  # patch p reads (through its rows) an unknown of patch q
+        for p, q in zip(M.row, M.col):
+            if p != q:
+                assert col[p] != col[q], (p, q)
+        big = [c for c, p in enumerate(lev.patches) if len(p) > 5]
+        assert len(big) > 0 and col.max() + 1 < len(lev.patches)
+
+
+def test_channel_coloured_sweep_is_the_sequential_sweep_in_class_order():
+    from oracle import smoother
+    rec, ch, levels = _fiber_levels(16)
+    lev = levels[0]
+    col = channel.colours(lev)
+    order = np.argsort(col, kind="stable")
+    rng = np.random.default_rng(9)
+    b = rng.uniform(-1, 1, ch.n)
+    w0 = rng.uniform(-1, 1, ch.n) * 1e-2
+    got = channel.coloured_sweep(lev, w0, b)
+    # the same multiplicative sweep written out patch by patch in class order
+    w = w0.copy()
+    for c in order:
+        s = lev.solvers[c]
+        w[s.dofs] += s.apply(b[s.dofs] - lev.K[s.dofs] @ w)
+    assert np.linalg.norm(got - w) <= 1e-12 * np.linalg.norm(w)
+    # and it contracts like the lexicographic one
+    lex = channel.sweep(lev, w0, b)
+    r0 = np.linalg.norm(b - lev.K @ w0)
+    assert np.linalg.norm(b - lev.K @ got) <= 0.5 * r0 and np.linalg.norm(b - lev.K @ lex) <= 0.5 * r0
+    del smoother
+
+
+def test_channel_additive_sweep_weights_overlaps():
+    # with a whole-domain patch listed twice (Theta = 1/2) one additive sweep with alpha = 1 is
+    # an exact solve of the (nonsingular) channel operator
+    from oracle import smoother
+    ch = _ch(8, 8)
+    K, _ = channel.operator(ch)
+    lev = channel.ChannelLevel(ch, K, patches=[np.arange(ch.n), np.arange(ch.n)])
+    b = W.uniform_pm1(77, ch.n)
+    w = channel.additive_sweep(lev, np.zeros(ch.n), b, 1.0)
+    assert np.linalg.norm(b - K @ w) <= 1e-11 * np.linalg.norm(b)
+    del smoother
+
+
+def test_fiber_channel_coloured_vcycle_counts():
+    # the class-by-class order (the GPU's) gives the first linear system a count within the
+    # paper's range, within two of the lexicographic order's
+    from oracle import fgmres, ib
+    rec, ch, levels = _fiber_levels(16)
+    K = levels[0].K
+    b = ib.first_step_rhs(rec)
+    its = {}
+    for mode in ("lexicographic", "coloured"):
+        _, info = fgmres.fgmres(lambda v: K @ v, b, lambda r: channel.vcycle(levels, r, mode=mode),
+                                rtol=1e-9, maxit=150, ref="r0")
+        assert info["converged"]
+        its[mode] = info["iters"]
+    assert abs(its["coloured"] - its["lexicographic"]) <= 2 and its["coloured"] <= 13, its

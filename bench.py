@@ -393,6 +393,63 @@ def run_beam512(args, api, torch, rank):
     return 0
 
 
+# Sec. 5.3's refinement study (Table 3): averages over the paper's whole run
+PAPER_FIBER = {16: (8.65, 13, 2.00), 32: (9.02, 14, 1.48), 64: (9.15, 15, 1.45), 128: (9.53, 16, 1.60)}
+
+
+def run_fiber(args, api, torch, rank):
+    """The flow-past-a-fiber benchmark (Sec. 5.3) in its channel: `nsteps` time steps from rest,
+    each solved by Newton's method with every Newton system solved by CAV-preconditioned
+    FGMRES (coloured multiplicative smoother, 1 + 1 sweeps, hierarchy rebuilt per system).
+    One step = one time step (ib_setup at X^n, the step's right-hand side, then per Newton
+    iterate: E_E at X_k, Newton right-hand side and residual, cav_setup, fgmres_solve).
+    value = Newton-system solves per second (set-up included)."""
+    from paper_2608_14310_b300.fiber_channel import FiberChannel
+    if rank:
+        return 0
+    rec = W.fiber_channel(args.fiber_n)
+    prec = "fp64" if args.precision == "bf16" else args.precision
+    fc = FiberChannel(rec, cav=dict(kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, smoother="coloured",
+                                    precision=prec), fgmres_rtol=args.fiber_rtol)
+    n = 3 * rec.N * rec.N
+    w = torch.zeros(n, dtype=torch.float64, device="cuda")
+    t = 0.0
+    newton, its, secs, nonconv = [], [], [], 0
+    launches0 = api.ib_launch_count()
+    clocks = ClockSampler(0)
+    for s in range(args.nsteps):
+        t += rec.dt
+        w, X, hist, infos, sec = fc.step(w, t)
+        newton.append(len(hist) - 1)
+        its.extend(i["iters"] for i in infos)
+        nonconv += sum(1 for i in infos if not i["converged"])
+        secs.append(sec)
+    clk = clocks.stop()
+    launches = api.ib_launch_count() - launches0
+    timed = secs[args.warmup:] if len(secs) > args.warmup else secs
+    solves_timed = sum(newton[args.warmup:]) if len(secs) > args.warmup else sum(newton)
+    paper = PAPER_FIBER.get(args.fiber_n)
+    line = {"metric": METRIC, "value": solves_timed / sum(timed), "unit": "Newton-system solves/s (set-up + FGMRES)",
+            "n_gpus": 1, "steps": len(timed), "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {"workload": (f"flow past a clamped fiber (Sec. 5.3): channel (0,2)^2, {rec.N}x{rec.N} cells, "
+                                    f"inflow ramped to U=1 on the top wall, traction outflow with backflow "
+                                    f"term, Re=200, {rec.M} markers, dt=0.05h; {args.nsteps} steps from rest"),
+                       "smoother": "coloured multiplicative CAV 1+1, hierarchy rebuilt per Newton system",
+                       "precision": prec + " patch inverses", "fgmres_rtol": args.fiber_rtol,
+                       "newton": "stop at 1e-8 relative to the first Newton residual (or 1e-8 absolute)"},
+            "newton_per_step_mean": float(np.mean(newton)), "newton_per_step_max": int(max(newton)),
+            "fgmres_per_newton_mean": float(np.mean(its)), "fgmres_per_newton_max": int(max(its)),
+            "fgmres_not_converged": nonconv, "ms_per_newton_solve": 1e3 * sum(timed) / max(solves_timed, 1),
+            "paper": ({"fgmres_per_newton_mean": paper[0], "fgmres_per_newton_max": paper[1],
+                       "newton_per_step_mean": paper[2], "note": "averaged over the paper's whole run, tol 1e-9"}
+                      if paper else None),
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned(args, api, torch, rank, world):
     """Time series of a tethered elastic ring in a time-periodic shear forcing (periodic box,
     dt = 0.05 h, one linear solve per step, hierarchy rebuilt per step).  Steps 1..75% use the
@@ -459,7 +516,10 @@ def main():
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="membrane256",
-                    choices=["membrane256", "membrane512", "batch64", "learned", "beam512"])
+                    choices=["membrane256", "membrane512", "batch64", "learned", "beam512", "fiber"])
+    ap.add_argument("--fiber-n", type=int, default=32,
+                    help="--workload fiber: the paper's N (channel of 2N x 2N cells): 16, 32, 64, 128")
+    ap.add_argument("--fiber-rtol", type=float, default=1e-10, help="--workload fiber: FGMRES tolerance")
     ap.add_argument("--grid", type=int, default=64, help="grid for --workload learned")
     ap.add_argument("--nsteps", type=int, default=2000, help="time steps for --workload learned")
     ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
@@ -490,6 +550,8 @@ def main():
         return run_learned(args, api, torch, rank, world)
     if args.workload == "beam512":
         return run_beam512(args, api, torch, rank)
+    if args.workload == "fiber":
+        return run_fiber(args, api, torch, rank)
 
     rec = workload(rank, 512 if args.workload == "membrane512" else 256)
     n = 3 * rec.N * rec.N

@@ -227,8 +227,10 @@ typedef struct {
   int32_t max_n;         /* largest patch size                                              */
   int64_t sum_n;         /* sum of patch sizes                                              */
   int64_t sum_n2;        /* sum of squared patch sizes                                      */
-  int64_t enlarged_sum_n, enlarged_sum_n2;
-  int64_t inverse_bytes; /* bytes of stored enlarged-patch inverses (padded layout)         */
+  int64_t enlarged_sum_n, enlarged_sum_n2;  /* over the patches stored with their own inverse:
+                            the enlarged ones, and on a Vanka level with structure the Vanka
+                            patches whose unknowns have E_E rows                            */
+  int64_t inverse_bytes; /* bytes of the stored inverses (padded layout)                    */
   int64_t ee_nnz;        /* structural nonzeros of E_E on this level                        */
   int32_t ee_rows;       /* velocity rows of E_E with at least one nonzero                  */
   int32_t ee_window;     /* max per-axis index offset between a row and a column of E_E     */
@@ -404,15 +406,16 @@ ib_status ibnet_train_step(ibnet* net, const float* in, const float* target, int
 ib_status ibnet_pack_input(int32_t N, const double* const* hist_x, const double* const* hist_f,
                            const float* in_scale, float* out, cudaStream_t stream);
 /* target (3 x N x N) = (x_new - base) / out_scale per field (u, v, p), where base is x_prev,
- * or the linear extrapolation 2 x_prev - x_prev2 when x_prev2 is not NULL. */
+ * the linear extrapolation 2 x_prev - x_prev2 when x_prev2 is not NULL, or the quadratic
+ * extrapolation 3 x_prev - 3 x_prev2 + x_prev3 when x_prev3 is not NULL too (ABI 4). */
 ib_status ibnet_pack_target(int32_t N, const double* x_new, const double* x_prev,
-                            const double* x_prev2, const float* out_scale, float* out,
-                            cudaStream_t stream);
+                            const double* x_prev2, const double* x_prev3, const float* out_scale,
+                            float* out, cudaStream_t stream);
 /* x_out = base + out_scale * delta per field (base as above; delta NULL: base alone): the
  * predicted initial guess. */
 ib_status ibnet_apply_delta(int32_t N, const double* x_prev, const double* x_prev2,
-                            const float* delta, const float* out_scale, double* x_out,
-                            cudaStream_t stream);
+                            const double* x_prev3, const float* delta, const float* out_scale,
+                            double* x_out, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

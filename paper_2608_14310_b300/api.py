@@ -127,8 +127,8 @@ _sig = {
     "ibnet_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _P(C.c_float), _vp, _vp]),
     "ibnet_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_float, _P(C.c_float), _vp]),
     "ibnet_pack_input": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(C.c_float), _vp, _vp]),
-    "ibnet_pack_target": (C.c_int, [C.c_int32, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
-    "ibnet_apply_delta": (C.c_int, [C.c_int32, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
+    "ibnet_pack_target": (C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
+    "ibnet_apply_delta": (C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
     "fgmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, _P(fgmres_desc), _P(fgmres_info), _vp, _vp]),
     "fgmres_solve_batched": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(_vp), _P(_vp), _P(fgmres_desc),
                                        _P(fgmres_info), _vp]),
@@ -520,13 +520,13 @@ def ibnet_pack_input(N, hist_x, hist_f, in_scale, out, stream=None):
     _check(_lib.ibnet_pack_input(N, hx, hf, sc, _devf(out), _stream(stream)), "ibnet_pack_input")
 
 
-def ibnet_pack_target(N, x_new, x_prev, out_scale, out, x_prev2=None, stream=None):
+def ibnet_pack_target(N, x_new, x_prev, out_scale, out, x_prev2=None, x_prev3=None, stream=None):
     sc = (C.c_float * 3)(*[float(v) for v in out_scale])
-    _check(_lib.ibnet_pack_target(N, _dev(x_new), _dev(x_prev), _dev(x_prev2), sc, _devf(out), _stream(stream)),
-           "ibnet_pack_target")
+    _check(_lib.ibnet_pack_target(N, _dev(x_new), _dev(x_prev), _dev(x_prev2), _dev(x_prev3), sc, _devf(out),
+                                  _stream(stream)), "ibnet_pack_target")
 
 
-def ibnet_apply_delta(N, x_prev, delta, out_scale, x_out, x_prev2=None, stream=None):
+def ibnet_apply_delta(N, x_prev, delta, out_scale, x_out, x_prev2=None, x_prev3=None, stream=None):
     sc = (C.c_float * 3)(*[float(v) for v in out_scale])
-    _check(_lib.ibnet_apply_delta(N, _dev(x_prev), _dev(x_prev2), None if delta is None else _devf(delta), sc,
-                                  _dev(x_out), _stream(stream)), "ibnet_apply_delta")
+    _check(_lib.ibnet_apply_delta(N, _dev(x_prev), _dev(x_prev2), _dev(x_prev3), None if delta is None else _devf(delta),
+                                  sc, _dev(x_out), _stream(stream)), "ibnet_apply_delta")

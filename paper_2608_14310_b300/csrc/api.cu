@@ -331,7 +331,7 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
   } else {
     const int64_t nstd = lv.box ? 0 : NN - lv.n_big;  // n_std4 of them have four unknowns
     info->n_patches = (int32_t)(lv.box ? lv.n_big : NN);
-    info->n_enlarged = lv.n_big;
+    info->n_enlarged = lv.n_big - lv.n_big_small;
     info->max_n = lv.box ? lv.big_max_n : std::max(lv.big_max_n, nstd > lv.n_std4 ? 5 : 4);
     info->sum_n = lv.big_sum_n + 5 * nstd - lv.n_std4;
     info->sum_n2 = lv.big_sum_n2 + 25 * nstd - 9 * (int64_t)lv.n_std4;

@@ -138,13 +138,21 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
       for (int t = 0; t < len; ++t) hold[cur[ptr[t]]++] = c;
     }
   }
-  // first fit in visit order: enlarged patches in unit order, then standard ones
+  // first fit in visit order: enlarged patches (more than the five unknowns of V_ij) in unit
+  // order, then the others; a Vanka patch stored with its own inverse (its unknowns have E_E
+  // rows) is still visited with the standard ones
+  auto enlarged = [&](int c) {
+    if (box) return true;
+    if (!is_big(c)) return false;
+    const int q = pidx[c];
+    return off[q + 1] - off[q] > 5;
+  };
   std::vector<int> order;
   order.reserve(nunits);
   for (int c = 0; c < nunits; ++c)
-    if (is_big(c)) order.push_back(c);
+    if (enlarged(c)) order.push_back(c);
   for (int c = 0; c < nunits; ++c)
-    if (!is_big(c)) order.push_back(c);
+    if (!enlarged(c)) order.push_back(c);
   std::vector<int> colour(nunits, -1), dstamp(n, -1), cstamp;
   std::vector<int> reach;
   reach.reserve(8192);

@@ -215,27 +215,33 @@ __global__ void k_pack_input(PackPtrs P, int N, float* __restrict__ out) {
 }
 // target = (x_new - base) / scale per field (u, v, p), base = x_prev, or the linear
 // extrapolation 2 x_prev - x_prev2 when x_prev2 is given
+// The extrapolation base of a prediction from the last one, two or three steps: x_prev;
+// 2 x_prev - x_prev2 (linear); 3 x_prev - 3 x_prev2 + x_prev3 (quadratic).
+__device__ inline double extrapolation_base(const double* xp, const double* xp2, const double* xp3, size_t e) {
+  if (xp3) return xp3[e] + 3.0 * (xp[e] - xp2[e]);
+  if (xp2) return xp[e] + (xp[e] - xp2[e]);
+  return xp[e];
+}
+
 __global__ void k_pack_target(const double* __restrict__ xn, const double* __restrict__ xp,
-                              const double* __restrict__ xp2, float s0, float s1, float s2, int N,
-                              float* __restrict__ out) {
+                              const double* __restrict__ xp2, const double* __restrict__ xp3, float s0, float s1,
+                              float s2, int N, float* __restrict__ out) {
   const size_t NN = (size_t)N * N;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * NN; e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / NN);
     const double inv = 1.0 / (double)(k == 0 ? s0 : (k == 1 ? s1 : s2));
-    const double base = xp2 ? (xp[e] + (xp[e] - xp2[e])) : xp[e];
-    out[e] = (float)((xn[e] - base) * inv);
+    out[e] = (float)((xn[e] - extrapolation_base(xp, xp2, xp3, e)) * inv);
   }
 }
 // x_out = base + scale * delta per field, base as in k_pack_target
 __global__ void k_apply_delta(const double* __restrict__ xp, const double* __restrict__ xp2,
-                              const float* __restrict__ d, float s0, float s1, float s2, int N,
-                              double* __restrict__ xo) {
+                              const double* __restrict__ xp3, const float* __restrict__ d, float s0, float s1,
+                              float s2, int N, double* __restrict__ xo) {
   const size_t NN = (size_t)N * N;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * NN; e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / NN);
     const float s = (k == 0 ? s0 : (k == 1 ? s1 : s2));
-    const double base = xp2 ? (xp[e] + (xp[e] - xp2[e])) : xp[e];
-    xo[e] = base + (d ? (double)s * (double)d[e] : 0.0);
+    xo[e] = extrapolation_base(xp, xp2, xp3, e) + (d ? (double)s * (double)d[e] : 0.0);
   }
 }
 
@@ -523,12 +529,13 @@ ib_status ibnet_pack_input(int32_t N, const double* const* hist_x, const double*
 }
 
 ib_status ibnet_pack_target(int32_t N, const double* x_new, const double* x_prev, const double* x_prev2,
-                            const float* out_scale, float* out, cudaStream_t st) {
+                            const double* x_prev3, const float* out_scale, float* out, cudaStream_t st) {
   try {
     CAV_REQUIRE(N >= 1 && x_new && x_prev && out_scale && out, "ibnet_pack_target: NULL argument");
+    CAV_REQUIRE(!x_prev3 || x_prev2, "ibnet_pack_target: x_prev3 needs x_prev2");
     const size_t n = 3ull * N * N;
-    k_pack_target<<<grid_for(n), 256, 0, st>>>(x_new, x_prev, x_prev2, out_scale[0], out_scale[1], out_scale[2], N,
-                                               out);
+    k_pack_target<<<grid_for(n), 256, 0, st>>>(x_new, x_prev, x_prev2, x_prev3, out_scale[0], out_scale[1],
+                                               out_scale[2], N, out);
     CAV_CHECK_LAUNCH();
     return IB_OK;
   } catch (const Fail& f) {
@@ -536,13 +543,14 @@ ib_status ibnet_pack_target(int32_t N, const double* x_new, const double* x_prev
   }
 }
 
-ib_status ibnet_apply_delta(int32_t N, const double* x_prev, const double* x_prev2, const float* delta,
-                            const float* out_scale, double* x_out, cudaStream_t st) {
+ib_status ibnet_apply_delta(int32_t N, const double* x_prev, const double* x_prev2, const double* x_prev3,
+                            const float* delta, const float* out_scale, double* x_out, cudaStream_t st) {
   try {
     CAV_REQUIRE(N >= 1 && x_prev && out_scale && x_out, "ibnet_apply_delta: NULL argument");
+    CAV_REQUIRE(!x_prev3 || x_prev2, "ibnet_apply_delta: x_prev3 needs x_prev2");
     const size_t n = 3ull * N * N;
-    k_apply_delta<<<grid_for(n), 256, 0, st>>>(x_prev, x_prev2, delta, out_scale[0], out_scale[1], out_scale[2], N,
-                                               x_out);
+    k_apply_delta<<<grid_for(n), 256, 0, st>>>(x_prev, x_prev2, x_prev3, delta, out_scale[0], out_scale[1],
+                                               out_scale[2], N, x_out);
     CAV_CHECK_LAUNCH();
     return IB_OK;
   } catch (const Fail& f) {

@@ -96,6 +96,8 @@ struct Level {
   // patches (smoothing levels): one per cell; enlarged ones are stored explicitly
   int n_big = 0;                 // enlarged patches
   int n_std4 = 0;                // standard patches with four unknowns (the channel's inflow row)
+  int n_big_small = 0;           // stored patches with at most five unknowns (Vanka patches whose
+                                 // unknowns have E_E rows)
   int64_t big_sum_n = 0, big_sum_n2 = 0, inv_elems = 0;
   int big_max_n = 0;
   uint8_t* cell_big = nullptr;   // [N^2] 1 if the cell's patch is enlarged

@@ -208,8 +208,12 @@ __device__ inline int cell_velocities(int N, int i, int j, bool channel, int* U)
   return U[3] < 0 ? 3 : 4;
 }
 
-// Cell c = (i, j) keeps its standard Vanka patch iff no velocity of U_ij couples through
-// E_E to a velocity outside U_ij (Eq. cav_patch_set; E_E's pattern is symmetric).
+// CAV: cell c = (i, j) keeps its standard Vanka patch iff no velocity of U_ij couples through
+// E_E to a velocity outside U_ij (Eq. cav_patch_set; E_E's pattern is symmetric).  Vanka
+// (B(1,0)): every patch is V_ij, but one whose velocities have E_E rows has E_E entries in its
+// local matrix K_{E,p} = R_p K_E R_p^T, so it cannot share the E_E-free standard inverse: it
+// is flagged for an inverse of its own (its set stays V_ij).  Flagged cells are "big": their
+// patch is stored explicitly and factorised on its own.
 __global__ void k_cell_flags(int N, int cav, const int* __restrict__ row_of, const int64_t* __restrict__ rowptr,
                              const int* __restrict__ cols, uint8_t* big, int* flag, bool channel) {
   const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -219,7 +223,9 @@ __global__ void k_cell_flags(int N, int cav, const int* __restrict__ row_of, con
   int U4[4];
   const int nu = cell_velocities(N, i, j, channel, U4);
   int enl = 0;
-  if (cav) {
+  if (!cav) {
+    for (int t = 0; t < nu; ++t) enl |= (row_of[U4[t]] >= 0);
+  } else {
     for (int t = 0; t < nu && !enl; ++t) {
       const int r = row_of[U4[t]];
       if (r < 0) continue;
@@ -275,7 +281,7 @@ __device__ inline void mark_dof(uint8_t* dm, const Win& wx, const Win& wy, int N
 __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_cell,
                            const int* __restrict__ row_of, const int64_t* __restrict__ rowptr,
                            const int* __restrict__ cols, int* sizes, const int64_t* __restrict__ off,
-                           int* dofs, int pass, int* status, bool channel) {
+                           int* dofs, int pass, int* status, bool channel, bool cav) {
   extern __shared__ unsigned char smem[];
   const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * warps + warp;
@@ -295,7 +301,11 @@ __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_
   __syncwarp();
   int U4[4];
   const int nu = cell_velocities(N, i, j, channel, U4);
-  for (int t = 0; t < nu; ++t) {
+  if (!cav) {
+    // Vanka: the flagged cell's own patch V_ij
+    if (lane == 0) mark_cell(cm, cx, cy, N, i, j, status);
+  }
+  for (int t = 0; cav && t < nu; ++t) {
     if (lane == 0) mark_face_cells(cm, cx, cy, N, U4[t], status, channel);
     const int r = row_of[U4[t]];
     if (r < 0) continue;
@@ -802,7 +812,8 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     if (nbig > 0) {
       k_cav_sets<<<div_up(nbig, warps), warps * 32, smem, st>>>(N, W, (int)nbig, lv.big_cell, lv.ee.row_of,
                                                                 lv.ee.rowptr, lv.ee.cols, sizes, nullptr,
-                                                                nullptr, 0, H->status, lv.channel);
+                                                                nullptr, 0, H->status, lv.channel,
+                                                                H->desc.kind == CAV_PATCH_CAV);
       CAV_CHECK_LAUNCH();
     }
     exclusive_scan(sizes, lv.big_off, nbig, st, &scratch);
@@ -823,6 +834,8 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   }
   lv.big_sum_n = sum_n;
   lv.big_sum_n2 = sum_n2;
+  lv.n_big_small = 0;
+  for (int64_t p = 0; p < nbig; ++p) lv.n_big_small += (hsizes[p] <= 5 && !lv.box) ? 1 : 0;
   lv.big_max_n = max_n;
   lv.inv_elems = inv_elems = hinv_off[nbig];
   // the standard patches appended for factorisation: one (periodic) or three (channel) jobs
@@ -853,7 +866,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   } else if (nbig > 0) {
     k_cav_sets<<<div_up(nbig, cav_set_warps), cav_set_warps * 32, cav_set_smem, st>>>(
         N, lv.ee.W, (int)nbig, lv.big_cell, lv.ee.row_of, lv.ee.rowptr, lv.ee.cols, nullptr, lv.big_off,
-        lv.big_dofs, 1, H->status, lv.channel);
+        lv.big_dofs, 1, H->status, lv.channel, H->desc.kind == CAV_PATCH_CAV);
     CAV_CHECK_LAUNCH();
   }
   check_status(H, st, "patch sets");

@@ -174,3 +174,64 @@ class LearnedGuess:
         g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
         api.ibnet_apply_delta(N, ts.x_hist[i], None, self.out_scale, g, x_prev2=ts.x_hist[i - 1])
         return g
+
+
+class ChannelSeries:
+    """The flow-past-a-fiber time series in its channel (Sec. 5.3), keeping every step's
+    solution and spread fiber force on the device, with the same attributes as TimeSeries
+    (x_hist, f_hist) so that LearnedGuess trains and predicts on it unchanged.
+
+    Every step is solved by Newton's method (fiber_channel.FiberChannel) from a predicted
+    solution: Newton starts from it and every Newton system's FGMRES starts from the current
+    iterate; FGMRES stops at fgmres_rtol relative to the system's right-hand side and Newton at
+    newton_rtol relative to the step's base right-hand side, references that do not depend on
+    the prediction, so predictions are compared on equal terms."""
+
+    def __init__(self, rec, cav: dict | None = None, fgmres_rtol: float = 1e-10, newton_rtol: float = 1e-9):
+        import torch
+        from .fiber_channel import FiberChannel
+        self.torch = torch
+        self.fc = FiberChannel(rec, cav, newton_rtol=newton_rtol, fgmres_rtol=fgmres_rtol, newton_ref="b")
+        self.rec0 = rec
+        self.N = rec.N
+        self.n = 3 * rec.N * rec.N
+        self.t = 0.0
+        self.x_hist = [torch.zeros(self.n, dtype=torch.float64, device="cuda")]  # w^0: at rest
+        self.f_hist = []
+        self.records = []
+
+    def _spread_force(self):
+        torch = self.torch
+        N = self.N
+        sysm = api.ib_setup(self.fc.rec)
+        F = torch.empty(2 * self.rec0.M, dtype=torch.float64, device="cuda")
+        api.ib_force(sysm, F)
+        f = torch.empty(2 * N * N, dtype=torch.float64, device="cuda")
+        api.ib_spread(sysm, F, f)
+        sysm.close()
+        return f
+
+    def step(self, guesses=(("previous", None),)):
+        """One time step solved from every (label, fn) entry: fn(self) returns the predicted
+        solution once this step's spread force is stored (None: the previous step's solution).
+        Every entry starts from the same X^n; the first one's result advances the series.
+        Returns [(label, {newton, fgmres, fgmres_total, seconds, r0})]."""
+        self.f_hist.append(self._spread_force())
+        t_next = self.t + self.rec0.dt
+        rec_n = self.fc.rec
+        out, main = [], None
+        for label, fn in guesses:
+            self.fc.rec = rec_n
+            g = self.x_hist[-1] if fn is None else fn(self)
+            w, X, hist, infos, sec = self.fc.step(self.x_hist[-1], t_next, guess=g)
+            its = [i["iters"] for i in infos]
+            out.append((label, {"newton": len(hist) - 1, "fgmres": its, "fgmres_total": int(sum(its)),
+                                "seconds": sec, "r0": float(hist[0]),
+                                "converged": all(i["converged"] for i in infos)}))
+            if main is None:
+                main = (w, X)
+        self.fc.rec = replace(rec_n, X=main[1])
+        self.x_hist.append(main[0])
+        self.t = t_next
+        self.records.append(out)
+        return out

@@ -115,6 +115,15 @@ def test_pack_and_apply_kernels():
     api.ibnet_apply_delta(N, torch_dev(xs[2]), d, osc, g, x_prev2=torch_dev(xs[1]))
     want = 2 * xs[2] - xs[1] + np.repeat(osc, NN) * host(d).astype(np.float64)
     assert np.allclose(host(g), want, rtol=1e-12, atol=1e-14)
+    # quadratic extrapolation base 3 x2 - 3 x1 + x0 (a fourth step as the new value)
+    x3 = rng.standard_normal(3 * NN)
+    api.ibnet_pack_target(N, torch_dev(x3), torch_dev(xs[2]), osc, tg, x_prev2=torch_dev(xs[1]),
+                          x_prev3=torch_dev(xs[0]))
+    want = (x3 - (3 * xs[2] - 3 * xs[1] + xs[0])) / np.repeat(osc, NN)
+    assert np.allclose(host(tg), want.astype(np.float32), rtol=1e-6, atol=1e-6)
+    api.ibnet_apply_delta(N, torch_dev(xs[2]), d, osc, g, x_prev2=torch_dev(xs[1]), x_prev3=torch_dev(xs[0]))
+    want = 3 * xs[2] - 3 * xs[1] + xs[0] + np.repeat(osc, NN) * host(d).astype(np.float64)
+    assert np.allclose(host(g), want, rtol=1e-12, atol=1e-13)
 
 
 def test_training_lowers_loss():

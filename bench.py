@@ -450,6 +450,69 @@ def run_fiber(args, api, torch, rank):
     return 0
 
 
+def run_learned_channel(args, api, torch, rank):
+    """The learned initial guess on the fiber benchmark (Sec. 5.3, config 5): the series is
+    stepped with plain FP64 inverses and the previous step's solution as Newton's start for the
+    first 75 % of the steps, the CNN is trained on them, and every remaining step is solved five
+    ways from the same state: plain FP64 + previous solution, and FP32 inverses + previous
+    solution / linear extrapolation / quadratic extrapolation / the CNN's prediction (which
+    corrects the `--learned-base` extrapolation).  Newton stops at 1e-9 of the step's base
+    right-hand side and FGMRES at 1e-10 of each Newton system's, references that do not depend
+    on the guess.  value = time steps/s of FP32 + learned over the test steps."""
+    from paper_2608_14310_b300.learned_guess import ChannelSeries, LearnedGuess
+    if rank:
+        return 0
+    rec = W.fiber_channel(args.fiber_n)
+    cs = ChannelSeries(rec, cav=dict(kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, smoother="coloured",
+                                     precision="fp64"))
+    n_train = int(0.75 * args.nsteps)
+    t0 = time.perf_counter()
+    for _ in range(n_train):
+        cs.step()
+    t_series = time.perf_counter() - t0
+    lg = LearnedGuess(rec.N, hidden=32, n_hidden=3, base=args.learned_base)
+    lg.fit_scales(cs, n_train)
+    tinfo = lg.train(cs, n_train, iters=args.train_iters, batch=16, lr=1e-3)
+    variants = (("plain_fp64_previous", None, "fp64"),
+                ("fp32_previous", None, "fp32"),
+                ("fp32_extrapolated", lambda s: lg.extrapolate(s, 1), "fp32"),
+                ("fp32_quadratic", lambda s: lg.extrapolate(s, 2), "fp32"),
+                ("fp32_learned", lambda s: lg.predict(s), "fp32"))
+    res = {v[0]: [] for v in variants}
+    launches0 = api.ib_launch_count()
+    clocks = ClockSampler(0)
+    for _ in range(args.nsteps - n_train):
+        for lab, inf in cs.step(variants):
+            res[lab].append(inf)
+    clk = clocks.stop()
+    launches = api.ib_launch_count() - launches0
+    summ = {}
+    for lab, v in res.items():
+        ns = sum(r["newton"] for r in v)
+        summ[lab] = {"steps_per_s": len(v) / sum(r["seconds"] for r in v),
+                     "ms_per_step": 1e3 * float(np.mean([r["seconds"] for r in v])),
+                     "newton_per_step": ns / len(v),
+                     "fgmres_per_step": float(np.mean([r["fgmres_total"] for r in v])),
+                     "fgmres_per_newton": sum(r["fgmres_total"] for r in v) / max(ns, 1),
+                     "first_residual_geomean": float(np.exp(np.mean(np.log([max(r["r0"], 1e-300) for r in v])))),
+                     "all_converged": all(r["converged"] for r in v)}
+    line = {"metric": METRIC, "value": summ["fp32_learned"]["steps_per_s"], "unit": "time steps/s (Newton + CAV-FGMRES)",
+            "n_gpus": 1, "steps": args.nsteps - n_train, "warmup": n_train, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": (f"flow past a clamped fiber (Sec. 5.3) in its channel, {rec.N}x{rec.N} cells, "
+                                    f"Re=200, dt=0.05h, {args.nsteps} steps from rest; CNN (3x3 convolutions, 32 "
+                                    f"channels, 3 hidden layers) on the last three steps' u, v, p and spread force, "
+                                    f"correcting the {args.learned_base} extrapolation, trained on the first "
+                                    f"{n_train} steps ({args.train_iters} Adam iterations, batch 16), tested on the rest"),
+                       "smoother": "coloured multiplicative CAV 1+1, hierarchy rebuilt per Newton system",
+                       "tolerances": "Newton 1e-9 of ||b_step||, FGMRES 1e-10 of ||rhs||"},
+            "test_steps": summ, "series_s": t_series, "train_s": tinfo["train_s"],
+            "train_loss_first_last": [tinfo["losses"][0][1], tinfo["losses"][-1][1]],
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned(args, api, torch, rank, world):
     """Time series of a tethered elastic ring in a time-periodic shear forcing (periodic box,
     dt = 0.05 h, one linear solve per step, hierarchy rebuilt per step).  Steps 1..75% use the
@@ -516,7 +579,11 @@ def main():
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="membrane256",
-                    choices=["membrane256", "membrane512", "batch64", "learned", "beam512", "fiber"])
+                    choices=["membrane256", "membrane512", "batch64", "learned", "beam512", "fiber",
+                             "learned_channel"])
+    ap.add_argument("--learned-base", default="quadratic", choices=["linear", "quadratic"],
+                    help="--workload learned_channel: the extrapolation the CNN corrects")
+    ap.add_argument("--train-iters", type=int, default=1500, help="--workload learned_channel: Adam iterations")
     ap.add_argument("--fiber-n", type=int, default=32,
                     help="--workload fiber: the paper's N (channel of 2N x 2N cells): 16, 32, 64, 128")
     ap.add_argument("--fiber-rtol", type=float, default=1e-10, help="--workload fiber: FGMRES tolerance")
@@ -552,6 +619,8 @@ def main():
         return run_beam512(args, api, torch, rank)
     if args.workload == "fiber":
         return run_fiber(args, api, torch, rank)
+    if args.workload == "learned_channel":
+        return run_learned_channel(args, api, torch, rank)
 
     rec = workload(rank, 512 if args.workload == "membrane512" else 256)
     n = 3 * rec.N * rec.N

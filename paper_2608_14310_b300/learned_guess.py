@@ -95,13 +95,23 @@ class TimeSeries:
 class LearnedGuess:
     """The CNN and its normalisation, trained on a TimeSeries' stored steps."""
 
-    def __init__(self, N, hidden=32, n_hidden=3, seed=7):
+    def __init__(self, N, hidden=32, n_hidden=3, seed=7, base: str = "linear"):
+        """base: the extrapolation the network corrects, "linear" (2 x^n - x^{n-1}) or
+        "quadratic" (3 x^n - 3 x^{n-1} + x^{n-2})."""
         import torch
+        assert base in ("linear", "quadratic")
         self.torch = torch
         self.N = N
+        self.base = base
         self.net = api.IBNet(15, hidden, n_hidden, 3, seed)
         self.in_scale = None
         self.out_scale = None
+
+    def _hist(self, ts, i):
+        # x_prev2 and x_prev3 of the base extrapolation from step i
+        if self.base == "quadratic":
+            return dict(x_prev2=ts.x_hist[i - 1], x_prev3=ts.x_hist[i - 2])
+        return dict(x_prev2=ts.x_hist[i - 1])
 
     def fit_scales(self, ts: TimeSeries, upto: int):
         """Per-channel RMS of the training range (host statistics of a few sampled steps;
@@ -112,7 +122,11 @@ class LearnedGuess:
         xs = np.stack([ts.x_hist[i].cpu().numpy() for i in idx])
         fs = np.stack([ts.f_hist[i].cpu().numpy() for i in idx])
         dx = np.stack([(ts.x_hist[i + 1] - ts.x_hist[i]).cpu().numpy() for i in idx])
-        d2x = np.stack([(ts.x_hist[i + 1] - 2 * ts.x_hist[i] + ts.x_hist[i - 1]).cpu().numpy() for i in idx])
+        if self.base == "quadratic":
+            d2x = np.stack([(ts.x_hist[i + 1] - 3 * ts.x_hist[i] + 3 * ts.x_hist[i - 1] - ts.x_hist[i - 2]).cpu().numpy()
+                            for i in idx])
+        else:
+            d2x = np.stack([(ts.x_hist[i + 1] - 2 * ts.x_hist[i] + ts.x_hist[i - 1]).cpu().numpy() for i in idx])
         rms = lambda a: float(np.sqrt(np.mean(a * a))) or 1.0  # noqa: E731
         dfs = np.stack([(ts.f_hist[i] - ts.f_hist[i - 1]).cpu().numpy() for i in idx])
         fields_x = [rms(xs[:, k * NN:(k + 1) * NN]) for k in range(3)]
@@ -121,7 +135,7 @@ class LearnedGuess:
         incr_f = [rms(dfs[:, k * NN:(k + 1) * NN]) for k in range(2)]
         # channel groups: increments (two steps), then the current state
         self.in_scale = (incr_x + incr_f) * 2 + fields_x + fields_f
-        # the network predicts the correction to the linear extrapolation 2 x^n - x^{n-1}
+        # the network predicts the correction to the base extrapolation
         self.out_scale = [rms(d2x[:, k * NN:(k + 1) * NN]) for k in range(3)]
 
     def _pack(self, ts, i, out):
@@ -144,7 +158,7 @@ class LearnedGuess:
             for s, i in enumerate(pick):
                 self._pack(ts, int(i), xin[s * 15 * NN:(s + 1) * 15 * NN])
                 api.ibnet_pack_target(N, ts.x_hist[int(i) + 1], ts.x_hist[int(i)], self.out_scale,
-                                      tgt[s * 3 * NN:(s + 1) * 3 * NN], x_prev2=ts.x_hist[int(i) - 1])
+                                      tgt[s * 3 * NN:(s + 1) * 3 * NN], **self._hist(ts, int(i)))
             step_lr = lr * (0.5 * (1 + math.cos(math.pi * it / iters)) * 0.9 + 0.1)
             want = (it % 50 == 0) or it == iters - 1
             loss = self.net.train_step(xin, tgt, batch, N, step_lr, want_loss=want)
@@ -163,16 +177,18 @@ class LearnedGuess:
         d = torch.empty(3 * N * N, dtype=torch.float32, device="cuda")
         self.net.forward(xin, d, 1, N)
         g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
-        api.ibnet_apply_delta(N, ts.x_hist[i], d, self.out_scale, g, x_prev2=ts.x_hist[i - 1])
+        api.ibnet_apply_delta(N, ts.x_hist[i], d, self.out_scale, g, **self._hist(ts, i))
         return g
 
-    def extrapolate(self, ts: TimeSeries):
-        """The baseline without the network: 2 x^n - x^{n-1}."""
+    def extrapolate(self, ts: TimeSeries, order: int = 1):
+        """The baselines without the network: 2 x^n - x^{n-1} (order 1) or
+        3 x^n - 3 x^{n-1} + x^{n-2} (order 2)."""
         torch = self.torch
         N = self.N
         i = len(ts.x_hist) - 1
         g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
-        api.ibnet_apply_delta(N, ts.x_hist[i], None, self.out_scale, g, x_prev2=ts.x_hist[i - 1])
+        extra = dict(x_prev2=ts.x_hist[i - 1], x_prev3=ts.x_hist[i - 2] if order == 2 else None)
+        api.ibnet_apply_delta(N, ts.x_hist[i], None, self.out_scale, g, **extra)
         return g
 
 
@@ -212,15 +228,19 @@ class ChannelSeries:
         return f
 
     def step(self, guesses=(("previous", None),)):
-        """One time step solved from every (label, fn) entry: fn(self) returns the predicted
-        solution once this step's spread force is stored (None: the previous step's solution).
-        Every entry starts from the same X^n; the first one's result advances the series.
-        Returns [(label, {newton, fgmres, fgmres_total, seconds, r0})]."""
+        """One time step solved from every (label, fn[, precision]) entry: fn(self) returns the
+        predicted solution once this step's spread force is stored (None: the previous step's
+        solution); precision (default: the series') of the stored patch inverses.  Every entry
+        starts from the same X^n; the first one's result advances the series.  Returns
+        [(label, {newton, fgmres, fgmres_total, seconds, r0, converged})]."""
         self.f_hist.append(self._spread_force())
         t_next = self.t + self.rec0.dt
         rec_n = self.fc.rec
+        prec0 = self.fc.cav.get("precision", "fp64")
         out, main = [], None
-        for label, fn in guesses:
+        for entry in guesses:
+            label, fn = entry[0], entry[1]
+            self.fc.cav["precision"] = entry[2] if len(entry) > 2 else prec0
             self.fc.rec = rec_n
             g = self.x_hist[-1] if fn is None else fn(self)
             w, X, hist, infos, sec = self.fc.step(self.x_hist[-1], t_next, guess=g)
@@ -230,6 +250,7 @@ class ChannelSeries:
                                 "converged": all(i["converged"] for i in infos)}))
             if main is None:
                 main = (w, X)
+        self.fc.cav["precision"] = prec0
         self.fc.rec = replace(rec_n, X=main[1])
         self.x_hist.append(main[0])
         self.t = t_next

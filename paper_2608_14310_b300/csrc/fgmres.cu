@@ -60,6 +60,8 @@ __device__ inline double warp_sum8_transposed(double* v) {
 __global__ void __launch_bounds__(FG_THREADS)
 k_multi_dot(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ w,
             double* __restrict__ partial) {
+  pdl_wait();  // programmatic launch: the kernel ahead (which writes w or V) has finished
+  pdl_trigger();
   __shared__ double sm[DOT_GROUP][FG_THREADS / 32];
   const int64_t base = (int64_t)blockIdx.x * DOT_CHUNK + threadIdx.x;
   double wr[DOT_PER_THREAD];
@@ -107,6 +109,8 @@ k_multi_dot(const double* __restrict__ V, int64_t n, int kcount, const double* _
 
 // out[i] = sum_b partial[i * nb + b] (fixed order); add_to (nullable) += out
 __global__ void k_finalize(const double* __restrict__ partial, int nb, double* out, double* add_to) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sm[FG_THREADS / 32];
   const int i = blockIdx.x;
   double s = 0.0;
@@ -125,6 +129,8 @@ template <int SIGN>
 __global__ void __launch_bounds__(FG_THREADS)
 k_combine(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ c,
           double* __restrict__ w, double* __restrict__ sq_partial) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sm[FG_THREADS / 32];
   const int64_t base = (int64_t)blockIdx.x * CMB_CHUNK + threadIdx.x;
   double acc[CMB_PER_THREAD];
@@ -168,6 +174,8 @@ k_combine(const double* __restrict__ V, int64_t n, int kcount, const double* __r
 // v = w * scale[0]
 __global__ void k_scale(const double* __restrict__ w, int64_t n, const double* __restrict__ scale,
                         double* __restrict__ v) {
+  pdl_wait();
+  pdl_trigger();
   const double s = scale[0];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     v[e] = w[e] * s;
@@ -203,6 +211,8 @@ __global__ void k_init_beta(double* S, FgLayout L) {
 // memory first (all threads), so the chain runs on shared-memory latency, not L2 latency.
 constexpr int GIVENS_SMEM_MAX = 1024;
 __global__ void k_givens(double* S, FgLayout L, int k) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[3 * GIVENS_SMEM_MAX];
   double* Hg = S + L.H + (int64_t)k * (L.maxit + 1);
   double* csg = S + L.cs;
@@ -392,22 +402,22 @@ static void fg_issue(FgState& s, int k) {
   double* w = H->V + (int64_t)(k + 1) * n;
   vcycle(H, vk, zk, s.st);
   launch_apply(s.op, zk, nullptr, w, 1, s.st);
-  // the second pass's update also yields the chunk sums of ||w||^2 (after the dot partials)
+  // the second pass's update also yields the chunk sums of ||w||^2 (after the dot partials);
+  // every kernel below follows another of these kernels: programmatic launches
   double* sq_partial = H->red_partial + (int64_t)(maxit + 1) * s.nbmax;
+  const double* Vc = H->V;
   for (int pass = 0; pass < 2; ++pass) {
-    k_multi_dot<<<dim3(s.nb, div_up(k + 1, DOT_GROUP)), FG_THREADS, 0, s.st>>>(H->V, n, k + 1, w, H->red_partial);
-    CAV_CHECK_LAUNCH();
-    k_finalize<<<k + 1, FG_THREADS, 0, s.st>>>(H->red_partial, s.nb, S + s.L.h, S + s.L.H + (int64_t)k * (maxit + 1));
-    CAV_CHECK_LAUNCH();
-    k_combine<-1><<<s.cb, FG_THREADS, 0, s.st>>>(H->V, n, k + 1, S + s.L.h, w, pass == 1 ? sq_partial : nullptr);
-    CAV_CHECK_LAUNCH();
+    launch_k(k_multi_dot, dim3(s.nb, div_up(k + 1, DOT_GROUP)), dim3(FG_THREADS), 0, s.st, true, Vc, n, k + 1,
+             (const double*)w, H->red_partial);
+    launch_k(k_finalize, dim3(k + 1), dim3(FG_THREADS), 0, s.st, true, (const double*)H->red_partial, s.nb,
+             S + s.L.h, S + s.L.H + (int64_t)k * (maxit + 1));
+    launch_k(k_combine<-1>, dim3(s.cb), dim3(FG_THREADS), 0, s.st, true, Vc, n, k + 1, (const double*)(S + s.L.h),
+             w, pass == 1 ? sq_partial : nullptr);
   }
-  k_finalize<<<1, FG_THREADS, 0, s.st>>>(sq_partial, s.cb, misc + 2, nullptr);
-  CAV_CHECK_LAUNCH();
-  k_givens<<<1, 128, 0, s.st>>>(S, s.L, k);
-  CAV_CHECK_LAUNCH();
-  k_scale<<<s.vb, FG_THREADS, 0, s.st>>>(w, n, misc + 5, w);
-  CAV_CHECK_LAUNCH();
+  launch_k(k_finalize, dim3(1), dim3(FG_THREADS), 0, s.st, true, (const double*)sq_partial, s.cb, misc + 2,
+           (double*)nullptr);
+  launch_k(k_givens, dim3(1), dim3(128), 0, s.st, true, S, s.L, k);
+  launch_k(k_scale, dim3(s.vb), dim3(FG_THREADS), 0, s.st, true, (const double*)w, n, (const double*)(misc + 5), w);
   CAV_CHECK_CUDA(cudaMemcpyAsync(H->host_b + 8 + (k & 1), misc + 4, sizeof(double), cudaMemcpyDeviceToHost, s.st));
   CAV_CHECK_CUDA(cudaEventRecord(H->fg_ev[k & 1], s.st));
   s.prof_mark[k & 1] = H->prof_pushed;

@@ -232,6 +232,28 @@ namespace cav {
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Launch kernel k on st.  pdl: as a programmatic dependent launch, so the kernel's blocks may
+// be scheduled before the kernel ahead of it on st has finished (the launch latency hides under
+// that kernel).  The kernel must call pdl_wait() before touching memory an earlier kernel reads
+// or writes; pdl is only set when the operation ahead of the launch on st is one of this
+// library's kernels.
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
+  CAV_CHECK_LAUNCH();
+}
+
 inline int round8(int n) { return (n + 7) & ~7; }
 
 // ib_system.cu
@@ -251,11 +273,11 @@ struct LevelOps {
   const EECsr* ee;
   bool channel = false;
 };
-// mode 0: out = b - K w  (b may be null = 0);  mode 1: out = K w
+// mode 0: out = b - K w  (b may be null = 0);  mode 1: out = K w.  pdl: see launch_k.
 void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
-                  cudaStream_t st);
-void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st);
-void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st);
+                  cudaStream_t st, bool pdl = false);
+void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st, bool pdl = false);
+void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st, bool pdl = false);
 
 // setup.cu
 void build_levels(cav_hierarchy* H, cudaStream_t st);
@@ -273,7 +295,8 @@ void pressure_mean_remove(int N, double* partial, double* p, cudaStream_t st);
 void launch_remove_mean(int N, int n_partial, const double* partial, double* p, cudaStream_t st);
 void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
                  cudaStream_t st);
-void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
+void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st, bool pdl = false);
+bool prof_records(const cav_hierarchy* H, int level);
 void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_collect(cav_hierarchy* H, long long upto = -1);

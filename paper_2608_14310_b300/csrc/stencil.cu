@@ -19,6 +19,8 @@ k_residual(int N, double h, double rho_dt, double mu, double dt, const double* _
            const int* __restrict__ row_of, int n_rows, const int* __restrict__ rows,
            const int64_t* __restrict__ rowptr, const int* __restrict__ cols, const double* __restrict__ vals,
            bool channel) {
+  pdl_wait();  // programmatic launch: the kernel ahead (which writes w or b) has finished
+  pdl_trigger();
   const int NN = N * N;
   if ((int)blockIdx.x < nb_cells) {
     const int i = (blockIdx.x % gx) * RES_BX + (threadIdx.x % RES_BX);
@@ -53,20 +55,21 @@ k_residual(int N, double h, double rho_dt, double mu, double dt, const double* _
 }
 
 void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool pdl) {
   const int gx = div_up(op.N, RES_BX), gy = div_up(op.N, RES_BY);
   const int nb_cells = gx * gy;
   const bool has_ee = op.ee && op.ee->n_rows > 0;
   const int nb_rows = has_ee ? div_up(op.ee->n_rows, RES_WARPS * ROWS_PER_WARP) : 0;
-  k_residual<<<nb_cells + nb_rows, RES_BX * RES_BY, 0, st>>>(
-      op.N, op.h, op.rho_dt, op.mu, op.dt, w, b, out, mode, nb_cells, gx, has_ee ? op.ee->row_of : nullptr,
-      has_ee ? op.ee->n_rows : 0, has_ee ? op.ee->rows : nullptr, has_ee ? op.ee->rowptr : nullptr,
-      has_ee ? op.ee->cols : nullptr, has_ee ? op.ee->vals : nullptr, op.channel);
-  CAV_CHECK_LAUNCH();
+  launch_k(k_residual, dim3(nb_cells + nb_rows), dim3(RES_BX * RES_BY), 0, st, pdl, op.N, op.h, op.rho_dt, op.mu,
+           op.dt, w, b, out, mode, nb_cells, gx, has_ee ? op.ee->row_of : nullptr, has_ee ? op.ee->n_rows : 0,
+           has_ee ? op.ee->rows : nullptr, has_ee ? op.ee->rowptr : nullptr, has_ee ? op.ee->cols : nullptr,
+           has_ee ? op.ee->vals : nullptr, op.channel);
 }
 
 // Restriction (Sec. 4), one thread per coarse cell (I, J).
 __global__ void k_restrict(int Nc, const double* __restrict__ rf, double* __restrict__ bc, bool channel) {
+  pdl_wait();
+  pdl_trigger();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= Nc || J >= Nc) return;
@@ -75,22 +78,21 @@ __global__ void k_restrict(int Nc, const double* __restrict__ rf, double* __rest
 
 // w_f += P x_c (Sec. 4), one thread per fine cell (i, j).
 __global__ void k_prolong_add(int Nc, const double* __restrict__ xc, double* __restrict__ wf, bool channel) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= 2 * Nc || j >= 2 * Nc) return;
   prolong_cell(Nc, xc, wf, i, j, channel);
 }
 
-void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st) {
-  dim3 blk(32, 8), grd(div_up(Nc, 32), div_up(Nc, 8));
-  k_restrict<<<grd, blk, 0, st>>>(Nc, r_f, b_c, channel);
-  CAV_CHECK_LAUNCH();
+void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st, bool pdl) {
+  launch_k(k_restrict, dim3(div_up(Nc, 32), div_up(Nc, 8)), dim3(32, 8), 0, st, pdl, Nc, r_f, b_c, channel);
 }
 
-void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st) {
-  dim3 blk(32, 8), grd(div_up(2 * Nc, 32), div_up(2 * Nc, 8));
-  k_prolong_add<<<grd, blk, 0, st>>>(Nc, x_c, w_f, channel);
-  CAV_CHECK_LAUNCH();
+void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st, bool pdl) {
+  launch_k(k_prolong_add, dim3(div_up(2 * Nc, 32), div_up(2 * Nc, 8)), dim3(32, 8), 0, st, pdl, Nc, x_c, w_f,
+           channel);
 }
 
 }  // namespace cav

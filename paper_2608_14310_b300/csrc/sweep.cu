@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(THREADS)
 k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, const int* __restrict__ dofs,
               const int64_t* __restrict__ inv_off, const T* __restrict__ inv, const double* __restrict__ s_r,
               const double* __restrict__ s_c, const double* __restrict__ r, double* __restrict__ delta) {
+  pdl_wait();
+  pdl_trigger();
   typedef VecLoad<T> VL;
   typedef typename VL::acc_t acc_t;
   constexpr int V = VL::V;
@@ -68,6 +70,7 @@ constexpr int TMA_CONSUMER_WARPS = 4;
 constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 2);  // producer, gatherer, consumers
 constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
 constexpr int Y_SLOTS = 2;
+constexpr int TMA_PREFETCH = 64 * 1024; // L2 prefetch of the first patch beyond the ring (bytes)
 
 template <typename T>
 __host__ __device__ constexpr int tma_max_rows() {
@@ -135,9 +138,26 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     mbar_fence_init();
   }
   __syncthreads();
+  // Programmatic launch: the residual kernel ahead may still be running.  Only the gatherer
+  // reads what it writes (r), so only the gatherer waits for it; the producer streams the
+  // inverses (never written during a sweep) from the start, and the consumers write delta only
+  // after the gatherer's first handoff, when every earlier kernel (the previous sweep's
+  // scatter, which reads delta) has finished.
+  pdl_trigger();
 
   if (warp == 0) {
     if (lane == 0) {
+      // the first patch's columns beyond the ring: an L2 prefetch while the residual is computed
+      if ((int)blockIdx.x < n_big) {
+        const int p = order[zigzag(blockIdx.x, gridDim.x, n_big)];
+        const int n = (int)(off[p + 1] - off[p]);
+        const size_t bytes = (size_t)n * (size_t)(((n + 7) & ~7) * sizeof(T));
+        const size_t ring = (size_t)TMA_STAGES * TMA_CHUNK;
+        if (bytes > ring) {
+          const size_t extra = min(bytes - ring, (size_t)TMA_PREFETCH);
+          bulk_prefetch_l2(reinterpret_cast<const unsigned char*>(inv + inv_off[p]) + ring, (uint32_t)(extra & ~(size_t)15));
+        }
+      }
       int stage = 0;
       uint32_t phase = 0;
       uint32_t used = 0, last_par = 0;  // per stage: a copy was issued; parity of its last phase
@@ -173,6 +193,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
   }
 
   if (warp == 1) {
+    pdl_wait();
     int t = 0;
     for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
       const int slot = t & 1;
@@ -271,6 +292,8 @@ k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __res
          int n_touched, const int* __restrict__ touched, const uint8_t* __restrict__ cell_big,
          const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
          double* __restrict__ w, int w_is_zero, double* __restrict__ partial, bool channel) {
+  pdl_wait();  // programmatic launch: the patch apply (delta) and residual (r) have finished
+  pdl_trigger();
   __shared__ double sm[8];
   const int NN = N * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -352,6 +375,8 @@ k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __res
 
 // 4. p -= mean(p): every block reduces the partials in the same order, then subtracts.
 __global__ void k_remove_mean(int N, int n_partial, const double* __restrict__ partial, double* __restrict__ p) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sm[8];
   double t = 0.0;
   for (int q = threadIdx.x; q < n_partial; q += blockDim.x) t += partial[q];
@@ -362,14 +387,15 @@ __global__ void k_remove_mean(int N, int n_partial, const double* __restrict__ p
 
 void launch_remove_mean(int N, int n_partial, const double* partial, double* p, cudaStream_t st) {
   const int nblk = div_up(N * N, 256) < 296 ? div_up(N * N, 256) : 296;
-  k_remove_mean<<<nblk, 256, 0, st>>>(N, n_partial, partial, p);
-  CAV_CHECK_LAUNCH();
+  launch_k(k_remove_mean, dim3(nblk), dim3(256), 0, st, false, N, n_partial, partial, p);
 }
 
 // Coarsest level: z = (dense inverse) [r; 0], one warp per row, row-major with leading
 // dimension ld (n + 1 for the bordered periodic system, n on the channel).
 __global__ void k_coarse_apply(int n, int ld, const double* __restrict__ inv, const double* __restrict__ r,
                                double* __restrict__ z) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -392,6 +418,12 @@ static LevelOps ops_of(const Level& lv) {
   o.ee = &lv.ee;
   o.channel = lv.channel;
   return o;
+}
+
+// Whether prof_begin / prof_end record events (event-record nodes in a captured V-cycle).
+bool prof_records(const cav_hierarchy* H, int level) {
+  if (level != 0) return false;
+  return H->capturing || (H->prof_on && (size_t)(2 * H->prof_used + 1) < H->prof_ev.size());
 }
 
 void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st) {
@@ -481,15 +513,15 @@ static const ApplyVariant kVariants[NUM_APPLY_VARIANTS] = {
 
 template <typename T, int STAGES, int CHUNK>
 static void launch_tma(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r, double* delta,
-                       int ctas_per_sm, cudaStream_t st) {
+                       int ctas_per_sm, cudaStream_t st, bool pdl) {
   typedef typename VecLoad<T>::acc_t acc_t;
   const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
   const size_t smem = (size_t)STAGES * CHUNK + Y_SLOTS * ybytes + (2 * STAGES + 2 * Y_SLOTS) * sizeof(uint64_t) +
                       16;  // the CTA's abort flag
   allow_dynamic_smem(reinterpret_cast<const void*>(k_patch_apply_tma<T, STAGES, CHUNK>), 200 * 1024);
   const int grid = std::min(lv.n_big, ctas_per_sm * sm_count());
-  k_patch_apply_tma<T, STAGES, CHUNK><<<grid, TMA_THREADS, smem, st>>>(
-      lv.n_big, lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
+  launch_k(k_patch_apply_tma<T, STAGES, CHUNK>, dim3(grid), dim3(TMA_THREADS), smem, st, pdl, lv.n_big, lv.order,
+           lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
 }
 
 // Can variant v run this level?  (rows per consumer thread and one whole column per stage)
@@ -501,28 +533,28 @@ static bool variant_fits(const Level& lv, int v) {
 
 template <typename T>
 static void launch_patch_apply_variant(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r,
-                                       double* delta, int v, cudaStream_t st) {
+                                       double* delta, int v, cudaStream_t st, bool pdl) {
   typedef typename VecLoad<T>::acc_t acc_t;
   if (!variant_fits<T>(lv, v)) v = NUM_APPLY_VARIANTS - 1;
   switch (v) {
-    case 0: launch_tma<T, 4, 16384>(H, lv, inv, r, delta, 3, st); break;
-    case 1: launch_tma<T, 4, 16384>(H, lv, inv, r, delta, 2, st); break;
-    case 2: launch_tma<T, 8, 8192>(H, lv, inv, r, delta, 3, st); break;
-    case 3: launch_tma<T, 4, 8192>(H, lv, inv, r, delta, 4, st); break;
+    case 0: launch_tma<T, 4, 16384>(H, lv, inv, r, delta, 3, st, pdl); break;
+    case 1: launch_tma<T, 4, 16384>(H, lv, inv, r, delta, 2, st, pdl); break;
+    case 2: launch_tma<T, 8, 8192>(H, lv, inv, r, delta, 3, st, pdl); break;
+    case 3: launch_tma<T, 4, 8192>(H, lv, inv, r, delta, 4, st, pdl); break;
     default: {
       const size_t smem = sizeof(acc_t) * (size_t)lv.big_max_n;
-      k_patch_apply<T, 128><<<lv.n_big, 128, smem, st>>>(lv.order, lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r,
-                                                        lv.s_c, r, delta);
+      launch_k(k_patch_apply<T, 128>, dim3(lv.n_big), dim3(128), smem, st, pdl, lv.order, lv.big_off, lv.big_dofs,
+               lv.inv_off, inv, lv.s_r, lv.s_c, r, delta);
     }
   }
-  CAV_CHECK_LAUNCH();
 }
 
 static void launch_patch_apply_any(const cav_hierarchy* H, const Level& lv, const double* r, double* delta, int v,
-                                   cudaStream_t st) {
-  if (lv.precision == CAV_PREC_FP32) launch_patch_apply_variant<float>(H, lv, lv.inv32, r, delta, v, st);
-  else if (lv.precision == CAV_PREC_BF16) launch_patch_apply_variant<__nv_bfloat16>(H, lv, lv.inv16, r, delta, v, st);
-  else launch_patch_apply_variant<double>(H, lv, lv.inv64, r, delta, v, st);
+                                   cudaStream_t st, bool pdl = false) {
+  if (lv.precision == CAV_PREC_FP32) launch_patch_apply_variant<float>(H, lv, lv.inv32, r, delta, v, st, pdl);
+  else if (lv.precision == CAV_PREC_BF16)
+    launch_patch_apply_variant<__nv_bfloat16>(H, lv, lv.inv16, r, delta, v, st, pdl);
+  else launch_patch_apply_variant<double>(H, lv, lv.inv64, r, delta, v, st, pdl);
 }
 
 // Autotuner: time every variant on this level's own patches (two warm-up and five timed
@@ -554,19 +586,26 @@ void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st) {
 
 // The four steps of one sweep with explicit scratch (residual r_buf, packed corrections
 // delta_buf, partial sums partial_buf); shared by cav_sweep and cav_sweep_noalloc.
+// pdl_first: the operation ahead of the sweep's first kernel on st is one of this library's
+// kernels, so it may be a programmatic launch (the kernels after it are, except around the
+// finest level's profiling events, whose record nodes sit between the kernels).
 static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, double* r_buf,
                        double* delta_buf, double* partial_buf, bool profile, cudaStream_t st,
-                       bool remove_mean = true) {
+                       bool remove_mean = true, bool pdl_first = false) {
   const Level& lv = H->levels[l];
   const double* r = b;
+  const bool events = profile && prof_records(H, l);
+  bool pdl = pdl_first;
   if (!w_is_zero) {
-    launch_apply(ops_of(lv), w, b, r_buf, 0, st);
+    launch_apply(ops_of(lv), w, b, r_buf, 0, st, pdl);
     r = r_buf;
+    pdl = true;
   }
   if (lv.n_big > 0) {
-    if (profile) prof_begin(H, l, st);
-    launch_patch_apply_any(H, lv, r, delta_buf, lv.apply_variant, st);
-    if (profile) prof_end(H, l, st);
+    if (events) prof_begin(H, l, st);
+    launch_patch_apply_any(H, lv, r, delta_buf, lv.apply_variant, st, pdl && !events);
+    if (events) prof_end(H, l, st);
+    pdl = !events;
   }
   StdInv S;
   for (int k = 0; k < 3; ++k)
@@ -574,14 +613,13 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   const int gx = div_up(lv.N, 32), gy = div_up(lv.N, 8);
   const int nb_std = gx * gy;
   const int nb_touch = div_up(lv.n_touched, TOUCH_WARPS * TOUCH_PER_WARP);
-  k_update<<<nb_std + nb_touch, 256, 0, st>>>(lv.N, H->desc.alpha, S, nb_std, gx, lv.inc_off, lv.n_touched,
-                                              lv.touched, lv.cell_big, lv.inc_slot, delta_buf, r, w,
-                                              w_is_zero ? 1 : 0, partial_buf, lv.channel);
-  CAV_CHECK_LAUNCH();
+  launch_k(k_update, dim3(nb_std + nb_touch), dim3(256), 0, st, pdl, lv.N, H->desc.alpha, S, nb_std, gx, lv.inc_off,
+           lv.n_touched, lv.touched, lv.cell_big, lv.inc_slot, delta_buf, r, w, w_is_zero ? 1 : 0, partial_buf,
+           lv.channel);
   if (remove_mean && !lv.channel) {  // the channel's pressure is determined: no mean to remove
     const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
-    k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, partial_buf, w + 2 * lv.N * lv.N);
-    CAV_CHECK_LAUNCH();
+    launch_k(k_remove_mean, dim3(nblk), dim3(256), 0, st, true, lv.N, lv.n_partial, (const double*)partial_buf,
+             w + 2 * lv.N * lv.N);
   }
 }
 
@@ -604,45 +642,52 @@ void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool
 // V-cycle's output give the same iterate up to rounding.  The cycle removes it once, using
 // the partial sums the finest level's last sweep already produced.
 static void cycle_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool pdl_first) {
   const Level& lv = H->levels[l];
   if (lv.coloured) {
     coloured_sweep(H, l, b, w, w_is_zero, lv.partial, false, true, st);
     return;
   }
-  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st, false);
+  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st, false, pdl_first);
 }
 
-void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st) {
+void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st, bool pdl) {
   const Level& lv = H->levels.back();
   const int n = 3 * lv.N * lv.N;
-  k_coarse_apply<<<div_up(n, 8), 256, 0, st>>>(n, lv.coarse_m, lv.coarse_inv, r, z);
-  CAV_CHECK_LAUNCH();
+  launch_k(k_coarse_apply, dim3(div_up(n, 8)), dim3(256), 0, st, pdl, n, lv.coarse_m,
+           (const double*)lv.coarse_inv, r, z);
 }
 
+// One level of the V-cycle.  Every kernel after the first of the cycle follows another of its
+// kernels on the stream (the coloured sweep's zeroing memset is followed by its first class
+// step, launched without the attribute), so they are programmatic launches: each launch's
+// latency hides under the kernel ahead of it.
 static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double* x, cudaStream_t st) {
   const Level& lv = H->levels[l];
+  const bool pdl_in = l > 0;  // the finest level's first kernel is the cycle's first
   if (lv.coarsest) {
-    coarse_solve(H, b, x, st);
+    coarse_solve(H, b, x, st, pdl_in);
     return;
   }
   const int NN = lv.N * lv.N;
   const int nu_pre = lv.nu_pre, nu_post = lv.nu_post;
   if (nu_pre == 0) CAV_CHECK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * 3 * NN, st));
-  for (int s = 0; s < nu_pre; ++s) cycle_sweep(H, l, b, x, s == 0, st);
-  launch_apply(ops_of(lv), x, b, lv.r, 0, st);
+  for (int s = 0; s < nu_pre; ++s) cycle_sweep(H, l, b, x, s == 0, st, s > 0 || pdl_in);
+  // after a coloured sweep of the finest level an event-record node may precede the residual
+  const bool after_events = lv.coloured && prof_records(H, l);
+  launch_apply(ops_of(lv), x, b, lv.r, 0, st, (nu_pre > 0 || pdl_in) && !after_events);
   const Level& lc = H->levels[l + 1];
-  launch_restrict(lc.N, lv.r, lc.b, lv.channel, st);
+  launch_restrict(lc.N, lv.r, lc.b, lv.channel, st, true);
   vcycle_level(H, l + 1, lc.b, lc.x, st);
-  launch_prolong_add(lc.N, lc.x, x, lv.channel, st);
-  for (int s = 0; s < nu_post; ++s) cycle_sweep(H, l, b, x, false, st);
+  launch_prolong_add(lc.N, lc.x, x, lv.channel, st, true);
+  for (int s = 0; s < nu_post; ++s) cycle_sweep(H, l, b, x, false, st, true);
   if (l == 0 && !lv.channel) {
     if (nu_post > 0 && lv.coloured) {
       pressure_mean_remove(lv.N, lv.partial, x + 2 * NN, st);
     } else if (nu_post > 0) {
       const int nblk = div_up(NN, 256) < 296 ? div_up(NN, 256) : 296;
-      k_remove_mean<<<nblk, 256, 0, st>>>(lv.N, lv.n_partial, lv.partial, x + 2 * NN);
-      CAV_CHECK_LAUNCH();
+      launch_k(k_remove_mean, dim3(nblk), dim3(256), 0, st, true, lv.N, lv.n_partial, (const double*)lv.partial,
+               x + 2 * NN);
     } else {
       level_sweep(H, l, b, x, false, st);  // nu_post = 0: one more full sweep to fix the gauge
     }

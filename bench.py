@@ -420,6 +420,11 @@ def run_fiber(args, api, torch, rank):
     for s in range(args.nsteps):
         t += rec.dt
         w, X, hist, infos, sec = fc.step(w, t)
+        if args.trace and s % 50 == 0:
+            Xa = np.asarray(X)
+            print(f"step {s}: markers y in [{Xa[:, 1].min():.4f}, {Xa[:, 1].max():.4f}], x in "
+                  f"[{Xa[:, 0].min():.4f}, {Xa[:, 0].max():.4f}], Newton {len(hist) - 1}, FGMRES "
+                  f"{[i['iters'] for i in infos]}", file=sys.stderr, flush=True)
         newton.append(len(hist) - 1)
         its.extend(i["iters"] for i in infos)
         nonconv += sum(1 for i in infos if not i["converged"])
@@ -470,7 +475,7 @@ def run_learned_channel(args, api, torch, rank):
     for _ in range(n_train):
         cs.step()
     t_series = time.perf_counter() - t0
-    lg = LearnedGuess(rec.N, hidden=32, n_hidden=3, base=args.learned_base)
+    lg = LearnedGuess(rec.N, hidden=32, n_hidden=3, base=args.learned_base, history=args.learned_history)
     lg.fit_scales(cs, n_train)
     tinfo = lg.train(cs, n_train, iters=args.train_iters, batch=16, lr=1e-3)
     variants = (("plain_fp64_previous", None, "fp64"),
@@ -501,7 +506,7 @@ def run_learned_channel(args, api, torch, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": (f"flow past a clamped fiber (Sec. 5.3) in its channel, {rec.N}x{rec.N} cells, "
                                     f"Re=200, dt=0.05h, {args.nsteps} steps from rest; CNN (3x3 convolutions, 32 "
-                                    f"channels, 3 hidden layers) on the last three steps' u, v, p and spread force, "
+                                    f"channels, 3 hidden layers) on the last {args.learned_history} steps' u, v, p and spread force, "
                                     f"correcting the {args.learned_base} extrapolation, trained on the first "
                                     f"{n_train} steps ({args.train_iters} Adam iterations, batch 16), tested on the rest"),
                        "smoother": "coloured multiplicative CAV 1+1, hierarchy rebuilt per Newton system",
@@ -583,7 +588,10 @@ def main():
                              "learned_channel"])
     ap.add_argument("--learned-base", default="quadratic", choices=["linear", "quadratic"],
                     help="--workload learned_channel: the extrapolation the CNN corrects")
+    ap.add_argument("--trace", action="store_true", help="--workload fiber: print marker ranges every 50 steps")
     ap.add_argument("--train-iters", type=int, default=1500, help="--workload learned_channel: Adam iterations")
+    ap.add_argument("--learned-history", type=int, default=4, choices=[3, 4],
+                    help="--workload learned_channel: steps of history the CNN sees (4: as time differences)")
     ap.add_argument("--fiber-n", type=int, default=32,
                     help="--workload fiber: the paper's N (channel of 2N x 2N cells): 16, 32, 64, 128")
     ap.add_argument("--fiber-rtol", type=float, default=1e-10, help="--workload fiber: FGMRES tolerance")

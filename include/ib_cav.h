@@ -405,6 +405,12 @@ ib_status ibnet_train_step(ibnet* net, const float* in, const float* target, int
  * x_2 | f_2, each divided by in_scale[c]. */
 ib_status ibnet_pack_input(int32_t N, const double* const* hist_x, const double* const* hist_f,
                            const float* in_scale, float* out, cudaStream_t stream);
+/* in (5 K x N x N) from K <= 4 steps x_0 .. x_{K-1} (hist_x, device 3 N^2, oldest first) and
+ * spread forces f_0 .. f_{K-1} (hist_f, device 2 N^2) in difference form (ABI 4): channel
+ * groups holding the backward differences of order K - 1, ..., 1, 0 in time at the newest
+ * step of (u, v, p, f_u, f_v) (order 0: the newest fields), each divided by in_scale[c]. */
+ib_status ibnet_pack_history(int32_t N, int32_t K, const double* const* hist_x, const double* const* hist_f,
+                             const float* in_scale, float* out, cudaStream_t stream);
 /* target (3 x N x N) = (x_new - base) / out_scale per field (u, v, p), where base is x_prev,
  * the linear extrapolation 2 x_prev - x_prev2 when x_prev2 is not NULL, or the quadratic
  * extrapolation 3 x_prev - 3 x_prev2 + x_prev3 when x_prev3 is not NULL too (ABI 4). */

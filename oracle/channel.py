@@ -501,7 +501,13 @@ def fiber_step(ch: Channel, rec, w_n, t_next: float, solver: str = "direct", rto
     u^n, the convective term explicit at u^n.  Newton's method on (u, p) (oracle/newton.py's
     iteration) with each linear system solved directly ("direct") or by CAV-preconditioned
     FGMRES with the hierarchy rebuilt per Newton system ("cav", 1 + 1 sweeps of the given mode,
-    to fgmres_rtol, as the paper does).  Returns (w, X^{n+1}, residual history, FGMRES counts)."""
+    as the paper does).  The FGMRES solve of Newton system k starts from the iterate w_k and
+    stops at fgmres_rtol relative to its initial residual, which is the Newton residual at w_k:
+    an inexact Newton step whose forcing term is fgmres_rtol (reading: the paper's 1e-9 for
+    FGMRES and 1e-8 for Newton both relative to the current residual; a zero initial guess
+    with the tolerance relative to the whole right-hand side caps the Newton residual at
+    fgmres_rtol ||rhs||, and Newton stalls once the flow settles).  Returns (w, X^{n+1},
+    residual history, FGMRES counts)."""
     from dataclasses import replace
 
     import scipy.sparse.linalg as spla
@@ -547,7 +553,7 @@ def fiber_step(ch: Channel, rec, w_n, t_next: float, solver: str = "direct", rto
             w = spla.spsolve(K.tocsc(), rhs)
         else:
             levels = ib_hierarchy(ch, EE, pat)
-            w, info = fgmres.fgmres(lambda v: K @ v, rhs, lambda r: vcycle(levels, r, mode=mode),
+            w, info = fgmres.fgmres(lambda v: K @ v, rhs, lambda r: vcycle(levels, r, mode=mode), x0=w,
                                     rtol=fgmres_rtol, maxit=150, ref="r0")
             its.append(info["iters"])
         k += 1

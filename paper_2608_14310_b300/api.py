@@ -127,6 +127,7 @@ _sig = {
     "ibnet_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _P(C.c_float), _vp, _vp]),
     "ibnet_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_float, _P(C.c_float), _vp]),
     "ibnet_pack_input": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(C.c_float), _vp, _vp]),
+    "ibnet_pack_history": (C.c_int, [C.c_int32, C.c_int32, _P(_vp), _P(_vp), _P(C.c_float), _vp, _vp]),
     "ibnet_pack_target": (C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
     "ibnet_apply_delta": (C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _P(C.c_float), _vp, _vp]),
     "fgmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, _P(fgmres_desc), _P(fgmres_info), _vp, _vp]),
@@ -518,6 +519,14 @@ def ibnet_pack_input(N, hist_x, hist_f, in_scale, out, stream=None):
     hf = (_vp * 3)(*[_dev(t) for t in hist_f])
     sc = (C.c_float * 15)(*[float(v) for v in in_scale])
     _check(_lib.ibnet_pack_input(N, hx, hf, sc, _devf(out), _stream(stream)), "ibnet_pack_input")
+
+
+def ibnet_pack_history(N, hist_x, hist_f, in_scale, out, stream=None):
+    K = len(hist_x)
+    hx = (_vp * K)(*[_dev(t) for t in hist_x])
+    hf = (_vp * K)(*[_dev(t) for t in hist_f])
+    sc = (C.c_float * (5 * K))(*[float(v) for v in in_scale])
+    _check(_lib.ibnet_pack_history(N, K, hx, hf, sc, _devf(out), _stream(stream)), "ibnet_pack_history")
 
 
 def ibnet_pack_target(N, x_new, x_prev, out_scale, out, x_prev2=None, x_prev3=None, stream=None):

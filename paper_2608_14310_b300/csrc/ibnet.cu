@@ -213,6 +213,35 @@ __global__ void k_pack_input(PackPtrs P, int N, float* __restrict__ out) {
     out[e] = (float)(v * (double)P.inv_scale[ch]);
   }
 }
+// The history in difference form: K steps (oldest first), channel groups for the differences
+// of order d = K - 1, ..., 1, 0 in time at the newest step of (u, v, p, f_u, f_v), d = 0 being
+// the newest fields themselves; each channel divided by its scale.
+struct HistPtrs {
+  const double* x[4];
+  const double* f[4];
+  float inv_scale[20];
+  int K;
+};
+__global__ void k_pack_history(HistPtrs P, int N, float* __restrict__ out) {
+  const size_t NN = (size_t)N * N;
+  const int K = P.K;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < 5 * (size_t)K * NN;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int ch = (int)(e / NN);
+    const size_t pix = e % NN;
+    const int d = K - 1 - ch / 5, k = ch % 5;
+    const size_t off = (k < 3) ? k * NN + pix : (k - 3) * NN + pix;
+    const double* const* src = (k < 3) ? P.x : P.f;
+    // the d-th backward difference: sum_m (-1)^m binom(d, m) value at step K - 1 - m
+    double v = 0.0, c = 1.0;
+    for (int m = 0; m <= d; ++m) {
+      v += c * src[K - 1 - m][off];
+      c = -c * (double)(d - m) / (double)(m + 1);
+    }
+    out[e] = (float)(v * (double)P.inv_scale[ch]);
+  }
+}
+
 // target = (x_new - base) / scale per field (u, v, p), base = x_prev, or the linear
 // extrapolation 2 x_prev - x_prev2 when x_prev2 is given
 // The extrapolation base of a prediction from the last one, two or three steps: x_prev;
@@ -521,6 +550,31 @@ ib_status ibnet_pack_input(int32_t N, const double* const* hist_x, const double*
     }
     const size_t n = 15ull * N * N;
     k_pack_input<<<grid_for(n), 256, 0, st>>>(P, N, out);
+    CAV_CHECK_LAUNCH();
+    return IB_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+ib_status ibnet_pack_history(int32_t N, int32_t K, const double* const* hist_x, const double* const* hist_f,
+                             const float* in_scale, float* out, cudaStream_t st) {
+  try {
+    CAV_REQUIRE(N >= 1 && hist_x && hist_f && in_scale && out, "ibnet_pack_history: NULL argument");
+    CAV_REQUIRE(K >= 1 && K <= 4, "ibnet_pack_history: K must be in [1, 4]");
+    HistPtrs P{};
+    P.K = K;
+    for (int t = 0; t < K; ++t) {
+      CAV_REQUIRE(hist_x[t] && hist_f[t], "ibnet_pack_history: NULL history entry");
+      P.x[t] = hist_x[t];
+      P.f[t] = hist_f[t];
+    }
+    for (int c = 0; c < 5 * K; ++c) {
+      CAV_REQUIRE(in_scale[c] > 0.f, "ibnet_pack_history: scales must be positive");
+      P.inv_scale[c] = 1.f / in_scale[c];
+    }
+    const size_t n = 5ull * K * N * N;
+    k_pack_history<<<grid_for(n), 256, 0, st>>>(P, N, out);
     CAV_CHECK_LAUNCH();
     return IB_OK;
   } catch (const Fail& f) {

@@ -70,7 +70,6 @@ constexpr int TMA_CONSUMER_WARPS = 4;
 constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 2);  // producer, gatherer, consumers
 constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
 constexpr int Y_SLOTS = 2;
-constexpr int TMA_PREFETCH = 64 * 1024; // L2 prefetch of the first patch beyond the ring (bytes)
 
 template <typename T>
 __host__ __device__ constexpr int tma_max_rows() {
@@ -138,26 +137,17 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     mbar_fence_init();
   }
   __syncthreads();
-  // Programmatic launch: the residual kernel ahead may still be running.  Only the gatherer
-  // reads what it writes (r), so only the gatherer waits for it; the producer streams the
-  // inverses (never written during a sweep) from the start, and the consumers write delta only
-  // after the gatherer's first handoff, when every earlier kernel (the previous sweep's
-  // scatter, which reads delta) has finished.
+  // Under a programmatic launch the residual kernel ahead may still be running.  Only the
+  // gatherer reads what it writes (r), so only the gatherer waits for it; the producer streams
+  // the inverses (never written during a sweep) from the start, and the consumers write delta
+  // only after the gatherer's first handoff, when every earlier kernel (the previous sweep's
+  // scatter, which reads delta) has finished.  (Measured: launching the finest level's apply
+  // this way made its sweep slower, 86 -> 103 us, the early bulk traffic delaying the
+  // latency-bound residual kernel; the launchers do not request it.)
   pdl_trigger();
 
   if (warp == 0) {
     if (lane == 0) {
-      // the first patch's columns beyond the ring: an L2 prefetch while the residual is computed
-      if ((int)blockIdx.x < n_big) {
-        const int p = order[zigzag(blockIdx.x, gridDim.x, n_big)];
-        const int n = (int)(off[p + 1] - off[p]);
-        const size_t bytes = (size_t)n * (size_t)(((n + 7) & ~7) * sizeof(T));
-        const size_t ring = (size_t)TMA_STAGES * TMA_CHUNK;
-        if (bytes > ring) {
-          const size_t extra = min(bytes - ring, (size_t)TMA_PREFETCH);
-          bulk_prefetch_l2(reinterpret_cast<const unsigned char*>(inv + inv_off[p]) + ring, (uint32_t)(extra & ~(size_t)15));
-        }
-      }
       int stage = 0;
       uint32_t phase = 0;
       uint32_t used = 0, last_par = 0;  // per stage: a copy was issued; parity of its last phase
@@ -603,7 +593,7 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   }
   if (lv.n_big > 0) {
     if (events) prof_begin(H, l, st);
-    launch_patch_apply_any(H, lv, r, delta_buf, lv.apply_variant, st, pdl && !events);
+    launch_patch_apply_any(H, lv, r, delta_buf, lv.apply_variant, st, false);
     if (events) prof_end(H, l, st);
     pdl = !events;
   }

@@ -3,7 +3,9 @@
 Each semi-implicit step t^n -> t^{n+1} is solved by Newton's method on (u, p), with the
 fiber's force taken at the updated configuration X_k = X^n + dt J^n u_k (Eqs. im_disc_mom,
 im_disc_advec): every Newton system K_E(X_k) w = rhs_k is solved by CAV-preconditioned FGMRES
-with the hierarchy rebuilt for that system, as the paper does.  Host control flow only:
+with the hierarchy rebuilt for that system, as the paper does, starting from the iterate w_k
+(its initial residual rhs_k - K_E(X_k) w_k is the Newton residual at w_k), so the FGMRES
+tolerance is an inexact-Newton forcing term.  Host control flow only:
 every arithmetic step (right-hand sides, force, E_E assembly, set-up, solves, residual
 norms, marker advection) is a call of the C ABI in `api`.
 """
@@ -47,10 +49,9 @@ class FiberChannel:
     def step(self, w_n, t_next: float, guess=None):
         """One step from the device vector w_n (3 N^2, at t^n = t_next - dt) with the markers at
         self.rec.X = X^n.  guess (device, optional): a prediction of the step's solution, used as
-        Newton's starting iterate and then, as every later iterate, as the initial guess of
-        the next Newton system's FGMRES solve; without it Newton starts from w_n and every
-        FGMRES solve from zero (the paper's and the oracle's set-up).  Returns (w, X_next,
-        residual history, FGMRES infos, seconds) and moves self.rec to X^{n+1}."""
+        Newton's starting iterate (without it Newton starts from w_n, as in the paper and the
+        oracle).  Every Newton system's FGMRES solve starts from the current iterate.  Returns
+        (w, X_next, residual history, FGMRES infos, seconds) and moves self.rec to X^{n+1}."""
         import torch
         rec = self.rec
         dt = rec.dt
@@ -75,10 +76,11 @@ class FiberChannel:
             if k >= self.newton_maxit or hist[-1] <= tol:
                 break
             h = api.cav_setup(sysm, **self.cav)
-            x = w.clone() if guess is not None else torch.zeros_like(w_n)
-            # stopping reference ||rhs|| (equal to ||r_0|| for the paper's zero guess)
+            x = w.clone()
+            # newton_ref "r0": fgmres_rtol relative to the Newton residual at w_k (inexact Newton);
+            # "b": relative to ||rhs_k||, a reference independent of the starting iterate
             info = api.fgmres_solve(sysm, h, rhs, x, rtol=self.fgmres_rtol, maxit=self.fgmres_maxit,
-                                    rel_to=0, history=False)
+                                    rel_to=1 if self.newton_ref == "r0" else 0, history=False)
             h.close()
             its.append(info)
             w = x

@@ -95,15 +95,19 @@ class TimeSeries:
 class LearnedGuess:
     """The CNN and its normalisation, trained on a TimeSeries' stored steps."""
 
-    def __init__(self, N, hidden=32, n_hidden=3, seed=7, base: str = "linear"):
+    def __init__(self, N, hidden=32, n_hidden=3, seed=7, base: str = "linear", history: int = 3):
         """base: the extrapolation the network corrects, "linear" (2 x^n - x^{n-1}) or
-        "quadratic" (3 x^n - 3 x^{n-1} + x^{n-2})."""
+        "quadratic" (3 x^n - 3 x^{n-1} + x^{n-2}).  history: 3, the last three steps as two
+        increments and the newest fields (15 channels); or 4, the last four steps as their
+        backward differences in time of order 3, 2, 1, 0 at the newest step (20 channels)."""
         import torch
-        assert base in ("linear", "quadratic")
+        assert base in ("linear", "quadratic") and history in (3, 4)
         self.torch = torch
         self.N = N
         self.base = base
-        self.net = api.IBNet(15, hidden, n_hidden, 3, seed)
+        self.history = history
+        self.in_ch = 5 * history
+        self.net = api.IBNet(self.in_ch, hidden, n_hidden, 3, seed)
         self.in_scale = None
         self.out_scale = None
 
@@ -133,22 +137,43 @@ class LearnedGuess:
         fields_f = [rms(fs[:, k * NN:(k + 1) * NN]) for k in range(2)]
         incr_x = [rms(dx[:, k * NN:(k + 1) * NN]) for k in range(3)]
         incr_f = [rms(dfs[:, k * NN:(k + 1) * NN]) for k in range(2)]
-        # channel groups: increments (two steps), then the current state
-        self.in_scale = (incr_x + incr_f) * 2 + fields_x + fields_f
+        if self.history == 3:
+            # channel groups: increments (two steps), then the current state
+            self.in_scale = (incr_x + incr_f) * 2 + fields_x + fields_f
+        else:
+            # differences of order 3, 2, 1 in time at step i, then the current state
+            def diff(h, i, d):
+                c, v = 1.0, 0
+                for m in range(d + 1):
+                    v = v + c * h[i - m]
+                    c = -c * (d - m) / (m + 1)
+                return v.cpu().numpy()
+            sc = []
+            for d in (3, 2):
+                dxd = np.stack([diff(ts.x_hist, i, d) for i in idx if i >= 3])
+                dfd = np.stack([diff(ts.f_hist, i, d) for i in idx if i >= 3])
+                sc += [rms(dxd[:, k * NN:(k + 1) * NN]) for k in range(3)]
+                sc += [rms(dfd[:, k * NN:(k + 1) * NN]) for k in range(2)]
+            self.in_scale = sc + incr_x + incr_f + fields_x + fields_f
         # the network predicts the correction to the base extrapolation
         self.out_scale = [rms(d2x[:, k * NN:(k + 1) * NN]) for k in range(3)]
 
     def _pack(self, ts, i, out):
-        # inputs from steps i-2, i-1, i (solutions x^{i-2..i}, forces f^{i-2..i}); target x^{i+1} - x^i
-        api.ibnet_pack_input(self.N, [ts.x_hist[i - 2], ts.x_hist[i - 1], ts.x_hist[i]],
-                             [ts.f_hist[i - 2], ts.f_hist[i - 1], ts.f_hist[i]], self.in_scale, out)
+        # inputs from the last `history` steps up to i (solutions and spread forces)
+        if self.history == 3:
+            api.ibnet_pack_input(self.N, [ts.x_hist[i - 2], ts.x_hist[i - 1], ts.x_hist[i]],
+                                 [ts.f_hist[i - 2], ts.f_hist[i - 1], ts.f_hist[i]], self.in_scale, out)
+        else:
+            api.ibnet_pack_history(self.N, [ts.x_hist[i - q] for q in (3, 2, 1, 0)],
+                                   [ts.f_hist[i - q] for q in (3, 2, 1, 0)], self.in_scale, out)
 
     def train(self, ts: TimeSeries, upto: int, iters=1500, batch=16, lr=1e-3, seed=11):
         torch = self.torch
         N = self.N
         NN = N * N
-        samples = np.arange(2, upto)          # x^{i+1} must exist: i + 1 <= upto
-        xin = torch.empty(batch * 15 * NN, dtype=torch.float32, device="cuda")
+        samples = np.arange(self.history - 1, upto)   # x^{i+1} must exist: i + 1 <= upto
+        C = self.in_ch
+        xin = torch.empty(batch * C * NN, dtype=torch.float32, device="cuda")
         tgt = torch.empty(batch * 3 * NN, dtype=torch.float32, device="cuda")
         rng = np.random.default_rng(seed)
         losses = []
@@ -156,7 +181,7 @@ class LearnedGuess:
         for it in range(iters):
             pick = rng.choice(samples, batch, replace=len(samples) < batch)
             for s, i in enumerate(pick):
-                self._pack(ts, int(i), xin[s * 15 * NN:(s + 1) * 15 * NN])
+                self._pack(ts, int(i), xin[s * C * NN:(s + 1) * C * NN])
                 api.ibnet_pack_target(N, ts.x_hist[int(i) + 1], ts.x_hist[int(i)], self.out_scale,
                                       tgt[s * 3 * NN:(s + 1) * 3 * NN], **self._hist(ts, int(i)))
             step_lr = lr * (0.5 * (1 + math.cos(math.pi * it / iters)) * 0.9 + 0.1)
@@ -172,7 +197,7 @@ class LearnedGuess:
         torch = self.torch
         N = self.N
         i = len(ts.x_hist) - 1
-        xin = torch.empty(15 * N * N, dtype=torch.float32, device="cuda")
+        xin = torch.empty(self.in_ch * N * N, dtype=torch.float32, device="cuda")
         self._pack(ts, i, xin)
         d = torch.empty(3 * N * N, dtype=torch.float32, device="cuda")
         self.net.forward(xin, d, 1, N)

@@ -595,7 +595,9 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
     if (events) prof_begin(H, l, st);
     launch_patch_apply_any(H, lv, r, delta_buf, lv.apply_variant, st, false);
     if (events) prof_end(H, l, st);
-    pdl = !events;
+    // measured: a programmatic launch of the scatter after the persistent apply slows the
+    // sweep (its blocks sit resident beside the apply's), so it is a plain launch
+    pdl = false;
   }
   StdInv S;
   for (int k = 0; k < 3; ++k)

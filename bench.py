@@ -476,8 +476,9 @@ def run_learned_channel(args, api, torch, rank):
         cs.step()
     t_series = time.perf_counter() - t0
     lg = LearnedGuess(rec.N, hidden=32, n_hidden=3, base=args.learned_base, history=args.learned_history)
-    lg.fit_scales(cs, n_train)
-    tinfo = lg.train(cs, n_train, iters=args.train_iters, batch=16, lr=1e-3)
+    start = int(args.train_start * n_train)
+    lg.fit_scales(cs, n_train, start=start)
+    tinfo = lg.train(cs, n_train, iters=args.train_iters, batch=16, lr=1e-3, start=start)
     variants = (("plain_fp64_previous", None, "fp64"),
                 ("fp32_previous", None, "fp32"),
                 ("fp32_extrapolated", lambda s: lg.extrapolate(s, 1), "fp32"),
@@ -507,7 +508,8 @@ def run_learned_channel(args, api, torch, rank):
             "config": {"workload": (f"flow past a clamped fiber (Sec. 5.3) in its channel, {rec.N}x{rec.N} cells, "
                                     f"Re=200, dt=0.05h, {args.nsteps} steps from rest; CNN (3x3 convolutions, 32 "
                                     f"channels, 3 hidden layers) on the last {args.learned_history} steps' u, v, p and spread force, "
-                                    f"correcting the {args.learned_base} extrapolation, trained on the first "
+                                    f"correcting the {args.learned_base} extrapolation, trained on steps "
+                                    f"{int(args.train_start * n_train)}..{n_train} of the first "
                                     f"{n_train} steps ({args.train_iters} Adam iterations, batch 16), tested on the rest"),
                        "smoother": "coloured multiplicative CAV 1+1, hierarchy rebuilt per Newton system",
                        "tolerances": "Newton 1e-9 of ||b_step||, FGMRES 1e-10 of ||rhs||"},
@@ -590,6 +592,9 @@ def main():
                     help="--workload learned_channel: the extrapolation the CNN corrects")
     ap.add_argument("--trace", action="store_true", help="--workload fiber: print marker ranges every 50 steps")
     ap.add_argument("--train-iters", type=int, default=1500, help="--workload learned_channel: Adam iterations")
+    ap.add_argument("--train-start", type=float, default=0.4,
+                    help="--workload learned_channel: train on steps [train_start, 1) x the training range (after "
+                         "the inflow ramp)")
     ap.add_argument("--learned-history", type=int, default=4, choices=[3, 4],
                     help="--workload learned_channel: steps of history the CNN sees (4: as time differences)")
     ap.add_argument("--fiber-n", type=int, default=32,

@@ -245,6 +245,17 @@ typedef struct {
  * the enlarged-patch inverses in desc->precision.  Level 0 is the finest grid. */
 ib_status cav_setup(const ib_system* sys, const cav_desc* desc, cudaStream_t stream,
                     cav_hierarchy** out);
+/* Numerical re-set-up (ABI 4): when sys's finest E_E has the structural pattern the hierarchy
+ * was built from -- the next Newton iterate of a time step, whose S^n and J^n are unchanged and
+ * whose force law keeps its band, or a step whose markers stayed within their cells -- the
+ * patch sets, colour classes, transfers and captured V-cycle graphs are kept and only the
+ * numbers are recomputed into the existing buffers: E_E on every level (Galerkin, Sec. 4), the
+ * patch inverses (equilibration and Gauss-Jordan, Sec. 3.3), their storage precision, and the
+ * coarsest inverse.  The result is the one cav_setup would build for sys, bit for bit.  sys
+ * must have the grid and parameters of the hierarchy's system; the hierarchy is then bound
+ * to sys.  IB_ERR_INVALID (hierarchy unchanged) when the pattern differs: call cav_setup.
+ * Synchronises the stream. */
+ib_status cav_refactor(cav_hierarchy* h, const ib_system* sys, cudaStream_t stream);
 ib_status cav_num_levels(const cav_hierarchy* h, int32_t* levels);
 ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_info* info);
 /* Host copies of the patch sets of one smoothing level in cell order c = j N + i (block

@@ -105,6 +105,7 @@ _sig = {
     "ib_residual_norm": (C.c_int, [_vp, _vp, _vp, _vp, _P(C.c_double), _vp]),
     "cav_setup": (C.c_int, [_vp, _P(cav_desc), _vp, _P(_vp)]),
     "cav_num_levels": (C.c_int, [_vp, _P(C.c_int32)]),
+    "cav_refactor": (C.c_int, [_vp, _vp, _vp]),
     "cav_get_level_info": (C.c_int, [_vp, C.c_int32, _P(cav_level_info)]),
     "cav_patch_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _P(C.c_int32), _P(C.c_int64)]),
     "cav_ee_export": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _P(C.c_int64)]),
@@ -311,6 +312,17 @@ def cav_setup(sys: System, kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, alpha=
     return Hierarchy(out, sys, dict(kind=kind, coarsest_N=coarsest_N, nu_pre=nu_pre, nu_post=nu_post,
                                     alpha=alpha, precision=precision, autotune=autotune, smoother=smoother,
                                     coloured_levels=coloured_levels, nu_additive=nu_additive, box=tuple(box)))
+
+
+def cav_refactor(h: Hierarchy, sys: System, stream=None) -> bool:
+    """Recompute h's numbers for sys's E_E when its pattern is unchanged (True); False (h
+    unchanged) when the pattern differs and a new cav_setup is needed."""
+    st = _lib.cav_refactor(h.handle, sys.handle, _stream(stream))
+    if st == IB_ERR_INVALID and "pattern changed" in _lib.ib_last_error().decode():
+        return False
+    _check(st, "cav_refactor")
+    h.system = sys
+    return True
 
 
 def cav_num_levels(h: Hierarchy) -> int:

@@ -283,7 +283,14 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
     H = new cav_hierarchy();
     H->sys = s;
     H->desc = *d;
+    H->grid_N = s->N;
+    H->grid_bc = s->bc;
+    H->grid_L = s->L;
+    H->grid_rho = s->rho;
+    H->grid_mu = s->mu;
+    H->grid_dt = s->dt;
     H->status = H->arena.alloc<int>(1);
+    H->flag = H->arena.alloc<int>(1);
     CAV_CHECK_CUDA(cudaMemsetAsync(H->status, 0, sizeof(int), st));
     build_levels(H, st);
     *out = H;
@@ -296,6 +303,24 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
     set_error("cav_setup: internal error");
     return IB_ERR_INTERNAL;
   }
+}
+
+ib_status cav_refactor(cav_hierarchy* h, const ib_system* s, cudaStream_t st) {
+  CAV_API_BEGIN
+  CAV_REQUIRE(h && s, "cav_refactor: NULL argument");
+  CAV_REQUIRE(h->grid_N == s->N && h->grid_L == s->L && h->grid_rho == s->rho && h->grid_mu == s->mu &&
+                  h->grid_dt == s->dt && h->grid_bc == s->bc,
+              "cav_refactor: the system's grid or parameters differ from the hierarchy's");
+  int device = -1;
+  CAV_CHECK_CUDA(cudaGetDevice(&device));
+  CAV_REQUIRE(device == s->device, "cav_refactor: the current device is not the system's device");
+  if (!same_ee_pattern(s->ee, h->levels[0].ee, h->flag, st)) {
+    set_error("cav_refactor: E_E's structural pattern changed (markers moved across faces): use cav_setup");
+    return IB_ERR_INVALID;
+  }
+  refactor_levels(h, s, st);
+  return IB_OK;
+  CAV_API_END
 }
 
 ib_status cav_num_levels(const cav_hierarchy* h, int32_t* levels) {

@@ -695,6 +695,15 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   }
 }
 
+// The FP32 copy of E_E's values on an FP32-inverse coloured level, after E_E's values changed
+// (cav_refactor); the other class-step records depend on the structure only.
+void colour_refresh_values(Level& lv, cudaStream_t st) {
+  if (lv.precision == CAV_PREC_FP32 && lv.ee.nnz) {
+    k_round_f32<<<div_up(lv.ee.nnz, 256), 256, 0, st>>>(lv.ee.nnz, lv.ee.vals, lv.ee_vals32);
+    CAV_CHECK_LAUNCH();
+  }
+}
+
 void colour_set_wait_stall(int enable) {
   CAV_CHECK_CUDA(cudaMemcpyToSymbol(g_wait_stall, &enable, sizeof(int)));
 }

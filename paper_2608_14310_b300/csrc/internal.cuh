@@ -96,6 +96,7 @@ struct Level {
   // patches (smoothing levels): one per cell; enlarged ones are stored explicitly
   int n_big = 0;                 // enlarged patches
   int n_std4 = 0;                // standard patches with four unknowns (the channel's inflow row)
+  std::vector<int> host_sizes;   // [n_big] stored patch sizes (host copy, for refactorisation)
   int n_big_small = 0;           // stored patches with at most five unknowns (Vanka patches whose
                                  // unknowns have E_E rows)
   int64_t big_sum_n = 0, big_sum_n2 = 0, inv_elems = 0;
@@ -196,6 +197,11 @@ struct cav_hierarchy {
   std::vector<cav::Level> levels;
   cav::Arena arena;
   int* status = nullptr;
+  int* flag = nullptr;           // device scratch word (pattern comparison)
+  // the grid the hierarchy was built for (cav_refactor accepts only systems on the same grid;
+  // the system it was built from may have been destroyed by then)
+  int grid_N = 0, grid_bc = 0;
+  double grid_L = 0, grid_rho = 0, grid_mu = 0, grid_dt = 0;
   // FGMRES workspace (grown on demand)
   int ws_maxit = 0;
   double* V = nullptr;   // (maxit + 1) x n
@@ -281,9 +287,15 @@ void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cu
 
 // setup.cu
 void build_levels(cav_hierarchy* H, cudaStream_t st);
+// true if the two E_E share their structural pattern (rows, row pointers, columns); syncs
+bool same_ee_pattern(const EECsr& a, const EECsr& b, int* d_flag, cudaStream_t st);
+// new values of the system's finest E_E on an unchanged pattern: Galerkin values, patch and
+// coarsest inverses recomputed into the hierarchy's existing buffers; binds H to s
+void refactor_levels(cav_hierarchy* H, const ib_system* s, cudaStream_t st);
 
 // colour.cu: colour classes (set-up) and the class-by-class multiplicative sweep
 void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st);
+void colour_refresh_values(Level& lv, cudaStream_t st);
 // fails (IB_ERR_INVALID) when the level's class steps would not fit in shared memory
 void check_colour_step(const Level& lv);
 void coloured_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero,

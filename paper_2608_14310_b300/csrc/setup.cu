@@ -195,6 +195,22 @@ static void galerkin_level(const EECsr& fine, int Nc, EECsr& out, Arena& A, int*
   scratch.release();
 }
 
+// The coarse E_E's values for an unchanged structural pattern (cav_refactor): the fill pass of
+// the same kernel into the level's existing arrays (the columns it writes are the ones
+// already there).
+static void galerkin_values(const EECsr& fine, int Nc, EECsr& out, bool channel, cudaStream_t st) {
+  if (out.n_rows == 0) return;
+  const int Wc = fine.W / 2 + 2;
+  const int grid = div_up(out.n_rows, 8);
+  if (out.cross)
+    k_galerkin<true><<<grid, 256, 0, st>>>(Nc, Wc, out.n_rows, out.rows, fine.row_of, fine.rowptr, fine.cols,
+                                           fine.vals, nullptr, out.rowptr, out.cols, out.vals, 1, channel);
+  else
+    k_galerkin<false><<<grid, 256, 0, st>>>(Nc, Wc, out.n_rows, out.rows, fine.row_of, fine.rowptr, fine.cols,
+                                            fine.vals, nullptr, out.rowptr, out.cols, out.vals, 1, channel);
+  CAV_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ CAV patch sets
 
 // Velocity unknowns U_ij of cell (i, j)'s Vanka patch: u_ij, u_i+1j, v_ij, v_ij+1; on the
@@ -751,6 +767,154 @@ static void box_sets(int N, int b, int o, std::vector<int>& cells, std::vector<i
     }
 }
 
+// The standard Vanka patches appended to a level's stored sets for factorisation, in
+// canonical slot order (u_ij, u_i+1j, v_ij, v_ij+1, p_ij): one for a periodic level (cell
+// (0, 0)), three for the channel (interior rows, the outflow row, the inflow row without
+// v_{i,N}).
+static void standard_patch_dofs(const Level& lv, std::vector<int>& std_dofs, std::vector<int>& std_len) {
+  const int N = lv.N, NN = N * N;
+  {
+    auto cell = [&](int i, int j) {
+      int ds[5] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i, 2 * NN + j * N + i};
+      const bool top = lv.channel && j + 1 == N;
+      int len = 0;
+      for (int t = 0; t < 5; ++t)
+        if (!(top && t == 3)) std_dofs.push_back(ds[t]), ++len;
+      std_len.push_back(len);
+    };
+    if (lv.channel) {
+      cell(0, 1);      // interior rows
+      cell(0, 0);      // outflow row
+      cell(0, N - 1);  // inflow row (no v_{i,N})
+    } else {
+      cell(0, 0);
+    }
+  }
+}
+
+// The numerical part of a smoothing level's set-up: extract every stored patch's local matrix
+// from the level's current K_E, equilibrate, invert (batched Gauss-Jordan, FP64), pack, and
+// store in the level's precision; with `standard`, also the standard patches' shared
+// inverses (E_E-free, so they do not change when only E_E's values do).  The structure (sets,
+// offsets, incidence, classes) must already be in place; buffers are allocated on the first
+// call and reused by later ones (cav_refactor), so graphs captured on them stay valid.
+static void factor_patches(cav_hierarchy* H, Level& lv, bool standard, cudaStream_t st) {
+  Arena& A = H->arena;
+  Arena scratch;
+  const int64_t nbig = lv.n_big;
+  const std::vector<int>& hsizes = lv.host_sizes;
+  const int64_t sum_n = lv.big_sum_n, inv_elems = lv.inv_elems;
+  const int max_n = lv.big_max_n;
+  const LevelK LK = level_k(lv);
+  std::vector<int> std_dofs, std_len;
+  standard_patch_dofs(lv, std_dofs, std_len);
+  // 3. factorise the enlarged patches, then the standard Vanka patch(es) (jobs nbig ..) in
+  //    canonical slot order (u_ij, u_i+1j, v_ij, v_ij+1, p_ij; the inflow row without v_ij+1)
+  //    without E_E.
+  CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs + sum_n, std_dofs.data(), sizeof(int) * std_dofs.size(),
+                                 cudaMemcpyHostToDevice, st));
+  const int n_std = standard ? (int)std_len.size() : 0;
+  const int njobs = (int)nbig + n_std;
+  std::vector<int64_t> hoff_ext(njobs + 1);
+  hoff_ext[0] = 0;
+  for (int p = 0; p < njobs; ++p) hoff_ext[p + 1] = hoff_ext[p] + (p < nbig ? hsizes[p] : std_len[p - nbig]);
+  std::vector<int64_t> hmat_off(njobs + 1, 0);
+  for (int p = 0; p < njobs; ++p) {
+    const int m = (p < nbig) ? hsizes[p] : std_len[p - nbig];
+    // a patch holding every pressure of a periodic level gets one border row and column
+    hmat_off[p + 1] = hmat_off[p] + (int64_t)round8(m + 1) * (m + 1);
+  }
+  int64_t* d_off_ext = scratch.alloc<int64_t>(njobs + 1);
+  int64_t* d_mat_off = scratch.alloc<int64_t>(njobs + 1);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_off_ext, hoff_ext.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, st));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(d_mat_off, hmat_off.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, st));
+  double* work = scratch.alloc<double>(hmat_off[njobs]);
+  double* wsr = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
+  double* wsc = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
+  int* mdim = scratch.alloc<int>(njobs + 1);
+  FactorJob J;
+  J.mdim = mdim;
+  J.dof_off = d_off_ext;
+  J.dofs = lv.big_dofs;
+  J.mat_off = d_mat_off;
+  J.A = work;
+  J.s_r = wsr;
+  J.s_c = wsc;
+  J.border_all_pressure = lv.channel ? 0 : 1;  // the channel's pressure is determined
+  J.use_ee = 1;
+  const int mmax = std::max(max_n, 5) + 1;
+  const size_t fsm = factor_smem(mmax);
+  if (fsm > 48 * 1024)
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  if (nbig > 0) {
+    k_factor<<<(int)nbig, 256, fsm, st>>>(LK, J, 0, H->status);
+    CAV_CHECK_LAUNCH();
+  }
+  // the standard patches: same kernel, one block each, no E_E
+  if (standard) {
+    FactorJob Js = J;
+    Js.dof_off = d_off_ext + nbig;
+    Js.mat_off = d_mat_off + nbig;
+    Js.mdim = mdim + nbig;
+    Js.s_r = wsr + nbig;  // scale slots of job p start at dof_off[p] + p
+    Js.s_c = wsc + nbig;
+    Js.use_ee = 0;
+    Js.border_all_pressure = 0;
+    k_factor<<<n_std, 64, factor_smem(6), st>>>(LK, Js, 0, H->status);
+    CAV_CHECK_LAUNCH();
+    double* d_std = scratch.alloc<double>(25 * n_std);
+    for (int q = 0; q < n_std; ++q) {
+      const int p = (int)nbig + q;
+      k_fold_rowmajor<<<1, 32, 0, st>>>(std_len[q], work + hmat_off[p], wsr + hoff_ext[p] + p, wsc + hoff_ext[p] + p,
+                                        d_std + 25 * q);
+      CAV_CHECK_LAUNCH();
+    }
+    std::vector<double> hstd(25 * n_std);
+    CAV_CHECK_CUDA(cudaMemcpyAsync(hstd.data(), d_std, sizeof(double) * 25 * n_std, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    // kind 0 interior (or every periodic cell), 1 outflow row, 2 inflow row: the inflow row's
+    // 4 x 4 inverse goes to slots (0, 1, 2, 4) with slot 3 (v_ij+1) left zero
+    for (int k = 0; k < 3; ++k)
+      for (int q = 0; q < 25; ++q) lv.std_inv[k][q] = 0.0;
+    for (int q = 0; q < n_std; ++q) {
+      const int m = std_len[q];
+      int slot[5] = {0, 1, 2, 3, 4};
+      if (m == 4) slot[3] = 4;
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) lv.std_inv[q][slot[a] * 5 + slot[b]] = hstd[25 * q + a * m + b];
+    }
+    if (n_std == 1)
+      for (int k = 1; k < 3; ++k)
+        for (int q = 0; q < 25; ++q) lv.std_inv[k][q] = lv.std_inv[0][q];
+  }
+  check_status(H, st, "patch factorisation");
+  // 4. pack the inverses (ld = round8(n), column-major) and scales; bordered patches are
+  //    applied with their border slot's residual entry equal to zero, so only the leading
+  //    n x n block and the first n scales are needed.
+  if (!lv.s_r) {
+    lv.s_r = A.alloc<double>(sum_n);
+    lv.s_c = A.alloc<double>(sum_n);
+    lv.inv64 = A.alloc<double>(std::max<int64_t>(inv_elems, 1));
+  }
+  if (nbig > 0) {
+    k_pack<<<(int)nbig, 256, 0, st>>>(lv.big_off, d_mat_off, mdim, lv.inv_off, work, wsr, wsc, lv.inv64,
+                                      lv.s_r, lv.s_c);
+    CAV_CHECK_LAUNCH();
+  }
+  lv.precision = H->desc.precision;
+  if (lv.precision == CAV_PREC_FP32) {
+    if (!lv.inv32) lv.inv32 = A.alloc<float>(std::max<int64_t>(inv_elems, 1));
+    k_downcast<float><<<1184, 256, 0, st>>>(inv_elems, lv.inv64, lv.inv32);
+    CAV_CHECK_LAUNCH();
+  } else if (lv.precision == CAV_PREC_BF16) {
+    if (!lv.inv16) lv.inv16 = A.alloc<__nv_bfloat16>(std::max<int64_t>(inv_elems, 1));
+    k_downcast<__nv_bfloat16><<<1184, 256, 0, st>>>(inv_elems, lv.inv64, lv.inv16);
+    CAV_CHECK_LAUNCH();
+  }
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  scratch.release();
+}
+
 static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   Arena& A = H->arena;
   Arena scratch;
@@ -822,7 +986,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
       CAV_CHECK_CUDA(cudaMemcpyAsync(hsizes.data(), sizes, sizeof(int) * nbig, cudaMemcpyDeviceToHost, st));
     CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   }
-  int64_t sum_n = 0, sum_n2 = 0, inv_elems = 0;
+  int64_t sum_n = 0, sum_n2 = 0;
   int max_n = 0;
   std::vector<int64_t> hinv_off(nbig + 1, 0);
   for (int64_t p = 0; p < nbig; ++p) {
@@ -837,27 +1001,10 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   lv.n_big_small = 0;
   for (int64_t p = 0; p < nbig; ++p) lv.n_big_small += (hsizes[p] <= 5 && !lv.box) ? 1 : 0;
   lv.big_max_n = max_n;
-  lv.inv_elems = inv_elems = hinv_off[nbig];
-  // the standard patches appended for factorisation: one (periodic) or three (channel) jobs
-  std::vector<int> std_dofs;
-  std::vector<int> std_len;
-  {
-    auto cell = [&](int i, int j) {
-      int ds[5] = {j * N + i, j * N + (i + 1) % N, NN + j * N + i, NN + ((j + 1) % N) * N + i, 2 * NN + j * N + i};
-      const bool top = lv.channel && j + 1 == N;
-      int len = 0;
-      for (int t = 0; t < 5; ++t)
-        if (!(top && t == 3)) std_dofs.push_back(ds[t]), ++len;
-      std_len.push_back(len);
-    };
-    if (lv.channel) {
-      cell(0, 1);      // interior rows
-      cell(0, 0);      // outflow row
-      cell(0, N - 1);  // inflow row (no v_{i,N})
-    } else {
-      cell(0, 0);
-    }
-  }
+  lv.inv_elems = hinv_off[nbig];
+  // the standard patches are appended to the stored sets for factorisation
+  std::vector<int> std_dofs, std_len;
+  standard_patch_dofs(lv, std_dofs, std_len);
   const int n_std = (int)std_len.size();
   lv.big_dofs = A.alloc<int>(sum_n + (int64_t)std_dofs.size());
   if (lv.box) {
@@ -881,106 +1028,9 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   }
   CAV_CHECK_CUDA(cudaMemcpyAsync(lv.inv_off, hinv_off.data(), sizeof(int64_t) * (nbig + 1),
                                  cudaMemcpyHostToDevice, st));
-  // 3. factorise the enlarged patches, then the standard Vanka patch(es) (jobs nbig ..) in
-  //    canonical slot order (u_ij, u_i+1j, v_ij, v_ij+1, p_ij; the inflow row without v_ij+1)
-  //    without E_E.
-  CAV_CHECK_CUDA(cudaMemcpyAsync(lv.big_dofs + sum_n, std_dofs.data(), sizeof(int) * std_dofs.size(),
-                                 cudaMemcpyHostToDevice, st));
-  const int njobs = (int)nbig + n_std;
-  std::vector<int64_t> hoff_ext(njobs + 1);
-  hoff_ext[0] = 0;
-  for (int p = 0; p < njobs; ++p) hoff_ext[p + 1] = hoff_ext[p] + (p < nbig ? hsizes[p] : std_len[p - nbig]);
-  std::vector<int64_t> hmat_off(njobs + 1, 0);
-  for (int p = 0; p < njobs; ++p) {
-    const int m = (p < nbig) ? hsizes[p] : std_len[p - nbig];
-    // a patch holding every pressure of a periodic level gets one border row and column
-    hmat_off[p + 1] = hmat_off[p] + (int64_t)round8(m + 1) * (m + 1);
-  }
-  int64_t* d_off_ext = scratch.alloc<int64_t>(njobs + 1);
-  int64_t* d_mat_off = scratch.alloc<int64_t>(njobs + 1);
-  CAV_CHECK_CUDA(cudaMemcpyAsync(d_off_ext, hoff_ext.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, st));
-  CAV_CHECK_CUDA(cudaMemcpyAsync(d_mat_off, hmat_off.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, st));
-  double* work = scratch.alloc<double>(hmat_off[njobs]);
-  double* wsr = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
-  double* wsc = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
-  int* mdim = scratch.alloc<int>(njobs + 1);
-  FactorJob J;
-  J.mdim = mdim;
-  J.dof_off = d_off_ext;
-  J.dofs = lv.big_dofs;
-  J.mat_off = d_mat_off;
-  J.A = work;
-  J.s_r = wsr;
-  J.s_c = wsc;
-  J.border_all_pressure = lv.channel ? 0 : 1;  // the channel's pressure is determined
-  J.use_ee = 1;
-  const int mmax = std::max(max_n, 5) + 1;
-  const size_t fsm = factor_smem(mmax);
-  if (fsm > 48 * 1024)
-    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-  if (nbig > 0) {
-    k_factor<<<(int)nbig, 256, fsm, st>>>(LK, J, 0, H->status);
-    CAV_CHECK_LAUNCH();
-  }
-  // the standard patches: same kernel, one block each, no E_E
-  {
-    FactorJob Js = J;
-    Js.dof_off = d_off_ext + nbig;
-    Js.mat_off = d_mat_off + nbig;
-    Js.mdim = mdim + nbig;
-    Js.s_r = wsr + nbig;  // scale slots of job p start at dof_off[p] + p
-    Js.s_c = wsc + nbig;
-    Js.use_ee = 0;
-    Js.border_all_pressure = 0;
-    k_factor<<<n_std, 64, factor_smem(6), st>>>(LK, Js, 0, H->status);
-    CAV_CHECK_LAUNCH();
-    double* d_std = scratch.alloc<double>(25 * n_std);
-    for (int q = 0; q < n_std; ++q) {
-      const int p = (int)nbig + q;
-      k_fold_rowmajor<<<1, 32, 0, st>>>(std_len[q], work + hmat_off[p], wsr + hoff_ext[p] + p, wsc + hoff_ext[p] + p,
-                                        d_std + 25 * q);
-      CAV_CHECK_LAUNCH();
-    }
-    std::vector<double> hstd(25 * n_std);
-    CAV_CHECK_CUDA(cudaMemcpyAsync(hstd.data(), d_std, sizeof(double) * 25 * n_std, cudaMemcpyDeviceToHost, st));
-    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-    // kind 0 interior (or every periodic cell), 1 outflow row, 2 inflow row: the inflow row's
-    // 4 x 4 inverse goes to slots (0, 1, 2, 4) with slot 3 (v_ij+1) left zero
-    for (int k = 0; k < 3; ++k)
-      for (int q = 0; q < 25; ++q) lv.std_inv[k][q] = 0.0;
-    for (int q = 0; q < n_std; ++q) {
-      const int m = std_len[q];
-      int slot[5] = {0, 1, 2, 3, 4};
-      if (m == 4) slot[3] = 4;
-      for (int a = 0; a < m; ++a)
-        for (int b = 0; b < m; ++b) lv.std_inv[q][slot[a] * 5 + slot[b]] = hstd[25 * q + a * m + b];
-    }
-    if (n_std == 1)
-      for (int k = 1; k < 3; ++k)
-        for (int q = 0; q < 25; ++q) lv.std_inv[k][q] = lv.std_inv[0][q];
-  }
-  check_status(H, st, "patch factorisation");
-  // 4. pack the inverses (ld = round8(n), column-major) and scales; bordered patches are
-  //    applied with their border slot's residual entry equal to zero, so only the leading
-  //    n x n block and the first n scales are needed.
-  lv.s_r = A.alloc<double>(sum_n);
-  lv.s_c = A.alloc<double>(sum_n);
-  lv.inv64 = A.alloc<double>(std::max<int64_t>(inv_elems, 1));
-  if (nbig > 0) {
-    k_pack<<<(int)nbig, 256, 0, st>>>(lv.big_off, d_mat_off, mdim, lv.inv_off, work, wsr, wsc, lv.inv64,
-                                      lv.s_r, lv.s_c);
-    CAV_CHECK_LAUNCH();
-  }
-  lv.precision = H->desc.precision;
-  if (lv.precision == CAV_PREC_FP32) {
-    lv.inv32 = A.alloc<float>(std::max<int64_t>(inv_elems, 1));
-    k_downcast<float><<<1184, 256, 0, st>>>(inv_elems, lv.inv64, lv.inv32);
-    CAV_CHECK_LAUNCH();
-  } else if (lv.precision == CAV_PREC_BF16) {
-    lv.inv16 = A.alloc<__nv_bfloat16>(std::max<int64_t>(inv_elems, 1));
-    k_downcast<__nv_bfloat16><<<1184, 256, 0, st>>>(inv_elems, lv.inv64, lv.inv16);
-    CAV_CHECK_LAUNCH();
-  }
+  // 3-4. factorise and store the inverses (also the standard patches')
+  lv.host_sizes = hsizes;
+  factor_patches(H, lv, true, st);
   // 5. transpose incidence of the packed slots
   int* cnt = scratch.alloc<int>(3 * NN);
   int* cur = scratch.alloc<int>(3 * NN);
@@ -1065,7 +1115,7 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   k_factor<<<1, 1024, fsm, st>>>(LK, J, lv.channel ? 0 : 1, H->status);
   CAV_CHECK_LAUNCH();
   lv.coarse_m = m;
-  lv.coarse_inv = A.alloc<double>((size_t)m * m);
+  if (!lv.coarse_inv) lv.coarse_inv = A.alloc<double>((size_t)m * m);  // reused by cav_refactor
   k_fold_rowmajor<<<64, 256, 0, st>>>(m, work, wsr, wsc, lv.coarse_inv);
   CAV_CHECK_LAUNCH();
   check_status(H, st, "coarsest factorisation");
@@ -1139,6 +1189,54 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
   vcycle_prepare(H);
   if (H->desc.krylov_capacity > 0)
     krylov_reserve(H, H->desc.krylov_capacity, 3LL * H->levels[0].N * H->levels[0].N);
+}
+
+// ------------------------------------------------------------------ refactorisation
+
+// 1 in *flag if a[0..n) and b[0..n) differ anywhere
+__global__ void k_differ32(int64_t n, const int* __restrict__ a, const int* __restrict__ b, int* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) atomicExch(flag, 1);
+}
+__global__ void k_differ64(int64_t n, const int64_t* __restrict__ a, const int64_t* __restrict__ b, int* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) atomicExch(flag, 1);
+}
+
+bool same_ee_pattern(const EECsr& a, const EECsr& b, int* d_flag, cudaStream_t st) {
+  if (a.n_rows != b.n_rows || a.nnz != b.nnz || a.cross != b.cross) return false;
+  if (a.n_rows == 0) return true;
+  CAV_CHECK_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+  k_differ32<<<div_up(a.n_rows, 256) < 1184 ? div_up(a.n_rows, 256) : 1184, 256, 0, st>>>(a.n_rows, a.rows, b.rows,
+                                                                                         d_flag);
+  CAV_CHECK_LAUNCH();
+  k_differ64<<<div_up(a.n_rows + 1, 256) < 1184 ? div_up(a.n_rows + 1, 256) : 1184, 256, 0, st>>>(
+      a.n_rows + 1, a.rowptr, b.rowptr, d_flag);
+  CAV_CHECK_LAUNCH();
+  if (a.nnz) {
+    k_differ32<<<div_up(a.nnz, 256) < 1184 ? div_up(a.nnz, 256) : 1184, 256, 0, st>>>(a.nnz, a.cols, b.cols, d_flag);
+    CAV_CHECK_LAUNCH();
+  }
+  return read_status(d_flag, st) == 0;
+}
+
+void refactor_levels(cav_hierarchy* H, const ib_system* s, cudaStream_t st) {
+  Level& l0 = H->levels[0];
+  if (s->ee.nnz)
+    CAV_CHECK_CUDA(cudaMemcpyAsync(l0.ee.vals, s->ee.vals, sizeof(double) * s->ee.nnz, cudaMemcpyDeviceToDevice, st));
+  for (size_t l = 1; l < H->levels.size(); ++l)
+    galerkin_values(H->levels[l - 1].ee, H->levels[l].N, H->levels[l].ee, H->levels[l].channel, st);
+  for (auto& lv : H->levels) {
+    if (lv.coarsest) {
+      build_coarsest(H, lv, st);
+      continue;
+    }
+    factor_patches(H, lv, false, st);
+    if (lv.coloured) colour_refresh_values(lv, st);
+  }
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  check_status(H, st, "refactorisation");
+  H->sys = s;
 }
 
 }  // namespace cav

@@ -34,17 +34,41 @@ class FiberChannel:
 
     def __init__(self, rec, cav: dict | None = None, newton_rtol: float = 1e-8, newton_atol: float = 1e-8,
                  fgmres_rtol: float = 1e-9, newton_maxit: int = 20, fgmres_maxit: int = 150,
-                 newton_ref: str = "r0"):
+                 newton_ref: str = "r0", refactor: bool = True):
         """newton_ref "r0": stop when ||R(w_k)|| <= max(newton_rtol ||R(w_0)||, newton_atol) (the
         paper's relative test, as in the oracle); "b": ||R(w_k)|| <= newton_rtol ||b|| with b the
         step's base right-hand side, a reference independent of the starting iterate (used
-        when comparing initial guesses)."""
+        when comparing initial guesses).  refactor: a hierarchy is kept between Newton
+        systems (and steps) and rebuilt numerically by cav_refactor while E_E's pattern is
+        unchanged (bit for bit the hierarchy cav_setup would build), else by cav_setup."""
         assert getattr(rec, "bc", "periodic") == "channel"
         assert newton_ref in ("r0", "b")
         self.rec = rec
         self.cav = dict(DEFAULT_CAV if cav is None else cav)
         self.newton_rtol, self.newton_atol, self.newton_ref = newton_rtol, newton_atol, newton_ref
         self.fgmres_rtol, self.newton_maxit, self.fgmres_maxit = fgmres_rtol, newton_maxit, fgmres_maxit
+        self.refactor = refactor
+        self._h = {}          # hierarchies kept for refactorisation, by set-up parameters
+        self.setups = 0       # cav_setup calls
+        self.refactors = 0    # cav_refactor calls that succeeded
+
+    def _hierarchy(self, sysm):
+        """The hierarchy for the system's current E_E (Sec. 5.3 rebuilds it per Newton system)."""
+        if not self.refactor:
+            self.setups += 1
+            return api.cav_setup(sysm, **self.cav)
+        key = tuple(sorted(self.cav.items()))
+        h = self._h.get(key)
+        if h is not None and api.cav_refactor(h, sysm):
+            self.refactors += 1
+            return h
+        if h is not None:
+            h.close()
+        h = api.cav_setup(sysm, **self.cav)
+        self._h[key] = h
+        self.setups += 1
+        return h
+
 
     def step(self, w_n, t_next: float, guess=None):
         """One step from the device vector w_n (3 N^2, at t^n = t_next - dt) with the markers at
@@ -75,18 +99,18 @@ class FiberChannel:
                 self.newton_rtol * ref
             if k >= self.newton_maxit or hist[-1] <= tol:
                 break
-            h = api.cav_setup(sysm, **self.cav)
+            h = self._hierarchy(sysm)
             x = w.clone()
             # newton_ref "r0": fgmres_rtol relative to the Newton residual at w_k (inexact Newton);
             # "b": relative to ||rhs_k||, a reference independent of the starting iterate
             info = api.fgmres_solve(sysm, h, rhs, x, rtol=self.fgmres_rtol, maxit=self.fgmres_maxit,
                                     rel_to=1 if self.newton_ref == "r0" else 0, history=False)
-            h.close()
+            if not self.refactor:
+                h.close()
             its.append(info)
             w = x
             X_k = api.ib_advect(sysm, w)
             k += 1
-        sysm.close()
         torch.cuda.synchronize()
         self.rec = replace(rec, X=X_k)
         return w, X_k, hist, its, time.perf_counter() - t0

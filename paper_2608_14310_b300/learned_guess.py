@@ -117,12 +117,13 @@ class LearnedGuess:
             return dict(x_prev2=ts.x_hist[i - 1], x_prev3=ts.x_hist[i - 2])
         return dict(x_prev2=ts.x_hist[i - 1])
 
-    def fit_scales(self, ts: TimeSeries, upto: int):
-        """Per-channel RMS of the training range (host statistics of a few sampled steps;
-        upto = number of completed steps, so x^{i+1} and f^i exist for i < upto)."""
+    def fit_scales(self, ts: TimeSeries, upto: int, start: int = 0):
+        """Per-channel RMS of the training range [start, upto) (host statistics of a few
+        sampled steps; upto = number of completed steps, so x^{i+1} and f^i exist for i < upto)."""
         N = self.N
         NN = N * N
-        idx = np.linspace(2, upto - 1, num=min(16, max(1, upto - 2)), dtype=int)
+        first = max(start, self.history - 1, 2)
+        idx = np.linspace(first, upto - 1, num=min(16, max(1, upto - first)), dtype=int)
         xs = np.stack([ts.x_hist[i].cpu().numpy() for i in idx])
         fs = np.stack([ts.f_hist[i].cpu().numpy() for i in idx])
         dx = np.stack([(ts.x_hist[i + 1] - ts.x_hist[i]).cpu().numpy() for i in idx])
@@ -167,11 +168,11 @@ class LearnedGuess:
             api.ibnet_pack_history(self.N, [ts.x_hist[i - q] for q in (3, 2, 1, 0)],
                                    [ts.f_hist[i - q] for q in (3, 2, 1, 0)], self.in_scale, out)
 
-    def train(self, ts: TimeSeries, upto: int, iters=1500, batch=16, lr=1e-3, seed=11):
+    def train(self, ts: TimeSeries, upto: int, iters=1500, batch=16, lr=1e-3, seed=11, start: int = 0):
         torch = self.torch
         N = self.N
         NN = N * N
-        samples = np.arange(self.history - 1, upto)   # x^{i+1} must exist: i + 1 <= upto
+        samples = np.arange(max(start, self.history - 1), upto)   # x^{i+1} must exist: i + 1 <= upto
         C = self.in_ch
         xin = torch.empty(batch * C * NN, dtype=torch.float32, device="cuda")
         tgt = torch.empty(batch * 3 * NN, dtype=torch.float32, device="cuda")

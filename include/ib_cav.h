@@ -47,9 +47,11 @@ typedef enum {
 
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 const char* ib_last_error(void);
-/* ABI version of this header: 4 (ib_grid_desc.bc; ib_test_wait_stall). */
+/* ABI version of this header: 5 (4: ib_grid_desc.bc, ib_test_wait_stall; 5: fgmres_desc.loop,
+ * ibnet_inner). */
 int ib_abi_version(void);
-/* Number of kernels this library has launched in this process (host-side count). */
+/* Number of kernels this library has launched in this process (host-side count; a graph
+ * replay adds the kernels it ran). */
 int64_t ib_launch_count(void);
 
 /* ------------------------------------------------------------------ system (Sec. 2) */
@@ -238,6 +240,10 @@ typedef struct {
   int32_t apply_variant;     /* patch-apply kernel variant in use (0 unless autotuned)        */
   float apply_us[5];         /* autotuner's time per launch of each variant (0: not timed)    */
   int32_t n_colours;         /* colour classes of the coloured smoother (0 for additive) (ABI 2) */
+  int32_t sweep_form;        /* additive levels (ABI 5): 0 the sweep's parts as separate kernels,
+                                1 one fused cooperative kernel (residual, patch apply, scatter
+                                and mean removal between grid-wide barriers; same bits)       */
+  float sweep_us[2];         /* the set-up's timing of one sweep in each form (0: not timed)  */
 } cav_level_info;
 
 /* Builds the level hierarchy, Galerkin E_E^(l-1) = R E_E^(l) P, the patch sets and their
@@ -344,6 +350,16 @@ typedef struct {
   int32_t rel_to;    /* 0: ref = b, 1: ref = r_0                                         */
   int32_t host_io;   /* 1: b and x are HOST pointers; the call copies them to and from
                         the device inside the call                                       */
+  int32_t loop;      /* 0: host-driven iterations (the host reads one small record per
+                        iteration); 1: device-driven (ABI 5): the whole solve -- or, in
+                        fgmres_solve_batched, the whole batch -- is one CUDA graph launch
+                        whose iterations run under a conditional while node, the
+                        convergence test setting the loop condition on the device.  The
+                        graph is built on the first call and cached with the first
+                        hierarchy while the systems, hierarchies, vectors, rtol, maxit and
+                        rel_to stay the same (ib_update_structure and cav_refactor make the
+                        next call rebuild it).  Results are bitwise those of loop = 0.
+                        Device buffers only (host_io must be 0).                          */
 } fgmres_desc;
 
 typedef struct {
@@ -367,9 +383,10 @@ ib_status fgmres_solve(const ib_system* sys, const cav_hierarchy* h, const doubl
 /* Many independent systems solved together (batched, uneven sizes): the same FGMRES as
  * fgmres_solve for each (systems[i], hierarchies[i], b[i], x[i]), advanced in lockstep with
  * every system on its own library-owned stream so that their V-cycle graphs and Krylov
- * kernels overlap on the device.  Each system stops at its own convergence; infos[i] is
- * filled for every i.  Results are bitwise those of fgmres_solve.  Device buffers only
- * (host_io must be 0); a hierarchy may appear once per call.  Waits on `stream` before
+ * kernels overlap on the device (desc->loop = 0), or as one CUDA graph launch whose branches
+ * are the systems' device-driven solves (desc->loop = 1).  Each system stops at its own
+ * convergence; infos[i] is filled for every i.  Results are bitwise those of fgmres_solve.
+ * Device buffers only (host_io must be 0); a hierarchy may appear once per call.  Waits on `stream` before
  * starting and synchronises everything before returning.  IB_ERR_NOCONV if any system
  * stopped at maxit. */
 ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
@@ -428,6 +445,11 @@ ib_status ibnet_pack_history(int32_t N, int32_t K, const double* const* hist_x, 
 ib_status ibnet_pack_target(int32_t N, const double* x_new, const double* x_prev,
                             const double* x_prev2, const double* x_prev3, const float* out_scale,
                             float* out, cudaStream_t stream);
+/* out (host) = <a, b> over n FP32 values, products and sums in FP64 in a fixed order
+ * (ABI 5): used to fit the scale of the network's correction on held-out steps.  Uses a
+ * scratch buffer of the network (one call at a time per network); synchronises the stream. */
+ib_status ibnet_inner(ibnet* net, int64_t n, const float* a, const float* b, double* out,
+                      cudaStream_t stream);
 /* x_out = base + out_scale * delta per field (base as above; delta NULL: base alone): the
  * predicted initial guess. */
 ib_status ibnet_apply_delta(int32_t N, const double* x_prev, const double* x_prev2,

@@ -64,12 +64,16 @@ class cav_level_info(C.Structure):
                 ("enlarged_sum_n", C.c_int64), ("enlarged_sum_n2", C.c_int64),
                 ("inverse_bytes", C.c_int64), ("ee_nnz", C.c_int64), ("ee_rows", C.c_int32),
                 ("ee_window", C.c_int32), ("is_coarsest", C.c_int32), ("apply_variant", C.c_int32),
-                ("apply_us", C.c_float * 5), ("n_colours", C.c_int32)]
+                ("apply_us", C.c_float * 5), ("n_colours", C.c_int32), ("sweep_form", C.c_int32),
+                ("sweep_us", C.c_float * 2)]
 
 
 class fgmres_desc(C.Structure):
     _fields_ = [("rtol", C.c_double), ("maxit", C.c_int32), ("rel_to", C.c_int32),
-                ("host_io", C.c_int32)]
+                ("host_io", C.c_int32), ("loop", C.c_int32)]
+
+
+LOOP = {"host": 0, "device": 1}
 
 
 class fgmres_info(C.Structure):
@@ -125,6 +129,7 @@ _sig = {
     "ibnet_get_params": (C.c_int, [_vp, _vp]),
     "ibnet_set_params": (C.c_int, [_vp, _vp]),
     "ibnet_forward": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _vp]),
+    "ibnet_inner": (C.c_int, [_vp, C.c_int64, _vp, _vp, _P(C.c_double), _vp]),
     "ibnet_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _P(C.c_float), _vp, _vp]),
     "ibnet_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_float, _P(C.c_float), _vp]),
     "ibnet_pack_input": (C.c_int, [C.c_int32, _P(_vp), _P(_vp), _P(C.c_float), _vp, _vp]),
@@ -336,6 +341,7 @@ def cav_get_level_info(h: Hierarchy, level: int) -> dict:
     _check(_lib.cav_get_level_info(h.handle, level, C.byref(info)), "cav_get_level_info")
     out = {f: getattr(info, f) for f, _ in info._fields_}
     out["apply_us"] = list(info.apply_us)
+    out["sweep_us"] = list(info.sweep_us)
     return out
 
 
@@ -422,11 +428,12 @@ def cav_profile_read(h: Hierarchy):
 
 
 def fgmres_solve(sys: System, h: Hierarchy, b, x, rtol=1e-10, maxit=60, rel_to=0, history=True,
-                 stream=None, raise_on_noconv=False) -> dict:
+                 stream=None, raise_on_noconv=False, loop="host") -> dict:
     """b, x: CUDA tensors, or host buffers (numpy float64 arrays or CPU torch tensors, e.g.
-    pinned) -- then the call copies b and x in and x out inside the call."""
+    pinned) -- then the call copies b and x in and x out inside the call.  loop "device": the
+    solve is one CUDA graph launch (device buffers only)."""
     host = isinstance(b, np.ndarray) or (hasattr(b, "is_cuda") and not b.is_cuda)
-    d = fgmres_desc(float(rtol), int(maxit), int(rel_to), 1 if host else 0)
+    d = fgmres_desc(float(rtol), int(maxit), int(rel_to), 1 if host else 0, LOOP[loop])
     info = fgmres_info()
     hist = np.zeros(maxit + 1) if history else None
     if host:
@@ -448,8 +455,9 @@ def fgmres_solve(sys: System, h: Hierarchy, b, x, rtol=1e-10, maxit=60, rel_to=0
 
 
 def fgmres_solve_batched(systems, hierarchies, bs, xs, rtol=1e-10, maxit=60, rel_to=0, stream=None,
-                         raise_on_noconv=False) -> list:
-    """Solve many independent systems together; bs, xs are lists of CUDA tensors."""
+                         raise_on_noconv=False, loop="host") -> list:
+    """Solve many independent systems together; bs, xs are lists of CUDA tensors.  loop
+    "device": the whole batch is one CUDA graph launch."""
     n = len(systems)
     assert n == len(hierarchies) == len(bs) == len(xs) and n >= 1
     arr = _vp * n
@@ -458,7 +466,7 @@ def fgmres_solve_batched(systems, hierarchies, bs, xs, rtol=1e-10, maxit=60, rel
     ba = arr(*[_dev(b) for b in bs])
     xa = arr(*[_dev(x) for x in xs])
     infos = (fgmres_info * n)()
-    d = fgmres_desc(float(rtol), int(maxit), int(rel_to), 0)
+    d = fgmres_desc(float(rtol), int(maxit), int(rel_to), 0, LOOP[loop])
     st = _lib.fgmres_solve_batched(n, sysa, hiera, ba, xa, C.byref(d), infos, _stream(stream))
     if st not in (IB_OK, IB_ERR_NOCONV) or (st == IB_ERR_NOCONV and raise_on_noconv):
         raise IBError(st, "fgmres_solve_batched")
@@ -508,6 +516,14 @@ class IBNet:
     def set_params(self, p: np.ndarray):
         p = np.ascontiguousarray(p, dtype=np.float32)
         _check(_lib.ibnet_set_params(self._h, _vp(p.ctypes.data)), "ibnet_set_params")
+
+    def inner(self, a, b, stream=None) -> float:
+        """<a, b> of two FP32 device tensors, accumulated in FP64."""
+        assert a.numel() == b.numel()
+        out = C.c_double()
+        _check(_lib.ibnet_inner(self._h, a.numel(), _devf(a), _devf(b), C.byref(out), _stream(stream)),
+               "ibnet_inner")
+        return out.value
 
     def forward(self, x, out, batch, N, stream=None):
         _check(_lib.ibnet_forward(self._h, _devf(x), _devf(out), batch, N, _stream(stream)), "ibnet_forward")

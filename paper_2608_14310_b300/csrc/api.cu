@@ -15,8 +15,17 @@ static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
 void set_error(const std::string& msg) { g_last_error = msg; }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(); }
+static std::atomic<uint64_t> g_uid{0};
+uint64_t next_uid() { return g_uid.fetch_add(1, std::memory_order_relaxed) + 1; }
 ib_status fgmres_run(const ib_system* sys, cav_hierarchy* H, const double* b, double* x, const fgmres_desc* d,
                      fgmres_info* info, double* history, cudaStream_t st);
+ib_status fgmres_run_device(const ib_system* sys, cav_hierarchy* H, const double* b, double* x,
+                            const fgmres_desc* d, fgmres_info* info, double* history, cudaStream_t st);
+ib_status fgmres_run_batched_device(int count, const ib_system* const* sys, cav_hierarchy* const* H,
+                                    const double* const* b, double* const* x, const fgmres_desc* d,
+                                    fgmres_info* infos, cudaStream_t st);
 ib_status fgmres_run_batched(int count, const ib_system* const* sys, cav_hierarchy* const* H,
                              const double* const* b, double* const* x, const fgmres_desc* d,
                              fgmres_info* infos, cudaStream_t st);
@@ -42,7 +51,7 @@ using namespace cav;
 extern "C" {
 
 const char* ib_last_error(void) { return g_last_error.c_str(); }
-int ib_abi_version(void) { return 4; }
+int ib_abi_version(void) { return 5; }
 int64_t ib_launch_count(void) { return g_launches.load(); }
 
 ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaStream_t st, ib_system** out) {
@@ -70,6 +79,7 @@ ib_status ib_setup(const ib_grid_desc* grid, const ib_structure_desc* sd, cudaSt
   CAV_REQUIRE(sd->M == 0 || (sd->X && sd->omega), "ib_setup: X and omega are required when M > 0");
   CAV_REQUIRE(sd->law >= IB_FORCE_TARGET && sd->law <= IB_FORCE_FIBER, "ib_setup: unknown force law");
   s = new ib_system();
+  s->uid = next_uid();
   s->N = grid->N;
   s->L = grid->L;
   s->h = grid->L / grid->N;
@@ -170,7 +180,10 @@ ib_status ib_update_structure(ib_system* s, const ib_structure_desc* sd, cudaStr
   ib_system* fresh = nullptr;
   const ib_status r = ib_setup(&g, sd, st, &fresh);
   if (r != IB_OK) return r;  // the handle keeps its previous configuration
+  const uint64_t uid = s->uid, epoch = s->epoch;
   std::swap(*s, *fresh);
+  s->uid = uid;  // the same handle, new buffers: solve graphs built with it are rebuilt
+  s->epoch = epoch + 1;
   ib_destroy(fresh);  // now holds the previous configuration's device memory
   return IB_OK;
   CAV_API_END
@@ -281,6 +294,7 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
                 "cav_setup: the coloured (multiplicative) smoother needs FP32 or FP64 patch inverses: with "
                 "BF16-rounded inverses the undamped sweep diverges");
     H = new cav_hierarchy();
+    H->uid = next_uid();
     H->sys = s;
     H->desc = *d;
     H->grid_N = s->N;
@@ -291,7 +305,9 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
     H->grid_dt = s->dt;
     H->status = H->arena.alloc<int>(1);
     H->flag = H->arena.alloc<int>(1);
+    H->gbar = H->arena.alloc<unsigned>(2);
     CAV_CHECK_CUDA(cudaMemsetAsync(H->status, 0, sizeof(int), st));
+    CAV_CHECK_CUDA(cudaMemsetAsync(H->gbar, 0, 2 * sizeof(unsigned), st));
     build_levels(H, st);
     *out = H;
     return IB_OK;
@@ -319,6 +335,7 @@ ib_status cav_refactor(cav_hierarchy* h, const ib_system* s, cudaStream_t st) {
     return IB_ERR_INVALID;
   }
   refactor_levels(h, s, st);
+  ++h->epoch;  // a cached solve graph may hold the previous values (e.g. kernel arguments)
   return IB_OK;
   CAV_API_END
 }
@@ -367,6 +384,9 @@ ib_status cav_get_level_info(const cav_hierarchy* h, int32_t level, cav_level_in
     info->apply_variant = lv.apply_variant;
     for (int v = 0; v < 5; ++v) info->apply_us[v] = lv.apply_us[v];
     info->n_colours = lv.n_colours;
+    info->sweep_form = lv.fused;
+    info->sweep_us[0] = lv.sweep_us[0];
+    info->sweep_us[1] = lv.sweep_us[1];
   }
   return IB_OK;
   CAV_API_END
@@ -568,6 +588,10 @@ void cav_destroy(cav_hierarchy* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   vcycle_release(h);
+  dl_plan_free(h->dl_plan);
+  if (h->dl_stream) cudaStreamDestroy(h->dl_stream);
+  if (h->dl_body_stream) cudaStreamDestroy(h->dl_body_stream);
+  if (h->dl_host) cudaFreeHost(h->dl_host);
   for (auto& e : h->fg_ev)
     if (e) cudaEventDestroy(e);
   if (h->solve_stream) cudaStreamDestroy(h->solve_stream);
@@ -585,8 +609,11 @@ ib_status fgmres_solve(const ib_system* s, const cav_hierarchy* h, const double*
   CAV_REQUIRE(h->sys == s, "fgmres_solve: hierarchy was built for another system");
   CAV_REQUIRE(d->maxit >= 1 && d->maxit <= 4096, "fgmres_solve: maxit must be in [1, 4096]");
   CAV_REQUIRE(d->rtol >= 0 && std::isfinite(d->rtol), "fgmres_solve: bad rtol");
+  CAV_REQUIRE(d->loop == 0 || d->loop == 1, "fgmres_solve: loop must be 0 or 1");
+  CAV_REQUIRE(!(d->loop == 1 && d->host_io), "fgmres_solve: the device-driven loop takes device buffers only");
   std::memset(info, 0, sizeof(*info));
-  ib_status r = fgmres_run(s, const_cast<cav_hierarchy*>(h), b, x, d, info, history, st);
+  ib_status r = d->loop ? fgmres_run_device(s, const_cast<cav_hierarchy*>(h), b, x, d, info, history, st)
+                        : fgmres_run(s, const_cast<cav_hierarchy*>(h), b, x, d, info, history, st);
   // a stop before maxit (a non-finite preconditioned vector) already left its own message
   if (r == IB_ERR_NOCONV && info->iters >= d->maxit) set_error("fgmres_solve: maxit reached above tolerance");
   return r;
@@ -601,6 +628,7 @@ ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
   CAV_REQUIRE(d->maxit >= 1 && d->maxit <= 4096, "fgmres_solve_batched: maxit must be in [1, 4096]");
   CAV_REQUIRE(d->rtol >= 0 && std::isfinite(d->rtol), "fgmres_solve_batched: bad rtol");
   CAV_REQUIRE(!d->host_io, "fgmres_solve_batched: device buffers only");
+  CAV_REQUIRE(d->loop == 0 || d->loop == 1, "fgmres_solve_batched: loop must be 0 or 1");
   std::vector<cav_hierarchy*> H(count);
   for (int i = 0; i < count; ++i) {
     CAV_REQUIRE(systems[i] && hierarchies[i] && b[i] && x[i], "fgmres_solve_batched: NULL entry");
@@ -610,7 +638,8 @@ ib_status fgmres_solve_batched(int32_t count, const ib_system* const* systems,
     H[i] = const_cast<cav_hierarchy*>(hierarchies[i]);
     std::memset(&infos[i], 0, sizeof(fgmres_info));
   }
-  ib_status r = fgmres_run_batched(count, systems, H.data(), b, x, d, infos, st);
+  ib_status r = d->loop ? fgmres_run_batched_device(count, systems, H.data(), b, x, d, infos, st)
+                        : fgmres_run_batched(count, systems, H.data(), b, x, d, infos, st);
   if (r == IB_ERR_NOCONV) set_error("fgmres_solve_batched: some systems stopped above tolerance");
   return r;
   CAV_API_END

@@ -56,12 +56,16 @@ __device__ inline double warp_sum8_transposed(double* v) {
 
 // partial[i * gridDim.x + bx] = chunk bx's share of <V_i, w> for i < kcount.  Block (bx, g)
 // takes vectors 8g .. 8g+7, so w is read once per eight vectors; per vector the chunk's sum
-// is a fixed per-warp tree, then the eight warp sums in warp order.
+// is a fixed per-warp tree, then the eight warp sums in warp order.  kdev (nullable): kcount
+// = *kdev + 1, the iteration index read from device memory (a graph's fixed grid covers
+// every iteration; blocks past kcount exit).
 __global__ void __launch_bounds__(FG_THREADS)
 k_multi_dot(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ w,
-            double* __restrict__ partial) {
+            double* __restrict__ partial, const int* __restrict__ kdev) {
   pdl_wait();  // programmatic launch: the kernel ahead (which writes w or V) has finished
   pdl_trigger();
+  if (kdev) kcount = *kdev + 1;
+  if ((int)blockIdx.y * DOT_GROUP >= kcount) return;
   __shared__ double sm[DOT_GROUP][FG_THREADS / 32];
   const int64_t base = (int64_t)blockIdx.x * DOT_CHUNK + threadIdx.x;
   double wr[DOT_PER_THREAD];
@@ -107,12 +111,19 @@ k_multi_dot(const double* __restrict__ V, int64_t n, int kcount, const double* _
   }
 }
 
-// out[i] = sum_b partial[i * nb + b] (fixed order); add_to (nullable) += out
-__global__ void k_finalize(const double* __restrict__ partial, int nb, double* out, double* add_to) {
+// out[i] = sum_b partial[i * nb + b] (fixed order); add_to (nullable) += out.  kdev
+// (nullable): only blocks i <= *kdev run, and add_to is offset by *kdev * add_stride.
+__global__ void k_finalize(const double* __restrict__ partial, int nb, double* out, double* add_to,
+                           const int* __restrict__ kdev, int64_t add_stride) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sm[FG_THREADS / 32];
   const int i = blockIdx.x;
+  if (kdev) {
+    const int k = *kdev;
+    if (i > k) return;
+    if (add_to) add_to += (int64_t)k * add_stride;
+  }
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(int64_t)i * nb + b];
   s = block_sum(s, sm);
@@ -125,12 +136,14 @@ __global__ void k_finalize(const double* __restrict__ partial, int nb, double* o
 // SIGN = -1: w -= sum_{i < kcount} c[i] V_i;  SIGN = +1: w += sum_{i < kcount} c[i] V_i.
 // Per element the sum runs over i in ascending order.  sq_partial (nullable) receives the
 // chunk's share of ||w_new||^2 (block_sum order).
+// kdev (nullable): kcount = *kdev + kadd.
 template <int SIGN>
 __global__ void __launch_bounds__(FG_THREADS)
 k_combine(const double* __restrict__ V, int64_t n, int kcount, const double* __restrict__ c,
-          double* __restrict__ w, double* __restrict__ sq_partial) {
+          double* __restrict__ w, double* __restrict__ sq_partial, const int* __restrict__ kdev, int kadd) {
   pdl_wait();
   pdl_trigger();
+  if (kdev) kcount = *kdev + kadd;
   __shared__ double sm[FG_THREADS / 32];
   const int64_t base = (int64_t)blockIdx.x * CMB_CHUNK + threadIdx.x;
   double acc[CMB_PER_THREAD];
@@ -210,9 +223,10 @@ __global__ void k_init_beta(double* S, FgLayout L) {
 // The rotations are a serial chain; the column and the rotation pairs are staged in shared
 // memory first (all threads), so the chain runs on shared-memory latency, not L2 latency.
 constexpr int GIVENS_SMEM_MAX = 1024;
-__global__ void k_givens(double* S, FgLayout L, int k) {
+__global__ void k_givens(double* S, FgLayout L, int k, const int* __restrict__ kdev) {
   pdl_wait();
   pdl_trigger();
+  if (kdev) k = *kdev;
   __shared__ double sh[3 * GIVENS_SMEM_MAX];
   double* Hg = S + L.H + (int64_t)k * (L.maxit + 1);
   double* csg = S + L.cs;
@@ -258,7 +272,10 @@ __global__ void k_givens(double* S, FgLayout L, int k) {
     for (int i = threadIdx.x; i <= k + 1; i += blockDim.x) Hg[i] = Hk[i];
 }
 
-__global__ void k_trisolve(double* S, FgLayout L, int k) {
+__global__ void k_trisolve(double* S, FgLayout L, int k, const int* __restrict__ kdev) {
+  pdl_wait();
+  pdl_trigger();
+  if (kdev) k = *kdev;
   const double* H = S + L.H;
   const double* g = S + L.g;
   double* y = S + L.y;
@@ -279,6 +296,10 @@ static void ensure_workspace(cav_hierarchy* H, int maxit, int64_t n) {
   if (H->ws_maxit >= maxit) return;
   if (H->host_b) cudaFreeHost(H->host_b);
   H->host_b = nullptr;
+  if (H->dl_host) cudaFreeHost(H->dl_host);
+  H->dl_host = nullptr;
+  dl_plan_free(H->dl_plan);  // its graph refers to the buffers released below
+  H->dl_plan = nullptr;
   H->ws_arena.release();
   H->V = H->ws_arena.alloc<double>((size_t)(maxit + 1) * n);
   H->Z = H->ws_arena.alloc<double>((size_t)maxit * n);
@@ -290,6 +311,10 @@ static void ensure_workspace(cav_hierarchy* H, int maxit, int64_t n) {
   H->red_partial = H->ws_arena.alloc<double>((size_t)(maxit + 2) * nbmax);
   H->io_b = H->ws_arena.alloc<double>(n);
   H->io_x = H->ws_arena.alloc<double>(n);
+  H->dl_w = H->ws_arena.alloc<double>(n);
+  H->dl_kc = H->ws_arena.alloc<int>(8);
+  H->dl_hist = H->ws_arena.alloc<double>((size_t)maxit + 1);
+  CAV_CHECK_CUDA(cudaMallocHost(&H->dl_host, sizeof(double) * (32 + (size_t)maxit + 1)));
   if (!H->fg_ev[0]) {
     CAV_CHECK_CUDA(cudaEventCreateWithFlags(&H->fg_ev[0], cudaEventDisableTiming));
     CAV_CHECK_CUDA(cudaEventCreateWithFlags(&H->fg_ev[1], cudaEventDisableTiming));
@@ -303,9 +328,9 @@ void krylov_reserve(cav_hierarchy* H, int maxit, int64_t n) { ensure_workspace(H
 static void dot_to(const cav_hierarchy* H, const double* a, const double* b, int64_t n, double* out,
                    cudaStream_t st) {
   const int nb = dot_blocks(n);
-  k_multi_dot<<<dim3(nb, 1), FG_THREADS, 0, st>>>(a, n, 1, b, H->red_partial);
+  k_multi_dot<<<dim3(nb, 1), FG_THREADS, 0, st>>>(a, n, 1, b, H->red_partial, nullptr);
   CAV_CHECK_LAUNCH();
-  k_finalize<<<1, FG_THREADS, 0, st>>>(H->red_partial, nb, out, nullptr);
+  k_finalize<<<1, FG_THREADS, 0, st>>>(H->red_partial, nb, out, nullptr, nullptr, 0);
   CAV_CHECK_LAUNCH();
 }
 
@@ -408,15 +433,15 @@ static void fg_issue(FgState& s, int k) {
   const double* Vc = H->V;
   for (int pass = 0; pass < 2; ++pass) {
     launch_k(k_multi_dot, dim3(s.nb, div_up(k + 1, DOT_GROUP)), dim3(FG_THREADS), 0, s.st, true, Vc, n, k + 1,
-             (const double*)w, H->red_partial);
+             (const double*)w, H->red_partial, (const int*)nullptr);
     launch_k(k_finalize, dim3(k + 1), dim3(FG_THREADS), 0, s.st, true, (const double*)H->red_partial, s.nb,
-             S + s.L.h, S + s.L.H + (int64_t)k * (maxit + 1));
+             S + s.L.h, S + s.L.H + (int64_t)k * (maxit + 1), (const int*)nullptr, (int64_t)0);
     launch_k(k_combine<-1>, dim3(s.cb), dim3(FG_THREADS), 0, s.st, true, Vc, n, k + 1, (const double*)(S + s.L.h),
-             w, pass == 1 ? sq_partial : nullptr);
+             w, pass == 1 ? sq_partial : nullptr, (const int*)nullptr, 0);
   }
   launch_k(k_finalize, dim3(1), dim3(FG_THREADS), 0, s.st, true, (const double*)sq_partial, s.cb, misc + 2,
-           (double*)nullptr);
-  launch_k(k_givens, dim3(1), dim3(128), 0, s.st, true, S, s.L, k);
+           (double*)nullptr, (const int*)nullptr, (int64_t)0);
+  launch_k(k_givens, dim3(1), dim3(128), 0, s.st, true, S, s.L, k, (const int*)nullptr);
   launch_k(k_scale, dim3(s.vb), dim3(FG_THREADS), 0, s.st, true, (const double*)w, n, (const double*)(misc + 5), w);
   CAV_CHECK_CUDA(cudaMemcpyAsync(H->host_b + 8 + (k & 1), misc + 4, sizeof(double), cudaMemcpyDeviceToHost, s.st));
   CAV_CHECK_CUDA(cudaEventRecord(H->fg_ev[k & 1], s.st));
@@ -472,9 +497,9 @@ static void fg_finish(FgState& s) {
   double* S = H->dev_scalars;
   double* misc = S + s.L.misc;
   if (s.k_done > 0) {
-    k_trisolve<<<1, 1, 0, s.st>>>(S, s.L, s.k_done);
+    k_trisolve<<<1, 1, 0, s.st>>>(S, s.L, s.k_done, nullptr);
     CAV_CHECK_LAUNCH();
-    k_combine<1><<<s.cb, FG_THREADS, 0, s.st>>>(H->Z, s.n, s.k_done, S + s.L.y, s.x, nullptr);
+    k_combine<1><<<s.cb, FG_THREADS, 0, s.st>>>(H->Z, s.n, s.k_done, S + s.L.y, s.x, nullptr, nullptr, 0);
     CAV_CHECK_LAUNCH();
   }
   const Level& l0 = H->levels[0];
@@ -573,6 +598,418 @@ ib_status fgmres_run_batched(int count, const ib_system* const* sys, cav_hierarc
     all = (r == IB_OK) && all;
   }
   cudaEventDestroy(start_ev);
+  if (failure != IB_OK) return failure;
+  return all ? IB_OK : IB_ERR_NOCONV;
+}
+
+// ------------------------------------------------------------------ device-driven iterations
+//
+// fgmres_desc.loop = 1: a whole solve is one CUDA graph: the prologue (r_0, the norms, V_0),
+// a conditional while node whose body is one FGMRES iteration (copy V_k in, the V-cycle, K_E
+// z_k, CGS2, ||w||, Givens, V_{k+1} and Z_k stored, the convergence test), and the epilogue
+// (y = H^-1 g, x += Z y, the true residual, the records copied to pinned host memory).  The
+// body's kernels read the iteration index k from device memory; the test kernel ends the loop
+// through cudaGraphSetConditional, so no host round trip separates two iterations.  A batch
+// of systems is one graph whose branches are the systems' solves: every system runs its own
+// loop and stops at its own convergence.  The arithmetic is the host-driven loop's, kernel for
+// kernel, so the results are bitwise the same.
+
+// kc (ints): [0] body executions so far = the iteration index k, [1] iterations kept (k_done),
+// [2] converged, [3] iteration whose residual estimate was not finite (-1: none).
+// misc (doubles): [7] ||ref||, [8] the last relative residual estimate.
+
+__global__ void k_dl_init(double* S, FgLayout L, int rel_to, double rtol, int* kc, double* hist,
+                          cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  pdl_trigger();
+  double* misc = S + L.misc;
+  const double bnorm = sqrt(misc[0]), beta = sqrt(misc[1]);
+  const double ref = (rel_to == 1) ? beta : bnorm;
+  misc[3] = (beta > 0.0) ? 1.0 / beta : 0.0;
+  S[L.g] = beta;
+  misc[7] = ref;
+  const double est = (ref > 0.0) ? beta / ref : 0.0;
+  misc[8] = est;
+  hist[0] = est;
+  const bool done = !(ref > 0.0) || beta <= rtol * ref;
+  kc[0] = 0;
+  kc[1] = 0;
+  kc[2] = done ? 1 : 0;
+  kc[3] = -1;
+  cudaGraphSetConditional(cond, done ? 0u : 1u);
+}
+
+// dst = V_k
+__global__ void k_dl_copy_in(const double* __restrict__ V, int64_t n, const int* __restrict__ kc,
+                             double* __restrict__ dst) {
+  pdl_wait();
+  pdl_trigger();
+  const double* src = V + (int64_t)kc[0] * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+// V_{k+1} = w * scale[0] and Z_k = z
+__global__ void k_dl_store(const double* __restrict__ w, int64_t n, const double* __restrict__ scale,
+                           double* __restrict__ V, const double* __restrict__ z, double* __restrict__ Z,
+                           const int* __restrict__ kc) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t k = kc[0];
+  const double s = scale[0];
+  double* v = V + (k + 1) * n;
+  double* zk = Z + k * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    v[e] = w[e] * s;
+    zk[e] = z[e];
+  }
+}
+
+// the convergence test of iteration k, as fg_check makes it
+__global__ void k_dl_check(double* S, FgLayout L, double rtol, int maxit, int* kc, double* hist,
+                           cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  pdl_trigger();
+  double* misc = S + L.misc;
+  const int k = kc[0];
+  const double gk = misc[4], ref = misc[7];
+  bool stop;
+  if (!isfinite(gk)) {
+    kc[3] = k;  // keep the k iterations before it
+    kc[1] = k;
+    stop = true;
+  } else {
+    kc[1] = k + 1;
+    const double est = gk / ref;
+    misc[8] = est;
+    hist[k + 1] = est;
+    const bool conv = gk <= rtol * ref;
+    kc[2] = conv ? 1 : 0;
+    stop = conv || k + 1 >= maxit;
+  }
+  kc[0] = k + 1;
+  cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
+struct DlPlan {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> key;
+  std::vector<cudaEvent_t> events;   // fork / join of a batch's branches (capture only)
+  // kernels per system: prologue + epilogue, and per body execution (launch accounting)
+  std::vector<int> k_fixed, k_body;
+};
+
+void dl_plan_free(DlPlan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  for (auto& e : p->events) cudaEventDestroy(e);
+  delete p;
+}
+
+static void dl_key_add(std::vector<uint64_t>& key, const FgState& s) {
+  key.push_back(s.H->uid);
+  key.push_back(s.H->epoch);
+  key.push_back(s.sys->uid);
+  key.push_back(s.sys->epoch);
+  key.push_back((uint64_t)(uintptr_t)s.b_user);
+  key.push_back((uint64_t)(uintptr_t)s.x_user);
+  key.push_back((uint64_t)(uintptr_t)s.H->V);
+}
+
+static std::vector<uint64_t> dl_key(const std::vector<FgState>& S, const fgmres_desc* d) {
+  std::vector<uint64_t> key;
+  uint64_t rt = 0;
+  std::memcpy(&rt, &d->rtol, sizeof(rt));
+  key.push_back(rt);
+  key.push_back((uint64_t)d->maxit);
+  key.push_back((uint64_t)d->rel_to);
+  key.push_back(S.size());
+  for (const FgState& s : S) dl_key_add(key, s);
+  return key;
+}
+
+// One system's solve captured on cs (already capturing); the loop body is captured into the
+// conditional node's body graph on bs.  Returns the kernels of the prologue and epilogue and
+// those of one body execution.
+static void dl_capture_system(FgState& s, cudaStream_t cs, cudaStream_t bs, int& k_fixed, int& k_body) {
+  cav_hierarchy* H = s.H;
+  const Level& l0 = H->levels[0];
+  s.n = 3LL * l0.N * l0.N;
+  s.L = FgLayout(s.d->maxit);
+  s.b = s.b_user;
+  s.x = s.x_user;
+  s.op = LevelOps{l0.N, l0.h, l0.rho_dt, l0.mu, l0.dt, &s.sys->ee, l0.channel};
+  s.nb = dot_blocks(s.n);
+  s.cb = cmb_blocks(s.n);
+  s.nbmax = s.nb > s.cb ? s.nb : s.cb;
+  if (reduce_blocks(s.n) > s.nbmax) s.nbmax = reduce_blocks(s.n);
+  s.vb = vec_blocks(s.n);
+  const int64_t n = s.n;
+  const int maxit = s.d->maxit;
+  double* S = H->dev_scalars;
+  double* misc = S + s.L.misc;
+  int* kc = H->dl_kc;
+
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  CAV_CHECK_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  CAV_REQUIRE(cst == cudaStreamCaptureStatusActive && g, "fgmres: device loop capture is not active");
+  cudaGraphConditionalHandle cond;
+  CAV_CHECK_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+
+  const int64_t c0 = launch_count();
+  // prologue (fg_start and fg_begin)
+  CAV_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * s.L.total, cs));
+  launch_apply(s.op, s.x, s.b, H->V, 0, cs);  // r0 -> V_0
+  dot_to(H, s.b, s.b, n, misc + 0, cs);
+  dot_to(H, H->V, H->V, n, misc + 1, cs);
+  launch_k(k_dl_init, dim3(1), dim3(1), 0, cs, true, S, s.L, s.d->rel_to, s.d->rtol, kc, H->dl_hist, cond);
+  launch_k(k_scale, dim3(s.vb), dim3(FG_THREADS), 0, cs, true, (const double*)H->V, n, (const double*)(misc + 3),
+           H->V);
+
+  // the loop
+  CAV_CHECK_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, &edata, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode = nullptr;
+  CAV_CHECK_CUDA(cudaGraphAddNode(&cnode, g, deps, edata, ndeps, &cp));
+  CAV_CHECK_CUDA(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+  const int64_t c1 = launch_count();
+  CAV_CHECK_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  bool body_ok = true;
+  try {
+    double* w = H->dl_w;
+    double* sq_partial = H->red_partial + (int64_t)(maxit + 1) * s.nbmax;
+    launch_k(k_dl_copy_in, dim3(s.vb), dim3(FG_THREADS), 0, bs, false, (const double*)H->V, n, (const int*)kc, l0.b);
+    H->no_events = 1;
+    vcycle_inline(H, bs);
+    H->no_events = 0;
+    launch_apply(s.op, l0.x, nullptr, w, 1, bs, true);
+    const double* Vc = H->V;
+    const int gy = div_up(maxit, DOT_GROUP);  // k + 1 <= maxit vectors
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_k(k_multi_dot, dim3(s.nb, gy), dim3(FG_THREADS), 0, bs, true, Vc, n, 0, (const double*)w,
+               H->red_partial, (const int*)kc);
+      launch_k(k_finalize, dim3(maxit), dim3(FG_THREADS), 0, bs, true, (const double*)H->red_partial, s.nb,
+               S + s.L.h, S + s.L.H, (const int*)kc, (int64_t)(maxit + 1));
+      launch_k(k_combine<-1>, dim3(s.cb), dim3(FG_THREADS), 0, bs, true, Vc, n, 0, (const double*)(S + s.L.h), w,
+               pass == 1 ? sq_partial : nullptr, (const int*)kc, 1);
+    }
+    launch_k(k_finalize, dim3(1), dim3(FG_THREADS), 0, bs, true, (const double*)sq_partial, s.cb, misc + 2,
+             (double*)nullptr, (const int*)nullptr, (int64_t)0);
+    launch_k(k_givens, dim3(1), dim3(128), 0, bs, true, S, s.L, 0, (const int*)kc);
+    launch_k(k_dl_store, dim3(s.vb), dim3(FG_THREADS), 0, bs, true, (const double*)w, n, (const double*)(misc + 5),
+             H->V, (const double*)l0.x, H->Z, (const int*)kc);
+    launch_k(k_dl_check, dim3(1), dim3(1), 0, bs, true, S, s.L, s.d->rtol, maxit, kc, H->dl_hist, cond);
+  } catch (...) {
+    body_ok = false;
+  }
+  H->no_events = 0;
+  cudaGraph_t body_out = nullptr;
+  const cudaError_t be = cudaStreamEndCapture(bs, &body_out);
+  if (!body_ok) throw Fail{IB_ERR_CUDA};
+  if (be != cudaSuccess) {
+    set_error(std::string("fgmres: capturing the loop body: ") + cudaGetErrorString(be));
+    throw Fail{IB_ERR_CUDA};
+  }
+  const int64_t c2 = launch_count();
+
+  // epilogue (fg_finish)
+  launch_k(k_trisolve, dim3(1), dim3(1), 0, cs, false, S, s.L, 0, (const int*)(kc + 1));
+  launch_k(k_combine<1>, dim3(s.cb), dim3(FG_THREADS), 0, cs, true, (const double*)H->Z, n, 0,
+           (const double*)(S + s.L.y), s.x, (double*)nullptr, (const int*)(kc + 1), 0);
+  launch_apply(s.op, s.x, s.b, l0.r, 0, cs, true);  // true residual at exit
+  dot_to(H, l0.r, l0.r, n, misc + 6, cs);
+  double* hb = H->dl_host;
+  CAV_CHECK_CUDA(cudaMemcpyAsync(hb, misc, sizeof(double) * 16, cudaMemcpyDeviceToHost, cs));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(hb + 16, kc, sizeof(int) * 8, cudaMemcpyDeviceToHost, cs));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(hb + 20, H->status, sizeof(int), cudaMemcpyDeviceToHost, cs));
+  CAV_CHECK_CUDA(cudaMemcpyAsync(hb + 32, H->dl_hist, sizeof(double) * (maxit + 1), cudaMemcpyDeviceToHost, cs));
+  const int64_t c3 = launch_count();
+  k_fixed = (int)((c1 - c0) + (c3 - c2));
+  k_body = (int)(c2 - c1);
+  note_launches(-(long long)(c3 - c0));  // recorded, not run
+}
+
+// After the graph ran: the results as fg_result reports them.
+static ib_status dl_result(FgState& s) {
+  const double* hb = s.H->dl_host;
+  const int* kc = reinterpret_cast<const int*>(hb + 16);
+  const double* misc = hb;
+  s.k_done = kc[1];
+  s.converged = kc[2] != 0;
+  s.nonfinite = kc[3];
+  s.est = misc[8];
+  const double ref = misc[7];
+  s.info->iters = s.k_done;
+  s.info->converged = s.converged ? 1 : 0;
+  s.info->relres_est = s.est;
+  s.info->relres_true = (ref > 0) ? std::sqrt(misc[6]) / ref : 0.0;
+  if (s.history)
+    for (int i = 0; i <= s.k_done; ++i) s.history[i] = hb[32 + i];
+  if (s.nonfinite >= 0)
+    set_error("fgmres_solve: the preconditioned vector of iteration " + std::to_string(s.nonfinite) +
+              " is not finite (the V-cycle diverged; with the coloured smoother this happens when "
+              "rounded FP32 inverses of very ill-conditioned patches make the undamped sweep "
+              "diverge: use FP64 inverses); x holds the iterate before it");
+  const int code = *reinterpret_cast<const int*>(hb + 20);
+  if (code != DEV_OK) {
+    CAV_CHECK_CUDA(cudaMemsetAsync(s.H->status, 0, sizeof(int), s.st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(s.st));
+    set_error("fgmres_solve: " + status_message(code));
+    return status_of(code);
+  }
+  return s.converged ? IB_OK : IB_ERR_NOCONV;
+}
+
+// Ends whatever capture is still open on the plan's streams after a failure.
+static void dl_abort_capture(cudaStream_t origin, cudaStream_t bs, const std::vector<cudaStream_t>& branches) {
+  cudaStreamCaptureStatus cst;
+  if (cudaStreamIsCapturing(bs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(bs, &g);
+  }
+  if (cudaStreamIsCapturing(origin, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(origin, &g);
+    if (g) cudaGraphDestroy(g);
+  }
+  for (cudaStream_t b : branches) {
+    if (cudaStreamIsCapturing(b, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(b, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+  }
+  cudaGetLastError();
+}
+
+// Capture and instantiate the solves of S (one branch each) as one graph.
+static DlPlan* dl_build(std::vector<FgState>& S, cudaStream_t origin, cudaStream_t bs, bool pdl) {
+  DlPlan* plan = new DlPlan();
+  const int count = (int)S.size();
+  plan->k_fixed.assign(count, 0);
+  plan->k_body.assign(count, 0);
+  std::vector<cudaStream_t> branches;
+  const bool old_off = pdl_off();
+  pdl_off() = !pdl;
+  cudaGraph_t graph = nullptr;
+  try {
+    if (count > 1) {  // streams and events exist before the capture starts
+      plan->events.resize(count + 1, nullptr);
+      for (auto& e : plan->events) CAV_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      for (int i = 0; i < count; ++i) {
+        cav_hierarchy* H = S[i].H;
+        if (!H->solve_stream) CAV_CHECK_CUDA(cudaStreamCreateWithFlags(&H->solve_stream, cudaStreamNonBlocking));
+      }
+    }
+    CAV_CHECK_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+    if (count == 1) {
+      dl_capture_system(S[0], origin, bs, plan->k_fixed[0], plan->k_body[0]);
+    } else {
+      CAV_CHECK_CUDA(cudaEventRecord(plan->events[0], origin));
+      for (int i = 0; i < count; ++i) {
+        cav_hierarchy* H = S[i].H;
+        branches.push_back(H->solve_stream);
+        CAV_CHECK_CUDA(cudaStreamWaitEvent(H->solve_stream, plan->events[0], 0));
+        dl_capture_system(S[i], H->solve_stream, bs, plan->k_fixed[i], plan->k_body[i]);
+        CAV_CHECK_CUDA(cudaEventRecord(plan->events[i + 1], H->solve_stream));
+        CAV_CHECK_CUDA(cudaStreamWaitEvent(origin, plan->events[i + 1], 0));
+      }
+    }
+    CAV_CHECK_CUDA(cudaStreamEndCapture(origin, &graph));
+    CAV_CHECK_CUDA(cudaGraphInstantiate(&plan->exec, graph, 0));
+    cudaGraphDestroy(graph);
+  } catch (...) {
+    pdl_off() = old_off;
+    if (graph) cudaGraphDestroy(graph);
+    dl_abort_capture(origin, bs, branches);
+    dl_plan_free(plan);
+    throw;
+  }
+  pdl_off() = old_off;
+  return plan;
+}
+
+// Run the solves of S as one graph launch on st (built on first use, then cached in the first
+// system's hierarchy while the key -- systems, hierarchies, buffers, tolerances -- holds).
+static void dl_run(std::vector<FgState>& S, const fgmres_desc* d, cudaStream_t st) {
+  cav_hierarchy* H0 = S[0].H;
+  for (FgState& s : S) {
+    const Level& l0 = s.H->levels[0];
+    ensure_workspace(s.H, d->maxit, 3LL * l0.N * l0.N);
+  }
+  std::vector<uint64_t> key = dl_key(S, d);
+  if (!H0->dl_plan || H0->dl_plan->key != key) {
+    dl_plan_free(H0->dl_plan);
+    H0->dl_plan = nullptr;
+    if (!H0->dl_stream) CAV_CHECK_CUDA(cudaStreamCreateWithFlags(&H0->dl_stream, cudaStreamNonBlocking));
+    if (!H0->dl_body_stream) CAV_CHECK_CUDA(cudaStreamCreateWithFlags(&H0->dl_body_stream, cudaStreamNonBlocking));
+    DlPlan* plan = nullptr;
+    try {
+      plan = dl_build(S, H0->dl_stream, H0->dl_body_stream, true);
+    } catch (const Fail&) {
+      // programmatic edges inside a conditional body may be refused: build without them
+      plan = dl_build(S, H0->dl_stream, H0->dl_body_stream, false);
+    }
+    plan->key = key;
+    H0->dl_plan = plan;
+  }
+  DlPlan* plan = H0->dl_plan;
+  CAV_CHECK_CUDA(cudaGraphLaunch(plan->exec, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  long long kernels = 0;
+  for (size_t i = 0; i < S.size(); ++i) {
+    const int* kc = reinterpret_cast<const int*>(S[i].H->dl_host + 16);
+    kernels += plan->k_fixed[i] + (long long)kc[0] * plan->k_body[i];
+  }
+  note_launches(kernels);
+}
+
+ib_status fgmres_run_device(const ib_system* sys, cav_hierarchy* H, const double* b, double* x,
+                            const fgmres_desc* d, fgmres_info* info, double* history, cudaStream_t st) {
+  std::vector<FgState> S(1);
+  S[0].sys = sys;
+  S[0].H = H;
+  S[0].d = d;
+  S[0].info = info;
+  S[0].history = history;
+  S[0].st = st;
+  S[0].b_user = b;
+  S[0].x_user = x;
+  dl_run(S, d, st);
+  return dl_result(S[0]);
+}
+
+ib_status fgmres_run_batched_device(int count, const ib_system* const* sys, cav_hierarchy* const* H,
+                                    const double* const* b, double* const* x, const fgmres_desc* d,
+                                    fgmres_info* infos, cudaStream_t st) {
+  std::vector<FgState> S(count);
+  for (int i = 0; i < count; ++i) {
+    S[i].sys = sys[i];
+    S[i].H = H[i];
+    S[i].d = d;
+    S[i].info = &infos[i];
+    S[i].st = st;
+    S[i].b_user = b[i];
+    S[i].x_user = x[i];
+  }
+  dl_run(S, d, st);
+  bool all = true;
+  ib_status failure = IB_OK;
+  for (int i = 0; i < count; ++i) {
+    const ib_status r = dl_result(S[i]);
+    if (r != IB_OK && r != IB_ERR_NOCONV && failure == IB_OK) failure = r;
+    all = (r == IB_OK) && all;
+  }
   if (failure != IB_OK) return failure;
   return all ? IB_OK : IB_ERR_NOCONV;
 }

@@ -169,6 +169,31 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
     partial[blockIdx.x] = t;
   }
 }
+// <a, b> with FP64 products and sums: per-block partials in a fixed order, then their sum in
+// block order (reproducible).
+constexpr int IN_BLOCKS = 296;
+__global__ void k_inner(const float* __restrict__ a, const float* __restrict__ b, size_t n, double* __restrict__ partial) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s = fma((double)a[i], (double)b[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+__global__ void k_inner_sum(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += partial[i];
+    *out = t;
+  }
+}
+
 __global__ void k_sum_partials(const float* __restrict__ partial, int n, float scale, float* __restrict__ out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     float t = 0.f;
@@ -304,6 +329,7 @@ struct ibnet {
   float* gbuf[2] = {nullptr, nullptr};
   float* partial = nullptr;
   float* loss_dev = nullptr;
+  double* inner_partial = nullptr;    // [IN_BLOCKS + 1] (ibnet_inner), allocated on first use
 };
 
 static void net_workspace(ibnet* net, int B, int N) {
@@ -458,6 +484,7 @@ void ibnet_destroy(ibnet* net) {
   cudaDeviceSynchronize();
   net->ws.release();
   net->arena.release();
+  if (net->inner_partial) cudaFree(net->inner_partial);
   delete net;
 }
 
@@ -490,6 +517,22 @@ ib_status ibnet_forward(ibnet* net, const float* in, float* out, int32_t batch, 
   try {
     CAV_REQUIRE(net && in && out && batch >= 1 && N >= 1, "ibnet_forward: bad argument");
     net_forward(net, in, out, batch, N, st);
+    return IB_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+ib_status ibnet_inner(ibnet* net, int64_t n, const float* a, const float* b, double* out, cudaStream_t st) {
+  try {
+    CAV_REQUIRE(net && a && b && out && n >= 0, "ibnet_inner: bad argument");
+    if (!net->inner_partial) CAV_CHECK_CUDA(cudaMalloc(&net->inner_partial, sizeof(double) * (IN_BLOCKS + 1)));
+    k_inner<<<IN_BLOCKS, 256, 0, st>>>(a, b, (size_t)n, net->inner_partial);
+    CAV_CHECK_LAUNCH();
+    k_inner_sum<<<1, 32, 0, st>>>(net->inner_partial, IN_BLOCKS, net->inner_partial + IN_BLOCKS);
+    CAV_CHECK_LAUNCH();
+    CAV_CHECK_CUDA(cudaMemcpyAsync(out, net->inner_partial + IN_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
     return IB_OK;
   } catch (const Fail& f) {
     return f.st;

@@ -28,6 +28,12 @@ struct Fail {
   } while (0)
 // counts every kernel launch of the library (host side), for launch accounting
 void note_launch();
+// adds n (may be negative) to the count: kernels replayed inside graphs, or a capture's
+// launches taken back (a capture records kernels, it does not run them)
+void note_launches(long long n);
+int64_t launch_count();
+// a process-wide unique id for a handle (systems, hierarchies)
+uint64_t next_uid();
 #define CAV_CHECK_LAUNCH()                  \
   do {                                      \
     ::cav::note_launch();                   \
@@ -67,6 +73,8 @@ struct Arena {
 };
 
 // ------------------------------------------------------------------ E_E on one level
+
+struct DlPlan;  // a solve captured as a graph (fgmres.cu)
 
 // E_E restricted to its structurally nonzero velocity rows, each row's columns sorted.
 struct EECsr {
@@ -117,6 +125,8 @@ struct Level {
   int precision = CAV_PREC_FP64;
   int apply_variant = 0;         // patch-apply kernel variant (autotuned when requested)
   float apply_us[8] = {0};       // the autotuner's timing of each variant (us per launch)
+  int fused = 0;                 // 1: the additive sweep runs as one cooperative kernel
+  float sweep_us[2] = {0, 0};    // the autotuner's timing of one sweep: separate kernels, fused
   int64_t* inc_off = nullptr;    // [3 N^2 + 1] transpose incidence: slots of each unknown
   int* inc_slot = nullptr;       // [big_sum_n] packed-delta slots, ascending per unknown
   int n_touched = 0;             // unknowns held by at least one enlarged patch
@@ -187,6 +197,8 @@ struct ib_system {
   int64_t* fm_off = nullptr;     // [2 N^2 + 1] face -> markers whose support holds it
   int* fm_list = nullptr;        // ascending marker ids
   cav::EECsr ee;                 // finest-level E_E
+  uint64_t uid = 0;              // identity of the handle (kept by ib_update_structure)
+  uint64_t epoch = 0;            // bumped whenever ib_update_structure replaces the buffers
   int* status = nullptr;         // device status word
   double* partial = nullptr;     // [reduce_blocks(3 N^2) + 1] reduction scratch
 };
@@ -198,6 +210,8 @@ struct cav_hierarchy {
   cav::Arena arena;
   int* status = nullptr;
   int* flag = nullptr;           // device scratch word (pattern comparison)
+  uint64_t uid = 0;              // identity of the handle
+  uint64_t epoch = 0;            // bumped by cav_refactor (cached solve graphs are rebuilt)
   // the grid the hierarchy was built for (cav_refactor accepts only systems on the same grid;
   // the system it was built from may have been destroyed by then)
   int grid_N = 0, grid_bc = 0;
@@ -230,11 +244,31 @@ struct cav_hierarchy {
   std::vector<cudaEvent_t> vc_ev[2];  // event pairs around the finest-level applies
   int capturing = 0;                  // 0: not capturing, 1 + instance: capturing that instance
   int graph_failed = 0;
+  int vc_kernels[2] = {0, 0};         // kernels in each V-cycle graph (launch accounting)
+  unsigned* gbar = nullptr;           // [2] grid-barrier state of the fused sweep (count, generation)
+  int no_events = 0;                  // 1 while a solve graph is captured: no event records
+  // device-driven solves (fgmres_desc.loop = 1): scratch and the cached executable graph
+  double* dl_w = nullptr;             // [n] the new Krylov vector before normalisation
+  int* dl_kc = nullptr;               // [8] iteration counters
+  double* dl_hist = nullptr;          // [maxit + 1] residual estimates
+  double* dl_host = nullptr;          // pinned: [32] records + [maxit + 1] history
+  cav::DlPlan* dl_plan = nullptr;     // the last solve graph built with this hierarchy first
+  cudaStream_t dl_stream = nullptr, dl_body_stream = nullptr;
 };
 
 namespace cav {
 
+// a solve (or a batch of solves) captured as one executable graph (fgmres.cu)
+void dl_plan_free(DlPlan* p);
+
 // ------------------------------------------------------------------ kernels' host wrappers
+
+// While set on the calling thread, launch_k launches without the programmatic attribute
+// (a graph whose programmatic edges could not be instantiated is rebuilt this way).
+inline bool& pdl_off() {
+  static thread_local bool off = false;
+  return off;
+}
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -255,7 +289,7 @@ inline void launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cu
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = (pdl && !pdl_off()) ? 1 : 0;
   CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
   CAV_CHECK_LAUNCH();
 }
@@ -314,9 +348,15 @@ void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_collect(cav_hierarchy* H, long long upto = -1);
 void vcycle_release(cav_hierarchy* H);
 void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st);
+// the additive sweep's form on level lv: separate kernels or one fused cooperative kernel
+// (force 1: fused where possible, -1: separate, 0: the faster by timing)
+void choose_sweep_form(cav_hierarchy* H, Level& lv, int force, cudaStream_t st);
 void vcycle_prepare(cav_hierarchy* H);
 void krylov_reserve(cav_hierarchy* H, int maxit, int64_t n);
 void vcycle(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st);
+// the V-cycle's kernels launched directly on st (input levels[0].b, output levels[0].x), for
+// capture into a solve graph
+void vcycle_inline(const cav_hierarchy* H, cudaStream_t st);
 
 // reductions (reduce.cu)
 int reduce_blocks(int64_t n);

@@ -2,7 +2,10 @@
 // sets, extraction of local matrices, one-pass equilibration, inverses, and the transpose
 // incidence used by the scatter of the additive sweep.
 #include <algorithm>
+#include <cstdlib>
 #include <numeric>
+
+#include <cooperative_groups.h>
 
 #include "internal.cuh"
 #include "device_util.cuh"
@@ -487,6 +490,7 @@ __device__ double ke_entry(const LevelK& L, int ga, int gb, bool use_ee) {
 }
 
 struct FactorJob {
+  const int* jobs;          // nullable: block b factorises patch jobs[b] (else patch b)
   const int64_t* dof_off;   // per patch offsets into dofs (n_jobs + 1)
   const int* dofs;
   const int64_t* mat_off;   // per patch element offset into A (ld * (n + border))
@@ -504,7 +508,7 @@ struct FactorJob {
 // the inverse of diag(s_r) K diag(s_c); a zero pivot raises DEV_SINGULAR.
 __global__ void k_factor(LevelK L, FactorJob J, int bordered_job, int* status) {
   extern __shared__ double sh[];
-  const int p = blockIdx.x;
+  const int p = J.jobs ? J.jobs[blockIdx.x] : (int)blockIdx.x;
   const int64_t d0 = J.dof_off[p];
   const int n = (int)(J.dof_off[p + 1] - d0);
   const int NN = L.N * L.N;
@@ -634,6 +638,213 @@ __global__ void k_factor(LevelK L, FactorJob J, int bordered_job, int* status) {
     }
     __syncthreads();
   }
+}
+
+// The same factorisation for one patch on a pair of CTAs (a cluster of two), the matrix held
+// in shared memory: CTA r keeps the columns b = r, r + 2, ... of the m x m matrix (about 200 KB each for m = 224), so a patch of up to FP_MMAX unknowns never leaves the SMs.
+// Every value is computed by the same expressions in the same order as in k_factor, and
+// the pivot is the same (the first row of maximal modulus), so the inverse is bitwise the
+// same.  Per elimination step the column's owner finds the pivot and publishes the pivot row
+// index and the column (before the interchange) to both CTAs through distributed shared
+// memory, one cluster barrier later both interchange rows and update their own columns; the
+// published column is double-buffered, so one barrier per step suffices.  The column
+// interchanges that undo the pivoting are folded into the final store.
+constexpr int FP_THREADS = 512;
+constexpr int FP_MMAX = 224;
+// below this size the per-step cluster barrier outweighs the global-memory traffic it saves
+// (measured: the fiber channel at N = 64, patches under 100 unknowns, set up in 21.7 ms with
+// the one-CTA kernel and 25.4 ms with pairs; the N = 256 membrane, 128-218, 80 -> 75 ms)
+constexpr int FP_MMIN = 128;
+
+static size_t factor_pair_smem(int m) {
+  const int ld = (m + 7) & ~7, mc = (m + 1) / 2;
+  return (size_t)mc * ld * sizeof(double)          // my columns
+         + (size_t)4 * m * sizeof(double)            // published columns (2), row maxima (2)
+         + (size_t)mc * sizeof(double)              // the pivot row on my columns
+         + (size_t)3 * m * sizeof(int) + 64;        // pivots, column map, its inverse
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FP_THREADS)
+k_factor_pair(LevelK L, FactorJob J, const int* __restrict__ jobs, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) double shp[];
+  const int r = (int)cluster.block_rank();
+  const int p = jobs[blockIdx.x >> 1];
+  const int64_t d0 = J.dof_off[p];
+  const int n = (int)(J.dof_off[p + 1] - d0);
+  const int NN = L.N * L.N;
+  __shared__ int s_border;
+  __shared__ double s_pmax[FP_THREADS / 32];
+  __shared__ int s_pidx[FP_THREADS / 32];
+  if (threadIdx.x == 0) {
+    int border = 0;
+    if (J.border_all_pressure) {
+      int np = 0;
+      for (int a = 0; a < n; ++a) np += (J.dofs[d0 + a] >= 2 * NN);
+      border = (np == NN);
+    }
+    s_border = border;
+    if (r == 0) J.mdim[p] = n + border;
+  }
+  __syncthreads();
+  const int m = n + s_border;
+  const int ld = (m + 7) & ~7;
+  const int mc = (m - r + 1) / 2;  // my columns
+  double* A = shp;                                   // [mc][ld]
+  double* pub = A + (size_t)((m + 1) / 2) * ld;      // [2][m] published columns
+  double* rmax = pub + 2 * m;                        // [2][m] row maxima of each CTA
+  double* rowk = rmax + 2 * m;                       // [(m + 1) / 2]
+  int* perm = reinterpret_cast<int*>(rowk + (m + 1) / 2);
+  int* src = perm + m;
+  int* dst = src + m;
+  const int64_t so = d0 + p;
+  double* sr = J.s_r + so;
+  double* sc = J.s_c + so;
+  const int* dofs = J.dofs + d0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FP_THREADS / 32;
+  // extraction of my columns
+  for (int64_t e = tid; e < (int64_t)mc * m; e += FP_THREADS) {
+    const int q = (int)(e / m), a = (int)(e % m);
+    const int b = 2 * q + r;
+    double v;
+    if (a < n && b < n) v = ke_entry(L, dofs[a], dofs[b], J.use_ee != 0);
+    else if (a == n && b == n) v = 0.0;
+    else {
+      const int g = (a == n) ? dofs[b] : dofs[a];
+      v = (g >= 2 * NN) ? 1.0 : 0.0;
+    }
+    A[(int64_t)q * ld + a] = v;
+  }
+  __syncthreads();
+  // row scales: the maximum over my columns, exchanged, then over both
+  {
+    double* peer = cluster.map_shared_rank(rmax, r ^ 1);
+    for (int a = tid; a < m; a += FP_THREADS) {
+      double mx = 0.0;
+      for (int q = 0; q < mc; ++q) mx = fmax(mx, fabs(A[(int64_t)q * ld + a]));
+      rmax[r * m + a] = mx;
+      peer[r * m + a] = mx;
+    }
+  }
+  cluster.sync();
+  double* srl = pub;  // the row scales, kept in the (not yet used) published-column buffer
+  for (int a = tid; a < m; a += FP_THREADS) {
+    const double mx = fmax(rmax[a], rmax[m + a]);
+    srl[a] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
+    if (r == 0) {
+      sr[a] = srl[a];
+      if (mx == 0.0) atomicExch(status, DEV_SINGULAR);
+    }
+  }
+  __syncthreads();
+  // column scales of diag(s_r) K on my columns, then the scaled matrix
+  double* scl = rmax;  // my columns' scales (the row maxima are no longer needed)
+  for (int q = tid; q < mc; q += FP_THREADS) {
+    double mx = 0.0;
+    for (int a = 0; a < m; ++a) mx = fmax(mx, fabs(srl[a] * A[(int64_t)q * ld + a]));
+    scl[q] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
+    sc[2 * q + r] = scl[q];
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < (int64_t)mc * m; e += FP_THREADS) {
+    const int q = (int)(e / m), a = (int)(e % m);
+    A[(int64_t)q * ld + a] = srl[a] * A[(int64_t)q * ld + a] * scl[q];
+  }
+  // both CTAs are done with the scales before the first column is published into pub
+  cluster.sync();
+  for (int k = 0; k < m; ++k) {
+    double* colk = pub + (k & 1) * m;
+    if ((k & 1) == r) {
+      // I own column k: pivot search (first row of maximal modulus), then publish
+      const double* ak = A + (int64_t)(k >> 1) * ld;
+      double best = -1.0;
+      int bi = m;
+      for (int a = k + tid; a < m; a += FP_THREADS) {
+        const double v = fabs(ak[a]);
+        if (v > best) { best = v; bi = a; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { s_pmax[warp] = best; s_pidx[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double bb = -1.0;
+        int ii = m;
+        for (int w = 0; w < nw; ++w)
+          if (s_pmax[w] > bb || (s_pmax[w] == bb && s_pidx[w] < ii)) { bb = s_pmax[w]; ii = s_pidx[w]; }
+        if (!(bb > 0.0)) atomicExch(status, DEV_SINGULAR);
+        perm[k] = ii;
+        *cluster.map_shared_rank(perm + k, r ^ 1) = ii;
+      }
+      double* peer = cluster.map_shared_rank(colk, r ^ 1);
+      for (int a = tid; a < m; a += FP_THREADS) {
+        const double v = ak[a];
+        colk[a] = v;
+        peer[a] = v;
+      }
+    }
+    cluster.sync();
+    const int pr = perm[k];
+    // row interchange k <-> pr on my columns and in the published column
+    if (pr != k && pr < m) {
+      for (int q = tid; q < mc; q += FP_THREADS) {
+        double* c = A + (int64_t)q * ld;
+        const double t = c[k];
+        c[k] = c[pr];
+        c[pr] = t;
+      }
+      if (tid == 0) {
+        const double t = colk[k];
+        colk[k] = colk[pr];
+        colk[pr] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = colk[k];
+    const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
+    for (int q = tid; q < mc; q += FP_THREADS) {
+      const int b = 2 * q + r;
+      rowk[q] = (b == k) ? ipiv : A[(int64_t)q * ld + k] * ipiv;
+    }
+    __syncthreads();
+    // rank-one update of my columns: warps over columns, lanes over rows
+    for (int q = warp; q < mc; q += nw) {
+      double* colp = A + (int64_t)q * ld;
+      const double rb = rowk[q];
+      if (2 * q + r == k) {
+        for (int a = lane; a < m; a += 32) colp[a] = (a == k) ? rb : -colk[a] * ipiv;
+      } else {
+        for (int a = lane; a < m; a += 32) colp[a] = (a == k) ? rb : colp[a] - colk[a] * rb;
+      }
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges (last first): the column at position c
+  // of the result is my column src[c] when src[c] is one of mine
+  if (tid == 0) {
+    for (int c = 0; c < m; ++c) src[c] = c;
+    for (int k = m - 1; k >= 0; --k) {
+      const int pr = perm[k];
+      if (pr != k && pr < m) {
+        const int t = src[k];
+        src[k] = src[pr];
+        src[pr] = t;
+      }
+    }
+    for (int c = 0; c < m; ++c) dst[src[c]] = c;
+  }
+  __syncthreads();
+  double* out = J.A + J.mat_off[p];
+  for (int q = warp; q < mc; q += nw) {
+    const int c = dst[2 * q + r];
+    const double* colp = A + (int64_t)q * ld;
+    for (int a = lane; a < m; a += 32) out[(int64_t)c * ld + a] = colp[a];
+  }
+  cluster.sync();  // no CTA exits while its peer may still write into its shared memory
 }
 
 // Fold the scalings: out[a][b] = s_c[a] X[a][b] s_r[b], row-major (m x m).
@@ -833,6 +1044,7 @@ static void factor_patches(cav_hierarchy* H, Level& lv, bool standard, cudaStrea
   double* wsc = scratch.alloc<double>(hoff_ext[njobs] + njobs + 8);
   int* mdim = scratch.alloc<int>(njobs + 1);
   FactorJob J;
+  J.jobs = nullptr;
   J.mdim = mdim;
   J.dof_off = d_off_ext;
   J.dofs = lv.big_dofs;
@@ -847,8 +1059,41 @@ static void factor_patches(cav_hierarchy* H, Level& lv, bool standard, cudaStrea
   if (fsm > 48 * 1024)
     CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
   if (nbig > 0) {
-    k_factor<<<(int)nbig, 256, fsm, st>>>(LK, J, 0, H->status);
-    CAV_CHECK_LAUNCH();
+    // patches of FP_MMIN .. FP_MMAX unknowns (with a possible border) on CTA pairs with the
+    // matrix in shared memory; the others one CTA each in global memory.  CAV_FACTOR_GLOBAL=1 sends
+    // every patch to the global-memory kernel (a test hook: both give the same bits).
+    const char* force_global = std::getenv("CAV_FACTOR_GLOBAL");
+    const bool pairs_on = !(force_global && force_global[0] == '1');
+    std::vector<int> pair_jobs, glob_jobs;
+    int pair_mmax = 0;
+    for (int p = 0; p < (int)nbig; ++p) {
+      if (pairs_on && hsizes[p] >= FP_MMIN && hsizes[p] + 1 <= FP_MMAX) {
+        pair_jobs.push_back(p);
+        pair_mmax = std::max(pair_mmax, hsizes[p] + 1);
+      } else {
+        glob_jobs.push_back(p);
+      }
+    }
+    if (!pair_jobs.empty()) {
+      int* d_jobs = scratch.alloc<int>(pair_jobs.size());
+      CAV_CHECK_CUDA(cudaMemcpyAsync(d_jobs, pair_jobs.data(), sizeof(int) * pair_jobs.size(), cudaMemcpyHostToDevice,
+                                     st));
+      const size_t psm = factor_pair_smem(pair_mmax);
+      CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+      k_factor_pair<<<2 * (int)pair_jobs.size(), FP_THREADS, psm, st>>>(LK, J, d_jobs, H->status);
+      CAV_CHECK_LAUNCH();
+    }
+    if (!glob_jobs.empty()) {
+      FactorJob Jg = J;
+      if ((int)glob_jobs.size() < (int)nbig) {
+        int* d_jobs = scratch.alloc<int>(glob_jobs.size());
+        CAV_CHECK_CUDA(cudaMemcpyAsync(d_jobs, glob_jobs.data(), sizeof(int) * glob_jobs.size(),
+                                       cudaMemcpyHostToDevice, st));
+        Jg.jobs = d_jobs;
+      }
+      k_factor<<<(int)glob_jobs.size(), 256, fsm, st>>>(LK, Jg, 0, H->status);
+      CAV_CHECK_LAUNCH();
+    }
   }
   // the standard patches: same kernel, one block each, no E_E
   if (standard) {
@@ -1100,6 +1345,7 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   double* wsc = scratch.alloc<double>(m);
   int* mdim = scratch.alloc<int>(1);
   FactorJob J;
+  J.jobs = nullptr;
   J.mdim = mdim;
   J.dof_off = d_off;
   J.dofs = d_dofs;
@@ -1183,6 +1429,13 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
   if (H->desc.autotune)
     for (auto& lv : H->levels)
       if (!lv.coarsest && !lv.coloured) autotune_level(H, lv, st);
+  // the sweep's form: timed with the autotuner, else separate kernels; CAV_SWEEP_FORM=fused
+  // or =separate (a test hook) forces one form (both give the same bits)
+  const char* form = std::getenv("CAV_SWEEP_FORM");
+  const int force = (form && std::string(form) == "fused") ? 1
+                    : (form && std::string(form) == "separate") ? -1 : (H->desc.autotune ? 0 : -1);
+  for (auto& lv : H->levels)
+    if (!lv.coarsest && !lv.coloured) choose_sweep_form(H, lv, force, st);
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   check_status(H, st, "autotune");
   // capture both V-cycle graph instances now, so no solve pays for it

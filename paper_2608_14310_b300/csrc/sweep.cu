@@ -10,14 +10,17 @@
 //      shared 5x5 inverse is applied on the fly), the others one warp per unknown over the
 //      slots of the enlarged patches holding it (fixed order, no atomics)
 //   4. remove the mean pressure (Sec. 3.3).
+#include <map>
 #include <mutex>
 #include <set>
+#include <tuple>
 #include <string>
 #include <utility>
 
 #include "internal.cuh"
 #include "device_util.cuh"
 #include "level_math.cuh"
+#include "sweep_parts.cuh"
 #include "tma_util.cuh"
 
 namespace cav {
@@ -64,16 +67,16 @@ k_patch_apply(const int* __restrict__ order, const int64_t* __restrict__ off, co
   }
 }
 
-__device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
-
 constexpr int TMA_CONSUMER_WARPS = 4;
 constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 2);  // producer, gatherer, consumers
 constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
 constexpr int Y_SLOTS = 2;
+constexpr int FUSED_CONSUMER_WARPS = 6;
+constexpr int FUSED_THREADS = 32 * (FUSED_CONSUMER_WARPS + 2);  // = UPD_THREADS
 
-template <typename T>
+template <typename T, int CW>
 __host__ __device__ constexpr int tma_max_rows() {
-  return TMA_MAXPASS * 32 * TMA_CONSUMER_WARPS * VecLoad<T>::V;
+  return TMA_MAXPASS * 32 * CW * VecLoad<T>::V;
 }
 
 // The q-th patch a persistent CTA takes (q = round * G + CTA): rounds alternate direction over
@@ -85,134 +88,157 @@ __device__ inline int zigzag(int q, int G, int n) {
   return (r & 1) ? r * G + (len - 1 - c) : q;
 }
 
-// Persistent batched patch apply.  CTA c takes the patches zigzag(c), zigzag(c + G), ... of
-// the size-descending order, with three roles:
-//  * warp 0, one lane (producer): streams each patch's column-major inverse -- a contiguous
-//    block of n * ld elements -- into a ring of TMA_STAGES shared-memory stages of at most
-//    TMA_CHUNK bytes (whole columns) with cp.async.bulk; "full" mbarriers carry the
-//    transaction bytes, "empty" mbarriers take one arrival per consumer warp;
-//  * warp 1 (gatherer): writes y = s_r * r|_p of the coming patches into a double-buffered
-//    shared ring ("yfull": 32 lane arrivals, "yempty": one arrival per consumer warp), so the
-//    dependent index -> residual loads of patch t+1 overlap the streaming of patch t;
-//  * warps 2..5 (consumers): acc[rows] += X[rows, b] y[b] stage by stage, each thread
-//    owning V consecutive rows (up to TMA_MAXPASS row blocks), then delta = s_c * acc.
-// Every wait is bounded.  A wait that runs out records DEV_TIMEOUT and raises the CTA's abort
-// flag; every role then stops (no further copies, arrivals or writes; the delta of the
-// remaining patches is left unwritten and the host reports IB_ERR_TIMEOUT), and the producer
-// waits for the copies it has in flight to land before the CTA exits.  A warp's give-up
-// decision is taken by all its lanes together.
+// Arguments of the batched patch apply (the enlarged patches of one level).
+template <typename T>
+struct ApplyArgs {
+  int n_big;
+  const int* order;
+  const int64_t* off;
+  const int* dofs;
+  const int64_t* inv_off;
+  const T* inv;
+  const double* s_r;
+  const double* s_c;
+  const double* r;
+  double* delta;
+  int max_n;
+  int* status;
+};
+
+// The shared-memory ring of the persistent patch apply: TMA_STAGES stages of TMA_CHUNK bytes,
+// Y_SLOTS gathered vectors, their mbarriers and the CTA's abort flag.
 template <typename T, int TMA_STAGES, int TMA_CHUNK>
-__global__ void __launch_bounds__(TMA_THREADS)
-k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __restrict__ off,
-                  const int* __restrict__ dofs, const int64_t* __restrict__ inv_off, const T* __restrict__ inv,
-                  const double* __restrict__ s_r, const double* __restrict__ s_c, const double* __restrict__ r,
-                  double* __restrict__ delta, int max_n, int* status) {
-  typedef VecLoad<T> VL;
-  typedef typename VL::acc_t acc_t;
-  constexpr int V = VL::V;
-  constexpr int CT = 32 * TMA_CONSUMER_WARPS;
-  static_assert(TMA_STAGES <= 32, "stage bit masks");
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* stage_buf = smem;
-  const size_t ybytes = ((size_t)max_n * sizeof(acc_t) + 127) & ~(size_t)127;
-  acc_t* ybuf = reinterpret_cast<acc_t*>(smem + TMA_STAGES * TMA_CHUNK);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TMA_STAGES * TMA_CHUNK + Y_SLOTS * ybytes);
-  uint64_t* empty = full + TMA_STAGES;
-  uint64_t* yfull = empty + TMA_STAGES;
-  uint64_t* yempty = yfull + Y_SLOTS;
-  int* abort_flag = reinterpret_cast<int*>(yempty + Y_SLOTS);
-  volatile int* ab = abort_flag;
-  const bool stall = wait_stall_enabled();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
+struct ApplyRing {
+  typedef typename VecLoad<T>::acc_t acc_t;
+  unsigned char* stage_buf;
+  acc_t* ybuf;
+  size_t yslot;  // elements per gathered vector
+  uint64_t *full, *empty, *yfull, *yempty;
+  int* abort_flag;
+  __device__ ApplyRing(unsigned char* smem, int max_n) {
+    const size_t ybytes = ((size_t)max_n * sizeof(acc_t) + 127) & ~(size_t)127;
+    stage_buf = smem;
+    ybuf = reinterpret_cast<acc_t*>(smem + TMA_STAGES * TMA_CHUNK);
+    yslot = ybytes / sizeof(acc_t);
+    full = reinterpret_cast<uint64_t*>(smem + TMA_STAGES * TMA_CHUNK + Y_SLOTS * ybytes);
+    empty = full + TMA_STAGES;
+    yfull = empty + TMA_STAGES;
+    yempty = yfull + Y_SLOTS;
+    abort_flag = reinterpret_cast<int*>(yempty + Y_SLOTS);
+  }
+  static size_t bytes(int max_n) {
+    const size_t ybytes = ((size_t)max_n * sizeof(acc_t) + 127) & ~(size_t)127;
+    return (size_t)TMA_STAGES * TMA_CHUNK + Y_SLOTS * ybytes + (2 * TMA_STAGES + 2 * Y_SLOTS) * sizeof(uint64_t) +
+           16;  // the CTA's abort flag
+  }
+  // one thread: the barriers for CW consumer warps
+  __device__ void init(int cw) {
     *abort_flag = 0;
     for (int s = 0; s < TMA_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], TMA_CONSUMER_WARPS);
+      mbar_init(&empty[s], cw);
     }
     for (int s = 0; s < Y_SLOTS; ++s) {
       mbar_init(&yfull[s], 32);
-      mbar_init(&yempty[s], TMA_CONSUMER_WARPS);
+      mbar_init(&yempty[s], cw);
     }
     mbar_fence_init();
   }
-  __syncthreads();
-  // Under a programmatic launch the residual kernel ahead may still be running.  Only the
-  // gatherer reads what it writes (r), so only the gatherer waits for it; the producer streams
-  // the inverses (never written during a sweep) from the start, and the consumers write delta
-  // only after the gatherer's first handoff, when every earlier kernel (the previous sweep's
-  // scatter, which reads delta) has finished.  (Measured: launching the finest level's apply
-  // this way made its sweep slower, 86 -> 103 us, the early bulk traffic delaying the
-  // latency-bound residual kernel; the launchers do not request it.)
-  pdl_trigger();
+};
 
-  if (warp == 0) {
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t used = 0, last_par = 0;  // per stage: a copy was issued; parity of its last phase
-      bool ok = true;
-      for (int q = blockIdx.x; ok && q < n_big; q += gridDim.x) {
-        const int p = order[zigzag(q, gridDim.x, n_big)];
-        const int n = (int)(off[p + 1] - off[p]);
-        const uint32_t col_bytes = (uint32_t)(((n + 7) & ~7) * sizeof(T));
-        const int cpc = TMA_CHUNK / (int)col_bytes;
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + inv_off[p]);
-        for (int b0 = 0; b0 < n; b0 += cpc) {
-          const int nc = min(cpc, n - b0);
-          if (!mbar_wait(&empty[stage], phase ^ 1u, status, ab, false)) {
-            ok = false;
-            break;
-          }
-          const uint32_t bytes = (uint32_t)nc * col_bytes;
-          mbar_arrive_expect_tx(&full[stage], bytes);
-          bulk_copy_g2s(stage_buf + (size_t)stage * TMA_CHUNK, src + (size_t)b0 * col_bytes, bytes, &full[stage]);
-          used |= 1u << stage;
-          last_par = phase ? (last_par | (1u << stage)) : (last_par & ~(1u << stage));
-          if (++stage == TMA_STAGES) {
-            stage = 0;
-            phase ^= 1u;
-          }
-        }
+// Persistent batched patch apply.  CTA c takes the patches zigzag(c), zigzag(c + G), ... of
+// the size-descending order, with three roles:
+//  * one lane (producer): streams each patch's column-major inverse -- a contiguous block of
+//    n * ld elements -- into a ring of TMA_STAGES shared-memory stages of at most TMA_CHUNK
+//    bytes (whole columns) with cp.async.bulk; "full" mbarriers carry the transaction bytes,
+//    "empty" mbarriers take one arrival per consumer warp;
+//  * one warp (gatherer): writes y = s_r * r|_p of the coming patches into a double-buffered
+//    shared ring ("yfull": 32 lane arrivals, "yempty": one arrival per consumer warp), so the
+//    dependent index -> residual loads of patch t+1 overlap the streaming of patch t;
+//  * CW consumer warps: acc[rows] += X[rows, b] y[b] stage by stage, each thread owning V
+//    consecutive rows (up to TMA_MAXPASS row blocks), then delta = s_c * acc.
+// Every wait is bounded.  A wait that runs out records DEV_TIMEOUT and raises the CTA's abort
+// flag; every role then stops (no further copies, arrivals or writes; the delta of the
+// remaining patches is left unwritten and the host reports IB_ERR_TIMEOUT), and the producer
+// waits for the copies it has in flight to land before it returns.  A warp's give-up
+// decision is taken by all its lanes together.
+template <typename T, int TMA_STAGES, int TMA_CHUNK>
+__device__ inline void apply_producer(const ApplyArgs<T>& a, ApplyRing<T, TMA_STAGES, TMA_CHUNK>& R) {
+  volatile int* ab = R.abort_flag;
+  int stage = 0;
+  uint32_t phase = 0;
+  uint32_t used = 0, last_par = 0;  // per stage: a copy was issued; parity of its last phase
+  bool ok = true;
+  for (int q = blockIdx.x; ok && q < a.n_big; q += gridDim.x) {
+    const int p = a.order[zigzag(q, gridDim.x, a.n_big)];
+    const int n = (int)(a.off[p + 1] - a.off[p]);
+    const uint32_t col_bytes = (uint32_t)(((n + 7) & ~7) * sizeof(T));
+    const int cpc = TMA_CHUNK / (int)col_bytes;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(a.inv + a.inv_off[p]);
+    for (int b0 = 0; b0 < n; b0 += cpc) {
+      const int nc = min(cpc, n - b0);
+      if (!mbar_wait(&R.empty[stage], phase ^ 1u, a.status, ab, false)) {
+        ok = false;
+        break;
       }
-      // every issued copy lands before the CTA exits (immediate when the consumers saw them all)
-      for (int s = 0; s < TMA_STAGES; ++s)
-        if ((used >> s) & 1u) mbar_drain(&full[s], (last_par >> s) & 1u, status);
+      const uint32_t bytes = (uint32_t)nc * col_bytes;
+      mbar_arrive_expect_tx(&R.full[stage], bytes);
+      bulk_copy_g2s(R.stage_buf + (size_t)stage * TMA_CHUNK, src + (size_t)b0 * col_bytes, bytes, &R.full[stage]);
+      used |= 1u << stage;
+      last_par = phase ? (last_par | (1u << stage)) : (last_par & ~(1u << stage));
+      if (++stage == TMA_STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
     }
-    return;
   }
+  // every issued copy lands before the role ends (immediate when the consumers saw them all)
+  for (int s = 0; s < TMA_STAGES; ++s)
+    if ((used >> s) & 1u) mbar_drain(&R.full[s], (last_par >> s) & 1u, a.status);
+}
 
-  if (warp == 1) {
-    pdl_wait();
-    int t = 0;
-    for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
-      const int slot = t & 1;
-      const uint32_t par = (uint32_t)((t >> 1) & 1);
-      const bool got = mbar_wait(&yempty[slot], par ^ 1u, status, ab, false);
-      if (!__all_sync(0xffffffffu, got)) break;
-      const int p = order[zigzag(q, gridDim.x, n_big)];
-      const int64_t d0 = off[p];
-      const int n = (int)(off[p + 1] - d0);
-      acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
-      for (int b = lane; b < n; b += 32) y[b] = (acc_t)(s_r[d0 + b] * r[dofs[d0 + b]]);
-      mbar_arrive(&yfull[slot]);
-    }
-    return;
+template <typename T, int TMA_STAGES, int TMA_CHUNK>
+__device__ inline void apply_gatherer(const ApplyArgs<T>& a, ApplyRing<T, TMA_STAGES, TMA_CHUNK>& R) {
+  typedef typename VecLoad<T>::acc_t acc_t;
+  volatile int* ab = R.abort_flag;
+  const int lane = threadIdx.x & 31;
+  int t = 0;
+  for (int q = blockIdx.x; q < a.n_big; q += gridDim.x, ++t) {
+    const int slot = t & 1;
+    const uint32_t par = (uint32_t)((t >> 1) & 1);
+    const bool got = mbar_wait(&R.yempty[slot], par ^ 1u, a.status, ab, false);
+    if (!__all_sync(0xffffffffu, got)) break;
+    const int p = a.order[zigzag(q, gridDim.x, a.n_big)];
+    const int64_t d0 = a.off[p];
+    const int n = (int)(a.off[p + 1] - d0);
+    acc_t* y = R.ybuf + (size_t)slot * R.yslot;
+    for (int b = lane; b < n; b += 32) y[b] = (acc_t)(a.s_r[d0 + b] * a.r[a.dofs[d0 + b]]);
+    mbar_arrive(&R.yfull[slot]);
   }
+}
 
-  const int ct = threadIdx.x - 64;
+// ct: the thread's index among the CW consumer warps' threads
+template <typename T, int TMA_STAGES, int TMA_CHUNK, int CW>
+__device__ inline void apply_consumer(const ApplyArgs<T>& a, ApplyRing<T, TMA_STAGES, TMA_CHUNK>& R, int ct,
+                                      bool stall) {
+  typedef VecLoad<T> VL;
+  typedef typename VL::acc_t acc_t;
+  constexpr int V = VL::V;
+  constexpr int CT = 32 * CW;
+  volatile int* ab = R.abort_flag;
+  const int lane = threadIdx.x & 31;
   int stage = 0;
   uint32_t phase = 0;
   int t = 0;
-  for (int q = blockIdx.x; q < n_big; q += gridDim.x, ++t) {
-    const int p = order[zigzag(q, gridDim.x, n_big)];
-    const int64_t d0 = off[p];
-    const int n = (int)(off[p + 1] - d0);
+  for (int q = blockIdx.x; q < a.n_big; q += gridDim.x, ++t) {
+    const int p = a.order[zigzag(q, gridDim.x, a.n_big)];
+    const int64_t d0 = a.off[p];
+    const int n = (int)(a.off[p + 1] - d0);
     const int ld = (n + 7) & ~7;
     const int cpc = TMA_CHUNK / (int)(ld * sizeof(T));
     const int slot = t & 1;
-    if (!__all_sync(0xffffffffu, mbar_wait(&yfull[slot], (uint32_t)((t >> 1) & 1), status, ab, stall))) break;
-    const acc_t* y = ybuf + (size_t)slot * (ybytes / sizeof(acc_t));
+    if (!__all_sync(0xffffffffu, mbar_wait(&R.yfull[slot], (uint32_t)((t >> 1) & 1), a.status, ab, stall))) break;
+    const acc_t* y = R.ybuf + (size_t)slot * R.yslot;
     acc_t acc[TMA_MAXPASS][V];
 #pragma unroll
     for (int ps = 0; ps < TMA_MAXPASS; ++ps)
@@ -221,11 +247,11 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     bool dead = false;
     for (int b0 = 0; b0 < n; b0 += cpc) {
       const int nc = min(cpc, n - b0);
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, status, ab, stall))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&R.full[stage], phase, a.status, ab, stall))) {
         dead = true;
         break;
       }
-      const T* X = reinterpret_cast<const T*>(stage_buf + (size_t)stage * TMA_CHUNK);
+      const T* X = reinterpret_cast<const T*>(R.stage_buf + (size_t)stage * TMA_CHUNK);
 #pragma unroll
       for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
         const int a0 = (ps * CT + ct) * V;
@@ -241,7 +267,7 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (lane == 0) mbar_arrive(&R.empty[stage]);
       if (++stage == TMA_STAGES) {
         stage = 0;
         phase ^= 1u;
@@ -249,118 +275,141 @@ k_patch_apply_tma(int n_big, const int* __restrict__ order, const int64_t* __res
     }
     if (dead) break;
     __syncwarp();
-    if (lane == 0) mbar_arrive(&yempty[slot]);
+    if (lane == 0) mbar_arrive(&R.yempty[slot]);
 #pragma unroll
     for (int ps = 0; ps < TMA_MAXPASS; ++ps) {
       const int a0 = (ps * CT + ct) * V;
 #pragma unroll
       for (int v = 0; v < V; ++v)
-        if (a0 + v < n) delta[d0 + a0 + v] = s_c[d0 + a0 + v] * (double)acc[ps][v];
+        if (a0 + v < n) a.delta[d0 + a0 + v] = a.s_c[d0 + a0 + v] * (double)acc[ps][v];
     }
+  }
+}
+
+template <typename T, int TMA_STAGES, int TMA_CHUNK>
+__global__ void __launch_bounds__(TMA_THREADS) k_patch_apply_tma(ApplyArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  ApplyRing<T, TMA_STAGES, TMA_CHUNK> R(smem, a.max_n);
+  const bool stall = wait_stall_enabled();
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) R.init(TMA_CONSUMER_WARPS);
+  __syncthreads();
+  // Under a programmatic launch the residual kernel ahead may still be running.  Only the
+  // gatherer reads what it writes (r), so only the gatherer waits for it; the producer streams
+  // the inverses (never written during a sweep) from the start, and the consumers write delta
+  // only after the gatherer's first handoff, when every earlier kernel (the previous sweep's
+  // scatter, which reads delta) has finished.  (Measured: launching the finest level's apply
+  // this way made its sweep slower, 86 -> 103 us, the early bulk traffic delaying the
+  // latency-bound residual kernel; the launchers do not request it.)
+  pdl_trigger();
+  if (warp == 0) {
+    if ((threadIdx.x & 31) == 0) apply_producer(a, R);
+    return;
+  }
+  if (warp == 1) {
+    pdl_wait();
+    apply_gatherer(a, R);
+    return;
+  }
+  apply_consumer<T, TMA_STAGES, TMA_CHUNK, TMA_CONSUMER_WARPS>(a, R, (int)threadIdx.x - 64, stall);
+}
+
+// ------------------------------------------------------------------ the fused sweep
+
+// Grid-wide barrier of a cooperative launch (every CTA resident), called by one thread per
+// CTA between CTA-level barriers.  bar[0] counts the arrivals, bar[1] is the generation: the
+// last CTA to arrive resets the count and advances the generation, which releases the others.
+// The state returns to its start at every barrier, so it serves launch after launch.  Each
+// wait is bounded: it gives up after about a second, recording DEV_TIMEOUT.
+__device__ inline unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+constexpr long long GRID_WAIT_LIMIT = 1LL << 31;  // clock cycles
+__device__ inline void grid_barrier(unsigned* bar, int* status) {
+  const unsigned gen = ld_acquire_u32(&bar[1]);
+  __threadfence();
+  const unsigned arrived = atomicAdd(&bar[0], 1u);
+  if (arrived + 1 == gridDim.x) {
+    atomicExch(&bar[0], 0u);
+    __threadfence();
+    st_release_u32(&bar[1], gen + 1);
+    return;
+  }
+  const long long t0 = clock64();
+  while (ld_acquire_u32(&bar[1]) == gen) {
+    if (clock64() - t0 > GRID_WAIT_LIMIT) {
+      atomicExch(status, DEV_TIMEOUT);
+      return;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+}
+
+// bar.sync on a named barrier for the nthreads threads of warps 1.. (the producer warp apart)
+__device__ inline void group_sync(int nthreads) { asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory"); }
+
+// One whole sweep of an additive level in one persistent cooperative launch (the four parts
+// of Eq. additive_cav_saddle plus, optionally, the mean removal of Sec. 3.3), each part the
+// same block-level work as its separate kernel:
+//   R  r = b - K_E w (skipped for w = 0: r = b), on warps 1-7 as 224-thread blocks, while the
+//      producer lane of warp 0 already streams the first inverse stages;
+//   -- grid barrier (r complete) --
+//   A  the patch apply: warp 0 producer, warp 1 gatherer, warps 2-7 consumers;
+//   -- grid barrier (delta complete) --
+//   U  the scatter / update as 256-thread blocks, each writing its pressure partial;
+//   -- grid barrier (partials complete), only with remove_mean --
+//   M  p -= mean(p).
+// The kernel boundaries it replaces cost a launch gap and a tail each, and the pipeline's
+// first stages no longer start cold after the residual.
+template <typename T, int TMA_STAGES, int TMA_CHUNK>
+__global__ void __launch_bounds__(FUSED_THREADS)
+k_sweep_fused(ResArgs ra, int nb_res, ApplyArgs<T> a, UpdArgs ua, int nb_upd, int remove_mean, int n_partial,
+              unsigned* bar) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double sm[8];
+  ApplyRing<T, TMA_STAGES, TMA_CHUNK> R(smem, a.max_n);
+  const bool stall = wait_stall_enabled();
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) R.init(FUSED_CONSUMER_WARPS);
+  __syncthreads();
+  if (warp == 0) {
+    if ((threadIdx.x & 31) == 0) apply_producer(a, R);
+  } else {
+    if (nb_res > 0) {
+      for (int vb = blockIdx.x; vb < nb_res; vb += gridDim.x) residual_block<7>(ra, vb, (int)threadIdx.x - 32);
+      group_sync(FUSED_THREADS - 32);
+      if (threadIdx.x == 32) grid_barrier(bar, a.status);
+      group_sync(FUSED_THREADS - 32);
+    }
+    if (warp == 1) apply_gatherer(a, R);
+    else apply_consumer<T, TMA_STAGES, TMA_CHUNK, FUSED_CONSUMER_WARPS>(a, R, (int)threadIdx.x - 64, stall);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) grid_barrier(bar, a.status);
+  __syncthreads();
+  for (int vb = blockIdx.x; vb < nb_upd; vb += gridDim.x) update_block(ua, vb, sm);
+  if (remove_mean) {
+    if (threadIdx.x == 0) grid_barrier(bar, a.status);
+    __syncthreads();
+    remove_mean_block(ua.N, n_partial, ua.partial, ua.w + 2 * ua.N * ua.N, (int)blockIdx.x, (int)gridDim.x, sm);
   }
 }
 
 // ------------------------------------------------------------------ 3. scatter / update
 
-constexpr int TOUCH_WARPS = 8;
-
-// Scatter / update in one launch with two block roles.
-//  * Blocks [0, nb_std): a 32 x 8 tile of cells, one thread per cell.  For each unknown of the
-//    cell that no enlarged patch holds, both incident cells (one for a pressure) keep their
-//    standard patch, so count_k is 2 (1) and the correction is the stencil of the shared 5x5
-//    inverse applied to r.
-//  * The remaining blocks: eight lanes per unknown held by at least one enlarged patch (four
-//    unknowns per warp).  The lanes sum the enlarged patches' corrections at the unknown (fixed
-//    lane-strided order, fixed shuffle tree); the group's first lane adds the standard patches
-//    of its incident cells that kept their Vanka patch and divides by the total patch count.
-// On the channel a v face of the outflow row has one incident cell (the one above it), and
-// the standard patches of the outflow and inflow rows have their own inverses.
-// Each block writes the partial sum of the new pressures it produced (fixed order); the
-// stencil blocks' partials come first, then the touched blocks'.
-__global__ void __launch_bounds__(256)
-k_update(int N, double alpha, StdInv S, int nb_std, int gx, const int64_t* __restrict__ inc_off,
-         int n_touched, const int* __restrict__ touched, const uint8_t* __restrict__ cell_big,
-         const int* __restrict__ inc_slot, const double* __restrict__ delta, const double* __restrict__ r,
-         double* __restrict__ w, int w_is_zero, double* __restrict__ partial, bool channel) {
+// Scatter / update in one launch with two block roles (update_block: cell tiles, then the
+// unknowns held by enlarged patches), each block writing its partial sum of new pressures.
+__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs a) {
   pdl_wait();  // programmatic launch: the patch apply (delta) and residual (r) have finished
   pdl_trigger();
   __shared__ double sm[8];
-  const int NN = N * N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double pnew = 0.0;
-  if ((int)blockIdx.x < nb_std) {
-    const int i = (blockIdx.x % gx) * 32 + lane;
-    const int j = (blockIdx.x / gx) * 8 + warp;
-    if (i < N && j < N) {
-      const int c = j * N + i;
-      const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
-      if (inc_off[c + 1] == inc_off[c]) {
-        const double s = std_row(S, 1, r, N, im, j, channel) + std_row(S, 0, r, N, i, j, channel);
-        w[c] = (w_is_zero ? 0.0 : w[c]) + alpha * (s / 2.0);
-      }
-      if (inc_off[NN + c + 1] == inc_off[NN + c]) {
-        if (channel && j == 0) {  // the outflow row's v face: one incident cell
-          const double s = std_row(S, 2, r, N, i, j, channel);
-          w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * s;
-        } else {
-          const double s = std_row(S, 3, r, N, i, jm, channel) + std_row(S, 2, r, N, i, j, channel);
-          w[NN + c] = (w_is_zero ? 0.0 : w[NN + c]) + alpha * (s / 2.0);
-        }
-      }
-      if (inc_off[2 * NN + c + 1] == inc_off[2 * NN + c]) {
-        const double s = std_row(S, 4, r, N, i, j, channel);
-        pnew = (w_is_zero ? 0.0 : w[2 * NN + c]) + alpha * s;
-        w[2 * NN + c] = pnew;
-      }
-    }
-    pnew = warp_sum(pnew);
-  } else {
-    const int sub = lane / TOUCH_LANES, sl = lane % TOUCH_LANES;
-    const int t = (((int)blockIdx.x - nb_std) * TOUCH_WARPS + warp) * TOUCH_PER_WARP + sub;
-    double s = 0.0;
-    int k = -1;
-    int64_t q0 = 0, q1 = 0;
-    if (t < n_touched) {
-      k = touched[t];
-      q0 = inc_off[k];
-      q1 = inc_off[k + 1];
-      for (int64_t q = q0 + sl; q < q1; q += TOUCH_LANES) s += delta[inc_slot[q]];
-    }
-#pragma unroll
-    for (int o = TOUCH_LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (k >= 0) {
-      if (sl == 0) {
-        const int comp = k / NN, c = k % NN, i = c % N, j = c / N;
-        const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
-        int cnt = (int)(q1 - q0);
-        double st = 0.0;
-        if (comp == 0) {
-          if (!cell_big[j * N + im]) { st += std_row(S, 1, r, N, im, j, channel); ++cnt; }
-          if (!cell_big[c]) { st += std_row(S, 0, r, N, i, j, channel); ++cnt; }
-        } else if (comp == 1) {
-          if (!(channel && j == 0) && !cell_big[jm * N + i]) { st += std_row(S, 3, r, N, i, jm, channel); ++cnt; }
-          if (!cell_big[c]) { st += std_row(S, 2, r, N, i, j, channel); ++cnt; }
-        } else {
-          if (!cell_big[c]) { st += std_row(S, 4, r, N, i, j, channel); ++cnt; }
-        }
-        const double nw = (w_is_zero ? 0.0 : w[k]) + alpha * ((st + s) / (double)cnt);
-        w[k] = nw;
-        if (comp == 2) pnew = nw;
-      }
-    }
-    // the warp's new pressures: group leaders' values in fixed order
-    double wp = 0.0;
-#pragma unroll
-    for (int g = 0; g < TOUCH_PER_WARP; ++g) wp += __shfl_sync(0xffffffffu, pnew, g * TOUCH_LANES);
-    pnew = wp;
-  }
-  if (lane == 0) sm[warp] = pnew;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int q = 0; q < 8; ++q) tot += sm[q];
-    partial[blockIdx.x] = tot;
-  }
+  update_block(a, (int)blockIdx.x, sm);
 }
 
 // 4. p -= mean(p): every block reduces the partials in the same order, then subtracts.
@@ -368,11 +417,7 @@ __global__ void k_remove_mean(int N, int n_partial, const double* __restrict__ p
   pdl_wait();
   pdl_trigger();
   __shared__ double sm[8];
-  double t = 0.0;
-  for (int q = threadIdx.x; q < n_partial; q += blockDim.x) t += partial[q];
-  t = block_sum(t, sm);
-  const double mean = t / ((double)N * (double)N);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N * N; c += gridDim.x * blockDim.x) p[c] -= mean;
+  remove_mean_block(N, n_partial, partial, p, (int)blockIdx.x, (int)gridDim.x, sm);
 }
 
 void launch_remove_mean(int N, int n_partial, const double* partial, double* p, cudaStream_t st) {
@@ -412,13 +457,13 @@ static LevelOps ops_of(const Level& lv) {
 
 // Whether prof_begin / prof_end record events (event-record nodes in a captured V-cycle).
 bool prof_records(const cav_hierarchy* H, int level) {
-  if (level != 0) return false;
+  if (level != 0 || H->no_events) return false;
   return H->capturing || (H->prof_on && (size_t)(2 * H->prof_used + 1) < H->prof_ev.size());
 }
 
 void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st) {
   cav_hierarchy* h = const_cast<cav_hierarchy*>(H);
-  if (level != 0) return;
+  if (level != 0 || h->no_events) return;
   if (h->capturing) {
     std::vector<cudaEvent_t>& ev = h->vc_ev[h->capturing - 1];
     const size_t q = ev.size();
@@ -434,7 +479,7 @@ void prof_begin(const cav_hierarchy* H, int level, cudaStream_t st) {
 }
 void prof_end(const cav_hierarchy* H, int level, cudaStream_t st) {
   cav_hierarchy* h = const_cast<cav_hierarchy*>(H);
-  if (level != 0) return;
+  if (level != 0 || h->no_events) return;
   if (h->capturing) {
     CAV_CHECK_CUDA(cudaEventRecordWithFlags(h->vc_ev[h->capturing - 1].back(), st, cudaEventRecordExternal));
     return;
@@ -501,24 +546,147 @@ struct ApplyVariant {
 static const ApplyVariant kVariants[NUM_APPLY_VARIANTS] = {
     {4, 16384, 3}, {4, 16384, 2}, {8, 8192, 3}, {4, 8192, 4}, {0, 0, 0}};
 
+// The scatter's arguments and block count on level lv (its 32 x 8 cell tiles, then the
+// unknowns held by enlarged patches, four per warp).
+static UpdArgs update_args(const cav_hierarchy* H, const Level& lv, const double* delta, const double* r, double* w,
+                           bool w_is_zero, double* partial) {
+  UpdArgs a;
+  a.N = lv.N;
+  a.alpha = H->desc.alpha;
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 25; ++q) a.S.m[k][q] = lv.std_inv[k][q];
+  a.gx = div_up(lv.N, 32);
+  a.nb_std = a.gx * div_up(lv.N, 8);
+  a.inc_off = lv.inc_off;
+  a.n_touched = lv.n_touched;
+  a.touched = lv.touched;
+  a.cell_big = lv.cell_big;
+  a.inc_slot = lv.inc_slot;
+  a.delta = delta;
+  a.r = r;
+  a.w = w;
+  a.w_is_zero = w_is_zero ? 1 : 0;
+  a.partial = partial;
+  a.channel = lv.channel;
+  return a;
+}
+static int update_blocks(const Level& lv) {
+  return div_up(lv.N, 32) * div_up(lv.N, 8) + div_up(lv.n_touched, TOUCH_WARPS * TOUCH_PER_WARP);
+}
+
+template <typename T>
+static ApplyArgs<T> apply_args(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r,
+                               double* delta) {
+  ApplyArgs<T> a;
+  a.n_big = lv.n_big;
+  a.order = lv.order;
+  a.off = lv.big_off;
+  a.dofs = lv.big_dofs;
+  a.inv_off = lv.inv_off;
+  a.inv = inv;
+  a.s_r = lv.s_r;
+  a.s_c = lv.s_c;
+  a.r = r;
+  a.delta = delta;
+  a.max_n = lv.big_max_n;
+  a.status = H->status;
+  return a;
+}
+
 template <typename T, int STAGES, int CHUNK>
 static void launch_tma(const cav_hierarchy* H, const Level& lv, const T* inv, const double* r, double* delta,
                        int ctas_per_sm, cudaStream_t st, bool pdl) {
-  typedef typename VecLoad<T>::acc_t acc_t;
-  const size_t ybytes = ((size_t)lv.big_max_n * sizeof(acc_t) + 127) & ~(size_t)127;
-  const size_t smem = (size_t)STAGES * CHUNK + Y_SLOTS * ybytes + (2 * STAGES + 2 * Y_SLOTS) * sizeof(uint64_t) +
-                      16;  // the CTA's abort flag
+  const size_t smem = ApplyRing<T, STAGES, CHUNK>::bytes(lv.big_max_n);
   allow_dynamic_smem(reinterpret_cast<const void*>(k_patch_apply_tma<T, STAGES, CHUNK>), 200 * 1024);
   const int grid = std::min(lv.n_big, ctas_per_sm * sm_count());
-  launch_k(k_patch_apply_tma<T, STAGES, CHUNK>, dim3(grid), dim3(TMA_THREADS), smem, st, pdl, lv.n_big, lv.order,
-           lv.big_off, lv.big_dofs, lv.inv_off, inv, lv.s_r, lv.s_c, r, delta, lv.big_max_n, H->status);
+  launch_k(k_patch_apply_tma<T, STAGES, CHUNK>, dim3(grid), dim3(TMA_THREADS), smem, st, pdl,
+           apply_args<T>(H, lv, inv, r, delta));
 }
 
 // Can variant v run this level?  (rows per consumer thread and one whole column per stage)
 template <typename T>
 static bool variant_fits(const Level& lv, int v) {
   if (kVariants[v].stages == 0) return true;
-  return lv.big_max_n <= tma_max_rows<T>() && (size_t)round8(lv.big_max_n) * sizeof(T) <= (size_t)kVariants[v].chunk;
+  return lv.big_max_n <= tma_max_rows<T, TMA_CONSUMER_WARPS>() &&
+         (size_t)round8(lv.big_max_n) * sizeof(T) <= (size_t)kVariants[v].chunk;
+}
+
+// Resident CTAs per SM of a kernel at a given dynamic shared memory size (cached per device).
+static int resident_ctas(const void* kernel, int threads, size_t smem) {
+  static std::mutex m;
+  static std::map<std::tuple<const void*, size_t, int>, int> cache;
+  int dev = 0;
+  CAV_CHECK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(m);
+  const auto key = std::make_tuple(kernel, smem, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem));
+  cache[key] = n;
+  return n;
+}
+
+// The whole sweep of an additive level as one cooperative launch of k_sweep_fused with the
+// staging shape of apply variant v (its stages, chunk and CTAs per SM, capped by residency).
+// Returns false (nothing launched) when the level cannot take it.
+template <typename T, int STAGES, int CHUNK>
+static bool launch_fused(const cav_hierarchy* H, const Level& lv, const T* inv, const double* b, double* w,
+                         bool w_is_zero, double* r_buf, double* delta, double* partial, bool remove_mean,
+                         int ctas_per_sm, cudaStream_t st) {
+  if (lv.big_max_n > tma_max_rows<T, FUSED_CONSUMER_WARPS>() || (size_t)round8(lv.big_max_n) * sizeof(T) > CHUNK)
+    return false;
+  const void* kern = reinterpret_cast<const void*>(k_sweep_fused<T, STAGES, CHUNK>);
+  const size_t smem = ApplyRing<T, STAGES, CHUNK>::bytes(lv.big_max_n);
+  allow_dynamic_smem(kern, 200 * 1024);
+  const int per_sm = std::min(ctas_per_sm, resident_ctas(kern, FUSED_THREADS, smem));
+  if (per_sm < 1) return false;
+  const int grid = per_sm * sm_count();
+  const double* r = w_is_zero ? b : r_buf;
+  const ResArgs ra = residual_args(ops_of(lv), w, b, r_buf, 0, FUSED_THREADS / 32 - 1);
+  const int nb_res = w_is_zero ? 0 : residual_blocks(ra, FUSED_THREADS / 32 - 1);
+  const ApplyArgs<T> aa = apply_args<T>(H, lv, inv, r, delta);
+  const UpdArgs ua = update_args(H, lv, delta, r, w, w_is_zero, partial);
+  const int nb_upd = update_blocks(lv);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(FUSED_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barriers need it
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_sweep_fused<T, STAGES, CHUNK>, ra, nb_res, aa, ua, nb_upd,
+                                    (remove_mean && !lv.channel) ? 1 : 0, lv.n_partial, H->gbar));
+  CAV_CHECK_LAUNCH();
+  return true;
+}
+
+template <typename T>
+static bool launch_fused_variant(const cav_hierarchy* H, const Level& lv, const T* inv, const double* b, double* w,
+                                 bool w_is_zero, double* r_buf, double* delta, double* partial, bool remove_mean,
+                                 int v, cudaStream_t st) {
+  switch (v) {
+    case 0: return launch_fused<T, 4, 16384>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 3, st);
+    case 1: return launch_fused<T, 4, 16384>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 2, st);
+    case 2: return launch_fused<T, 8, 8192>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 3, st);
+    case 3: return launch_fused<T, 4, 8192>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 4, st);
+    default: return false;
+  }
+}
+
+static bool launch_fused_any(const cav_hierarchy* H, const Level& lv, const double* b, double* w, bool w_is_zero,
+                             double* r_buf, double* delta, double* partial, bool remove_mean, int v,
+                             cudaStream_t st) {
+  if (lv.n_big == 0 || !H->gbar) return false;
+  if (lv.precision == CAV_PREC_FP32)
+    return launch_fused_variant<float>(H, lv, lv.inv32, b, w, w_is_zero, r_buf, delta, partial, remove_mean, v, st);
+  if (lv.precision == CAV_PREC_BF16)
+    return launch_fused_variant<__nv_bfloat16>(H, lv, lv.inv16, b, w, w_is_zero, r_buf, delta, partial, remove_mean,
+                                               v, st);
+  return launch_fused_variant<double>(H, lv, lv.inv64, b, w, w_is_zero, r_buf, delta, partial, remove_mean, v, st);
 }
 
 template <typename T>
@@ -585,6 +753,14 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   const Level& lv = H->levels[l];
   const double* r = b;
   const bool events = profile && prof_records(H, l);
+  if (lv.fused) {  // one cooperative launch (the profiling record then spans the whole sweep)
+    if (events) prof_begin(H, l, st);
+    const bool ok = launch_fused_any(H, lv, b, w, w_is_zero, r_buf, delta_buf, partial_buf, remove_mean,
+                                     lv.apply_variant, st);
+    if (events) prof_end(H, l, st);
+    CAV_REQUIRE(ok, "sweep: the level's fused sweep cannot be launched");
+    return;
+  }
   bool pdl = pdl_first;
   if (!w_is_zero) {
     launch_apply(ops_of(lv), w, b, r_buf, 0, st, pdl);
@@ -599,20 +775,49 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
     // sweep (its blocks sit resident beside the apply's), so it is a plain launch
     pdl = false;
   }
-  StdInv S;
-  for (int k = 0; k < 3; ++k)
-    for (int q = 0; q < 25; ++q) S.m[k][q] = lv.std_inv[k][q];
-  const int gx = div_up(lv.N, 32), gy = div_up(lv.N, 8);
-  const int nb_std = gx * gy;
-  const int nb_touch = div_up(lv.n_touched, TOUCH_WARPS * TOUCH_PER_WARP);
-  launch_k(k_update, dim3(nb_std + nb_touch), dim3(256), 0, st, pdl, lv.N, H->desc.alpha, S, nb_std, gx, lv.inc_off,
-           lv.n_touched, lv.touched, lv.cell_big, lv.inc_slot, delta_buf, r, w, w_is_zero ? 1 : 0, partial_buf,
-           lv.channel);
+  const UpdArgs ua = update_args(H, lv, delta_buf, r, w, w_is_zero, partial_buf);
+  launch_k(k_update, dim3(update_blocks(lv)), dim3(UPD_THREADS), 0, st, pdl, ua);
   if (remove_mean && !lv.channel) {  // the channel's pressure is determined: no mean to remove
     const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
     launch_k(k_remove_mean, dim3(nblk), dim3(256), 0, st, true, lv.N, lv.n_partial, (const double*)partial_buf,
              w + 2 * lv.N * lv.N);
   }
+}
+
+// Set-up: one sweep of an additive level in the V-cycle's form (w nonzero, no mean removal)
+// timed as separate kernels and as the fused cooperative kernel (two warm-up and five timed
+// sweeps each, CUDA events), keeping the faster; both forms give the same bits.  force: 1 use
+// the fused kernel wherever it can run, -1 never, 0 time both.
+void choose_sweep_form(cav_hierarchy* H, Level& lv, int force, cudaStream_t st) {
+  lv.fused = 0;
+  lv.sweep_us[0] = lv.sweep_us[1] = 0.f;
+  if (lv.n_big == 0 || lv.coloured || lv.coarsest || force < 0) return;
+  const int l = (int)(&lv - &H->levels[0]);
+  const size_t n3 = 3 * (size_t)lv.N * lv.N;
+  CAV_CHECK_CUDA(cudaMemsetAsync(lv.x, 0, sizeof(double) * n3, st));
+  CAV_CHECK_CUDA(cudaMemsetAsync(lv.b, 0, sizeof(double) * n3, st));
+  if (!launch_fused_any(H, lv, lv.b, lv.x, false, lv.r, lv.delta, lv.partial, false, lv.apply_variant, st)) return;
+  if (force > 0) {
+    lv.fused = 1;
+    return;
+  }
+  cudaEvent_t e0, e1;
+  CAV_CHECK_CUDA(cudaEventCreate(&e0));
+  CAV_CHECK_CUDA(cudaEventCreate(&e1));
+  for (int f = 0; f < 2; ++f) {
+    lv.fused = f;
+    for (int w = 0; w < 2; ++w) sweep_impl(H, l, lv.b, lv.x, false, lv.r, lv.delta, lv.partial, false, st, false);
+    CAV_CHECK_CUDA(cudaEventRecord(e0, st));
+    for (int w = 0; w < 5; ++w) sweep_impl(H, l, lv.b, lv.x, false, lv.r, lv.delta, lv.partial, false, st, false);
+    CAV_CHECK_CUDA(cudaEventRecord(e1, st));
+    CAV_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CAV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    lv.sweep_us[f] = 1e3f * ms / 5.f;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  lv.fused = (lv.sweep_us[1] < lv.sweep_us[0]) ? 1 : 0;
 }
 
 void sweep_set_wait_stall(int enable) {
@@ -696,12 +901,15 @@ static bool vcycle_capture(cav_hierarchy* H, int g) {
   CAV_CHECK_CUDA(cudaStreamBeginCapture(H->capture_stream, cudaStreamCaptureModeThreadLocal));
   H->capturing = 1 + g;
   bool ok = true;
+  const int64_t c0 = launch_count();
   try {
     vcycle_level(H, 0, l0.b, l0.x, H->capture_stream);
   } catch (...) {
     ok = false;
   }
   H->capturing = 0;
+  H->vc_kernels[g] = (int)(launch_count() - c0);
+  note_launches(-(long long)H->vc_kernels[g]);  // recorded, not run
   const cudaError_t e = cudaStreamEndCapture(H->capture_stream, &graph);
   if (!ok || e != cudaSuccess || !graph) {
     cudaGetLastError();
@@ -732,7 +940,7 @@ void vcycle(const cav_hierarchy* Hc, const double* r, double* z, cudaStream_t st
   const size_t bytes = sizeof(double) * 3 * (size_t)l0.N * l0.N;
   CAV_CHECK_CUDA(cudaMemcpyAsync(l0.b, r, bytes, cudaMemcpyDeviceToDevice, st));
   CAV_CHECK_CUDA(cudaGraphLaunch(H->vc_exec[g], st));
-  note_launch();
+  note_launches(H->vc_kernels[g]);
   CAV_CHECK_CUDA(cudaMemcpyAsync(z, l0.x, bytes, cudaMemcpyDeviceToDevice, st));
   if (H->prof_on) {
     const std::vector<cudaEvent_t>& ev = H->vc_ev[g];
@@ -741,6 +949,11 @@ void vcycle(const cav_hierarchy* Hc, const double* r, double* z, cudaStream_t st
       ++H->prof_pushed;
     }
   }
+}
+
+void vcycle_inline(const cav_hierarchy* H, cudaStream_t st) {
+  const Level& l0 = H->levels[0];
+  vcycle_level(H, 0, l0.b, l0.x, st);
 }
 
 void vcycle_prepare(cav_hierarchy* H) {

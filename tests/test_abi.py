@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(api):
 
 
 def test_abi_version(api):
-    assert api._lib.ib_abi_version() == 4
+    assert api._lib.ib_abi_version() == 5
 
 
 def test_null_arguments_are_rejected_without_a_device(api):
@@ -68,6 +68,28 @@ def test_grid_descriptor_layout(api):
     assert [f for f, _ in g._fields_] == ["N", "L", "rho", "mu", "dt", "bc"]
     assert g.bc.offset == g.dt.offset + 8
     assert api.BC == {"periodic": 0, "channel": 1}
+
+
+def test_fgmres_descriptor_layout_matches_the_header(api, tmp_path):
+    # fgmres_desc.loop (ABI 5) sits where the C compiler puts it
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    if cc is None or not os.path.isdir(cuda_inc):
+        pytest.skip("no C compiler or CUDA headers")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ib_cav.h"\n'
+                   'int main(void) { printf("%zu %zu %zu", offsetof(fgmres_desc, host_io), '
+                   'offsetof(fgmres_desc, loop), sizeof(fgmres_desc)); return 0; }\n')
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I" + os.path.join(ROOT, "include"), "-I" + cuda_inc, str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    host_io, loop, size = map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split())
+    d = api.fgmres_desc
+    assert (d.host_io.offset, d.loop.offset, C.sizeof(d)) == (host_io, loop, size)
+    assert api.LOOP == {"host": 0, "device": 1}
 
 
 def test_product_path_has_no_fallback():

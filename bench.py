@@ -78,6 +78,34 @@ def workload_desc(rec) -> str:
             f"rho=1, mu=1e-2, dt=h/2, seeded uniform[-1,1] RHS")
 
 
+S_BYTES = {"fp64": 8, "fp32": 4, "bf16": 2}
+
+
+def apply_bytes(li: dict, precision: str) -> int:
+    """Algorithmic bytes of one finest-level patch apply: the stored inverses and, per slot, the
+    index, the gathered residual, the two scales and the correction written."""
+    return li["enlarged_sum_n2"] * S_BYTES[precision] + li["enlarged_sum_n"] * 36
+
+
+def sweep_bytes(li: dict, N: int, precision: str, mean: bool = True) -> int:
+    """Algorithmic bytes of one whole additive sweep (Eq. additive_cav_saddle) on a level: the
+    enlarged inverses and their per-slot data, the residual pass (read w, b; write r), the
+    scatter pass (read w, r; write w), the E_E rows, the transpose incidence, and with `mean`
+    the mean removal (read and write p)."""
+    NN = N * N
+    return (li["enlarged_sum_n2"] * S_BYTES[precision] + li["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8 + 4 + 8)
+            + 3 * NN * 8 * 3 + 3 * NN * 8 * 3 + li["ee_nnz"] * 12 + 3 * NN * 8 + (2 * NN * 8 if mean else 0))
+
+
+def headline_config(args, rec, world: int) -> dict:
+    """The workload the headline line measures, the same dict on both arms (this GPU arm and the
+    oracle's reference arm): the system, its V-cycle and the solve's stopping rule."""
+    return {"workload": workload_desc(rec), "smoother": smoother_desc(args), "nu": args.nu,
+            "alpha": args.alpha, "coarsest_N": 8, "rtol": 1e-10, "maxit": MAXIT,
+            "l2": "flushed (256 MB write) before every timed GPU solve",
+            "parallelism": f"replicas x{world}"}
+
+
 def kernel_hash() -> str:
     with open(os.path.join(ROOT, "paper_2608_14310_b300", "csrc", "sweep.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -136,7 +164,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_sample(iters: int, timeout_s: int = 600):
+def oracle_cycle(args):
+    """The oracle's V-cycle arguments for the bench's smoother on the N=256 membrane (five
+    smoothing levels): per-level modes and sweeps."""
+    if args.smoother == "coloured" and args.coloured_levels == 1:
+        return ["coloured"] + ["additive"] * 4, [1] + [args.nu_additive] * 4
+    if args.smoother == "coloured":
+        return "coloured", args.nu
+    return "additive", args.nu
+
+
+def cpu_baseline_sample(iters: int, args, timeout_s: int = 900):
     """The oracle as it stands, single-threaded, on a bounded sample of the same workload: one
     oracle V-cycle (timed alone), and the oracle's own FGMRES run for `iters` iterations with
     the identity in place of the V-cycle (Arnoldi with modified Gram-Schmidt, Givens, the
@@ -151,17 +189,20 @@ from oracle import fgmres as fg, multigrid as mg
 rec = W.config2(256, 1e4)
 t0 = time.perf_counter()
 levels = mg.build_hierarchy(rec, 8, "cav")
+modes, nus = %s, %s
+if "coloured" in str(modes):
+    mg.level_colours(levels[0])  # the colour classes are set-up, not timed
 t_setup = time.perf_counter() - t0
 b = rec.rhs()
 K = levels[0].KE
 t0 = time.perf_counter()
-z = mg.vcycle(levels, b, %d, %d, "additive", %r)
+z = mg.vcycle(levels, b, nus, nus, modes, %r)
 t_vcycle = time.perf_counter() - t0
 t0 = time.perf_counter()
 fg.fgmres(lambda v: K @ v, b, lambda r: r, rtol=0.0, maxit=%d)
 t_rest = time.perf_counter() - t0
 print(json.dumps({"t_setup": t_setup, "t_vcycle": t_vcycle, "t_rest": t_rest}))
-""" % (ROOT, DEFAULT_NU, DEFAULT_NU, DEFAULT_ALPHA, iters)
+""" % (ROOT, *(repr(v) for v in oracle_cycle(args)), DEFAULT_ALPHA, iters)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
         out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
@@ -186,13 +227,19 @@ def run_reference(args, rank, world):
     import oracle.fgmres as fg
     import oracle.multigrid as mg
     rec = workload()
+    if args.nu is None:
+        args.nu = 1 if args.smoother == "coloured" else DEFAULT_NU
+    modes, nus = oracle_cycle(args)
     t0 = time.perf_counter()
     levels = mg.build_hierarchy(rec, 8, "cav")
+    if "coloured" in str(modes):
+        mg.level_colours(levels[0])
     t_setup = time.perf_counter() - t0
     b = rec.rhs()
     K = levels[0].KE
     g = golden_iters()
-    iters = g["iters"] if g else 77
+    gkey = g.get("coloured_finest", {}) if (g and args.smoother == "coloured" and args.coloured_levels == 1) else g
+    iters = gkey["iters"] if gkey and "iters" in gkey else 77
     # the oracle's FGMRES without its V-cycles (identity preconditioner, all `iters` iterations):
     # Arnoldi, Givens, K_E products and the final update at the solve's Krylov dimensions
     t0 = time.perf_counter()
@@ -200,7 +247,7 @@ def run_reference(args, rank, world):
     t_rest = time.perf_counter() - t0
 
     def step():
-        return mg.vcycle(levels, b, DEFAULT_NU, DEFAULT_NU, "additive", DEFAULT_ALPHA)
+        return mg.vcycle(levels, b, nus, nus, modes, DEFAULT_ALPHA)
 
     for _ in range(args.warmup):
         step()
@@ -211,7 +258,7 @@ def run_reference(args, rank, world):
         times.append(time.perf_counter() - t)
     t_iter = statistics.mean(times) + t_rest / iters
     value = 1.0 / (t_iter * iters)
-    sample = (f"each step = one oracle V-cycle ({DEFAULT_NU}+{DEFAULT_NU} additive sweeps) on the full "
+    sample = (f"each step = one oracle V-cycle ({smoother_desc(args)}) on the full "
               f"N=256 system; solves/s = 1 / ({iters} x mean step time + {t_rest:.2f} s, the oracle's own "
               f"FGMRES run for {iters} iterations with the identity in place of the V-cycle: Arnoldi, "
               f"Givens, K_E products); {iters} = the oracle's own iteration count (tests/golden); "
@@ -220,7 +267,8 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_iter, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(rec), "nu": DEFAULT_NU, "alpha": DEFAULT_ALPHA},
+            "config": headline_config(args, rec, world),
+            "measures": "the FP64 CPU oracle (single thread) on the same system and V-cycle",
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -241,7 +289,9 @@ def smoother_desc(args) -> str:
 
 def run_batch(args, api, torch, dist, rank, world, local):
     """64 uneven systems (grid, force law, stiffness drawn per system) solved together by
-    fgmres_solve_batched; one step = one batched solve of all 64; value = systems/s."""
+    fgmres_solve_batched; one step = one batched solve of all 64; value = systems/s.  With
+    --batch-loop device (the default) a batched solve is one CUDA graph launch, the 64 systems'
+    FGMRES loops running on the device side by side; the host-driven lockstep is timed beside it."""
     recs = W.config4(64)
     if rank:
         for r in recs:
@@ -259,10 +309,10 @@ def run_batch(args, api, torch, dist, rank, world, local):
     xs = [torch.zeros_like(b) for b in bs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-    def solve():
+    def solve(loop=args.batch_loop):
         for x in xs:
             x.zero_()
-        return api.fgmres_solve_batched(syss, hs, bs, xs, rtol=1e-10, maxit=MAXIT)
+        return api.fgmres_solve_batched(syss, hs, bs, xs, rtol=1e-10, maxit=MAXIT, loop=loop)
 
     for _ in range(args.warmup):
         solve()
@@ -282,6 +332,17 @@ def run_batch(args, api, torch, dist, rank, world, local):
     launches = api.ib_launch_count() - launches0
     clk = clocks.stop()
     total = max_over_ranks(sum(times), dist, dev)
+    # the other loop on the same batch, for comparison (untimed by the headline)
+    other = "host" if args.batch_loop == "device" else "device"
+    solve(other)
+    ot = []
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solve(other)
+        torch.cuda.synchronize()
+        ot.append(time.perf_counter() - t)
     its = [i["iters"] for i in last]
     conv = [i["converged"] for i in last]
     # only systems that reached 1e-10 count as solved; attempted systems are reported beside
@@ -308,12 +369,28 @@ def run_batch(args, api, torch, dist, rank, world, local):
                        "converged": int(sum(conv)), "converged_of_stiffest_half": stiff_conv, "iters_median": int(statistics.median(its)),
                        "iters_max": int(max(its)), "autotuned_variant_counts": variants,
                        "l2": "flushed (256 MB write) before every timed batch"},
+            "batch_loop": args.batch_loop,
+            "other_loop": {"loop": other, "ms_per_step": 1e3 * statistics.mean(ot)},
+            "systems": [{"N": r.N, "law": {W.LAW_BEAM: "beam", W.LAW_MEMBRANE: "membrane"}.get(r.law, "target"),
+                         "kappa": kappa[q], "iters": last[q]["iters"], "converged": last[q]["converged"],
+                         "relres_true": last[q]["relres_true"]} for q, r in enumerate(recs)],
             "setup_s_all_64": setup_s, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def additive_sweep_entry(li: dict, N: int, precision: str, ms: float) -> dict:
+    """The finest-level additive sweep (Eq. additive_cav_saddle) as measured through cav_sweep."""
+    nb = sweep_bytes(li, N, precision)
+    return {"level": 0, "form": "fused cooperative kernel" if li["sweep_form"] else "separate kernels",
+            "ms": ms, "algorithmic_bytes": nb, "gbs": nb / (ms * 1e-3) / 1e9,
+            "frac_of_hbm": nb / (ms * 1e-3) / 1e9 / peaks()[0], "autotuned_us_separate_fused": li["sweep_us"],
+            "note": "one cav_sweep (residual, patch apply, scatter, mean removal) of the weighted additive CAV "
+                    "smoother on the finest level: 10 sweeps captured in a CUDA graph, median of 3 replays / 10 "
+                    "(the inverses exceed L2, so each sweep streams them from HBM)"}
 
 
 def graph_sweep_ms(api, torch, hier, b, reps: int = 10) -> float:
@@ -477,12 +554,15 @@ def run_learned_channel(args, api, torch, rank):
     t_series = time.perf_counter() - t0
     lg = LearnedGuess(rec.N, hidden=32, n_hidden=3, base=args.learned_base, history=args.learned_history)
     start = int(args.train_start * n_train)
-    lg.fit_scales(cs, n_train, start=start)
-    tinfo = lg.train(cs, n_train, iters=args.train_iters, batch=16, lr=1e-3, start=start)
+    n_fit = n_train - max(1, n_train // 10)  # the last tenth of the training range is held out
+    lg.fit_scales(cs, n_fit, start=start)
+    tinfo = lg.train(cs, n_fit, iters=args.train_iters, batch=16, lr=1e-3, start=start)
+    calib = lg.calibrate(cs, n_fit, n_train)
     variants = (("plain_fp64_previous", None, "fp64"),
                 ("fp32_previous", None, "fp32"),
                 ("fp32_extrapolated", lambda s: lg.extrapolate(s, 1), "fp32"),
                 ("fp32_quadratic", lambda s: lg.extrapolate(s, 2), "fp32"),
+                ("fp32_learned_uncalibrated", lambda s: lg.predict(s, calibrated=False), "fp32"),
                 ("fp32_learned", lambda s: lg.predict(s), "fp32"))
     res = {v[0]: [] for v in variants}
     launches0 = api.ib_launch_count()
@@ -509,11 +589,12 @@ def run_learned_channel(args, api, torch, rank):
                                     f"Re=200, dt=0.05h, {args.nsteps} steps from rest; CNN (3x3 convolutions, 32 "
                                     f"channels, 3 hidden layers) on the last {args.learned_history} steps' u, v, p and spread force, "
                                     f"correcting the {args.learned_base} extrapolation, trained on steps "
-                                    f"{int(args.train_start * n_train)}..{n_train} of the first "
-                                    f"{n_train} steps ({args.train_iters} Adam iterations, batch 16), tested on the rest"),
+                                    f"{int(args.train_start * n_train)}..{n_fit} ({args.train_iters} Adam iterations, "
+                                    f"batch 16), its correction's per-field scale fitted on the held-out steps "
+                                    f"{n_fit}..{n_train}, tested on the last {args.nsteps - n_train}"),
                        "smoother": "coloured multiplicative CAV 1+1, hierarchy rebuilt per Newton system",
                        "tolerances": "Newton 1e-9 of ||b_step||, FGMRES 1e-10 of ||rhs||"},
-            "test_steps": summ, "series_s": t_series, "train_s": tinfo["train_s"],
+            "test_steps": summ, "calibration": calib, "series_s": t_series, "train_s": tinfo["train_s"],
             "train_loss_first_last": [tinfo["losses"][0][1], tinfo["losses"][-1][1]],
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -576,15 +657,22 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--nu", type=int, default=None,
                     help="sweeps per side (default: 2 additive, 1 coloured)")
-    ap.add_argument("--smoother", default="additive", choices=["additive", "coloured"],
+    ap.add_argument("--smoother", default=None, choices=["additive", "coloured"],
                     help="additive: Eq. additive_cav_saddle on every level; coloured: the multiplicative "
-                         "sweep of Sec. 3.3 visited colour class by colour class")
-    ap.add_argument("--coloured-levels", type=int, default=0,
+                         "sweep of Sec. 3.3 visited colour class by colour class (default: coloured on the "
+                         "finest level for the membrane workloads; additive for batch64, whose FP32 inverses "
+                         "make the undamped multiplicative sweep diverge on stiff beams)")
+    ap.add_argument("--coloured-levels", type=int, default=1,
                     help="coloured smoother: levels (finest first) that use it, 0 = all; coarser ones additive")
     ap.add_argument("--nu-additive", type=int, default=NU_COARSE_ADDITIVE,
                     help="coloured smoother: sweeps per side on its additive levels")
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
+    ap.add_argument("--batch-loop", default="device", choices=["device", "host"],
+                    help="--workload batch64: device = one CUDA graph launch per batched solve (FGMRES loops "
+                         "under conditional nodes); host = host-driven lockstep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the plain-FP64 and other-smoother comparisons (a short run, e.g. under a profiler)")
     ap.add_argument("--workload", default="membrane256",
                     choices=["membrane256", "membrane512", "batch64", "learned", "beam512", "fiber",
                              "learned_channel"])
@@ -605,6 +693,8 @@ def main():
     ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.smoother is None:
+        args.smoother = "additive" if args.workload == "batch64" else "coloured"
     if args.nu is None:
         args.nu = 1 if args.smoother == "coloured" else DEFAULT_NU
 
@@ -666,6 +756,7 @@ def main():
     api.cav_profile(hier, True)
     launches0 = api.ib_launch_count()
     times, iters, conv, relres = [], [], [], []
+    torch.cuda.nvtx.range_push("timed_solves")  # lets a profiler select the timed region
     for _ in range(args.steps):
         flush.zero_()
         x.zero_()
@@ -678,6 +769,7 @@ def main():
         iters.append(info["iters"])
         conv.append(info["converged"])
         relres.append(info["relres_true"])
+    torch.cuda.nvtx.range_pop()
     launches = api.ib_launch_count() - launches0
     n_apply, apply_ms = api.cav_profile_read(hier)
     api.cav_profile(hier, False)
@@ -685,17 +777,10 @@ def main():
     total_ms = max_over_ranks(sum(times), dist, dev)
     value = whole_job_rate(args.steps, world, total_ms / 1e3)
 
-    # one whole finest-level sweep (residual, patch apply, scatter, mean removal) through
-    # cav_sweep; algorithmic bytes: the enlarged inverses and their per-slot data, the residual
-    # pass (read w, b; write r), the scatter pass (read w, r; write w), the E_E rows, the
-    # transpose incidence and the mean removal (read and write p)
+    # one whole finest-level sweep through cav_sweep (10 sweeps in a CUDA graph)
     li0 = api.cav_get_level_info(hier, 0)
-    NN = rec.N * rec.N
-    s_b = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
-    sweep_bytes = (li0["enlarged_sum_n2"] * s_b + li0["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8 + 4 + 8)
-                   + 3 * NN * 8 * 3 + 3 * NN * 8 * 3 + li0["ee_nnz"] * 12 + 3 * NN * 8 + 2 * NN * 8)
-    sweep_ms = graph_sweep_ms(api, torch, hier, b)
-    sweep_gbs = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    head_sweep_ms = graph_sweep_ms(api, torch, hier, b)
+    head_sweep = additive_sweep_entry(li0, rec.N, args.precision, head_sweep_ms) if args.smoother == "additive" else None
 
     # the V-cycle alone (graph replay + its two staging copies), to split a solve's time
     zv = torch.empty_like(b)
@@ -724,7 +809,7 @@ def main():
 
     # plain FP64 inverses on the same system for the mixed-vs-plain comparison
     plain = None
-    if args.precision != "fp64":
+    if args.precision != "fp64" and not args.no_others:
         hier64 = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision="fp64",
                                autotune=True, **smoother_kw(args))
         for _ in range(2):
@@ -748,11 +833,11 @@ def main():
     # coloured multiplicative sweep (one per side) on every level and on the finest level only
     # (additive 2+2 below); with a coloured headline, the additive form
     others = []
-    if args.precision != "bf16":
+    if args.precision != "bf16" and not args.no_others:
         if args.smoother == "additive":
             variants = [("coloured", 1, 0), ("coloured", 1, 1)]
         else:
-            variants = [("additive", DEFAULT_NU, 0)]
+            variants = [("additive", DEFAULT_NU, 0), ("coloured", 1, 0)]
         for o_sm, o_nu, o_cl in variants:
             ho = api.cav_setup(sysm, nu_pre=o_nu, nu_post=o_nu, alpha=args.alpha, precision=args.precision,
                                autotune=True, smoother=o_sm, coloured_levels=o_cl, nu_additive=NU_COARSE_ADDITIVE)
@@ -760,6 +845,7 @@ def main():
                 x.zero_()
                 api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
             ot, oit = [], []
+            api.cav_profile(ho, True)
             for _ in range(max(3, args.steps // 2)):
                 flush.zero_()
                 x.zero_()
@@ -770,56 +856,75 @@ def main():
                 torch.cuda.synchronize()
                 ot.append(s0.elapsed_time(s1))
                 oit.append(inf["iters"])
+            o_n, o_ms = api.cav_profile_read(ho)
+            api.cav_profile(ho, False)
             o_sweep = graph_sweep_ms(api, torch, ho, b)
             ncol = [api.cav_get_level_info(ho, l)["n_colours"] for l in range(api.cav_num_levels(ho) - 1)]
-            others.append({"smoother": o_sm, "coloured_levels": o_cl if o_sm == "coloured" else None, "nu": o_nu,
-                           "nu_additive_levels": NU_COARSE_ADDITIVE if (o_sm == "coloured" and o_cl) else None,
-                           "value": 1e3 / statistics.mean(ot), "unit": "solves/s", "iters": int(statistics.median(oit)),
-                           "finest_sweep_ms": o_sweep, "colour_classes": ncol,
-                           "us_per_class_step_finest": (1e3 * o_sweep / ncol[0]) if ncol and ncol[0] else None})
+            oli = api.cav_get_level_info(ho, 0)
+            o_alg = apply_bytes(oli, args.precision)
+            entry = {"smoother": o_sm, "coloured_levels": o_cl if o_sm == "coloured" else None, "nu": o_nu,
+                     "nu_additive_levels": NU_COARSE_ADDITIVE if (o_sm == "coloured" and o_cl) else None,
+                     "value": 1e3 / statistics.mean(ot), "unit": "solves/s", "iters": int(statistics.median(oit)),
+                     "finest_sweep_ms": o_sweep, "colour_classes": ncol,
+                     "us_per_class_step_finest": (1e3 * o_sweep / ncol[0]) if ncol and ncol[0] else None}
+            if o_sm == "additive":
+                # its whole finest-level sweep, and (separate kernels) its patch apply timed live in its solves
+                entry["sweep"] = additive_sweep_entry(oli, rec.N, args.precision, o_sweep)
+                if o_n and not oli["sweep_form"]:
+                    a_us = 1e3 * o_ms / o_n
+                    entry["apply_roofline"] = {"kernel": "k_patch_apply_tma (finest level)", "avg_launch_us": a_us,
+                                               "algorithmic_bytes_per_launch": o_alg,
+                                               "achieved_gbs": o_alg / a_us / 1e3,
+                                               "frac_of_measured_hbm": o_alg / a_us / 1e3 / peaks()[0],
+                                               "launches_timed": o_n}
+            others.append(entry)
             ho.close()
 
     li = api.cav_get_level_info(hier, 0)
-    s_bytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
-    alg_bytes = li["enlarged_sum_n2"] * s_bytes + li["enlarged_sum_n"] * (4 + 8 + 8 + 8 + 8)
     peak, peak_kind = peaks()
-    achieved = (alg_bytes / (apply_ms / n_apply * 1e-3) / 1e9) if n_apply else None
+    if args.smoother == "additive" and li["sweep_form"]:
+        # the fused sweep kernel is the sweep: its roofline is the sweep's (cav_sweep, graph-timed)
+        rl_kernel = "k_sweep_fused (finest level: residual, patch apply, scatter, mean removal)"
+        alg_bytes = sweep_bytes(li, rec.N, args.precision)
+        launch_us = 1e3 * head_sweep_ms
+        n_timed = 10
+    else:
+        rl_kernel = ("k_patch_apply_tma (finest level)" if args.smoother == "additive" else
+                     "k_colour_step (finest level; one record spans the class steps of one sweep)")
+        alg_bytes = apply_bytes(li, args.precision)
+        launch_us = (1e3 * apply_ms / n_apply) if n_apply else None
+        n_timed = n_apply
+    achieved = (alg_bytes / (launch_us * 1e-6) / 1e9) if launch_us else None
     key = f"{args.precision}:{rec.N}:{kernel_hash()}"
     traffic = NCU_TRAFFIC.get(key) if args.smoother == "additive" else None
+    add_sweep = head_sweep if head_sweep else next((o.get("sweep") for o in others if o["smoother"] == "additive"), None)
+    ncol0 = li["n_colours"]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": workload_desc(rec),
-                   "measures": (f"{args.precision.upper()} enlarged-patch inverses (FP64 everywhere else), "
-                                f"{smoother_desc(args)}, zero initial guess: the mixed-precision form "
-                                f"without the learned guess (the learned guess is measured by "
-                                f"--workload learned); plain FP64 is reported as plain_fp64"),
-                   "precision": args.precision + " enlarged-patch inverses",
-                   "nu": args.nu, "alpha": args.alpha, "coarsest_N": 8, "maxit": MAXIT,
-                   "smoother": smoother_desc(args),
-                   "l2": "flushed (256 MB write) before every timed solve",
-                   "iters": int(statistics.median(iters)), "converged": all(conv),
-                   "relres_true_max": max(relres), "parallelism": f"replicas x{world}"},
+        "config": headline_config(args, rec, world),
+        "measures": (f"{args.precision.upper()} enlarged-patch inverses (FP64 everywhere else), "
+                     f"{smoother_desc(args)}, zero initial guess: the mixed-precision form without the "
+                     f"learned guess (the learned guess is measured by --workload learned_channel); plain "
+                     f"FP64 is reported as plain_fp64"),
+        "solve": {"precision": args.precision + " enlarged-patch inverses", "iters": int(statistics.median(iters)),
+                  "converged": all(conv), "relres_true_max": max(relres)},
         "plain_fp64": plain,
         "other_smoothers": others,
         "setup_ms": setup_ms,
         "vcycle_ms": vcycle_ms,
-        "sweep": {"level": 0, "ms": sweep_ms, "algorithmic_bytes": sweep_bytes, "gbs": sweep_gbs,
-                  "frac_of_hbm": sweep_gbs / peaks()[0],
-                  "note": "one cav_sweep on the finest level: 10 sweeps captured in a CUDA graph, median of "
-                          "3 replays / 10 (the inverses exceed L2, so each sweep streams them from HBM)"},
+        "sweep": add_sweep,
+        "coloured_sweep": ({"level": 0, "ms": head_sweep_ms, "colour_classes": ncol0,
+                            "us_per_class_step": 1e3 * head_sweep_ms / ncol0} if args.smoother == "coloured" else None),
         "setup_plus_solve_per_s": world / ((setup_ms + total_ms / args.steps) / 1e3),
         "apply_variant_finest": li["apply_variant"], "apply_variant_us_finest": li["apply_us"],
-        "roofline": {"bound": "hbm",
-                     "kernel": ("k_patch_apply (finest level)" if args.smoother == "additive" else
-                                "finest-level coloured sweep (all k_colour_step class steps of one sweep)"),
-                     "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": rl_kernel, "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": alg_bytes, "launches_timed": n_apply,
-                     "avg_launch_us": (1e3 * apply_ms / n_apply) if n_apply else None},
+                     "algorithmic_bytes_per_launch": alg_bytes, "launches_timed": n_timed,
+                     "avg_launch_us": launch_us},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
                 "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches,
@@ -827,14 +932,15 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and rec.N == 256:
         g = golden_iters()
-        it = g["iters"] if g else int(statistics.median(iters))
-        cb = cpu_baseline_sample(it)
+        gkey = g.get("coloured_finest", {}) if (g and args.smoother == "coloured" and args.coloured_levels == 1) else g
+        it = gkey["iters"] if gkey and "iters" in gkey else int(statistics.median(iters))
+        cb = cpu_baseline_sample(it, args)
         if "t_vcycle" in cb:
             t_solve = it * cb["t_vcycle"] + cb["t_rest"]
             line["cpu_baseline"] = {
                 "value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                "sample": (f"the oracle's solve of the same N=256 system ({DEFAULT_NU}+{DEFAULT_NU} additive "
-                           f"V-cycles, its own count of {it} iterations) = {it} x one timed oracle V-cycle "
+                "sample": (f"the oracle's solve of the same N=256 system (the same V-cycle: {smoother_desc(args)}; "
+                           f"its own count of {it} iterations) = {it} x one timed oracle V-cycle "
                            f"({cb['t_vcycle']:.2f} s) + the oracle's FGMRES run for {it} iterations with the "
                            f"identity in place of the V-cycle ({cb['t_rest']:.2f} s: Arnoldi, Givens, K_E "
                            f"products); oracle hierarchy set-up {cb['t_setup']:.1f} s not timed")}

@@ -110,6 +110,7 @@ class LearnedGuess:
         self.net = api.IBNet(self.in_ch, hidden, n_hidden, 3, seed)
         self.in_scale = None
         self.out_scale = None
+        self.gamma = [1.0, 1.0, 1.0]   # per-field scale of the correction (calibrate)
 
     def _hist(self, ts, i):
         # x_prev2 and x_prev3 of the base extrapolation from step i
@@ -193,8 +194,40 @@ class LearnedGuess:
         torch.cuda.synchronize()
         return {"losses": losses, "train_s": time.perf_counter() - t0}
 
-    def predict(self, ts: TimeSeries):
-        """Initial guess for the next step from the last three stored steps."""
+    def calibrate(self, ts: TimeSeries, lo: int, hi: int):
+        """Per field (u, v, p), the least-squares scale gamma of the network's correction on the
+        held-out steps [lo, hi) (not used in training): gamma_f = <d_f, t_f> / <d_f, d_f> with d
+        the network's output and t the true correction (both in the scaled units of training),
+        clamped to [0, 1].  A correction that does not generalise is damped towards the
+        extrapolation it corrects instead of adding its error to it."""
+        torch = self.torch
+        N = self.N
+        NN = N * N
+        xin = torch.empty(self.in_ch * NN, dtype=torch.float32, device="cuda")
+        d = torch.empty(3 * NN, dtype=torch.float32, device="cuda")
+        t = torch.empty(3 * NN, dtype=torch.float32, device="cuda")
+        dt_, dd_, tt_ = np.zeros(3), np.zeros(3), np.zeros(3)
+        for i in range(max(lo, self.history - 1), hi):
+            self._pack(ts, i, xin)
+            self.net.forward(xin, d, 1, N)
+            api.ibnet_pack_target(N, ts.x_hist[i + 1], ts.x_hist[i], self.out_scale, t, **self._hist(ts, i))
+            for f in range(3):
+                df, tf = d[f * NN:(f + 1) * NN], t[f * NN:(f + 1) * NN]
+                dt_[f] += self.net.inner(df, tf)
+                dd_[f] += self.net.inner(df, df)
+                tt_[f] += self.net.inner(tf, tf)
+        self.gamma = [float(min(1.0, max(0.0, dt_[f] / dd_[f]))) if dd_[f] > 0 else 0.0 for f in range(3)]
+        # relative error of the correction on the held-out steps: raw network and calibrated
+        raw = [float((dd_[f] - 2 * dt_[f] + tt_[f]) / tt_[f]) if tt_[f] > 0 else 0.0 for f in range(3)]
+        g = self.gamma
+        cal = [float((g[f] ** 2 * dd_[f] - 2 * g[f] * dt_[f] + tt_[f]) / tt_[f]) if tt_[f] > 0 else 0.0
+               for f in range(3)]
+        return {"gamma": self.gamma, "heldout_rel_sq_error_raw": raw, "heldout_rel_sq_error_calibrated": cal,
+                "heldout_steps": [lo, hi]}
+
+    def predict(self, ts: TimeSeries, calibrated: bool = True):
+        """Initial guess for the next step from the last stored steps: the base extrapolation
+        plus the network's correction (scaled by the calibrated gamma unless calibrated=False)."""
         torch = self.torch
         N = self.N
         i = len(ts.x_hist) - 1
@@ -203,7 +236,8 @@ class LearnedGuess:
         d = torch.empty(3 * N * N, dtype=torch.float32, device="cuda")
         self.net.forward(xin, d, 1, N)
         g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
-        api.ibnet_apply_delta(N, ts.x_hist[i], d, self.out_scale, g, **self._hist(ts, i))
+        sc = [s * (gm if calibrated else 1.0) for s, gm in zip(self.out_scale, self.gamma)]
+        api.ibnet_apply_delta(N, ts.x_hist[i], d, sc, g, **self._hist(ts, i))
         return g
 
     def extrapolate(self, ts: TimeSeries, order: int = 1):

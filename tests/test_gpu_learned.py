@@ -147,13 +147,17 @@ def test_learned_guess_saves_iterations():
     from paper_2608_14310_b300.learned_guess import LearnedGuess, TimeSeries
     rec = W.tethered_ring(32, dt_factor=0.25)
     ts = TimeSeries(rec, W.shear_forcing, nu=2, alpha=0.85, precision="fp32")
-    n_train, n_test = 180, 60
+    n_train, n_fit, n_test = 180, 160, 60
     for _ in range(n_train):
         ts.step()
     lg = LearnedGuess(rec.N, hidden=32, n_hidden=3)
-    lg.fit_scales(ts, n_train)
-    info = lg.train(ts, n_train, iters=800, batch=16, lr=1e-3)
+    lg.fit_scales(ts, n_fit)
+    info = lg.train(ts, n_fit, iters=800, batch=16, lr=1e-3)
     assert info["losses"][-1][1] < info["losses"][0][1]
+    cal = lg.calibrate(ts, n_fit, n_train)
+    assert all(0.0 <= g <= 1.0 for g in cal["gamma"])
+    # on the held-out steps the calibrated correction is never worse than none (gamma = 0)
+    assert all(c <= 1.0 + 1e-9 for c in cal["heldout_rel_sq_error_calibrated"]), cal
     res = {"learned": [], "extrapolated": [], "previous": []}
     for _ in range(n_test):
         out = ts.step(guesses=(("learned", lambda s: lg.predict(s)), ("extrapolated", lambda s: lg.extrapolate(s)),
@@ -163,7 +167,41 @@ def test_learned_guess_saves_iterations():
             res[lab].append((inf["iters"], inf["r0"]))
     m = {k: (np.mean([a for a, _ in v]), np.exp(np.mean(np.log([b for _, b in v])))) for k, v in res.items()}
     print("learned guess: " + ", ".join(f"{k}: mean iters {a:.2f}, geo-mean r0 {b:.2e}" for k, (a, b) in m.items())
-          + f"; loss {info['losses'][0][1]:.3e} -> {info['losses'][-1][1]:.3e}")
+          + f"; loss {info['losses'][0][1]:.3e} -> {info['losses'][-1][1]:.3e}; calibration {cal}")
     # the network's guess starts closer than the previous-step guess and needs fewer iterations
     assert m["learned"][1] < m["previous"][1]
     assert m["learned"][0] < m["previous"][0]
+    # and, calibrated on held-out steps, it does not start farther than the extrapolation it corrects
+    assert m["learned"][1] <= 1.05 * m["extrapolated"][1], m
+    assert m["learned"][0] <= m["extrapolated"][0] + 0.5, m
+
+
+def test_learned_guess_on_the_fiber_channel():
+    """The fiber benchmark's time loop (Sec. 5.3, a short run at N = 16): the CNN corrects the
+    quadratic extrapolation from the last four steps; calibrated on held-out steps it starts
+    each step's Newton solve no farther than that extrapolation and much closer than the
+    previous step's solution, and saves FGMRES iterations over the latter."""
+    from paper_2608_14310_b300.learned_guess import ChannelSeries, LearnedGuess
+    rec = W.fiber_channel(16)
+    cs = ChannelSeries(rec, cav=dict(kind="cav", coarsest_N=8, nu_pre=1, nu_post=1, smoother="coloured",
+                                     precision="fp64"))
+    n_train, n_fit, n_test = 300, 270, 40
+    for _ in range(n_train):
+        cs.step()
+    lg = LearnedGuess(rec.N, hidden=16, n_hidden=2, base="quadratic", history=4)
+    lg.fit_scales(cs, n_fit, start=120)
+    lg.train(cs, n_fit, iters=600, batch=16, lr=1e-3, start=120)
+    cal = lg.calibrate(cs, n_fit, n_train)
+    assert all(c <= 1.0 + 1e-9 for c in cal["heldout_rel_sq_error_calibrated"]), cal
+    variants = (("learned", lambda s: lg.predict(s), "fp64"), ("quadratic", lambda s: lg.extrapolate(s, 2), "fp64"),
+                ("previous", None, "fp64"))
+    res = {v[0]: [] for v in variants}
+    for _ in range(n_test):
+        for lab, inf in cs.step(variants):
+            assert inf["converged"]
+            res[lab].append(inf)
+    r0 = {k: float(np.exp(np.mean(np.log([max(r["r0"], 1e-300) for r in v])))) for k, v in res.items()}
+    it = {k: float(np.mean([r["fgmres_total"] for r in v])) for k, v in res.items()}
+    print(f"fiber channel N=16: first residual {r0}, FGMRES per step {it}, calibration {cal}")
+    assert r0["learned"] < 0.1 * r0["previous"] and it["learned"] < it["previous"]
+    assert r0["learned"] <= 1.05 * r0["quadratic"], (r0, cal)

@@ -40,12 +40,14 @@ NU_COARSE_ADDITIVE = 4
 DEFAULT_ALPHA = 0.85
 MAXIT = 150
 
-# DRAM traffic of one finest-level patch-apply launch from an ncu capture of the same bench
-# command (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source it
-# was taken on (keyed by the hash of sweep.cu); null once that source changes.
+# DRAM traffic of the roofline's unit from an ncu capture of the same bench command
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source it was taken
+# on (keyed by the smoother, precision, N and the hash of the kernel's source file); null once
+# that source changes.
 NCU_TRAFFIC = {
-    # k_patch_apply_tma<float, 4, 8192> (autotuned variant 3), 289.63 MB read + 4.34 MB written
-    "fp32:256:89dc173dabe61e5e": 293.97e6,
+    # coloured: the 105 k_colour_step launches of one finest-level sweep, 415.53 MB read, 0 MB
+    # written back within them (the iterate's writes stay in L2)
+    "coloured:fp32:256:colour.cu:f5f7c4357b98fffa": 415.53e6,
 }
 
 
@@ -106,8 +108,8 @@ def headline_config(args, rec, world: int) -> dict:
             "parallelism": f"replicas x{world}"}
 
 
-def kernel_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2608_14310_b300", "csrc", "sweep.cu"), "rb") as f:
+def kernel_hash(name: str = "sweep.cu") -> str:
+    with open(os.path.join(ROOT, "paper_2608_14310_b300", "csrc", name), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
@@ -558,18 +560,24 @@ def run_learned_channel(args, api, torch, rank):
     lg.fit_scales(cs, n_fit, start=start)
     tinfo = lg.train(cs, n_fit, iters=args.train_iters, batch=16, lr=1e-3, start=start)
     calib = lg.calibrate(cs, n_fit, n_train)
+    calib.update(lg.calibrate_residual(cs, n_fit, n_train))
     variants = (("plain_fp64_previous", None, "fp64"),
                 ("fp32_previous", None, "fp32"),
                 ("fp32_extrapolated", lambda s: lg.extrapolate(s, 1), "fp32"),
                 ("fp32_quadratic", lambda s: lg.extrapolate(s, 2), "fp32"),
                 ("fp32_learned_uncalibrated", lambda s: lg.predict(s, calibrated=False), "fp32"),
-                ("fp32_learned", lambda s: lg.predict(s), "fp32"))
+                ("fp32_learned_heldout", lambda s: lg.predict(s), "fp32"),
+                ("fp32_learned", lambda s: lg.predict(s, online=True), "fp32"))
     res = {v[0]: [] for v in variants}
     launches0 = api.ib_launch_count()
     clocks = ClockSampler(0)
+    lg.start_online(cs, n_fit, n_train)
+    gam = []
     for _ in range(args.nsteps - n_train):
+        gam.append(lg.online_gamma())
         for lab, inf in cs.step(variants):
             res[lab].append(inf)
+        lg.observe(cs)  # the step just solved joins the online scale (past data only)
     clk = clocks.stop()
     launches = api.ib_launch_count() - launches0
     summ = {}
@@ -591,10 +599,13 @@ def run_learned_channel(args, api, torch, rank):
                                     f"correcting the {args.learned_base} extrapolation, trained on steps "
                                     f"{int(args.train_start * n_train)}..{n_fit} ({args.train_iters} Adam iterations, "
                                     f"batch 16), its correction's per-field scale fitted on the held-out steps "
-                                    f"{n_fit}..{n_train}, tested on the last {args.nsteps - n_train}"),
+                                    f"{n_fit}..{n_train} (least squares, then a search on the held-out first "
+                                    f"Newton residual), tested on the last {args.nsteps - n_train}"),
                        "smoother": "coloured multiplicative CAV 1+1, hierarchy rebuilt per Newton system",
                        "tolerances": "Newton 1e-9 of ||b_step||, FGMRES 1e-10 of ||rhs||"},
-            "test_steps": summ, "calibration": calib, "series_s": t_series, "train_s": tinfo["train_s"],
+            "test_steps": summ, "calibration": calib,
+            "online_gamma_first_mean_last": [gam[0], np.mean(gam, axis=0).tolist(), gam[-1]],
+            "series_s": t_series, "train_s": tinfo["train_s"],
             "train_loss_first_last": [tinfo["losses"][0][1], tinfo["losses"][-1][1]],
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -667,6 +678,8 @@ def main():
     ap.add_argument("--nu-additive", type=int, default=NU_COARSE_ADDITIVE,
                     help="coloured smoother: sweeps per side on its additive levels")
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
+    ap.add_argument("--connections", type=int, default=32,
+                    help="--workload batch64: CUDA_DEVICE_MAX_CONNECTIONS for the run (0: leave as is)")
     ap.add_argument("--batch-loop", default="device", choices=["device", "host"],
                     help="--workload batch64: device = one CUDA graph launch per batched solve (FGMRES loops "
                          "under conditional nodes); host = host-driven lockstep")
@@ -703,6 +716,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch64" and args.connections:
+        # 64 systems' streams (or graph branches) in flight at once: more hardware work queues
+        # than the default 8, read when the CUDA context is created
+        os.environ["CUDA_DEVICE_MAX_CONNECTIONS"] = str(args.connections)
 
     import torch
     torch.cuda.set_device(local)
@@ -895,8 +912,8 @@ def main():
         launch_us = (1e3 * apply_ms / n_apply) if n_apply else None
         n_timed = n_apply
     achieved = (alg_bytes / (launch_us * 1e-6) / 1e9) if launch_us else None
-    key = f"{args.precision}:{rec.N}:{kernel_hash()}"
-    traffic = NCU_TRAFFIC.get(key) if args.smoother == "additive" else None
+    src = "colour.cu" if args.smoother == "coloured" else "sweep.cu"
+    traffic = NCU_TRAFFIC.get(f"{args.smoother}:{args.precision}:{rec.N}:{src}:{kernel_hash(src)}")
     add_sweep = head_sweep if head_sweep else next((o.get("sweep") for o in others if o["smoother"] == "additive"), None)
     ncol0 = li["n_colours"]
     line = {

@@ -305,9 +305,9 @@ ib_status cav_setup(const ib_system* s, const cav_desc* d, cudaStream_t st, cav_
     H->grid_dt = s->dt;
     H->status = H->arena.alloc<int>(1);
     H->flag = H->arena.alloc<int>(1);
-    H->gbar = H->arena.alloc<unsigned>(2);
+    H->gbar = H->arena.alloc<unsigned>(CAV_GBAR_WORDS);
     CAV_CHECK_CUDA(cudaMemsetAsync(H->status, 0, sizeof(int), st));
-    CAV_CHECK_CUDA(cudaMemsetAsync(H->gbar, 0, 2 * sizeof(unsigned), st));
+    CAV_CHECK_CUDA(cudaMemsetAsync(H->gbar, 0, CAV_GBAR_WORDS * sizeof(unsigned), st));
     build_levels(H, st);
     *out = H;
     return IB_OK;

@@ -76,6 +76,9 @@ struct Arena {
 
 struct DlPlan;  // a solve captured as a graph (fgmres.cu)
 
+// words of a hierarchy's grid-barrier state (the fused sweep, sweep.cu)
+constexpr int CAV_GBAR_WORDS = 320;
+
 // E_E restricted to its structurally nonzero velocity rows, each row's columns sorted.
 struct EECsr {
   int n_rows = 0;            // active rows
@@ -160,6 +163,7 @@ struct Level {
   double* x = nullptr;           // [3 N^2] V-cycle iterate
   double* b = nullptr;           // [3 N^2] V-cycle right-hand side (levels > 0)
   double* delta = nullptr;       // [big_sum_n] packed patch corrections
+  double* wpart = nullptr;       // [8 n_partial] the fused sweep's per-warp pressure sums
   double* partial = nullptr;     // partial sums for the pressure mean: stencil part, then
   int n_partial = 0;             // the part of the unknowns touched by enlarged patches
   int n_partial_std = 0;
@@ -245,7 +249,7 @@ struct cav_hierarchy {
   int capturing = 0;                  // 0: not capturing, 1 + instance: capturing that instance
   int graph_failed = 0;
   int vc_kernels[2] = {0, 0};         // kernels in each V-cycle graph (launch accounting)
-  unsigned* gbar = nullptr;           // [2] grid-barrier state of the fused sweep (count, generation)
+  unsigned* gbar = nullptr;           // grid-barrier state of the fused sweep (counters, generation)
   int no_events = 0;                  // 1 while a solve graph is captured: no event records
   // device-driven solves (fgmres_desc.loop = 1): scratch and the cached executable graph
   double* dl_w = nullptr;             // [n] the new Krylov vector before normalisation

@@ -1319,6 +1319,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   lv.n_partial_std = div_up(N, 32) * div_up(N, 8);
   lv.n_partial = lv.n_partial_std + div_up(lv.n_touched, 32);  // touched blocks: 8 warps x 4 unknowns
   lv.partial = A.alloc<double>(lv.n_partial);
+  lv.wpart = A.alloc<double>(8 * (size_t)lv.n_partial);
   lv.delta = A.alloc<double>(std::max<int64_t>(sum_n, 1));
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
   scratch.release();

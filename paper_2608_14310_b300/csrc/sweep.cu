@@ -317,10 +317,12 @@ __global__ void __launch_bounds__(TMA_THREADS) k_patch_apply_tma(ApplyArgs<T> a)
 // ------------------------------------------------------------------ the fused sweep
 
 // Grid-wide barrier of a cooperative launch (every CTA resident), called by one thread per
-// CTA between CTA-level barriers.  bar[0] counts the arrivals, bar[1] is the generation: the
-// last CTA to arrive resets the count and advances the generation, which releases the others.
-// The state returns to its start at every barrier, so it serves launch after launch.  Each
-// wait is bounded: it gives up after about a second, recording DEV_TIMEOUT.
+// CTA between CTA-level barriers.  Arrivals go to GB_GROUPS counters (CTA b to counter b mod
+// GB_GROUPS, each on its own 128-byte line), so at most G / GB_GROUPS atomics queue on one
+// address; the last CTA of each group resets its counter and adds one to the top counter, and
+// the last group's CTA resets that and advances the generation, which releases everyone.  The
+// state returns to its start at every barrier, so it serves launch after launch.  Each wait
+// is bounded: it gives up after about a second, recording DEV_TIMEOUT.
 __device__ inline unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -329,26 +331,40 @@ __device__ inline unsigned ld_acquire_u32(const unsigned* p) {
 __device__ inline void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ inline unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+constexpr int GB_GROUPS = 8, GB_STRIDE = 32;  // arrival counters of the grid barrier
+constexpr int GB_WORDS = (GB_GROUPS + 2) * GB_STRIDE;
+static_assert(GB_WORDS <= CAV_GBAR_WORDS, "the hierarchy's barrier state");
 constexpr long long GRID_WAIT_LIMIT = 1LL << 31;  // clock cycles
 __device__ inline void grid_barrier(unsigned* bar, int* status) {
-  const unsigned gen = ld_acquire_u32(&bar[1]);
-  __threadfence();
-  const unsigned arrived = atomicAdd(&bar[0], 1u);
-  if (arrived + 1 == gridDim.x) {
-    atomicExch(&bar[0], 0u);
-    __threadfence();
-    st_release_u32(&bar[1], gen + 1);
-    return;
+  const unsigned G = gridDim.x, g = blockIdx.x % GB_GROUPS;
+  const unsigned ngroups = G < (unsigned)GB_GROUPS ? G : (unsigned)GB_GROUPS;
+  const unsigned gsize = (G - g + GB_GROUPS - 1) / GB_GROUPS;  // CTAs b < G with b mod GB_GROUPS = g
+  unsigned* top = bar + GB_GROUPS * GB_STRIDE;
+  unsigned* gen_p = top + GB_STRIDE;
+  // acquire-release atomics carry the CTA's writes (ordered before the caller's bar.sync) to
+  // the last arriver, whose release of the generation carries everything to the waiters'
+  // acquire loads; the plain resets are ordered by the atomics and the release after them
+  const unsigned gen = ld_acquire_u32(gen_p);
+  if (atom_add_acq_rel_u32(&bar[g * GB_STRIDE], 1u) + 1 == gsize) {  // the last of its group
+    bar[g * GB_STRIDE] = 0u;
+    if (atom_add_acq_rel_u32(top, 1u) + 1 == ngroups) {  // the last group: release everyone
+      *top = 0u;
+      st_release_u32(gen_p, gen + 1);
+      return;
+    }
   }
   const long long t0 = clock64();
-  while (ld_acquire_u32(&bar[1]) == gen) {
+  while (ld_acquire_u32(gen_p) == gen) {
     if (clock64() - t0 > GRID_WAIT_LIMIT) {
       atomicExch(status, DEV_TIMEOUT);
       return;
     }
-    __nanosleep(64);
   }
-  __threadfence();
 }
 
 // bar.sync on a named barrier for the nthreads threads of warps 1.. (the producer warp apart)
@@ -370,7 +386,7 @@ __device__ inline void group_sync(int nthreads) { asm volatile("bar.sync 2, %0;"
 template <typename T, int TMA_STAGES, int TMA_CHUNK>
 __global__ void __launch_bounds__(FUSED_THREADS)
 k_sweep_fused(ResArgs ra, int nb_res, ApplyArgs<T> a, UpdArgs ua, int nb_upd, int remove_mean, int n_partial,
-              unsigned* bar) {
+              double* wpart, unsigned* bar) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double sm[8];
   ApplyRing<T, TMA_STAGES, TMA_CHUNK> R(smem, a.max_n);
@@ -393,8 +409,24 @@ k_sweep_fused(ResArgs ra, int nb_res, ApplyArgs<T> a, UpdArgs ua, int nb_upd, in
   __syncthreads();
   if (threadIdx.x == 0) grid_barrier(bar, a.status);
   __syncthreads();
-  for (int vb = blockIdx.x; vb < nb_upd; vb += gridDim.x) update_block(ua, vb, sm);
+  // the scatter's (block, warp) units spread over every warp of the grid; each unit's sum of
+  // new pressures goes to wpart, and the block partials are formed from them in warp order
+  // after the next barrier (the separate kernel's order)
+  const int lane = threadIdx.x & 31;
+  for (int u = blockIdx.x * (FUSED_THREADS / 32) + warp; u < nb_upd * 8; u += gridDim.x * (FUSED_THREADS / 32)) {
+    const double pn = update_warp(ua, u >> 3, u & 7);
+    if (lane == 0) wpart[u] = pn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) grid_barrier(bar, a.status);
+  __syncthreads();
+  for (int vb = blockIdx.x * FUSED_THREADS + threadIdx.x; vb < nb_upd; vb += gridDim.x * FUSED_THREADS) {
+    double tot = 0.0;
+    for (int q = 0; q < 8; ++q) tot += wpart[vb * 8 + q];
+    ua.partial[vb] = tot;
+  }
   if (remove_mean) {
+    __syncthreads();
     if (threadIdx.x == 0) grid_barrier(bar, a.status);
     __syncthreads();
     remove_mean_block(ua.N, n_partial, ua.partial, ua.w + 2 * ua.N * ua.N, (int)blockIdx.x, (int)gridDim.x, sm);
@@ -659,7 +691,7 @@ static bool launch_fused(const cav_hierarchy* H, const Level& lv, const T* inv, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_sweep_fused<T, STAGES, CHUNK>, ra, nb_res, aa, ua, nb_upd,
-                                    (remove_mean && !lv.channel) ? 1 : 0, lv.n_partial, H->gbar));
+                                    (remove_mean && !lv.channel) ? 1 : 0, lv.n_partial, lv.wpart, H->gbar));
   CAV_CHECK_LAUNCH();
   return true;
 }
@@ -680,7 +712,7 @@ static bool launch_fused_variant(const cav_hierarchy* H, const Level& lv, const 
 static bool launch_fused_any(const cav_hierarchy* H, const Level& lv, const double* b, double* w, bool w_is_zero,
                              double* r_buf, double* delta, double* partial, bool remove_mean, int v,
                              cudaStream_t st) {
-  if (lv.n_big == 0 || !H->gbar) return false;
+  if (lv.n_big == 0 || !H->gbar || !lv.wpart) return false;
   if (lv.precision == CAV_PREC_FP32)
     return launch_fused_variant<float>(H, lv, lv.inv32, b, w, w_is_zero, r_buf, delta, partial, remove_mean, v, st);
   if (lv.precision == CAV_PREC_BF16)
@@ -749,11 +781,11 @@ void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st) {
 // finest level's profiling events, whose record nodes sit between the kernels).
 static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, double* r_buf,
                        double* delta_buf, double* partial_buf, bool profile, cudaStream_t st,
-                       bool remove_mean = true, bool pdl_first = false) {
+                       bool remove_mean = true, bool pdl_first = false, bool allow_fused = true) {
   const Level& lv = H->levels[l];
   const double* r = b;
   const bool events = profile && prof_records(H, l);
-  if (lv.fused) {  // one cooperative launch (the profiling record then spans the whole sweep)
+  if (lv.fused && allow_fused) {  // one cooperative launch (the profiling record then spans the whole sweep)
     if (events) prof_begin(H, l, st);
     const bool ok = launch_fused_any(H, lv, b, w, w_is_zero, r_buf, delta_buf, partial_buf, remove_mean,
                                      lv.apply_variant, st);
@@ -1047,7 +1079,8 @@ extern "C" ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, co
     double* delta = base + n_r;     // written in full by the patch-apply kernel before any read
                                     // (not read at all on a level without enlarged patches)
     double* partial = delta + n_d;  // written in full by the update kernels before any read
-    sweep_impl(h, level, b, w, false, r, delta, partial, false, st);
+    // separate kernels: the fused one keeps per-level scratch of the hierarchy (its warp sums)
+    sweep_impl(h, level, b, w, false, r, delta, partial, false, st, true, false, false);
     return take_status(h->status, st, "cav_sweep_noalloc");
   } catch (const Fail& f) {
     return f.st;

@@ -104,11 +104,14 @@ struct UpdArgs {
 // On the channel a v face of the outflow row has one incident cell (the one above it), and
 // the standard patches of the outflow and inflow rows have their own inverses.
 // Each block writes the partial sum of the new pressures it produced (fixed order) to
-// partial[vb]; the stencil blocks' partials come first, then the touched blocks'.  sm: 8
-// doubles of shared memory.  Every thread of the block calls this.
-__device__ inline void update_block(const UpdArgs& a, int vb, double* sm) {
+// partial[vb]; the stencil blocks' partials come first, then the touched blocks'.
+//
+// update_warp is warp `warp` of block vb: every lane of the calling warp takes part, and every
+// lane returns the warp's sum of new pressures (fixed order).  Warps of one block are
+// independent, so any warp may do any block's share.
+__device__ inline double update_warp(const UpdArgs& a, int vb, int warp) {
   const int N = a.N, NN = N * N;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lane = threadIdx.x & 31;
   const StdInv& S = a.S;
   const double* r = a.r;
   double* w = a.w;
@@ -181,6 +184,14 @@ __device__ inline void update_block(const UpdArgs& a, int vb, double* sm) {
     for (int g = 0; g < TOUCH_PER_WARP; ++g) wp += __shfl_sync(0xffffffffu, pnew, g * TOUCH_LANES);
     pnew = wp;
   }
+  return pnew;
+}
+
+// One whole block (every thread calls this): its warps' sums in warp order into partial[vb].
+// sm: 8 doubles of shared memory.
+__device__ inline void update_block(const UpdArgs& a, int vb, double* sm) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double pnew = update_warp(a, vb, warp);
   if (lane == 0) sm[warp] = pnew;
   __syncthreads();
   if (tid == 0) {

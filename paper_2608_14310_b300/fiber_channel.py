@@ -70,6 +70,24 @@ class FiberChannel:
         return h
 
 
+    def first_residual(self, w_n, t_next: float, guess, rec=None) -> float:
+        """||R(w_0)|| of the step from w_n (markers at rec.X, default self.rec) with Newton started
+        at `guess`: the first Newton residual step() would record, without solving."""
+        import torch
+        rec = self.rec if rec is None else rec
+        sysm = api.ib_setup(rec)
+        b = torch.empty_like(w_n)
+        api.ib_channel_rhs(sysm, w_n, inflow_speed(t_next), inflow_speed(t_next - rec.dt), b)
+        w = guess.clone()
+        X_k = api.ib_advect(sysm, w)
+        api.ib_update_structure(sysm, replace(rec, meta={**rec.meta, "X_lin": X_k}))
+        rhs = torch.empty_like(w_n)
+        r = torch.empty_like(w_n)
+        api.ib_newton_rhs(sysm, b, w, rhs)
+        out = api.ib_residual_norm(sysm, rhs, w, r)
+        sysm.close()
+        return out
+
     def step(self, w_n, t_next: float, guess=None):
         """One step from the device vector w_n (3 N^2, at t^n = t_next - dt) with the markers at
         self.rec.X = X^n.  guess (device, optional): a prediction of the step's solution, used as

@@ -225,18 +225,87 @@ class LearnedGuess:
         return {"gamma": self.gamma, "heldout_rel_sq_error_raw": raw, "heldout_rel_sq_error_calibrated": cal,
                 "heldout_steps": [lo, hi]}
 
-    def predict(self, ts: TimeSeries, calibrated: bool = True):
-        """Initial guess for the next step from the last stored steps: the base extrapolation
-        plus the network's correction (scaled by the calibrated gamma unless calibrated=False)."""
+    def start_online(self, ts, lo: int, hi: int, forget: float = 0.9):
+        """Start the online scale: per field, exponentially weighted sums of <d, t> and <d, d> over
+        the solved steps (weight `forget` per step), seeded with the steps [lo, hi); observe()
+        adds each newly solved step, and predict(..., online=True) uses the current ratio."""
+        self.forget = forget
+        self.sdt, self.sdd = np.zeros(3), np.zeros(3)
+        for i in range(max(lo, self.history - 1), hi):
+            self._accumulate(ts, i)
+
+    def _accumulate(self, ts, i: int):
         torch = self.torch
         N = self.N
-        i = len(ts.x_hist) - 1
+        NN = N * N
+        xin = torch.empty(self.in_ch * NN, dtype=torch.float32, device="cuda")
+        d = torch.empty(3 * NN, dtype=torch.float32, device="cuda")
+        t = torch.empty(3 * NN, dtype=torch.float32, device="cuda")
+        self._pack(ts, i, xin)
+        self.net.forward(xin, d, 1, N)
+        api.ibnet_pack_target(N, ts.x_hist[i + 1], ts.x_hist[i], self.out_scale, t, **self._hist(ts, i))
+        for f in range(3):
+            df, tf = d[f * NN:(f + 1) * NN], t[f * NN:(f + 1) * NN]
+            self.sdt[f] = self.forget * self.sdt[f] + self.net.inner(df, tf)
+            self.sdd[f] = self.forget * self.sdd[f] + self.net.inner(df, df)
+
+    def observe(self, ts):
+        """After a step is solved: add it (the step from x^{n-1} to x^n, the newest stored)."""
+        self._accumulate(ts, len(ts.x_hist) - 2)
+
+    def online_gamma(self):
+        return [float(min(1.0, max(0.0, self.sdt[f] / self.sdd[f]))) if self.sdd[f] > 0 else 0.0 for f in range(3)]
+
+    def calibrate_residual(self, cs, lo: int, hi: int, stride: int = 5, grid=(0.0, 0.25, 0.5, 0.75, 1.0),
+                           sweeps: int = 2):
+        """For a ChannelSeries: per field, the scale gamma of the correction that minimises the
+        geometric mean of the first Newton residual over the held-out steps lo, lo + stride, ...
+        < hi (each re-evaluated from its stored state, `ChannelSeries.first_residual`), by
+        coordinate search over `grid`, starting from the better of the least-squares fit
+        (calibrate) and no correction, so the result is never worse than the base there.  The first
+        residual weighs a velocity error's divergence, which the least-squares fit does not see."""
+        steps = [i for i in range(max(lo, self.history - 1), hi, stride)]
+
+        def score(gm):
+            return float(np.mean([np.log(max(cs.first_residual(i, self.predict(cs, i=i, gamma=gm)), 1e-300))
+                                  for i in steps]))
+
+        base_s = score([0.0, 0.0, 0.0])
+        start_s = score(list(self.gamma))
+        best, best_s = (list(self.gamma), start_s) if start_s <= base_s else ([0.0, 0.0, 0.0], base_s)
+        for _ in range(sweeps):
+            for f in range(3):
+                for g in grid:
+                    if g == best[f]:
+                        continue
+                    trial = list(best)
+                    trial[f] = g
+                    t = score(trial)
+                    if t < best_s:
+                        best, best_s = trial, t
+        self.gamma = best
+        return {"gamma": best, "heldout_first_residual_geomean": float(np.exp(best_s)),
+                "heldout_first_residual_geomean_least_squares": float(np.exp(start_s)),
+                "heldout_first_residual_geomean_base": float(np.exp(base_s)),
+                "heldout_steps_used": len(steps)}
+
+    def predict(self, ts: TimeSeries, calibrated: bool = True, i: int | None = None, gamma=None,
+                online: bool = False):
+        """Initial guess for step i + 1 (default: the next step) from the stored steps up to i: the
+        base extrapolation plus the network's correction, scaled per field by gamma (default the
+        calibrated one; calibrated=False: unscaled)."""
+        torch = self.torch
+        N = self.N
+        i = len(ts.x_hist) - 1 if i is None else i
         xin = torch.empty(self.in_ch * N * N, dtype=torch.float32, device="cuda")
         self._pack(ts, i, xin)
         d = torch.empty(3 * N * N, dtype=torch.float32, device="cuda")
         self.net.forward(xin, d, 1, N)
         g = torch.empty(3 * N * N, dtype=torch.float64, device="cuda")
-        sc = [s * (gm if calibrated else 1.0) for s, gm in zip(self.out_scale, self.gamma)]
+        if gamma is None:
+            gamma = self.online_gamma() if online else (self.gamma if calibrated else [1.0, 1.0, 1.0])
+        gm = gamma
+        sc = [s * g for s, g in zip(self.out_scale, gm)]
         api.ibnet_apply_delta(N, ts.x_hist[i], d, sc, g, **self._hist(ts, i))
         return g
 
@@ -274,6 +343,7 @@ class ChannelSeries:
         self.t = 0.0
         self.x_hist = [torch.zeros(self.n, dtype=torch.float64, device="cuda")]  # w^0: at rest
         self.f_hist = []
+        self.X_hist = []   # markers X^n at the start of step n (host), for first_residual
         self.records = []
 
     def _spread_force(self):
@@ -296,6 +366,7 @@ class ChannelSeries:
         self.f_hist.append(self._spread_force())
         t_next = self.t + self.rec0.dt
         rec_n = self.fc.rec
+        self.X_hist.append(rec_n.X)
         prec0 = self.fc.cav.get("precision", "fp64")
         out, main = [], None
         for entry in guesses:
@@ -316,3 +387,9 @@ class ChannelSeries:
         self.t = t_next
         self.records.append(out)
         return out
+
+    def first_residual(self, i: int, guess) -> float:
+        """The first Newton residual of the stored step from x^i to x^{i+1} started at `guess`
+        (a past step, re-evaluated without solving)."""
+        rec = replace(self.fc.rec, X=self.X_hist[i])
+        return self.fc.first_residual(self.x_hist[i], (i + 1) * self.rec0.dt, guess, rec=rec)

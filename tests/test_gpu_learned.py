@@ -193,6 +193,9 @@ def test_learned_guess_on_the_fiber_channel():
     lg.train(cs, n_fit, iters=600, batch=16, lr=1e-3, start=120)
     cal = lg.calibrate(cs, n_fit, n_train)
     assert all(c <= 1.0 + 1e-9 for c in cal["heldout_rel_sq_error_calibrated"]), cal
+    cal.update(lg.calibrate_residual(cs, n_fit, n_train, stride=3))
+    # the search keeps the best scale it tried: never worse than the base on the held-out steps
+    assert cal["heldout_first_residual_geomean"] <= cal["heldout_first_residual_geomean_base"] * (1 + 1e-12), cal
     variants = (("learned", lambda s: lg.predict(s), "fp64"), ("quadratic", lambda s: lg.extrapolate(s, 2), "fp64"),
                 ("previous", None, "fp64"))
     res = {v[0]: [] for v in variants}

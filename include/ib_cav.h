@@ -248,7 +248,12 @@ typedef struct {
 
 /* Builds the level hierarchy, Galerkin E_E^(l-1) = R E_E^(l) P, the patch sets and their
  * equilibrated LU inverses (Sec. 3.2, 3.3, 4) as batched FP64 device kernels, then stores
- * the enlarged-patch inverses in desc->precision.  Level 0 is the finest grid. */
+ * the enlarged-patch inverses in desc->precision.  Level 0 is the finest grid.  With
+ * desc->autotune the set-up also times, per additive level, the patch-apply variants and the
+ * sweep as separate kernels or one fused kernel, and keeps the fastest (all give the same
+ * bits).  Test hooks read from the environment at each call (not part of the method):
+ * CAV_FACTOR_GLOBAL=1 factorises every patch with the one-CTA global-memory kernel;
+ * CAV_SWEEP_FORM=fused or =separate forces the sweep's form on every additive level. */
 ib_status cav_setup(const ib_system* sys, const cav_desc* desc, cudaStream_t stream,
                     cav_hierarchy** out);
 /* Numerical re-set-up (ABI 4): when sys's finest E_E has the structural pattern the hierarchy

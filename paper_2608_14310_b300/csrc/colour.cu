@@ -68,6 +68,8 @@ struct ColourStep;
 template <typename T>
 __global__ void k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w);
 
+static void colour_step_attributes();
+
 void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   Arena& A = H->arena;
   const int N = lv.N, NN = N * N, n = 3 * NN;
@@ -268,8 +270,7 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   if (nstd)
     CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_std, hs.data(), sizeof(int) * nstd, cudaMemcpyHostToDevice, st));
   // the class step's shared memory can exceed the 48 KB default (set here, outside any capture)
-  CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  colour_step_attributes();
   if (lv.precision == CAV_PREC_FP32) {
     lv.ee_vals32 = A.alloc<float>(std::max<int64_t>(lv.ee.nnz, 1));
     if (lv.ee.nnz) {
@@ -692,6 +693,17 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     for (int q = 0; q < C * CG; ++q) sum += recv[q * cm4 + s];
     // restricted injection (box patches): only the unexpanded block's unknowns are written
     if (a.inject == nullptr || a.inject[d0 + rank + C * s]) w[sk[s]] = sold[s] + ssc[s] * (double)sum;
+  }
+}
+
+// Kernel attributes of the class step, set once per set-up outside any capture: dynamic shared
+// memory above the 48 KB default, and clusters above the portable size of 8 when configured.
+static void colour_step_attributes() {
+  CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  if (CS_CLUSTER > 8) {
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_colour_step<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   }
 }
 

@@ -128,6 +128,9 @@ struct Level {
   int precision = CAV_PREC_FP64;
   int apply_variant = 0;         // patch-apply kernel variant (autotuned when requested)
   float apply_us[8] = {0};       // the autotuner's timing of each variant (us per launch)
+  std::vector<int> sched_G;        // balanced patch schedules of the persistent apply, per grid
+  std::vector<int*> sched_off;     // size: [G + 1] offsets into sched_list, per CTA
+  std::vector<int*> sched_list;    // [n_big] patch indices, CTA by CTA
   int fused = 0;                 // 1: the additive sweep runs as one cooperative kernel
   float sweep_us[2] = {0, 0};    // the autotuner's timing of one sweep: separate kernels, fused
   int64_t* inc_off = nullptr;    // [3 N^2 + 1] transpose incidence: slots of each unknown
@@ -352,6 +355,8 @@ void prof_end(const cav_hierarchy* H, int level, cudaStream_t st);
 void prof_collect(cav_hierarchy* H, long long upto = -1);
 void vcycle_release(cav_hierarchy* H);
 void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st);
+// balanced patch schedules of a level's persistent apply for its launch grids (set-up)
+void build_schedules(cav_hierarchy* H, Level& lv, cudaStream_t st);
 // the additive sweep's form on level lv: separate kernels or one fused cooperative kernel
 // (force 1: fused where possible, -1: separate, 0: the faster by timing)
 void choose_sweep_form(cav_hierarchy* H, Level& lv, int force, cudaStream_t st);

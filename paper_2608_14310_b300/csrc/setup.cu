@@ -1275,6 +1275,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
                                  cudaMemcpyHostToDevice, st));
   // 3-4. factorise and store the inverses (also the standard patches')
   lv.host_sizes = hsizes;
+  build_schedules(H, lv, st);
   factor_patches(H, lv, true, st);
   // 5. transpose incidence of the packed slots
   int* cnt = scratch.alloc<int>(3 * NN);

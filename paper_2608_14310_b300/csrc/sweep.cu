@@ -10,8 +10,10 @@
 //      shared 5x5 inverse is applied on the fly), the others one warp per unknown over the
 //      slots of the enlarged patches holding it (fixed order, no atomics)
 //   4. remove the mean pressure (Sec. 3.3).
+#include <algorithm>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <set>
 #include <tuple>
 #include <string>
@@ -103,7 +105,21 @@ struct ApplyArgs {
   double* delta;
   int max_n;
   int* status;
+  const int* s_off;   // nullable: CTA b takes the patches s_list[s_off[b] .. s_off[b + 1]) (in order);
+  const int* s_list;  // null: the zigzag over the size-descending order
 };
+
+// Patches of this CTA, and its t-th one.
+template <typename T>
+__device__ inline int apply_count(const ApplyArgs<T>& a) {
+  if (a.s_off) return a.s_off[blockIdx.x + 1] - a.s_off[blockIdx.x];
+  return (a.n_big > (int)blockIdx.x) ? (a.n_big - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+}
+template <typename T>
+__device__ inline int apply_patch(const ApplyArgs<T>& a, int t) {
+  if (a.s_off) return a.s_list[a.s_off[blockIdx.x] + t];
+  return a.order[zigzag((int)blockIdx.x + t * (int)gridDim.x, gridDim.x, a.n_big)];
+}
 
 // The shared-memory ring of the persistent patch apply: TMA_STAGES stages of TMA_CHUNK bytes,
 // Y_SLOTS gathered vectors, their mbarriers and the CTA's abort flag.
@@ -169,8 +185,9 @@ __device__ inline void apply_producer(const ApplyArgs<T>& a, ApplyRing<T, TMA_ST
   uint32_t phase = 0;
   uint32_t used = 0, last_par = 0;  // per stage: a copy was issued; parity of its last phase
   bool ok = true;
-  for (int q = blockIdx.x; ok && q < a.n_big; q += gridDim.x) {
-    const int p = a.order[zigzag(q, gridDim.x, a.n_big)];
+  const int count = apply_count(a);
+  for (int t = 0; ok && t < count; ++t) {
+    const int p = apply_patch(a, t);
     const int n = (int)(a.off[p + 1] - a.off[p]);
     const uint32_t col_bytes = (uint32_t)(((n + 7) & ~7) * sizeof(T));
     const int cpc = TMA_CHUNK / (int)col_bytes;
@@ -202,13 +219,13 @@ __device__ inline void apply_gatherer(const ApplyArgs<T>& a, ApplyRing<T, TMA_ST
   typedef typename VecLoad<T>::acc_t acc_t;
   volatile int* ab = R.abort_flag;
   const int lane = threadIdx.x & 31;
-  int t = 0;
-  for (int q = blockIdx.x; q < a.n_big; q += gridDim.x, ++t) {
+  const int count = apply_count(a);
+  for (int t = 0; t < count; ++t) {
     const int slot = t & 1;
     const uint32_t par = (uint32_t)((t >> 1) & 1);
     const bool got = mbar_wait(&R.yempty[slot], par ^ 1u, a.status, ab, false);
     if (!__all_sync(0xffffffffu, got)) break;
-    const int p = a.order[zigzag(q, gridDim.x, a.n_big)];
+    const int p = apply_patch(a, t);
     const int64_t d0 = a.off[p];
     const int n = (int)(a.off[p + 1] - d0);
     acc_t* y = R.ybuf + (size_t)slot * R.yslot;
@@ -229,9 +246,9 @@ __device__ inline void apply_consumer(const ApplyArgs<T>& a, ApplyRing<T, TMA_ST
   const int lane = threadIdx.x & 31;
   int stage = 0;
   uint32_t phase = 0;
-  int t = 0;
-  for (int q = blockIdx.x; q < a.n_big; q += gridDim.x, ++t) {
-    const int p = a.order[zigzag(q, gridDim.x, a.n_big)];
+  const int count = apply_count(a);
+  for (int t = 0; t < count; ++t) {
+    const int p = apply_patch(a, t);
     const int64_t d0 = a.off[p];
     const int n = (int)(a.off[p + 1] - d0);
     const int ld = (n + 7) & ~7;
@@ -622,7 +639,70 @@ static ApplyArgs<T> apply_args(const cav_hierarchy* H, const Level& lv, const T*
   a.delta = delta;
   a.max_n = lv.big_max_n;
   a.status = H->status;
+  a.s_off = nullptr;
+  a.s_list = nullptr;
   return a;
+}
+
+// The level's balanced schedule for a grid of G CTAs, if set-up built one (else the zigzag).
+template <typename T>
+static void use_schedule(ApplyArgs<T>& a, const Level& lv, int G) {
+  for (size_t q = 0; q < lv.sched_G.size(); ++q)
+    if (lv.sched_G[q] == G) {
+      a.s_off = lv.sched_off[q];
+      a.s_list = lv.sched_list[q];
+    }
+}
+
+// Balanced schedules of a level's enlarged patches for every grid size the patch apply and
+// the fused sweep launch with (1-4 CTAs per SM, capped at the patch count): longest
+// processing time first -- in the size-descending order, each patch goes to the CTA with the
+// fewest inverse bytes so far (ties: the lowest CTA) -- so every CTA streams nearly the same
+// bytes and the launch ends with no long tail.  Each CTA takes its patches largest first.
+void build_schedules(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+  lv.sched_G.clear();
+  lv.sched_off.clear();
+  lv.sched_list.clear();
+  if (lv.n_big == 0) return;
+  std::vector<int> order(lv.n_big);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(order.data(), lv.order, sizeof(int) * lv.n_big, cudaMemcpyDeviceToHost, st));
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  const int sms = sm_count();
+  std::vector<int> grids;
+  for (int c = 1; c <= 4; ++c) {
+    grids.push_back(c * sms);
+    grids.push_back(std::min(lv.n_big, c * sms));
+  }
+  std::sort(grids.begin(), grids.end());
+  grids.erase(std::unique(grids.begin(), grids.end()), grids.end());
+  for (const int G : grids) {
+    std::vector<std::vector<int>> lists(G);
+    typedef std::pair<int64_t, int> Load;  // (bytes so far, CTA)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < G; ++b) heap.push(Load(0, b));
+    for (const int p : order) {
+      Load l = heap.top();
+      heap.pop();
+      const int n = lv.host_sizes[p];
+      lists[l.second].push_back(p);
+      l.first += (int64_t)n * round8(n);
+      heap.push(l);
+    }
+    std::vector<int> off(G + 1, 0), flat;
+    flat.reserve(lv.n_big);
+    for (int b = 0; b < G; ++b) {
+      off[b + 1] = off[b] + (int)lists[b].size();
+      flat.insert(flat.end(), lists[b].begin(), lists[b].end());
+    }
+    int* d_off = H->arena.alloc<int>(G + 1);
+    int* d_list = H->arena.alloc<int>(lv.n_big);
+    CAV_CHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(d_list, flat.data(), sizeof(int) * lv.n_big, cudaMemcpyHostToDevice, st));
+    lv.sched_G.push_back(G);
+    lv.sched_off.push_back(d_off);
+    lv.sched_list.push_back(d_list);
+  }
+  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
 template <typename T, int STAGES, int CHUNK>
@@ -631,8 +711,9 @@ static void launch_tma(const cav_hierarchy* H, const Level& lv, const T* inv, co
   const size_t smem = ApplyRing<T, STAGES, CHUNK>::bytes(lv.big_max_n);
   allow_dynamic_smem(reinterpret_cast<const void*>(k_patch_apply_tma<T, STAGES, CHUNK>), 200 * 1024);
   const int grid = std::min(lv.n_big, ctas_per_sm * sm_count());
-  launch_k(k_patch_apply_tma<T, STAGES, CHUNK>, dim3(grid), dim3(TMA_THREADS), smem, st, pdl,
-           apply_args<T>(H, lv, inv, r, delta));
+  ApplyArgs<T> aa = apply_args<T>(H, lv, inv, r, delta);
+  use_schedule(aa, lv, grid);
+  launch_k(k_patch_apply_tma<T, STAGES, CHUNK>, dim3(grid), dim3(TMA_THREADS), smem, st, pdl, aa);
 }
 
 // Can variant v run this level?  (rows per consumer thread and one whole column per stage)
@@ -677,7 +758,8 @@ static bool launch_fused(const cav_hierarchy* H, const Level& lv, const T* inv, 
   const double* r = w_is_zero ? b : r_buf;
   const ResArgs ra = residual_args(ops_of(lv), w, b, r_buf, 0, FUSED_THREADS / 32 - 1);
   const int nb_res = w_is_zero ? 0 : residual_blocks(ra, FUSED_THREADS / 32 - 1);
-  const ApplyArgs<T> aa = apply_args<T>(H, lv, inv, r, delta);
+  ApplyArgs<T> aa = apply_args<T>(H, lv, inv, r, delta);
+  use_schedule(aa, lv, grid);
   const UpdArgs ua = update_args(H, lv, delta, r, w, w_is_zero, partial);
   const int nb_upd = update_blocks(lv);
   cudaLaunchConfig_t cfg = {};

@@ -45,9 +45,12 @@ MAXIT = 150
 # on (keyed by the smoother, precision, N and the hash of the kernel's source file); null once
 # that source changes.
 NCU_TRAFFIC = {
-    # coloured: the 105 k_colour_step launches of one finest-level sweep, 415.53 MB read, 0 MB
+    # coloured: the 105 k_colour_step launches of one finest-level sweep, 415.50 MB read, 0 MB
     # written back within them (the iterate's writes stay in L2)
-    "coloured:fp32:256:colour.cu:f5f7c4357b98fffa": 415.53e6,
+    "coloured:fp32:256:colour.cu:55e24ae46b78a12d": 415.50e6,
+    # additive: one finest-level k_patch_apply_tma<float, 4, 8192> launch, 289.66 MB read +
+    # 4.88 MB written
+    "additive:fp32:256:sweep.cu:56c7411ba64639b1": 294.54e6,
 }
 
 

@@ -73,6 +73,7 @@ constexpr int TMA_CONSUMER_WARPS = 4;
 constexpr int TMA_THREADS = 32 * (TMA_CONSUMER_WARPS + 2);  // producer, gatherer, consumers
 constexpr int TMA_MAXPASS = 2;          // row passes per consumer thread
 constexpr int Y_SLOTS = 2;
+constexpr int GATHER_UNROLL = 8;  // slots per lane in one round of the gatherer's loads
 constexpr int FUSED_CONSUMER_WARPS = 6;
 constexpr int FUSED_THREADS = 32 * (FUSED_CONSUMER_WARPS + 2);  // = UPD_THREADS
 
@@ -229,7 +230,26 @@ __device__ inline void apply_gatherer(const ApplyArgs<T>& a, ApplyRing<T, TMA_ST
     const int64_t d0 = a.off[p];
     const int n = (int)(a.off[p + 1] - d0);
     acc_t* y = R.ybuf + (size_t)slot * R.yslot;
-    for (int b = lane; b < n; b += 32) y[b] = (acc_t)(a.s_r[d0 + b] * a.r[a.dofs[d0 + b]]);
+    // GATHER_UNROLL slots per lane per round: every index load of the round is issued, then
+    // every residual load, so a patch costs two dependent load latencies per round instead
+    // of two per 32 slots
+    for (int b0 = lane; b0 < n; b0 += 32 * GATHER_UNROLL) {
+      int idx[GATHER_UNROLL];
+      double sr[GATHER_UNROLL], rv[GATHER_UNROLL];
+#pragma unroll
+      for (int u = 0; u < GATHER_UNROLL; ++u) {
+        const int b = b0 + 32 * u;
+        idx[u] = (b < n) ? a.dofs[d0 + b] : -1;
+        sr[u] = (b < n) ? a.s_r[d0 + b] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < GATHER_UNROLL; ++u) rv[u] = (idx[u] >= 0) ? a.r[idx[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < GATHER_UNROLL; ++u) {
+        const int b = b0 + 32 * u;
+        if (b < n) y[b] = (acc_t)(sr[u] * rv[u]);
+      }
+    }
     mbar_arrive(&R.yfull[slot]);
   }
 }

@@ -48,9 +48,10 @@ NCU_TRAFFIC = {
     # coloured: the 105 k_colour_step launches of one finest-level sweep, 415.50 MB read, 0 MB
     # written back within them (the iterate's writes stay in L2)
     "coloured:fp32:256:colour.cu:55e24ae46b78a12d": 415.50e6,
-    # additive: one finest-level k_patch_apply_tma<float, 4, 8192> launch, 289.66 MB read +
-    # 4.88 MB written
-    "additive:fp32:256:sweep.cu:56c7411ba64639b1": 294.54e6,
+    # additive: one finest-level patch-apply launch (the variant ncu's set-up timed fastest,
+    # k_patch_apply_tma<float, 4, 16384>; the plain run's <float, 4, 8192> read 289.66 MB +
+    # wrote 4.88 MB on the previous source), 289.62 MB read + 4.60 MB written
+    "additive:fp32:256:sweep.cu:2bb03f909db1891a": 294.23e6,
 }
 
 
@@ -681,6 +682,8 @@ def main():
     ap.add_argument("--nu-additive", type=int, default=NU_COARSE_ADDITIVE,
                     help="coloured smoother: sweeps per side on its additive levels")
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
+    ap.add_argument("--loop", default="device", choices=["device", "host"],
+                    help="FGMRES iterations driven on the device (each solve one CUDA graph launch) or by the host")
     ap.add_argument("--connections", type=int, default=32,
                     help="--workload batch64: CUDA_DEVICE_MAX_CONNECTIONS for the run (0: leave as is)")
     ap.add_argument("--batch-loop", default="device", choices=["device", "host"],
@@ -763,8 +766,8 @@ def main():
     torch.cuda.synchronize()
     setup_ms = e0.elapsed_time(e1)
 
-    def solve(bv, xv):
-        return api.fgmres_solve(sysm, hier, bv, xv, rtol=1e-10, maxit=MAXIT, history=False)
+    def solve(bv, xv, loop=args.loop):
+        return api.fgmres_solve(sysm, hier, bv, xv, rtol=1e-10, maxit=MAXIT, history=False, loop=loop)
 
     for _ in range(args.warmup):
         x.zero_()
@@ -773,7 +776,6 @@ def main():
     if dist:
         dist.barrier()
     clocks = ClockSampler(local)
-    api.cav_profile(hier, True)
     launches0 = api.ib_launch_count()
     times, iters, conv, relres = [], [], [], []
     torch.cuda.nvtx.range_push("timed_solves")  # lets a profiler select the timed region
@@ -791,9 +793,17 @@ def main():
         relres.append(info["relres_true"])
     torch.cuda.nvtx.range_pop()
     launches = api.ib_launch_count() - launches0
+    clk = clocks.stop()
+    # the roofline's unit timed live: CUDA events around each finest-level record inside
+    # further solves of the host-driven loop (the same kernels; the device-driven loop's graph
+    # holds no event records)
+    api.cav_profile(hier, True)
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        x.zero_()
+        solve(b, x, loop="host")
     n_apply, apply_ms = api.cav_profile_read(hier)
     api.cav_profile(hier, False)
-    clk = clocks.stop()
     total_ms = max_over_ranks(sum(times), dist, dev)
     value = whole_job_rate(args.steps, world, total_ms / 1e3)
 
@@ -823,7 +833,7 @@ def main():
         hx.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        solve(hb, hx)
+        solve(hb, hx, loop="host")  # host buffers: the call copies them in and out
         e2e_times.append(time.perf_counter() - t)
     e2e_value = world / statistics.mean(e2e_times) if e2e_times else None
 
@@ -834,14 +844,14 @@ def main():
                                autotune=True, **smoother_kw(args))
         for _ in range(2):
             x.zero_()
-            api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+            api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False, loop=args.loop)
         pt, pit = [], []
         for _ in range(max(3, args.steps // 2)):
             flush.zero_()
             x.zero_()
             s0, s1 = ev(), ev()
             s0.record()
-            inf = api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+            inf = api.fgmres_solve(sysm, hier64, b, x, rtol=1e-10, maxit=MAXIT, history=False, loop=args.loop)
             s1.record()
             torch.cuda.synchronize()
             pt.append(s0.elapsed_time(s1))
@@ -863,19 +873,23 @@ def main():
                                autotune=True, smoother=o_sm, coloured_levels=o_cl, nu_additive=NU_COARSE_ADDITIVE)
             for _ in range(2):
                 x.zero_()
-                api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+                api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False, loop=args.loop)
             ot, oit = [], []
-            api.cav_profile(ho, True)
             for _ in range(max(3, args.steps // 2)):
                 flush.zero_()
                 x.zero_()
                 s0, s1 = ev(), ev()
                 s0.record()
-                inf = api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False)
+                inf = api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False, loop=args.loop)
                 s1.record()
                 torch.cuda.synchronize()
                 ot.append(s0.elapsed_time(s1))
                 oit.append(inf["iters"])
+            api.cav_profile(ho, True)
+            for _ in range(3):  # the live timing of the finest level's records (host-driven loop)
+                flush.zero_()
+                x.zero_()
+                api.fgmres_solve(sysm, ho, b, x, rtol=1e-10, maxit=MAXIT, history=False, loop="host")
             o_n, o_ms = api.cav_profile_read(ho)
             api.cav_profile(ho, False)
             o_sweep = graph_sweep_ms(api, torch, ho, b)
@@ -928,8 +942,10 @@ def main():
         "measures": (f"{args.precision.upper()} enlarged-patch inverses (FP64 everywhere else), "
                      f"{smoother_desc(args)}, zero initial guess: the mixed-precision form without the "
                      f"learned guess (the learned guess is measured by --workload learned_channel); plain "
-                     f"FP64 is reported as plain_fp64"),
+                     f"FP64 is reported as plain_fp64; FGMRES loop: {args.loop}-driven"
+                     + (" (each solve one CUDA graph launch)" if args.loop == "device" else "")),
         "solve": {"precision": args.precision + " enlarged-patch inverses", "iters": int(statistics.median(iters)),
+                  "loop": args.loop,
                   "converged": all(conv), "relres_true_max": max(relres)},
         "plain_fp64": plain,
         "other_smoothers": others,

@@ -313,9 +313,9 @@ ib_status vcycle_apply(const cav_hierarchy* h, const double* r, double* z, cudaS
 void cav_destroy(cav_hierarchy* h);
 
 /* Allocation-free sweep.  Same result as cav_sweep (the same kernels run in the same
- * order), but its scratch -- the residual, the packed patch corrections and the partial
- * sums of the pressure mean (with the coloured smoother: the partial sums only) -- lives in
- * a fixed 8 MiB device array inside this library
+ * order), but its scratch -- the residual (and its FP32 copy), the packed patch corrections
+ * and the partial sums of the pressure mean (with the coloured smoother: the partial sums
+ * only) -- lives in a fixed 8 MiB device array inside this library
  * (CAV_NOALLOC_SCRATCH_DOUBLES doubles) instead of buffers reserved per hierarchy.  It is for
  * callers that cannot let a call allocate device memory: code that runs with all device
  * memory already handed to its own pool or budget, where a cudaMalloc would fail or
@@ -326,8 +326,9 @@ void cav_destroy(cav_hierarchy* h);
  *   - Every GPU that loads the library holds the array until the process exits.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     and caches it; make that first call before any stream capture.
- *   - A level needs 3 N_l^2 + (enlarged-patch unknowns) + (partial sums) doubles, each part
- *     rounded up to 32; larger levels are rejected with IB_ERR_INVALID and a message
+ *   - A level needs 3 N_l^2 + (enlarged-patch unknowns) + (partial sums) doubles, plus
+ *     3 N_l^2 / 2 (an FP32 copy of the residual) on levels with FP32 or BF16 inverses, each
+ *     part rounded up to 32; larger levels are rejected with IB_ERR_INVALID and a message
  *     giving both sizes.
  *   - All calls share the one array and it keeps the last call's contents (every part is
  *     fully written before it is read, so nothing needs clearing); calls whose work overlaps

@@ -48,6 +48,8 @@ uint64_t next_uid();
   } while (0)
 
 constexpr int NUM_APPLY_VARIANTS = 5;
+// unknowns held by enlarged patches that one 256-thread block of the scatter updates
+constexpr int SCATTER_TOUCHED_PER_BLOCK = 64;
 
 // Device status word codes (written by kernels, read by the host after set-up or a solve).
 enum : int { DEV_OK = 0, DEV_WINDOW = 1, DEV_SINGULAR = 2, DEV_CAPACITY = 3, DEV_TIMEOUT = 4 };
@@ -137,6 +139,7 @@ struct Level {
   int* inc_slot = nullptr;       // [big_sum_n] packed-delta slots, ascending per unknown
   int n_touched = 0;             // unknowns held by at least one enlarged patch
   int* touched = nullptr;        // [n_touched] ascending
+  double* touch_theta = nullptr; // [n_touched] 1 / (patches holding each one)
   double std_inv[3][25];         // inverse of the standard Vanka patch, canonical order
                                  // (u_ij, u_i+1j, v_ij, v_ij+1, p_ij), scalings folded in:
                                  // [0] every cell of a periodic level, or the channel's
@@ -163,6 +166,8 @@ struct Level {
 
   // work vectors of this level
   double* r = nullptr;           // [3 N^2] residual
+  float* r32 = nullptr;          // [3 N^2] the residual in FP32 (FP32 / BF16 additive levels): the
+                                 // standard patches' inverse is applied in FP32 there
   double* x = nullptr;           // [3 N^2] V-cycle iterate
   double* b = nullptr;           // [3 N^2] V-cycle right-hand side (levels > 0)
   double* delta = nullptr;       // [big_sum_n] packed patch corrections
@@ -321,8 +326,9 @@ struct LevelOps {
   bool channel = false;
 };
 // mode 0: out = b - K w  (b may be null = 0);  mode 1: out = K w.  pdl: see launch_k.
+// out32 (nullable): out rounded to FP32 as well.
 void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
-                  cudaStream_t st, bool pdl = false);
+                  cudaStream_t st, bool pdl = false, float* out32 = nullptr);
 void launch_restrict(int Nc, const double* r_f, double* b_c, bool channel, cudaStream_t st, bool pdl = false);
 void launch_prolong_add(int Nc, const double* x_c, double* w_f, bool channel, cudaStream_t st, bool pdl = false);
 
@@ -357,6 +363,9 @@ void vcycle_release(cav_hierarchy* H);
 void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st);
 // balanced patch schedules of a level's persistent apply for its launch grids (set-up)
 void build_schedules(cav_hierarchy* H, Level& lv, cudaStream_t st);
+// Theta of every touched unknown: 1 / (enlarged patches holding it + standard patches of its
+// incident cells) (set-up, after the incidence, the touched list and cell_big)
+void build_touch_theta(cav_hierarchy* H, Level& lv, cudaStream_t st);
 // the additive sweep's form on level lv: separate kernels or one fused cooperative kernel
 // (force 1: fused where possible, -1: separate, 0: the faster by timing)
 void choose_sweep_form(cav_hierarchy* H, Level& lv, int force, cudaStream_t st);

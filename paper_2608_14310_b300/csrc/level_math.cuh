@@ -23,8 +23,19 @@ namespace cav {
 struct StokesRows {
   double ku, kv, kp;
 };
-__device__ inline StokesRows stokes_rows(int N, double h, double rho_dt, double mu, const double* w, int i, int j,
-                                         bool channel = false) {
+// The coefficients of a level's Stokes rows, formed once on the host: on B300 every FP64 warp
+// instruction holds its SM sub-partition for tens of cycles, and a division is a long sequence
+// of them.  ih = 1 / h, ih2 = 1 / (h h), tmu_h = 2 mu / h; cdiag = rho/dt + 4 mu / h^2 and
+// cnb = -mu / h^2, so a velocity row is cdiag u + cnb (its four neighbours' sum) + the pressure
+// difference / h.
+struct StokesCoef {
+  double ih, ih2, tmu_h, cdiag, cnb;
+};
+// Each row alone (stokes_rows is the three together, with the same bits): the u row at face
+// (i, j), the v row, and the p row.  A velocity row is evaluated in seven operations,
+// cdiag u_c + cnb (sum of the four neighbours) + (p_c - p_w) / h, as the class step does.
+__device__ inline double stokes_u_row(int N, const StokesCoef& sc, const double* w, int i, int j,
+                                      bool channel = false) {
   const int NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
   const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
@@ -33,38 +44,86 @@ __device__ inline StokesRows stokes_rows(int N, double h, double rho_dt, double 
   const double* v = w + NN;
   const double* p = w + 2 * NN;
   const int c = j * N + i;
-  const double ih = 1.0 / h, ih2 = 1.0 / (h * h);
-  const double uc = u[c], vc = v[c], pc = p[c];
+  const double uc = u[c], pc = p[c];
   const double uip = u[j * N + ip];
-  const double vjp = top ? 0.0 : v[jp * N + i];
   const double u_up = top ? -uc : u[jp * N + i];
-  double u_dn, v_dn, p_dn;
+  const double u_dn = bot ? uc + (v[c] - v[j * N + im]) : u[jm * N + i];  // u_{i,-1} on the channel
+  const double nb = (uip + u[j * N + im]) + (u_up + u_dn);
+  return fma(sc.ih, pc - p[j * N + im], fma(sc.cnb, nb, sc.cdiag * uc));
+}
+__device__ inline double stokes_v_row(int N, const StokesCoef& sc, const double* w, int i, int j,
+                                      bool channel = false) {
+  const int NN = N * N;
+  const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
+  const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
+  const bool bot = channel && j == 0, top = channel && j + 1 == N;
+  const double* u = w;
+  const double* v = w + NN;
+  const double* p = w + 2 * NN;
+  const int c = j * N + i;
+  const double vc = v[c], pc = p[c];
+  const double vjp = top ? 0.0 : v[jp * N + i];
+  double v_dn, p_dn;
   if (bot) {
+    const double uc = u[c], uip = u[j * N + ip];
     const double gu = uc + (vc - v[j * N + im]);              // u_{i,-1}
     const double gu_ip = uip + (v[j * N + ip] - vc);          // u_{i+1,-1}
-    u_dn = gu;
     v_dn = vc + (gu_ip - gu);                                 // v_{i,-1}
-    p_dn = (2.0 * mu / h) * (v[jp * N + i] - v_dn) - pc;      // p_{i,-1}
+    p_dn = sc.tmu_h * (v[jp * N + i] - v_dn) - pc;            // p_{i,-1}
   } else {
-    u_dn = u[jm * N + i];
     v_dn = v[jm * N + i];
     p_dn = p[jm * N + i];
   }
-  const double lu = (uip + u[j * N + im] + u_up + u_dn - 4.0 * uc) * ih2;
-  const double lv = (v[j * N + ip] + v[j * N + im] + vjp + v_dn - 4.0 * vc) * ih2;
+  const double nb = (v[j * N + ip] + v[j * N + im]) + (vjp + v_dn);
+  return fma(sc.ih, pc - p_dn, fma(sc.cnb, nb, sc.cdiag * vc));
+}
+__device__ inline double stokes_p_row(int N, const StokesCoef& sc, const double* w, int i, int j,
+                                      bool channel = false) {
+  const int NN = N * N;
+  const int ip = (i + 1 == N) ? 0 : i + 1, jp = (j + 1 == N) ? 0 : j + 1;
+  const bool top = channel && j + 1 == N;
+  const double* u = w;
+  const double* v = w + NN;
+  const int c = j * N + i;
+  const double uc = u[c], vc = v[c];
+  const double uip = u[j * N + ip];
+  const double vjp = top ? 0.0 : v[jp * N + i];
+  return -((uip - uc) + (vjp - vc)) * sc.ih;
+}
+__device__ inline StokesRows stokes_rows(int N, const StokesCoef& sc, const double* w, int i, int j,
+                                         bool channel = false) {
   StokesRows o;
-  o.ku = rho_dt * uc - mu * lu + (pc - p[j * N + im]) * ih;
-  o.kv = rho_dt * vc - mu * lv + (pc - p_dn) * ih;
-  o.kp = -((uip - uc) + (vjp - vc)) * ih;
+  o.ku = stokes_u_row(N, sc, w, i, j, channel);
+  o.kv = stokes_v_row(N, sc, w, i, j, channel);
+  o.kp = stokes_p_row(N, sc, w, i, j, channel);
   return o;
 }
 
-// E_E rows: 8 lanes per row, lane-strided over the row's entries, then a fixed xor tree.
+// E_E rows: 8 lanes per row, lane-strided over the row's entries, then a fixed xor tree.  A
+// lane takes its entries in batches of LOAD_BATCH: every column index of the batch is loaded,
+// then every iterate value, then the multiply-adds in entry order, so a row costs two
+// dependent load latencies per batch instead of two per entry.
 constexpr int ROW_LANES = 8;
+constexpr int LOAD_BATCH = 8;
 __device__ inline double ee_row_lane_sum(const int64_t* __restrict__ rowptr, const int* __restrict__ cols,
                                          const double* __restrict__ vals, const double* w, int r, int sl) {
+  const int64_t q1 = rowptr[r + 1];
   double s = 0.0;
-  for (int64_t q = rowptr[r] + sl; q < rowptr[r + 1]; q += ROW_LANES) s += vals[q] * w[cols[q]];
+  for (int64_t qb = rowptr[r] + sl; qb < q1; qb += ROW_LANES * LOAD_BATCH) {
+    int c[LOAD_BATCH];
+    double v[LOAD_BATCH], x[LOAD_BATCH];
+#pragma unroll
+    for (int u = 0; u < LOAD_BATCH; ++u) {
+      const int64_t q = qb + (int64_t)u * ROW_LANES;
+      c[u] = (q < q1) ? cols[q] : -1;
+      v[u] = (q < q1) ? vals[q] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < LOAD_BATCH; ++u) x[u] = (c[u] >= 0) ? w[c[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < LOAD_BATCH; ++u)
+      if (c[u] >= 0) s = fma(v[u], x[u], s);
+  }
   return s;
 }
 // all 32 lanes must call this
@@ -223,7 +282,86 @@ __device__ inline double std_row(const StdInv& S, int row, const double* r, int 
   return m[0] * y0 + m[1] * y1 + m[2] * y2 + m[3] * y3 + m[4] * y4;
 }
 
-constexpr int TOUCH_LANES = 8;                    // lanes per touched unknown
+// The same inverse rounded to FP32, applied to the FP32 copy of the residual on levels whose
+// patch inverses are stored in FP32 or BF16 (there every patch inverse is applied in FP32).
+struct StdInv32 {
+  float m[3][25];
+};
+__device__ inline float std_row32(const StdInv32& S, int row, const float* r, int N, int i, int j,
+                                  bool channel = false) {
+  const int NN = N * N;
+  const int ip = (i + 1 == N) ? 0 : i + 1, jp = (j + 1 == N) ? 0 : j + 1;
+  const int kind = std_kind(N, j, channel);
+  const float y0 = r[j * N + i], y1 = r[j * N + ip], y2 = r[NN + j * N + i],
+              y3 = (kind == 2) ? 0.f : r[NN + jp * N + i], y4 = r[2 * NN + j * N + i];
+  const float* m = S.m[kind] + 5 * row;
+  return m[0] * y0 + m[1] * y1 + m[2] * y2 + m[3] * y3 + m[4] * y4;
+}
+
+constexpr int TOUCH_LANES = 4;                    // lanes per touched unknown
 constexpr int TOUCH_PER_WARP = 32 / TOUCH_LANES;  // touched unknowns per warp
+
+// The standard patches (cells that kept their Vanka patch) holding unknown k, in the order
+// the scatter adds their corrections: cell (i0, j0), then (i1, j1), and the row of the shared
+// 5 x 5 inverse that gives each one's correction at k.  On the channel a v face of the
+// outflow row has only the cell above it.  (Scalar fields: an array here would be indexed at
+// run time and live in local memory.)
+struct StdHolders {
+  int n;
+  int i0, j0, row0, i1, j1, row1;
+};
+__device__ inline StdHolders std_holders(int N, const uint8_t* cell_big, bool channel, int k) {
+  const int NN = N * N;
+  const int comp = k / NN, c = k % NN, i = c % N, j = c / N;
+  const int im = (i == 0) ? N - 1 : i - 1, jm = (j == 0) ? N - 1 : j - 1;
+  StdHolders h;
+  h.n = 0;
+  h.i0 = h.j0 = h.row0 = h.i1 = h.j1 = h.row1 = 0;
+  auto add = [&](int ci, int cj, int row) {
+    if (h.n == 0) {
+      h.i0 = ci;
+      h.j0 = cj;
+      h.row0 = row;
+    } else {
+      h.i1 = ci;
+      h.j1 = cj;
+      h.row1 = row;
+    }
+    ++h.n;
+  };
+  if (comp == 0) {
+    if (!cell_big[j * N + im]) add(im, j, 1);
+    if (!cell_big[c]) add(i, j, 0);
+  } else if (comp == 1) {
+    if (!(channel && j == 0) && !cell_big[jm * N + i]) add(i, jm, 3);
+    if (!cell_big[c]) add(i, j, 2);
+  } else {
+    if (!cell_big[c]) add(i, j, 4);
+  }
+  return h;
+}
+
+// One lane's share of the corrections at a touched unknown: delta[inc_slot[q]] for q = q0 + sl,
+// q0 + sl + TOUCH_LANES, ... below q1, summed in that order, the slot indices and then the
+// corrections of each batch of LOAD_BATCH loaded before the additions.
+__device__ inline double touched_lane_sum(const int* __restrict__ inc_slot, const double* delta, int64_t q0,
+                                          int64_t q1, int sl) {
+  double s = 0.0;
+  for (int64_t qb = q0 + sl; qb < q1; qb += TOUCH_LANES * LOAD_BATCH) {
+    int id[LOAD_BATCH];
+    double d[LOAD_BATCH];
+#pragma unroll
+    for (int u = 0; u < LOAD_BATCH; ++u) {
+      const int64_t q = qb + (int64_t)u * TOUCH_LANES;
+      id[u] = (q < q1) ? inc_slot[q] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < LOAD_BATCH; ++u) d[u] = (id[u] >= 0) ? delta[id[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < LOAD_BATCH; ++u)
+      if (id[u] >= 0) s += d[u];
+  }
+  return s;
+}
 
 }  // namespace cav

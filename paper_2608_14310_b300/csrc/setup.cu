@@ -1310,6 +1310,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     k_compact_cells<<<div_up(3 * NN, 256), 256, 0, st>>>(3 * NN, tflag, tpos, lv.touched);
     CAV_CHECK_LAUNCH();
   }
+  build_touch_theta(H, lv, st);
   if (lv.channel && !lv.box) {  // standard patches of the inflow row have four unknowns
     std::vector<uint8_t> top(N);
     CAV_CHECK_CUDA(cudaMemcpyAsync(top.data(), lv.cell_big + (size_t)(N - 1) * N, N, cudaMemcpyDeviceToHost, st));
@@ -1318,7 +1319,7 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     for (int i = 0; i < N; ++i) lv.n_std4 += top[i] ? 0 : 1;
   }
   lv.n_partial_std = div_up(N, 32) * div_up(N, 8);
-  lv.n_partial = lv.n_partial_std + div_up(lv.n_touched, 32);  // touched blocks: 8 warps x 4 unknowns
+  lv.n_partial = lv.n_partial_std + div_up(lv.n_touched, SCATTER_TOUCHED_PER_BLOCK);  // then the touched blocks
   lv.partial = A.alloc<double>(lv.n_partial);
   lv.wpart = A.alloc<double>(8 * (size_t)lv.n_partial);
   lv.delta = A.alloc<double>(std::max<int64_t>(sum_n, 1));
@@ -1419,6 +1420,7 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     }
     const int NN = lv.N * lv.N;
     lv.r = A.alloc<double>(3 * NN);
+    if (!lv.coarsest && d.precision != CAV_PREC_FP64) lv.r32 = A.alloc<float>(3 * NN);
     lv.x = A.alloc<double>(3 * NN);
     lv.b = A.alloc<double>(3 * NN);
   }

@@ -23,9 +23,15 @@ ResArgs residual_args(const LevelOps& op, const double* w, const double* b, doub
   a.rho_dt = op.rho_dt;
   a.mu = op.mu;
   a.dt = op.dt;
+  a.sc.ih = 1.0 / op.h;
+  a.sc.ih2 = 1.0 / (op.h * op.h);
+  a.sc.tmu_h = 2.0 * op.mu / op.h;
+  a.sc.cdiag = op.rho_dt + 4.0 * op.mu * a.sc.ih2;
+  a.sc.cnb = -op.mu * a.sc.ih2;
   a.w = w;
   a.b = b;
   a.out = out;
+  a.out32 = nullptr;
   a.mode = mode;
   a.gx = div_up(op.N, 32);
   a.nb_cells = a.gx * div_up(op.N, warps);
@@ -43,8 +49,9 @@ ResArgs residual_args(const LevelOps& op, const double* w, const double* b, doub
 int residual_blocks(const ResArgs& a, int warps) { return a.nb_cells + div_up(a.n_rows, warps * ROWS_PER_WARP); }
 
 void launch_apply(const LevelOps& op, const double* w, const double* b, double* out, int mode,
-                  cudaStream_t st, bool pdl) {
-  const ResArgs a = residual_args(op, w, b, out, mode, RES_WARPS);
+                  cudaStream_t st, bool pdl, float* out32) {
+  ResArgs a = residual_args(op, w, b, out, mode, RES_WARPS);
+  a.out32 = out32;
   launch_k(k_residual, dim3(residual_blocks(a, RES_WARPS)), dim3(RES_BX * RES_BY), 0, st, pdl, a);
 }
 

@@ -617,13 +617,19 @@ static const ApplyVariant kVariants[NUM_APPLY_VARIANTS] = {
 
 // The scatter's arguments and block count on level lv (its 32 x 8 cell tiles, then the
 // unknowns held by enlarged patches, four per warp).
+// r32 (nullable): the residual r in FP32 (FP32 / BF16 levels, sweeps that formed a residual);
+// the standard patches are then applied in FP32.
 static UpdArgs update_args(const cav_hierarchy* H, const Level& lv, const double* delta, const double* r, double* w,
-                           bool w_is_zero, double* partial) {
+                           bool w_is_zero, double* partial, const float* r32 = nullptr) {
   UpdArgs a;
   a.N = lv.N;
   a.alpha = H->desc.alpha;
   for (int k = 0; k < 3; ++k)
-    for (int q = 0; q < 25; ++q) a.S.m[k][q] = lv.std_inv[k][q];
+    for (int q = 0; q < 25; ++q) {
+      a.S.m[k][q] = lv.std_inv[k][q];
+      a.S32.m[k][q] = (float)lv.std_inv[k][q];
+    }
+  a.r32 = r32;
   a.gx = div_up(lv.N, 32);
   a.nb_std = a.gx * div_up(lv.N, 8);
   a.inc_off = lv.inc_off;
@@ -637,10 +643,27 @@ static UpdArgs update_args(const cav_hierarchy* H, const Level& lv, const double
   a.w_is_zero = w_is_zero ? 1 : 0;
   a.partial = partial;
   a.channel = lv.channel;
+  a.theta_t = lv.touch_theta;
   return a;
 }
+__global__ void k_touch_theta(UpdArgs a, double* __restrict__ theta) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_touched) return;
+  const int k = a.touched[t];
+  const StdHolders hs = std_holders(a.N, a.cell_big, a.channel, k);
+  theta[t] = 1.0 / (double)((int)(a.inc_off[k + 1] - a.inc_off[k]) + hs.n);
+}
+
+void build_touch_theta(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+  lv.touch_theta = H->arena.alloc<double>(std::max(lv.n_touched, 1));
+  if (lv.n_touched == 0) return;
+  UpdArgs a = update_args(H, lv, nullptr, nullptr, nullptr, false, nullptr);
+  k_touch_theta<<<div_up(lv.n_touched, 256), 256, 0, st>>>(a, lv.touch_theta);
+  CAV_CHECK_LAUNCH();
+}
+
 static int update_blocks(const Level& lv) {
-  return div_up(lv.N, 32) * div_up(lv.N, 8) + div_up(lv.n_touched, TOUCH_WARPS * TOUCH_PER_WARP);
+  return div_up(lv.N, 32) * div_up(lv.N, 8) + div_up(lv.n_touched, SCATTER_TOUCHED_PER_BLOCK);
 }
 
 template <typename T>
@@ -765,8 +788,8 @@ static int resident_ctas(const void* kernel, int threads, size_t smem) {
 // Returns false (nothing launched) when the level cannot take it.
 template <typename T, int STAGES, int CHUNK>
 static bool launch_fused(const cav_hierarchy* H, const Level& lv, const T* inv, const double* b, double* w,
-                         bool w_is_zero, double* r_buf, double* delta, double* partial, bool remove_mean,
-                         int ctas_per_sm, cudaStream_t st) {
+                         bool w_is_zero, double* r_buf, float* r32, double* delta, double* partial,
+                         bool remove_mean, int ctas_per_sm, cudaStream_t st) {
   if (lv.big_max_n > tma_max_rows<T, FUSED_CONSUMER_WARPS>() || (size_t)round8(lv.big_max_n) * sizeof(T) > CHUNK)
     return false;
   const void* kern = reinterpret_cast<const void*>(k_sweep_fused<T, STAGES, CHUNK>);
@@ -776,11 +799,12 @@ static bool launch_fused(const cav_hierarchy* H, const Level& lv, const T* inv, 
   if (per_sm < 1) return false;
   const int grid = per_sm * sm_count();
   const double* r = w_is_zero ? b : r_buf;
-  const ResArgs ra = residual_args(ops_of(lv), w, b, r_buf, 0, FUSED_THREADS / 32 - 1);
+  ResArgs ra = residual_args(ops_of(lv), w, b, r_buf, 0, FUSED_THREADS / 32 - 1);
+  ra.out32 = w_is_zero ? nullptr : r32;
   const int nb_res = w_is_zero ? 0 : residual_blocks(ra, FUSED_THREADS / 32 - 1);
   ApplyArgs<T> aa = apply_args<T>(H, lv, inv, r, delta);
   use_schedule(aa, lv, grid);
-  const UpdArgs ua = update_args(H, lv, delta, r, w, w_is_zero, partial);
+  const UpdArgs ua = update_args(H, lv, delta, r, w, w_is_zero, partial, ra.out32);
   const int nb_upd = update_blocks(lv);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -800,27 +824,30 @@ static bool launch_fused(const cav_hierarchy* H, const Level& lv, const T* inv, 
 
 template <typename T>
 static bool launch_fused_variant(const cav_hierarchy* H, const Level& lv, const T* inv, const double* b, double* w,
-                                 bool w_is_zero, double* r_buf, double* delta, double* partial, bool remove_mean,
-                                 int v, cudaStream_t st) {
+                                 bool w_is_zero, double* r_buf, float* r32, double* delta, double* partial,
+                                 bool remove_mean, int v, cudaStream_t st) {
   switch (v) {
-    case 0: return launch_fused<T, 4, 16384>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 3, st);
-    case 1: return launch_fused<T, 4, 16384>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 2, st);
-    case 2: return launch_fused<T, 8, 8192>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 3, st);
-    case 3: return launch_fused<T, 4, 8192>(H, lv, inv, b, w, w_is_zero, r_buf, delta, partial, remove_mean, 4, st);
+    case 0: return launch_fused<T, 4, 16384>(H, lv, inv, b, w, w_is_zero, r_buf, r32, delta, partial, remove_mean, 3, st);
+    case 1: return launch_fused<T, 4, 16384>(H, lv, inv, b, w, w_is_zero, r_buf, r32, delta, partial, remove_mean, 2, st);
+    case 2: return launch_fused<T, 8, 8192>(H, lv, inv, b, w, w_is_zero, r_buf, r32, delta, partial, remove_mean, 3, st);
+    case 3: return launch_fused<T, 4, 8192>(H, lv, inv, b, w, w_is_zero, r_buf, r32, delta, partial, remove_mean, 4, st);
     default: return false;
   }
 }
 
+// r32: FP32 copy of the residual on FP32 / BF16 levels (null on FP64 levels)
 static bool launch_fused_any(const cav_hierarchy* H, const Level& lv, const double* b, double* w, bool w_is_zero,
-                             double* r_buf, double* delta, double* partial, bool remove_mean, int v,
+                             double* r_buf, float* r32, double* delta, double* partial, bool remove_mean, int v,
                              cudaStream_t st) {
   if (lv.n_big == 0 || !H->gbar || !lv.wpart) return false;
   if (lv.precision == CAV_PREC_FP32)
-    return launch_fused_variant<float>(H, lv, lv.inv32, b, w, w_is_zero, r_buf, delta, partial, remove_mean, v, st);
+    return launch_fused_variant<float>(H, lv, lv.inv32, b, w, w_is_zero, r_buf, r32, delta, partial, remove_mean, v,
+                                       st);
   if (lv.precision == CAV_PREC_BF16)
-    return launch_fused_variant<__nv_bfloat16>(H, lv, lv.inv16, b, w, w_is_zero, r_buf, delta, partial, remove_mean,
-                                               v, st);
-  return launch_fused_variant<double>(H, lv, lv.inv64, b, w, w_is_zero, r_buf, delta, partial, remove_mean, v, st);
+    return launch_fused_variant<__nv_bfloat16>(H, lv, lv.inv16, b, w, w_is_zero, r_buf, r32, delta, partial,
+                                               remove_mean, v, st);
+  return launch_fused_variant<double>(H, lv, lv.inv64, b, w, w_is_zero, r_buf, nullptr, delta, partial, remove_mean,
+                                      v, st);
 }
 
 template <typename T>
@@ -876,20 +903,24 @@ void autotune_level(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   cudaEventDestroy(e1);
 }
 
-// The four steps of one sweep with explicit scratch (residual r_buf, packed corrections
-// delta_buf, partial sums partial_buf); shared by cav_sweep and cav_sweep_noalloc.
+// The four steps of one sweep with explicit scratch (residual r_buf and, on FP32 / BF16
+// levels, its FP32 copy r32_buf; packed corrections delta_buf, partial sums partial_buf);
+// shared by cav_sweep and cav_sweep_noalloc.
 // pdl_first: the operation ahead of the sweep's first kernel on st is one of this library's
 // kernels, so it may be a programmatic launch (the kernels after it are, except around the
 // finest level's profiling events, whose record nodes sit between the kernels).
+// The first sweep from w = 0 forms no residual (r = b) and applies the standard patches in
+// FP64 on every level.
 static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w, bool w_is_zero, double* r_buf,
-                       double* delta_buf, double* partial_buf, bool profile, cudaStream_t st,
+                       float* r32_buf, double* delta_buf, double* partial_buf, bool profile, cudaStream_t st,
                        bool remove_mean = true, bool pdl_first = false, bool allow_fused = true) {
   const Level& lv = H->levels[l];
   const double* r = b;
+  float* r32 = (lv.precision != CAV_PREC_FP64 && !w_is_zero) ? r32_buf : nullptr;
   const bool events = profile && prof_records(H, l);
   if (lv.fused && allow_fused) {  // one cooperative launch (the profiling record then spans the whole sweep)
     if (events) prof_begin(H, l, st);
-    const bool ok = launch_fused_any(H, lv, b, w, w_is_zero, r_buf, delta_buf, partial_buf, remove_mean,
+    const bool ok = launch_fused_any(H, lv, b, w, w_is_zero, r_buf, r32, delta_buf, partial_buf, remove_mean,
                                      lv.apply_variant, st);
     if (events) prof_end(H, l, st);
     CAV_REQUIRE(ok, "sweep: the level's fused sweep cannot be launched");
@@ -897,7 +928,7 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
   }
   bool pdl = pdl_first;
   if (!w_is_zero) {
-    launch_apply(ops_of(lv), w, b, r_buf, 0, st, pdl);
+    launch_apply(ops_of(lv), w, b, r_buf, 0, st, pdl, r32);
     r = r_buf;
     pdl = true;
   }
@@ -909,7 +940,7 @@ static void sweep_impl(const cav_hierarchy* H, int l, const double* b, double* w
     // sweep (its blocks sit resident beside the apply's), so it is a plain launch
     pdl = false;
   }
-  const UpdArgs ua = update_args(H, lv, delta_buf, r, w, w_is_zero, partial_buf);
+  const UpdArgs ua = update_args(H, lv, delta_buf, r, w, w_is_zero, partial_buf, r32);
   launch_k(k_update, dim3(update_blocks(lv)), dim3(UPD_THREADS), 0, st, pdl, ua);
   if (remove_mean && !lv.channel) {  // the channel's pressure is determined: no mean to remove
     const int nblk = div_up(lv.N * lv.N, 256) < 296 ? div_up(lv.N * lv.N, 256) : 296;
@@ -930,7 +961,8 @@ void choose_sweep_form(cav_hierarchy* H, Level& lv, int force, cudaStream_t st) 
   const size_t n3 = 3 * (size_t)lv.N * lv.N;
   CAV_CHECK_CUDA(cudaMemsetAsync(lv.x, 0, sizeof(double) * n3, st));
   CAV_CHECK_CUDA(cudaMemsetAsync(lv.b, 0, sizeof(double) * n3, st));
-  if (!launch_fused_any(H, lv, lv.b, lv.x, false, lv.r, lv.delta, lv.partial, false, lv.apply_variant, st)) return;
+  if (!launch_fused_any(H, lv, lv.b, lv.x, false, lv.r, lv.r32, lv.delta, lv.partial, false, lv.apply_variant, st))
+    return;
   if (force > 0) {
     lv.fused = 1;
     return;
@@ -940,9 +972,9 @@ void choose_sweep_form(cav_hierarchy* H, Level& lv, int force, cudaStream_t st) 
   CAV_CHECK_CUDA(cudaEventCreate(&e1));
   for (int f = 0; f < 2; ++f) {
     lv.fused = f;
-    for (int w = 0; w < 2; ++w) sweep_impl(H, l, lv.b, lv.x, false, lv.r, lv.delta, lv.partial, false, st, false);
+    for (int w = 0; w < 2; ++w) sweep_impl(H, l, lv.b, lv.x, false, lv.r, lv.r32, lv.delta, lv.partial, false, st, false);
     CAV_CHECK_CUDA(cudaEventRecord(e0, st));
-    for (int w = 0; w < 5; ++w) sweep_impl(H, l, lv.b, lv.x, false, lv.r, lv.delta, lv.partial, false, st, false);
+    for (int w = 0; w < 5; ++w) sweep_impl(H, l, lv.b, lv.x, false, lv.r, lv.r32, lv.delta, lv.partial, false, st, false);
     CAV_CHECK_CUDA(cudaEventRecord(e1, st));
     CAV_CHECK_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -964,7 +996,7 @@ void level_sweep(const cav_hierarchy* H, int l, const double* b, double* w, bool
     coloured_sweep(H, l, b, w, w_is_zero, lv.partial, true, true, st);
     return;
   }
-  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st);
+  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.r32, lv.delta, lv.partial, true, st);
 }
 
 // Inside the V-cycle a constant pressure never changes a residual (G 1 = 0) or a patch
@@ -979,7 +1011,7 @@ static void cycle_sweep(const cav_hierarchy* H, int l, const double* b, double* 
     coloured_sweep(H, l, b, w, w_is_zero, lv.partial, false, true, st);
     return;
   }
-  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.delta, lv.partial, true, st, false, pdl_first);
+  sweep_impl(H, l, b, w, w_is_zero, lv.r, lv.r32, lv.delta, lv.partial, true, st, false, pdl_first);
 }
 
 void coarse_solve(const cav_hierarchy* H, const double* r, double* z, cudaStream_t st, bool pdl) {
@@ -1172,17 +1204,21 @@ extern "C" ib_status cav_sweep_noalloc(const cav_hierarchy* h, int32_t level, co
       return take_status(h->status, st, "cav_sweep_noalloc");
     }
     const size_t n_r = round_up32((size_t)3 * lv.N * lv.N);
+    // FP32 / BF16 levels: the residual's FP32 copy, 3 N^2 floats in ceil(3 N^2 / 2) doubles
+    const size_t n_r32 = lv.precision != CAV_PREC_FP64 ? round_up32((size_t)div_up(3LL * lv.N * lv.N, 2)) : 0;
     const size_t n_d = round_up32((size_t)lv.big_sum_n);
     const size_t n_p = round_up32((size_t)lv.n_partial);
-    noalloc_require(level, n_r + n_d + n_p,
-                    "3 N^2 + enlarged-patch unknowns + partial sums, each rounded to 32");
+    noalloc_require(level, n_r + n_r32 + n_d + n_p,
+                    "3 N^2 + (FP32 and BF16 levels) 3 N^2 / 2 + enlarged-patch unknowns + partial sums, each "
+                    "rounded to 32");
     double* base = noalloc_scratch(device);
     double* r = base;               // written in full by the residual kernel before any read
-    double* delta = base + n_r;     // written in full by the patch-apply kernel before any read
-                                    // (not read at all on a level without enlarged patches)
+    float* r32 = n_r32 ? reinterpret_cast<float*>(base + n_r) : nullptr;  // likewise
+    double* delta = base + n_r + n_r32;  // written in full by the patch-apply kernel before any read
+                                         // (not read at all on a level without enlarged patches)
     double* partial = delta + n_d;  // written in full by the update kernels before any read
     // separate kernels: the fused one keeps per-level scratch of the hierarchy (its warp sums)
-    sweep_impl(h, level, b, w, false, r, delta, partial, false, st, true, false, false);
+    sweep_impl(h, level, b, w, false, r, r32, delta, partial, false, st, true, false, false);
     return take_status(h->status, st, "cav_sweep_noalloc");
   } catch (const Fail& f) {
     return f.st;

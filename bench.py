@@ -38,6 +38,10 @@ DEFAULT_NU = 2
 # (the coarse levels are cheap; 4 took the N=256 membrane from 30 to 21 iterations)
 NU_COARSE_ADDITIVE = 4
 DEFAULT_ALPHA = 0.85
+# the membrane workloads' coarsest grid: a 32 x 32 level solved directly (its dense inverse
+# applied as one GEMV) took the N=256 headline from 21 to 19 FGMRES iterations and 28.3 to
+# 35.7 solves/s against the 8 x 8 grid of the paper's tests, for about 100 ms more set-up
+DEFAULT_COARSEST = 32
 MAXIT = 150
 
 # DRAM traffic of the roofline's unit from an ncu capture of the same bench command
@@ -107,7 +111,7 @@ def headline_config(args, rec, world: int) -> dict:
     """The workload the headline line measures, the same dict on both arms (this GPU arm and the
     oracle's reference arm): the system, its V-cycle and the solve's stopping rule."""
     return {"workload": workload_desc(rec), "smoother": smoother_desc(args), "nu": args.nu,
-            "alpha": args.alpha, "coarsest_N": 8, "rtol": 1e-10, "maxit": MAXIT,
+            "alpha": args.alpha, "coarsest_N": args.coarsest, "rtol": 1e-10, "maxit": MAXIT,
             "l2": "flushed (256 MB write) before every timed GPU solve",
             "parallelism": f"replicas x{world}"}
 
@@ -170,14 +174,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_cycle(args):
-    """The oracle's V-cycle arguments for the bench's smoother on the N=256 membrane (five
-    smoothing levels): per-level modes and sweeps."""
+def oracle_cycle(args, n_smooth: int):
+    """The oracle's V-cycle arguments for the bench's smoother on a hierarchy with n_smooth
+    smoothing levels: per-level modes and sweeps."""
     if args.smoother == "coloured" and args.coloured_levels == 1:
-        return ["coloured"] + ["additive"] * 4, [1] + [args.nu_additive] * 4
+        return ["coloured"] + ["additive"] * (n_smooth - 1), [1] + [args.nu_additive] * (n_smooth - 1)
     if args.smoother == "coloured":
         return "coloured", args.nu
     return "additive", args.nu
+
+
+def golden_for(args):
+    """The oracle's own iteration count for the bench's V-cycle (tests/golden), or None."""
+    g = golden_iters()
+    if not g:
+        return None
+    if args.coarsest != 8:
+        g = g.get(f"coarsest_{args.coarsest}")
+        if not g:
+            return None
+    gkey = g.get("coloured_finest", {}) if (args.smoother == "coloured" and args.coloured_levels == 1) else g
+    return gkey.get("iters") if gkey else None
 
 
 def cpu_baseline_sample(iters: int, args, timeout_s: int = 900):
@@ -194,7 +211,7 @@ import ib_workloads as W
 from oracle import fgmres as fg, multigrid as mg
 rec = W.config2(256, 1e4)
 t0 = time.perf_counter()
-levels = mg.build_hierarchy(rec, 8, "cav")
+levels = mg.build_hierarchy(rec, %d, "cav")
 modes, nus = %s, %s
 if "coloured" in str(modes):
     mg.level_colours(levels[0])  # the colour classes are set-up, not timed
@@ -208,7 +225,8 @@ t0 = time.perf_counter()
 fg.fgmres(lambda v: K @ v, b, lambda r: r, rtol=0.0, maxit=%d)
 t_rest = time.perf_counter() - t0
 print(json.dumps({"t_setup": t_setup, "t_vcycle": t_vcycle, "t_rest": t_rest}))
-""" % (ROOT, *(repr(v) for v in oracle_cycle(args)), DEFAULT_ALPHA, iters)
+""" % (ROOT, args.coarsest, *(repr(v) for v in oracle_cycle(args, n_smooth_levels(256, args.coarsest))),
+       DEFAULT_ALPHA, iters)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
         out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
@@ -216,6 +234,15 @@ print(json.dumps({"t_setup": t_setup, "t_vcycle": t_vcycle, "t_rest": t_rest}))
         return json.loads(out.stdout.strip().splitlines()[-1])
     except Exception as e:  # pragma: no cover
         return {"error": str(e)}
+
+
+def n_smooth_levels(N: int, coarsest: int) -> int:
+    """Smoothing levels of the hierarchy (halve while N / 2 >= coarsest, as cav_setup does)."""
+    n = 0
+    while N // 2 >= coarsest and N % 2 == 0:
+        N //= 2
+        n += 1
+    return n
 
 
 def golden_iters():
@@ -235,17 +262,15 @@ def run_reference(args, rank, world):
     rec = workload()
     if args.nu is None:
         args.nu = 1 if args.smoother == "coloured" else DEFAULT_NU
-    modes, nus = oracle_cycle(args)
     t0 = time.perf_counter()
-    levels = mg.build_hierarchy(rec, 8, "cav")
+    levels = mg.build_hierarchy(rec, args.coarsest, "cav")
+    modes, nus = oracle_cycle(args, len(levels) - 1)
     if "coloured" in str(modes):
         mg.level_colours(levels[0])
     t_setup = time.perf_counter() - t0
     b = rec.rhs()
     K = levels[0].KE
-    g = golden_iters()
-    gkey = g.get("coloured_finest", {}) if (g and args.smoother == "coloured" and args.coloured_levels == 1) else g
-    iters = gkey["iters"] if gkey and "iters" in gkey else 77
+    iters = golden_for(args) or 77
     # the oracle's FGMRES without its V-cycles (identity preconditioner, all `iters` iterations):
     # Arnoldi, Givens, K_E products and the final update at the solve's Krylov dimensions
     t0 = time.perf_counter()
@@ -350,8 +375,12 @@ def run_batch(args, api, torch, dist, rank, world, local):
         torch.cuda.synchronize()
         ot.append(time.perf_counter() - t)
     its = [i["iters"] for i in last]
-    conv = [i["converged"] for i in last]
-    # only systems that reached 1e-10 count as solved; attempted systems are reported beside
+    flagged = [i["converged"] for i in last]
+    # a system counts as solved only when its true residual (recomputed in FP64 after the solve)
+    # reached 1e-10; FGMRES's own estimate can reach it while the true residual does not (the
+    # stiffest draws, where FP64 evaluation of K_E w loses the last digits); attempted systems
+    # and the estimate's count are reported beside
+    conv = [1 if (i["relres_true"] <= 1e-10) else 0 for i in last]
     value = whole_job_rate(int(sum(conv)) * args.steps, world, total)
     attempted = whole_job_rate(len(recs) * args.steps, world, total)
     kappa = [r.k_bend if r.law == W.LAW_BEAM else (r.k_stretch if r.law == W.LAW_MEMBRANE else r.k_target)
@@ -372,13 +401,14 @@ def run_batch(args, api, torch, dist, rank, world, local):
                                    "beam}, stiffness log-uniform [1e2,1e6], M=4N, seeded RHS; FP32 inverses, "
                                    "autotuned patch-apply variants, fgmres_solve_batched",
                        "nu": args.nu, "alpha": args.alpha, "maxit": MAXIT, "smoother": smoother_desc(args),
-                       "converged": int(sum(conv)), "converged_of_stiffest_half": stiff_conv, "iters_median": int(statistics.median(its)),
+                       "converged": int(sum(conv)), "converged_by_fgmres_estimate": int(sum(flagged)),
+                       "converged_of_stiffest_half": stiff_conv, "iters_median": int(statistics.median(its)),
                        "iters_max": int(max(its)), "autotuned_variant_counts": variants,
                        "l2": "flushed (256 MB write) before every timed batch"},
             "batch_loop": args.batch_loop,
             "other_loop": {"loop": other, "ms_per_step": 1e3 * statistics.mean(ot)},
             "systems": [{"N": r.N, "law": {W.LAW_BEAM: "beam", W.LAW_MEMBRANE: "membrane"}.get(r.law, "target"),
-                         "kappa": kappa[q], "iters": last[q]["iters"], "converged": last[q]["converged"],
+                         "kappa": kappa[q], "iters": last[q]["iters"], "converged": conv[q],
                          "relres_true": last[q]["relres_true"]} for q, r in enumerate(recs)],
             "setup_s_all_64": setup_s, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
@@ -682,6 +712,10 @@ def main():
     ap.add_argument("--nu-additive", type=int, default=NU_COARSE_ADDITIVE,
                     help="coloured smoother: sweeps per side on its additive levels")
     ap.add_argument("--alpha", type=float, default=DEFAULT_ALPHA)
+    ap.add_argument("--coarsest", type=int, default=None,
+                    help="coarsest grid of the membrane workloads' hierarchies, solved directly (default 32: a "
+                         "3073-unknown dense inverse, factorised on every SM at set-up; the paper's own tests "
+                         "use 8)")
     ap.add_argument("--loop", default="device", choices=["device", "host"],
                     help="FGMRES iterations driven on the device (each solve one CUDA graph launch) or by the host")
     ap.add_argument("--connections", type=int, default=32,
@@ -712,6 +746,8 @@ def main():
     ap.add_argument("--dtfactor", type=float, default=0.05, help="dt / h for --workload learned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.coarsest is None:
+        args.coarsest = DEFAULT_COARSEST if args.workload in ("membrane256", "membrane512") else 8
     if args.smoother is None:
         args.smoother = "additive" if args.workload == "batch64" else "coloured"
     if args.nu is None:
@@ -760,7 +796,8 @@ def main():
     e0, e1 = ev(), ev()
     e0.record()
     sysm = api.ib_setup(rec)
-    hier = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision=args.precision,
+    hier = api.cav_setup(sysm, coarsest_N=args.coarsest, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha,
+                         precision=args.precision,
                          autotune=True, **smoother_kw(args))
     e1.record()
     torch.cuda.synchronize()
@@ -840,7 +877,8 @@ def main():
     # plain FP64 inverses on the same system for the mixed-vs-plain comparison
     plain = None
     if args.precision != "fp64" and not args.no_others:
-        hier64 = api.cav_setup(sysm, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha, precision="fp64",
+        hier64 = api.cav_setup(sysm, coarsest_N=args.coarsest, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha,
+                               precision="fp64",
                                autotune=True, **smoother_kw(args))
         for _ in range(2):
             x.zero_()
@@ -869,7 +907,8 @@ def main():
         else:
             variants = [("additive", DEFAULT_NU, 0), ("coloured", 1, 0)]
         for o_sm, o_nu, o_cl in variants:
-            ho = api.cav_setup(sysm, nu_pre=o_nu, nu_post=o_nu, alpha=args.alpha, precision=args.precision,
+            ho = api.cav_setup(sysm, coarsest_N=args.coarsest, nu_pre=o_nu, nu_post=o_nu, alpha=args.alpha,
+                               precision=args.precision,
                                autotune=True, smoother=o_sm, coloured_levels=o_cl, nu_additive=NU_COARSE_ADDITIVE)
             for _ in range(2):
                 x.zero_()
@@ -967,9 +1006,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and rec.N == 256:
-        g = golden_iters()
-        gkey = g.get("coloured_finest", {}) if (g and args.smoother == "coloured" and args.coloured_levels == 1) else g
-        it = gkey["iters"] if gkey and "iters" in gkey else int(statistics.median(iters))
+        it = golden_for(args) or int(statistics.median(iters))
         cb = cpu_baseline_sample(it, args)
         if "t_vcycle" in cb:
             t_solve = it * cb["t_vcycle"] + cb["t_rest"]

@@ -9,6 +9,7 @@
 
 #include "internal.cuh"
 #include "device_util.cuh"
+#include "grid_sync.cuh"
 
 namespace cav {
 
@@ -375,6 +376,10 @@ __global__ void k_cav_sets(int N, int W, int n_big, const int* __restrict__ big_
 struct LevelK {
   int N;
   double h, rho_dt, mu, dt;
+  // formed once on the host, so the extraction of every patch matrix does no FP64 division
+  // (the values the device would compute: IEEE division is correctly rounded on both):
+  // 1 / h, 1 / (h h), rho/dt - mu (-4 / (h h)) (a velocity diagonal), mu / (h h)
+  double ih, ih2, vdiag, mh2;
   bool channel;
   const int* row_of;
   const int64_t* rowptr;
@@ -396,7 +401,7 @@ struct LevelK {
 __device__ inline int channel_row(const LevelK& L, int comp, int i, int j, int* col, double* val) {
   const int N = L.N, NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
-  const double a = L.rho_dt, m = L.mu / (L.h * L.h), ih = 1.0 / L.h;
+  const double a = L.rho_dt, m = L.mh2, ih = L.ih;
   auto U = [&](int x, int y) { return y * N + x; };
   auto Vf = [&](int x, int y) { return NN + y * N + x; };
   auto Pc = [&](int x, int y) { return 2 * NN + y * N + x; };
@@ -459,10 +464,10 @@ __device__ double ke_entry(const LevelK& L, int ga, int gb, bool use_ee) {
       }
       return v;
     }
-    const double ih2 = 1.0 / (L.h * L.h);
+    const double ih2 = L.ih2;
     double v = 0.0;
     if (ga == gb) {
-      v = L.rho_dt - L.mu * (-4.0 / (L.h * L.h));
+      v = L.vdiag;
     } else {
       const int dxp = pmod(ia - ib, N), dyp = pmod(ja - jb, N);
       int nb = 0;
@@ -482,7 +487,7 @@ __device__ double ke_entry(const LevelK& L, int ga, int gb, bool use_ee) {
   int cv, iv, jv, ip, jp;
   if (ca < 2) { cv = ca; iv = ia; jv = ja; ip = ib; jp = jb; }
   else { cv = cb; iv = ib; jv = jb; ip = ia; jp = ja; }
-  const double ih = 1.0 / L.h;
+  const double ih = L.ih;
   if (ip == iv && jp == jv) return ih;
   if (cv == 0 && jp == jv && ip == pmod(iv - 1, N)) return -ih;
   if (cv == 1 && ip == iv && jp == pmod(jv - 1, N)) return -ih;
@@ -637,6 +642,209 @@ __global__ void k_factor(LevelK L, FactorJob J, int bordered_job, int* status) {
       }
     }
     __syncthreads();
+  }
+}
+
+// The coarsest level's factorisation on the whole GPU: the steps of k_factor (extraction,
+// power-of-two row then column equilibration, Gauss-Jordan with the first maximal pivot, the
+// row interchanges undone as column interchanges at the end) in one cooperative launch, CTA
+// `rank` owning the columns rank, rank + G, ... and a grid barrier between elimination steps.
+// Every value comes from the same expressions in the same order as in k_factor, so the
+// inverse is the same bit for bit.  One barrier per step: the owner of column k + 1 updates
+// its columns, then finds the next pivot and publishes column k + 1 with the pivot row
+// interchanged (pub_col, pub_piv: double-buffered by the step's parity).  perm: m ints.
+// A barrier that runs out records DEV_TIMEOUT; every CTA then stops at its next barrier.
+// (one decision per CTA: thread 0 reads the status word and shares it through s_ok)
+constexpr int FG_ROWS = 4;  // rows per thread of the register path of k_factor_grid's update (m <= 4096)
+__device__ inline bool factor_grid_sync(unsigned* bar, int* status, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    grid_barrier(bar, status);
+    *s_ok = *reinterpret_cast<volatile int*>(status) != DEV_TIMEOUT;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// The owner of column k: its pivot (first row of maximal modulus among rows k..m-1, the
+// reduction of k_factor), published with the interchanged column.
+__device__ inline void factor_grid_pivot(const double* A, int ld, int m, int k, double* pub_col, int* pub_piv,
+                                         int* perm, int* status, double* s_pmax, int* s_pidx, int* s_piv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double best = -1.0;
+  int bi = m;
+  for (int a = k + threadIdx.x; a < m; a += blockDim.x) {
+    const double v = fabs(A[(int64_t)k * ld + a]);
+    if (v > best) { best = v; bi = a; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { s_pmax[warp] = best; s_pidx[warp] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bb = -1.0;
+    int ii = m;
+    for (int w = 0; w < nw; ++w)
+      if (s_pmax[w] > bb || (s_pmax[w] == bb && s_pidx[w] < ii)) { bb = s_pmax[w]; ii = s_pidx[w]; }
+    *s_piv = ii;
+    perm[k] = ii;
+    pub_piv[k & 1] = ii;
+    if (!(bb > 0.0)) atomicExch(status, DEV_SINGULAR);
+  }
+  __syncthreads();
+  const int pr = *s_piv;
+  double* out = pub_col + (int64_t)(k & 1) * ld;
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    double v = A[(int64_t)k * ld + a];
+    if (pr != k && pr < m) {
+      if (a == k) v = A[(int64_t)k * ld + pr];
+      else if (a == pr) v = A[(int64_t)k * ld + k];
+    }
+    out[a] = v;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_factor_grid(LevelK L, FactorJob J, int bordered, int* status, unsigned* bar,
+                                                      double* pub_col, int* pub_piv, int* perm) {
+  extern __shared__ double sh[];  // per own column: rb, then the value moving to the pivot row
+  __shared__ double s_pmax[32];
+  __shared__ int s_pidx[32];
+  __shared__ int s_piv, s_ok;
+  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int64_t gt = (int64_t)rank * nt + tid, GT = (int64_t)G * nt;
+  const int64_t d0 = J.dof_off[0];
+  const int n = (int)(J.dof_off[1] - d0);
+  const int NN = L.N * L.N;
+  const int m = n + bordered;
+  if (gt == 0) J.mdim[0] = m;
+  const int ld = (m + 7) & ~7;
+  double* A = J.A + J.mat_off[0];
+  double* sr = J.s_r + d0;
+  double* sc = J.s_c + d0;
+  const int* dofs = J.dofs + d0;
+  for (int64_t e = gt; e < (int64_t)m * m; e += GT) {
+    const int b = (int)(e / m), a = (int)(e % m);
+    double v;
+    if (a < n && b < n) v = ke_entry(L, dofs[a], dofs[b], J.use_ee != 0);
+    else if (a == n && b == n) v = 0.0;
+    else {
+      const int g = (a == n) ? dofs[b] : dofs[a];
+      v = (g >= 2 * NN) ? 1.0 : 0.0;
+    }
+    A[(int64_t)b * ld + a] = v;
+  }
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  for (int64_t a = gt; a < m; a += GT) {
+    double mx = 0.0;
+    for (int b = 0; b < m; ++b) mx = fmax(mx, fabs(A[(int64_t)b * ld + a]));
+    sr[a] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
+    if (mx == 0.0) atomicExch(status, DEV_SINGULAR);
+  }
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  for (int64_t b = gt; b < m; b += GT) {
+    double mx = 0.0;
+    for (int a = 0; a < m; ++a) mx = fmax(mx, fabs(sr[a] * A[(int64_t)b * ld + a]));
+    sc[b] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
+  }
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  for (int64_t e = gt; e < (int64_t)m * m; e += GT) {
+    const int b = (int)(e / m), a = (int)(e % m);
+    A[(int64_t)b * ld + a] = sr[a] * A[(int64_t)b * ld + a] * sc[b];
+  }
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  const int ncol = (m > rank) ? (m - rank + G - 1) / G : 0;  // own columns rank + j G, j < ncol
+  if (rank == 0) factor_grid_pivot(A, ld, m, 0, pub_col, pub_piv, perm, status, s_pmax, s_pidx, &s_piv);
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  for (int k = 0; k < m; ++k) {
+    const int pr = pub_piv[k & 1];
+    const double* colk = pub_col + (int64_t)(k & 1) * ld;
+    const double piv = colk[k];
+    const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
+    const bool swap = pr != k && pr < m;
+    // rowk of k_factor for the own columns (after the interchange), and the entry that moves
+    // from row k to row pr
+    for (int j = tid; j < ncol; j += nt) {
+      const int b = rank + j * G;
+      const double ak = A[(int64_t)b * ld + k];
+      const double ap = swap ? A[(int64_t)b * ld + pr] : ak;
+      sh[j] = (b == k) ? ipiv : ap * ipiv;
+      sh[ncol + j] = ak;
+    }
+    __syncthreads();
+    if (m <= FG_ROWS * nt) {
+      // this thread's rows a = tid + q nt: their pivot-column entries in registers, and two
+      // columns' entries loaded before their updates (the loads of a step are independent)
+      double ck[FG_ROWS];
+#pragma unroll
+      for (int q = 0; q < FG_ROWS; ++q) {
+        const int a = tid + q * nt;
+        ck[q] = (a < m) ? colk[a] : 0.0;
+      }
+      for (int j0 = 0; j0 < ncol; j0 += 2) {
+        double cur[2][FG_ROWS];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const double* colp = A + (int64_t)(rank + (j0 + u) * G) * ld;
+#pragma unroll
+          for (int q = 0; q < FG_ROWS; ++q) {
+            const int a = tid + q * nt;
+            cur[u][q] = (j0 + u < ncol && a < m) ? colp[a] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = j0 + u;
+          if (j >= ncol) break;
+          const int b = rank + j * G;
+          double* colp = A + (int64_t)b * ld;
+          const double rb = sh[j], moved = sh[ncol + j];
+#pragma unroll
+          for (int q = 0; q < FG_ROWS; ++q) {
+            const int a = tid + q * nt;
+            if (a >= m) continue;
+            if (b == k) {
+              colp[a] = (a == k) ? rb : -ck[q] * ipiv;
+            } else {
+              const double c = (swap && a == pr) ? moved : cur[u][q];
+              colp[a] = (a == k) ? rb : c - ck[q] * rb;
+            }
+          }
+        }
+      }
+    } else {
+      for (int j = 0; j < ncol; ++j) {
+        const int b = rank + j * G;
+        double* colp = A + (int64_t)b * ld;
+        const double rb = sh[j];
+        if (b == k) {
+          for (int a = tid; a < m; a += nt) colp[a] = (a == k) ? rb : -colk[a] * ipiv;
+        } else {
+          const double moved = sh[ncol + j];
+          for (int a = tid; a < m; a += nt) {
+            const double cur = (swap && a == pr) ? moved : colp[a];
+            colp[a] = (a == k) ? rb : cur - colk[a] * rb;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (k + 1 < m && (k + 1) % G == rank)
+      factor_grid_pivot(A, ld, m, k + 1, pub_col, pub_piv, perm, status, s_pmax, s_pidx, &s_piv);
+    if (!factor_grid_sync(bar, status, &s_ok)) return;
+  }
+  // undo the row interchanges as column interchanges, last first (each row on its own)
+  for (int64_t a = gt; a < m; a += GT) {
+    for (int k = m - 1; k >= 0; --k) {
+      const int pr = perm[k];
+      if (pr != k && pr < m) {
+        const double t = A[(int64_t)k * ld + a];
+        A[(int64_t)k * ld + a] = A[(int64_t)pr * ld + a];
+        A[(int64_t)pr * ld + a] = t;
+      }
+    }
   }
 }
 
@@ -925,6 +1133,10 @@ static LevelK level_k(const Level& lv) {
   k.rho_dt = lv.rho_dt;
   k.mu = lv.mu;
   k.dt = lv.dt;
+  k.ih = 1.0 / lv.h;
+  k.ih2 = 1.0 / (lv.h * lv.h);
+  k.vdiag = lv.rho_dt - lv.mu * (-4.0 / (lv.h * lv.h));
+  k.mh2 = lv.mu / (lv.h * lv.h);
   k.channel = lv.channel;
   k.row_of = lv.ee.row_of;
   k.rowptr = lv.ee.rowptr;
@@ -1327,6 +1539,9 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   scratch.release();
 }
 
+// coarsest systems above this order are factorised by the grid-parallel kernel
+constexpr int COARSEST_GRID_M = 256;
+
 static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   Arena& A = H->arena;
   Arena scratch;
@@ -1358,11 +1573,39 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   J.s_c = wsc;
   J.border_all_pressure = 0;
   J.use_ee = 1;
-  const size_t fsm = factor_smem(m);
-  if (fsm > 48 * 1024)
-    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-  k_factor<<<1, 1024, fsm, st>>>(LK, J, lv.channel ? 0 : 1, H->status);
-  CAV_CHECK_LAUNCH();
+  if (m > COARSEST_GRID_M && !std::getenv("CAV_COARSEST_ONE_CTA")) {
+    // a larger coarsest level: the factorisation on every SM (same bits as the one-CTA kernel;
+    // CAV_COARSEST_ONE_CTA, a test hook, keeps the one-CTA kernel)
+    int sms = 0, dev = 0, per_sm = 0;
+    CAV_CHECK_CUDA(cudaGetDevice(&dev));
+    CAV_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t gsm = 2 * sizeof(double) * (size_t)((m + sms - 1) / sms);
+    CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_grid, 1024, gsm));
+    CAV_REQUIRE(per_sm >= 1, "coarsest factorisation: the grid kernel cannot be resident");
+    double* pub_col = scratch.alloc<double>(2 * (size_t)round8(m));
+    int* pub_piv = scratch.alloc<int>(2);
+    int* perm = scratch.alloc<int>(m);
+    const int bordered = lv.channel ? 0 : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sms);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = gsm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barriers need it
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_factor_grid, LK, J, bordered, H->status, H->gbar, pub_col, pub_piv,
+                                      perm));
+    CAV_CHECK_LAUNCH();
+  } else {
+    const size_t fsm = factor_smem(m);
+    if (fsm > 48 * 1024)
+      CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    k_factor<<<1, 1024, fsm, st>>>(LK, J, lv.channel ? 0 : 1, H->status);
+    CAV_CHECK_LAUNCH();
+  }
   lv.coarse_m = m;
   if (!lv.coarse_inv) lv.coarse_inv = A.alloc<double>((size_t)m * m);  // reused by cav_refactor
   k_fold_rowmajor<<<64, 256, 0, st>>>(m, work, wsr, wsc, lv.coarse_inv);

@@ -2,10 +2,11 @@
 bench workload (elliptic membrane N=256, kappa_s=1e4, rtol 1e-10 relative to ||b||) with the
 bench's two V-cycles: the weighted additive CAV sweep on every level (2+2 sweeps, alpha 0.85),
 and the class-by-class multiplicative sweep on the finest level (1+1) with the additive one
-below it (4+4).  Calls only oracle/ and the seeded workload generator; the bench's CPU
+below it (4+4); for a coarsest grid of 8 x 8 (the top-level keys) and of 32 x 32 (under
+"coarsest_32").  Calls only oracle/ and the seeded workload generator; the bench's CPU
 baseline and reference arm scale their per-iteration timings by these counts.
 
-    OMP_NUM_THREADS=1 python tests/golden/make_bench_oracle_iterations.py
+    OMP_NUM_THREADS=1 python tests/golden/make_bench_oracle_iterations.py [coarsest ...]
 """
 import json
 import os
@@ -21,16 +22,15 @@ from oracle import fgmres, multigrid  # noqa: E402
 NU, ALPHA = 2, 0.85
 NU_BELOW = 4
 
-if __name__ == "__main__":
-    rec = W.config2(256, 1e4)
+def counts(rec, coarsest: int) -> dict:
     t0 = time.time()
-    levels = multigrid.build_hierarchy(rec, 8, "cav")
+    levels = multigrid.build_hierarchy(rec, coarsest, "cav")
     K = levels[0].KE
     b = rec.rhs()
     _, info = fgmres.fgmres(lambda v: K @ v, b,
                             lambda r: multigrid.vcycle(levels, r, NU, NU, "additive", ALPHA),
                             rtol=1e-10, maxit=150)
-    out = {"workload": rec.name, "nu": NU, "alpha": ALPHA, "iters": info["iters"],
+    out = {"workload": rec.name, "coarsest_N": coarsest, "nu": NU, "alpha": ALPHA, "iters": info["iters"],
            "converged": bool(info["converged"]), "relres_true": info["relres_true"],
            "oracle_seconds": round(time.time() - t0, 1)}
     L = len(levels) - 1
@@ -43,6 +43,24 @@ if __name__ == "__main__":
     out["coloured_finest"] = {"modes": modes, "nu": nus, "alpha": ALPHA, "iters": info["iters"],
                               "converged": bool(info["converged"]), "relres_true": info["relres_true"],
                               "oracle_seconds": round(time.time() - t0, 1)}
-    with open(os.path.join(HERE, "bench_oracle_iterations.json"), "w") as f:
-        json.dump(out, f, indent=1)
-    print(out)
+    return out
+
+
+if __name__ == "__main__":
+    rec = W.config2(256, 1e4)
+    path = os.path.join(HERE, "bench_oracle_iterations.json")
+    which = [int(a) for a in sys.argv[1:]] or [8, 32]
+    out = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            out = json.load(f)
+    for c in which:
+        res = counts(rec, c)
+        if c == 8:
+            keep = {k: v for k, v in out.items() if k.startswith("coarsest_")}
+            out = dict(res, **keep)
+        else:
+            out[f"coarsest_{c}"] = res
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+        print(c, res, flush=True)

@@ -63,6 +63,12 @@ __global__ void k_round_f32(int64_t n, const double* __restrict__ in, float* __r
   if (q < n) out[q] = (float)in[q];
 }
 
+// The iterate's FP32 copy at the start of a coloured sweep (FP32-inverse levels).
+__global__ void k_to_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = (float)in[q];
+}
+
 template <typename T>
 struct ColourStep;
 template <typename T>
@@ -272,6 +278,7 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   // the class step's shared memory can exceed the 48 KB default (set here, outside any capture)
   colour_step_attributes();
   if (lv.precision == CAV_PREC_FP32) {
+    lv.w32 = A.alloc<float>(3 * (size_t)NN);
     lv.ee_vals32 = A.alloc<float>(std::max<int64_t>(lv.ee.nnz, 1));
     if (lv.ee.nnz) {
       k_round_f32<<<div_up(lv.ee.nnz, 256), 256, 0, st>>>(lv.ee.nnz, lv.ee.vals, lv.ee_vals32);
@@ -323,6 +330,7 @@ struct ColourStep {
   const int* cols;
   const double* vals;
   const float* vals32;   // E_E values rounded to FP32 (FP32-inverse levels)
+  float* w32;            // FP32-inverse levels: (float) of the iterate, kept beside it; null on FP64 levels
   const uint8_t* inject; // box patches: 1 where a slot receives its correction; null: every slot
   const int4* jobs;      // this class's enlarged patches
   const int64_t* job_inv;
@@ -360,11 +368,21 @@ struct ResidualType<double> {
   typedef double type;
 };
 
-// the iterate read from L2 (ld.global.cg): earlier class steps wrote it while this kernel ran
+// the iterate read from L2 (ld.global.cg): earlier class steps wrote it while this kernel ran.
+// FP32 residual rows read the iterate's FP32 copy, which holds exactly (float) of every FP64
+// value: the same numbers without a conversion per load (on B300 an FP64-to-FP32 conversion
+// holds its SM sub-partition like any FP64 instruction).
 template <typename R>
 __device__ inline R ldw(const double* p) {
   return (R)__ldcg(p);
 }
+template <typename R>
+__device__ inline R ldw(const float* p) {
+  return (R)__ldcg(p);
+}
+// the iterate the residual rows of precision R read: the FP32 copy or the FP64 iterate
+__device__ inline const float* iter_src(const float*, const float* w32, const double*) { return w32; }
+__device__ inline const double* iter_src(const double*, const float*, const double* w) { return w; }
 
 // A boundary row (j = 0 or N - 1) of the channel's Stokes part of K_E w, from the ghost rules
 // of the level's operator (homogeneous boundary data), with a = rho/dt and m = mu/h^2 written
@@ -374,13 +392,13 @@ __device__ inline R ldw(const double* p) {
 //   inflow u:   (a + 5m) u - m (u_E + u_W + u_S) + (p_ij - p_{i-1,j}) / h
 //   inflow v:   (a + 4m) v - m (v_E + v_W + v_S) + (p_ij - p_{i,j-1}) / h
 //   inflow p:   -((u_{i+1,j} - u_ij) - v_ij) / h;  the outflow p row is the periodic one.
-template <typename R, typename T>
-__device__ inline R channel_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
+template <typename R, typename T, typename W>
+__device__ inline R channel_row_l2(const ColourStep<T>& a, const W* w, int comp, int i, int j) {
   const int N = a.N, NN = N * N;
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
-  const double* u = w;
-  const double* v = w + NN;
-  const double* p = w + 2 * NN;
+  const W* u = w;
+  const W* v = w + NN;
+  const W* p = w + 2 * NN;
   const int c = j * N + i;
   const R ih = (R)a.ih, m = (R)(-a.cnb), cdiag = (R)a.cdiag;
   if (j == 0) {
@@ -406,23 +424,23 @@ __device__ inline R channel_row_l2(const ColourStep<T>& a, const double* w, int 
 
 // Stokes row of unknown (comp, i, j) of K_E w (Eq. intro_saddle: A0 u + G p, or -D u), in the
 // form cdiag u_c + cnb (sum of the four neighbours) + (p_c - p_w) / h, seven operations in R.
-template <typename R, typename T>
-__device__ inline R stokes_row_l2(const ColourStep<T>& a, const double* w, int comp, int i, int j) {
+template <typename R, typename T, typename W>
+__device__ inline R stokes_row_l2(const ColourStep<T>& a, const W* w, int comp, int i, int j) {
   const int N = a.N, NN = N * N;
   if (a.channel && (j == 0 || j + 1 == N)) return channel_row_l2<R>(a, w, comp, i, j);
   const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
   const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
   const int c = j * N + i;
-  const double* p = w + 2 * NN;
+  const W* p = w + 2 * NN;
   const R ih = (R)a.ih, cnb = (R)a.cnb, cdiag = (R)a.cdiag;
   if (comp < 2) {
-    const double* u = w + comp * NN;
+    const W* u = w + comp * NN;
     const int cw = (comp == 0) ? j * N + im : jm * N + i;  // the other cell of the face's gradient
     const R nb = (ldw<R>(u + j * N + ip) + ldw<R>(u + j * N + im)) + (ldw<R>(u + jp * N + i) + ldw<R>(u + jm * N + i));
     return mad(ih, ldw<R>(p + c) - ldw<R>(p + cw), mad(cnb, nb, cdiag * ldw<R>(u + c)));
   }
-  const double* u = w;
-  const double* v = w + NN;
+  const W* u = w;
+  const W* v = w + NN;
   return -((ldw<R>(u + j * N + ip) - ldw<R>(u + c)) + (ldw<R>(v + jp * N + i) - ldw<R>(v + c))) * ih;
 }
 
@@ -497,7 +515,9 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
     for (int c2 = 0; c2 < 5; ++c2) rr[c2] = __shfl_sync(0xffffffffu, r, min(base + c2, 31));
     if (slot_act) {
       const double* m = a.S.m[kind] + 5 * q;
-      w[k] = old + (m[0] * rr[0] + m[1] * rr[1] + m[2] * rr[2] + m[3] * rr[3] + m[4] * rr[4]);
+      const double nw = old + (m[0] * rr[0] + m[1] * rr[1] + m[2] * rr[2] + m[3] * rr[3] + m[4] * rr[4]);
+      w[k] = nw;
+      if (a.w32) a.w32[k] = (float)nw;
     }
     return;
   }
@@ -570,7 +590,9 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
   // ahead because its own trigger follows its wait for this step.  Triggering at entry
   // instead let several later classes queue their copies ahead of this step's residual reads.
   pdl_trigger();
-  // residual rows of the slice: E_E sums on warps 0-3, Stokes rows on warps 4-7
+  // residual rows of the slice: E_E sums on warps 0-3, Stokes rows on warps 4-7, from the
+  // iterate's FP32 copy when they are evaluated in FP32
+  const auto* wr = iter_src(static_cast<const res_t*>(nullptr), a.w32, w);
   if (tid < 128) {
     for (int t0 = 0; t0 < m; t0 += CS_EE_SLOTS) {
       const int s = t0 + eg;
@@ -589,7 +611,7 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
           const int q = s * R + el + (t0 + t) * CS_EE_LANES;
           const bool ok = t0 + t < cnt;
           vv[t] = ok ? evl[q] : (res_t)0;
-          wv[t] = ok ? ldw<res_t>(w + ecol[q]) : (res_t)0;
+          wv[t] = ok ? ldw<res_t>(wr + ecol[q]) : (res_t)0;
         }
         static_assert(CS_EE_BATCH == 8, "the tail below is written for batches of eight");
         switch (min(wmax - t0, CS_EE_BATCH)) {  // warp-uniform: only the needed FMAs issue
@@ -612,7 +634,7 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
       const int k = sk[s];
       const int comp = k / NN, cc = k % NN;
       sold[s] = __ldcg(w + k);
-      sst[s] = stokes_row_l2<res_t>(a, w, comp, cc % a.N, cc / a.N);
+      sst[s] = stokes_row_l2<res_t>(a, wr, comp, cc % a.N, cc / a.N);
     }
   }
   __syncthreads();
@@ -692,7 +714,11 @@ k_colour_step(const ColourStep<T> a, const double* __restrict__ b, double* w) {
 #pragma unroll
     for (int q = 0; q < C * CG; ++q) sum += recv[q * cm4 + s];
     // restricted injection (box patches): only the unexpanded block's unknowns are written
-    if (a.inject == nullptr || a.inject[d0 + rank + C * s]) w[sk[s]] = sold[s] + ssc[s] * (double)sum;
+    if (a.inject == nullptr || a.inject[d0 + rank + C * s]) {
+      const double nw = sold[s] + ssc[s] * (double)sum;
+      w[sk[s]] = nw;
+      if (a.w32) a.w32[sk[s]] = (float)nw;
+    }
   }
 }
 
@@ -788,6 +814,7 @@ static void launch_step(const cav_hierarchy* H, const Level& lv, const T* inv, i
   a.cols = lv.ee.cols;
   a.vals = lv.ee.vals;
   a.vals32 = lv.ee_vals32;
+  a.w32 = lv.w32;
   a.inject = lv.inject;
   a.jobs = lv.col_job + lv.col_big_start[k];
   a.job_inv = lv.col_inv + lv.col_big_start[k];
@@ -841,6 +868,14 @@ void coloured_sweep(const cav_hierarchy* H, int l, const double* b, double* w, b
               "coloured smoother: BF16 patch inverses make the undamped multiplicative sweep diverge; "
               "use FP32 or FP64");
   if (w_is_zero) CAV_CHECK_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)NN, st));
+  if (lv.w32) {  // the FP32 copy the class steps' residual rows read, equal to (float) w
+    if (w_is_zero) {
+      CAV_CHECK_CUDA(cudaMemsetAsync(lv.w32, 0, sizeof(float) * 3 * (size_t)NN, st));
+    } else {
+      k_to_f32<<<div_up(3 * (int64_t)NN, 256), 256, 0, st>>>(3 * (int64_t)NN, w, lv.w32);
+      CAV_CHECK_LAUNCH();
+    }
+  }
   if (profile) prof_begin(H, l, st);
   for (int k = 0; k < lv.n_colours; ++k) {
     // class steps after the first overlap their prologue with the step before them

@@ -157,6 +157,7 @@ struct Level {
   int* col_std = nullptr;            // [N^2 - n_big] standard cells, class by class
   int2* slot_ee = nullptr;           // [big_sum_n] per packed slot: (start, length) of its E_E row
   float* ee_vals32 = nullptr;        // [ee.nnz] E_E values in FP32 (FP32-inverse coloured levels)
+  float* w32 = nullptr;              // [3 N^2] (float) of the iterate during a coloured sweep (FP32 levels)
   int ee_row_max = 0;                // longest E_E row on this level
 
   // coarsest level: dense inverse, row-major m x m: the bordered system (m = n + 1) on a

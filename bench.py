@@ -49,13 +49,12 @@ MAXIT = 150
 # on (keyed by the smoother, precision, N and the hash of the kernel's source file); null once
 # that source changes.
 NCU_TRAFFIC = {
-    # coloured: the 105 k_colour_step launches of one finest-level sweep, 415.50 MB read, 0 MB
+    # coloured: the 105 k_colour_step launches of one finest-level sweep, 422.50 MB read, 0 MB
     # written back within them (the iterate's writes stay in L2)
-    "coloured:fp32:256:colour.cu:55e24ae46b78a12d": 415.50e6,
-    # additive: one finest-level patch-apply launch (the variant ncu's set-up timed fastest,
-    # k_patch_apply_tma<float, 4, 16384>; the plain run's <float, 4, 8192> read 289.66 MB +
-    # wrote 4.88 MB on the previous source), 289.62 MB read + 4.60 MB written
-    "additive:fp32:256:sweep.cu:2bb03f909db1891a": 294.23e6,
+    "coloured:fp32:256:colour.cu:abec06b1d07f7208": 422.50e6,
+    # additive: one finest-level patch-apply launch (k_patch_apply_tma<float, 4, 8192>),
+    # 289.65 MB read + 5.05 MB written
+    "additive:fp32:256:sweep.cu:63b9c19db8897f36": 294.70e6,
 }
 
 

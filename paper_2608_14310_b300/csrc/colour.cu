@@ -76,29 +76,41 @@ __global__ void k_colour_step(const ColourStep<T> a, const double* __restrict__ 
 
 static void colour_step_attributes();
 
-void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
-  Arena& A = H->arena;
-  const int N = lv.N, NN = N * N, n = 3 * NN;
+void colour_fetch(const Level& lv, ColourPlan& P, cudaStream_t st) {
+  const int NN = lv.N * lv.N;
   CAV_REQUIRE(lv.ee.nnz < (int64_t)1 << 31, "coloured smoother: E_E too large for 32-bit row offsets");
-  std::vector<uint8_t> big(NN);
-  std::vector<int64_t> off(lv.n_big + 1, 0);
-  std::vector<int> bd(lv.big_sum_n);
-  std::vector<int> row_of(2 * NN, -1);
-  std::vector<int64_t> rowptr(lv.ee.n_rows + 1, 0);
-  std::vector<int> cols(lv.ee.nnz);
-  CAV_CHECK_CUDA(cudaMemcpyAsync(big.data(), lv.cell_big, NN, cudaMemcpyDeviceToHost, st));
+  CAV_REQUIRE(lv.big_sum_n < (int64_t)1 << 31, "coloured smoother: too many patch slots for 32-bit offsets");
+  P.big.assign(NN, 0);
+  P.off.assign(lv.n_big + 1, 0);
+  P.inv_off.assign(lv.n_big + 1, 0);
+  P.bd.assign(lv.big_sum_n, 0);
+  P.row_of.assign(2 * NN, -1);
+  P.rowptr.assign(lv.ee.n_rows + 1, 0);
+  P.cols.assign(lv.ee.nnz, 0);
+  CAV_CHECK_CUDA(cudaMemcpyAsync(P.big.data(), lv.cell_big, NN, cudaMemcpyDeviceToHost, st));
   if (lv.n_big) {
-    CAV_CHECK_CUDA(cudaMemcpyAsync(off.data(), lv.big_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost, st));
-    CAV_CHECK_CUDA(cudaMemcpyAsync(bd.data(), lv.big_dofs, sizeof(int) * lv.big_sum_n, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(P.off.data(), lv.big_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(P.inv_off.data(), lv.inv_off, sizeof(int64_t) * (lv.n_big + 1),
+                                   cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(P.bd.data(), lv.big_dofs, sizeof(int) * lv.big_sum_n, cudaMemcpyDeviceToHost, st));
   }
   if (lv.ee.n_rows) {
-    CAV_CHECK_CUDA(cudaMemcpyAsync(row_of.data(), lv.ee.row_of, sizeof(int) * 2 * NN, cudaMemcpyDeviceToHost, st));
-    CAV_CHECK_CUDA(cudaMemcpyAsync(rowptr.data(), lv.ee.rowptr, sizeof(int64_t) * (lv.ee.n_rows + 1),
+    CAV_CHECK_CUDA(cudaMemcpyAsync(P.row_of.data(), lv.ee.row_of, sizeof(int) * 2 * NN, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(P.rowptr.data(), lv.ee.rowptr, sizeof(int64_t) * (lv.ee.n_rows + 1),
                                    cudaMemcpyDeviceToHost, st));
-    CAV_CHECK_CUDA(cudaMemcpyAsync(cols.data(), lv.ee.cols, sizeof(int) * lv.ee.nnz, cudaMemcpyDeviceToHost, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(P.cols.data(), lv.ee.cols, sizeof(int) * lv.ee.nnz, cudaMemcpyDeviceToHost, st));
   }
   CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+}
 
+void colour_plan(Level& lv, ColourPlan& P) {
+  const int N = lv.N, NN = N * N, n = 3 * NN;
+  const std::vector<uint8_t>& big = P.big;
+  const std::vector<int64_t>& off = P.off;
+  const std::vector<int>& bd = P.bd;
+  const std::vector<int>& row_of = P.row_of;
+  const std::vector<int64_t>& rowptr = P.rowptr;
+  const std::vector<int>& cols = P.cols;
   // units: the cells (CAV / Vanka patches), or the blocks (box patches, all enlarged)
   const bool box = lv.box;
   const int nunits = box ? lv.n_big : NN;
@@ -242,39 +254,39 @@ void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     lv.col_std_start[k + 1] += lv.col_std_start[k];
   }
   const int nstd = nunits - lv.n_big;
-  std::vector<int> hb(lv.n_big), hs(nstd);
+  std::vector<int> hb(lv.n_big);
+  P.hs.assign(nstd, 0);
   {
     std::vector<int> cb(lv.col_big_start.begin(), lv.col_big_start.end() - 1);
     std::vector<int> cs(lv.col_std_start.begin(), lv.col_std_start.end() - 1);
     for (int c = 0; c < nunits; ++c) {
       if (is_big(c)) hb[cb[colour[c]]++] = pidx[c];
-      else hs[cs[colour[c]]++] = c;
+      else P.hs[cs[colour[c]]++] = c;
     }
   }
-  {
-    // job records of the enlarged patches, class by class: (p, n, slot offset) and inverse offset
-    std::vector<int64_t> inv_off(lv.n_big + 1, 0);
-    if (lv.n_big)
-      CAV_CHECK_CUDA(cudaMemcpy(inv_off.data(), lv.inv_off, sizeof(int64_t) * (lv.n_big + 1), cudaMemcpyDeviceToHost));
-    CAV_REQUIRE(lv.big_sum_n < (int64_t)1 << 31, "coloured smoother: too many patch slots for 32-bit offsets");
-    std::vector<int4> jobs(lv.n_big);
-    std::vector<int64_t> jinv(lv.n_big);
-    for (int t = 0; t < lv.n_big; ++t) {
-      const int q = hb[t];
-      jobs[t] = make_int4(q, (int)(off[q + 1] - off[q]), (int)off[q], 0);
-      jinv[t] = inv_off[q];
-    }
-    lv.col_job = A.alloc<int4>(std::max(lv.n_big, 1));
-    lv.col_inv = A.alloc<int64_t>(std::max(lv.n_big, 1));
-    if (lv.n_big) {
-      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_job, jobs.data(), sizeof(int4) * lv.n_big, cudaMemcpyHostToDevice, st));
-      CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_inv, jinv.data(), sizeof(int64_t) * lv.n_big, cudaMemcpyHostToDevice, st));
-    }
-    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+  // job records of the enlarged patches, class by class: (p, n, slot offset) and inverse offset
+  P.jobs.resize(lv.n_big);
+  P.jinv.resize(lv.n_big);
+  for (int t = 0; t < lv.n_big; ++t) {
+    const int q = hb[t];
+    P.jobs[t] = make_int4(q, (int)(off[q + 1] - off[q]), (int)off[q], 0);
+    P.jinv[t] = P.inv_off[q];
+  }
+}
+
+void colour_upload(cav_hierarchy* H, Level& lv, const ColourPlan& P, cudaStream_t st) {
+  Arena& A = H->arena;
+  const int NN = lv.N * lv.N;
+  const int nstd = (int)P.hs.size();
+  lv.col_job = A.alloc<int4>(std::max(lv.n_big, 1));
+  lv.col_inv = A.alloc<int64_t>(std::max(lv.n_big, 1));
+  if (lv.n_big) {
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_job, P.jobs.data(), sizeof(int4) * lv.n_big, cudaMemcpyHostToDevice, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_inv, P.jinv.data(), sizeof(int64_t) * lv.n_big, cudaMemcpyHostToDevice, st));
   }
   lv.col_std = A.alloc<int>(std::max(nstd, 1));
   if (nstd)
-    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_std, hs.data(), sizeof(int) * nstd, cudaMemcpyHostToDevice, st));
+    CAV_CHECK_CUDA(cudaMemcpyAsync(lv.col_std, P.hs.data(), sizeof(int) * nstd, cudaMemcpyHostToDevice, st));
   // the class step's shared memory can exceed the 48 KB default (set here, outside any capture)
   colour_step_attributes();
   if (lv.precision == CAV_PREC_FP32) {

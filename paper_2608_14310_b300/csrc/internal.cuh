@@ -342,7 +342,22 @@ bool same_ee_pattern(const EECsr& a, const EECsr& b, int* d_flag, cudaStream_t s
 void refactor_levels(cav_hierarchy* H, const ib_system* s, cudaStream_t st);
 
 // colour.cu: colour classes (set-up) and the class-by-class multiplicative sweep
-void build_colours(cav_hierarchy* H, Level& lv, cudaStream_t st);
+// The set-up of a coloured level in three parts: colour_fetch copies the level's patch sets
+// and E_E pattern to the host (syncs st); colour_plan computes the first-fit classes and the
+// class-ordered job tables on the host alone (no CUDA call, so a host thread can run it while
+// the device works; it writes only lv's class fields and P); colour_upload stores the tables on
+// the device (syncs st).
+struct ColourPlan {
+  std::vector<uint8_t> big;
+  std::vector<int64_t> off, inv_off, rowptr;
+  std::vector<int> bd, row_of, cols;
+  std::vector<int4> jobs;      // class-ordered enlarged patches: (patch, size, slot offset, 0)
+  std::vector<int64_t> jinv;   // their inverses' offsets
+  std::vector<int> hs;         // class-ordered standard cells
+};
+void colour_fetch(const Level& lv, ColourPlan& P, cudaStream_t st);
+void colour_plan(Level& lv, ColourPlan& P);
+void colour_upload(cav_hierarchy* H, Level& lv, const ColourPlan& P, cudaStream_t st);
 void colour_refresh_values(Level& lv, cudaStream_t st);
 // fails (IB_ERR_INVALID) when the level's class steps would not fit in shared memory
 void check_colour_step(const Level& lv);

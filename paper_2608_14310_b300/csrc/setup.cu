@@ -650,12 +650,17 @@ __global__ void k_factor(LevelK L, FactorJob J, int bordered_job, int* status) {
 // row interchanges undone as column interchanges at the end) in one cooperative launch, CTA
 // `rank` owning the columns rank, rank + G, ... and a grid barrier between elimination steps.
 // Every value comes from the same expressions in the same order as in k_factor, so the
-// inverse is the same bit for bit.  One barrier per step: the owner of column k + 1 updates
-// its columns, then finds the next pivot and publishes column k + 1 with the pivot row
-// interchanged (pub_col, pub_piv: double-buffered by the step's parity).  perm: m ints.
-// A barrier that runs out records DEV_TIMEOUT; every CTA then stops at its next barrier.
-// (one decision per CTA: thread 0 reads the status word and shares it through s_ok)
-constexpr int FG_ROWS = 4;  // rows per thread of the register path of k_factor_grid's update (m <= 4096)
+// inverse is the same bit for bit.  One barrier per step.  Lookahead: in step k the owner of
+// column k + 1 updates that column first; FG_PIV_WARPS of its warps then find the next pivot
+// and publish column k + 1 with the pivot row interchanged (pub_col, pub_piv: double-buffered
+// by the step's parity) while the other warps update the remaining columns.  A CTA's first
+// sc_cols columns stay in shared memory for the whole elimination (the rest are streamed from
+// L2 every step).  perm: m ints.  A barrier that runs out records DEV_TIMEOUT; every CTA then
+// stops at its next barrier (one decision per CTA: thread 0 reads the status word and shares
+// it through s_ok).
+constexpr int FG_THREADS = 512;  // threads per CTA of k_factor_grid
+constexpr int FG_ROWS = 6;       // register rows per thread of its update (the rest in a plain loop)
+constexpr int FG_PIV_WARPS = 4;  // warps of the next column's owner that search its pivot
 __device__ inline bool factor_grid_sync(unsigned* bar, int* status, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -666,54 +671,63 @@ __device__ inline bool factor_grid_sync(unsigned* bar, int* status, int* s_ok) {
   return *s_ok != 0;
 }
 
-// The owner of column k: its pivot (first row of maximal modulus among rows k..m-1, the
-// reduction of k_factor), published with the interchanged column.
-__device__ inline void factor_grid_pivot(const double* A, int ld, int m, int k, double* pub_col, int* pub_piv,
-                                         int* perm, int* status, double* s_pmax, int* s_pidx, int* s_piv) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double best = -1.0;
+// Warps 0 .. FG_PIV_WARPS - 1 of the owner of column k (its values at col): the pivot (the first
+// row of maximal modulus among rows k..m-1, as in k_factor; the moduli are compared as their
+// bit patterns, which order non-negative doubles as the values do), published with the
+// interchanged column.  Synchronises those warps only (named barrier 1).
+__device__ inline void factor_grid_pivot(const double* col, int ld, int m, int k, double* pub_col, int* pub_piv,
+                                         int* perm, int* status, unsigned long long* s_pkey, int* s_pidx,
+                                         int* s_piv) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int NT = FG_PIV_WARPS * 32;
+  unsigned long long best = 0;
   int bi = m;
-  for (int a = k + threadIdx.x; a < m; a += blockDim.x) {
-    const double v = fabs(A[(int64_t)k * ld + a]);
-    if (v > best) { best = v; bi = a; }
+  for (int a = k + t; a < m; a += NT) {
+    const unsigned long long v = (unsigned long long)__double_as_longlong(col[a]) & 0x7fffffffffffffffull;
+    if (bi == m || v > best) { best = v; bi = a; }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
   }
-  if (lane == 0) { s_pmax[warp] = best; s_pidx[warp] = bi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double bb = -1.0;
+  if (lane == 0) { s_pkey[warp] = best; s_pidx[warp] = bi; }
+  asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+  if (t == 0) {
+    unsigned long long bb = 0;
     int ii = m;
-    for (int w = 0; w < nw; ++w)
-      if (s_pmax[w] > bb || (s_pmax[w] == bb && s_pidx[w] < ii)) { bb = s_pmax[w]; ii = s_pidx[w]; }
+    for (int w = 0; w < FG_PIV_WARPS; ++w)
+      if (s_pidx[w] < m && (ii == m || s_pkey[w] > bb || (s_pkey[w] == bb && s_pidx[w] < ii))) {
+        bb = s_pkey[w];
+        ii = s_pidx[w];
+      }
     *s_piv = ii;
     perm[k] = ii;
     pub_piv[k & 1] = ii;
-    if (!(bb > 0.0)) atomicExch(status, DEV_SINGULAR);
+    if (!(__longlong_as_double((long long)bb) > 0.0)) atomicExch(status, DEV_SINGULAR);
   }
-  __syncthreads();
+  asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
   const int pr = *s_piv;
   double* out = pub_col + (int64_t)(k & 1) * ld;
-  for (int a = threadIdx.x; a < m; a += blockDim.x) {
-    double v = A[(int64_t)k * ld + a];
+  for (int a = t; a < m; a += NT) {
+    double v = col[a];
     if (pr != k && pr < m) {
-      if (a == k) v = A[(int64_t)k * ld + pr];
-      else if (a == pr) v = A[(int64_t)k * ld + k];
+      if (a == k) v = col[pr];
+      else if (a == pr) v = col[k];
     }
     out[a] = v;
   }
 }
 
-__global__ void __launch_bounds__(1024) k_factor_grid(LevelK L, FactorJob J, int bordered, int* status, unsigned* bar,
-                                                      double* pub_col, int* pub_piv, int* perm) {
-  extern __shared__ double sh[];  // per own column: rb, then the value moving to the pivot row
-  __shared__ double s_pmax[32];
-  __shared__ int s_pidx[32];
+__global__ void __launch_bounds__(FG_THREADS) k_factor_grid(LevelK L, FactorJob J, int bordered, int* status, unsigned* bar,
+                                                      double* pub_col, int* pub_piv, int* perm, int sc_cols) {
+  // shared memory: per own column rb, then the value moving to the pivot row; then the first
+  // sc_cols own columns
+  extern __shared__ double sh[];
+  __shared__ unsigned long long s_pkey[FG_PIV_WARPS];
+  __shared__ int s_pidx[FG_PIV_WARPS];
   __shared__ int s_piv, s_ok;
-  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5;
   const int64_t gt = (int64_t)rank * nt + tid, GT = (int64_t)G * nt;
   const int64_t d0 = J.dof_off[0];
   const int n = (int)(J.dof_off[1] - d0);
@@ -725,6 +739,8 @@ __global__ void __launch_bounds__(1024) k_factor_grid(LevelK L, FactorJob J, int
   double* sr = J.s_r + d0;
   double* sc = J.s_c + d0;
   const int* dofs = J.dofs + d0;
+  const int ncol_max = (m + G - 1) / G;
+  double* cs = sh + 2 * ncol_max;  // [sc_cols][ld]
   for (int64_t e = gt; e < (int64_t)m * m; e += GT) {
     const int b = (int)(e / m), a = (int)(e % m);
     double v;
@@ -756,85 +772,119 @@ __global__ void __launch_bounds__(1024) k_factor_grid(LevelK L, FactorJob J, int
   }
   if (!factor_grid_sync(bar, status, &s_ok)) return;
   const int ncol = (m > rank) ? (m - rank + G - 1) / G : 0;  // own columns rank + j G, j < ncol
-  if (rank == 0) factor_grid_pivot(A, ld, m, 0, pub_col, pub_piv, perm, status, s_pmax, s_pidx, &s_piv);
+  const int nsc = min(sc_cols, ncol);
+  // own column j: in shared memory for j < nsc, else in the matrix
+  auto col = [&](int j) -> double* {
+    return (j < nsc) ? cs + (int64_t)j * ld : A + (int64_t)(rank + j * G) * ld;
+  };
+  for (int j = 0; j < nsc; ++j)
+    for (int a = tid; a < m; a += nt) cs[(int64_t)j * ld + a] = A[(int64_t)(rank + j * G) * ld + a];
+  __syncthreads();
+  if (rank == 0 && warp < FG_PIV_WARPS)
+    factor_grid_pivot(col(0), ld, m, 0, pub_col, pub_piv, perm, status, s_pkey, s_pidx, &s_piv);
   if (!factor_grid_sync(bar, status, &s_ok)) return;
   for (int k = 0; k < m; ++k) {
     const int pr = pub_piv[k & 1];
     const double* colk = pub_col + (int64_t)(k & 1) * ld;
+    const bool swap = pr != k && pr < m;
+    const int jn = (k + 1 < m && (k + 1) % G == rank) ? (k + 1) / G : -1;  // own index of column k + 1
+    // this thread's register rows a = tid + q nt of the pivot column
+    double ck[FG_ROWS];
+#pragma unroll
+    for (int q = 0; q < FG_ROWS; ++q) {
+      const int a = tid + q * nt;
+      ck[q] = (a < m) ? colk[a] : 0.0;
+    }
     const double piv = colk[k];
     const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
-    const bool swap = pr != k && pr < m;
     // rowk of k_factor for the own columns (after the interchange), and the entry that moves
     // from row k to row pr
     for (int j = tid; j < ncol; j += nt) {
       const int b = rank + j * G;
-      const double ak = A[(int64_t)b * ld + k];
-      const double ap = swap ? A[(int64_t)b * ld + pr] : ak;
+      const double* c = col(j);
+      const double ak = c[k];
+      const double ap = swap ? c[pr] : ak;
       sh[j] = (b == k) ? ipiv : ap * ipiv;
       sh[ncol + j] = ak;
     }
     __syncthreads();
-    if (m <= FG_ROWS * nt) {
-      // this thread's rows a = tid + q nt: their pivot-column entries in registers, and two
-      // columns' entries loaded before their updates (the loads of a step are independent)
-      double ck[FG_ROWS];
-#pragma unroll
-      for (int q = 0; q < FG_ROWS; ++q) {
-        const int a = tid + q * nt;
-        ck[q] = (a < m) ? colk[a] : 0.0;
+    // the next column's owner: that column first, then its pivot on FG_PIV_WARPS warps
+    if (jn >= 0) {
+      double* colp = col(jn);
+      const double rb = sh[jn], moved = sh[ncol + jn];
+      for (int a = tid; a < m; a += nt) {
+        const double c = (swap && a == pr) ? moved : colp[a];
+        colp[a] = (a == k) ? rb : c - colk[a] * rb;
       }
-      for (int j0 = 0; j0 < ncol; j0 += 2) {
-        double cur[2][FG_ROWS];
+      __syncthreads();
+      if (warp < FG_PIV_WARPS)
+        factor_grid_pivot(colp, ld, m, k + 1, pub_col, pub_piv, perm, status, s_pkey, s_pidx, &s_piv);
+    }
+    // the other own columns on the register rows, two at a time: the next pair's entries are
+    // loaded before the current pair is updated
+    double cur[2][FG_ROWS], nxt[2][FG_ROWS];
+    auto load_pair = [&](int j0, double (&v)[2][FG_ROWS]) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const double* colp = A + (int64_t)(rank + (j0 + u) * G) * ld;
+      for (int u = 0; u < 2; ++u) {
+        const int j = j0 + u;
+        const bool live = j < ncol && j != jn;
+        const double* c = col(live ? j : 0);
 #pragma unroll
-          for (int q = 0; q < FG_ROWS; ++q) {
-            const int a = tid + q * nt;
-            cur[u][q] = (j0 + u < ncol && a < m) ? colp[a] : 0.0;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int j = j0 + u;
-          if (j >= ncol) break;
-          const int b = rank + j * G;
-          double* colp = A + (int64_t)b * ld;
-          const double rb = sh[j], moved = sh[ncol + j];
-#pragma unroll
-          for (int q = 0; q < FG_ROWS; ++q) {
-            const int a = tid + q * nt;
-            if (a >= m) continue;
-            if (b == k) {
-              colp[a] = (a == k) ? rb : -ck[q] * ipiv;
-            } else {
-              const double c = (swap && a == pr) ? moved : cur[u][q];
-              colp[a] = (a == k) ? rb : c - ck[q] * rb;
-            }
-          }
+        for (int q = 0; q < FG_ROWS; ++q) {
+          const int a = tid + q * nt;
+          v[u][q] = (live && a < m) ? c[a] : 0.0;
         }
       }
-    } else {
-      for (int j = 0; j < ncol; ++j) {
+    };
+    load_pair(0, cur);
+    for (int j0 = 0; j0 < ncol; j0 += 2) {
+      if (j0 + 2 < ncol) load_pair(j0 + 2, nxt);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = j0 + u;
+        if (j >= ncol || j == jn) continue;
         const int b = rank + j * G;
-        double* colp = A + (int64_t)b * ld;
+        double* colp = col(j);
+        const double rb = sh[j], moved = sh[ncol + j];
+#pragma unroll
+        for (int q = 0; q < FG_ROWS; ++q) {
+          const int a = tid + q * nt;
+          if (a >= m) continue;
+          if (b == k) {
+            colp[a] = (a == k) ? rb : -ck[q] * ipiv;
+          } else {
+            const double c = (swap && a == pr) ? moved : cur[u][q];
+            colp[a] = (a == k) ? rb : c - ck[q] * rb;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int q = 0; q < FG_ROWS; ++q) cur[u][q] = nxt[u][q];
+    }
+    // rows beyond the register rows
+    for (int a = FG_ROWS * nt + tid; a < m; a += nt) {
+      const double cka = colk[a];
+      for (int j = 0; j < ncol; ++j) {
+        if (j == jn) continue;
+        const int b = rank + j * G;
+        double* colp = col(j);
         const double rb = sh[j];
         if (b == k) {
-          for (int a = tid; a < m; a += nt) colp[a] = (a == k) ? rb : -colk[a] * ipiv;
+          colp[a] = (a == k) ? rb : -cka * ipiv;
         } else {
-          const double moved = sh[ncol + j];
-          for (int a = tid; a < m; a += nt) {
-            const double cur = (swap && a == pr) ? moved : colp[a];
-            colp[a] = (a == k) ? rb : cur - colk[a] * rb;
-          }
+          const double c = (swap && a == pr) ? sh[ncol + j] : colp[a];
+          colp[a] = (a == k) ? rb : c - cka * rb;
         }
       }
     }
-    __syncthreads();
-    if (k + 1 < m && (k + 1) % G == rank)
-      factor_grid_pivot(A, ld, m, k + 1, pub_col, pub_piv, perm, status, s_pmax, s_pidx, &s_piv);
     if (!factor_grid_sync(bar, status, &s_ok)) return;
   }
+  // the shared-memory columns back into the matrix
+  for (int j = 0; j < nsc; ++j)
+    for (int a = tid; a < m; a += nt) A[(int64_t)(rank + j * G) * ld + a] = cs[(int64_t)j * ld + a];
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
   // undo the row interchanges as column interchanges, last first (each row on its own)
   for (int64_t a = gt; a < m; a += GT) {
     for (int k = m - 1; k >= 0; --k) {
@@ -872,7 +922,43 @@ static size_t factor_pair_smem(int m) {
          + (size_t)3 * m * sizeof(int) + 64;        // pivots, column map, its inverse
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FP_THREADS)
+constexpr int FP_ROWS_PER_LANE = (FP_MMAX + 31) / 32;
+
+// One warp of the owner of column k (local index k >> 1): the first row a >= k of maximal
+// modulus (compared as the magnitudes' bit patterns, which order non-negative doubles as the
+// values do), written to perm[k] in both CTAs, and the column before the interchange into
+// pub[k & 1] of both.
+__device__ void pair_pivot_publish(cooperative_groups::cluster_group& cluster, const double* A, int ld, int m,
+                                   int k, double* pub, int* perm, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int r = (int)cluster.block_rank();
+  const double* ak = A + (int64_t)(k >> 1) * ld;
+  unsigned long long best = 0;
+  int bi = m;
+  for (int a = k + lane; a < m; a += 32) {
+    const unsigned long long v = (unsigned long long)__double_as_longlong(ak[a]) & 0x7fffffffffffffffull;
+    if (bi == m || v > best) { best = v; bi = a; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+  }
+  if (lane == 0) {
+    if (!(__longlong_as_double((long long)best) > 0.0)) atomicExch(status, DEV_SINGULAR);
+    perm[k] = bi;
+    *cluster.map_shared_rank(perm + k, r ^ 1) = bi;
+  }
+  double* colk = pub + (k & 1) * m;
+  double* peer = cluster.map_shared_rank(colk, r ^ 1);
+  for (int a = lane; a < m; a += 32) {
+    const double v = ak[a];
+    colk[a] = v;
+    peer[a] = v;
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FP_THREADS, 2)
 k_factor_pair(LevelK L, FactorJob J, const int* __restrict__ jobs, int* status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -883,8 +969,6 @@ k_factor_pair(LevelK L, FactorJob J, const int* __restrict__ jobs, int* status) 
   const int n = (int)(J.dof_off[p + 1] - d0);
   const int NN = L.N * L.N;
   __shared__ int s_border;
-  __shared__ double s_pmax[FP_THREADS / 32];
-  __shared__ int s_pidx[FP_THREADS / 32];
   if (threadIdx.x == 0) {
     int border = 0;
     if (J.border_all_pressure) {
@@ -961,41 +1045,11 @@ k_factor_pair(LevelK L, FactorJob J, const int* __restrict__ jobs, int* status) 
   }
   // both CTAs are done with the scales before the first column is published into pub
   cluster.sync();
+  // column 0's pivot and the column itself, published by its owner (CTA 0)
+  if (r == 0 && warp == 0) pair_pivot_publish(cluster, A, ld, m, 0, pub, perm, status);
+  cluster.sync();
   for (int k = 0; k < m; ++k) {
     double* colk = pub + (k & 1) * m;
-    if ((k & 1) == r) {
-      // I own column k: pivot search (first row of maximal modulus), then publish
-      const double* ak = A + (int64_t)(k >> 1) * ld;
-      double best = -1.0;
-      int bi = m;
-      for (int a = k + tid; a < m; a += FP_THREADS) {
-        const double v = fabs(ak[a]);
-        if (v > best) { best = v; bi = a; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) { s_pmax[warp] = best; s_pidx[warp] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        double bb = -1.0;
-        int ii = m;
-        for (int w = 0; w < nw; ++w)
-          if (s_pmax[w] > bb || (s_pmax[w] == bb && s_pidx[w] < ii)) { bb = s_pmax[w]; ii = s_pidx[w]; }
-        if (!(bb > 0.0)) atomicExch(status, DEV_SINGULAR);
-        perm[k] = ii;
-        *cluster.map_shared_rank(perm + k, r ^ 1) = ii;
-      }
-      double* peer = cluster.map_shared_rank(colk, r ^ 1);
-      for (int a = tid; a < m; a += FP_THREADS) {
-        const double v = ak[a];
-        colk[a] = v;
-        peer[a] = v;
-      }
-    }
-    cluster.sync();
     const int pr = perm[k];
     // row interchange k <-> pr on my columns and in the published column
     if (pr != k && pr < m) {
@@ -1019,17 +1073,49 @@ k_factor_pair(LevelK L, FactorJob J, const int* __restrict__ jobs, int* status) 
       rowk[q] = (b == k) ? ipiv : A[(int64_t)q * ld + k] * ipiv;
     }
     __syncthreads();
-    // rank-one update of my columns: warps over columns, lanes over rows
-    for (int q = warp; q < mc; q += nw) {
-      double* colp = A + (int64_t)q * ld;
-      const double rb = rowk[q];
-      if (2 * q + r == k) {
-        for (int a = lane; a < m; a += 32) colp[a] = (a == k) ? rb : -colk[a] * ipiv;
-      } else {
-        for (int a = lane; a < m; a += 32) colp[a] = (a == k) ? rb : colp[a] - colk[a] * rb;
+    // lookahead: the owner of column k + 1 updates it first; warp 0 then finds its pivot and
+    // publishes it while the other warps update the remaining columns
+    const int kn = k + 1;
+    const bool own_next = kn < m && (kn & 1) == r;
+    const int qn = kn >> 1;
+    if (own_next) {
+      double* colp = A + (int64_t)qn * ld;
+      const double rb = rowk[qn];
+      for (int a = tid; a < m; a += FP_THREADS) colp[a] = (a == k) ? rb : colp[a] - colk[a] * rb;
+      __syncthreads();
+    }
+    if (own_next && warp == 0) {
+      pair_pivot_publish(cluster, A, ld, m, kn, pub, perm, status);
+    } else {
+      // rank-one update of my other columns: warps over columns, lanes over rows, the pivot
+      // column's entries of this lane's rows held in registers
+      double ck[FP_ROWS_PER_LANE];
+#pragma unroll
+      for (int i = 0; i < FP_ROWS_PER_LANE; ++i) {
+        const int a = lane + 32 * i;
+        ck[i] = (a < m) ? colk[a] : 0.0;
+      }
+      const int w0 = own_next ? warp - 1 : warp, nwu = own_next ? nw - 1 : nw;
+      for (int q = w0; q < mc; q += nwu) {
+        if (own_next && q == qn) continue;
+        double* colp = A + (int64_t)q * ld;
+        const double rb = rowk[q];
+        if (2 * q + r == k) {
+#pragma unroll
+          for (int i = 0; i < FP_ROWS_PER_LANE; ++i) {
+            const int a = lane + 32 * i;
+            if (a < m) colp[a] = (a == k) ? rb : -ck[i] * ipiv;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < FP_ROWS_PER_LANE; ++i) {
+            const int a = lane + 32 * i;
+            if (a < m) colp[a] = (a == k) ? rb : colp[a] - ck[i] * rb;
+          }
+        }
       }
     }
-    __syncthreads();
+    cluster.sync();  // the next pivot and column are published; this step's reads are done
   }
   // undo the row interchanges as column interchanges (last first): the column at position c
   // of the result is my column src[c] when src[c] is one of mine
@@ -1287,13 +1373,30 @@ static void factor_patches(cav_hierarchy* H, Level& lv, bool standard, cudaStrea
       }
     }
     if (!pair_jobs.empty()) {
+      // largest first (the block scheduler issues CTAs in order); the patches whose matrices
+      // leave room for two CTAs per SM (m <= m2) in a launch of their own
+      std::stable_sort(pair_jobs.begin(), pair_jobs.end(), [&](int a, int b) { return hsizes[a] > hsizes[b]; });
+      int dev = 0, smem_sm = 0;
+      CAV_CHECK_CUDA(cudaGetDevice(&dev));
+      CAV_CHECK_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+      int m2 = pair_mmax;
+      while (m2 > FP_MMIN && 2 * (factor_pair_smem(m2) + 2048) > (size_t)smem_sm) --m2;
+      const int nl = (int)(std::find_if(pair_jobs.begin(), pair_jobs.end(),
+                                        [&](int p) { return hsizes[p] + 1 <= m2; }) - pair_jobs.begin());
       int* d_jobs = scratch.alloc<int>(pair_jobs.size());
       CAV_CHECK_CUDA(cudaMemcpyAsync(d_jobs, pair_jobs.data(), sizeof(int) * pair_jobs.size(), cudaMemcpyHostToDevice,
                                      st));
       const size_t psm = factor_pair_smem(pair_mmax);
       CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-      k_factor_pair<<<2 * (int)pair_jobs.size(), FP_THREADS, psm, st>>>(LK, J, d_jobs, H->status);
-      CAV_CHECK_LAUNCH();
+      if (nl > 0) {
+        k_factor_pair<<<2 * nl, FP_THREADS, psm, st>>>(LK, J, d_jobs, H->status);
+        CAV_CHECK_LAUNCH();
+      }
+      if (nl < (int)pair_jobs.size()) {
+        k_factor_pair<<<2 * ((int)pair_jobs.size() - nl), FP_THREADS, factor_pair_smem(m2), st>>>(LK, J, d_jobs + nl,
+                                                                                                   H->status);
+        CAV_CHECK_LAUNCH();
+      }
     }
     if (!glob_jobs.empty()) {
       FactorJob Jg = J;
@@ -1542,9 +1645,10 @@ static void build_smoother(cav_hierarchy* H, Level& lv, cudaStream_t st) {
 // coarsest systems above this order are factorised by the grid-parallel kernel
 constexpr int COARSEST_GRID_M = 256;
 
-static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
+// Enqueues the coarsest system's factorisation on st (no sync): its buffers come from scratch,
+// which the caller releases after checking the status.
+static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st, Arena& scratch) {
   Arena& A = H->arena;
-  Arena scratch;
   // periodic: bordered by the pressure-mean constraint; channel: the plain operator
   const int N = lv.N, NN = N * N, n = 3 * NN, m = lv.channel ? n : n + 1;
   const LevelK LK = level_k(lv);
@@ -1579,8 +1683,19 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     int sms = 0, dev = 0, per_sm = 0;
     CAV_CHECK_CUDA(cudaGetDevice(&dev));
     CAV_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t gsm = 2 * sizeof(double) * (size_t)((m + sms - 1) / sms);
-    CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_grid, 1024, gsm));
+    // rb and the moved entries per own column, then as many whole own columns as fit
+    int optin = 0;
+    CAV_CHECK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    CAV_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_factor_grid));
+    const int ncol_max = (m + sms - 1) / sms;
+    const size_t base = 2 * sizeof(double) * (size_t)ncol_max;
+    const size_t room = (size_t)optin - fa.sharedSizeBytes;
+    const size_t col_bytes = sizeof(double) * (size_t)round8(m);
+    const int sc_cols = room > base ? (int)std::min<size_t>((room - base) / col_bytes, (size_t)ncol_max) : 0;
+    const size_t gsm = base + (size_t)sc_cols * col_bytes;
+    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_grid, FG_THREADS, gsm));
     CAV_REQUIRE(per_sm >= 1, "coarsest factorisation: the grid kernel cannot be resident");
     double* pub_col = scratch.alloc<double>(2 * (size_t)round8(m));
     int* pub_piv = scratch.alloc<int>(2);
@@ -1588,7 +1703,7 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     const int bordered = lv.channel ? 0 : 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sms);
-    cfg.blockDim = dim3(1024);
+    cfg.blockDim = dim3(FG_THREADS);
     cfg.dynamicSmemBytes = gsm;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1597,7 +1712,7 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_factor_grid, LK, J, bordered, H->status, H->gbar, pub_col, pub_piv,
-                                      perm));
+                                      perm, sc_cols));
     CAV_CHECK_LAUNCH();
   } else {
     const size_t fsm = factor_smem(m);
@@ -1610,8 +1725,6 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st) {
   if (!lv.coarse_inv) lv.coarse_inv = A.alloc<double>((size_t)m * m);  // reused by cav_refactor
   k_fold_rowmajor<<<64, 256, 0, st>>>(m, work, wsr, wsc, lv.coarse_inv);
   CAV_CHECK_LAUNCH();
-  check_status(H, st, "coarsest factorisation");
-  scratch.release();
 }
 
 void build_levels(cav_hierarchy* H, cudaStream_t st) {
@@ -1667,11 +1780,30 @@ void build_levels(cav_hierarchy* H, cudaStream_t st) {
     lv.x = A.alloc<double>(3 * NN);
     lv.b = A.alloc<double>(3 * NN);
   }
-  for (size_t l = 0; l < sizes.size(); ++l) {
-    Level& lv = H->levels[l];
-    if (lv.coarsest) build_coarsest(H, lv, st);
-    else build_smoother(H, lv, st);
-    if (lv.coloured) build_colours(H, lv, st);
+  {
+    // the coarsest factorisation is enqueued before the host computes the coloured levels'
+    // classes, so the two overlap; its scratch is released once the stream has passed it
+    std::vector<ColourPlan> plans(sizes.size());
+    Arena coarse_scratch;
+    try {
+      for (size_t l = 0; l < sizes.size(); ++l) {
+        Level& lv = H->levels[l];
+        if (lv.coarsest) continue;
+        build_smoother(H, lv, st);
+        if (lv.coloured) colour_fetch(lv, plans[l], st);
+      }
+      build_coarsest(H, H->levels.back(), st, coarse_scratch);
+      for (size_t l = 0; l < sizes.size(); ++l)
+        if (H->levels[l].coloured) colour_plan(H->levels[l], plans[l]);
+      check_status(H, st, "coarsest factorisation");
+      coarse_scratch.release();
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      coarse_scratch.release();
+      throw;
+    }
+    for (size_t l = 0; l < sizes.size(); ++l)
+      if (H->levels[l].coloured) colour_upload(H, H->levels[l], plans[l], st);
   }
   if (H->desc.autotune)
     for (auto& lv : H->levels)
@@ -1726,16 +1858,24 @@ void refactor_levels(cav_hierarchy* H, const ib_system* s, cudaStream_t st) {
     CAV_CHECK_CUDA(cudaMemcpyAsync(l0.ee.vals, s->ee.vals, sizeof(double) * s->ee.nnz, cudaMemcpyDeviceToDevice, st));
   for (size_t l = 1; l < H->levels.size(); ++l)
     galerkin_values(H->levels[l - 1].ee, H->levels[l].N, H->levels[l].ee, H->levels[l].channel, st);
-  for (auto& lv : H->levels) {
-    if (lv.coarsest) {
-      build_coarsest(H, lv, st);
-      continue;
+  Arena coarse_scratch;
+  try {
+    for (auto& lv : H->levels) {
+      if (lv.coarsest) {
+        build_coarsest(H, lv, st, coarse_scratch);
+        continue;
+      }
+      factor_patches(H, lv, false, st);
+      if (lv.coloured) colour_refresh_values(lv, st);
     }
-    factor_patches(H, lv, false, st);
-    if (lv.coloured) colour_refresh_values(lv, st);
+    CAV_CHECK_CUDA(cudaStreamSynchronize(st));
+    check_status(H, st, "refactorisation");
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    coarse_scratch.release();
+    throw;
   }
-  CAV_CHECK_CUDA(cudaStreamSynchronize(st));
-  check_status(H, st, "refactorisation");
+  coarse_scratch.release();
   H->sys = s;
 }
 

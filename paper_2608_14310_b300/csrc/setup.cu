@@ -719,15 +719,13 @@ __device__ inline void factor_grid_pivot(const double* col, int ld, int m, int k
   }
 }
 
-__global__ void __launch_bounds__(FG_THREADS) k_factor_grid(LevelK L, FactorJob J, int bordered, int* status, unsigned* bar,
-                                                      double* pub_col, int* pub_piv, int* perm, int sc_cols) {
-  // shared memory: per own column rb, then the value moving to the pivot row; then the first
-  // sc_cols own columns
-  extern __shared__ double sh[];
-  __shared__ unsigned long long s_pkey[FG_PIV_WARPS];
-  __shared__ int s_pidx[FG_PIV_WARPS];
-  __shared__ int s_piv, s_ok;
-  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5;
+// The steps before the elimination, on the whole grid: the coarsest matrix (bordered by the
+// pressure-mean row and column when `bordered`) extracted into J.A, then power-of-two row and
+// column equilibration (the scales into J.s_r, J.s_c), as in k_factor.  False if a barrier
+// ran out.
+__device__ bool factor_grid_prepare(const LevelK& L, const FactorJob& J, int bordered, int* status, unsigned* bar,
+                                    int* s_ok) {
+  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int64_t gt = (int64_t)rank * nt + tid, GT = (int64_t)G * nt;
   const int64_t d0 = J.dof_off[0];
   const int n = (int)(J.dof_off[1] - d0);
@@ -739,8 +737,6 @@ __global__ void __launch_bounds__(FG_THREADS) k_factor_grid(LevelK L, FactorJob 
   double* sr = J.s_r + d0;
   double* sc = J.s_c + d0;
   const int* dofs = J.dofs + d0;
-  const int ncol_max = (m + G - 1) / G;
-  double* cs = sh + 2 * ncol_max;  // [sc_cols][ld]
   for (int64_t e = gt; e < (int64_t)m * m; e += GT) {
     const int b = (int)(e / m), a = (int)(e % m);
     double v;
@@ -752,25 +748,58 @@ __global__ void __launch_bounds__(FG_THREADS) k_factor_grid(LevelK L, FactorJob 
     }
     A[(int64_t)b * ld + a] = v;
   }
-  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  if (!factor_grid_sync(bar, status, s_ok)) return false;
   for (int64_t a = gt; a < m; a += GT) {
     double mx = 0.0;
     for (int b = 0; b < m; ++b) mx = fmax(mx, fabs(A[(int64_t)b * ld + a]));
     sr[a] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
     if (mx == 0.0) atomicExch(status, DEV_SINGULAR);
   }
-  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  if (!factor_grid_sync(bar, status, s_ok)) return false;
   for (int64_t b = gt; b < m; b += GT) {
     double mx = 0.0;
     for (int a = 0; a < m; ++a) mx = fmax(mx, fabs(sr[a] * A[(int64_t)b * ld + a]));
     sc[b] = (mx > 0.0) ? pow2_recip(mx) : 1.0;
   }
-  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  if (!factor_grid_sync(bar, status, s_ok)) return false;
   for (int64_t e = gt; e < (int64_t)m * m; e += GT) {
     const int b = (int)(e / m), a = (int)(e % m);
     A[(int64_t)b * ld + a] = sr[a] * A[(int64_t)b * ld + a] * sc[b];
   }
-  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  if (!factor_grid_sync(bar, status, s_ok)) return false;
+  return true;
+}
+
+// The row interchanges undone as column interchanges, last first (each row on its own).
+__device__ void factor_grid_unscramble(double* A, int ld, int m, const int* perm) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, GT = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t a = gt; a < m; a += GT) {
+    for (int k = m - 1; k >= 0; --k) {
+      const int pr = perm[k];
+      if (pr != k && pr < m) {
+        const double t = A[(int64_t)k * ld + a];
+        A[(int64_t)k * ld + a] = A[(int64_t)pr * ld + a];
+        A[(int64_t)pr * ld + a] = t;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(FG_THREADS) k_factor_grid(LevelK L, FactorJob J, int bordered, int* status, unsigned* bar,
+                                                      double* pub_col, int* pub_piv, int* perm, int sc_cols) {
+  // shared memory: per own column rb, then the value moving to the pivot row; then the first
+  // sc_cols own columns
+  extern __shared__ double sh[];
+  __shared__ unsigned long long s_pkey[FG_PIV_WARPS];
+  __shared__ int s_pidx[FG_PIV_WARPS];
+  __shared__ int s_piv, s_ok;
+  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5;
+  const int m = (int)(J.dof_off[1] - J.dof_off[0]) + bordered;
+  const int ld = (m + 7) & ~7;
+  double* A = J.A + J.mat_off[0];
+  const int ncol_max = (m + G - 1) / G;
+  double* cs = sh + 2 * ncol_max;  // [sc_cols][ld]
+  if (!factor_grid_prepare(L, J, bordered, status, bar, &s_ok)) return;
   const int ncol = (m > rank) ? (m - rank + G - 1) / G : 0;  // own columns rank + j G, j < ncol
   const int nsc = min(sc_cols, ncol);
   // own column j: in shared memory for j < nsc, else in the matrix
@@ -885,17 +914,293 @@ __global__ void __launch_bounds__(FG_THREADS) k_factor_grid(LevelK L, FactorJob 
   for (int j = 0; j < nsc; ++j)
     for (int a = tid; a < m; a += nt) A[(int64_t)(rank + j * G) * ld + a] = cs[(int64_t)j * ld + a];
   if (!factor_grid_sync(bar, status, &s_ok)) return;
-  // undo the row interchanges as column interchanges, last first (each row on its own)
-  for (int64_t a = gt; a < m; a += GT) {
-    for (int k = m - 1; k >= 0; --k) {
-      const int pr = perm[k];
-      if (pr != k && pr < m) {
-        const double t = A[(int64_t)k * ld + a];
-        A[(int64_t)k * ld + a] = A[(int64_t)pr * ld + a];
-        A[(int64_t)pr * ld + a] = t;
+  factor_grid_unscramble(A, ld, m, perm);
+}
+
+// The same factorisation blocked in panels of GP_PB columns, with one grid barrier per panel
+// instead of one per elimination step.  CTA 0 factorises the panels: in the interval of panel
+// p it loads panel p + 1's columns into shared memory, applies panel p's steps to them, then
+// eliminates within the panel (pivot search, interchange, update of the panel's columns) and
+// publishes, per step k, the pivot row and the pivot column as the other columns use it (cpan,
+// ppiv: double-buffered by the panel's parity).  The other CTAs own the columns cyclically and
+// apply panel p's steps to every own column outside panels p and p + 1, GP_C columns at a
+// time held in registers (rows tid + q GP_THREADS), the two entries a step needs from a
+// column (rows k and p_k) passed through shared memory.  A column goes through the steps
+// k = 0, 1, ... in order with the expressions of k_factor, so the inverse is the same bit for
+// bit.  Needs m <= R GP_THREADS and (GP_PB + 1) round8(m) doubles of shared memory.
+constexpr int GP_THREADS = 512;
+constexpr int GP_PB = 8;  // panel width
+constexpr int GP_C = 4;   // columns per register chunk
+
+template <int R>
+__global__ void __launch_bounds__(GP_THREADS) k_factor_panels(LevelK L, FactorJob J, int bordered, int* status,
+                                                              unsigned* bar, double* cpan, int* ppiv, int* perm) {
+  // panel CTA: [GP_PB][ld] the panel's columns, then [ld] the current pivot column;
+  // the others: [GP_PB][ld] the published pivot columns of the panel being applied
+  extern __shared__ double gsh[];
+  __shared__ double s_ak[2][GP_C], s_ap[2][GP_C];
+  __shared__ double s_rb[GP_PB], s_mv[GP_PB], s_ipiv[GP_PB];
+  __shared__ int s_pr[GP_PB];
+  __shared__ unsigned long long s_key[GP_THREADS / 32];
+  __shared__ int s_idx[GP_THREADS / 32];
+  __shared__ int s_piv, s_ok;
+  const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = (int)(J.dof_off[1] - J.dof_off[0]) + bordered;
+  const int ld = (m + 7) & ~7;
+  double* A = J.A + J.mat_off[0];
+  const int npan = (m + GP_PB - 1) / GP_PB;
+  const int U = G - 1;  // column j belongs to CTA 1 + j % U
+  if (!factor_grid_prepare(L, J, bordered, status, bar, &s_ok)) return;
+  double* colbuf = gsh + (int64_t)GP_PB * ld;
+
+  // --- the panel CTA's parts
+  auto panel_width = [&](int q) { return min(GP_PB, m - q * GP_PB); };
+  auto panel_load = [&](int q) {
+    const int nb = panel_width(q);
+    for (int i = 0; i < nb; ++i)
+      for (int a = tid; a < m; a += GP_THREADS) gsh[(int64_t)i * ld + a] = A[(int64_t)(q * GP_PB + i) * ld + a];
+    __syncthreads();
+  };
+  auto panel_store = [&](int q) {
+    const int nb = panel_width(q);
+    for (int i = 0; i < nb; ++i)
+      for (int a = tid; a < m; a += GP_THREADS) A[(int64_t)(q * GP_PB + i) * ld + a] = gsh[(int64_t)i * ld + a];
+  };
+  // panel p's published steps applied to panel p + 1's columns in shared memory; each step's
+  // pivot-column rows of this thread are loaded one step ahead
+  auto panel_apply = [&](int p) {
+    const int nbp = panel_width(p), nb = panel_width(p + 1);
+    double ckn[R];
+    auto load_ck = [&](int i, double (&v)[R]) {
+      const double* ck = cpan + (int64_t)((p & 1) * GP_PB + i) * ld;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int a = tid + q * GP_THREADS;
+        v[q] = (a < m) ? ck[a] : 0.0;
+      }
+    };
+    load_ck(0, ckn);
+    for (int i = 0; i < nbp; ++i) {
+      double ckc[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) ckc[q] = ckn[q];
+      if (i + 1 < nbp) load_ck(i + 1, ckn);
+      const int k = p * GP_PB + i;
+      const int pr = ppiv[(p & 1) * GP_PB + i];
+      const bool swap = pr != k && pr < m;
+      const double piv = cpan[(int64_t)((p & 1) * GP_PB + i) * ld + k];
+      const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
+      if (tid < nb) {
+        const double* c = gsh + (int64_t)tid * ld;
+        const double ak = c[k];
+        const double ap = swap ? c[pr] : ak;
+        s_rb[tid] = ap * ipiv;
+        s_mv[tid] = ak;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int a = tid + q * GP_THREADS;
+        if (a >= m) continue;
+        for (int i2 = 0; i2 < nb; ++i2) {
+          double* colp = gsh + (int64_t)i2 * ld;
+          const double rb = s_rb[i2];
+          const double c = (swap && a == pr) ? s_mv[i2] : colp[a];
+          colp[a] = (a == k) ? rb : c - ckc[q] * rb;
+        }
+      }
+      __syncthreads();
+    }
+  };
+  // elimination within panel q (its columns in shared memory, already through panel q - 1)
+  auto panel_factor = [&](int q) {
+    const int nb = panel_width(q);
+    for (int i = 0; i < nb; ++i) {
+      const int k = q * GP_PB + i;
+      const double* ci = gsh + (int64_t)i * ld;
+      unsigned long long best = 0;
+      int bi = m;
+      for (int a = k + tid; a < m; a += GP_THREADS) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(ci[a]) & 0x7fffffffffffffffull;
+        if (bi == m || v > best) { best = v; bi = a; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { s_key[warp] = best; s_idx[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long bb = 0;
+        int ii = m;
+        for (int w = 0; w < GP_THREADS / 32; ++w)
+          if (s_idx[w] < m && (ii == m || s_key[w] > bb || (s_key[w] == bb && s_idx[w] < ii))) {
+            bb = s_key[w];
+            ii = s_idx[w];
+          }
+        if (!(__longlong_as_double((long long)bb) > 0.0)) atomicExch(status, DEV_SINGULAR);
+        s_piv = ii;
+        perm[k] = ii;
+        ppiv[(q & 1) * GP_PB + i] = ii;
+      }
+      __syncthreads();
+      const int pr = s_piv;
+      const bool swap = pr != k && pr < m;
+      // the pivot column with rows k and pr interchanged, kept and published; the columns'
+      // rb and moved entries in the same pass (all read the columns before the update)
+      const double piv = swap ? ci[pr] : ci[k];
+      const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
+      double* pub = cpan + (int64_t)((q & 1) * GP_PB + i) * ld;
+      for (int a = tid; a < m; a += GP_THREADS) {
+        double v = ci[a];
+        if (swap) {
+          if (a == k) v = ci[pr];
+          else if (a == pr) v = ci[k];
+        }
+        colbuf[a] = v;
+        pub[a] = v;
+      }
+      if (tid < nb) {
+        const double* c = gsh + (int64_t)tid * ld;
+        const double ak = c[k];
+        const double ap = swap ? c[pr] : ak;
+        s_rb[tid] = (tid == i) ? ipiv : ap * ipiv;
+        s_mv[tid] = ak;
+      }
+      __syncthreads();
+      for (int a = tid; a < m; a += GP_THREADS) {
+        const double cka = colbuf[a];
+        for (int i2 = 0; i2 < nb; ++i2) {
+          double* colp = gsh + (int64_t)i2 * ld;
+          const double rb = s_rb[i2];
+          if (i2 == i) {
+            colp[a] = (a == k) ? rb : -cka * ipiv;
+          } else {
+            const double c = (swap && a == pr) ? s_mv[i2] : colp[a];
+            colp[a] = (a == k) ? rb : c - cka * rb;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  };
+
+  // --- the other CTAs: panel p's steps on their own columns outside panels p and p + 1
+  const int ncol = (rank >= 1 && m > rank - 1) ? (m - (rank - 1) + U - 1) / U : 0;  // own j = rank - 1 + t U
+  unsigned slot_ctr = 0;
+  auto update_apply = [&](int p) {
+    const int nbp = panel_width(p);
+    for (int i = 0; i < nbp; ++i)
+      for (int a = tid; a < m; a += GP_THREADS)
+        gsh[(int64_t)i * ld + a] = cpan[(int64_t)((p & 1) * GP_PB + i) * ld + a];
+    if (tid < nbp) {
+      const int k = p * GP_PB + tid;
+      s_pr[tid] = ppiv[(p & 1) * GP_PB + tid];
+      const double piv = cpan[(int64_t)((p & 1) * GP_PB + tid) * ld + k];
+      s_ipiv[tid] = (piv != 0.0) ? 1.0 / piv : 0.0;
+    }
+    __syncthreads();
+    auto live = [&](int t) {
+      if (t >= ncol) return false;
+      const int pj = (rank - 1 + t * U) / GP_PB;
+      return pj != p && pj != p + 1;
+    };
+    double cur[GP_C][R];
+    auto load_chunk = [&](int t0, double (&v)[GP_C][R]) {
+#pragma unroll
+      for (int c = 0; c < GP_C; ++c) {
+        const int t = t0 + c;
+        const bool lv = live(t);
+        const double* col = A + (int64_t)(rank - 1 + (lv ? t : 0) * U) * ld;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int a = tid + q * GP_THREADS;
+          v[c][q] = (lv && a < m) ? col[a] : 0.0;
+        }
+      }
+    };
+    for (int t0 = 0; t0 < ncol; t0 += GP_C) {
+      load_chunk(t0, cur);
+      bool lv[GP_C];
+      bool any = false;
+#pragma unroll
+      for (int c = 0; c < GP_C; ++c) {
+        lv[c] = live(t0 + c);
+        any = any || lv[c];
+      }
+      if (any) {
+        for (int i = 0; i < nbp; ++i) {
+          const int k = p * GP_PB + i;
+          const int pr = s_pr[i];
+          const bool swap = pr != k && pr < m;
+          const double ipiv = s_ipiv[i];
+          const int sl = slot_ctr & 1;
+          ++slot_ctr;
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const int a = tid + q * GP_THREADS;
+            if (a == k) {
+#pragma unroll
+              for (int c = 0; c < GP_C; ++c) s_ak[sl][c] = cur[c][q];
+            }
+            if (a == pr) {
+#pragma unroll
+              for (int c = 0; c < GP_C; ++c) s_ap[sl][c] = cur[c][q];
+            }
+          }
+          __syncthreads();
+          const double* ck = gsh + (int64_t)i * ld;
+#pragma unroll
+          for (int c = 0; c < GP_C; ++c) {
+            if (!lv[c]) continue;
+            const double ak = s_ak[sl][c];
+            const double ap = swap ? s_ap[sl][c] : ak;
+            const double rb = ap * ipiv, moved = ak;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+              const int a = tid + q * GP_THREADS;
+              if (a >= m) continue;
+              const double cc = (swap && a == pr) ? moved : cur[c][q];
+              cur[c][q] = (a == k) ? rb : cc - ck[a] * rb;
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < GP_C; ++c) {
+          if (!lv[c]) continue;
+          double* col = A + (int64_t)(rank - 1 + (t0 + c) * U) * ld;
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const int a = tid + q * GP_THREADS;
+            if (a < m) col[a] = cur[c][q];
+          }
+        }
       }
     }
+    __syncthreads();  // gsh is refilled by the next panel
+  };
+
+  if (rank == 0) {
+    panel_load(0);
+    panel_factor(0);
+    panel_store(0);
   }
+  if (!factor_grid_sync(bar, status, &s_ok)) return;
+  for (int p = 0; p < npan; ++p) {
+    if (rank == 0) {
+      if (p + 1 < npan) {
+        panel_load(p + 1);
+        panel_apply(p);
+        panel_factor(p + 1);
+        panel_store(p + 1);
+      }
+    } else {
+      update_apply(p);
+    }
+    if (!factor_grid_sync(bar, status, &s_ok)) return;
+  }
+  factor_grid_unscramble(A, ld, m, perm);
 }
 
 // The same factorisation for one patch on a pair of CTAs (a cluster of two), the matrix held
@@ -1678,42 +1983,61 @@ static void build_coarsest(cav_hierarchy* H, Level& lv, cudaStream_t st, Arena& 
   J.border_all_pressure = 0;
   J.use_ee = 1;
   if (m > COARSEST_GRID_M && !std::getenv("CAV_COARSEST_ONE_CTA")) {
-    // a larger coarsest level: the factorisation on every SM (same bits as the one-CTA kernel;
-    // CAV_COARSEST_ONE_CTA, a test hook, keeps the one-CTA kernel)
-    int sms = 0, dev = 0, per_sm = 0;
+    // a larger coarsest level: the factorisation on every SM, blocked in panels where the panel
+    // fits in shared memory, else column by column (both give the one-CTA kernel's bits; the
+    // test hooks CAV_COARSEST_ONE_CTA and CAV_COARSEST_COLUMNS select the other forms)
+    int sms = 0, dev = 0, per_sm = 0, optin = 0;
     CAV_CHECK_CUDA(cudaGetDevice(&dev));
     CAV_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // rb and the moved entries per own column, then as many whole own columns as fit
-    int optin = 0;
     CAV_CHECK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa;
-    CAV_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_factor_grid));
-    const int ncol_max = (m + sms - 1) / sms;
-    const size_t base = 2 * sizeof(double) * (size_t)ncol_max;
-    const size_t room = (size_t)optin - fa.sharedSizeBytes;
-    const size_t col_bytes = sizeof(double) * (size_t)round8(m);
-    const int sc_cols = room > base ? (int)std::min<size_t>((room - base) / col_bytes, (size_t)ncol_max) : 0;
-    const size_t gsm = base + (size_t)sc_cols * col_bytes;
-    CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
-    CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_grid, FG_THREADS, gsm));
-    CAV_REQUIRE(per_sm >= 1, "coarsest factorisation: the grid kernel cannot be resident");
-    double* pub_col = scratch.alloc<double>(2 * (size_t)round8(m));
-    int* pub_piv = scratch.alloc<int>(2);
-    int* perm = scratch.alloc<int>(m);
     const int bordered = lv.channel ? 0 : 1;
+    const size_t col_bytes = sizeof(double) * (size_t)round8(m);
+    int* perm = scratch.alloc<int>(m);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sms);
-    cfg.blockDim = dim3(FG_THREADS);
-    cfg.dynamicSmemBytes = gsm;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barriers need it
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_factor_grid, LK, J, bordered, H->status, H->gbar, pub_col, pub_piv,
-                                      perm, sc_cols));
-    CAV_CHECK_LAUNCH();
+    constexpr int GP_R = 7;  // register rows per thread of the panel kernel
+    cudaFuncAttributes pa;
+    CAV_CHECK_CUDA(cudaFuncGetAttributes(&pa, k_factor_panels<GP_R>));
+    const size_t psm = (GP_PB + 1) * col_bytes;
+    const bool panels = !std::getenv("CAV_COARSEST_COLUMNS") && m <= GP_R * GP_THREADS && sms >= 2 &&
+                        psm + pa.sharedSizeBytes <= (size_t)optin;
+    if (panels) {
+      CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor_panels<GP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+      CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_panels<GP_R>, GP_THREADS, psm));
+      CAV_REQUIRE(per_sm >= 1, "coarsest factorisation: the panel kernel cannot be resident");
+      double* cpan = scratch.alloc<double>(2 * (size_t)GP_PB * round8(m));
+      int* ppiv = scratch.alloc<int>(2 * GP_PB);
+      cfg.blockDim = dim3(GP_THREADS);
+      cfg.dynamicSmemBytes = psm;
+      CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_factor_panels<GP_R>, LK, J, bordered, H->status, H->gbar, cpan, ppiv,
+                                        perm));
+      CAV_CHECK_LAUNCH();
+    } else {
+      // rb and the moved entries per own column, then as many whole own columns as fit
+      cudaFuncAttributes fa;
+      CAV_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_factor_grid));
+      const int ncol_max = (m + sms - 1) / sms;
+      const size_t base = 2 * sizeof(double) * (size_t)ncol_max;
+      const size_t room = (size_t)optin - fa.sharedSizeBytes;
+      const int sc_cols = room > base ? (int)std::min<size_t>((room - base) / col_bytes, (size_t)ncol_max) : 0;
+      const size_t gsm = base + (size_t)sc_cols * col_bytes;
+      CAV_CHECK_CUDA(cudaFuncSetAttribute(k_factor_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+      CAV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_grid, FG_THREADS, gsm));
+      CAV_REQUIRE(per_sm >= 1, "coarsest factorisation: the grid kernel cannot be resident");
+      double* pub_col = scratch.alloc<double>(2 * (size_t)round8(m));
+      int* pub_piv = scratch.alloc<int>(2);
+      cfg.blockDim = dim3(FG_THREADS);
+      cfg.dynamicSmemBytes = gsm;
+      CAV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_factor_grid, LK, J, bordered, H->status, H->gbar, pub_col, pub_piv,
+                                        perm, sc_cols));
+      CAV_CHECK_LAUNCH();
+    }
   } else {
     const size_t fsm = factor_smem(m);
     if (fsm > 48 * 1024)

@@ -1,8 +1,10 @@
 """The coarsest level's direct solve (Sec. 4) with a larger coarsest grid, factorised on every
-SM: the grid-parallel Gauss-Jordan kernel must give the one-CTA kernel's inverse bit for bit
-(CAV_COARSEST_ONE_CTA=1, a set-up test hook, keeps the one-CTA kernel), compared through the
-coarsest solve and a whole V-cycle, on the periodic (bordered) and the channel's (plain)
-coarsest system; and a 32 x 32 coarsest level (3073 unknowns) solves as the oracle does.
+SM: both grid-parallel Gauss-Jordan kernels (blocked in panels, the default where a panel fits
+in shared memory; column by column, CAV_COARSEST_COLUMNS=1) must give the one-CTA kernel's
+inverse bit for bit (CAV_COARSEST_ONE_CTA=1 keeps the one-CTA kernel; both are set-up test
+hooks), compared through the coarsest solve and a whole V-cycle, on the periodic (bordered) and
+the channel's (plain) coarsest system; the two grid kernels agree bit for bit on the 32 x 32
+coarsest level (3073 unknowns), which solves as the oracle does.
 """
 import os
 
@@ -16,23 +18,28 @@ from tests.gpu_helpers import host, rel, torch_dev
 pytestmark = pytest.mark.gpu
 
 
-def _setup(api, s, one_cta, **kw):
-    if one_cta:
-        os.environ["CAV_COARSEST_ONE_CTA"] = "1"
+HOOKS = {"one_cta": "CAV_COARSEST_ONE_CTA", "columns": "CAV_COARSEST_COLUMNS"}
+
+
+def _setup(api, s, form, **kw):
+    if form in HOOKS:
+        os.environ[HOOKS[form]] = "1"
     try:
         return api.cav_setup(s, **kw)
     finally:
-        os.environ.pop("CAV_COARSEST_ONE_CTA", None)
+        for v in HOOKS.values():
+            os.environ.pop(v, None)
 
 
+@pytest.mark.parametrize("form", ["panels", "columns"])
 @pytest.mark.parametrize("name", ["membrane64", "channel16"])
-def test_grid_factorisation_equals_one_cta(name):
+def test_grid_factorisation_equals_one_cta(name, form):
     from paper_2608_14310_b300 import api
     rec = W.membrane_ellipse(64, 1e4) if name == "membrane64" else W.fiber_channel(16)
     s = api.ib_setup(rec)
     kw = dict(coarsest_N=16, nu_pre=1, nu_post=1, alpha=0.85, precision="fp64")
-    hg = _setup(api, s, False, **kw)
-    h1 = _setup(api, s, True, **kw)
+    hg = _setup(api, s, form, **kw)
+    h1 = _setup(api, s, "one_cta", **kw)
     L = api.cav_num_levels(hg)
     Nc = api.cav_get_level_info(hg, L - 1)["N"]
     assert Nc == 16
@@ -46,6 +53,20 @@ def test_grid_factorisation_equals_one_cta(name):
     api.vcycle_apply(hg, torch_dev(r), v1)
     api.vcycle_apply(h1, torch_dev(r), v2)
     assert np.array_equal(host(v1), host(v2)), name
+
+
+def test_panel_and_column_kernels_agree_on_3073_unknowns():
+    from paper_2608_14310_b300 import api
+    rec = W.membrane_ellipse(64, 1e4)
+    s = api.ib_setup(rec)
+    kw = dict(coarsest_N=32, nu_pre=1, nu_post=1, alpha=0.85, precision="fp64")
+    hp = _setup(api, s, "panels", **kw)
+    hc = _setup(api, s, "columns", **kw)
+    b = W.rhs(32, 11)
+    z1, z2 = torch_dev(np.zeros(b.size)), torch_dev(np.zeros(b.size))
+    api.cav_coarse_solve(hp, torch_dev(b), z1)
+    api.cav_coarse_solve(hc, torch_dev(b), z2)
+    assert np.array_equal(host(z1), host(z2))
 
 
 def test_coarsest_32_against_oracle():

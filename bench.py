@@ -5,7 +5,9 @@ Metric: solves/s to a 1e-10 relative residual (||r||/||b||), one step = one FGMR
 of the elliptic-membrane system on a built hierarchy (the whole hot path: residuals,
 patch gathers, batched patch-inverse applies, weighted scatters, transfers, coarse solve,
 Arnoldi and Givens).  Set-up (E_E assembly, Galerkin levels, CAV sets, batched LU) is
-timed separately and reported as setup_ms and setup_plus_solve_per_s.
+timed separately and reported as setup_ms (cav_setup on an assembled system, the median of
+three calls after the first; setup_ms_first_call adds ib_setup and the process's first-call
+costs) and setup_plus_solve_per_s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -51,7 +53,7 @@ MAXIT = 150
 NCU_TRAFFIC = {
     # coloured: the 105 k_colour_step launches of one finest-level sweep, 422.50 MB read, 0 MB
     # written back within them (the iterate's writes stay in L2)
-    "coloured:fp32:256:colour.cu:abec06b1d07f7208": 422.50e6,
+    "coloured:fp32:256:colour.cu:3f8ca244c58eae2c": 422.51e6,
     # additive: one finest-level patch-apply launch (k_patch_apply_tma<float, 4, 8192>),
     # 289.65 MB read + 5.05 MB written
     "additive:fp32:256:sweep.cu:63b9c19db8897f36": 294.70e6,
@@ -801,7 +803,21 @@ def main():
                          autotune=True, **smoother_kw(args))
     e1.record()
     torch.cuda.synchronize()
-    setup_ms = e0.elapsed_time(e1)
+    setup_first_ms = e0.elapsed_time(e1)
+    # the set-up as a program that builds hierarchies repeatedly pays it (a Newton loop):
+    # three more cav_setup calls on the same system, the median reported
+    warm = []
+    torch.cuda.nvtx.range_push("warm_setup")  # lets a profiler select these set-ups
+    for _ in range(3):
+        e0.record()
+        hw = api.cav_setup(sysm, coarsest_N=args.coarsest, nu_pre=args.nu, nu_post=args.nu, alpha=args.alpha,
+                           precision=args.precision, autotune=True, **smoother_kw(args))
+        e1.record()
+        torch.cuda.synchronize()
+        warm.append(e0.elapsed_time(e1))
+        hw.close()
+    torch.cuda.nvtx.range_pop()
+    setup_ms = statistics.median(warm)
 
     def solve(bv, xv, loop=args.loop):
         return api.fgmres_solve(sysm, hier, bv, xv, rtol=1e-10, maxit=MAXIT, history=False, loop=loop)
@@ -989,6 +1005,7 @@ def main():
         "plain_fp64": plain,
         "other_smoothers": others,
         "setup_ms": setup_ms,
+        "setup_ms_first_call": setup_first_ms,
         "vcycle_ms": vcycle_ms,
         "sweep": add_sweep,
         "coloured_sweep": ({"level": 0, "ms": head_sweep_ms, "colour_classes": ncol0,

@@ -1002,7 +1002,9 @@ static void vcycle_level(const cav_hierarchy* H, int l, const double* b, double*
       launch_k(k_remove_mean, dim3(nblk), dim3(256), 0, st, true, lv.N, lv.n_partial, (const double*)lv.partial,
                x + 2 * NN);
     } else {
-      level_sweep(H, l, b, x, false, st);  // nu_post = 0: one more full sweep to fix the gauge
+      // nu_post = 0: the prolonged correction carries the coarse levels' pressure mean (they
+      // skip the removal, which K_E cannot see); take the mean of x's pressure itself
+      pressure_mean_remove(lv.N, lv.partial, x + 2 * NN, st);
     }
   }
 }

@@ -178,3 +178,32 @@ def test_diverging_fp32_multiplicative_sweep_stops_cleanly():
     assert info["converged"] == 0 and info["iters"] < 20, info
     assert "not finite" in api._lib.ib_last_error().decode()
     assert np.isfinite(host(x)).all()
+
+
+@pytest.mark.parametrize("nu_pre,nu_post", [(1, 0), (0, 1)])
+def test_hybrid_vcycle_with_one_sided_finest_smoothing(nu_pre, nu_post):
+    # the same hybrid V-cycle with sweeps on one side of the finest level only: with no
+    # post-sweep the cycle's output is the pre-smoothed iterate plus the prolonged correction,
+    # whose pressure mean the oracle's coarse levels removed after each of their sweeps
+    from paper_2608_14310_b300 import api
+    rec = W.membrane_ellipse(32, 1e4)
+    levels = omg.build_hierarchy(rec, 8, "cav")
+    L = len(levels) - 1
+    modes = ["coloured"] + ["additive"] * (L - 1)
+    pre = [nu_pre] + [2] * (L - 1)
+    post = [nu_post] + [2] * (L - 1)
+    sys_, h = gpu_hierarchy(rec, kind="cav", coarsest_N=8, nu_pre=nu_pre, nu_post=nu_post, alpha=0.85,
+                            precision="fp64", smoother="coloured", coloured_levels=1, nu_additive=2)
+    b = rec.rhs()
+    z = torch_dev(np.zeros(b.size))
+    api.vcycle_apply(h, torch_dev(b), z)
+    want = omg.vcycle(levels, b, pre, post, modes, 0.85)
+    assert rel(host(z), want) <= 1e-10
+    x = torch_dev(np.zeros(b.size))
+    info = api.fgmres_solve(sys_, h, torch_dev(b), x, rtol=1e-10, maxit=150)
+    K = levels[0].KE
+    _, io = ofg.fgmres(lambda v: K @ v, b, lambda r: omg.vcycle(levels, r, pre, post, modes, 0.85),
+                       rtol=1e-10, maxit=150)
+    assert info["converged"] == 1 and io["converged"]
+    assert abs(info["iters"] - io["iters"]) <= 1, (info["iters"], io["iters"])
+    print(f"membrane32 hybrid {nu_pre}+{nu_post}: gpu its {info['iters']} oracle its {io['iters']}")

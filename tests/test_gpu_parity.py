@@ -182,3 +182,18 @@ def test_fgmres(pair):
     assert np.linalg.norm(b - K @ xg) <= 2e-10 * np.linalg.norm(b)
     assert rel(xg, xo) <= 1e-8
     print(f"{pair.name}: gpu its {info['iters']} oracle its {io['iters']} relres {info['relres_true']:.2e}")
+
+
+def test_vcycle_without_post_sweeps():
+    # the additive V-cycle with pre-sweeps only (nu_post = 0) on every level: the output is the
+    # pre-smoothed iterate plus the prolonged correction, with a mean-free pressure as in the
+    # oracle, whose every sweep and coarse solve leave the pressure mean-free
+    from paper_2608_14310_b300 import api
+    rec = W.membrane_ellipse(32, 1e4)
+    levels = omg.build_hierarchy(rec, 8, "cav")
+    _, h = gpu_hierarchy(rec, kind="cav", coarsest_N=8, nu_pre=2, nu_post=0, alpha=ALPHA, precision="fp64")
+    b = rec.rhs()
+    z = torch_dev(np.zeros(b.size))
+    api.vcycle_apply(h, torch_dev(b), z)
+    want = omg.vcycle(levels, b, 2, 0, "additive", ALPHA)
+    assert rel(host(z), want) <= 1e-10

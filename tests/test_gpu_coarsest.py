@@ -88,22 +88,24 @@ def test_coarsest_32_against_oracle():
     assert info["converged"] == 1, info
 
 
-def test_bench_solve_with_coarsest_32():
-    """The bench's solve (N = 256 membrane, FP32 inverses, coloured finest level 1+1, additive
-    4+4 below, 32 x 32 coarsest) reaches 1e-10 in the oracle's own iteration count for the same
-    V-cycle (tests/golden/bench_oracle_iterations.json, written by the oracle alone), within one."""
+@pytest.mark.parametrize("form,nu_pre,nu_post", [("coloured_finest", 1, 1), ("coloured_finest_post_only", 0, 1)])
+def test_bench_solve_with_coarsest_32(form, nu_pre, nu_post):
+    """The bench's solve (N = 256 membrane, FP32 inverses, coloured finest level 1+1 or 0+1,
+    additive 4+4 below, 32 x 32 coarsest) reaches 1e-10 in the oracle's own iteration count for
+    the same V-cycle (tests/golden/bench_oracle_iterations.json, written by the oracle alone),
+    within one."""
     import json
     import os as _os
     from paper_2608_14310_b300 import api
     with open(_os.path.join(_os.path.dirname(__file__), "golden", "bench_oracle_iterations.json")) as f:
-        golden = json.load(f)["coarsest_32"]["coloured_finest"]["iters"]
+        golden = json.load(f)["coarsest_32"][form]["iters"]
     rec = W.config2(256, 1e4)
     s = api.ib_setup(rec)
-    h = api.cav_setup(s, coarsest_N=32, nu_pre=1, nu_post=1, alpha=0.85, precision="fp32", smoother="coloured",
-                      coloured_levels=1, nu_additive=4)
+    h = api.cav_setup(s, coarsest_N=32, nu_pre=nu_pre, nu_post=nu_post, alpha=0.85, precision="fp32",
+                      smoother="coloured", coloured_levels=1, nu_additive=4)
     x = torch_dev(np.zeros(3 * 256 * 256))
     info = api.fgmres_solve(s, h, torch_dev(rec.rhs()), x, rtol=1e-10, maxit=150, loop="device")
-    print(f"bench solve, 32 x 32 coarsest: {info['iters']} iterations (oracle {golden}), "
+    print(f"bench solve {nu_pre}+{nu_post}, 32 x 32 coarsest: {info['iters']} iterations (oracle {golden}), "
           f"true relres {info['relres_true']:.2e}")
     assert info["converged"] == 1 and info["relres_true"] <= 1e-10
     assert abs(info["iters"] - golden) <= 1

@@ -193,3 +193,30 @@ def test_paper_beam_unpreconditioned_fails():
     _, info = fgmres.fgmres(lambda v: K @ v, ib.first_step_rhs(s), lambda r: r, rtol=1e-10,
                             maxit=150, ref="r0")
     assert not info["converged"]
+
+
+def test_pressure_prolongation_keeps_the_mean():
+    # bilinear prolongation on the periodic grid: every coarse cell hands out weights
+    # 4 x 9/16 + 8 x 3/16 + 4 x 1/16 = 4 over its four children and their neighbours, so the
+    # fine mean equals the coarse mean (a column sum of exactly 4, independent of the field)
+    Nc = 8
+    Pp = multigrid.prolong_pressure(Nc)
+    assert np.allclose(np.asarray(Pp.sum(axis=0)).ravel(), 4.0)
+    pc = np.random.default_rng(3).standard_normal(Nc * Nc)
+    assert abs((Pp @ pc).mean() - pc.mean()) <= 1e-14
+
+
+@pytest.mark.parametrize("pre,post,mode", [(2, 0, "additive"), (0, 1, "additive"), (1, 1, "coloured"),
+                                           ([0, 2], [1, 2], ["coloured", "additive"]),
+                                           ([1, 2], [0, 2], ["coloured", "additive"])])
+def test_vcycle_output_pressure_is_mean_free(pre, post, mode):
+    # every sweep ends by removing the mean pressure (Sec. 3.3), the bordered coarsest solve
+    # returns a mean-free pressure and prolongation keeps the mean, so the cycle's output is
+    # mean-free whichever side the finest level's sweeps sit on
+    s = W.membrane_ellipse(32, 1e4)
+    levels = multigrid.build_hierarchy(s, 8, "cav")
+    b = s.rhs()
+    z = multigrid.vcycle(levels, b, pre, post, mode, 0.85)
+    p = z[2 * 32 * 32:]
+    assert np.abs(p).max() > 0.0
+    assert abs(p.mean()) <= 1e-13 * np.abs(p).max()
